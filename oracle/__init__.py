@@ -1,0 +1,415 @@
+"""FP64 CPU oracle for the real-space / imaginary-time GW sweep (arXiv:1911.05633).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library and its
+Python binding never call it, and it shares no code with them: its inputs come
+from the seeded generator ``synth`` only.
+
+Plain NumPy / SciPy in float64 (complex128), written for clarity, not speed.
+Every function follows one statement of the paper, cited in its docstring:
+
+* Sec. 2, "basic approximation" (Fig. 1): two-point functions F^R_{rr'} are kept
+  only for |R + r - r'| <= R_max, and the k-mesh must be at least the number of
+  cells the R_max sphere encloses or crosses.  -> ``kmesh_rule``, ``pair_list``
+* Sec. 2, transformations between R and k spaces over the kept pairs
+  -> ``fourier_k_to_R``, ``fourier_R_to_k``
+* Eq. P_MM with the sign and the tau pairing of Eq. P_II -> ``polarizability_R``
+  and the momentum route of Eq. P_old -> ``polarizability_q_kspace``
+* Eq. W_1 (W = V + V P W, with W~ = W - V) -> ``screened_W``
+* Eq. S_MM (dynamic part) and the exchange rule stated after Eq. P_II
+  (W~(tau) -> V, G(tau) -> -G(beta)) -> ``self_energy_R``, ``exchange_R``,
+  and the momentum route of Eq. S_old -> ``self_energy_k_kspace``
+* Appendix A, the sparse Matsubara grid: tau <-> i omega transforms, read as
+  exact Fourier integrals of the polynomial that interpolates the tau nodes
+  -> ``fourier_matrix``, ``inverse_matrix``
+
+Readings where the paper is silent or garbled (each listed in the design notes):
+P(x, x'; tau) = -s G(x, x'; tau) G(x', x; beta - tau) and G(x', x) = G(x, x')^*;
+Sigma(x, x'; tau) = -G(x, x'; tau) W~(x, x'; tau) (the G_{tL;t'L'} of Eq. S_MM
+is read as G_{tL'';t'L'''}); pair classes are taken modulo the k-mesh
+supercell with minimum-image distances.
+
+Parity pins for every function live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+from scipy.special import roots_legendre
+
+__all__ = [
+    "kmesh_rule",
+    "pair_list",
+    "green0_k_tau",
+    "fourier_k_to_R",
+    "fourier_R_to_k",
+    "polarizability_R",
+    "polarizability_q_kspace",
+    "fourier_matrix",
+    "inverse_matrix",
+    "transform",
+    "screened_W",
+    "self_energy_R",
+    "exchange_R",
+    "self_energy_k_kspace",
+    "OracleSystem",
+]
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2: cutoff sphere, k-mesh rule and the pair list
+# ----------------------------------------------------------------------------
+
+def kmesh_rule(lattice: np.ndarray, rmax: float) -> Tuple[int, int, int]:
+    """Smallest k-mesh with no periodic image inside the R_max sphere (Sec. 2, Fig. 1).
+
+    Along a_i the sphere (diameter 2 R_max) can meet at most ceil(2 R_max / d_i) + 1
+    cells, d_i = V / |a_j x a_k| being the spacing of the lattice planes that a_i
+    crosses; the mesh needs at least that many points along b_i.
+    """
+    A = np.asarray(lattice, dtype=np.float64)
+    vol = abs(float(np.linalg.det(A)))
+    out = []
+    for i in range(3):
+        j, k = (i + 1) % 3, (i + 2) % 3
+        d = vol / float(np.linalg.norm(np.cross(A[j], A[k])))
+        out.append(int(math.ceil(2.0 * rmax / d - 1e-12)) + 1)
+    return tuple(out)
+
+
+def pair_list(lattice: np.ndarray, frac: np.ndarray, kmesh: Sequence[int], cutoff: float) -> np.ndarray:
+    """Kept pair entries (a, b, class) with their minimum-image lattice vector.
+
+    For every ordered atom pair (a, b) and every lattice class c (R modulo the
+    k-mesh supercell, c_i in [0, N_i)), the image R = c + N*m closest to the
+    pair, |R + t_b - t_a| minimal, represents the class; the entry is kept when
+    that distance is <= cutoff (every class is kept when cutoff <= 0).  Ties
+    (squared distances within 1e-9 bohr^2) go to the lexicographically smallest
+    R.  Rows: (a, b, c1, c2, c3, R1, R2, R3), sorted by (a, b, c).
+    """
+    A = np.asarray(lattice, dtype=np.float64)
+    frac = np.asarray(frac, dtype=np.float64)
+    N = np.asarray(kmesh, dtype=np.int64)
+    rows = []
+    for a in range(len(frac)):
+        for b in range(len(frac)):
+            d0 = frac[b] - frac[a]
+            for c in np.ndindex(*[int(x) for x in N]):
+                best = None
+                for m in np.ndindex(5, 5, 5):
+                    R = np.array(c, dtype=np.int64) + N * (np.array(m, dtype=np.int64) - 2)
+                    x = (R.astype(np.float64) + d0) @ A
+                    d2 = float(x @ x)
+                    key = (d2, tuple(int(v) for v in R))
+                    if best is None or d2 < best[0] - 1e-9 or (abs(d2 - best[0]) <= 1e-9 and key[1] < best[1]):
+                        best = key
+                if cutoff <= 0.0 or math.sqrt(best[0]) <= cutoff:
+                    rows.append((a, b) + tuple(int(v) for v in c) + best[1])
+    return np.array(rows, dtype=np.int64).reshape(-1, 8)
+
+
+def _class_phase(kint: np.ndarray, kmesh: Sequence[int], cls: np.ndarray) -> np.ndarray:
+    """e^{+i k.R} on the mesh, k = sum (m_i/N_i) b_i, for integer k-indices and classes."""
+    N = np.asarray(kmesh, dtype=np.float64)
+    arg = 2.0 * np.pi * ((kint.astype(np.float64) / N) @ cls.astype(np.float64).T)
+    return np.exp(1j * arg)
+
+
+# ----------------------------------------------------------------------------
+# the non-interacting input, written independently of the generator
+# ----------------------------------------------------------------------------
+
+def green0_k_tau(H_k: np.ndarray, mu: float, beta: float, tau: np.ndarray) -> np.ndarray:
+    """G0(k, tau) = -e^{-(H - mu) tau} (1 + e^{-beta (H - mu)})^{-1}, 0+ <= tau <= beta-.
+
+    (The Hartree-level G0 entering Eq. G_1.)  Evaluated in the eigenbasis with
+    both exponentials combined into one bounded factor per level; valid for
+    tau in (-beta, beta) too, where G0(tau) = -G0(tau + beta) for tau < 0.
+    """
+    e, U = np.linalg.eigh(H_k)
+    xi = e - mu
+    out = np.empty((H_k.shape[0], len(tau)) + H_k.shape[1:], np.complex128)
+    for i, t in enumerate(np.asarray(tau, dtype=np.float64)):
+        if t < 0.0:
+            d = +_occ_factor(xi, t + beta, beta)   # G0(tau) = -G0(tau + beta)
+        else:
+            d = -_occ_factor(xi, t, beta)
+        out[:, i] = np.einsum("kij,kj,klj->kil", U, d, U.conj())
+    return out
+
+
+def _occ_factor(xi: np.ndarray, t: float, beta: float) -> np.ndarray:
+    # e^{-xi t}/(1+e^{-beta xi}) = 1/(e^{xi t} + e^{xi (t - beta)})
+    a = np.clip(xi * t, -700, 700)
+    b = np.clip(xi * (t - beta), -700, 700)
+    return 1.0 / (np.exp(a) + np.exp(b))
+
+
+# ----------------------------------------------------------------------------
+# Sec. 2: R <-> k transforms restricted to the kept entries
+# ----------------------------------------------------------------------------
+
+def fourier_k_to_R(F_k: np.ndarray, entries: np.ndarray, kmesh, row_off, col_off) -> List[np.ndarray]:
+    """F_ab(R) = (1/N_k) sum_k e^{-i k.R} F_ab(k) for each kept entry (brute force).
+
+    F_k: [N_k][n_slices][N][N].  Returns a list over entries of [n_slices][n_a][n_b].
+    """
+    kint = np.array(list(np.ndindex(*kmesh)), dtype=np.int64)
+    ph = _class_phase(kint, kmesh, entries[:, 2:5])  # [N_k][E]
+    nk = len(kint)
+    out = []
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        blk = F_k[:, :, row_off[a]:row_off[a + 1], col_off[b]:col_off[b + 1]]
+        out.append(np.einsum("k,ksij->sij", np.conj(ph[:, e]), blk) / nk)
+    return out
+
+
+def fourier_R_to_k(F_R: Sequence[np.ndarray], entries: np.ndarray, kmesh, row_off, col_off) -> np.ndarray:
+    """F_ab(k) = sum_{kept R} e^{+i k.R} F_ab(R) (brute force), dense [N_k][n_slices][N][N]."""
+    kint = np.array(list(np.ndindex(*kmesh)), dtype=np.int64)
+    ph = _class_phase(kint, kmesh, entries[:, 2:5])
+    ns = F_R[0].shape[0]
+    out = np.zeros((len(kint), ns, row_off[-1], col_off[-1]), np.complex128)
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        out[:, :, row_off[a]:row_off[a + 1], col_off[b]:col_off[b + 1]] += (
+            ph[:, e][:, None, None, None] * F_R[e][None])
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Eq. P_MM (MT-MT polarizability) and Eq. P_old (momentum route)
+# ----------------------------------------------------------------------------
+
+def polarizability_R(G_R: Sequence[np.ndarray], entries: np.ndarray, C_atom: Sequence[np.ndarray],
+                     spin: int = 2) -> List[np.ndarray]:
+    """P_{aK, bK'}(R, tau_i) per kept entry (Eq. P_MM, sign and pairing of Eq. P_II).
+
+    P = -s sum_{L L'' L' L'''} C^a_{K; L L''} G_{aL, bL'}(R, tau_i)
+            conj(G_{aL'', bL'''}(R, beta - tau_i)) C^b_{K'; L' L'''},
+    beta - tau_i being the mirrored node tau_{N-1-i}.
+    """
+    out = []
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        G = G_R[e]
+        Gm = np.conj(G[::-1])
+        P = -spin * np.einsum("kAB,tAC,tBD,qCD->tkq", C_atom[a], G, Gm, C_atom[b], optimize=True)
+        out.append(P)
+    return out
+
+
+def polarizability_q_kspace(G_k: np.ndarray, C_atom, orb_off, pb_off, kmesh, spin: int = 2) -> np.ndarray:
+    """P_ab(q, tau_i) = -(s/N_k) sum_k C^a [G_ab(k, tau_i) (x) conj G_ab(k - q, beta - tau_i)] C^b.
+
+    The momentum-space convolution of Eq. P_old, evaluated at the tau nodes
+    (every pair class included).  Returns dense [N_k][N_tau][N_PB][N_PB].
+    """
+    kint = np.array(list(np.ndindex(*kmesh)), dtype=np.int64)
+    N = np.asarray(kmesh, dtype=np.int64)
+    index = {tuple(k): i for i, k in enumerate(kint)}
+    nk, nt = G_k.shape[0], G_k.shape[1]
+    nat = len(orb_off) - 1
+    out = np.zeros((nk, nt, pb_off[-1], pb_off[-1]), np.complex128)
+    for iq, q in enumerate(kint):
+        for ik, k in enumerate(kint):
+            ikq = index[tuple(int(v) for v in np.mod(k - q, N))]
+            for a in range(nat):
+                for b in range(nat):
+                    G1 = G_k[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]]
+                    G2 = np.conj(G_k[ikq, ::-1, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]])
+                    out[iq, :, pb_off[a]:pb_off[a + 1], pb_off[b]:pb_off[b + 1]] += np.einsum(
+                        "kAB,tAC,tBD,qCD->tkq", C_atom[a], G1, G2, C_atom[b], optimize=True)
+    return -spin * out / nk
+
+
+# ----------------------------------------------------------------------------
+# Appendix A: tau <-> i omega on the sparse Matsubara grid
+# ----------------------------------------------------------------------------
+
+def _barycentric_weights(x: np.ndarray) -> np.ndarray:
+    n = len(x)
+    w = np.ones(n)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                w[i] /= (x[i] - x[j])
+    return w
+
+
+def _lagrange_at(xn: np.ndarray, w: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """l_i(x) for the interpolation nodes xn (second barycentric form), [len(x)][n]."""
+    d = x[:, None] - xn[None, :]
+    hit = d == 0.0
+    d[hit] = 1.0
+    t = w[None, :] / d
+    L = t / t.sum(axis=1, keepdims=True)
+    r, c = np.nonzero(hit)
+    L[r] = 0.0
+    L[r, c] = 1.0
+    return L
+
+
+def fourier_matrix(beta: float, tau: np.ndarray, idx: np.ndarray, statistics: str) -> np.ndarray:
+    """T[n, i] = int_0^beta e^{i w_n tau} l_i(tau) d tau, l_i the Lagrange polynomial
+    of the tau nodes; w_n = (2n+1) pi/beta ('F') or 2n pi/beta ('B').
+
+    A function known at the nodes is read as the polynomial through them, and
+    its transform is that polynomial's exact Fourier integral.  Gauss-Legendre
+    quadrature with enough points is exact up to rounding for this entire integrand.
+    """
+    tau = np.asarray(tau, dtype=np.float64)
+    x_n = 2.0 * tau / beta - 1.0
+    w = _barycentric_weights(x_n)
+    idx = np.asarray(idx, dtype=np.int64)
+    if statistics == "F":
+        a = (2 * idx + 1) * np.pi / 2.0
+    elif statistics == "B":
+        a = idx * np.pi * 1.0
+    else:
+        raise ValueError(statistics)
+    out = np.empty((len(idx), len(tau)), np.complex128)
+    M = int(len(tau) / 2 + 0.75 * np.max(np.abs(a)) + 48)
+    xg, wg = roots_legendre(M)
+    L = _lagrange_at(x_n, w, xg)  # [M][N]
+    for r, ar in enumerate(a):
+        # tau = beta (x + 1)/2 ; e^{i w tau} = e^{i a} e^{i a x}
+        out[r] = (0.5 * beta) * np.exp(1j * ar) * ((wg * np.exp(1j * ar * xg)) @ L)
+    return out
+
+
+def inverse_matrix(T: np.ndarray) -> np.ndarray:
+    """The least-squares inverse of T (its Moore-Penrose pseudo-inverse): the
+    polynomial on the tau nodes whose transform best fits the sampled values."""
+    return np.linalg.pinv(T, rcond=1e-15)
+
+
+def transform(T: np.ndarray, F: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Apply a tau/frequency matrix to each entry: out[e][m] = sum_i T[m, i] F[e][i]."""
+    return [np.einsum("mi,i...->m...", T, f) for f in F]
+
+
+# ----------------------------------------------------------------------------
+# Eq. W_1: screened interaction, W~ = (1 - v P)^{-1} v - v per (q, nu)
+# ----------------------------------------------------------------------------
+
+def screened_W(P_R_iw: Sequence[np.ndarray], entries: np.ndarray, v_q: np.ndarray, kmesh, pb_off,
+               nu_subset=None, q_subset=None):
+    """W~(R, i nu) on the kept entries (Eq. W_1 with W = V + W~).
+
+    P(q, i nu) = sum_{kept R} e^{+i q.R} P(R, i nu); W(q) solves
+    (I - v(q) P(q)) W = v(q) (Eq. W_1 rearranged), W~ = W - v; and
+    W~(R) = (1/N_k) sum_q e^{-i q.R} W~(q).  ``nu_subset``/``q_subset``
+    restrict the returned W~(q) (for sampled checks); W~(R) needs all q.
+    """
+    nk = v_q.shape[0]
+    n_nu = P_R_iw[0].shape[0]
+    P_q = fourier_R_to_k(P_R_iw, entries, kmesh, pb_off, pb_off)  # [N_k][N_nu][N][N]
+    I = np.eye(v_q.shape[1])
+    if q_subset is not None or nu_subset is not None:
+        qs = range(nk) if q_subset is None else q_subset
+        ns = range(n_nu) if nu_subset is None else nu_subset
+        return {(q, n): np.linalg.solve(I - v_q[q] @ P_q[q, n], v_q[q]) - v_q[q] for q in qs for n in ns}
+    Wt_q = np.empty_like(P_q)
+    for q in range(nk):
+        for n in range(n_nu):
+            Wt_q[q, n] = np.linalg.solve(I - v_q[q] @ P_q[q, n], v_q[q]) - v_q[q]
+    return fourier_k_to_R(Wt_q, entries, kmesh, pb_off, pb_off), Wt_q
+
+
+# ----------------------------------------------------------------------------
+# Eq. S_MM (dynamic part), the exchange rule, and Eq. S_old (momentum route)
+# ----------------------------------------------------------------------------
+
+def self_energy_R(G_R, Wt_R, entries, C_atom) -> List[np.ndarray]:
+    """Sigma_{aL, bL'}(R, tau_i) = -sum C^a_{K; L L''} G_{aL'', bL'''}(R, tau_i)
+    W~_{aK, bK'}(R, tau_i) C^b_{K'; L' L'''}  (Eq. S_MM, indices as read above)."""
+    out = []
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        out.append(-np.einsum("kLM,tMN,tkq,qPN->tLP", C_atom[a], G_R[e], Wt_R[e], C_atom[b], optimize=True))
+    return out
+
+
+def exchange_R(G_R, v_R, entries, C_atom) -> List[np.ndarray]:
+    """Static exchange: Eq. S_MM with W~(tau) -> v and G(tau) -> -G(beta-):
+    Sigma_x = +sum C^a G(R, beta-) v(R) C^b  (= -rho o v, the Fock term)."""
+    out = []
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        Gb = G_R[e][-1]
+        out.append(np.einsum("kLM,MN,kq,qPN->LP", C_atom[a], Gb, v_R[e], C_atom[b], optimize=True))
+    return out
+
+
+def self_energy_k_kspace(G_k: np.ndarray, Wt_q_tau: np.ndarray, C_atom, orb_off, pb_off, kmesh) -> np.ndarray:
+    """Sigma_ab(k, tau_i) = -(1/N_k) sum_q C^a [G_ab(k - q, tau_i) (x) W~_ab(q, tau_i)] C^b
+    (the momentum route of Eq. S_old, at the tau nodes, every pair class included)."""
+    kint = np.array(list(np.ndindex(*kmesh)), dtype=np.int64)
+    N = np.asarray(kmesh, dtype=np.int64)
+    index = {tuple(k): i for i, k in enumerate(kint)}
+    nk, nt = G_k.shape[0], G_k.shape[1]
+    nat = len(orb_off) - 1
+    out = np.zeros((nk, nt, orb_off[-1], orb_off[-1]), np.complex128)
+    for ik, k in enumerate(kint):
+        for iq, q in enumerate(kint):
+            ikq = index[tuple(int(v) for v in np.mod(k - q, N))]
+            for a in range(nat):
+                for b in range(nat):
+                    G = G_k[ikq, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]]
+                    W = Wt_q_tau[iq, :, pb_off[a]:pb_off[a + 1], pb_off[b]:pb_off[b + 1]]
+                    out[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]] -= np.einsum(
+                        "kLM,tMN,tkq,qPN->tLP", C_atom[a], G, W, C_atom[b], optimize=True)
+    return out / nk
+
+
+# ----------------------------------------------------------------------------
+# convenience: one whole sweep on a synthetic cell
+# ----------------------------------------------------------------------------
+
+class OracleSystem:
+    """Holds one synthetic cell's inputs and runs the oracle's steps in order."""
+
+    def __init__(self, cell, entries: np.ndarray = None):
+        self.cell = cell
+        self.kmesh = tuple(int(x) for x in cell.kmesh)
+        self.entries = pair_list(cell.lattice, cell.frac, self.kmesh, cell.cutoff) if entries is None else entries
+        self.orb_off = cell.orb_offsets
+        self.pb_off = cell.pb_offsets
+        self.C_atom = [cell.species[s].C for s in cell.species_of_atom]
+        self.spin = cell.spin
+        self.beta = cell.beta
+        self.tau = cell.tau
+        self.F_fwd = fourier_matrix(cell.beta, self.tau, cell.omega_idx, "F")
+        self.B_fwd = fourier_matrix(cell.beta, self.tau, cell.nu_idx, "B")
+        self.F_inv = inverse_matrix(self.F_fwd)
+        self.B_inv = inverse_matrix(self.B_fwd)
+
+    def v_R(self, v_class: np.ndarray) -> List[np.ndarray]:
+        out = []
+        for row in self.entries:
+            a, b = int(row[0]), int(row[1])
+            c = int(np.ravel_multi_index(tuple(row[2:5]), self.kmesh))
+            Ka = self.pb_off[a + 1] - self.pb_off[a]
+            Kb = self.pb_off[b + 1] - self.pb_off[b]
+            out.append(v_class[a, b, c, :Ka, :Kb].astype(np.complex128))
+        return out
+
+    def sweep(self, G_k: np.ndarray, v_q: np.ndarray, v_class: np.ndarray) -> dict:
+        r = {}
+        r["G_R"] = fourier_k_to_R(G_k, self.entries, self.kmesh, self.orb_off, self.orb_off)
+        r["P_R"] = polarizability_R(r["G_R"], self.entries, self.C_atom, self.spin)
+        r["P_iw"] = transform(self.B_fwd, r["P_R"])
+        r["Wt_iw"], r["Wt_q"] = screened_W(r["P_iw"], self.entries, v_q, self.kmesh, self.pb_off)
+        r["Wt_R"] = transform(self.B_inv, r["Wt_iw"])
+        r["v_R"] = self.v_R(v_class)
+        r["Sig_R"] = self_energy_R(r["G_R"], r["Wt_R"], self.entries, self.C_atom)
+        r["Sigx_R"] = exchange_R(r["G_R"], r["v_R"], self.entries, self.C_atom)
+        r["Sig_iw"] = transform(self.F_fwd, r["Sig_R"])
+        r["Sig_k"] = fourier_R_to_k(r["Sig_iw"], self.entries, self.kmesh, self.orb_off, self.orb_off)
+        r["Sigx_k"] = fourier_R_to_k([s[None] for s in r["Sigx_R"]], self.entries, self.kmesh,
+                                     self.orb_off, self.orb_off)[:, 0]
+        return r

@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks one oracle function against something other than itself:
+printed worked values, closed forms, an independent library routine, a second
+route through the same physics, or an invariant.  No GPU is needed.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------
+# k-mesh rule and pair list (Sec. 2, Fig. 1; worked values in Sec. 3 and Sec. 4)
+# ----------------------------------------------------------------------------
+
+def _fcc(a=10.26):
+    return 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+
+
+def test_kmesh_rule_printed_values():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "kmesh_rule.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        m = np.array([int(x) for x in r[:3]])
+        rmax = float(r[3])
+        want = tuple(int(x) for x in r[4:7])
+        lat = _fcc() * m[:, None]
+        assert oracle.kmesh_rule(lat, rmax) == want
+    # the totals printed in the paper
+    assert np.prod(oracle.kmesh_rule(_fcc(), 14.0)) == 216
+    assert np.prod(oracle.kmesh_rule(_fcc(), 10.0)) == 125
+    assert np.prod(oracle.kmesh_rule(_fcc() * np.array([4, 3, 3])[:, None], 10.0)) == 18
+
+
+def _brute_pairs(lat, frac, cutoff, span=4):
+    out = set()
+    for a in range(len(frac)):
+        for b in range(len(frac)):
+            for R in np.ndindex(2 * span + 1, 2 * span + 1, 2 * span + 1):
+                R = np.array(R) - span
+                if np.linalg.norm((R + frac[b] - frac[a]) @ lat) <= cutoff:
+                    out.add((a, b) + tuple(int(x) for x in R))
+    return out
+
+
+def test_pair_list_equals_brute_force_when_mesh_obeys_rule():
+    # simple cubic a = 5, two atoms, cutoff 9: rule gives ceil(18/5)+1 = 5 -> 5x5x5 is alias free
+    lat = np.eye(3) * 5.0
+    frac = np.array([[0, 0, 0], [0.5, 0.5, 0.5]])
+    assert oracle.kmesh_rule(lat, 9.0) == (5, 5, 5)
+    ent = oracle.pair_list(lat, frac, (5, 5, 5), 9.0)
+    got = {(int(r[0]), int(r[1]), int(r[5]), int(r[6]), int(r[7])) for r in ent}
+    assert got == _brute_pairs(lat, frac, 9.0)
+    assert len(got) == len(ent)
+    # class of the representative is the stored class
+    assert np.all(np.mod(ent[:, 5:8], 5) == ent[:, 2:5])
+
+
+def test_pair_list_diamond_count_and_symmetry():
+    cell = synth.make_config(1, build=False)
+    ent = oracle.pair_list(cell.lattice, cell.frac, cell.kmesh, cell.cutoff)
+    brute = _brute_pairs(cell.lattice, cell.frac, cell.cutoff, span=2)
+    assert len(ent) == len(brute) == 376
+    keys = {(int(r[0]), int(r[1]), int(r[5]), int(r[6]), int(r[7])) for r in ent}
+    for a, b, r1, r2, r3 in keys:
+        assert (b, a, -r1, -r2, -r3) in keys
+
+
+def test_pair_list_keeps_all_classes_without_cutoff():
+    cell = synth.make_config(0, build=False)
+    ent = oracle.pair_list(cell.lattice, cell.frac, cell.kmesh, 0.0)
+    assert len(ent) == 2 * 2 * 8
+    # a tie: classes at distance a from the same atom have two images (+-5); the smaller R wins
+    same = ent[(ent[:, 0] == 0) & (ent[:, 1] == 0)]
+    row = same[(same[:, 2] == 1) & (same[:, 3] == 0) & (same[:, 4] == 0)][0]
+    assert tuple(row[5:8]) == (-1, 0, 0)
+
+
+# ----------------------------------------------------------------------------
+# G0(k, tau): closed form against the matrix exponential, invariants
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cell0():
+    return synth.make_config(0)
+
+
+def test_green0_against_expm(cell0):
+    H = cell0.H_k
+    mu, beta = cell0.mu, 8.0  # moderate beta so that expm stays well scaled
+    tau = np.array([0.0, 0.7, 3.1, 8.0])
+    G = oracle.green0_k_tau(H, mu, beta, tau)
+    I = np.eye(H.shape[1])
+    for k in range(H.shape[0]):
+        h = H[k] - mu * I
+        inv = np.linalg.inv(I + expm(-beta * h))
+        for i, t in enumerate(tau):
+            ref = -expm(-t * h) @ inv
+            assert np.abs(G[k, i] - ref).max() < 1e-12
+
+
+def test_green0_invariants(cell0):
+    c = cell0
+    tau = c.tau
+    G = oracle.green0_k_tau(c.H_k, c.mu, c.beta, tau)
+    I = np.eye(c.n_orb_total)
+    # jump G(0+) + G(beta-) = -S^{-1} = -I
+    assert np.abs(G[:, 0] + G[:, -1] + I[None]).max() < 1e-13
+    # Hermitian at every tau
+    assert np.abs(G - G.conj().transpose(0, 1, 3, 2)).max() < 1e-14
+    # antiperiodicity G(tau - beta) = -G(tau)
+    t = np.array([3.3, 17.0, 41.2])
+    Gp = oracle.green0_k_tau(c.H_k, c.mu, c.beta, t)
+    Gm = oracle.green0_k_tau(c.H_k, c.mu, c.beta, t - c.beta)
+    assert np.abs(Gp + Gm).max() < 1e-13
+    # particle number: s * (1/N_k) sum_k tr rho(k) = N_e with rho = -G(beta-), half filling
+    n = c.spin * np.real(np.trace(-G[:, -1], axis1=1, axis2=2)).sum() / c.n_k
+    e = np.linalg.eigvalsh(c.H_k)
+    nref = c.spin * synth.fermi(e - c.mu, c.beta).sum() / c.n_k
+    assert abs(n - nref) < 1e-12
+    assert abs(n - c.n_orb_total) < 1e-6
+    # the generator's input G is this G0
+    assert np.abs(c.green_k_tau() - G).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# R <-> k transforms against numpy's FFT and a round trip
+# ----------------------------------------------------------------------------
+
+def test_fourier_matches_fft_and_round_trips(cell0):
+    c = cell0
+    ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
+    G = oracle.green0_k_tau(c.H_k, c.mu, c.beta, c.tau[:3])
+    oo = c.orb_offsets
+    GR = oracle.fourier_k_to_R(G, ent, c.kmesh, oo, oo)
+    # numpy FFT of the (a, b) = (0, 1) block: F(R) = (1/N) sum_k e^{-ikR} F(k) = ifftn over k
+    blk = G[:, :, oo[0]:oo[1], oo[1]:oo[2]].reshape(c.kmesh + (3, 4, 4))
+    ref = np.fft.ifftn(blk, axes=(0, 1, 2))
+    for e, row in enumerate(ent):
+        if row[0] == 0 and row[1] == 1:
+            assert np.abs(GR[e] - ref[tuple(row[2:5])]).max() < 1e-15
+    back = oracle.fourier_R_to_k(GR, ent, c.kmesh, oo, oo)
+    assert np.abs(back - G).max() < 1e-14
+    # Hermiticity in R: G_ba(-R) = G_ab(R)^dagger
+    key = {(int(r[0]), int(r[1]), tuple(int(x) for x in r[2:5])): e for e, r in enumerate(ent)}
+    for e, r in enumerate(ent):
+        mc = tuple(int(x) for x in np.mod(-r[2:5], c.kmesh))
+        e2 = key[(int(r[1]), int(r[0]), mc)]
+        assert np.abs(GR[e2] - GR[e].conj().transpose(0, 2, 1)).max() < 1e-15
+
+
+# ----------------------------------------------------------------------------
+# polarizability: Lindhard closed form, second route, invariants
+# ----------------------------------------------------------------------------
+
+def test_polarizability_lindhard_chain_tau():
+    ch = synth.chain_cell(n_cells_k=8, beta=20.0, n_tau=24)
+    ent = oracle.pair_list(ch.lattice, ch.frac, ch.kmesh, 0.0)
+    G = oracle.green0_k_tau(ch.H_k, ch.mu, ch.beta, ch.tau)
+    GR = oracle.fourier_k_to_R(G, ent, ch.kmesh, [0, 1], [0, 1])
+    PR = oracle.polarizability_R(GR, ent, [np.ones((1, 1, 1))], spin=2)
+    Pq = oracle.fourier_R_to_k(PR, ent, ch.kmesh, [0, 1], [0, 1])[:, :, 0, 0]
+    xi = np.linalg.eigvalsh(ch.H_k)[:, 0] - ch.mu
+    f = synth.fermi(xi, ch.beta)
+    N = ch.n_k
+    for q in range(N):
+        for i, t in enumerate(ch.tau):
+            ref = 0.0
+            for k in range(N):
+                kq = (k - q) % N
+                # (1 - f_k) e^{-xi_k t} f_kq e^{+xi_kq t}, each factor in its bounded form
+                ref += (1.0 / (math.exp(xi[k] * t) + math.exp(xi[k] * (t - ch.beta)))
+                        / (math.exp(xi[kq] * (ch.beta - t)) + math.exp(-xi[kq] * t)))
+            ref *= -2.0 / N
+            assert abs(Pq[q, i] - ref) < 1e-14 * max(1.0, abs(ref)) * 4
+
+
+def test_polarizability_real_space_equals_kspace_route(cell0):
+    c = cell0
+    ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
+    G = c.green_k_tau()
+    oo, po = c.orb_offsets, c.pb_offsets
+    C = [c.species[s].C for s in c.species_of_atom]
+    PR = oracle.polarizability_R(oracle.fourier_k_to_R(G, ent, c.kmesh, oo, oo), ent, C)
+    Pq_real = oracle.fourier_R_to_k(PR, ent, c.kmesh, po, po)
+    Pq_k = oracle.polarizability_q_kspace(G, C, oo, po, c.kmesh)
+    assert np.abs(Pq_real - Pq_k).max() < 1e-14 * np.abs(Pq_k).max() * 10
+
+
+def test_polarizability_invariants(cell0):
+    c = cell0
+    ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
+    G = c.green_k_tau()
+    oo, po = c.orb_offsets, c.pb_offsets
+    C = [c.species[s].C for s in c.species_of_atom]
+    PR = oracle.polarizability_R(oracle.fourier_k_to_R(G, ent, c.kmesh, oo, oo), ent, C)
+    scale = max(np.abs(p).max() for p in PR)
+    key = {(int(r[0]), int(r[1]), tuple(int(x) for x in r[2:5])): e for e, r in enumerate(ent)}
+    for e, r in enumerate(ent):
+        # P(beta - tau) = P(tau)^* for C symmetric in (L, L'')
+        assert np.abs(PR[e][::-1] - PR[e].conj()).max() < 1e-14 * scale
+        # P_ba(-R) = P_ab(R)^dagger
+        e2 = key[(int(r[1]), int(r[0]), tuple(int(x) for x in np.mod(-r[2:5], c.kmesh)))]
+        assert np.abs(PR[e2] - PR[e].conj().transpose(0, 2, 1)).max() < 1e-14 * scale
+    # P(q, i nu = 0) is Hermitian negative semidefinite
+    B = oracle.fourier_matrix(c.beta, c.tau, np.array([0]), "B")
+    P0 = oracle.fourier_R_to_k(oracle.transform(B, PR), ent, c.kmesh, po, po)[:, 0]
+    for q in range(c.n_k):
+        assert np.abs(P0[q] - P0[q].conj().T).max() < 1e-12 * np.abs(P0[q]).max()
+        assert np.linalg.eigvalsh(0.5 * (P0[q] + P0[q].conj().T)).max() < 1e-10 * np.abs(P0[q]).max()
+
+
+def test_polarizability_complete_product_basis():
+    # K = n^2 and C_{(L1 L2); L L''} = delta_{L1 L} delta_{L2 L''}: P is the orbital product
+    rng = np.random.default_rng(3)
+    n, nt = 3, 6
+    G = rng.standard_normal((nt, n, n)) + 1j * rng.standard_normal((nt, n, n))
+    C = np.zeros((n * n, n, n))
+    for L1 in range(n):
+        for L2 in range(n):
+            C[L1 * n + L2, L1, L2] = 1.0
+    ent = np.array([[0, 0, 0, 0, 0, 0, 0, 0]])
+    P = oracle.polarizability_R([G], ent, [C], spin=2)[0]
+    for t in range(nt):
+        assert np.abs(P[t] + 2.0 * np.kron(G[t], np.conj(G[nt - 1 - t]))).max() < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# tau <-> i omega matrices: exactness on polynomials, high precision, round trip
+# ----------------------------------------------------------------------------
+
+def _poly_moment(m, w, beta):
+    """int_0^beta tau^m e^{i w tau} d tau by repeated integration by parts (w != 0)."""
+    iw = 1j * w
+    s = 0.0
+    for j in range(m + 1):
+        s += (-1) ** j * math.factorial(m) / math.factorial(m - j) * beta ** (m - j) / iw ** (j + 1)
+    val = np.exp(iw * beta) * s - (-1) ** m * math.factorial(m) / iw ** (m + 1)
+    return val
+
+
+@pytest.mark.parametrize("stat", ["F", "B"])
+def test_transform_exact_on_polynomials(stat):
+    beta, N = 37.0, 24
+    tau = synth.tau_nodes(beta, N)
+    fer, bos = synth.matsubara_sets(N)
+    idx = fer if stat == "F" else bos
+    T = oracle.fourier_matrix(beta, tau, idx, stat)
+    for m in range(5):
+        g = tau ** m
+        got = T @ g
+        for r, n in enumerate(idx):
+            w = (2 * n + 1) * np.pi / beta if stat == "F" else 2 * n * np.pi / beta
+            ref = beta ** (m + 1) / (m + 1) if w == 0 else _poly_moment(m, w, beta)
+            assert abs(got[r] - ref) < 1e-12 * beta ** (m + 1)
+
+
+def test_transform_matrix_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    beta, N = 50.0, 12
+    tau = synth.tau_nodes(beta, N)
+    idx = np.array([-7, 0, 3, 40])
+    T = oracle.fourier_matrix(beta, tau, idx, "F")
+    xs = [mp.mpf(2) * mp.mpf(t) / beta - 1 for t in tau]
+    xs[0], xs[-1] = mp.mpf(-1), mp.mpf(1)
+    for r, n in enumerate(idx):
+        a = mp.mpf(2 * int(n) + 1) * mp.pi / 2
+        for i in (0, 3, N - 1):
+            def li(x, i=i):
+                p = mp.mpf(1)
+                for j in range(N):
+                    if j != i:
+                        p *= (x - xs[j]) / (xs[i] - xs[j])
+                return p
+            val = mp.quad(lambda x: mp.expj(a * x) * li(x), mp.linspace(-1, 1, 9))
+            ref = complex(mp.mpf(beta) / 2 * mp.expj(a) * val)
+            assert abs(T[r, i] - ref) < 1e-13 * beta
+
+
+def test_transform_round_trip_and_conditioning():
+    for N in (24, 48, 64):
+        tau = synth.tau_nodes(1000.0, N)
+        fer, bos = synth.matsubara_sets(N)
+        for idx, st in ((fer, "F"), (bos, "B")):
+            T = oracle.fourier_matrix(1000.0, tau, idx, st)
+            U = oracle.inverse_matrix(T)
+            assert np.abs(U @ T - np.eye(N)).max() < 1e-11
+            assert np.linalg.cond(T) < 1e4
+
+
+def test_transform_converges_to_single_pole():
+    # g(tau) = -e^{-xi tau}/(1+e^{-beta xi}) has g(i w_n) = 1/(i w_n - xi)
+    beta, xi = 10.0, 0.3
+    for N, tol in ((24, 1e-3), (48, 1e-6), (64, 1e-9)):
+        tau = synth.tau_nodes(beta, N)
+        fer, _ = synth.matsubara_sets(N)
+        T = oracle.fourier_matrix(beta, tau, fer, "F")
+        g = -np.exp(-xi * tau) / (1 + np.exp(-beta * xi))
+        w = (2 * fer + 1) * np.pi / beta
+        err = np.abs(T @ g - 1.0 / (1j * w - xi)).max()
+        assert err < tol, (N, err)
+
+
+# ----------------------------------------------------------------------------
+# screened interaction
+# ----------------------------------------------------------------------------
+
+def _one_entry_system(v, P):
+    """One atom, one pair class, K x K blocks: P(q) = P(R=0), W~(R=0) = W~(q)."""
+    ent = np.array([[0, 0, 0, 0, 0, 0, 0, 0]])
+    return ent, [P[None]], v[None]
+
+
+def test_screened_W_scalar_closed_form():
+    v, p = 0.7, -0.35
+    ent, PR, vq = _one_entry_system(np.array([[v]], complex), np.array([[p]], complex))
+    WR, _ = oracle.screened_W(PR, ent, vq, (1, 1, 1), [0, 1])
+    assert abs(WR[0][0, 0, 0] - v * v * p / (1 - v * p)) < 1e-15
+
+
+def test_screened_W_neumann_series():
+    rng = np.random.default_rng(5)
+    K = 6
+    A = rng.standard_normal((K, K))
+    v = (A @ A.T / K + np.eye(K)).astype(complex)
+    P = 1e-4 * (rng.standard_normal((K, K)) + 1j * rng.standard_normal((K, K)))
+    ent, PR, vq = _one_entry_system(v, P)
+    WR, _ = oracle.screened_W(PR, ent, vq, (1, 1, 1), [0, K])
+    ref = v @ P @ v + v @ P @ v @ P @ v
+    assert np.abs(WR[0][0] - ref).max() < 10 * np.abs(v @ P @ v @ P @ v @ P @ v).max()
+    # the leading term alone misses the second order by its size
+    assert np.abs(WR[0][0] - v @ P @ v).max() > 0.5 * np.abs(v @ P @ v @ P @ v).max()
+
+
+def test_screened_W_screens_static(cell0):
+    # P(q, 0) <= 0 and v > 0 give W(q, 0) = v + W~ <= v  (screening)
+    c = cell0
+    ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
+    sysm = oracle.OracleSystem(c, ent)
+    vq, vc = c.coulomb()
+    G = c.green_k_tau()
+    PR = oracle.polarizability_R(oracle.fourier_k_to_R(G, ent, c.kmesh, c.orb_offsets, c.orb_offsets), ent, sysm.C_atom)
+    i0 = int(np.nonzero(c.nu_idx == 0)[0][0])
+    Piw = [x[i0:i0 + 1] for x in oracle.transform(sysm.B_fwd, PR)]
+    _, Wq = oracle.screened_W(Piw, ent, vq, c.kmesh, c.pb_offsets)
+    for q in range(c.n_k):
+        Wt = Wq[q, 0]
+        assert np.linalg.eigvalsh(0.5 * (Wt + Wt.conj().T)).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# self-energy: Fock closed form, second route, invariants
+# ----------------------------------------------------------------------------
+
+def test_exchange_fock_chain():
+    ch = synth.chain_cell(n_cells_k=8, beta=20.0, n_tau=12)
+    ent = oracle.pair_list(ch.lattice, ch.frac, ch.kmesh, 0.0)
+    G = oracle.green0_k_tau(ch.H_k, ch.mu, ch.beta, ch.tau)
+    GR = oracle.fourier_k_to_R(G, ent, ch.kmesh, [0, 1], [0, 1])
+    N = ch.n_k
+    vcls = np.array([1.0 / (1.0 + abs(min(c, N - c)) * 3.0) for c in range(N)])
+    vR = [np.array([[vcls[int(r[2])]]], complex) for r in ent]
+    SxR = oracle.exchange_R(GR, vR, ent, [np.ones((1, 1, 1))])
+    Sxk = oracle.fourier_R_to_k([s[None] for s in SxR], ent, ch.kmesh, [0, 1], [0, 1])[:, 0, 0, 0]
+    vq = np.array([sum(vcls[c] * np.exp(2j * np.pi * q * c / N) for c in range(N)) for q in range(N)])
+    f = synth.fermi(np.linalg.eigvalsh(ch.H_k)[:, 0] - ch.mu, ch.beta)
+    for k in range(N):
+        ref = -sum(vq[q] * f[(k - q) % N] for q in range(N)) / N
+        assert abs(Sxk[k] - ref) < 1e-14
+
+
+def test_self_energy_real_space_equals_kspace_route(cell0):
+    c = cell0
+    ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
+    G = c.green_k_tau()
+    oo, po = c.orb_offsets, c.pb_offsets
+    C = [c.species[s].C for s in c.species_of_atom]
+    rng = np.random.default_rng(11)
+    # an arbitrary W~(q, tau) with the Hermitian symmetry of a screened interaction
+    Wq = rng.standard_normal((c.n_k, c.n_tau, c.n_pb_total, c.n_pb_total)) * (1 + 0j)
+    Wq = Wq + 1j * rng.standard_normal(Wq.shape)
+    WR = oracle.fourier_k_to_R(Wq, ent, c.kmesh, po, po)
+    GR = oracle.fourier_k_to_R(G, ent, c.kmesh, oo, oo)
+    SR = oracle.self_energy_R(GR, WR, ent, C)
+    Sk_real = oracle.fourier_R_to_k(SR, ent, c.kmesh, oo, oo)
+    Sk = oracle.self_energy_k_kspace(G, Wq, C, oo, po, c.kmesh)
+    assert np.abs(Sk_real - Sk).max() < 1e-13 * np.abs(Sk).max()
+
+
+def test_self_energy_hermiticity(cell0):
+    c = cell0
+    sysm = oracle.OracleSystem(c)
+    vq, vc = c.coulomb()
+    r = sysm.sweep(c.green_k_tau(), vq, vc)
+    ent = sysm.entries
+    key = {(int(x[0]), int(x[1]), tuple(int(y) for y in x[2:5])): e for e, x in enumerate(ent)}
+    sc = max(np.abs(s).max() for s in r["Sig_R"])
+    sx = max(np.abs(s).max() for s in r["Sigx_R"])
+    for e, x in enumerate(ent):
+        e2 = key[(int(x[1]), int(x[0]), tuple(int(y) for y in np.mod(-x[2:5], c.kmesh)))]
+        assert np.abs(r["Sig_R"][e2] - r["Sig_R"][e].conj().transpose(0, 2, 1)).max() < 1e-11 * sc
+        assert np.abs(r["Sigx_R"][e2] - r["Sigx_R"][e].conj().T).max() < 1e-13 * sx
+    # Sigma_x(k) Hermitian and negative semidefinite for the positive v used here? Only Hermitian.
+    for k in range(c.n_k):
+        assert np.abs(r["Sigx_k"][k] - r["Sigx_k"][k].conj().T).max() < 1e-13 * sx
+
+
+def test_self_energy_vanishes_without_screening(cell0):
+    c = cell0
+    sysm = oracle.OracleSystem(c)
+    G = c.green_k_tau()
+    GR = oracle.fourier_k_to_R(G, sysm.entries, c.kmesh, c.orb_offsets, c.orb_offsets)
+    WR = [np.zeros((c.n_tau, 8, 8), complex) for _ in sysm.entries]
+    SR = oracle.self_energy_R(GR, WR, sysm.entries, sysm.C_atom)
+    assert max(np.abs(s).max() for s in SR) == 0.0
