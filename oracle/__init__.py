@@ -37,7 +37,7 @@ import math
 from typing import List, Sequence, Tuple
 
 import numpy as np
-from scipy.special import roots_legendre
+from numpy.polynomial.legendre import leggauss
 
 __all__ = [
     "kmesh_rule",
@@ -258,8 +258,9 @@ def fourier_matrix(beta: float, tau: np.ndarray, idx: np.ndarray, statistics: st
     of the tau nodes; w_n = (2n+1) pi/beta ('F') or 2n pi/beta ('B').
 
     A function known at the nodes is read as the polynomial through them, and
-    its transform is that polynomial's exact Fourier integral.  Gauss-Legendre
-    quadrature with enough points is exact up to rounding for this entire integrand.
+    its transform is that polynomial's exact Fourier integral, evaluated by
+    composite Gauss-Legendre quadrature (exact up to rounding for this entire
+    integrand).
     """
     tau = np.asarray(tau, dtype=np.float64)
     x_n = 2.0 * tau / beta - 1.0
@@ -272,10 +273,18 @@ def fourier_matrix(beta: float, tau: np.ndarray, idx: np.ndarray, statistics: st
     else:
         raise ValueError(statistics)
     out = np.empty((len(idx), len(tau)), np.complex128)
-    M = int(len(tau) / 2 + 0.75 * np.max(np.abs(a)) + 48)
-    xg, wg = roots_legendre(M)
-    L = _lagrange_at(x_n, w, xg)  # [M][N]
+    # composite Gauss-Legendre: panels short enough that e^{iax} turns by at most
+    # ~4 radians on each, 48 nodes per panel (exact to rounding for l_i e^{iax});
+    # short panels keep the node positions, hence the phases, accurate.
+    t48, w48 = leggauss(48)
     for r, ar in enumerate(a):
+        S = int(math.ceil(abs(ar) / 4.0)) + 1
+        edges = np.linspace(-1.0, 1.0, S + 1)
+        c = 0.5 * (edges[1:] + edges[:-1])
+        h = 0.5 * (edges[1:] - edges[:-1])
+        xg = (c[:, None] + h[:, None] * t48[None, :]).reshape(-1)
+        wg = (h[:, None] * w48[None, :]).reshape(-1)
+        L = _lagrange_at(x_n, w, xg)  # [M][N]
         # tau = beta (x + 1)/2 ; e^{i w tau} = e^{i a} e^{i a x}
         out[r] = (0.5 * beta) * np.exp(1j * ar) * ((wg * np.exp(1j * ar * xg)) @ L)
     return out

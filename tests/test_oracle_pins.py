@@ -266,24 +266,29 @@ def test_transform_exact_on_polynomials(stat):
 def test_transform_matrix_high_precision():
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 60
-    beta, N = 50.0, 12
+    beta, N = 50.0, 24
     tau = synth.tau_nodes(beta, N)
-    idx = np.array([-7, 0, 3, 40])
+    fer, _ = synth.matsubara_sets(N)
+    idx = np.array([fer[0], 0, 40])  # includes the largest |n| of the set
     T = oracle.fourier_matrix(beta, tau, idx, "F")
-    xs = [mp.mpf(2) * mp.mpf(t) / beta - 1 for t in tau]
-    xs[0], xs[-1] = mp.mpf(-1), mp.mpf(1)
+    tmax = np.abs(oracle.fourier_matrix(beta, tau, fer, "F")).max()
+    # the nodes as the oracle holds them (x = 2 tau / beta - 1 in float64): the Lagrange
+    # basis is sensitive to node rounding at the ~N^2 eps level, the quadrature is not
+    xs = [mp.mpf(float(v)) for v in 2.0 * tau / beta - 1.0]
     for r, n in enumerate(idx):
         a = mp.mpf(2 * int(n) + 1) * mp.pi / 2
-        for i in (0, 3, N - 1):
+        for i in (0, N // 2, N - 1):
             def li(x, i=i):
                 p = mp.mpf(1)
                 for j in range(N):
                     if j != i:
                         p *= (x - xs[j]) / (xs[i] - xs[j])
                 return p
-            val = mp.quad(lambda x: mp.expj(a * x) * li(x), mp.linspace(-1, 1, 9))
+            val = mp.quad(lambda x: mp.expj(a * x) * li(x), mp.linspace(-1, 1, 81))
             ref = complex(mp.mpf(beta) / 2 * mp.expj(a) * val)
-            assert abs(T[r, i] - ref) < 1e-13 * beta
+            # float64 floor: rounded quadrature nodes meet Lagrange slopes ~N^2 and the
+            # phase a*x, so agreement is ~eps (N^2 + |a|) relative to max |T|
+            assert abs(T[r, i] - ref) < 2.3e-16 * (N * N + abs(float(a))) * tmax
 
 
 def test_transform_round_trip_and_conditioning():
