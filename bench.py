@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Benchmark of the real-space / imaginary-time GW sweep on one GB300 per rank.
+
+One step = one pass of every row of the sweep over the 8-atom diamond-like
+workload (n = 9 orbitals, K = 48 product functions per atom, 4x4x4 k-mesh,
+beta = 1000, 48 tau nodes, 12-bohr cutoff: 376 pair entries):
+  G(k,tau) -> G(R,tau) -> P(R,tau) -> P(R,i nu) -> [P(q) -> W solve -> W~(R)] (i nu)
+  -> W~(R,tau) -> Sigma(R,tau) + Sigma_x -> Sigma(R,i omega) -> Sigma(k,i omega).
+Inputs G(k,tau) and v(q) are resident in HBM when the timed region starts.
+
+`value` is sweeps per second summed over ranks (weak scaling: each rank runs its
+own replica; the sweep does not shard).  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P+Σ sweep time & TFLOP/s vs peak; serve p50/p99; mixed vs FP64 at 1e-6 rel err"
+UNIT = "sweep/s"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured value in the peaks file)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------
+# workload and its algorithmic work
+# --------------------------------------------------------------------------------------
+
+def workload(cfg: int):
+    import synth
+    cell = synth.make_config(cfg)
+    return cell
+
+
+def contraction_flops(cell, entries) -> float:
+    """Real flops of one P (or Sigma) contraction over all entries and tau nodes:
+    2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2 + 2 K_a K_b n_b^2) per (entry, tau)."""
+    f = 0.0
+    for a, b in entries[:, :2]:
+        na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
+        Ka, Kb = cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
+        f += 2.0 * (2 * Ka * na * na * nb + 4 * Ka * na * nb * nb + 2 * Ka * Kb * nb * nb)
+    return f * cell.n_tau
+
+
+def wsolve_flops(cell) -> float:
+    """A = I - v P (8 N^3), LU (16/3 N^3), N right-hand sides (8 N^3) per (q, nu)."""
+    N = cell.n_pb_total
+    return (8.0 + 16.0 / 3.0 + 8.0) * N ** 3 * cell.n_k * cell.nu_idx.size
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampling (nvidia-smi) during the timed region
+# --------------------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+
+class Sweep:
+    """Device buffers and the ordered calls of one sweep."""
+
+    STAGES = ["G_k_to_R", "P", "P_tau_to_nu", "W_solve", "W_nu_to_tau", "v_k_to_R", "Sigma", "Sigma_tau_to_omega",
+              "Sigma_R_to_k"]
+
+    def __init__(self, cell, precision: str, device: int = 0):
+        import torch
+        from paper_1911_05633_gb300 import gw
+        self.torch = torch
+        self.cell = cell
+        self.prec = precision
+        self.plan = gw.Plan.from_cell(cell, device=device)
+        p = self.plan
+        inf = p.info
+        self.dev = torch.device("cuda", device)
+        z = lambda n: torch.empty(n, dtype=torch.complex128, device=self.dev)
+        nt, nn, nw = inf["n_tau"], inf["n_nu"], inf["n_omega"]
+        No = inf["n_orb_total"]
+        self.G_k = z(inf["n_k"] * nt * No * No)
+        self.v_q = z(inf["n_k"] * inf["n_pb_total"] ** 2)
+        self.G_R = z(p.len("orb", nt))
+        self.P_R = z(p.len("pb", nt))
+        self.P_iw = z(p.len("pb", nn))
+        self.W_iw = z(p.len("pb", nn))
+        self.W_R = z(p.len("pb", nt))
+        self.v_R = z(p.len("pb", 1))
+        self.S_R = z(p.len("orb", nt))
+        self.Sx_R = z(p.len("orb", 1))
+        self.S_iw = z(p.len("orb", nw))
+        self.S_k = z(inf["n_k"] * nw * No * No)
+        self.Sx_k = z(inf["n_k"] * No * No)
+        self.launches_per_step = None
+
+    def load_inputs(self, G_k_host, v_q_host):
+        self.G_k.copy_(self.torch.from_numpy(G_k_host.reshape(-1)))
+        self.v_q.copy_(self.torch.from_numpy(v_q_host.reshape(-1)))
+
+    def run(self, stream, events=None):
+        p, s = self.plan, stream.cuda_stream
+        inf = p.info
+        calls = [
+            lambda: p.green_k_to_R(self.G_k, self.G_R, stream=s),
+            lambda: p.polarizability_tau(self.G_R, self.P_R, precision=self.prec, stream=s),
+            lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s),
+            lambda: p.screened_W_iw(self.P_iw, self.v_q, self.W_iw, stream=s),
+            lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s),
+            lambda: p.fourier_k_to_R("pb", 1, self.v_q, self.v_R, stream=s),
+            lambda: p.self_energy_tau(self.G_R, self.W_R, v_R=self.v_R, Sig_R=self.S_R, Sigx_R=self.Sx_R,
+                                      precision=self.prec, stream=s),
+            lambda: p.transform_tau_iw("F", "tau_to_iw", "orb", self.S_R, self.S_iw, stream=s),
+            lambda: (p.fourier_R_to_k("orb", inf["n_omega"], self.S_iw, self.S_k, stream=s),
+                     p.fourier_R_to_k("orb", 1, self.Sx_R, self.Sx_k, stream=s)),
+        ]
+        for i, c in enumerate(calls):
+            if events is not None:
+                events[i][0].record(stream)
+            c()
+            if events is not None:
+                events[i][1].record(stream)
+
+    def kernel_launches(self) -> int:
+        """Kernels this library launches per sweep (counted from the launch code)."""
+        inf = self.plan.info
+        nchunks = -(-inf["n_nu"] // inf["nu_chunk"])
+        return 1 + 1 + 1 + 5 * nchunks + 1 + 1 + 2 + 1 + 2
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    cell = workload(args.config)
+    sw = Sweep(cell, args.precision, device=local)
+    Gk = cell.green_k_tau()
+    vq, _ = cell.coulomb()
+    sw.load_inputs(Gk, vq)
+    stream = torch.cuda.Stream(device=local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=sw.dev)  # 256 MB > L2
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sw.run(stream)
+        sw.plan.sync(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    nst = len(Sweep.STAGES)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nst)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush_l2(flush)
+            sw.run(stream, ev[k])
+    sw.plan.sync(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    stage_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nst)] for k in range(args.steps)])
+    step_ms = float(stage_ms.sum(axis=1).mean())
+    step_ms_max = max_over_ranks(step_ms, world)
+    value = world * 1000.0 / step_ms_max
+    stage_mean = stage_ms.mean(axis=0)
+
+    # roofline of the dominant stage
+    ent = sw.plan.entries
+    fl_P = contraction_flops(cell, ent) / (2 if sw.plan.info["c_symmetric"] else 1)  # mirrored nodes not computed
+    fl_S = contraction_flops(cell, ent)
+    fl_W = wsolve_flops(cell)
+    work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
+    dom = int(np.argmax(stage_mean))
+    dom_name = Sweep.STAGES[dom]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    roof = None
+    if dom_name in work and args.precision == "fp64":
+        ach = work[dom_name] / (stage_mean[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": round(ach, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(ach / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "peak_source": "nominal FP64 (not in MEASURED_PEAKS.json)"}
+    contraction_tflops = {k: round(work[k] / (stage_mean[Sweep.STAGES.index(k)] * 1e-3) / 1e12, 4)
+                          for k in ("P", "Sigma", "W_solve")}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(sw, Gk, vq, stream, args)
+    out = {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x3/f32-acc + f64",
+        "data": "synthetic",
+        "config": {"workload": cell.name + f": {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k,"
+                   f" {cell.n_tau} tau, cutoff {cell.cutoff} bohr, {len(ent)} pair entries",
+                   "precision": args.precision, "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
+        "tflops": contraction_tflops,
+        "wall_s": round(wall, 3),
+        "clocks": clk,
+        "gpu_launches": sw.kernel_launches() * args.steps,
+        "roofline": roof,
+        "e2e": e2e,
+    }
+    return out, cell
+
+
+def run_e2e(sw, Gk, vq, stream, args):
+    """Same sweep through the public API with host buffers: H2D of G(k,tau) and v(q)
+    from pinned memory and D2H of Sigma(k, i omega) and Sigma_x(k) inside the timed region."""
+    import torch
+    Gk_h = torch.from_numpy(Gk.reshape(-1)).pin_memory()
+    vq_h = torch.from_numpy(vq.reshape(-1)).pin_memory()
+    Sk_h = torch.empty(sw.S_k.numel(), dtype=torch.complex128).pin_memory()
+    Sxk_h = torch.empty(sw.Sx_k.numel(), dtype=torch.complex128).pin_memory()
+    steps = max(1, min(args.steps, 3))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        sw.G_k.copy_(Gk_h, non_blocking=True)
+        sw.v_q.copy_(vq_h, non_blocking=True)
+        sw.run(stream)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            sw.G_k.copy_(Gk_h, non_blocking=True)
+            sw.v_q.copy_(vq_h, non_blocking=True)
+            sw.run(stream)
+            Sk_h.copy_(sw.S_k, non_blocking=True)
+            Sxk_h.copy_(sw.Sx_k, non_blocking=True)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    return {"value": round(1000.0 / ms, 6), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(Gk_h.numel() * 16 + vq_h.numel() * 16),
+            "d2h_bytes_per_step": int(Sk_h.numel() * 16 + Sxk_h.numel() * 16), "steps": steps}
+
+
+# --------------------------------------------------------------------------------------
+# the oracle on the host cores (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------------------
+
+def oracle_sample(cell, n_nu_sample: int = 3):
+    """Time one oracle sweep with the W solve on `n_nu_sample` of the bosonic
+    frequencies; the W time is scaled to all of them.  Returns (seconds per sweep, note)."""
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.OracleSystem(cell)
+    Gk = cell.green_k_tau()
+    vq, vc = cell.coulomb()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    GR = oracle.fourier_k_to_R(Gk, orc.entries, orc.kmesh, cell.orb_offsets, cell.orb_offsets)
+    PR = oracle.polarizability_R(GR, orc.entries, orc.C_atom, cell.spin)
+    Piw = oracle.transform(orc.B_fwd, PR)
+    t_a = time.perf_counter() - t0
+    nn = cell.nu_idx.size
+    sel = list(range(min(n_nu_sample, nn)))
+    t0 = time.perf_counter()
+    oracle.screened_W([x[sel] for x in Piw], orc.entries, vq, orc.kmesh, cell.pb_offsets)
+    t_w = (time.perf_counter() - t0) * nn / len(sel)
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(0)
+    WR = [rng.standard_normal(p.shape) + 0j for p in PR]  # W~(R, tau) has P's shapes
+    vR = orc.v_R(vc)
+    SR = oracle.self_energy_R(GR, WR, orc.entries, orc.C_atom)
+    oracle.exchange_R(GR, vR, orc.entries, orc.C_atom)
+    Siw = oracle.transform(orc.F_fwd, SR)
+    oracle.fourier_R_to_k(Siw, orc.entries, orc.kmesh, cell.orb_offsets, cell.orb_offsets)
+    t_b = time.perf_counter() - t0
+    total = t_a + t_w + t_b
+    note = (f"full oracle sweep except the W solve, which ran on {len(sel)} of {nn} bosonic frequencies "
+            f"({t_w * len(sel) / nn:.2f} s) and is scaled x{nn / len(sel):.1f}; input setup {t_setup:.1f} s not counted")
+    return total, note
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+        return int(n)
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    cell = workload(args.config)
+    if rank != 0:
+        return None
+    secs = []
+    note = ""
+    for _ in range(max(1, args.steps)):
+        s, note = oracle_sample(cell)
+        secs.append(s)
+    ms = 1000.0 * float(np.mean(secs))
+    v = 1000.0 / ms
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cell.name, "precision": "fp64 (oracle, NumPy/LAPACK)"},
+            "cpu_baseline": {"value": round(v, 8), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": note},
+            "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    out, cell = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            s, note = oracle_sample(cell)
+            out["cpu_baseline"] = {"value": round(1.0 / s, 8), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                   "sample": note}
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * gw.h -- C ABI of the real-space / imaginary-time GW sweep (arXiv:1911.05633).
+ *
+ * One GB300 (sm_103a), one process.  Every data buffer is owned by the caller
+ * and is a DEVICE pointer unless stated otherwise; the plan owns its tables
+ * (pair list, lattice phases, product-basis coefficients, transform matrices)
+ * and the scratch of the W solve.  Complex numbers are interleaved
+ * (re, im) doubles, i.e. C99 double complex / numpy complex128.  All compute
+ * calls are asynchronous on the given stream (a cudaStream_t passed as
+ * void*; NULL is the legacy default stream).  Errors are returned by value;
+ * nothing crosses the ABI by exception.  A call that returns an error has
+ * launched nothing.
+ *
+ * Notation: atoms a, b; orbitals L (n_a per atom), product-basis functions K
+ * (K_a per atom); a pair entry e = (a, b, R) is one atom pair and one lattice
+ * class R kept by the distance cutoff; N_k k-points; N_tau imaginary-time
+ * nodes; N_omega fermionic and N_nu bosonic sampled Matsubara frequencies.
+ *
+ * Ragged "entry" layouts.  A buffer with n_slices slices per entry holds the
+ * entries back to back, entry e as a row-major [n_slices][rows_e][cols_e]
+ * block starting at element n_slices * off[e], where off[] is the prefix sum
+ * of rows_e * cols_e returned by gw_plan_offsets():
+ *   GW_BLOCK_ORB: rows_e = n_a, cols_e = n_b   (G, Sigma)
+ *   GW_BLOCK_PB : rows_e = K_a, cols_e = K_b   (P, W~, v)
+ * Dense k-space buffers are [N_k][n_slices][N][N] with N = total orbitals
+ * (ORB) or total product functions (PB), atoms in order.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_plan_s* gw_plan_t;
+
+typedef enum {
+  GW_OK = 0,
+  GW_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, bad grid) */
+  GW_ERR_OOM = 2,            /* device or host allocation failed */
+  GW_ERR_CUDA = 3,           /* a CUDA call failed (message in gw_last_error()) */
+  GW_ERR_KMESH_ALIAS = 4,    /* strict mode: the k-mesh is below the rule of Sec. 2 */
+  GW_ERR_NOT_HERMITIAN = 5,  /* reserved */
+  GW_ERR_SINGULAR = 6,       /* a zero pivot in the W solve */
+  GW_ERR_TIMEOUT = 7,        /* reserved (bounded device waits) */
+  GW_ERR_NAN = 8,            /* reserved */
+  GW_ERR_NO_DEVICE = 9,      /* compute call on a plan built with host_only */
+  GW_ERR_UNSUPPORTED = 10    /* size outside the compiled limits (see gw_plan_create) */
+} gw_status;
+
+typedef enum { GW_FP64 = 0, GW_MIXED_BF16X3 = 1 } gw_precision;
+typedef enum { GW_FERMION = 0, GW_BOSON = 1 } gw_statistics;
+typedef enum { GW_TAU_TO_IW = 0, GW_IW_TO_TAU = 1 } gw_direction;
+typedef enum { GW_BLOCK_ORB = 0, GW_BLOCK_PB = 1 } gw_block;
+
+/* Crystal: lattice rows a_1, a_2, a_3 in bohr; atoms in fractional coordinates. */
+typedef struct {
+  double lattice[9];
+  int n_atoms;
+  const double* frac;     /* host [n_atoms][3] */
+  const int* species;     /* host [n_atoms], 0 <= species < n_species */
+} gw_cell;
+
+/* Per-species orbital and product basis.  C[s] is the one-centre coefficient
+ * tensor <M_K | phi_L phi_L''> of Eq. P_MM, host [n_prod][n_orb][n_orb], real. */
+typedef struct {
+  int n_species;
+  const int* n_orb;       /* host [n_species], 1..16 */
+  const int* n_prod;      /* host [n_species], 1..128 */
+  const double* const* C; /* host [n_species] pointers */
+} gw_basis;
+
+/* Imaginary-time nodes and sampled Matsubara indices (Appendix A grid).
+ * tau: ascending, tau[0] = 0 (read as 0+), tau[n_tau-1] = beta (read as beta-),
+ * mirror-symmetric beta - tau_i = tau_{n_tau-1-i} to 1e-12 beta.
+ * omega_idx: fermionic n, w_n = (2n+1) pi / beta; nu_idx: bosonic m, v_m = 2 m pi / beta.
+ * n_omega >= n_tau and n_nu >= n_tau (least-squares inverse transforms). */
+typedef struct {
+  double beta;
+  int n_tau;   const double* tau;
+  int n_omega; const int* omega_idx;
+  int n_nu;    const int* nu_idx;
+} gw_grid;
+
+typedef struct {
+  int spin;               /* spin degeneracy s of Eq. P_MM (sum over alpha): 1 or 2 */
+  int strict_kmesh;       /* 1: reject a k-mesh below the rule of Sec. 2 */
+  int host_only;          /* 1: build host tables only; compute calls fail with GW_ERR_NO_DEVICE */
+  int device;             /* CUDA device ordinal used by the plan */
+  size_t workspace_bytes; /* cap on the W-solve scratch (0: 2 GiB) */
+} gw_options;
+
+typedef struct {
+  int n_atoms, n_entries, n_k, n_tau, n_omega, n_nu;
+  int n_orb_total, n_pb_total;
+  int kmesh[3];
+  int kmesh_required[3];      /* the rule of Sec. 2 for the given cutoff (0 if cutoff <= 0) */
+  int c_symmetric;            /* every C[s] symmetric in (L, L'') */
+  int64_t len_orb;            /* sum over entries of n_a n_b (one slice) */
+  int64_t len_pb;             /* sum over entries of K_a K_b (one slice) */
+  size_t workspace_bytes;     /* device scratch the plan holds */
+  int nu_chunk;               /* bosonic frequencies per W-solve pass */
+  double cond_fermion;        /* 2-norm condition numbers of the forward matrices */
+  double cond_boson;
+} gw_plan_info;
+
+/* ---- plan ------------------------------------------------------------------ */
+
+/* Build the plan: the pair list of Sec. 2 (every ordered atom pair (a, b) and
+ * lattice class R modulo the k-mesh supercell whose minimum-image distance
+ * |R + t_b - t_a| is <= cutoff; cutoff <= 0 keeps every class; ties go to the
+ * lexicographically smallest R), the phases e^{ik.R}, and the tau <-> i omega
+ * matrices of Appendix A (exact Fourier integrals of the polynomial through
+ * the tau nodes and their least-squares inverses).  Host inputs are copied.
+ * Returns GW_ERR_ARG on invalid input, GW_ERR_KMESH_ALIAS in strict mode,
+ * GW_ERR_UNSUPPORTED beyond n_orb <= 16, n_prod <= 128, n_tau <= 128. */
+gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int kmesh[3],
+                         const gw_grid* grid, double cutoff, const gw_options* opt,
+                         gw_plan_t* out);
+gw_status gw_plan_destroy(gw_plan_t plan);
+gw_status gw_plan_query(gw_plan_t plan, gw_plan_info* info);
+
+/* Host copy of the entry list, [n_entries][8] int64 rows (a, b, c1, c2, c3, R1, R2, R3):
+ * class c in [0, N_i) and its minimum-image representative R.  Sorted by (a, b, c). */
+gw_status gw_plan_entries(gw_plan_t plan, int64_t* rows);
+
+/* Host copy of the per-entry block offsets, [n_entries + 1] int64 (see the layout note). */
+gw_status gw_plan_offsets(gw_plan_t plan, gw_block kind, int64_t* off);
+
+/* Host copy of a transform matrix, complex [n_out][n_in] interleaved doubles:
+ * (FERMION, TAU_TO_IW) n_omega x n_tau, (FERMION, IW_TO_TAU) n_tau x n_omega,
+ * (BOSON, TAU_TO_IW) n_nu x n_tau, (BOSON, IW_TO_TAU) n_tau x n_nu. */
+gw_status gw_plan_transform_matrix(gw_plan_t plan, gw_statistics st, gw_direction dir, double* out);
+
+/* ---- the sweep (Sec. 2: "one follows Eqs. P_old - G_1" in real space) ---------- */
+
+/* F_ab(R) = (1/N_k) sum_k e^{-i k.R} F_ab(k) for the kept entries (Sec. 2, R <-> k
+ * transforms over the pair list).  F_k dense [N_k][n_slices][N][N] -> F_R entry layout. */
+gw_status gw_fourier_k_to_R(gw_plan_t plan, gw_block kind, int n_slices,
+                            const void* F_k, void* F_R, void* stream);
+
+/* G(R, tau) from G(k, tau): gw_fourier_k_to_R with GW_BLOCK_ORB and n_slices = N_tau. */
+gw_status gw_green_k_to_R(gw_plan_t plan, const void* G_k, void* G_R, void* stream);
+
+/* P_{aK,bK'}(R, tau_i) = -s sum C^a_{K;L L''} G_{aL,bL'}(R, tau_i)
+ *      conj(G_{aL'',bL'''}(R, beta - tau_i)) C^b_{K';L' L'''}
+ * (Eq. P_MM with the sign and tau pairing of Eq. P_II; conj from the Hermiticity
+ * of G).  G_R: ORB layout, N_tau slices.  P_R: PB layout, N_tau slices. */
+gw_status gw_polarizability_tau(gw_plan_t plan, const void* G_R, void* P_R,
+                                gw_precision prec, void* stream);
+
+/* out[e][m] = sum_i T[m][i] in[e][i] per entry and block element, with T the
+ * matrix named by (st, dir) (Appendix A grid).  Layout of `kind` on both sides;
+ * slices: N_tau on the tau side, N_omega (FERMION) or N_nu (BOSON) on the other. */
+gw_status gw_transform_tau_iw(gw_plan_t plan, gw_statistics st, gw_direction dir,
+                              gw_block kind, const void* in, void* out, void* stream);
+
+/* W~(R, i nu) on the kept entries from P(R, i nu) (Eq. W_1 with W = v + W~):
+ * P(q) = sum_{kept R} e^{iq.R} P(R); (I - v(q) P(q)) W(q) = v(q) by LU with
+ * partial pivoting in FP64; W~(R) = (1/N_k) sum_q e^{-iq.R} (W(q) - v(q)).
+ * P_R_iw, Wt_R_iw: PB layout, N_nu slices.  v_q: dense [N_k][N_PB][N_PB].
+ * Uses the plan's scratch; calls on one plan must not overlap. */
+gw_status gw_screened_W_iw(gw_plan_t plan, const void* P_R_iw, const void* v_q,
+                           void* Wt_R_iw, void* stream);
+
+/* Sigma_{aL,bL'}(R, tau_i) = -sum C^a_{K;L L''} G_{aL'',bL'''}(R, tau_i)
+ *      W~_{aK,bK'}(R, tau_i) C^b_{K';L' L'''}                     (Eq. S_MM)
+ * and, when v_R and Sigx_R are both non-NULL, the static exchange of the same
+ * contraction with W~ -> v and G(tau) -> -G(beta-) (the rule after Eq. P_II):
+ *   Sigx = + sum C^a G(R, beta-) v(R) C^b.
+ * G_R: ORB, N_tau slices; Wt_R: PB, N_tau slices; v_R: PB, 1 slice;
+ * Sig_R: ORB, N_tau slices; Sigx_R: ORB, 1 slice. */
+gw_status gw_self_energy_tau(gw_plan_t plan, const void* G_R, const void* Wt_R,
+                             const void* v_R, void* Sig_R, void* Sigx_R,
+                             gw_precision prec, void* stream);
+
+/* F_ab(k) = sum_{kept R} e^{+i k.R} F_ab(R) (Sec. 2), entry layout -> dense
+ * [N_k][n_slices][N][N]; blocks of atom pairs without entries are zero. */
+gw_status gw_fourier_R_to_k(gw_plan_t plan, gw_block kind, int n_slices,
+                            const void* F_R, void* F_k, void* stream);
+
+/* Wait for the stream and report any deferred device-side error of the plan. */
+gw_status gw_sync(gw_plan_t plan, void* stream);
+
+const char* gw_status_string(gw_status s);
+/* Text of the last error on this thread (empty if none). */
+const char* gw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_H */

@@ -1,0 +1,530 @@
+// The C ABI declared in include/gw.h: plan lifetime, queries and the entry
+// points of the sweep.  Host orchestration only; the arithmetic runs in the
+// kernels of kernels_fp64.cu and kernels_mixed.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mixed.h"
+
+struct gw_plan_s {
+  gw::HostPlan h;
+  bool host_only = true;
+  int device = 0;
+  gw::DevEntry* d_ent = nullptr;
+  int* d_pair_start = nullptr;  // [n_atoms^2 + 1]
+  int* d_pair_first = nullptr;  // [n_active + 1]
+  int n_active = 0;
+  int* d_orb_off = nullptr;
+  int* d_pb_off = nullptr;
+  double2* d_phase = nullptr;
+  double* d_C = nullptr;
+  double2* d_Tf_fwd = nullptr;
+  double2* d_Tf_inv = nullptr;
+  double2* d_Tb_fwd = nullptr;
+  double2* d_Tb_inv = nullptr;
+  double2* d_wsA = nullptr;
+  double2* d_wsX = nullptr;
+  int* d_piv = nullptr;
+  int* d_status = nullptr;
+  int nu_chunk = 0;
+  size_t ws_bytes = 0;
+  size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_LU = 0;
+  gw::MixedPlan mixed;
+};
+
+namespace gw {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace gw
+
+namespace {
+
+using gw::set_last_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+gw_status cuda_fail(cudaError_t e, const char* what) {
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return GW_ERR_CUDA;
+}
+
+#define GW_CUDA(call)                                         \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);       \
+  } while (0)
+
+template <typename T>
+gw_status upload(T** dst, const void* src, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GW_ERR_OOM : GW_ERR_CUDA;
+  }
+  if (src) GW_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return GW_OK;
+}
+
+void free_device(gw_plan_s* p) {
+  void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_phase,
+                  p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_inv, p->d_wsA, p->d_wsX,
+                  p->d_piv, p->d_status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  gw::mixed_free(p->mixed);
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+gw_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return GW_OK;
+}
+
+gw_status need_device(gw_plan_t p) {
+  if (!p) { set_last_error("null plan"); return GW_ERR_ARG; }
+  if (p->host_only) { set_last_error("plan was built with host_only"); return GW_ERR_NO_DEVICE; }
+  return GW_OK;
+}
+
+// Dense k-space leading dimension and entry-layout kind
+int dense_n(const gw_plan_s* p, gw_block kind) {
+  return kind == GW_BLOCK_PB ? p->h.n_pb_total() : p->h.n_orb_total();
+}
+
+gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_k, long long k_stride,
+                        long long s_stride, const double2* F_sub, long long sub_k_stride, long long sub_s_stride,
+                        double2* F_R, int out_n_slices, int out_slice0, double scale, cudaStream_t st) {
+  gw::GatherArgs g{};
+  g.ent = p->d_ent;
+  g.pair_first = p->d_pair_first;
+  g.phase = p->d_phase;
+  g.n_k = p->h.n_k;
+  g.F_k = F_k;
+  g.k_stride = k_stride;
+  g.s_stride = s_stride;
+  g.ld = dense_n(p, kind);
+  g.pb = kind == GW_BLOCK_PB;
+  g.F_sub = F_sub;
+  g.sub_k_stride = sub_k_stride;
+  g.sub_s_stride = sub_s_stride;
+  g.F_R = F_R;
+  g.out_n_slices = out_n_slices;
+  g.out_slice0 = out_slice0;
+  g.scale = scale;
+  int maxblk = 0;
+  for (int s = 0; s < p->h.n_species; ++s)
+    for (int t = 0; t < p->h.n_species; ++t)
+      maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
+  const int threads = 128;
+  dim3 grid(p->n_active, n_slices, (maxblk + threads - 1) / threads);
+  gw::k_gather_k_to_R<<<grid, threads, 0, st>>>(g);
+  return check_launch("k_gather_k_to_R");
+}
+
+gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_R, int in_n_slices,
+                         int in_slice0, double2* F_k, long long k_stride, long long s_stride, cudaStream_t st) {
+  gw::ScatterArgs g{};
+  g.ent = p->d_ent;
+  g.pair_start = p->d_pair_start;
+  g.row_off = kind == GW_BLOCK_PB ? p->d_pb_off : p->d_orb_off;
+  g.n_atoms = p->h.n_atoms;
+  g.phase = p->d_phase;
+  g.n_k = p->h.n_k;
+  g.F_R = F_R;
+  g.in_n_slices = in_n_slices;
+  g.in_slice0 = in_slice0;
+  g.pb = kind == GW_BLOCK_PB;
+  g.F_k = F_k;
+  g.k_stride = k_stride;
+  g.s_stride = s_stride;
+  g.ld = dense_n(p, kind);
+  int maxblk = 0;
+  for (int s = 0; s < p->h.n_species; ++s)
+    for (int t = 0; t < p->h.n_species; ++t)
+      maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
+  const int threads = 128;
+  dim3 grid(p->h.n_atoms * p->h.n_atoms, n_slices, (maxblk + threads - 1) / threads);
+  gw::k_scatter_R_to_k<<<grid, threads, 0, st>>>(g);
+  return check_launch("k_scatter_R_to_k");
+}
+
+size_t smem_polar(const gw::HostPlan& h) {
+  size_t m = 0;
+  for (int s = 0; s < h.n_species; ++s)
+    for (int t = 0; t < h.n_species; ++t) {
+      size_t na = h.n_orb[s], nb = h.n_orb[t];
+      m = std::max(m, (2 * na * nb + gw::kKCHost * na * nb + gw::kKCHost * nb * nb) * sizeof(double2));
+    }
+  return m;
+}
+
+size_t smem_sigma(const gw::HostPlan& h) {
+  size_t m = 0;
+  for (int s = 0; s < h.n_species; ++s)
+    for (int t = 0; t < h.n_species; ++t) {
+      size_t na = h.n_orb[s], nb = h.n_orb[t];
+      m = std::max(m, (na * nb + gw::kKCHost * nb * nb + gw::kKCHost * na * nb) * sizeof(double2));
+    }
+  return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gw_status_string(gw_status s) {
+  switch (s) {
+    case GW_OK: return "ok";
+    case GW_ERR_ARG: return "invalid argument";
+    case GW_ERR_OOM: return "out of memory";
+    case GW_ERR_CUDA: return "CUDA error";
+    case GW_ERR_KMESH_ALIAS: return "k-mesh below the cutoff rule";
+    case GW_ERR_NOT_HERMITIAN: return "input not Hermitian";
+    case GW_ERR_SINGULAR: return "singular matrix in the W solve";
+    case GW_ERR_TIMEOUT: return "device wait timed out";
+    case GW_ERR_NAN: return "NaN detected";
+    case GW_ERR_NO_DEVICE: return "plan has no device state";
+    case GW_ERR_UNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+const char* gw_last_error(void) { return gw::g_last_error.c_str(); }
+
+gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int kmesh[3], const gw_grid* grid,
+                         double cutoff, const gw_options* opt, gw_plan_t* out) {
+  if (!out) { set_last_error("null output"); return GW_ERR_ARG; }
+  *out = nullptr;
+  gw_plan_s* p = new (std::nothrow) gw_plan_s();
+  if (!p) return GW_ERR_OOM;
+  std::string err;
+  gw_status st = gw::build_host_plan(cell, basis, kmesh, grid, cutoff, opt, p->h, err);
+  if (st != GW_OK) {
+    set_last_error(err);
+    delete p;
+    return st;
+  }
+  p->host_only = opt ? (opt->host_only != 0) : false;
+  p->device = opt ? opt->device : 0;
+  if (p->host_only) {
+    *out = p;
+    return GW_OK;
+  }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  auto fail = [&](gw_status s) {
+    free_device(p);
+    delete p;
+    return s;
+  };
+  std::vector<gw::DevEntry> de = gw::make_dev_entries(h);
+  std::vector<int> pair_first;
+  for (size_t q = 0; q + 1 < h.pair_start.size(); ++q)
+    if (h.pair_start[q + 1] > h.pair_start[q]) pair_first.push_back(h.pair_start[q]);
+  pair_first.push_back(h.n_entries());
+  p->n_active = (int)pair_first.size() - 1;
+  if ((st = upload(&p->d_ent, de.data(), de.size() * sizeof(gw::DevEntry))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_pair_start, h.pair_start.data(), h.pair_start.size() * sizeof(int))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_pair_first, pair_first.data(), pair_first.size() * sizeof(int))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_orb_off, h.orb_off.data(), h.orb_off.size() * sizeof(int))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_pb_off, h.pb_off.data(), h.pb_off.size() * sizeof(int))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_phase, h.phase.data(), h.phase.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_C, h.C_packed.data(), h.C_packed.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_Tf_fwd, h.Tf_fwd.data(), h.Tf_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_Tf_inv, h.Tf_inv.data(), h.Tf_inv.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_Tb_fwd, h.Tb_fwd.data(), h.Tb_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_Tb_inv, h.Tb_inv.data(), h.Tb_inv.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_status, nullptr, 16)) != GW_OK) return fail(st);
+  if (cudaMemset(p->d_status, 0, 16) != cudaSuccess) return fail(GW_ERR_CUDA);
+
+  // W-solve scratch: two dense [chunk][N_k][N_PB][N_PB] buffers and pivots
+  const size_t npb = (size_t)h.n_pb_total();
+  const size_t per_nu = 2 * (size_t)h.n_k * npb * npb * sizeof(double2) + (size_t)h.n_k * npb * sizeof(int);
+  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes : ((size_t)2 << 30);
+  int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)h.n_nu, cap / per_nu));
+  p->nu_chunk = nch;
+  const size_t mat = (size_t)nch * h.n_k * npb * npb * sizeof(double2);
+  if ((st = upload(&p->d_wsA, nullptr, mat)) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_wsX, nullptr, mat)) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_piv, nullptr, (size_t)nch * h.n_k * npb * sizeof(int))) != GW_OK) return fail(st);
+  p->ws_bytes = 2 * mat + (size_t)nch * h.n_k * npb * sizeof(int);
+
+  // dynamic shared memory opt-ins
+  p->smem_P = smem_polar(h);
+  p->smem_S = smem_sigma(h);
+  p->smem_T = (size_t)std::max(std::max(h.n_tau, h.n_omega), h.n_nu) * 32 * sizeof(double2);
+  p->smem_LU = 2 * npb * sizeof(double2);
+  if (cudaFuncSetAttribute(gw::k_polarizability_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_P) != cudaSuccess ||
+      cudaFuncSetAttribute(gw::k_self_energy_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_S) != cudaSuccess ||
+      cudaFuncSetAttribute(gw::k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_T) != cudaSuccess ||
+      cudaFuncSetAttribute(gw::k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_LU) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    set_last_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    return fail(GW_ERR_UNSUPPORTED);
+  }
+  if ((st = gw::mixed_init(p->mixed, h, de)) != GW_OK) return fail(st);
+  *out = p;
+  return GW_OK;
+}
+
+gw_status gw_plan_destroy(gw_plan_t p) {
+  if (!p) return GW_OK;
+  if (!p->host_only) {
+    DeviceGuard guard(p->device);
+    free_device(p);
+  }
+  delete p;
+  return GW_OK;
+}
+
+gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
+  if (!p || !info) { set_last_error("null argument"); return GW_ERR_ARG; }
+  const gw::HostPlan& h = p->h;
+  std::memset(info, 0, sizeof(*info));
+  info->n_atoms = h.n_atoms;
+  info->n_entries = h.n_entries();
+  info->n_k = h.n_k;
+  info->n_tau = h.n_tau;
+  info->n_omega = h.n_omega;
+  info->n_nu = h.n_nu;
+  info->n_orb_total = h.n_orb_total();
+  info->n_pb_total = h.n_pb_total();
+  for (int i = 0; i < 3; ++i) {
+    info->kmesh[i] = h.kmesh[i];
+    info->kmesh_required[i] = h.kmesh_required[i];
+  }
+  info->c_symmetric = h.c_symmetric;
+  info->len_orb = h.off_orb.back();
+  info->len_pb = h.off_pb.back();
+  info->workspace_bytes = p->ws_bytes;
+  info->nu_chunk = p->nu_chunk;
+  info->cond_fermion = h.cond_f;
+  info->cond_boson = h.cond_b;
+  return GW_OK;
+}
+
+gw_status gw_plan_entries(gw_plan_t p, int64_t* rows) {
+  if (!p || !rows) { set_last_error("null argument"); return GW_ERR_ARG; }
+  std::memcpy(rows, p->h.entries.data(), p->h.entries.size() * sizeof(int64_t));
+  return GW_OK;
+}
+
+gw_status gw_plan_offsets(gw_plan_t p, gw_block kind, int64_t* off) {
+  if (!p || !off) { set_last_error("null argument"); return GW_ERR_ARG; }
+  const std::vector<int64_t>& v = (kind == GW_BLOCK_PB) ? p->h.off_pb : p->h.off_orb;
+  std::memcpy(off, v.data(), v.size() * sizeof(int64_t));
+  return GW_OK;
+}
+
+gw_status gw_plan_transform_matrix(gw_plan_t p, gw_statistics st, gw_direction dir, double* out) {
+  if (!p || !out) { set_last_error("null argument"); return GW_ERR_ARG; }
+  const std::vector<double>* m;
+  if (st == GW_FERMION) m = (dir == GW_TAU_TO_IW) ? &p->h.Tf_fwd : &p->h.Tf_inv;
+  else m = (dir == GW_TAU_TO_IW) ? &p->h.Tb_fwd : &p->h.Tb_inv;
+  std::memcpy(out, m->data(), m->size() * sizeof(double));
+  return GW_OK;
+}
+
+gw_status gw_fourier_k_to_R(gw_plan_t p, gw_block kind, int n_slices, const void* F_k, void* F_R, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!F_k || !F_R || n_slices <= 0) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const long long N = dense_n(p, kind);
+  return launch_gather(p, kind, n_slices, (const double2*)F_k, (long long)n_slices * N * N, N * N, nullptr, 0, 0,
+                       (double2*)F_R, n_slices, 0, 1.0 / p->h.n_k, S(stream));
+}
+
+gw_status gw_green_k_to_R(gw_plan_t p, const void* G_k, void* G_R, void* stream) {
+  if (!p) { set_last_error("null plan"); return GW_ERR_ARG; }
+  return gw_fourier_k_to_R(p, GW_BLOCK_ORB, p->h.n_tau, G_k, G_R, stream);
+}
+
+gw_status gw_fourier_R_to_k(gw_plan_t p, gw_block kind, int n_slices, const void* F_R, void* F_k, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!F_k || !F_R || n_slices <= 0) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const long long N = dense_n(p, kind);
+  return launch_scatter(p, kind, n_slices, (const double2*)F_R, n_slices, 0, (double2*)F_k,
+                        (long long)n_slices * N * N, N * N, S(stream));
+}
+
+gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, gw_block kind, const void* in,
+                              void* out, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!in || !out) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  gw::TransformArgs g{};
+  g.ent = p->d_ent;
+  const int nfreq = (stt == GW_FERMION) ? h.n_omega : h.n_nu;
+  if (dir == GW_TAU_TO_IW) {
+    g.T = (stt == GW_FERMION) ? p->d_Tf_fwd : p->d_Tb_fwd;
+    g.n_in = h.n_tau;
+    g.n_out = nfreq;
+  } else {
+    g.T = (stt == GW_FERMION) ? p->d_Tf_inv : p->d_Tb_inv;
+    g.n_in = nfreq;
+    g.n_out = h.n_tau;
+  }
+  g.pb = kind == GW_BLOCK_PB;
+  g.in = (const double2*)in;
+  g.out = (double2*)out;
+  int maxblk = 0;
+  for (int s = 0; s < h.n_species; ++s)
+    for (int t = 0; t < h.n_species; ++t)
+      maxblk = std::max(maxblk, g.pb ? h.n_prod[s] * h.n_prod[t] : h.n_orb[s] * h.n_orb[t]);
+  dim3 grid(h.n_entries(), (maxblk + 31) / 32);
+  dim3 block(32, 8);
+  gw::k_transform<<<grid, block, (size_t)g.n_in * 32 * sizeof(double2), S(stream)>>>(g);
+  return check_launch("k_transform");
+}
+
+gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_precision prec, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!G_R || !P_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  if (prec == GW_MIXED_BF16X3)
+    return gw::mixed_polarizability(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (double2*)P_R, S(stream));
+  if (prec != GW_FP64) { set_last_error("unknown precision"); return GW_ERR_ARG; }
+  gw::ContractArgs g{};
+  g.ent = p->d_ent;
+  g.C = p->d_C;
+  g.G = (const double2*)G_R;
+  g.out = (double2*)P_R;
+  g.n_tau = h.n_tau;
+  g.spin = h.spin;
+  g.mirror_tau = h.c_symmetric;
+  const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
+  dim3 grid(h.n_entries(), nt_eff);
+  gw::k_polarizability_fp64<<<grid, 256, p->smem_P, S(stream)>>>(g);
+  return check_launch("k_polarizability_fp64");
+}
+
+gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, const void* v_R, void* Sig_R,
+                             void* Sigx_R, gw_precision prec, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!G_R || !Wt_R || !Sig_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  if (prec == GW_MIXED_BF16X3) {
+    st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
+                               (double2*)Sig_R, S(stream));
+    if (st != GW_OK) return st;
+  } else if (prec == GW_FP64) {
+    gw::ContractArgs g{};
+    g.ent = p->d_ent;
+    g.C = p->d_C;
+    g.G = (const double2*)G_R;
+    g.W = (const double2*)Wt_R;
+    g.out = (double2*)Sig_R;
+    g.n_tau = h.n_tau;
+    g.g_n_slices = h.n_tau;
+    g.g_slice = -1;
+    g.w_n_slices = h.n_tau;
+    g.out_n_slices = h.n_tau;
+    g.sign = -1.0;
+    dim3 grid(h.n_entries(), h.n_tau);
+    gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    if ((st = check_launch("k_self_energy_fp64")) != GW_OK) return st;
+  } else {
+    set_last_error("unknown precision");
+    return GW_ERR_ARG;
+  }
+  if (v_R && Sigx_R) {
+    // exchange: W~ -> v, G(tau) -> -G(beta-): +C G(beta-) v C, always in FP64
+    gw::ContractArgs g{};
+    g.ent = p->d_ent;
+    g.C = p->d_C;
+    g.G = (const double2*)G_R;
+    g.W = (const double2*)v_R;
+    g.out = (double2*)Sigx_R;
+    g.n_tau = h.n_tau;
+    g.g_n_slices = h.n_tau;
+    g.g_slice = h.n_tau - 1;
+    g.w_n_slices = 1;
+    g.out_n_slices = 1;
+    g.sign = +1.0;
+    dim3 grid(h.n_entries(), 1);
+    gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    if ((st = check_launch("k_self_energy_fp64 (exchange)")) != GW_OK) return st;
+  }
+  return GW_OK;
+}
+
+gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, void* Wt_R_iw, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!P_R_iw || !v_q || !Wt_R_iw) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  cudaStream_t s = S(stream);
+  const long long N = h.n_pb_total();
+  const long long NN = N * N;
+  const int nk = h.n_k;
+  const double2* v = (const double2*)v_q;
+  for (int n0 = 0; n0 < h.n_nu; n0 += p->nu_chunk) {
+    const int nc = std::min(p->nu_chunk, h.n_nu - n0);
+    // P(q, nu) for nu in the chunk -> wsX as [nu][q][N][N]
+    if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, n0, p->d_wsX, NN, nk * NN, s)) != GW_OK)
+      return st;
+    const int batch = nc * nk;
+    dim3 g1((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)batch);
+    gw::k_form_A<<<g1, 256, 0, s>>>(v, p->d_wsX, p->d_wsA, (int)N, nk);
+    if ((st = check_launch("k_form_A")) != GW_OK) return st;
+    gw::k_lu<<<batch, 512, p->smem_LU, s>>>(p->d_wsA, p->d_piv, (int)N, p->d_status);
+    if ((st = check_launch("k_lu")) != GW_OK) return st;
+    dim3 g2((unsigned)((N + 31) / 32), (unsigned)batch);
+    gw::k_lu_solve<<<g2, 256, 0, s>>>(p->d_wsA, p->d_piv, v, p->d_wsX, (int)N, nk);
+    if ((st = check_launch("k_lu_solve")) != GW_OK) return st;
+    // W~(R) = (1/N_k) sum_q e^{-iqR} (X - v)
+    if ((st = launch_gather(p, GW_BLOCK_PB, nc, p->d_wsX, NN, nk * NN, v, NN, 0, (double2*)Wt_R_iw, h.n_nu, n0,
+                            1.0 / nk, s)) != GW_OK)
+      return st;
+  }
+  return GW_OK;
+}
+
+gw_status gw_sync(gw_plan_t p, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  DeviceGuard guard(p->device);
+  GW_CUDA(cudaStreamSynchronize(S(stream)));
+  int flag = 0;
+  GW_CUDA(cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    set_last_error("zero pivot in the W solve");
+    return GW_ERR_SINGULAR;
+  }
+  return GW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Kernel argument blocks and kernel declarations (device code only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gw {
+
+struct GatherArgs {
+  const DevEntry* ent;
+  const int* pair_first;   // [n_active + 1] entry range of each active atom pair
+  const double2* phase;    // [E][N_k] e^{+i k.R}
+  int n_k;
+  const double2* F_k;      // dense input
+  long long k_stride, s_stride;
+  int ld;
+  int pb;                  // 1: product-basis blocks, 0: orbital blocks
+  const double2* F_sub;    // optional dense input subtracted from F_k
+  long long sub_k_stride, sub_s_stride;
+  double2* F_R;            // entry layout output
+  int out_n_slices, out_slice0;
+  double scale;
+};
+
+struct ScatterArgs {
+  const DevEntry* ent;
+  const int* pair_start;   // [n_atoms^2 + 1]
+  const int* row_off;      // [n_atoms + 1] orbital or product offsets
+  int n_atoms;
+  const double2* phase;
+  int n_k;
+  const double2* F_R;      // entry layout input
+  int in_n_slices, in_slice0;
+  int pb;
+  double2* F_k;            // dense output
+  long long k_stride, s_stride;
+  int ld;
+};
+
+struct TransformArgs {
+  const DevEntry* ent;
+  const double2* T;        // [n_out][n_in]
+  int n_in, n_out;
+  int pb;
+  const double2* in;
+  double2* out;
+};
+
+struct ContractArgs {
+  const DevEntry* ent;
+  const double* C;         // packed per-species coefficients
+  const double2* G;        // orbital entry layout
+  const double2* W;        // product entry layout (Sigma only)
+  double2* out;
+  int n_tau;
+  int spin;
+  int mirror_tau;          // P: write the mirrored node as the conjugate
+  int g_n_slices, g_slice; // Sigma: slices of G and a fixed slice (or -1: = blockIdx.y)
+  int w_n_slices;
+  int out_n_slices;
+  double sign;
+};
+
+__global__ void k_gather_k_to_R(GatherArgs g);
+__global__ void k_scatter_R_to_k(ScatterArgs g);
+__global__ void k_transform(TransformArgs g);
+__global__ void k_polarizability_fp64(ContractArgs g);
+__global__ void k_self_energy_fp64(ContractArgs g);
+__global__ void k_form_A(const double2* __restrict__ v, const double2* __restrict__ P,
+                         double2* __restrict__ A, int N, int n_k);
+__global__ void k_lu(double2* __restrict__ A, int* __restrict__ piv, int N, int* status);
+__global__ void k_lu_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
+                           const double2* __restrict__ v, double2* __restrict__ X, int N, int n_k);
+
+constexpr int kKCHost = 16;  // must match kKC in kernels_fp64.cu
+
+}  // namespace gw

@@ -1,0 +1,480 @@
+// FP64 kernels of the sweep: lattice Fourier gather/scatter over the pair list
+// (Sec. 2), tau <-> i omega transforms (Appendix A grid), the P and Sigma
+// contractions of Eqs. P_MM and S_MM, and the batched W solve of Eq. W_1.
+//
+// Complex numbers are double2 (re, im).  Every kernel is bounds-checked against
+// the sizes it is given; launch shapes are computed in launch_fp64.cu.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace gw {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c + a * conj(b)
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.y, b.x, fma(-a.x, b.y, c.y)));
+}
+// c + conj(a) * b
+__device__ __forceinline__ double2 cfma_conj_a(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+// c + r * b (r real)
+__device__ __forceinline__ double2 rfma(double r, double2 b, double2 c) {
+  return make_double2(fma(r, b.x, c.x), fma(r, b.y, c.y));
+}
+
+// ---------------------------------------------------------------------------
+// k -> R gather:  F_R[e][s][i][j] = scale * sum_k conj(ph[e][k]) (F_k - F_sub)[k][s][oa+i][ob+j]
+// grid: (active pair, slice, element chunk of blockDim.x)
+// ---------------------------------------------------------------------------
+constexpr int kGatherEnt = 8;
+
+__global__ void k_gather_k_to_R(GatherArgs g) {
+  const int p = blockIdx.x;
+  const int s = blockIdx.y;
+  const int e0 = g.pair_first[p];
+  const int e1 = g.pair_first[p + 1];
+  const DevEntry E0 = g.ent[e0];
+  const int rows = g.pb ? E0.Ka : E0.na;
+  const int cols = g.pb ? E0.Kb : E0.nb;
+  const int ro = g.pb ? E0.pa : E0.oa;
+  const int co = g.pb ? E0.pb : E0.ob;
+  const int blk = rows * cols;
+  const int idx = blockIdx.z * blockDim.x + threadIdx.x;
+  if (idx >= blk) return;
+  const int i = idx / cols, j = idx - i * cols;
+  const long long in_el = (long long)(ro + i) * g.ld + (co + j);
+  for (int eb = e0; eb < e1; eb += kGatherEnt) {
+    const int ne = min(kGatherEnt, e1 - eb);
+    double2 acc[kGatherEnt];
+#pragma unroll
+    for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
+    for (int k = 0; k < g.n_k; ++k) {
+      double2 v = g.F_k[(long long)k * g.k_stride + (long long)s * g.s_stride + in_el];
+      if (g.F_sub) {
+        double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
+        v.x -= w.x;
+        v.y -= w.y;
+      }
+#pragma unroll
+      for (int m = 0; m < kGatherEnt; ++m)
+        if (m < ne) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < kGatherEnt; ++m) {
+      if (m < ne) {
+        const DevEntry& E = g.ent[eb + m];
+        const long long off = g.pb ? E.off_pb : E.off_orb;
+        double2 r = make_double2(acc[m].x * g.scale, acc[m].y * g.scale);
+        g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * blk + idx] = r;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// R -> k scatter:  F_k[k][s][oa+i][ob+j] = sum_{e in (a,b)} ph[e][k] F_R[e][s][i][j]
+// grid: (ordered atom pair a*n_atoms+b, slice, element chunk)
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_R_to_k(ScatterArgs g) {
+  const int p = blockIdx.x;
+  const int s = blockIdx.y;
+  const int a = p / g.n_atoms, b = p - (p / g.n_atoms) * g.n_atoms;
+  const int ro = g.row_off[a], co = g.row_off[b];
+  const int rows = g.row_off[a + 1] - ro, cols = g.row_off[b + 1] - co;
+  const int blk = rows * cols;
+  const int idx = blockIdx.z * blockDim.x + threadIdx.x;
+  if (idx >= blk) return;
+  const int i = idx / cols, j = idx - i * cols;
+  const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
+  const long long out_el = (long long)(ro + i) * g.ld + (co + j);
+  for (int eb = e0; eb < e1 || eb == e0; eb += kGatherEnt) {
+    const int ne = max(0, min(kGatherEnt, e1 - eb));
+    double2 v[kGatherEnt];
+#pragma unroll
+    for (int m = 0; m < kGatherEnt; ++m) {
+      v[m] = make_double2(0.0, 0.0);
+      if (m < ne) {
+        const DevEntry& E = g.ent[eb + m];
+        const long long off = g.pb ? E.off_pb : E.off_orb;
+        v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * blk + idx];
+      }
+    }
+    for (int k = 0; k < g.n_k; ++k) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int m = 0; m < kGatherEnt; ++m)
+        if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
+      double2* o = g.F_k + (long long)k * g.k_stride + (long long)s * g.s_stride + out_el;
+      if (eb == e0) {
+        *o = acc;
+      } else {
+        double2 t = *o;
+        *o = cadd(t, acc);
+      }
+    }
+    if (e1 <= e0) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tau <-> i omega:  out[e][m][c] = sum_i T[m][i] in[e][i][c]
+// grid: (entry, column chunk of 32); block (32, 8); input tile staged in smem.
+// ---------------------------------------------------------------------------
+__global__ void k_transform(TransformArgs g) {
+  extern __shared__ double2 tile[];  // [n_in][32]
+  const int e = blockIdx.x;
+  const DevEntry E = g.ent[e];
+  const int blk = g.pb ? E.Ka * E.Kb : E.na * E.nb;
+  const long long off = g.pb ? E.off_pb : E.off_orb;
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= blk) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = c0 + tx;
+  const double2* in = g.in + off * g.n_in;
+  double2* out = g.out + off * g.n_out;
+  for (int i = ty; i < g.n_in; i += blockDim.y)
+    tile[i * 32 + tx] = (c < blk) ? in[(long long)i * blk + c] : make_double2(0.0, 0.0);
+  __syncthreads();
+  if (c >= blk) return;
+  for (int m = ty; m < g.n_out; m += blockDim.y) {
+    const double2* Tm = g.T + (long long)m * g.n_in;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < g.n_in; ++i) acc = cfma(Tm[i], tile[i * 32 + tx], acc);
+    out[(long long)m * blk + c] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. P_MM, FP64.  One block per (entry, tau node i); with C symmetric in
+// (L, L'') the block also writes the mirrored node N-1-i as the conjugate.
+//   X[K][L''][L'] = sum_L C^a[K][L][L''] G(tau_i)[L][L']
+//   Y[K][L'][L''']= sum_L'' X[K][L''][L'] conj(G(beta - tau_i)[L''][L'''])
+//   P[K][K']      = -s sum_{L' L'''} Y[K][L'][L'''] C^b[K'][L'][L''']
+// ---------------------------------------------------------------------------
+constexpr int kKC = 16;  // product functions of atom a per pass
+
+__global__ void k_polarizability_fp64(ContractArgs g) {
+  extern __shared__ double2 sm[];
+  const int e = blockIdx.x;
+  const int it = blockIdx.y;
+  const DevEntry E = g.ent[e];
+  const int na = E.na, nb = E.nb, Ka = E.Ka, Kb = E.Kb;
+  const int N = g.n_tau;
+  const int im = N - 1 - it;
+  double2* G1 = sm;                 // [na][nb]
+  double2* G2 = G1 + na * nb;       // [na][nb]
+  double2* X = G2 + na * nb;        // [kKC][na][nb]
+  double2* Y = X + kKC * na * nb;   // [kKC][nb][nb]
+  const double2* Gin = g.G + E.off_orb * N;
+  for (int x = threadIdx.x; x < na * nb; x += blockDim.x) {
+    G1[x] = Gin[(long long)it * na * nb + x];
+    G2[x] = Gin[(long long)im * na * nb + x];
+  }
+  __syncthreads();
+  const double* Ca = g.C + E.ca;
+  const double* Cb = g.C + E.cb;
+  double2* Pout = g.out + E.off_pb * N;
+  const double ms = -(double)g.spin;
+  const bool mirror = g.mirror_tau && (im != it);
+  for (int k0 = 0; k0 < Ka; k0 += kKC) {
+    const int kc = min(kKC, Ka - k0);
+    for (int x = threadIdx.x; x < kc * na * nb; x += blockDim.x) {
+      const int K = x / (na * nb);
+      const int r = x - K * na * nb;
+      const int L2 = r / nb, L1 = r - L2 * nb;  // X[K][L''=L2][L'=L1]
+      const double* c = Ca + (long long)(k0 + K) * na * na;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int L = 0; L < na; ++L) acc = rfma(c[L * na + L2], G1[L * nb + L1], acc);
+      X[x] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < kc * nb * nb; x += blockDim.x) {
+      const int K = x / (nb * nb);
+      const int r = x - K * nb * nb;
+      const int L1 = r / nb, L3 = r - L1 * nb;  // Y[K][L'=L1][L'''=L3]
+      const double2* xk = X + K * na * nb;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int L2 = 0; L2 < na; ++L2) acc = cfmac(xk[L2 * nb + L1], G2[L2 * nb + L3], acc);
+      Y[x] = acc;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < kc * Kb; x += blockDim.x) {
+      const int K = x / Kb, Kp = x - (x / Kb) * Kb;
+      const double2* y = Y + K * nb * nb;
+      const double* c = Cb + (long long)Kp * nb * nb;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int j = 0; j < nb * nb; ++j) acc = rfma(c[j], y[j], acc);
+      acc.x *= ms;
+      acc.y *= ms;
+      const long long o = (long long)(k0 + K) * Kb + Kp;
+      Pout[(long long)it * Ka * Kb + o] = acc;
+      if (mirror) Pout[(long long)im * Ka * Kb + o] = make_double2(acc.x, -acc.y);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. S_MM, FP64.  One block per (entry, slice).
+//   B[K][L'][L''']  = sum_K' W[K][K'] C^b[K'][L'][L''']
+//   D[K][L''][L']   = sum_L''' G[L''][L'''] B[K][L'][L''']
+//   S[L][L']       += sum_{K, L''} C^a[K][L][L''] D[K][L''][L']
+// out = sign * S  (sign -1: dynamic part; +1 with G(beta-) and v: exchange)
+// ---------------------------------------------------------------------------
+__global__ void k_self_energy_fp64(ContractArgs g) {
+  extern __shared__ double2 sm[];
+  const int e = blockIdx.x;
+  const int s = blockIdx.y;
+  const DevEntry E = g.ent[e];
+  const int na = E.na, nb = E.nb, Ka = E.Ka, Kb = E.Kb;
+  double2* Gs = sm;                  // [na][nb]
+  double2* B = Gs + na * nb;         // [kKC][nb][nb]
+  double2* D = B + kKC * nb * nb;    // [kKC][na][nb]
+  const int gs = (g.g_slice >= 0) ? g.g_slice : s;
+  const double2* Gin = g.G + E.off_orb * g.g_n_slices + (long long)gs * na * nb;
+  for (int x = threadIdx.x; x < na * nb; x += blockDim.x) Gs[x] = Gin[x];
+  const double2* W = g.W + E.off_pb * g.w_n_slices + (long long)s * Ka * Kb;
+  const double* Ca = g.C + E.ca;
+  const double* Cb = g.C + E.cb;
+  double2 acc = make_double2(0.0, 0.0);
+  const int own = threadIdx.x;  // output (L, L') owned by this thread
+  __syncthreads();
+  for (int k0 = 0; k0 < Ka; k0 += kKC) {
+    const int kc = min(kKC, Ka - k0);
+    for (int x = threadIdx.x; x < kc * nb * nb; x += blockDim.x) {
+      const int K = x / (nb * nb);
+      const int j = x - K * nb * nb;
+      const double2* w = W + (long long)(k0 + K) * Kb;
+      double2 t = make_double2(0.0, 0.0);
+      for (int Kp = 0; Kp < Kb; ++Kp) t = rfma(Cb[(long long)Kp * nb * nb + j], w[Kp], t);
+      B[x] = t;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < kc * na * nb; x += blockDim.x) {
+      const int K = x / (na * nb);
+      const int r = x - K * na * nb;
+      const int L2 = r / nb, L1 = r - L2 * nb;  // D[K][L''=L2][L'=L1]
+      const double2* bk = B + K * nb * nb + L1 * nb;
+      double2 t = make_double2(0.0, 0.0);
+      for (int L3 = 0; L3 < nb; ++L3) t = cfma(Gs[L2 * nb + L3], bk[L3], t);
+      D[x] = t;
+    }
+    __syncthreads();
+    if (own < na * nb) {
+      const int L = own / nb, L1 = own - (own / nb) * nb;
+      for (int K = 0; K < kc; ++K) {
+        const double* c = Ca + (long long)(k0 + K) * na * na + L * na;
+        const double2* dk = D + K * na * nb;
+        for (int L2 = 0; L2 < na; ++L2) acc = rfma(c[L2], dk[L2 * nb + L1], acc);
+      }
+    }
+    __syncthreads();
+  }
+  if (own < na * nb) {
+    double2* o = g.out + E.off_orb * g.out_n_slices + (long long)s * na * nb;
+    o[own] = make_double2(g.sign * acc.x, g.sign * acc.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// W solve (Eq. W_1): A_b = I - v(q_b) P_b, LU with partial pivoting, X_b = A_b^{-1} v(q_b)
+// ---------------------------------------------------------------------------
+constexpr int kGT = 32;  // tile
+constexpr int kGK = 16;  // k step
+
+// A[b] = I - v[q(b)] * P[b], q(b) = b % n_k; 256 threads, 32x32 tile, 2x2 per thread.
+__global__ void k_form_A(const double2* __restrict__ v, const double2* __restrict__ P,
+                         double2* __restrict__ A, int N, int n_k) {
+  __shared__ double2 As[kGT][kGK + 1];
+  __shared__ double2 Bs[kGK][kGT + 1];
+  const int b = blockIdx.z;
+  const int q = b % n_k;
+  const double2* V = v + (long long)q * N * N;
+  const double2* Pb = P + (long long)b * N * N;
+  double2* Ab = A + (long long)b * N * N;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  double2 acc[2][2];
+  for (int u = 0; u < 2; ++u)
+    for (int w = 0; w < 2; ++w) acc[u][w] = make_double2(0.0, 0.0);
+  for (int l0 = 0; l0 < N; l0 += kGK) {
+    for (int x = threadIdx.x; x < kGT * kGK; x += blockDim.x) {
+      int r = x / kGK, c = x - r * kGK;
+      int gi = i0 + r, gl = l0 + c;
+      As[r][c] = (gi < N && gl < N) ? V[(long long)gi * N + gl] : make_double2(0.0, 0.0);
+      int r2 = x / kGT, c2 = x - r2 * kGT;
+      int gl2 = l0 + r2, gj = j0 + c2;
+      Bs[r2][c2] = (gl2 < N && gj < N) ? Pb[(long long)gl2 * N + gj] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < kGK; ++l) {
+      double2 a0 = As[ty][l], a1 = As[ty + 16][l];
+      double2 b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+      acc[0][0] = cfma(a0, b0, acc[0][0]);
+      acc[0][1] = cfma(a0, b1, acc[0][1]);
+      acc[1][0] = cfma(a1, b0, acc[1][0]);
+      acc[1][1] = cfma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  for (int u = 0; u < 2; ++u)
+    for (int w = 0; w < 2; ++w) {
+      int gi = i0 + ty + 16 * u, gj = j0 + tx + 16 * w;
+      if (gi < N && gj < N) {
+        double2 r = make_double2(-acc[u][w].x, -acc[u][w].y);
+        if (gi == gj) r.x += 1.0;
+        Ab[(long long)gi * N + gj] = r;
+      }
+    }
+}
+
+// In-place LU with partial pivoting (|re| + |im| pivot measure), one block per matrix.
+// piv[k] is the row exchanged with row k at step k.  A zero pivot sets *status.
+__global__ void k_lu(double2* __restrict__ A, int* __restrict__ piv, int N, int* status) {
+  extern __shared__ unsigned char smraw[];
+  double2* rowk = reinterpret_cast<double2*>(smraw);  // [N]
+  double2* colk = rowk + N;                            // [N]
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  const int b = blockIdx.x;
+  double2* M = A + (long long)b * N * N;
+  int* pv = piv + (long long)b * N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int k = 0; k < N; ++k) {
+    // pivot search
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < N; i += nt) {
+      double2 z = M[(long long)i * N + k];
+      double m = fabs(z.x) + fabs(z.y);
+      if (m > best) { best = m; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    __syncthreads();
+    if (wid == 0) {
+      best = (lane < nw) ? rv[lane] : -1.0;
+      bi = (lane < nw) ? ri[lane] : N;
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        ri[0] = bi;
+        pv[k] = bi;
+        if (!(best > 0.0)) atomicExch(status, 1);
+      }
+    }
+    __syncthreads();
+    const int p = ri[0];
+    // swap rows k and p, keep row k in smem
+    for (int j = tid; j < N; j += nt) {
+      double2 zk = M[(long long)k * N + j];
+      double2 zp = M[(long long)p * N + j];
+      if (p != k) {
+        M[(long long)k * N + j] = zp;
+        M[(long long)p * N + j] = zk;
+      }
+      rowk[j] = (p != k) ? zp : zk;
+    }
+    __syncthreads();
+    const double2 d = rowk[k];
+    const double den = d.x * d.x + d.y * d.y;
+    const double2 inv = (den > 0.0) ? make_double2(d.x / den, -d.y / den) : make_double2(0.0, 0.0);
+    for (int i = k + 1 + tid; i < N; i += nt) {
+      double2 l = cmul(M[(long long)i * N + k], inv);
+      M[(long long)i * N + k] = l;
+      colk[i] = l;
+    }
+    __syncthreads();
+    const int m = N - k - 1;
+    for (long long x = tid; x < (long long)m * m; x += nt) {
+      const int i = k + 1 + (int)(x / m);
+      const int j = k + 1 + (int)(x - (x / m) * m);
+      double2 l = colk[i];
+      double2 u = rowk[j];
+      double2 z = M[(long long)i * N + j];
+      z = cfma(make_double2(-l.x, -l.y), u, z);
+      M[(long long)i * N + j] = z;
+    }
+    __syncthreads();
+  }
+}
+
+// X[b][:, c0:c0+32] = A_b^{-1} v[q(b)][:, c0:c0+32] from the LU factors; 256 threads.
+__global__ void k_lu_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
+                           const double2* __restrict__ v, double2* __restrict__ X, int N, int n_k) {
+  const int b = blockIdx.y;
+  const int q = b % n_k;
+  const int c0 = blockIdx.x * 32;
+  const double2* M = LU + (long long)b * N * N;
+  const int* pv = piv + (long long)b * N;
+  const double2* V = v + (long long)q * N * N;
+  double2* Xb = X + (long long)b * N * N;
+  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;  // 8 row lanes
+  const int c = c0 + cx;
+  const bool active = c < N;
+  for (int i = ry; i < N; i += 8)
+    if (active) Xb[(long long)i * N + c] = V[(long long)i * N + c];
+  __syncthreads();
+  if (ry == 0 && active) {
+    for (int k = 0; k < N; ++k) {
+      int p = pv[k];
+      if (p != k) {
+        double2 t = Xb[(long long)k * N + c];
+        Xb[(long long)k * N + c] = Xb[(long long)p * N + c];
+        Xb[(long long)p * N + c] = t;
+      }
+    }
+  }
+  __syncthreads();
+  // forward: unit lower triangle
+  for (int k = 0; k < N - 1; ++k) {
+    double2 xk = active ? Xb[(long long)k * N + c] : make_double2(0.0, 0.0);
+    for (int i = k + 1 + ry; i < N; i += 8) {
+      if (active) {
+        double2 l = M[(long long)i * N + k];
+        double2 z = Xb[(long long)i * N + c];
+        Xb[(long long)i * N + c] = cfma(make_double2(-l.x, -l.y), xk, z);
+      }
+    }
+    __syncthreads();
+  }
+  // backward: upper triangle
+  for (int k = N - 1; k >= 0; --k) {
+    if (ry == 0 && active) {
+      double2 d = M[(long long)k * N + k];
+      double den = d.x * d.x + d.y * d.y;
+      double2 inv = (den > 0.0) ? make_double2(d.x / den, -d.y / den) : make_double2(0.0, 0.0);
+      Xb[(long long)k * N + c] = cmul(Xb[(long long)k * N + c], inv);
+    }
+    __syncthreads();
+    double2 xk = active ? Xb[(long long)k * N + c] : make_double2(0.0, 0.0);
+    for (int i = ry; i < k; i += 8) {
+      if (active) {
+        double2 u = M[(long long)i * N + k];
+        double2 z = Xb[(long long)i * N + c];
+        Xb[(long long)i * N + c] = cfma(make_double2(-u.x, -u.y), xk, z);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gw

@@ -32,6 +32,7 @@ __all__ = [
     "SynthCell",
     "make_config",
     "chain_cell",
+    "mixed_species_cell",
     "tau_nodes",
     "matsubara_sets",
     "fermi",
@@ -391,12 +392,12 @@ def matsubara_sets(n_tau: int) -> Tuple[np.ndarray, np.ndarray]:
     """Sampled Matsubara indices (fermionic n: (2n+1)pi/beta, bosonic m: 2m pi/beta).
 
     The lowest round(3 N/8) non-negative fermionic indices are equidistant, the
-    rest of the N/2 non-negative ones grow geometrically up to 3N (the sparse,
-    progressively spaced shape of the paper's appendix A).  The fermionic set
-    is symmetric (n <-> -n-1, N indices); the bosonic set is {0, +-(n+1)}
-    (N + 1 indices).  Ascending order.
+    rest of the ceil(N/2) non-negative ones grow geometrically up to 3N (the
+    sparse, progressively spaced shape of the paper's appendix A).  The
+    fermionic set is symmetric (n <-> -n-1, 2 ceil(N/2) indices); the bosonic
+    set is {0, +-(n+1)} (2 ceil(N/2) + 1 indices).  Ascending order.
     """
-    npos = n_tau // 2
+    npos = (n_tau + 1) // 2
     neq = max(1, int(round(0.375 * n_tau)))
     nmax = 3 * n_tau
     idx = list(range(min(neq, npos)))
@@ -476,4 +477,22 @@ def chain_cell(n_cells_k: int = 8, t_hop: float = 0.25, beta: float = 20.0, n_ta
     e = np.linalg.eigvalsh(cell.H_k)[:, 0]
     cell.mu = float(np.median(e)) + 0.013  # a metal: mu inside the band
     del rng
+    return cell
+
+
+def mixed_species_cell(n_tau: int = 15, kmesh=(2, 2, 2), cutoff: float = 0.0, seed: int = 31,
+                       n_orb=(4, 5), n_prod=(8, 19), symmetric_C: bool = True) -> SynthCell:
+    """Two species on a simple-cubic a = 5 bohr two-atom cell: ragged blocks
+    (n_a != n_b, K_a != K_b, K not a multiple of 16), an odd tau count (the middle
+    node is its own mirror) and, optionally, coefficients C not symmetric in (L, L'')."""
+    lat = np.eye(3) * 5.0
+    frac = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    sp = [Species("A", n_orb[0], n_prod[0], None), Species("B", n_orb[1], n_prod[1], None)]
+    cell = SynthCell("mixed2", lat, frac, np.array([0, 1], np.int32), sp, tuple(kmesh), 30.0, n_tau,
+                     cutoff, seed=seed, gap=None, hop_cutoff=8.0)
+    cell.build()
+    if not symmetric_C:
+        rng = np.random.default_rng(seed + 1)
+        for spc in cell.species:
+            spc.C = rng.standard_normal(spc.C.shape) / spc.n_orb
     return cell

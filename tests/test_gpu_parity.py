@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every row of the sweep is compared element by element with the oracle on the
+same seeded inputs: the k -> R gather, the P contraction, the tau <-> i omega
+transforms, the W solve, the Sigma contraction with its exchange term, and the
+R -> k scatter; then the whole chain end to end.  FP64 bar: relative Frobenius
+error <= 1e-10 (the tolerance stated for the plain FP64 path).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(autouse=True)
+def _need_cuda():
+    _torch()
+
+
+def dev(x):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128).reshape(-1)).to("cuda")
+
+
+def host(t):
+    _torch().cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def pack(blocks):
+    return np.concatenate([np.ascontiguousarray(b).reshape(-1) for b in blocks]).astype(np.complex128)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Sys:
+    """One synthetic system: the plan, the oracle and the seeded inputs."""
+
+    def __init__(self, cell, **plan_kw):
+        from paper_1911_05633_gb300 import gw
+        self.cell = cell
+        self.plan = gw.Plan.from_cell(cell, **plan_kw)
+        self.orc = oracle.OracleSystem(cell)
+        assert np.array_equal(self.plan.entries, self.orc.entries)
+        self.G_k = cell.green_k_tau()
+        self.v_q, self.v_class = cell.coulomb()
+        self.nt = cell.n_tau
+
+    def G_R(self):
+        if not hasattr(self, "_GR"):
+            c = self.cell
+            self._GR = oracle.fourier_k_to_R(self.G_k, self.orc.entries, self.orc.kmesh, c.orb_offsets, c.orb_offsets)
+        return self._GR
+
+
+_CACHE = {}
+
+
+def system(name):
+    if name not in _CACHE:
+        if name == "c0":
+            _CACHE[name] = Sys(synth.make_config(0))
+        elif name == "mixed":
+            _CACHE[name] = Sys(synth.mixed_species_cell())
+        elif name == "mixed_nonsym":
+            _CACHE[name] = Sys(synth.mixed_species_cell(symmetric_C=False, n_tau=10))
+        elif name == "c1":
+            _CACHE[name] = Sys(synth.make_config(1))
+        elif name == "c1_cut5":
+            _CACHE[name] = Sys(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)))
+        else:
+            raise KeyError(name)
+    return _CACHE[name]
+
+
+SMALL = ["c0", "mixed", "mixed_nonsym", "c1_cut5"]
+
+
+@pytest.mark.parametrize("name", SMALL + ["c1"])
+def test_green_k_to_R(name):
+    s = system(name)
+    GR = host(s.plan.green_k_to_R(dev(s.G_k)))
+    assert rel(GR, pack(s.G_R())) < TOL
+
+
+@pytest.mark.parametrize("name", SMALL + ["c1"])
+def test_polarizability(name):
+    s = system(name)
+    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    P = host(s.plan.polarizability_tau(dev(pack(s.G_R()))))
+    assert rel(P, pack(ref)) < TOL
+
+
+@pytest.mark.parametrize("name", SMALL + ["c1"])
+@pytest.mark.parametrize("st,direction,kind", [("B", "tau_to_iw", "pb"), ("B", "iw_to_tau", "pb"),
+                                               ("F", "tau_to_iw", "orb"), ("F", "iw_to_tau", "orb")])
+def test_transform(name, st, direction, kind):
+    s = system(name)
+    rng = np.random.default_rng(17)
+    T = s.orc.B_fwd if st == "B" else s.orc.F_fwd
+    if direction == "iw_to_tau":
+        T = s.orc.B_inv if st == "B" else s.orc.F_inv
+    n_in = T.shape[1]
+    blocks = []
+    for row in s.orc.entries:
+        a, b = int(row[0]), int(row[1])
+        r = s.cell.n_prod_of(a) if kind == "pb" else s.cell.n_orb_of(a)
+        c = s.cell.n_prod_of(b) if kind == "pb" else s.cell.n_orb_of(b)
+        blocks.append(rng.standard_normal((n_in, r, c)) + 1j * rng.standard_normal((n_in, r, c)))
+    ref = oracle.transform(T, blocks)
+    out = host(s.plan.transform_tau_iw(st, direction, kind, dev(pack(blocks))))
+    assert rel(out, pack(ref)) < TOL
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_screened_W(name):
+    s = system(name)
+    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    Piw = oracle.transform(s.orc.B_fwd, PR)
+    ref, _ = oracle.screened_W(Piw, s.orc.entries, s.v_q, s.orc.kmesh, s.cell.pb_offsets)
+    W = host(s.plan.screened_W_iw(dev(pack(Piw)), dev(s.v_q)))
+    s.plan.sync()
+    assert rel(W, pack(ref)) < TOL
+
+
+def test_screened_W_sampled_full_size():
+    """The 8-atom, 4x4x4, 48-node workload: W~ checked on three bosonic frequencies."""
+    s = system("c1")
+    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    Piw = oracle.transform(s.orc.B_fwd, PR)
+    W = host(s.plan.screened_W_iw(dev(pack(Piw)), dev(s.v_q)))
+    s.plan.sync()
+    nn = s.cell.nu_idx.size
+    sel = [0, nn // 2, nn - 1]
+    ref, _ = oracle.screened_W([x[sel] for x in Piw], s.orc.entries, s.v_q, s.orc.kmesh, s.cell.pb_offsets)
+    off = s.plan.off_pb
+    num = den = 0.0
+    for e in range(len(off) - 1):
+        blk = W[nn * off[e]: nn * off[e + 1]].reshape(nn, -1)[sel]
+        r = ref[e].reshape(len(sel), -1)
+        num += np.linalg.norm(blk - r) ** 2
+        den += np.linalg.norm(r) ** 2
+    assert (num / den) ** 0.5 < TOL
+
+
+def _random_W(s, seed=23):
+    rng = np.random.default_rng(seed)
+    out = []
+    for row in s.orc.entries:
+        a, b = int(row[0]), int(row[1])
+        Ka, Kb = s.cell.n_prod_of(a), s.cell.n_prod_of(b)
+        out.append(rng.standard_normal((s.nt, Ka, Kb)) + 1j * rng.standard_normal((s.nt, Ka, Kb)))
+    return out
+
+
+@pytest.mark.parametrize("name", SMALL + ["c1"])
+def test_self_energy_and_exchange(name):
+    s = system(name)
+    WR = _random_W(s)
+    vR = s.orc.v_R(s.v_class)
+    ref = oracle.self_energy_R(s.G_R(), WR, s.orc.entries, s.orc.C_atom)
+    refx = oracle.exchange_R(s.G_R(), vR, s.orc.entries, s.orc.C_atom)
+    Sig, Sigx = s.plan.self_energy_tau(dev(pack(s.G_R())), dev(pack(WR)), v_R=dev(pack(vR)))
+    assert rel(host(Sig), pack(ref)) < TOL
+    assert rel(host(Sigx), pack(refx)) < TOL
+
+
+@pytest.mark.parametrize("name", SMALL + ["c1"])
+def test_fourier_R_to_k(name):
+    s = system(name)
+    rng = np.random.default_rng(5)
+    blocks = []
+    for row in s.orc.entries:
+        a, b = int(row[0]), int(row[1])
+        na, nb = s.cell.n_orb_of(a), s.cell.n_orb_of(b)
+        blocks.append(rng.standard_normal((3, na, nb)) + 1j * rng.standard_normal((3, na, nb)))
+    oo = s.cell.orb_offsets
+    ref = oracle.fourier_R_to_k(blocks, s.orc.entries, s.orc.kmesh, oo, oo)
+    out = host(s.plan.fourier_R_to_k("orb", 3, dev(pack(blocks))))
+    assert rel(out, ref.reshape(-1)) < TOL
+    # product-basis blocks, one slice (the k -> R inverse on all-class systems)
+    vq = host(s.plan.fourier_R_to_k("pb", 1, dev(pack(s.orc.v_R(s.v_class)))))
+    po = s.cell.pb_offsets
+    refv = oracle.fourier_R_to_k([x[None] for x in s.orc.v_R(s.v_class)], s.orc.entries, s.orc.kmesh, po, po)
+    assert rel(vq, refv.reshape(-1)) < TOL
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5"])
+def test_whole_sweep(name):
+    """All rows chained on the device from G(k, tau) and v(q); every stage vs the oracle."""
+    s = system(name)
+    p = s.plan
+    r = s.orc.sweep(s.G_k, s.v_q, s.v_class)
+    GR = p.green_k_to_R(dev(s.G_k))
+    PR = p.polarizability_tau(GR)
+    Piw = p.transform_tau_iw("B", "tau_to_iw", "pb", PR)
+    Wiw = p.screened_W_iw(Piw, dev(s.v_q))
+    WR = p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw)
+    vR = p.fourier_k_to_R("pb", 1, dev(s.v_q))
+    Sig, Sigx = p.self_energy_tau(GR, WR, v_R=vR)
+    Siw = p.transform_tau_iw("F", "tau_to_iw", "orb", Sig)
+    Sk = p.fourier_R_to_k("orb", s.cell.omega_idx.size, Siw)
+    Sxk = p.fourier_R_to_k("orb", 1, Sigx)
+    p.sync()
+    assert rel(host(GR), pack(r["G_R"])) < TOL
+    assert rel(host(PR), pack(r["P_R"])) < TOL
+    assert rel(host(Piw), pack(r["P_iw"])) < TOL
+    assert rel(host(Wiw), pack(r["Wt_iw"])) < TOL
+    assert rel(host(WR), pack(r["Wt_R"])) < TOL
+    assert rel(host(vR), pack(r["v_R"])) < TOL
+    assert rel(host(Sig), pack(r["Sig_R"])) < TOL
+    assert rel(host(Sigx), pack(r["Sigx_R"])) < TOL
+    assert rel(host(Sk), r["Sig_k"].reshape(-1)) < TOL
+    assert rel(host(Sxk), r["Sigx_k"].reshape(-1)) < TOL
+
+
+def test_largest_blocks():
+    """n = 16 orbitals and K = 128 product functions (the compiled maxima), one atom."""
+    lat = np.eye(3) * 6.0
+    sp = [synth.Species("big", 16, 128, None)]
+    cell = synth.SynthCell("big1", lat, np.zeros((1, 3)), np.zeros(1, np.int32), sp, (2, 1, 1), 20.0, 8, 0.0,
+                           seed=77, gap=None, hop_cutoff=6.5).build()
+    s = Sys(cell)
+    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, cell.spin)
+    assert rel(host(s.plan.polarizability_tau(dev(pack(s.G_R())))), pack(ref)) < TOL
+    WR = _random_W(s)
+    refS = oracle.self_energy_R(s.G_R(), WR, s.orc.entries, s.orc.C_atom)
+    assert rel(host(s.plan.self_energy_tau(dev(pack(s.G_R())), dev(pack(WR)))), pack(refS)) < TOL
+
+
+def test_full_size_72_atoms_sampled():
+    """The 72-atom, 2x2x2, 64-node workload: G(R), P and Sigma on sampled entries."""
+    cell = synth.make_config(2)
+    from paper_1911_05633_gb300 import gw
+    plan = gw.Plan.from_cell(cell)
+    ent = plan.entries
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(len(ent), 12, replace=False))
+    Gk = cell.green_k_tau()
+    GR_dev = plan.green_k_to_R(dev(Gk))
+    GR = host(GR_dev)
+    oo = cell.orb_offsets
+    refG = oracle.fourier_k_to_R(Gk, ent[sample], cell.kmesh, oo, oo)
+    del Gk
+    nt = cell.n_tau
+    C_atom = [cell.species[s].C for s in cell.species_of_atom]
+    P = host(plan.polarizability_tau(GR_dev))
+    refP = oracle.polarizability_R(refG, ent[sample], C_atom, cell.spin)
+    # W~ is zero except on the sampled entries (the full array would be 14 GB on the host)
+    torch = _torch()
+    W_dev = torch.zeros(plan.len("pb", nt), dtype=torch.complex128, device="cuda")
+    rw = np.random.default_rng(9)
+    WS = []
+    for e in sample:
+        w = rw.standard_normal((nt, 64, 64)) + 1j * rw.standard_normal((nt, 64, 64))
+        WS.append(w)
+        W_dev[nt * plan.off_pb[e]: nt * plan.off_pb[e + 1]] = dev(w)
+    Sig = host(plan.self_energy_tau(GR_dev, W_dev))
+    refS = oracle.self_energy_R(refG, WS, ent[sample], C_atom)
+    keep = np.zeros(len(ent), bool)
+    keep[sample] = True
+    for e in np.nonzero(~keep)[0][:50]:
+        assert not Sig[nt * plan.off_orb[e]: nt * plan.off_orb[e + 1]].any()
+    for j, e in enumerate(sample):
+        g = GR[nt * plan.off_orb[e]: nt * plan.off_orb[e + 1]]
+        assert rel(g, refG[j].reshape(-1)) < TOL
+        pe = P[nt * plan.off_pb[e]: nt * plan.off_pb[e + 1]]
+        assert rel(pe, refP[j].reshape(-1)) < TOL
+        se = Sig[nt * plan.off_orb[e]: nt * plan.off_orb[e + 1]]
+        assert rel(se, refS[j].reshape(-1)) < TOL

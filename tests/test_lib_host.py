@@ -1,0 +1,114 @@
+"""Host-side checks of libgw: the library loads, exports what include/gw.h
+declares, and its plan tables (pair list, k-mesh rule, transform matrices)
+agree with the oracle.  No GPU is needed: plans are built with host_only."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(gw_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(gwlib):
+    names = _declared_symbols()
+    assert {"gw_plan_create", "gw_polarizability_tau", "gw_self_energy_tau", "gw_screened_W_iw"} <= names
+    for n in sorted(names):
+        assert hasattr(gwlib, n), n
+    from paper_1911_05633_gb300 import gw
+    assert set(gw.EXPORTED) <= names
+
+
+def _plan(cell, **kw):
+    from paper_1911_05633_gb300 import gw
+    return gw.Plan.from_cell(cell, host_only=True, **kw)
+
+
+@pytest.mark.parametrize("which", ["c0", "c1", "mixed", "c1_short_cutoff", "c2_16"])
+def test_plan_tables_match_oracle(gwlib, which):
+    if which == "c0":
+        cell = synth.make_config(0)
+    elif which == "c1":
+        cell = synth.make_config(1, build=False)
+        cell._draw_basis(np.random.default_rng(0))
+    elif which == "mixed":
+        cell = synth.mixed_species_cell()
+    elif which == "c1_short_cutoff":
+        cell = synth.make_config(1, build=False, cutoff=5.0)
+        cell._draw_basis(np.random.default_rng(0))
+    else:
+        cell = synth.make_config(2, atoms=16, build=False)
+        cell._draw_basis(np.random.default_rng(0))
+    p = _plan(cell)
+    ent = oracle.pair_list(cell.lattice, cell.frac, cell.kmesh, cell.cutoff)
+    assert np.array_equal(p.entries, ent)
+    if cell.cutoff > 0:
+        assert tuple(p.info["kmesh_required"]) == oracle.kmesh_rule(cell.lattice, cell.cutoff)
+    # offsets are the prefix sums of the block sizes
+    no = [cell.n_orb_of(int(a)) * cell.n_orb_of(int(b)) for a, b in ent[:, :2]]
+    npb = [cell.n_prod_of(int(a)) * cell.n_prod_of(int(b)) for a, b in ent[:, :2]]
+    assert np.array_equal(p.off_orb, np.concatenate([[0], np.cumsum(no)]))
+    assert np.array_equal(p.off_pb, np.concatenate([[0], np.cumsum(npb)]))
+    for st, idx in (("F", cell.omega_idx), ("B", cell.nu_idx)):
+        T = oracle.fourier_matrix(cell.beta, cell.tau, idx, st)
+        U = oracle.inverse_matrix(T)
+        Tl = p.transform_matrix(st, "tau_to_iw")
+        Ul = p.transform_matrix(st, "iw_to_tau")
+        n = len(cell.tau)
+        assert np.abs(Tl - T).max() < 2.3e-16 * (n * n + np.pi * np.abs(idx).max() + 10) * np.abs(T).max()
+        assert np.abs(Ul - U).max() < 1e-11 * np.abs(U).max()
+        assert np.abs(Ul @ Tl - np.eye(n)).max() < 1e-11
+
+
+def test_plan_errors(gwlib):
+    from paper_1911_05633_gb300 import gw
+    cell = synth.make_config(1, build=False)
+    cell._draw_basis(np.random.default_rng(0))
+    # strict k-mesh rule: 2x2x2 is below the rule for a 12-bohr cutoff on this cell
+    with pytest.raises(gw.GwError) as ex:
+        gw.Plan(
+            cell.lattice, cell.frac, cell.species_of_atom, [9], [48], [cell.species[0].C], (2, 2, 2),
+            cell.beta, cell.tau, cell.omega_idx, cell.nu_idx, cell.cutoff, strict_kmesh=True, host_only=True)
+    assert ex.value.status == 4
+    # tau grid not mirror symmetric
+    tau = cell.tau.copy()
+    tau[3] += 1e-3
+    with pytest.raises(gw.GwError) as ex:
+        gw.Plan(cell.lattice, cell.frac, cell.species_of_atom, [9], [48], [cell.species[0].C], cell.kmesh,
+                cell.beta, tau, cell.omega_idx, cell.nu_idx, cell.cutoff, host_only=True)
+    assert ex.value.status == 1
+    # the smallest pair list: a tiny cutoff keeps only the onsite (a, a, R = 0) entries
+    p = gw.Plan(cell.lattice, cell.frac, cell.species_of_atom, [9], [48], [cell.species[0].C], cell.kmesh,
+                cell.beta, cell.tau, cell.omega_idx, cell.nu_idx, 1e-3, host_only=True)
+    assert p.info["n_entries"] == cell.n_atoms
+    assert np.array_equal(p.entries[:, 0], p.entries[:, 1]) and not p.entries[:, 2:].any()
+    # too few Matsubara samples
+    with pytest.raises(gw.GwError) as ex:
+        gw.Plan(cell.lattice, cell.frac, cell.species_of_atom, [9], [48], [cell.species[0].C], cell.kmesh,
+                cell.beta, cell.tau, cell.omega_idx[:10], cell.nu_idx, cell.cutoff, host_only=True)
+    assert ex.value.status == 1
+    # compiled limits
+    big = np.zeros((129, 9, 9))
+    with pytest.raises(gw.GwError) as ex:
+        gw.Plan(cell.lattice, cell.frac, cell.species_of_atom, [9], [129], [big], cell.kmesh,
+                cell.beta, cell.tau, cell.omega_idx, cell.nu_idx, cell.cutoff, host_only=True)
+    assert ex.value.status == 10
+    # compute calls on a host-only plan are refused
+    p = gw.Plan.from_cell(cell, host_only=True)
+    lib = gw.load_library()
+    st = lib.gw_green_k_to_R(p._h, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
+    assert st == 9
+    assert lib.gw_status_string(9) == b"plan has no device state"
