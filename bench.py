@@ -94,10 +94,13 @@ def contraction_flops(cell, entries) -> float:
     return f * cell.n_tau
 
 
-def wsolve_flops(cell) -> float:
-    """A = I - v P (8 N^3), LU (16/3 N^3), N right-hand sides (8 N^3) per (q, nu)."""
+def wsolve_flops(cell, info) -> float:
+    """Gauss-Jordan inverses of v(q) and of v(q)^{-1} - P(q, i nu): 8 N^3 real flops
+    each, over the momenta and frequencies the plan actually solves."""
     N = cell.n_pb_total
-    return (8.0 + 16.0 / 3.0 + 8.0) * N ** 3 * cell.n_k * cell.nu_idx.size
+    nq = info["n_q_solved"]
+    nnu = int((cell.nu_idx >= 0).sum()) if info["w_symmetric"] else cell.nu_idx.size
+    return 8.0 * N ** 3 * nq * (nnu + 1)
 
 
 # --------------------------------------------------------------------------------------
@@ -222,8 +225,10 @@ class Sweep:
     def kernel_launches(self) -> int:
         """Kernels this library launches per sweep (counted from the launch code)."""
         inf = self.plan.info
-        nchunks = -(-inf["n_nu"] // inf["nu_chunk"])
-        return 1 + 1 + 1 + 5 * nchunks + 1 + 1 + 2 + 1 + 2
+        nnu = int((self.cell.nu_idx >= 0).sum()) if inf["w_symmetric"] else inf["n_nu"]
+        nchunks = -(-nnu // inf["nu_chunk"])
+        w = 2 + 3 * nchunks + (1 if inf["w_symmetric"] else 0)
+        return 1 + 1 + 1 + w + 1 + 1 + 2 + 1 + 2
 
 
 def flush_l2(buf):
@@ -271,7 +276,7 @@ def run_ours(args, rank, world, local):
     ent = sw.plan.entries
     fl_P = contraction_flops(cell, ent) / (2 if sw.plan.info["c_symmetric"] else 1)  # mirrored nodes not computed
     fl_S = contraction_flops(cell, ent)
-    fl_W = wsolve_flops(cell)
+    fl_W = wsolve_flops(cell, sw.plan.info)
     work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
     dom = int(np.argmax(stage_mean))
     dom_name = Sweep.STAGES[dom]

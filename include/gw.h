@@ -44,14 +44,16 @@ typedef enum {
   GW_ERR_CUDA = 3,           /* a CUDA call failed (message in gw_last_error()) */
   GW_ERR_KMESH_ALIAS = 4,    /* strict mode: the k-mesh is below the rule of Sec. 2 */
   GW_ERR_NOT_HERMITIAN = 5,  /* reserved */
-  GW_ERR_SINGULAR = 6,       /* a zero pivot in the W solve */
+  GW_ERR_SINGULAR = 6,       /* a zero pivot in the W solve (reported by gw_sync) */
   GW_ERR_TIMEOUT = 7,        /* reserved (bounded device waits) */
   GW_ERR_NAN = 8,            /* reserved */
   GW_ERR_NO_DEVICE = 9,      /* compute call on a plan built with host_only */
   GW_ERR_UNSUPPORTED = 10    /* size outside the compiled limits (see gw_plan_create) */
 } gw_status;
 
-typedef enum { GW_FP64 = 0, GW_MIXED_BF16X3 = 1 } gw_precision;
+/* GW_MIXED: the P and Sigma contractions in reduced precision with FP32
+ * accumulation (everything else stays FP64); target 1e-6 relative error. */
+typedef enum { GW_FP64 = 0, GW_MIXED = 1 } gw_precision;
 typedef enum { GW_FERMION = 0, GW_BOSON = 1 } gw_statistics;
 typedef enum { GW_TAU_TO_IW = 0, GW_IW_TO_TAU = 1 } gw_direction;
 typedef enum { GW_BLOCK_ORB = 0, GW_BLOCK_PB = 1 } gw_block;
@@ -91,6 +93,7 @@ typedef struct {
   int host_only;          /* 1: build host tables only; compute calls fail with GW_ERR_NO_DEVICE */
   int device;             /* CUDA device ordinal used by the plan */
   size_t workspace_bytes; /* cap on the W-solve scratch (0: 2 GiB) */
+  int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
 } gw_options;
 
 typedef struct {
@@ -105,6 +108,8 @@ typedef struct {
   int nu_chunk;               /* bosonic frequencies per W-solve pass */
   double cond_fermion;        /* 2-norm condition numbers of the forward matrices */
   double cond_boson;
+  int w_symmetric;            /* the W solve runs on nu >= 0 and half of the q mesh (see gw_screened_W_iw) */
+  int n_q_solved;             /* momenta solved per frequency */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */
@@ -159,10 +164,16 @@ gw_status gw_transform_tau_iw(gw_plan_t plan, gw_statistics st, gw_direction dir
                               gw_block kind, const void* in, void* out, void* stream);
 
 /* W~(R, i nu) on the kept entries from P(R, i nu) (Eq. W_1 with W = v + W~):
- * P(q) = sum_{kept R} e^{iq.R} P(R); (I - v(q) P(q)) W(q) = v(q) by LU with
- * partial pivoting in FP64; W~(R) = (1/N_k) sum_q e^{-iq.R} (W(q) - v(q)).
+ * P(q) = sum_{kept R} e^{iq.R} P(R); W(q) = (I - v(q) P(q))^{-1} v(q), computed in
+ * FP64 as (v(q)^{-1} - P(q))^{-1} by Gauss-Jordan with partial pivoting;
+ * W~(R) = (1/N_k) sum_q e^{-iq.R} (W(q) - v(q)).
  * P_R_iw, Wt_R_iw: PB layout, N_nu slices.  v_q: dense [N_k][N_PB][N_PB].
- * Uses the plan's scratch; calls on one plan must not overlap. */
+ * When the plan reports w_symmetric (C symmetric in (L, L''), a symmetric bosonic
+ * set, option no_symmetry unset) the solve runs on nu >= 0 and on one momentum of
+ * each pair (q, -q) only, and the rest follows from the symmetries that P obtained
+ * from a Hermitian G(tau) has: P(R, i nu) real and P_ab(R, -i nu) = P_ba(-R, i nu)^T,
+ * with v(-q) = v(q)^*.  Inputs without these symmetries need no_symmetry.
+ * Uses the plan's scratch; calls on one plan must not overlap on the GPU. */
 gw_status gw_screened_W_iw(gw_plan_t plan, const void* P_R_iw, const void* v_q,
                            void* Wt_R_iw, void* stream);
 

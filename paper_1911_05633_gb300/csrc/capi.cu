@@ -29,13 +29,21 @@ struct gw_plan_s {
   double2* d_Tf_inv = nullptr;
   double2* d_Tb_fwd = nullptr;
   double2* d_Tb_inv = nullptr;
-  double2* d_wsA = nullptr;
-  double2* d_wsX = nullptr;
-  int* d_piv = nullptr;
+  // W solve: momenta and frequencies solved, and scratch
+  bool w_sym = false;
+  int n_qh = 0;                 // momenta solved per frequency
+  int* d_qh = nullptr;          // [n_qh] mesh index of each solved momentum
+  double* d_qw = nullptr;       // [n_qh] weight (2 for a (q, -q) pair, else 1); symmetric mode only
+  int nu_start = 0;             // first solved bosonic slot (the nu >= 0 ones in symmetric mode)
+  int n_neg = 0;                // negative-frequency slots filled by symmetry
+  int* d_numirror = nullptr;    // [n_neg] slot of -nu for each negative slot
+  double2* d_wsV = nullptr;     // [n_qh][N][N] v(q)^{-1}
+  double2* d_wsA = nullptr;     // [nu_chunk][n_qh][N][N]
+  int* d_perm = nullptr;        // [nu_chunk * n_qh][N]
   int* d_status = nullptr;
   int nu_chunk = 0;
   size_t ws_bytes = 0;
-  size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_LU = 0;
+  size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_GJ = 0;
   gw::MixedPlan mixed;
 };
 
@@ -87,8 +95,8 @@ gw_status upload(T** dst, const void* src, size_t bytes) {
 
 void free_device(gw_plan_s* p) {
   void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_phase,
-                  p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_inv, p->d_wsA, p->d_wsX,
-                  p->d_piv, p->d_status};
+                  p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_inv, p->d_qh, p->d_qw,
+                  p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
@@ -115,12 +123,18 @@ int dense_n(const gw_plan_s* p, gw_block kind) {
 
 gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_k, long long k_stride,
                         long long s_stride, const double2* F_sub, long long sub_k_stride, long long sub_s_stride,
-                        double2* F_R, int out_n_slices, int out_slice0, double scale, cudaStream_t st) {
+                        double2* F_R, int out_n_slices, int out_slice0, double scale, cudaStream_t st,
+                        const int* k_list = nullptr, const double* k_weight = nullptr, int n_k_in = -1,
+                        int real_only = 0) {
   gw::GatherArgs g{};
   g.ent = p->d_ent;
   g.pair_first = p->d_pair_first;
   g.phase = p->d_phase;
   g.n_k = p->h.n_k;
+  g.k_list = k_list;
+  g.k_weight = k_weight;
+  g.n_k_in = n_k_in < 0 ? p->h.n_k : n_k_in;
+  g.real_only = real_only;
   g.F_k = F_k;
   g.k_stride = k_stride;
   g.s_stride = s_stride;
@@ -144,7 +158,9 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
 }
 
 gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_R, int in_n_slices,
-                         int in_slice0, double2* F_k, long long k_stride, long long s_stride, cudaStream_t st) {
+                         int in_slice0, double2* F_k, long long k_stride, long long s_stride, cudaStream_t st,
+                         const int* k_list = nullptr, int n_k_out = -1, const double2* base = nullptr,
+                         double coef = 1.0) {
   gw::ScatterArgs g{};
   g.ent = p->d_ent;
   g.pair_start = p->d_pair_start;
@@ -152,6 +168,10 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   g.n_atoms = p->h.n_atoms;
   g.phase = p->d_phase;
   g.n_k = p->h.n_k;
+  g.k_list = k_list;
+  g.n_k_out = n_k_out < 0 ? p->h.n_k : n_k_out;
+  g.base = base;
+  g.coef = coef;
   g.F_R = F_R;
   g.in_n_slices = in_n_slices;
   g.in_slice0 = in_slice0;
@@ -220,6 +240,8 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   gw_plan_s* p = new (std::nothrow) gw_plan_s();
   if (!p) return GW_ERR_OOM;
   std::string err;
+  std::vector<int> qh, numirror;
+  std::vector<double> qw;
   gw_status st = gw::build_host_plan(cell, basis, kmesh, grid, cutoff, opt, p->h, err);
   if (st != GW_OK) {
     set_last_error(err);
@@ -227,6 +249,37 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     return st;
   }
   p->host_only = opt ? (opt->host_only != 0) : false;
+  const gw::HostPlan& hh = p->h;
+  // W solve: which momenta and frequencies are solved, and the scratch
+  {
+    bool nu_sym = true;
+    for (int j = 0; j < hh.n_nu; ++j) {
+      bool found = false;
+      for (int l = 0; l < hh.n_nu; ++l) found |= (hh.nu_idx[l] == -hh.nu_idx[j]);
+      nu_sym &= found;
+    }
+    for (int j = 1; j < hh.n_nu; ++j) nu_sym &= (hh.nu_idx[j] > hh.nu_idx[j - 1]);
+    p->w_sym = p->h.c_symmetric && nu_sym && !(opt && opt->no_symmetry);
+  }
+    for (int q = 0, q1 = 0; q1 < hh.kmesh[0]; ++q1)
+    for (int q2 = 0; q2 < hh.kmesh[1]; ++q2)
+      for (int q3 = 0; q3 < hh.kmesh[2]; ++q3, ++q) {
+        const int m1 = (hh.kmesh[0] - q1) % hh.kmesh[0], m2 = (hh.kmesh[1] - q2) % hh.kmesh[1],
+                  m3 = (hh.kmesh[2] - q3) % hh.kmesh[2];
+        const int mq = (m1 * hh.kmesh[1] + m2) * hh.kmesh[2] + m3;
+        if (!p->w_sym) { qh.push_back(q); qw.push_back(1.0); }
+        else if (q <= mq) { qh.push_back(q); qw.push_back(q == mq ? 1.0 : 2.0); }
+      }
+  p->n_qh = (int)qh.size();
+  if (p->w_sym) {
+    int n_neg = 0;
+    while (n_neg < hh.n_nu && hh.nu_idx[n_neg] < 0) ++n_neg;
+    p->n_neg = n_neg;
+    p->nu_start = n_neg;
+    for (int j = 0; j < n_neg; ++j)
+      for (int l = 0; l < hh.n_nu; ++l)
+        if (hh.nu_idx[l] == -hh.nu_idx[j]) numirror.push_back(l);
+  }
   p->device = opt ? opt->device : 0;
   if (p->host_only) {
     *out = p;
@@ -259,27 +312,36 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_status, nullptr, 16)) != GW_OK) return fail(st);
   if (cudaMemset(p->d_status, 0, 16) != cudaSuccess) return fail(GW_ERR_CUDA);
 
-  // W-solve scratch: two dense [chunk][N_k][N_PB][N_PB] buffers and pivots
+  // W-solve scratch
   const size_t npb = (size_t)h.n_pb_total();
-  const size_t per_nu = 2 * (size_t)h.n_k * npb * npb * sizeof(double2) + (size_t)h.n_k * npb * sizeof(int);
+  if ((st = upload(&p->d_qh, qh.data(), qh.size() * sizeof(int))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_qw, qw.data(), qw.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
+  const size_t mat = npb * npb * sizeof(double2);
+  const size_t per_nu = (size_t)p->n_qh * (mat + npb * sizeof(int));
   const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes : ((size_t)2 << 30);
-  int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)h.n_nu, cap / per_nu));
+  const int n_work_nu = h.n_nu - p->nu_start;
+  const size_t base_bytes = (size_t)p->n_qh * mat;
+  int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_work_nu, cap > base_bytes ? (cap - base_bytes) / per_nu : 1));
   p->nu_chunk = nch;
-  const size_t mat = (size_t)nch * h.n_k * npb * npb * sizeof(double2);
-  if ((st = upload(&p->d_wsA, nullptr, mat)) != GW_OK) return fail(st);
-  if ((st = upload(&p->d_wsX, nullptr, mat)) != GW_OK) return fail(st);
-  if ((st = upload(&p->d_piv, nullptr, (size_t)nch * h.n_k * npb * sizeof(int))) != GW_OK) return fail(st);
-  p->ws_bytes = 2 * mat + (size_t)nch * h.n_k * npb * sizeof(int);
+  if ((st = upload(&p->d_wsV, nullptr, (size_t)p->n_qh * mat)) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_wsA, nullptr, (size_t)nch * p->n_qh * mat)) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_perm, nullptr, (size_t)nch * p->n_qh * npb * sizeof(int))) != GW_OK) return fail(st);
+  p->ws_bytes = (size_t)p->n_qh * mat + (size_t)nch * per_nu;
 
   // dynamic shared memory opt-ins
   p->smem_P = smem_polar(h);
   p->smem_S = smem_sigma(h);
   p->smem_T = (size_t)std::max(std::max(h.n_tau, h.n_omega), h.n_nu) * 32 * sizeof(double2);
-  p->smem_LU = 2 * npb * sizeof(double2);
+  p->smem_GJ = 2 * npb * sizeof(double2);
+  if (p->smem_GJ > 227 * 1024) {
+    set_last_error("product basis too large for the single-block Gauss-Jordan solve");
+    return fail(GW_ERR_UNSUPPORTED);
+  }
   if (cudaFuncSetAttribute(gw::k_polarizability_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_P) != cudaSuccess ||
       cudaFuncSetAttribute(gw::k_self_energy_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_S) != cudaSuccess ||
       cudaFuncSetAttribute(gw::k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_T) != cudaSuccess ||
-      cudaFuncSetAttribute(gw::k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_LU) != cudaSuccess) {
+      cudaFuncSetAttribute(gw::k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_GJ) != cudaSuccess) {
     cudaError_t e = cudaGetLastError();
     set_last_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     return fail(GW_ERR_UNSUPPORTED);
@@ -322,6 +384,8 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->nu_chunk = p->nu_chunk;
   info->cond_fermion = h.cond_f;
   info->cond_boson = h.cond_b;
+  info->w_symmetric = p->w_sym ? 1 : 0;
+  info->n_q_solved = p->n_qh;
   return GW_OK;
 }
 
@@ -410,8 +474,9 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   if (!G_R || !P_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
   const gw::HostPlan& h = p->h;
-  if (prec == GW_MIXED_BF16X3)
-    return gw::mixed_polarizability(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (double2*)P_R, S(stream));
+  if (prec == GW_MIXED)
+    return gw::mixed_polarizability(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (double2*)P_R, p->d_status,
+                                    S(stream));
   if (prec != GW_FP64) { set_last_error("unknown precision"); return GW_ERR_ARG; }
   gw::ContractArgs g{};
   g.ent = p->d_ent;
@@ -434,7 +499,7 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
   if (!G_R || !Wt_R || !Sig_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
   const gw::HostPlan& h = p->h;
-  if (prec == GW_MIXED_BF16X3) {
+  if (prec == GW_MIXED) {
     st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
                                (double2*)Sig_R, S(stream));
     if (st != GW_OK) return st;
@@ -488,26 +553,37 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
   cudaStream_t s = S(stream);
   const long long N = h.n_pb_total();
   const long long NN = N * N;
-  const int nk = h.n_k;
+  const int nq = p->n_qh;
   const double2* v = (const double2*)v_q;
-  for (int n0 = 0; n0 < h.n_nu; n0 += p->nu_chunk) {
-    const int nc = std::min(p->nu_chunk, h.n_nu - n0);
-    // P(q, nu) for nu in the chunk -> wsX as [nu][q][N][N]
-    if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, n0, p->d_wsX, NN, nk * NN, s)) != GW_OK)
+  // v(q)^{-1} for the solved momenta
+  {
+    dim3 g((unsigned)std::min<long long>((NN + 255) / 256, 1024), (unsigned)nq);
+    gw::k_copy_mats<<<g, 256, 0, s>>>(v, p->d_qh, p->d_wsV, NN);
+    if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
+    gw::k_gj_inverse<<<nq, 512, p->smem_GJ, s>>>(p->d_wsV, p->d_perm, (int)N, NN, p->d_status);
+    if ((st = check_launch("k_gj_inverse (v)")) != GW_OK) return st;
+  }
+  const int n_work = h.n_nu - p->nu_start;
+  for (int c0 = 0; c0 < n_work; c0 += p->nu_chunk) {
+    const int nc = std::min(p->nu_chunk, n_work - c0);
+    const int slot0 = p->nu_start + c0;
+    // A = v(q)^{-1} - P(q, nu) for the chunk, [nu][q][N][N]
+    if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, slot0, p->d_wsA, NN,
+                             (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0)) != GW_OK)
       return st;
-    const int batch = nc * nk;
-    dim3 g1((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32), (unsigned)batch);
-    gw::k_form_A<<<g1, 256, 0, s>>>(v, p->d_wsX, p->d_wsA, (int)N, nk);
-    if ((st = check_launch("k_form_A")) != GW_OK) return st;
-    gw::k_lu<<<batch, 512, p->smem_LU, s>>>(p->d_wsA, p->d_piv, (int)N, p->d_status);
-    if ((st = check_launch("k_lu")) != GW_OK) return st;
-    dim3 g2((unsigned)((N + 31) / 32), (unsigned)batch);
-    gw::k_lu_solve<<<g2, 256, 0, s>>>(p->d_wsA, p->d_piv, v, p->d_wsX, (int)N, nk);
-    if ((st = check_launch("k_lu_solve")) != GW_OK) return st;
-    // W~(R) = (1/N_k) sum_q e^{-iqR} (X - v)
-    if ((st = launch_gather(p, GW_BLOCK_PB, nc, p->d_wsX, NN, nk * NN, v, NN, 0, (double2*)Wt_R_iw, h.n_nu, n0,
-                            1.0 / nk, s)) != GW_OK)
+    gw::k_gj_inverse<<<nc * nq, 512, p->smem_GJ, s>>>(p->d_wsA, p->d_perm, (int)N, NN, p->d_status);
+    if ((st = check_launch("k_gj_inverse")) != GW_OK) return st;
+    // W~(R) = (1/N_k) sum_q e^{-iqR} (W(q) - v(q)); in symmetric mode the sum runs over
+    // one momentum of each (q, -q) pair with weight 2 and keeps the (exactly real) real part
+    if ((st = launch_gather(p, GW_BLOCK_PB, nc, p->d_wsA, NN, (long long)nq * NN, v, NN, 0, (double2*)Wt_R_iw,
+                            h.n_nu, slot0, 1.0 / h.n_k, s, p->d_qh, p->w_sym ? p->d_qw : nullptr, nq,
+                            p->w_sym ? 1 : 0)) != GW_OK)
       return st;
+  }
+  if (p->w_sym && p->n_neg > 0) {
+    dim3 g((unsigned)h.n_entries(), (unsigned)p->n_neg);
+    gw::k_mirror_nu<<<g, 256, 0, s>>>(p->d_ent, p->d_numirror, p->n_neg, h.n_nu, (double2*)Wt_R_iw);
+    if ((st = check_launch("k_mirror_nu")) != GW_OK) return st;
   }
   return GW_OK;
 }
@@ -521,6 +597,10 @@ gw_status gw_sync(gw_plan_t p, void* stream) {
   GW_CUDA(cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     cudaMemset(p->d_status, 0, sizeof(int));
+    if (flag == 2) {
+      set_last_error("a tensor-core wait gave up (bounded wait)");
+      return GW_ERR_TIMEOUT;
+    }
     set_last_error("zero pivot in the W solve");
     return GW_ERR_SINGULAR;
   }

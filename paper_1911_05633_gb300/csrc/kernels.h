@@ -11,7 +11,11 @@ struct GatherArgs {
   const DevEntry* ent;
   const int* pair_first;   // [n_active + 1] entry range of each active atom pair
   const double2* phase;    // [E][N_k] e^{+i k.R}
-  int n_k;
+  int n_k;                 // mesh size (phase row length)
+  const int* k_list;       // optional: input k index kk -> mesh k (n_k_in entries)
+  const double* k_weight;  // optional: weight per input k index
+  int n_k_in;              // number of input k indices summed over
+  int real_only;           // keep the real part of the result
   const double2* F_k;      // dense input
   long long k_stride, s_stride;
   int ld;
@@ -29,7 +33,11 @@ struct ScatterArgs {
   const int* row_off;      // [n_atoms + 1] orbital or product offsets
   int n_atoms;
   const double2* phase;
-  int n_k;
+  int n_k;                 // mesh size (phase row length)
+  const int* k_list;       // optional: output k index kk -> mesh k (n_k_out entries)
+  int n_k_out;
+  const double2* base;     // optional dense [n_k_out][N][N] added to the result
+  double coef;             // result = base + coef * sum
   const double2* F_R;      // entry layout input
   int in_n_slices, in_slice0;
   int pb;
@@ -67,11 +75,15 @@ __global__ void k_scatter_R_to_k(ScatterArgs g);
 __global__ void k_transform(TransformArgs g);
 __global__ void k_polarizability_fp64(ContractArgs g);
 __global__ void k_self_energy_fp64(ContractArgs g);
-__global__ void k_form_A(const double2* __restrict__ v, const double2* __restrict__ P,
-                         double2* __restrict__ A, int N, int n_k);
-__global__ void k_lu(double2* __restrict__ A, int* __restrict__ piv, int N, int* status);
-__global__ void k_lu_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
-                           const double2* __restrict__ v, double2* __restrict__ X, int N, int n_k);
+// In-place Gauss-Jordan inverse of a batch of N x N complex matrices (partial pivoting).
+__global__ void k_gj_inverse(double2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
+                             int* status);
+// dst[b] = src[map[b]] for dense N x N matrices (used to stage v(q) before inversion).
+__global__ void k_copy_mats(const double2* __restrict__ src, const int* __restrict__ map, double2* __restrict__ dst,
+                            long long NN);
+// W~(R, -nu_j) = W~(mirror(R), nu_{mirror j})^T for the negative frequencies (real blocks).
+__global__ void k_mirror_nu(const DevEntry* __restrict__ ent, const int* __restrict__ nu_mirror, int n_neg, int n_nu,
+                            double2* __restrict__ W);
 
 constexpr int kKCHost = 16;  // must match kKC in kernels_fp64.cu
 

@@ -57,12 +57,18 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
     double2 acc[kGatherEnt];
 #pragma unroll
     for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
-    for (int k = 0; k < g.n_k; ++k) {
-      double2 v = g.F_k[(long long)k * g.k_stride + (long long)s * g.s_stride + in_el];
+    for (int kk = 0; kk < g.n_k_in; ++kk) {
+      const int k = g.k_list ? g.k_list[kk] : kk;
+      double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
       if (g.F_sub) {
         double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
         v.x -= w.x;
         v.y -= w.y;
+      }
+      if (g.k_weight) {
+        const double wk = g.k_weight[kk];
+        v.x *= wk;
+        v.y *= wk;
       }
 #pragma unroll
       for (int m = 0; m < kGatherEnt; ++m)
@@ -73,7 +79,7 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
       if (m < ne) {
         const DevEntry& E = g.ent[eb + m];
         const long long off = g.pb ? E.off_pb : E.off_orb;
-        double2 r = make_double2(acc[m].x * g.scale, acc[m].y * g.scale);
+        double2 r = make_double2(acc[m].x * g.scale, g.real_only ? 0.0 : acc[m].y * g.scale);
         g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * blk + idx] = r;
       }
     }
@@ -108,13 +114,17 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
         v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * blk + idx];
       }
     }
-    for (int k = 0; k < g.n_k; ++k) {
+    for (int kk = 0; kk < g.n_k_out; ++kk) {
+      const int k = g.k_list ? g.k_list[kk] : kk;
       double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
       for (int m = 0; m < kGatherEnt; ++m)
         if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
-      double2* o = g.F_k + (long long)k * g.k_stride + (long long)s * g.s_stride + out_el;
+      acc.x *= g.coef;
+      acc.y *= g.coef;
+      double2* o = g.F_k + (long long)kk * g.k_stride + (long long)s * g.s_stride + out_el;
       if (eb == e0) {
+        if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
         *o = acc;
       } else {
         double2 t = *o;
@@ -286,73 +296,25 @@ __global__ void k_self_energy_fp64(ContractArgs g) {
 }
 
 // ---------------------------------------------------------------------------
-// W solve (Eq. W_1): A_b = I - v(q_b) P_b, LU with partial pivoting, X_b = A_b^{-1} v(q_b)
+// W solve (Eq. W_1): W = (v^{-1} - P)^{-1} per (q, nu), by in-place Gauss-Jordan
 // ---------------------------------------------------------------------------
-constexpr int kGT = 32;  // tile
-constexpr int kGK = 16;  // k step
 
-// A[b] = I - v[q(b)] * P[b], q(b) = b % n_k; 256 threads, 32x32 tile, 2x2 per thread.
-__global__ void k_form_A(const double2* __restrict__ v, const double2* __restrict__ P,
-                         double2* __restrict__ A, int N, int n_k) {
-  __shared__ double2 As[kGT][kGK + 1];
-  __shared__ double2 Bs[kGK][kGT + 1];
-  const int b = blockIdx.z;
-  const int q = b % n_k;
-  const double2* V = v + (long long)q * N * N;
-  const double2* Pb = P + (long long)b * N * N;
-  double2* Ab = A + (long long)b * N * N;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
-  double2 acc[2][2];
-  for (int u = 0; u < 2; ++u)
-    for (int w = 0; w < 2; ++w) acc[u][w] = make_double2(0.0, 0.0);
-  for (int l0 = 0; l0 < N; l0 += kGK) {
-    for (int x = threadIdx.x; x < kGT * kGK; x += blockDim.x) {
-      int r = x / kGK, c = x - r * kGK;
-      int gi = i0 + r, gl = l0 + c;
-      As[r][c] = (gi < N && gl < N) ? V[(long long)gi * N + gl] : make_double2(0.0, 0.0);
-      int r2 = x / kGT, c2 = x - r2 * kGT;
-      int gl2 = l0 + r2, gj = j0 + c2;
-      Bs[r2][c2] = (gl2 < N && gj < N) ? Pb[(long long)gl2 * N + gj] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int l = 0; l < kGK; ++l) {
-      double2 a0 = As[ty][l], a1 = As[ty + 16][l];
-      double2 b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
-      acc[0][0] = cfma(a0, b0, acc[0][0]);
-      acc[0][1] = cfma(a0, b1, acc[0][1]);
-      acc[1][0] = cfma(a1, b0, acc[1][0]);
-      acc[1][1] = cfma(a1, b1, acc[1][1]);
-    }
-    __syncthreads();
-  }
-  for (int u = 0; u < 2; ++u)
-    for (int w = 0; w < 2; ++w) {
-      int gi = i0 + ty + 16 * u, gj = j0 + tx + 16 * w;
-      if (gi < N && gj < N) {
-        double2 r = make_double2(-acc[u][w].x, -acc[u][w].y);
-        if (gi == gj) r.x += 1.0;
-        Ab[(long long)gi * N + gj] = r;
-      }
-    }
-}
-
-// In-place LU with partial pivoting (|re| + |im| pivot measure), one block per matrix.
-// piv[k] is the row exchanged with row k at step k.  A zero pivot sets *status.
-__global__ void k_lu(double2* __restrict__ A, int* __restrict__ piv, int N, int* status) {
+// In-place Gauss-Jordan inverse with partial pivoting (|re| + |im| measure), one
+// block per matrix.  Row exchanges are recorded in perm and undone on the columns
+// at the end.  A zero pivot sets *status and leaves the matrix undefined.
+__global__ void k_gj_inverse(double2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
+                             int* status) {
   extern __shared__ unsigned char smraw[];
-  double2* rowk = reinterpret_cast<double2*>(smraw);  // [N]
-  double2* colk = rowk + N;                            // [N]
+  double2* rowk = reinterpret_cast<double2*>(smraw);  // [N] scaled pivot row
+  double2* colk = rowk + N;                            // [N] multipliers
   __shared__ double rv[32];
   __shared__ int ri[32];
   const int b = blockIdx.x;
-  double2* M = A + (long long)b * N * N;
-  int* pv = piv + (long long)b * N;
+  double2* M = A + (long long)b * mat_stride;
+  int* pm = perm + (long long)b * N;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   for (int k = 0; k < N; ++k) {
-    // pivot search
     double best = -1.0;
     int bi = k;
     for (int i = k + tid; i < N; i += nt) {
@@ -377,103 +339,85 @@ __global__ void k_lu(double2* __restrict__ A, int* __restrict__ piv, int N, int*
       }
       if (lane == 0) {
         ri[0] = bi;
-        pv[k] = bi;
+        pm[k] = bi;
         if (!(best > 0.0)) atomicExch(status, 1);
       }
     }
     __syncthreads();
     const int p = ri[0];
-    // swap rows k and p, keep row k in smem
+    // exchange rows k and p; the pivot row goes to shared memory
     for (int j = tid; j < N; j += nt) {
       double2 zk = M[(long long)k * N + j];
       double2 zp = M[(long long)p * N + j];
-      if (p != k) {
-        M[(long long)k * N + j] = zp;
-        M[(long long)p * N + j] = zk;
-      }
+      if (p != k) M[(long long)p * N + j] = zk;
       rowk[j] = (p != k) ? zp : zk;
+    }
+    for (int i = tid; i < N; i += nt) {
+      const int src = (i == p) ? k : i;  // row p now holds the old row k
+      colk[i] = (i == k) ? make_double2(0.0, 0.0) : M[(long long)src * N + k];
     }
     __syncthreads();
     const double2 d = rowk[k];
     const double den = d.x * d.x + d.y * d.y;
     const double2 inv = (den > 0.0) ? make_double2(d.x / den, -d.y / den) : make_double2(0.0, 0.0);
-    for (int i = k + 1 + tid; i < N; i += nt) {
-      double2 l = cmul(M[(long long)i * N + k], inv);
-      M[(long long)i * N + k] = l;
-      colk[i] = l;
+    __syncthreads();
+    // scaled pivot row: r_j = a_kj / d (j != k), r_k = 1 / d
+    for (int j = tid; j < N; j += nt) {
+      double2 r = (j == k) ? inv : cmul(rowk[j], inv);
+      rowk[j] = r;
+      M[(long long)k * N + j] = r;
     }
     __syncthreads();
-    const int m = N - k - 1;
-    for (long long x = tid; x < (long long)m * m; x += nt) {
-      const int i = k + 1 + (int)(x / m);
-      const int j = k + 1 + (int)(x - (x / m) * m);
-      double2 l = colk[i];
-      double2 u = rowk[j];
-      double2 z = M[(long long)i * N + j];
-      z = cfma(make_double2(-l.x, -l.y), u, z);
-      M[(long long)i * N + j] = z;
+    // every other row: a_ij <- (j == k ? 0 : a_ij) - f_i r_j
+    for (long long x = tid; x < (long long)N * N; x += nt) {
+      const int i = (int)(x / N);
+      const int j = (int)(x - (long long)i * N);
+      if (i == k) continue;
+      double2 f = colk[i];
+      double2 z = (j == k) ? make_double2(0.0, 0.0) : M[x];
+      M[x] = cfma(make_double2(-f.x, -f.y), rowk[j], z);
+    }
+    __syncthreads();
+  }
+  // undo the row exchanges on the columns of the inverse, last exchange first
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = pm[k];
+    if (p != k) {
+      for (int i = tid; i < N; i += nt) {
+        double2 t = M[(long long)i * N + k];
+        M[(long long)i * N + k] = M[(long long)i * N + p];
+        M[(long long)i * N + p] = t;
+      }
     }
     __syncthreads();
   }
 }
 
-// X[b][:, c0:c0+32] = A_b^{-1} v[q(b)][:, c0:c0+32] from the LU factors; 256 threads.
-__global__ void k_lu_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
-                           const double2* __restrict__ v, double2* __restrict__ X, int N, int n_k) {
+__global__ void k_copy_mats(const double2* __restrict__ src, const int* __restrict__ map, double2* __restrict__ dst,
+                            long long NN) {
   const int b = blockIdx.y;
-  const int q = b % n_k;
-  const int c0 = blockIdx.x * 32;
-  const double2* M = LU + (long long)b * N * N;
-  const int* pv = piv + (long long)b * N;
-  const double2* V = v + (long long)q * N * N;
-  double2* Xb = X + (long long)b * N * N;
-  const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;  // 8 row lanes
-  const int c = c0 + cx;
-  const bool active = c < N;
-  for (int i = ry; i < N; i += 8)
-    if (active) Xb[(long long)i * N + c] = V[(long long)i * N + c];
-  __syncthreads();
-  if (ry == 0 && active) {
-    for (int k = 0; k < N; ++k) {
-      int p = pv[k];
-      if (p != k) {
-        double2 t = Xb[(long long)k * N + c];
-        Xb[(long long)k * N + c] = Xb[(long long)p * N + c];
-        Xb[(long long)p * N + c] = t;
-      }
-    }
-  }
-  __syncthreads();
-  // forward: unit lower triangle
-  for (int k = 0; k < N - 1; ++k) {
-    double2 xk = active ? Xb[(long long)k * N + c] : make_double2(0.0, 0.0);
-    for (int i = k + 1 + ry; i < N; i += 8) {
-      if (active) {
-        double2 l = M[(long long)i * N + k];
-        double2 z = Xb[(long long)i * N + c];
-        Xb[(long long)i * N + c] = cfma(make_double2(-l.x, -l.y), xk, z);
-      }
-    }
-    __syncthreads();
-  }
-  // backward: upper triangle
-  for (int k = N - 1; k >= 0; --k) {
-    if (ry == 0 && active) {
-      double2 d = M[(long long)k * N + k];
-      double den = d.x * d.x + d.y * d.y;
-      double2 inv = (den > 0.0) ? make_double2(d.x / den, -d.y / den) : make_double2(0.0, 0.0);
-      Xb[(long long)k * N + c] = cmul(Xb[(long long)k * N + c], inv);
-    }
-    __syncthreads();
-    double2 xk = active ? Xb[(long long)k * N + c] : make_double2(0.0, 0.0);
-    for (int i = ry; i < k; i += 8) {
-      if (active) {
-        double2 u = M[(long long)i * N + k];
-        double2 z = Xb[(long long)i * N + c];
-        Xb[(long long)i * N + c] = cfma(make_double2(-u.x, -u.y), xk, z);
-      }
-    }
-    __syncthreads();
+  const double2* s = src + (long long)map[b] * NN;
+  double2* d = dst + (long long)b * NN;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < NN; x += (long long)gridDim.x * blockDim.x)
+    d[x] = s[x];
+}
+
+// One block per (entry, negative-frequency slot j): copy the transposed block of the
+// mirror entry at the mirrored (non-negative) frequency.  Blocks are K_a x K_b.
+__global__ void k_mirror_nu(const DevEntry* __restrict__ ent, const int* __restrict__ nu_mirror, int n_neg, int n_nu,
+                            double2* __restrict__ W) {
+  const int e = blockIdx.x;
+  const int j = blockIdx.y;
+  if (j >= n_neg) return;
+  const DevEntry E = ent[e];
+  const DevEntry F = ent[E.mirror];
+  const int Ka = E.Ka, Kb = E.Kb;  // mirror block is Kb x Ka
+  const int jm = nu_mirror[j];
+  const double2* src = W + F.off_pb * n_nu + (long long)jm * Kb * Ka;
+  double2* dst = W + E.off_pb * n_nu + (long long)j * Ka * Kb;
+  for (int x = threadIdx.x; x < Ka * Kb; x += blockDim.x) {
+    const int r = x / Kb, c = x - (x / Kb) * Kb;
+    dst[x] = src[c * Ka + r];
   }
 }
 

@@ -1,0 +1,320 @@
+// Tensor-core (tcgen05) form of the P contraction of Eq. P_MM for the mixed path.
+//
+// Per (entry, tau node) the first two stages run in FP32 on the CUDA cores:
+//   X[K][L''][L'] = sum_L C^a[K][L][L''] G(tau)[L][L']
+//   Y[K][j]       = sum_L'' X[K][L''][L'] conj(G(beta - tau)[L''][L''']),  j = (L', L''')
+// and the dense third stage, P[K][K'] = -s sum_j Y[K][j] C^b[K'][j], runs on the
+// tensor cores: the rows (Re Y; Im Y) form the 128-row A operand, C^b the B
+// operand, both split into three BF16 terms (x = hi + mid + lo, 24 significant
+// bits) and multiplied as the six products with i + j <= 2, accumulated in FP32
+// in tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "kernels.h"
+#include "mixed.h"
+#include "umma.h"
+
+namespace gw {
+
+namespace {
+
+using namespace umma;
+
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ void split3(float y, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(y);
+  const float r1 = y - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(m);
+  l = __float2bfloat16_rn(r2);
+}
+
+struct TcLayout {
+  int KD;      // padded reduction length (n_b^2 rounded up to 16)
+  int NP;      // padded N (K_b rounded up to 16)
+  uint32_t offA, offB, offX, offG, offP, offBar, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int na, int nb, int Ka, int Kb) {
+  TcLayout L;
+  L.KD = ((nb * nb + 15) / 16) * 16;
+  L.NP = ((Kb + 15) / 16) * 16;
+  uint32_t o = 0;
+  L.offA = o; o += 3u * 128u * L.KD * 2u;
+  L.offB = o; o += 3u * (uint32_t)L.NP * L.KD * 2u;
+  L.offX = o; o += (uint32_t)Ka * na * nb * 8u;
+  L.offG = o; o += 2u * na * nb * 8u;
+  L.offP = o; o += (uint32_t)Ka * Kb * 8u;
+  o = (o + 15u) & ~15u;
+  L.offBar = o; o += 16u;
+  L.total = o;
+  return L;
+}
+
+// grid (entry, tau chunk); 256 threads.  taus: the computed nodes it = 0 .. n_eff-1.
+__global__ void __launch_bounds__(256, 1)
+k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, const uint16_t* __restrict__ Bsplit,
+                    const int* __restrict__ Bsplit_off, const int* __restrict__ species_of_atom,
+                    const double2* __restrict__ G, double2* __restrict__ out, int n_tau, int n_eff, int tau_per_cta,
+                    int spin, int mirror_tau, int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  const int e = blockIdx.x;
+  const DevEntry E = ent[e];
+  const int na = E.na, nb = E.nb, Ka = E.Ka, Kb = E.Kb;
+  const TcLayout L = tc_layout(na, nb, Ka, Kb);
+  unsigned char* Ap = sm + L.offA;
+  unsigned char* Bp = sm + L.offB;
+  float2* X = reinterpret_cast<float2*>(sm + L.offX);
+  float2* G1 = reinterpret_cast<float2*>(sm + L.offG);
+  float2* G2 = G1 + na * nb;
+  float2* Ps = reinterpret_cast<float2*>(sm + L.offP);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.offBar);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // tensor-memory accumulator: 128 lanes x NP columns (allocation: power of two >= 32)
+  uint32_t ncols = 32;
+  while ((int)ncols < L.NP) ncols <<= 1;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  // B operand (C^b split in three planes, canonical layout) and a zeroed A operand
+  const int sb = species_of_atom[E.b];
+  const uint4* bsrc = reinterpret_cast<const uint4*>(Bsplit + Bsplit_off[sb]);
+  uint4* bdst = reinterpret_cast<uint4*>(Bp);
+  const int nb16 = (int)(3u * L.NP * L.KD * 2u / 16u);
+  for (int x = tid; x < nb16; x += blockDim.x) bdst[x] = bsrc[x];
+  uint4* az = reinterpret_cast<uint4*>(Ap);
+  const int na16 = (int)(3u * 128u * L.KD * 2u / 16u);
+  for (int x = tid; x < na16; x += blockDim.x) az[x] = make_uint4(0, 0, 0, 0);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tm = tmem_base;
+  const uint32_t idesc = idesc_bf16_f32(128, L.NP);
+  const uint32_t aBase = smem_u32(Ap), bBase = smem_u32(Bp);
+  const uint32_t aPlane = 128u * L.KD * 2u, bPlane = (uint32_t)L.NP * L.KD * 2u;
+  const float* Ca = C + E.ca;
+  const double2* Gin = G + E.off_orb * n_tau;
+  double2* Pout = out + E.off_pb * n_tau;
+  const double ms = -(double)spin;
+  const int t0 = blockIdx.y * tau_per_cta;
+  const int t1 = min(n_eff, t0 + tau_per_cta);
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int it = t0; it < t1 && ok; ++it) {
+    const int im = n_tau - 1 - it;
+    for (int x = tid; x < na * nb; x += blockDim.x) {
+      const double2 g1 = Gin[(long long)it * na * nb + x];
+      const double2 g2 = Gin[(long long)im * na * nb + x];
+      G1[x] = make_float2((float)g1.x, (float)g1.y);
+      G2[x] = make_float2((float)g2.x, (float)g2.y);
+    }
+    __syncthreads();
+    // stage 1: X[K][L''][L']
+    for (int x = tid; x < Ka * na * nb; x += blockDim.x) {
+      const int K = x / (na * nb);
+      const int r = x - K * na * nb;
+      const int L2 = r / nb, L1 = r - L2 * nb;
+      const float* c = Ca + (long long)K * na * na;
+      float ax = 0.f, ay = 0.f;
+      for (int l = 0; l < na; ++l) {
+        const float cv = c[l * na + L2];
+        const float2 g = G1[l * nb + L1];
+        ax = fmaf(cv, g.x, ax);
+        ay = fmaf(cv, g.y, ay);
+      }
+      X[x] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    // stage 2 + split: rows K (Re) and Ka + K (Im), column j = L' nb + L'''
+    for (int x = tid; x < Ka * nb * nb; x += blockDim.x) {
+      const int K = x / (nb * nb);
+      const int j = x - K * nb * nb;
+      const int L1 = j / nb, L3 = j - L1 * nb;
+      const float2* xk = X + K * na * nb;
+      float yr = 0.f, yi = 0.f;
+      for (int L2 = 0; L2 < na; ++L2) {
+        const float2 a = xk[L2 * nb + L1];
+        const float2 b = G2[L2 * nb + L3];
+        // a * conj(b)
+        yr = fmaf(a.x, b.x, fmaf(a.y, b.y, yr));
+        yi = fmaf(a.y, b.x, fmaf(-a.x, b.y, yi));
+      }
+      __nv_bfloat16 h, m, l;
+      split3(yr, h, m, l);
+      uint32_t o = kmajor_offset(128, K, j);
+      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+      split3(yi, h, m, l);
+      o = kmajor_offset(128, Ka + K, j);
+      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+    }
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const int nks = L.KD / 16;
+      uint32_t acc = 0;
+      for (int s = 0; s < nks; ++s) {
+        const uint32_t ao = (uint32_t)s * 128u * 32u, bo = (uint32_t)s * (uint32_t)L.NP * 32u;
+        // the six split products with i + j <= 2 (0 = hi, 1 = mid, 2 = lo)
+        const int pa[6] = {0, 0, 1, 0, 1, 2};
+        const int pb[6] = {0, 1, 0, 2, 1, 0};
+        for (int q = 0; q < 6; ++q) {
+          const uint64_t da = smem_desc(aBase + pa[q] * aPlane + ao, 128, 256);
+          const uint64_t db = smem_desc(bBase + pb[q] * bPlane + bo, 128, 256);
+          mma_bf16(tm, da, db, idesc, acc);
+          acc = 1;
+        }
+      }
+      mma_commit(bar);
+    }
+    // every thread waits; the block acts on one common verdict
+    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitLimit) ? 1 : 0) != 0;
+    phase ^= 1u;
+    fence_after_sync();
+    if (!ok) {
+      if (tid == 0) atomicExch(status, 2);
+      // give the tensor core a second bounded chance to finish before the
+      // accumulator is released
+      mbar_wait(bar, phase ^ 1u, kWaitLimit);
+      break;
+    }
+    // epilogue: TMEM rows (Re | Im) -> Ps[K][K'] -> P(tau) and its mirror
+    if (warp < 4) {
+      const int r = 32 * warp + lane;
+      for (int c0 = 0; c0 < L.NP; c0 += 16) {
+        float v[16];
+        tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int Kp = c0 + i;
+          if (Kp < Kb) {
+            if (r < Ka) Ps[r * Kb + Kp].x = v[i];
+            else if (r < 2 * Ka) Ps[(r - Ka) * Kb + Kp].y = v[i];
+          }
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+    const bool mirror = mirror_tau && (im != it);
+    for (int x = tid; x < Ka * Kb; x += blockDim.x) {
+      const float2 p = Ps[x];
+      const double2 z = make_double2(ms * (double)p.x, ms * (double)p.y);
+      Pout[(long long)it * Ka * Kb + x] = z;
+      if (mirror) Pout[(long long)im * Ka * Kb + x] = make_double2(z.x, -z.y);
+    }
+    __syncthreads();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, ncols);
+}
+
+}  // namespace
+
+// Host side: eligibility, B-operand planes per species, launch.
+bool tc_eligible(const HostPlan& h, size_t* smem_out) {
+  size_t smax = 0;
+  for (int s = 0; s < h.n_species; ++s)
+    for (int t = 0; t < h.n_species; ++t) {
+      const int na = h.n_orb[s], nb = h.n_orb[t], Ka = h.n_prod[s], Kb = h.n_prod[t];
+      if (2 * Ka > 128 || nb * nb > 128 || Kb > 128) return false;
+      smax = std::max<size_t>(smax, tc_layout(na, nb, Ka, Kb).total);
+    }
+  if (smax > 200 * 1024) return false;
+  *smem_out = smax;
+  return true;
+}
+
+gw_status tc_init(MixedPlan& m, const HostPlan& h) {
+  m.tc_ready = false;
+  size_t smem = 0;
+  if (!tc_eligible(h, &smem)) return GW_OK;
+  // C^b in three BF16 planes per species, canonical K-major layout of an NP x KD operand
+  std::vector<uint16_t> planes;
+  std::vector<int> off;
+  for (int s = 0; s < h.n_species; ++s) {
+    const int nb = h.n_orb[s], Kb = h.n_prod[s];
+    const TcLayout L = tc_layout(nb, nb, Kb, Kb);
+    off.push_back((int)planes.size());
+    const size_t plane = (size_t)L.NP * L.KD;
+    std::vector<uint16_t> buf(3 * plane, 0);
+    for (int Kp = 0; Kp < Kb; ++Kp)
+      for (int j = 0; j < nb * nb; ++j) {
+        double c = h.C[s][(size_t)Kp * nb * nb + j];
+        float v[3];
+        for (int q = 0; q < 3; ++q) {
+          // round to bf16 (nearest even) on the host, keep the remainder
+          float f = (float)c;
+          uint32_t u;
+          std::memcpy(&u, &f, 4);
+          const uint32_t rb = ((u >> 16) & 1u) + 0x7FFFu;
+          u = (u + rb) & 0xFFFF0000u;
+          std::memcpy(&v[q], &u, 4);
+          c -= (double)v[q];
+          const uint32_t byte_off = umma::kmajor_offset(L.NP, Kp, j);
+          buf[q * plane + byte_off / 2] = (uint16_t)(u >> 16);
+        }
+      }
+    planes.insert(planes.end(), buf.begin(), buf.end());
+  }
+  cudaError_t e = cudaMalloc((void**)&m.d_Bsplit, planes.size() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMemcpy(m.d_Bsplit, planes.data(), planes.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m.d_Bsplit_off, off.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(m.d_Bsplit_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m.d_species, h.species.size() * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m.d_species, h.species.data(), h.species.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_polarizability_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("tensor-core setup: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  m.smem_tc = smem;
+  m.tc_ready = true;
+  return GW_OK;
+}
+
+void tc_free(MixedPlan& m) {
+  if (m.d_Bsplit) cudaFree(m.d_Bsplit);
+  if (m.d_Bsplit_off) cudaFree(m.d_Bsplit_off);
+  if (m.d_species) cudaFree(m.d_species);
+  m.d_Bsplit = nullptr;
+  m.d_Bsplit_off = nullptr;
+  m.d_species = nullptr;
+  m.tc_ready = false;
+}
+
+gw_status tc_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent, const double2* G_R, double2* P_R,
+                            int* d_status, cudaStream_t st) {
+  const int n_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
+  const int per = 4;
+  dim3 grid(h.n_entries(), (n_eff + per - 1) / per);
+  k_polarizability_tc<<<grid, 256, m.smem_tc, st>>>(d_ent, m.d_Cf, m.d_Bsplit, m.d_Bsplit_off, m.d_species, G_R, P_R,
+                                                    h.n_tau, n_eff, per, h.spin, h.c_symmetric, d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("k_polarizability_tc: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
+}
+
+}  // namespace gw

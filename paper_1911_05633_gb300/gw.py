@@ -16,12 +16,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgw.so")
 
-GW_FP64, GW_MIXED_BF16X3 = 0, 1
+GW_FP64, GW_MIXED = 0, 1
 GW_FERMION, GW_BOSON = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU = 0, 1
 GW_BLOCK_ORB, GW_BLOCK_PB = 0, 1
 
-_PREC = {"fp64": GW_FP64, "mixed": GW_MIXED_BF16X3, "bf16x3": GW_MIXED_BF16X3}
+_PREC = {"fp64": GW_FP64, "mixed": GW_MIXED}
 _STAT = {"F": GW_FERMION, "B": GW_BOSON, "fermion": GW_FERMION, "boson": GW_BOSON}
 _DIR = {"tau_to_iw": GW_TAU_TO_IW, "iw_to_tau": GW_IW_TO_TAU}
 _BLK = {"orb": GW_BLOCK_ORB, "pb": GW_BLOCK_PB}
@@ -52,7 +52,7 @@ class GwGrid(C.Structure):
 
 class GwOptions(C.Structure):
     _fields_ = [("spin", C.c_int), ("strict_kmesh", C.c_int), ("host_only", C.c_int), ("device", C.c_int),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("no_symmetry", C.c_int)]
 
 
 class GwPlanInfo(C.Structure):
@@ -60,7 +60,8 @@ class GwPlanInfo(C.Structure):
                 ("n_omega", C.c_int), ("n_nu", C.c_int), ("n_orb_total", C.c_int), ("n_pb_total", C.c_int),
                 ("kmesh", C.c_int * 3), ("kmesh_required", C.c_int * 3), ("c_symmetric", C.c_int),
                 ("len_orb", C.c_int64), ("len_pb", C.c_int64), ("workspace_bytes", C.c_size_t),
-                ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double)]
+                ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
+                ("w_symmetric", C.c_int), ("n_q_solved", C.c_int)]
 
 
 class GwError(RuntimeError):
@@ -121,7 +122,8 @@ class Plan:
 
     def __init__(self, lattice, frac, species, n_orb: Sequence[int], n_prod: Sequence[int], C_list,
                  kmesh, beta: float, tau, omega_idx, nu_idx, cutoff: float, spin: int = 2,
-                 strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0):
+                 strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0,
+                 no_symmetry: bool = False):
         lib = load_library()
         self._lib = lib
         self._keep = []
@@ -140,7 +142,8 @@ class Plan:
         basis = GwBasis(len(Cs), _ptr(n_orb, C.c_int), _ptr(n_prod, C.c_int), Cptr)
         grid = GwGrid(float(beta), len(tau), _ptr(tau, C.c_double), len(om), _ptr(om, C.c_int),
                       len(nu), _ptr(nu, C.c_int))
-        opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes))
+        opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes),
+                        int(bool(no_symmetry)))
         km = (C.c_int * 3)(*[int(x) for x in kmesh])
         h = C.c_void_p()
         _check(lib.gw_plan_create(C.byref(cell), C.byref(basis), km, C.byref(grid), float(cutoff),

@@ -74,6 +74,8 @@ def system(name):
     if name not in _CACHE:
         if name == "c0":
             _CACHE[name] = Sys(synth.make_config(0))
+        elif name == "c0_nosym":
+            _CACHE[name] = Sys(synth.make_config(0), no_symmetry=True)
         elif name == "mixed":
             _CACHE[name] = Sys(synth.mixed_species_cell())
         elif name == "mixed_nonsym":
@@ -126,7 +128,7 @@ def test_transform(name, st, direction, kind):
     assert rel(out, pack(ref)) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("name", SMALL + ["c0_nosym"])
 def test_screened_W(name):
     s = system(name)
     PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
@@ -199,7 +201,7 @@ def test_fourier_R_to_k(name):
     assert rel(vq, refv.reshape(-1)) < TOL
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5"])
+@pytest.mark.parametrize("name", ["c0", "c0_nosym", "mixed", "mixed_nonsym", "c1_cut5"])
 def test_whole_sweep(name):
     """All rows chained on the device from G(k, tau) and v(q); every stage vs the oracle."""
     s = system(name)
