@@ -44,6 +44,7 @@ struct gw_plan_s {
   int nu_chunk = 0;
   size_t ws_bytes = 0;
   size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_GJ = 0;
+  bool gj_blocked = false;
   gw::MixedPlan mixed;
 };
 
@@ -190,6 +191,15 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   return check_launch("k_scatter_R_to_k");
 }
 
+// Batched in-place inverse of `batch` dense N x N matrices (perm and status from the plan).
+gw_status launch_gj(gw_plan_s* p, double2* mats, int batch, long long N, cudaStream_t st) {
+  if (p->gj_blocked)
+    gw::k_gj_inverse_blocked<<<batch, 512, p->smem_GJ, st>>>(mats, p->d_perm, (int)N, N * N, p->d_status);
+  else
+    gw::k_gj_inverse<<<batch, 512, p->smem_GJ, st>>>(mats, p->d_perm, (int)N, N * N, p->d_status);
+  return check_launch("k_gj_inverse");
+}
+
 size_t smem_polar(const gw::HostPlan& h) {
   size_t m = 0;
   for (int s = 0; s < h.n_species; ++s)
@@ -333,7 +343,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   p->smem_P = smem_polar(h);
   p->smem_S = smem_sigma(h);
   p->smem_T = (size_t)std::max(std::max(h.n_tau, h.n_omega), h.n_nu) * 32 * sizeof(double2);
-  p->smem_GJ = 2 * npb * sizeof(double2);
+  // Gauss-Jordan form: blocked (panel in shared memory) when the panel fits, else unblocked
+  p->gj_blocked = npb >= 64 && (2 * npb * gw::kGJB + npb) * sizeof(double2) <= 220 * 1024;
+  p->smem_GJ = p->gj_blocked ? (2 * npb * gw::kGJB + npb) * sizeof(double2) : 2 * npb * sizeof(double2);
   if (p->smem_GJ > 227 * 1024) {
     set_last_error("product basis too large for the single-block Gauss-Jordan solve");
     return fail(GW_ERR_UNSUPPORTED);
@@ -341,7 +353,8 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if (cudaFuncSetAttribute(gw::k_polarizability_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_P) != cudaSuccess ||
       cudaFuncSetAttribute(gw::k_self_energy_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_S) != cudaSuccess ||
       cudaFuncSetAttribute(gw::k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_T) != cudaSuccess ||
-      cudaFuncSetAttribute(gw::k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_GJ) != cudaSuccess) {
+      cudaFuncSetAttribute(p->gj_blocked ? gw::k_gj_inverse_blocked : gw::k_gj_inverse,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_GJ) != cudaSuccess) {
     cudaError_t e = cudaGetLastError();
     set_last_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     return fail(GW_ERR_UNSUPPORTED);
@@ -501,7 +514,7 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
   const gw::HostPlan& h = p->h;
   if (prec == GW_MIXED) {
     st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
-                               (double2*)Sig_R, S(stream));
+                               (double2*)Sig_R, p->d_status, S(stream));
     if (st != GW_OK) return st;
   } else if (prec == GW_FP64) {
     gw::ContractArgs g{};
@@ -560,8 +573,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     dim3 g((unsigned)std::min<long long>((NN + 255) / 256, 1024), (unsigned)nq);
     gw::k_copy_mats<<<g, 256, 0, s>>>(v, p->d_qh, p->d_wsV, NN);
     if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
-    gw::k_gj_inverse<<<nq, 512, p->smem_GJ, s>>>(p->d_wsV, p->d_perm, (int)N, NN, p->d_status);
-    if ((st = check_launch("k_gj_inverse (v)")) != GW_OK) return st;
+    if ((st = launch_gj(p, p->d_wsV, nq, N, s)) != GW_OK) return st;
   }
   const int n_work = h.n_nu - p->nu_start;
   for (int c0 = 0; c0 < n_work; c0 += p->nu_chunk) {
@@ -571,8 +583,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, slot0, p->d_wsA, NN,
                              (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0)) != GW_OK)
       return st;
-    gw::k_gj_inverse<<<nc * nq, 512, p->smem_GJ, s>>>(p->d_wsA, p->d_perm, (int)N, NN, p->d_status);
-    if ((st = check_launch("k_gj_inverse")) != GW_OK) return st;
+    if ((st = launch_gj(p, p->d_wsA, nc * nq, N, s)) != GW_OK) return st;
     // W~(R) = (1/N_k) sum_q e^{-iqR} (W(q) - v(q)); in symmetric mode the sum runs over
     // one momentum of each (q, -q) pair with weight 2 and keeps the (exactly real) real part
     if ((st = launch_gather(p, GW_BLOCK_PB, nc, p->d_wsA, NN, (long long)nq * NN, v, NN, 0, (double2*)Wt_R_iw,

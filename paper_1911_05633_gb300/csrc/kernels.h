@@ -78,6 +78,9 @@ __global__ void k_self_energy_fp64(ContractArgs g);
 // In-place Gauss-Jordan inverse of a batch of N x N complex matrices (partial pivoting).
 __global__ void k_gj_inverse(double2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
                              int* status);
+constexpr int kGJB = 16;  // panel width of the blocked Gauss-Jordan inverse
+__global__ void k_gj_inverse_blocked(double2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
+                                     int* status);
 // dst[b] = src[map[b]] for dense N x N matrices (used to stage v(q) before inversion).
 __global__ void k_copy_mats(const double2* __restrict__ src, const int* __restrict__ map, double2* __restrict__ dst,
                             long long NN);

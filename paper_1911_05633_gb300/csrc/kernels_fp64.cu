@@ -393,6 +393,142 @@ __global__ void k_gj_inverse(double2* __restrict__ A, int* __restrict__ perm, in
   }
 }
 
+// Blocked form of the same in-place Gauss-Jordan inverse, panels of kGJB columns.
+// The panel's elementary steps (pivot, row exchange, scaling, elimination) run in
+// shared memory on the N x kGJB panel only; their product is I + Z with Z nonzero
+// in the panel columns, so the rest of the matrix is updated once per panel by
+// the row exchanges followed by the rank-kGJB product A[:, T] += Z A[panel rows, T].
+// Same pivot choice and result as k_gj_inverse; the matrix is read and written
+// once per panel instead of once per column.  Requires 2 N kGJB complex values of
+// shared memory (N <= 430).
+__global__ void k_gj_inverse_blocked(double2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
+                                     int* status) {
+  extern __shared__ unsigned char smraw[];
+  double2* Pan = reinterpret_cast<double2*>(smraw);  // [N][kGJB] panel columns
+  double2* Prow = Pan + (size_t)N * kGJB;            // [kGJB][N] pivot rows (pre-update)
+  double2* colk = Prow + (size_t)N * kGJB;           // [N]
+  __shared__ double2 rowk[kGJB];
+  __shared__ int pmk[kGJB];
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  const int b = blockIdx.x;
+  double2* M = A + (long long)b * mat_stride;
+  int* pm = perm + (long long)b * N;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int k0 = 0; k0 < N; k0 += kGJB) {
+    const int bb = min(kGJB, N - k0);
+    // load the panel
+    for (int x = tid; x < N * bb; x += nt) {
+      const int i = x / bb, m = x - (x / bb) * bb;
+      Pan[i * kGJB + m] = M[(long long)i * N + k0 + m];
+    }
+    __syncthreads();
+    for (int m = 0; m < bb; ++m) {
+      const int k = k0 + m;
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + tid; i < N; i += nt) {
+        const double2 z = Pan[i * kGJB + m];
+        const double a = fabs(z.x) + fabs(z.y);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+      __syncthreads();
+      if (wid == 0) {
+        best = (lane < nw) ? rv[lane] : -1.0;
+        bi = (lane < nw) ? ri[lane] : N;
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          ri[0] = bi;
+          pm[k] = bi;
+          pmk[m] = bi;
+          if (!(best > 0.0)) atomicExch(status, 1);
+        }
+      }
+      __syncthreads();
+      const int p = ri[0];
+      if (p != k && tid < bb) {
+        const double2 t = Pan[k * kGJB + tid];
+        Pan[k * kGJB + tid] = Pan[p * kGJB + tid];
+        Pan[p * kGJB + tid] = t;
+      }
+      __syncthreads();
+      const double2 d = Pan[k * kGJB + m];
+      const double den = d.x * d.x + d.y * d.y;
+      const double2 inv = (den > 0.0) ? make_double2(d.x / den, -d.y / den) : make_double2(0.0, 0.0);
+      for (int i = tid; i < N; i += nt) colk[i] = (i == k) ? make_double2(0.0, 0.0) : Pan[i * kGJB + m];
+      if (tid < bb) rowk[tid] = (tid == m) ? inv : cmul(Pan[k * kGJB + tid], inv);
+      __syncthreads();
+      for (int x = tid; x < N * bb; x += nt) {
+        const int i = x / bb, j = x - (x / bb) * bb;
+        if (i == k) {
+          Pan[i * kGJB + j] = rowk[j];
+        } else {
+          const double2 f = colk[i];
+          const double2 z = (j == m) ? make_double2(0.0, 0.0) : Pan[i * kGJB + j];
+          Pan[i * kGJB + j] = cfma(make_double2(-f.x, -f.y), rowk[j], z);
+        }
+      }
+      __syncthreads();
+    }
+    // row exchanges on the other columns, then the pivot rows (pre-update) to shared memory
+    for (int j = tid; j < N; j += nt) {
+      if (j >= k0 && j < k0 + bb) continue;
+      for (int m = 0; m < bb; ++m) {
+        const int k = k0 + m, p = pmk[m];
+        if (p != k) {
+          const double2 t = M[(long long)k * N + j];
+          M[(long long)k * N + j] = M[(long long)p * N + j];
+          M[(long long)p * N + j] = t;
+        }
+      }
+      for (int m = 0; m < bb; ++m) Prow[m * N + j] = M[(long long)(k0 + m) * N + j];
+    }
+    __syncthreads();
+    // A[:, T] += (Pan - I[:, panel]) Prow
+    for (long long x = tid; x < (long long)N * N; x += nt) {
+      const int i = (int)(x / N);
+      const int j = (int)(x - (long long)i * N);
+      if (j >= k0 && j < k0 + bb) continue;
+      double2 acc = M[x];
+      const double2* z = Pan + i * kGJB;
+      for (int m = 0; m < bb; ++m) {
+        double2 zm = z[m];
+        if (i == k0 + m) zm.x -= 1.0;
+        acc = cfma(zm, Prow[m * N + j], acc);
+      }
+      M[x] = acc;
+    }
+    // the panel itself
+    for (int x = tid; x < N * bb; x += nt) {
+      const int i = x / bb, m = x - (x / bb) * bb;
+      M[(long long)i * N + k0 + m] = Pan[i * kGJB + m];
+    }
+    __syncthreads();
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = pm[k];
+    if (p != k) {
+      for (int i = tid; i < N; i += nt) {
+        const double2 t = M[(long long)i * N + k];
+        M[(long long)i * N + k] = M[(long long)i * N + p];
+        M[(long long)i * N + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_copy_mats(const double2* __restrict__ src, const int* __restrict__ map, double2* __restrict__ dst,
                             long long NN) {
   const int b = blockIdx.y;

@@ -215,8 +215,9 @@ gw_status mixed_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* 
 }
 
 gw_status mixed_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent, const double*,
-                            const double2* G_R, const double2* Wt_R, double2* Sig_R, cudaStream_t st) {
+                            const double2* G_R, const double2* Wt_R, double2* Sig_R, int* d_status, cudaStream_t st) {
   if (!m.ready) { set_last_error("mixed path not initialised"); return GW_ERR_ARG; }
+  if (m.tc_s_ready) return tc_self_energy(m, h, d_ent, G_R, Wt_R, Sig_R, d_status, st);
   dim3 grid(h.n_entries(), h.n_tau);
   k_self_energy_f32<<<grid, 256, m.smem_S, st>>>(d_ent, m.d_Cf, G_R, Wt_R, Sig_R, h.n_tau);
   cudaError_t e = cudaGetLastError();

@@ -226,6 +226,191 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
   if (warp == 0) tmem_dealloc(tm, ncols);
 }
 
+struct TcLayoutS {
+  int KK;      // padded reduction length (K_b rounded up to 16)
+  int NJ;      // padded N (n_b^2 rounded up to 16)
+  uint32_t offA, offB, offBm, offD, offG, offBar, total;
+};
+
+__host__ __device__ inline TcLayoutS tc_layout_s(int na, int nb, int Ka, int Kb) {
+  TcLayoutS L;
+  L.KK = ((Kb + 15) / 16) * 16;
+  L.NJ = ((nb * nb + 15) / 16) * 16;
+  uint32_t o = 0;
+  L.offA = o; o += 3u * 128u * L.KK * 2u;
+  L.offB = o; o += 3u * (uint32_t)L.NJ * L.KK * 2u;
+  L.offBm = o; o += (uint32_t)Ka * nb * nb * 8u;
+  L.offD = o; o += (uint32_t)Ka * na * nb * 8u;
+  L.offG = o; o += (uint32_t)na * nb * 8u;
+  o = (o + 15u) & ~15u;
+  L.offBar = o; o += 16u;
+  L.total = o;
+  return L;
+}
+
+// Sigma contraction (Eq. S_MM, dynamic part), mixed path.  Stage A on the tensor
+// cores: Bm[(Re|Im) K][j] = sum_K2 W~[K][K2] C^b[K2][j] (A = W~ split in three
+// BF16 terms, B = (C^b)^T split likewise, six products); stages B and C in FP32:
+//   D[K][L2][L1]  = sum_L3 G[L2][L3] Bm[K][L1 nb + L3]
+//   Sigma[L][L1]  = -sum_{K, L2} C^a[K][L][L2] D[K][L2][L1]
+// grid (entry, tau chunk); 256 threads.
+__global__ void __launch_bounds__(256, 1)
+k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, const uint16_t* __restrict__ BsplitT,
+                 const int* __restrict__ BsplitT_off, const int* __restrict__ species_of_atom,
+                 const double2* __restrict__ G, const double2* __restrict__ W, double2* __restrict__ out, int n_tau,
+                 int tau_per_cta, int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  const int e = blockIdx.x;
+  const DevEntry E = ent[e];
+  const int na = E.na, nb = E.nb, Ka = E.Ka, Kb = E.Kb;
+  const TcLayoutS L = tc_layout_s(na, nb, Ka, Kb);
+  unsigned char* Ap = sm + L.offA;
+  unsigned char* Bp = sm + L.offB;
+  float2* Bm = reinterpret_cast<float2*>(sm + L.offBm);
+  float2* D = reinterpret_cast<float2*>(sm + L.offD);
+  float2* Gs = reinterpret_cast<float2*>(sm + L.offG);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.offBar);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t ncols = 32;
+  while ((int)ncols < L.NJ) ncols <<= 1;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  const int sb = species_of_atom[E.b];
+  const uint4* bsrc = reinterpret_cast<const uint4*>(BsplitT + BsplitT_off[sb]);
+  uint4* bdst = reinterpret_cast<uint4*>(Bp);
+  const int nb16 = (int)(3u * L.NJ * L.KK * 2u / 16u);
+  for (int x = tid; x < nb16; x += blockDim.x) bdst[x] = bsrc[x];
+  uint4* az = reinterpret_cast<uint4*>(Ap);
+  const int na16 = (int)(3u * 128u * L.KK * 2u / 16u);
+  for (int x = tid; x < na16; x += blockDim.x) az[x] = make_uint4(0, 0, 0, 0);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tm = tmem_base;
+  const uint32_t idesc = idesc_bf16_f32(128, L.NJ);
+  const uint32_t aBase = smem_u32(Ap), bBase = smem_u32(Bp);
+  const uint32_t aPlane = 128u * L.KK * 2u, bPlane = (uint32_t)L.NJ * L.KK * 2u;
+  const float* Ca = C + E.ca;
+  const int t0 = blockIdx.y * tau_per_cta;
+  const int t1 = min(n_tau, t0 + tau_per_cta);
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int it = t0; it < t1 && ok; ++it) {
+    const double2* Gin = G + E.off_orb * n_tau + (long long)it * na * nb;
+    const double2* Win = W + E.off_pb * n_tau + (long long)it * Ka * Kb;
+    for (int x = tid; x < na * nb; x += blockDim.x) {
+      const double2 g = Gin[x];
+      Gs[x] = make_float2((float)g.x, (float)g.y);
+    }
+    // A operand: rows K (Re W~) and Ka + K (Im W~), reduction index K2
+    for (int x = tid; x < Ka * Kb; x += blockDim.x) {
+      const int K = x / Kb, Kp = x - (x / Kb) * Kb;
+      const double2 w = Win[x];
+      __nv_bfloat16 h, m, l;
+      split3((float)w.x, h, m, l);
+      uint32_t o = kmajor_offset(128, K, Kp);
+      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+      split3((float)w.y, h, m, l);
+      o = kmajor_offset(128, Ka + K, Kp);
+      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
+      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+    }
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+      const int nks = L.KK / 16;
+      uint32_t acc = 0;
+      const int pa[6] = {0, 0, 1, 0, 1, 2};
+      const int pb[6] = {0, 1, 0, 2, 1, 0};
+      for (int s2 = 0; s2 < nks; ++s2) {
+        const uint32_t ao = (uint32_t)s2 * 128u * 32u, bo = (uint32_t)s2 * (uint32_t)L.NJ * 32u;
+        for (int q = 0; q < 6; ++q) {
+          const uint64_t da = smem_desc(aBase + pa[q] * aPlane + ao, 128, 256);
+          const uint64_t db = smem_desc(bBase + pb[q] * bPlane + bo, 128, 256);
+          mma_bf16(tm, da, db, idesc, acc);
+          acc = 1;
+        }
+      }
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitLimit) ? 1 : 0) != 0;
+    phase ^= 1u;
+    fence_after_sync();
+    if (!ok) {
+      if (tid == 0) atomicExch(status, 2);
+      mbar_wait(bar, phase ^ 1u, kWaitLimit);
+      break;
+    }
+    // TMEM -> Bm[K][j] (complex FP32)
+    if (warp < 4) {
+      const int r = 32 * warp + lane;
+      for (int c0 = 0; c0 < L.NJ; c0 += 16) {
+        float v[16];
+        tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = c0 + i;
+          if (j < nb * nb) {
+            if (r < Ka) Bm[r * nb * nb + j].x = v[i];
+            else if (r < 2 * Ka) Bm[(r - Ka) * nb * nb + j].y = v[i];
+          }
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+    // stage B: D[K][L2][L1] = sum_L3 G[L2][L3] Bm[K][L1 nb + L3]
+    for (int x = tid; x < Ka * na * nb; x += blockDim.x) {
+      const int K = x / (na * nb);
+      const int r = x - K * na * nb;
+      const int L2 = r / nb, L1 = r - L2 * nb;
+      const float2* bk = Bm + K * nb * nb + L1 * nb;
+      float tx = 0.f, ty = 0.f;
+      for (int L3 = 0; L3 < nb; ++L3) {
+        const float2 g = Gs[L2 * nb + L3];
+        const float2 bv = bk[L3];
+        tx = fmaf(g.x, bv.x, fmaf(-g.y, bv.y, tx));
+        ty = fmaf(g.x, bv.y, fmaf(g.y, bv.x, ty));
+      }
+      D[x] = make_float2(tx, ty);
+    }
+    __syncthreads();
+    // stage C: one output (L, L1) per thread
+    if (tid < na * nb) {
+      const int Lr = tid / nb, L1 = tid - (tid / nb) * nb;
+      float ax = 0.f, ay = 0.f;
+      for (int K = 0; K < Ka; ++K) {
+        const float* c = Ca + (long long)K * na * na + Lr * na;
+        const float2* dk = D + K * na * nb;
+        for (int L2 = 0; L2 < na; ++L2) {
+          const float cv = c[L2];
+          const float2 d = dk[L2 * nb + L1];
+          ax = fmaf(cv, d.x, ax);
+          ay = fmaf(cv, d.y, ay);
+        }
+      }
+      double2* o = out + E.off_orb * n_tau + (long long)it * na * nb;
+      o[tid] = make_double2(-(double)ax, -(double)ay);
+    }
+    __syncthreads();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, ncols);
+}
+
 }  // namespace
 
 // Host side: eligibility, B-operand planes per species, launch.
@@ -240,6 +425,32 @@ bool tc_eligible(const HostPlan& h, size_t* smem_out) {
   if (smax > 200 * 1024) return false;
   *smem_out = smax;
   return true;
+}
+
+static bool tc_eligible_s(const HostPlan& h, size_t* smem_out) {
+  size_t smax = 0;
+  for (int s = 0; s < h.n_species; ++s)
+    for (int t = 0; t < h.n_species; ++t) {
+      const int na = h.n_orb[s], nb = h.n_orb[t], Ka = h.n_prod[s], Kb = h.n_prod[t];
+      if (2 * Ka > 128 || nb * nb > 256 || Kb > 128) return false;
+      smax = std::max<size_t>(smax, tc_layout_s(na, nb, Ka, Kb).total);
+    }
+  if (smax > 200 * 1024) return false;
+  *smem_out = smax;
+  return true;
+}
+
+// Round to BF16 (nearest even) on the host; returns the bits and the rounded value.
+static uint16_t bf16_round(double c, double* rounded) {
+  float f = (float)c;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t rb = ((u >> 16) & 1u) + 0x7FFFu;
+  u = (u + rb) & 0xFFFF0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  *rounded = (double)r;
+  return (uint16_t)(u >> 16);
 }
 
 gw_status tc_init(MixedPlan& m, const HostPlan& h) {
@@ -258,18 +469,11 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
     for (int Kp = 0; Kp < Kb; ++Kp)
       for (int j = 0; j < nb * nb; ++j) {
         double c = h.C[s][(size_t)Kp * nb * nb + j];
-        float v[3];
+        const uint32_t byte_off = umma::kmajor_offset(L.NP, Kp, j);
         for (int q = 0; q < 3; ++q) {
-          // round to bf16 (nearest even) on the host, keep the remainder
-          float f = (float)c;
-          uint32_t u;
-          std::memcpy(&u, &f, 4);
-          const uint32_t rb = ((u >> 16) & 1u) + 0x7FFFu;
-          u = (u + rb) & 0xFFFF0000u;
-          std::memcpy(&v[q], &u, 4);
-          c -= (double)v[q];
-          const uint32_t byte_off = umma::kmajor_offset(L.NP, Kp, j);
-          buf[q * plane + byte_off / 2] = (uint16_t)(u >> 16);
+          double r;
+          buf[q * plane + byte_off / 2] = bf16_round(c, &r);
+          c -= r;
         }
       }
     planes.insert(planes.end(), buf.begin(), buf.end());
@@ -289,10 +493,66 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
   }
   m.smem_tc = smem;
   m.tc_ready = true;
+
+  // Sigma: (C^b)^T, rows j = (L1, L3), reduction K2, three BF16 planes per species
+  size_t smem_s = 0;
+  if (!tc_eligible_s(h, &smem_s)) return GW_OK;
+  std::vector<uint16_t> tplanes;
+  std::vector<int> toff;
+  for (int s = 0; s < h.n_species; ++s) {
+    const int nb = h.n_orb[s], Kb = h.n_prod[s];
+    const TcLayoutS L = tc_layout_s(nb, nb, Kb, Kb);
+    toff.push_back((int)tplanes.size());
+    const size_t plane = (size_t)L.NJ * L.KK;
+    std::vector<uint16_t> buf(3 * plane, 0);
+    for (int Kp = 0; Kp < Kb; ++Kp)
+      for (int j = 0; j < nb * nb; ++j) {
+        double c = h.C[s][(size_t)Kp * nb * nb + j];
+        const uint32_t byte_off = umma::kmajor_offset(L.NJ, j, Kp);
+        for (int q = 0; q < 3; ++q) {
+          double r;
+          buf[q * plane + byte_off / 2] = bf16_round(c, &r);
+          c -= r;
+        }
+      }
+    tplanes.insert(tplanes.end(), buf.begin(), buf.end());
+  }
+  e = cudaMalloc((void**)&m.d_BsplitT, tplanes.size() * sizeof(uint16_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m.d_BsplitT, tplanes.data(), tplanes.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m.d_BsplitT_off, toff.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(m.d_BsplitT_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_self_energy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("tensor-core setup (Sigma): ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  m.smem_tc_s = smem_s;
+  m.tc_s_ready = true;
+  return GW_OK;
+}
+
+gw_status tc_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent, const double2* G_R,
+                         const double2* Wt_R, double2* Sig_R, int* d_status, cudaStream_t st) {
+  const int per = 4;
+  dim3 grid(h.n_entries(), (h.n_tau + per - 1) / per);
+  k_self_energy_tc<<<grid, 256, m.smem_tc_s, st>>>(d_ent, m.d_Cf, m.d_BsplitT, m.d_BsplitT_off, m.d_species, G_R,
+                                                   Wt_R, Sig_R, h.n_tau, per, d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("k_self_energy_tc: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
   return GW_OK;
 }
 
 void tc_free(MixedPlan& m) {
+  if (m.d_BsplitT) cudaFree(m.d_BsplitT);
+  if (m.d_BsplitT_off) cudaFree(m.d_BsplitT_off);
+  m.d_BsplitT = nullptr;
+  m.d_BsplitT_off = nullptr;
+  m.tc_s_ready = false;
   if (m.d_Bsplit) cudaFree(m.d_Bsplit);
   if (m.d_Bsplit_off) cudaFree(m.d_Bsplit_off);
   if (m.d_species) cudaFree(m.d_species);
