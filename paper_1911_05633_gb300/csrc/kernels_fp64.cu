@@ -368,14 +368,16 @@ __global__ void k_gj_inverse(double2* __restrict__ A, int* __restrict__ perm, in
       M[(long long)k * N + j] = r;
     }
     __syncthreads();
-    // every other row: a_ij <- (j == k ? 0 : a_ij) - f_i r_j
-    for (long long x = tid; x < (long long)N * N; x += nt) {
-      const int i = (int)(x / N);
-      const int j = (int)(x - (long long)i * N);
+    // every other row: a_ij <- (j == k ? 0 : a_ij) - f_i r_j   (one warp per row, lanes along j)
+    for (int i = wid; i < N; i += nw) {
       if (i == k) continue;
-      double2 f = colk[i];
-      double2 z = (j == k) ? make_double2(0.0, 0.0) : M[x];
-      M[x] = cfma(make_double2(-f.x, -f.y), rowk[j], z);
+      const double2 f = colk[i];
+      const double2 mf = make_double2(-f.x, -f.y);
+      double2* Mi = M + (long long)i * N;
+      for (int j = lane; j < N; j += 32) {
+        const double2 z = (j == k) ? make_double2(0.0, 0.0) : Mi[j];
+        Mi[j] = cfma(mf, rowk[j], z);
+      }
     }
     __syncthreads();
   }
@@ -495,19 +497,23 @@ __global__ void k_gj_inverse_blocked(double2* __restrict__ A, int* __restrict__ 
       for (int m = 0; m < bb; ++m) Prow[m * N + j] = M[(long long)(k0 + m) * N + j];
     }
     __syncthreads();
-    // A[:, T] += (Pan - I[:, panel]) Prow
-    for (long long x = tid; x < (long long)N * N; x += nt) {
-      const int i = (int)(x / N);
-      const int j = (int)(x - (long long)i * N);
-      if (j >= k0 && j < k0 + bb) continue;
-      double2 acc = M[x];
-      const double2* z = Pan + i * kGJB;
-      for (int m = 0; m < bb; ++m) {
-        double2 zm = z[m];
-        if (i == k0 + m) zm.x -= 1.0;
-        acc = cfma(zm, Prow[m * N + j], acc);
+    // A[:, T] += (Pan - I[:, panel]) Prow   (one warp per row, lanes along j)
+    for (int i = wid; i < N; i += nw) {
+      double2 z[kGJB];
+#pragma unroll
+      for (int m = 0; m < kGJB; ++m) {
+        z[m] = (m < bb) ? Pan[i * kGJB + m] : make_double2(0.0, 0.0);
+        if (i == k0 + m) z[m].x -= 1.0;
       }
-      M[x] = acc;
+      double2* Mi = M + (long long)i * N;
+      for (int j = lane; j < N; j += 32) {
+        if (j >= k0 && j < k0 + bb) continue;
+        double2 acc = Mi[j];
+#pragma unroll
+        for (int m = 0; m < kGJB; ++m)
+          if (m < bb) acc = cfma(z[m], Prow[m * N + j], acc);
+        Mi[j] = acc;
+      }
     }
     // the panel itself
     for (int x = tid; x < N * bb; x += nt) {

@@ -250,7 +250,7 @@ class SynthCell:
         lo, hi = 0.0, 1.0
         while gap_of(hi) < target:
             hi *= 2.0
-        for _ in range(80):
+        for _ in range(60):
             mid = 0.5 * (lo + hi)
             if gap_of(mid) < target:
                 lo = mid

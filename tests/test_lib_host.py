@@ -112,3 +112,21 @@ def test_plan_errors(gwlib):
     st = lib.gw_green_k_to_R(p._h, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
     assert st == 9
     assert lib.gw_status_string(9) == b"plan has no device state"
+
+
+def test_w_solve_mode(gwlib):
+    """Which momenta and frequencies the W solve runs on (host-side plan logic)."""
+    from paper_1911_05633_gb300 import gw
+    c0 = synth.make_config(0)
+    p = gw.Plan.from_cell(c0, host_only=True)
+    assert p.info["w_symmetric"] == 1 and p.info["n_q_solved"] == 8  # 2x2x2: every q is its own -q
+    p = gw.Plan.from_cell(c0, host_only=True, no_symmetry=True)
+    assert p.info["w_symmetric"] == 0 and p.info["n_q_solved"] == 8
+    c1 = synth.make_config(1, build=False)
+    c1._draw_basis(np.random.default_rng(0))
+    p = gw.Plan.from_cell(c1, host_only=True)
+    # 4x4x4 mesh: 8 momenta with q = -q and 28 pairs
+    assert p.info["w_symmetric"] == 1 and p.info["n_q_solved"] == 36
+    ns = synth.mixed_species_cell(symmetric_C=False, n_tau=10)
+    p = gw.Plan.from_cell(ns, host_only=True)
+    assert p.info["c_symmetric"] == 0 and p.info["w_symmetric"] == 0
