@@ -30,7 +30,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "P+Σ sweep time & TFLOP/s vs peak; serve p50/p99; mixed vs FP64 at 1e-6 rel err"
 UNIT = "sweep/s"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured value in the peaks file)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (used only if the live probe fails)
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), valid
+# only while the kernel's source file is unchanged since the capture.
+TRAFFIC = {}
 
 
 def parse():
@@ -231,6 +235,18 @@ class Sweep:
         return 1 + 1 + 1 + w + 1 + 1 + 2 + 1 + 2
 
 
+def traffic_of(stage: str):
+    """DRAM bytes per launch of the stage's dominant kernel from a committed ncu
+    capture, or None when there is none or its source has changed since."""
+    import hashlib
+    t = TRAFFIC.get(stage)
+    if not t:
+        return None
+    src = os.path.join(ROOT, "paper_1911_05633_gb300", "csrc", t["file"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return t["bytes_per_launch"] if sha == t["src_sha"] else None
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -245,6 +261,11 @@ def run_ours(args, rank, world, local):
     sw.load_inputs(Gk, vq)
     stream = torch.cuda.Stream(device=local)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=sw.dev)  # 256 MB > L2
+    try:
+        from paper_1911_05633_gb300 import gw
+        fp64_peak, fp32_peak = gw.fp_peak(local)
+    except Exception:
+        fp64_peak, fp32_peak = None, None
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             sw.run(stream)
@@ -286,11 +307,14 @@ def run_ours(args, rank, world, local):
     except Exception:
         pass
     roof = None
-    if dom_name in work and args.precision == "fp64":
+    if dom_name == "W_solve" or (dom_name in work and args.precision == "fp64"):
         ach = work[dom_name] / (stage_mean[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": round(ach, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(ach / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
-                "peak_source": "nominal FP64 (not in MEASURED_PEAKS.json)"}
+        peak, src = fp64_peak, "FP64 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
+        if not peak:
+            peak, src = FP64_NOMINAL_TFLOPS, "nominal FP64 (probe unavailable)"
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_of(dom_name),
+                "peak_source": src}
     contraction_tflops = {k: round(work[k] / (stage_mean[Sweep.STAGES.index(k)] * 1e-3) / 1e12, 4)
                           for k in ("P", "Sigma", "W_solve")}
 
@@ -308,6 +332,7 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
         "tflops": contraction_tflops,
+        "fp64_peak_tflops_measured": fp64_peak, "fp32_peak_tflops_measured": fp32_peak,
         "wall_s": round(wall, 3),
         "clocks": clk,
         "gpu_launches": sw.kernel_launches() * args.steps,

@@ -92,7 +92,7 @@ typedef struct {
   int strict_kmesh;       /* 1: reject a k-mesh below the rule of Sec. 2 */
   int host_only;          /* 1: build host tables only; compute calls fail with GW_ERR_NO_DEVICE */
   int device;             /* CUDA device ordinal used by the plan */
-  size_t workspace_bytes; /* cap on the W-solve scratch (0: 2 GiB) */
+  size_t workspace_bytes; /* cap on the W-solve scratch (0: 4 GiB) */
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
 } gw_options;
 

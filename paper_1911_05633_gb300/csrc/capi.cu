@@ -329,7 +329,7 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
   const size_t mat = npb * npb * sizeof(double2);
   const size_t per_nu = (size_t)p->n_qh * (mat + npb * sizeof(int));
-  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes : ((size_t)2 << 30);
+  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes : ((size_t)4 << 30);
   const int n_work_nu = h.n_nu - p->nu_start;
   const size_t base_bytes = (size_t)p->n_qh * mat;
   int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_work_nu, cap > base_bytes ? (cap - base_bytes) / per_nu : 1));

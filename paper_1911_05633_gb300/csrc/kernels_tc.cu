@@ -23,7 +23,7 @@ namespace {
 
 using namespace umma;
 
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint64_t kWaitNs = 200ull * 1000ull * 1000ull;  // 200 ms per wait
 
 __device__ __forceinline__ void split3(float y, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
   h = __float2bfloat16_rn(y);
@@ -184,14 +184,14 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
       mma_commit(bar);
     }
     // every thread waits; the block acts on one common verdict
-    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitLimit) ? 1 : 0) != 0;
+    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitNs, status) ? 1 : 0) != 0;
     phase ^= 1u;
     fence_after_sync();
     if (!ok) {
       if (tid == 0) atomicExch(status, 2);
       // give the tensor core a second bounded chance to finish before the
       // accumulator is released
-      mbar_wait(bar, phase ^ 1u, kWaitLimit);
+      mbar_wait(bar, phase ^ 1u, kWaitNs, nullptr);
       break;
     }
     // epilogue: TMEM rows (Re | Im) -> Ps[K][K'] -> P(tau) and its mirror
@@ -345,12 +345,12 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
       }
       mma_commit(bar);
     }
-    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitLimit) ? 1 : 0) != 0;
+    ok = __syncthreads_and(mbar_wait(bar, phase, kWaitNs, status) ? 1 : 0) != 0;
     phase ^= 1u;
     fence_after_sync();
     if (!ok) {
       if (tid == 0) atomicExch(status, 2);
-      mbar_wait(bar, phase ^ 1u, kWaitLimit);
+      mbar_wait(bar, phase ^ 1u, kWaitNs, nullptr);
       break;
     }
     // TMEM -> Bm[K][j] (complex FP32)

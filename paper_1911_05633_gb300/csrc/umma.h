@@ -91,11 +91,20 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for the mbarrier phase with the given parity; gives up after `limit`
-// polls and returns false (the caller records a timeout instead of hanging).
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the mbarrier phase with the given parity.  Gives up and returns false
+// after `timeout_ns` of wall time, or as soon as *abort is non-zero (another block
+// already gave up), so that a failure costs one timeout, not one per block.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t timeout_ns,
+                                          const volatile int* abort) {
   const uint32_t a = smem_u32(mbar);
-  for (uint32_t i = 0; i < limit; ++i) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -103,8 +112,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done) : "r"(a), "r"(parity) : "memory");
     if (done) return true;
+    if ((i & 63) == 63) {
+      if (abort && *abort) return false;
+      if (global_ns() - t0 > timeout_ns) return false;
+    }
   }
-  return false;
 }
 
 // 32 lanes x 16 consecutive FP32 columns: thread t of the warp gets row (lane_base + t).

@@ -30,7 +30,7 @@ EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
-    "gw_status_string", "gw_last_error",
+    "gw_status_string", "gw_last_error", "gw_fp_peak",
 ]
 
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_self_energy_tau.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, vp]
     lib.gw_fourier_R_to_k.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_sync.argtypes = [vp, vp]
+    lib.gw_fp_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.gw_status_string.argtypes = [C.c_int]
     lib.gw_status_string.restype = C.c_char_p
     lib.gw_last_error.restype = C.c_char_p
@@ -115,6 +116,14 @@ def _check(status: int, what: str):
 
 def _ptr(arr: np.ndarray, ctype):
     return arr.ctypes.data_as(C.POINTER(ctype))
+
+
+def fp_peak(device: int = 0):
+    """(FP64, FP32) dense FMA throughput in TFLOP/s measured on `device` (gw_fp_peak)."""
+    lib = load_library()
+    a, b = C.c_double(), C.c_double()
+    _check(lib.gw_fp_peak(int(device), C.byref(a), C.byref(b)), "gw_fp_peak")
+    return a.value, b.value
 
 
 class Plan:
