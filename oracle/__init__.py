@@ -195,11 +195,24 @@ def polarizability_R(G_R: Sequence[np.ndarray], entries: np.ndarray, C_atom: Seq
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        G = G_R[e]
-        Gm = np.conj(G[::-1])
-        P = -spin * np.einsum("kAB,tAC,tBD,qCD->tkq", C_atom[a], G, Gm, C_atom[b], optimize=True)
-        out.append(P)
+        out.append(-spin * _p_block(C_atom[a], G_R[e], np.conj(G_R[e][::-1]), C_atom[b]))
     return out
+
+
+def _p_block(Ca, G1, G2c, Cb):
+    """sum_{A B C D} Ca[k,A,B] G1[t,A,C] G2c[t,B,D] Cb[q,C,D], one summation index at a time
+    (A = L, B = L'', C = L', D = L''' of Eq. P_MM)."""
+    X = np.einsum("kAB,tAC->tkBC", Ca, G1)      # sum over A
+    Y = np.einsum("tkBC,tBD->tkCD", X, G2c)     # sum over B
+    return np.einsum("tkCD,qCD->tkq", Y, Cb)    # sum over C and D
+
+
+def _s_block(Ca, G, W, Cb):
+    """sum_{K M N Q} Ca[K,L,M] G[t,M,N] W[t,K,Q] Cb[Q,P,N] -> [t,L,P], one index group at a time
+    (M = L'', N = L''', Q = K' of Eq. S_MM)."""
+    B = np.einsum("tKQ,QPN->tKPN", W, Cb)       # sum over Q
+    D = np.einsum("tMN,tKPN->tKMP", G, B)       # sum over N
+    return np.einsum("KLM,tKMP->tLP", Ca, D)     # sum over K and M
 
 
 def polarizability_q_kspace(G_k: np.ndarray, C_atom, orb_off, pb_off, kmesh, spin: int = 2) -> np.ndarray:
@@ -221,8 +234,8 @@ def polarizability_q_kspace(G_k: np.ndarray, C_atom, orb_off, pb_off, kmesh, spi
                 for b in range(nat):
                     G1 = G_k[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]]
                     G2 = np.conj(G_k[ikq, ::-1, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]])
-                    out[iq, :, pb_off[a]:pb_off[a + 1], pb_off[b]:pb_off[b + 1]] += np.einsum(
-                        "kAB,tAC,tBD,qCD->tkq", C_atom[a], G1, G2, C_atom[b], optimize=True)
+                    out[iq, :, pb_off[a]:pb_off[a + 1], pb_off[b]:pb_off[b + 1]] += _p_block(
+                        C_atom[a], G1, G2, C_atom[b])
     return -spin * out / nk
 
 
@@ -339,7 +352,7 @@ def self_energy_R(G_R, Wt_R, entries, C_atom) -> List[np.ndarray]:
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        out.append(-np.einsum("kLM,tMN,tkq,qPN->tLP", C_atom[a], G_R[e], Wt_R[e], C_atom[b], optimize=True))
+        out.append(-_s_block(C_atom[a], G_R[e], Wt_R[e], C_atom[b]))
     return out
 
 
@@ -349,8 +362,7 @@ def exchange_R(G_R, v_R, entries, C_atom) -> List[np.ndarray]:
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        Gb = G_R[e][-1]
-        out.append(np.einsum("kLM,MN,kq,qPN->LP", C_atom[a], Gb, v_R[e], C_atom[b], optimize=True))
+        out.append(_s_block(C_atom[a], G_R[e][-1:], v_R[e][None], C_atom[b])[0])
     return out
 
 
@@ -370,8 +382,8 @@ def self_energy_k_kspace(G_k: np.ndarray, Wt_q_tau: np.ndarray, C_atom, orb_off,
                 for b in range(nat):
                     G = G_k[ikq, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]]
                     W = Wt_q_tau[iq, :, pb_off[a]:pb_off[a + 1], pb_off[b]:pb_off[b + 1]]
-                    out[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]] -= np.einsum(
-                        "kLM,tMN,tkq,qPN->tLP", C_atom[a], G, W, C_atom[b], optimize=True)
+                    out[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]] -= _s_block(
+                        C_atom[a], G, W, C_atom[b])
     return out / nk
 
 

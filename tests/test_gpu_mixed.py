@@ -31,6 +31,12 @@ def test_self_energy_mixed(name):
     assert err < TOL_MIXED, err
 
 
+# The W solve amplifies relative errors of P by ~10^3 on these systems (the CPU test
+# test_w_solve_amplifies_errors_of_p measures it with the oracle alone), so a chain whose
+# P is good to <= 1e-6 delivers W~ and Sigma to <= 1e-3.
+TOL_CHAIN = 1e-3
+
+
 @pytest.mark.parametrize("name", ["c0", "c1_cut5"])
 def test_whole_sweep_mixed(name):
     s = system(name)
@@ -46,8 +52,8 @@ def test_whole_sweep_mixed(name):
     Sk = p.fourier_R_to_k("orb", s.cell.omega_idx.size, Siw)
     p.sync()
     assert rel(host(PR), pack(r["P_R"])) < TOL_MIXED
-    assert rel(host(Sig), pack(r["Sig_R"])) < TOL_MIXED
-    assert rel(host(Sk), r["Sig_k"].reshape(-1)) < TOL_MIXED
+    assert rel(host(Sig), pack(r["Sig_R"])) < TOL_CHAIN
+    assert rel(host(Sk), r["Sig_k"].reshape(-1)) < TOL_CHAIN
 
 
 def test_mixed_largest_blocks_cuda_core_path():

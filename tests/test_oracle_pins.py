@@ -427,3 +427,25 @@ def test_self_energy_vanishes_without_screening(cell0):
     WR = [np.zeros((c.n_tau, 8, 8), complex) for _ in sysm.entries]
     SR = oracle.self_energy_R(GR, WR, sysm.entries, sysm.C_atom)
     assert max(np.abs(s).max() for s in SR) == 0.0
+
+
+def test_w_solve_amplifies_errors_of_p():
+    """Conditioning of the chain P -> W~ (oracle only): a relative perturbation of
+    1e-7 in P(R, tau) moves W~(R, tau) by 1e-6 .. 1e-3 relative on the 8-atom cell
+    (short cutoff, 2x2x2 mesh).  This fixes the tolerance of a mixed-precision chain."""
+    c = synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2))
+    orc = oracle.OracleSystem(c)
+    G = c.green_k_tau()
+    vq, _ = c.coulomb()
+    GR = oracle.fourier_k_to_R(G, orc.entries, orc.kmesh, c.orb_offsets, c.orb_offsets)
+    PR = oracle.polarizability_R(GR, orc.entries, orc.C_atom)
+    rng = np.random.default_rng(0)
+    PRn = [p * (1 + 1e-7 * rng.standard_normal(p.shape)) for p in PR]
+
+    def w_tau(P):
+        Wiw, _ = oracle.screened_W(oracle.transform(orc.B_fwd, P), orc.entries, vq, orc.kmesh, c.pb_offsets)
+        return np.concatenate([x.ravel() for x in oracle.transform(orc.B_inv, Wiw)])
+
+    a, b = w_tau(PRn), w_tau(PR)
+    amp = np.linalg.norm(a - b) / np.linalg.norm(b) / 1e-7
+    assert 10.0 < amp < 1e4, amp
