@@ -94,6 +94,8 @@ typedef struct {
   int device;             /* CUDA device ordinal used by the plan */
   size_t workspace_bytes; /* cap on the W-solve scratch (0: 4 GiB) */
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
+  int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is a multiple of 128),
+                             1: FP64 Gauss-Jordan inverse always */
 } gw_options;
 
 typedef struct {
@@ -110,6 +112,7 @@ typedef struct {
   double cond_boson;
   int w_symmetric;            /* the W solve runs on nu >= 0 and half of the q mesh (see gw_screened_W_iw) */
   int n_q_solved;             /* momenta solved per frequency */
+  int w_tensor;               /* inverses by FP32 Gauss-Jordan + one tensor-core refinement */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */
@@ -164,8 +167,10 @@ gw_status gw_transform_tau_iw(gw_plan_t plan, gw_statistics st, gw_direction dir
                               gw_block kind, const void* in, void* out, void* stream);
 
 /* W~(R, i nu) on the kept entries from P(R, i nu) (Eq. W_1 with W = v + W~):
- * P(q) = sum_{kept R} e^{iq.R} P(R); W(q) = (I - v(q) P(q))^{-1} v(q), computed in
- * FP64 as (v(q)^{-1} - P(q))^{-1} by Gauss-Jordan with partial pivoting;
+ * P(q) = sum_{kept R} e^{iq.R} P(R); W(q) = (I - v(q) P(q))^{-1} v(q), computed as
+ * (v(q)^{-1} - P(q))^{-1}, each inverse either by FP64 Gauss-Jordan with partial
+ * pivoting or (w_tensor) by FP32 Gauss-Jordan refined once with a residual
+ * I - A X0 evaluated to FP64 accuracy on the tensor cores (exact BF16 slices);
  * W~(R) = (1/N_k) sum_q e^{-iq.R} (W(q) - v(q)).
  * P_R_iw, Wt_R_iw: PB layout, N_nu slices.  v_q: dense [N_k][N_PB][N_PB].
  * When the plan reports w_symmetric (C symmetric in (L, L''), a symmetric bosonic

@@ -11,7 +11,9 @@
 #include <vector>
 
 #include "kernels.h"
+#include "smem_limit.h"
 #include "mixed.h"
+#include "wtc.h"
 
 struct gw_plan_s {
   gw::HostPlan h;
@@ -45,6 +47,16 @@ struct gw_plan_s {
   size_t ws_bytes = 0;
   size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_GJ = 0;
   bool gj_blocked = false;
+  // tensor-core inverse (FP32 Gauss-Jordan + sliced FP64-accurate residual)
+  bool w_tensor = false;
+  size_t smem_GJ32 = 0;
+  float2* t_X32 = nullptr;
+  double2* t_X1 = nullptr;
+  double2* t_R = nullptr;
+  uint16_t* t_Asl = nullptr;
+  uint16_t* t_Xsl = nullptr;
+  int* t_eA = nullptr;
+  int* t_eX = nullptr;
   gw::MixedPlan mixed;
 };
 
@@ -97,7 +109,8 @@ gw_status upload(T** dst, const void* src, size_t bytes) {
 void free_device(gw_plan_s* p) {
   void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_phase,
                   p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_inv, p->d_qh, p->d_qw,
-                  p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status};
+                  p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_X1, p->t_R, p->t_Asl,
+                  p->t_Xsl, p->t_eA, p->t_eX};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
@@ -200,6 +213,13 @@ gw_status launch_gj(gw_plan_s* p, double2* mats, int batch, long long N, cudaStr
   return check_launch("k_gj_inverse");
 }
 
+// In place: mats[b] (FP64, N x N) -> its inverse by the tensor-core refinement (kernels_wtc.cu).
+gw_status launch_tensor_inverse(gw_plan_s* p, double2* mats, int batch, long long N, cudaStream_t st) {
+  gw::WtcBuffers w{p->t_X32, p->t_X1, p->t_R, p->t_Asl, p->t_Xsl, p->t_eA, p->t_eX, p->d_perm, p->d_status};
+  gw::wtc_inverse(w, mats, batch, (int)N, p->smem_GJ32, st);
+  return check_launch("tensor-core inverse");
+}
+
 size_t smem_polar(const gw::HostPlan& h) {
   size_t m = 0;
   for (int s = 0; s < h.n_species; ++s)
@@ -290,6 +310,12 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
       for (int l = 0; l < hh.n_nu; ++l)
         if (hh.nu_idx[l] == -hh.nu_idx[j]) numirror.push_back(l);
   }
+  {
+    // tensor-core inverse: N a multiple of 128 and the FP32 panel in shared memory
+    const size_t n = (size_t)hh.n_pb_total();
+    p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 &&
+                  (2 * n * gw::kGJB + n) * sizeof(float2) <= 220 * 1024;
+  }
   p->device = opt ? opt->device : 0;
   if (p->host_only) {
     *out = p;
@@ -328,8 +354,15 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_qw, qw.data(), qw.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
   const size_t mat = npb * npb * sizeof(double2);
-  const size_t per_nu = (size_t)p->n_qh * (mat + npb * sizeof(int));
-  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes : ((size_t)4 << 30);
+  // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) FP32 copy, residual,
+  // the BF16 slices of both operands and the scale exponents
+  const size_t per_mat = mat + npb * sizeof(int) +
+                         (p->w_tensor ? npb * npb * (sizeof(float2) + 2 * sizeof(double2) + 2 * (gw::kWSA + gw::kWSX1) * 2) +
+                                            2 * npb * sizeof(int)
+                                      : 0);
+  const size_t per_nu = (size_t)p->n_qh * per_mat;
+  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes
+                                                    : (p->w_tensor ? ((size_t)24 << 30) : ((size_t)4 << 30));
   const int n_work_nu = h.n_nu - p->nu_start;
   const size_t base_bytes = (size_t)p->n_qh * mat;
   int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_work_nu, cap > base_bytes ? (cap - base_bytes) / per_nu : 1));
@@ -338,6 +371,22 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_wsA, nullptr, (size_t)nch * p->n_qh * mat)) != GW_OK) return fail(st);
   if ((st = upload(&p->d_perm, nullptr, (size_t)nch * p->n_qh * npb * sizeof(int))) != GW_OK) return fail(st);
   p->ws_bytes = (size_t)p->n_qh * mat + (size_t)nch * per_nu;
+  if (p->w_tensor) {
+    const size_t nm = (size_t)nch * p->n_qh;
+    if ((st = upload(&p->t_X32, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_X1, nullptr, nm * npb * npb * sizeof(double2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_R, nullptr, nm * npb * npb * sizeof(double2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_Asl, nullptr, nm * npb * npb * 2 * gw::kWSA * 2)) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_Xsl, nullptr, nm * npb * npb * 2 * gw::kWSX1 * 2)) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_eA, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_eX, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
+    p->smem_GJ32 = (2 * npb * gw::kGJB + npb) * sizeof(float2);
+    if (gw::wtc_setup(p->smem_GJ32) != cudaSuccess) {
+      cudaError_t e = cudaGetLastError();
+      set_last_error(std::string("cudaFuncSetAttribute (tensor W): ") + cudaGetErrorString(e));
+      return fail(GW_ERR_UNSUPPORTED);
+    }
+  }
 
   // dynamic shared memory opt-ins
   p->smem_P = smem_polar(h);
@@ -350,11 +399,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     set_last_error("product basis too large for the single-block Gauss-Jordan solve");
     return fail(GW_ERR_UNSUPPORTED);
   }
-  if (cudaFuncSetAttribute(gw::k_polarizability_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_P) != cudaSuccess ||
-      cudaFuncSetAttribute(gw::k_self_energy_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_S) != cudaSuccess ||
-      cudaFuncSetAttribute(gw::k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_T) != cudaSuccess ||
-      cudaFuncSetAttribute(p->gj_blocked ? gw::k_gj_inverse_blocked : gw::k_gj_inverse,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_GJ) != cudaSuccess) {
+  if (gw::raise_smem_limit(gw::k_polarizability_fp64, (int)p->smem_P) != cudaSuccess ||
+      gw::raise_smem_limit(gw::k_self_energy_fp64, (int)p->smem_S) != cudaSuccess ||
+      gw::raise_smem_limit(gw::k_transform, (int)p->smem_T) != cudaSuccess ||
+      gw::raise_smem_limit(p->gj_blocked ? gw::k_gj_inverse_blocked : gw::k_gj_inverse, (int)p->smem_GJ) != cudaSuccess) {
     cudaError_t e = cudaGetLastError();
     set_last_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     return fail(GW_ERR_UNSUPPORTED);
@@ -398,6 +446,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->cond_fermion = h.cond_f;
   info->cond_boson = h.cond_b;
   info->w_symmetric = p->w_sym ? 1 : 0;
+  info->w_tensor = p->w_tensor ? 1 : 0;
   info->n_q_solved = p->n_qh;
   return GW_OK;
 }
@@ -573,7 +622,9 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     dim3 g((unsigned)std::min<long long>((NN + 255) / 256, 1024), (unsigned)nq);
     gw::k_copy_mats<<<g, 256, 0, s>>>(v, p->d_qh, p->d_wsV, NN);
     if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
-    if ((st = launch_gj(p, p->d_wsV, nq, N, s)) != GW_OK) return st;
+    if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsV, nq, N, s);
+    else st = launch_gj(p, p->d_wsV, nq, N, s);
+    if (st != GW_OK) return st;
   }
   const int n_work = h.n_nu - p->nu_start;
   for (int c0 = 0; c0 < n_work; c0 += p->nu_chunk) {
@@ -583,7 +634,9 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, slot0, p->d_wsA, NN,
                              (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0)) != GW_OK)
       return st;
-    if ((st = launch_gj(p, p->d_wsA, nc * nq, N, s)) != GW_OK) return st;
+    if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsA, nc * nq, N, s);
+    else st = launch_gj(p, p->d_wsA, nc * nq, N, s);
+    if (st != GW_OK) return st;
     // W~(R) = (1/N_k) sum_q e^{-iqR} (W(q) - v(q)); in symmetric mode the sum runs over
     // one momentum of each (q, -q) pair with weight 2 and keeps the (exactly real) real part
     if ((st = launch_gather(p, GW_BLOCK_PB, nc, p->d_wsA, NN, (long long)nq * NN, v, NN, 0, (double2*)Wt_R_iw,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "smem_limit.h"
 #include "mixed.h"
 
 namespace gw {
@@ -184,9 +185,9 @@ gw_status mixed_init(MixedPlan& m, const HostPlan& h, const std::vector<DevEntry
   }
   m.smem_P = smem_p32(h);
   m.smem_S = smem_s32(h);
-  if (cudaFuncSetAttribute(k_polarizability_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem_P) !=
+  if (gw::raise_smem_limit(k_polarizability_f32, (int)m.smem_P) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_self_energy_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem_S) !=
+      gw::raise_smem_limit(k_self_energy_f32, (int)m.smem_S) !=
           cudaSuccess) {
     set_last_error("cudaFuncSetAttribute failed for the mixed kernels");
     return GW_ERR_UNSUPPORTED;

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "kernels.h"
+#include "smem_limit.h"
 #include "mixed.h"
 #include "umma.h"
 
@@ -486,7 +487,7 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
   if (e == cudaSuccess)
     e = cudaMemcpy(m.d_species, h.species.data(), h.species.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_polarizability_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = gw::raise_smem_limit(k_polarizability_tc, (int)smem);
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core setup: ") + cudaGetErrorString(e));
     return GW_ERR_CUDA;
@@ -523,7 +524,7 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&m.d_BsplitT_off, toff.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(m.d_BsplitT_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_self_energy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    e = gw::raise_smem_limit(k_self_energy_tc, (int)smem_s);
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core setup (Sigma): ") + cudaGetErrorString(e));
     return GW_ERR_CUDA;

@@ -119,6 +119,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint6
   }
 }
 
+// Instruction descriptor as idesc_bf16_f32 with the A operand negated (D += -A B^T).
+__host__ __device__ __forceinline__ uint32_t idesc_bf16_f32_negA(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 13);
+}
+
+// Expect `bytes` of asynchronous copies on the mbarrier and arrive once.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared (both 16-byte aligned, size a multiple of 16), completing
+// its bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
 // 32 lanes x 16 consecutive FP32 columns: thread t of the warp gets row (lane_base + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];

@@ -54,6 +54,8 @@ class Sys:
         from paper_1911_05633_gb300 import gw
         self.cell = cell
         self.plan = gw.Plan.from_cell(cell, **plan_kw)
+        # N_PB a multiple of 128 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
+        assert self.plan.info["w_tensor"] == int(cell.n_pb_total % 128 == 0 and plan_kw.get("w_solver") != "gauss_jordan")
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
         self.G_k = cell.green_k_tau()
@@ -84,6 +86,8 @@ def system(name):
             _CACHE[name] = Sys(synth.make_config(1))
         elif name == "c1_cut5":
             _CACHE[name] = Sys(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)))
+        elif name == "c1_cut5_gj":
+            _CACHE[name] = Sys(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)), w_solver="gauss_jordan")
         else:
             raise KeyError(name)
     return _CACHE[name]
@@ -128,7 +132,7 @@ def test_transform(name, st, direction, kind):
     assert rel(out, pack(ref)) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL + ["c0_nosym"])
+@pytest.mark.parametrize("name", SMALL + ["c0_nosym", "c1_cut5_gj"])
 def test_screened_W(name):
     s = system(name)
     PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
@@ -201,7 +205,7 @@ def test_fourier_R_to_k(name):
     assert rel(vq, refv.reshape(-1)) < TOL
 
 
-@pytest.mark.parametrize("name", ["c0", "c0_nosym", "mixed", "mixed_nonsym", "c1_cut5"])
+@pytest.mark.parametrize("name", ["c0", "c0_nosym", "mixed", "mixed_nonsym", "c1_cut5", "c1_cut5_gj"])
 def test_whole_sweep(name):
     """All rows chained on the device from G(k, tau) and v(q); every stage vs the oracle."""
     s = system(name)
