@@ -231,7 +231,9 @@ class Sweep:
         inf = self.plan.info
         nnu = int((self.cell.nu_idx >= 0).sum()) if inf["w_symmetric"] else inf["n_nu"]
         nchunks = -(-nnu // inf["nu_chunk"])
-        w = 2 + 3 * nchunks + (1 if inf["w_symmetric"] else 0)
+        inv = 12 if inf["w_tensor"] else 1  # launches per batched inverse
+        # copy of v, inverse of v, per chunk (scatter, inverse, gather), mirror
+        w = 1 + inv + nchunks * (2 + inv) + (1 if inf["w_symmetric"] else 0)
         return 1 + 1 + 1 + w + 1 + 1 + 2 + 1 + 2
 
 

@@ -94,7 +94,7 @@ typedef struct {
   int device;             /* CUDA device ordinal used by the plan */
   size_t workspace_bytes; /* cap on the W-solve scratch (0: 4 GiB) */
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
-  int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is a multiple of 128),
+  int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384),
                              1: FP64 Gauss-Jordan inverse always */
 } gw_options;
 
@@ -197,6 +197,18 @@ gw_status gw_self_energy_tau(gw_plan_t plan, const void* G_R, const void* Wt_R,
  * [N_k][n_slices][N][N]; blocks of atom pairs without entries are zero. */
 gw_status gw_fourier_R_to_k(gw_plan_t plan, gw_block kind, int n_slices,
                             const void* F_R, void* F_k, void* stream);
+
+/* Per-kernel device timing (an instrumentation aid; no counterpart in the paper).
+ * gw_timing_enable(plan, 1) makes every later kernel launch of this plan's entry points
+ * record a CUDA event before and after it on the launching stream (off by default;
+ * keep it off while a stream is being captured into a graph).  gw_timing_read waits for
+ * the recorded events, adds their elapsed times per kernel name and reports entry
+ * `index` (GW_ERR_ARG past the last one): `*name` stays valid until the next
+ * gw_timing_reset or gw_plan_destroy, `*total_ms` is the summed device time and
+ * `*launches` the number of launches.  gw_timing_reset clears the totals. */
+gw_status gw_timing_enable(gw_plan_t plan, int enable);
+gw_status gw_timing_read(gw_plan_t plan, int index, const char** name, double* total_ms, long long* launches);
+gw_status gw_timing_reset(gw_plan_t plan);
 
 /* Wait for the stream and report any deferred device-side error of the plan. */
 gw_status gw_sync(gw_plan_t plan, void* stream);

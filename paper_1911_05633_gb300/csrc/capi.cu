@@ -14,6 +14,7 @@
 #include "smem_limit.h"
 #include "mixed.h"
 #include "wtc.h"
+#include "ktimer.h"
 
 struct gw_plan_s {
   gw::HostPlan h;
@@ -58,12 +59,18 @@ struct gw_plan_s {
   int* t_eA = nullptr;
   int* t_eX = nullptr;
   gw::MixedPlan mixed;
+  gw::KernelTimer timer;  // optional per-kernel event timing (gw_timing_*)
 };
 
 namespace gw {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+KernelTimer*& current_timer() {
+  static thread_local KernelTimer* t = nullptr;
+  return t;
+}
 
 }  // namespace gw
 
@@ -167,7 +174,10 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
       maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
   const int threads = 128;
   dim3 grid(p->n_active, n_slices, (maxblk + threads - 1) / threads);
-  gw::k_gather_k_to_R<<<grid, threads, 0, st>>>(g);
+  {
+    gw::TimedLaunch tl_("k_gather_k_to_R", st);
+    gw::k_gather_k_to_R<<<grid, threads, 0, st>>>(g);
+  }
   return check_launch("k_gather_k_to_R");
 }
 
@@ -200,16 +210,22 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
       maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
   const int threads = 128;
   dim3 grid(p->h.n_atoms * p->h.n_atoms, n_slices, (maxblk + threads - 1) / threads);
-  gw::k_scatter_R_to_k<<<grid, threads, 0, st>>>(g);
+  {
+    gw::TimedLaunch tl_("k_scatter_R_to_k", st);
+    gw::k_scatter_R_to_k<<<grid, threads, 0, st>>>(g);
+  }
   return check_launch("k_scatter_R_to_k");
 }
 
 // Batched in-place inverse of `batch` dense N x N matrices (perm and status from the plan).
 gw_status launch_gj(gw_plan_s* p, double2* mats, int batch, long long N, cudaStream_t st) {
-  if (p->gj_blocked)
+  if (p->gj_blocked) {
+    gw::TimedLaunch tl_("k_gj_inverse_blocked", st);
     gw::k_gj_inverse_blocked<<<batch, 512, p->smem_GJ, st>>>(mats, p->d_perm, (int)N, N * N, p->d_status);
-  else
+  } else {
+    gw::TimedLaunch tl_("k_gj_inverse", st);
     gw::k_gj_inverse<<<batch, 512, p->smem_GJ, st>>>(mats, p->d_perm, (int)N, N * N, p->d_status);
+  }
   return check_launch("k_gj_inverse");
 }
 
@@ -311,10 +327,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
         if (hh.nu_idx[l] == -hh.nu_idx[j]) numirror.push_back(l);
   }
   {
-    // tensor-core inverse: N a multiple of 128 and the FP32 panel in shared memory
+    // tensor-core inverse: N a multiple of 128, at most 384 (the bound under which the
+    // FP32 level accumulators of the residual are exact)
     const size_t n = (size_t)hh.n_pb_total();
-    p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 &&
-                  (2 * n * gw::kGJB + n) * sizeof(float2) <= 220 * 1024;
+    p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 && n <= (size_t)gw::kWNmax;
   }
   p->device = opt ? opt->device : 0;
   if (p->host_only) {
@@ -416,6 +432,7 @@ gw_status gw_plan_destroy(gw_plan_t p) {
   if (!p) return GW_OK;
   if (!p->host_only) {
     DeviceGuard guard(p->device);
+    p->timer.release();
     free_device(p);
   }
   delete p;
@@ -478,6 +495,7 @@ gw_status gw_fourier_k_to_R(gw_plan_t p, gw_block kind, int n_slices, const void
   if (st != GW_OK) return st;
   if (!F_k || !F_R || n_slices <= 0) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const long long N = dense_n(p, kind);
   return launch_gather(p, kind, n_slices, (const double2*)F_k, (long long)n_slices * N * N, N * N, nullptr, 0, 0,
                        (double2*)F_R, n_slices, 0, 1.0 / p->h.n_k, S(stream));
@@ -493,6 +511,7 @@ gw_status gw_fourier_R_to_k(gw_plan_t p, gw_block kind, int n_slices, const void
   if (st != GW_OK) return st;
   if (!F_k || !F_R || n_slices <= 0) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const long long N = dense_n(p, kind);
   return launch_scatter(p, kind, n_slices, (const double2*)F_R, n_slices, 0, (double2*)F_k,
                         (long long)n_slices * N * N, N * N, S(stream));
@@ -504,6 +523,7 @@ gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, 
   if (st != GW_OK) return st;
   if (!in || !out) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   gw::TransformArgs g{};
   g.ent = p->d_ent;
@@ -526,7 +546,10 @@ gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, 
       maxblk = std::max(maxblk, g.pb ? h.n_prod[s] * h.n_prod[t] : h.n_orb[s] * h.n_orb[t]);
   dim3 grid(h.n_entries(), (maxblk + 31) / 32);
   dim3 block(32, 8);
-  gw::k_transform<<<grid, block, (size_t)g.n_in * 32 * sizeof(double2), S(stream)>>>(g);
+  {
+    gw::TimedLaunch tl_("k_transform", S(stream));
+    gw::k_transform<<<grid, block, (size_t)g.n_in * 32 * sizeof(double2), S(stream)>>>(g);
+  }
   return check_launch("k_transform");
 }
 
@@ -535,6 +558,7 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   if (st != GW_OK) return st;
   if (!G_R || !P_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   if (prec == GW_MIXED)
     return gw::mixed_polarizability(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (double2*)P_R, p->d_status,
@@ -550,7 +574,10 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   g.mirror_tau = h.c_symmetric;
   const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
   dim3 grid(h.n_entries(), nt_eff);
-  gw::k_polarizability_fp64<<<grid, 256, p->smem_P, S(stream)>>>(g);
+  {
+    gw::TimedLaunch tl_("k_polarizability_fp64", S(stream));
+    gw::k_polarizability_fp64<<<grid, 256, p->smem_P, S(stream)>>>(g);
+  }
   return check_launch("k_polarizability_fp64");
 }
 
@@ -560,6 +587,7 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
   if (st != GW_OK) return st;
   if (!G_R || !Wt_R || !Sig_R) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   if (prec == GW_MIXED) {
     st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
@@ -579,7 +607,10 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
     g.out_n_slices = h.n_tau;
     g.sign = -1.0;
     dim3 grid(h.n_entries(), h.n_tau);
-    gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    {
+      gw::TimedLaunch tl_("k_self_energy_fp64", S(stream));
+      gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    }
     if ((st = check_launch("k_self_energy_fp64")) != GW_OK) return st;
   } else {
     set_last_error("unknown precision");
@@ -600,7 +631,10 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
     g.out_n_slices = 1;
     g.sign = +1.0;
     dim3 grid(h.n_entries(), 1);
-    gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    {
+      gw::TimedLaunch tl_("k_self_energy_fp64", S(stream));
+      gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    }
     if ((st = check_launch("k_self_energy_fp64 (exchange)")) != GW_OK) return st;
   }
   return GW_OK;
@@ -611,6 +645,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
   if (st != GW_OK) return st;
   if (!P_R_iw || !v_q || !Wt_R_iw) { set_last_error("bad argument"); return GW_ERR_ARG; }
   DeviceGuard guard(p->device);
+  gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   cudaStream_t s = S(stream);
   const long long N = h.n_pb_total();
@@ -620,7 +655,10 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
   // v(q)^{-1} for the solved momenta
   {
     dim3 g((unsigned)std::min<long long>((NN + 255) / 256, 1024), (unsigned)nq);
-    gw::k_copy_mats<<<g, 256, 0, s>>>(v, p->d_qh, p->d_wsV, NN);
+    {
+      gw::TimedLaunch tl_("k_copy_mats", s);
+      gw::k_copy_mats<<<g, 256, 0, s>>>(v, p->d_qh, p->d_wsV, NN);
+    }
     if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
     if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsV, nq, N, s);
     else st = launch_gj(p, p->d_wsV, nq, N, s);
@@ -646,7 +684,10 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
   }
   if (p->w_sym && p->n_neg > 0) {
     dim3 g((unsigned)h.n_entries(), (unsigned)p->n_neg);
-    gw::k_mirror_nu<<<g, 256, 0, s>>>(p->d_ent, p->d_numirror, p->n_neg, h.n_nu, (double2*)Wt_R_iw);
+    {
+      gw::TimedLaunch tl_("k_mirror_nu", s);
+      gw::k_mirror_nu<<<g, 256, 0, s>>>(p->d_ent, p->d_numirror, p->n_neg, h.n_nu, (double2*)Wt_R_iw);
+    }
     if ((st = check_launch("k_mirror_nu")) != GW_OK) return st;
   }
   return GW_OK;
@@ -667,6 +708,38 @@ gw_status gw_sync(gw_plan_t p, void* stream) {
     }
     set_last_error("zero pivot in the W solve");
     return GW_ERR_SINGULAR;
+  }
+  return GW_OK;
+}
+
+gw_status gw_timing_enable(gw_plan_t p, int enable) {
+  if (!p) { set_last_error("null plan"); return GW_ERR_ARG; }
+  p->timer.on = enable != 0;
+  return GW_OK;
+}
+
+gw_status gw_timing_read(gw_plan_t p, int index, const char** name, double* total_ms, long long* launches) {
+  if (!p || index < 0) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  if (!p->host_only) {
+    DeviceGuard guard(p->device);
+    cudaError_t e = p->timer.collect();
+    if (e != cudaSuccess) return cuda_fail(e, "gw_timing_read");
+  }
+  if (index >= (int)p->timer.totals.size()) { set_last_error("no such timing entry"); return GW_ERR_ARG; }
+  const gw::KernelTimer::Total& t = p->timer.totals[(size_t)index];
+  if (name) *name = t.name.c_str();
+  if (total_ms) *total_ms = t.ms;
+  if (launches) *launches = t.launches;
+  return GW_OK;
+}
+
+gw_status gw_timing_reset(gw_plan_t p) {
+  if (!p) { set_last_error("null plan"); return GW_ERR_ARG; }
+  if (!p->host_only) {
+    DeviceGuard guard(p->device);
+    p->timer.reset();
+  } else {
+    p->timer.totals.clear();
   }
   return GW_OK;
 }

@@ -7,6 +7,7 @@
 #include "kernels.h"
 #include "smem_limit.h"
 #include "mixed.h"
+#include "ktimer.h"
 
 namespace gw {
 
@@ -209,7 +210,10 @@ gw_status mixed_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* 
   if (m.tc_ready) return tc_polarizability(m, h, d_ent, G_R, P_R, d_status, st);
   const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
   dim3 grid(h.n_entries(), nt_eff);
-  k_polarizability_f32<<<grid, 256, m.smem_P, st>>>(d_ent, m.d_Cf, G_R, P_R, h.n_tau, h.spin, h.c_symmetric);
+  {
+    gw::TimedLaunch tl_("k_polarizability_f32", st);
+    k_polarizability_f32<<<grid, 256, m.smem_P, st>>>(d_ent, m.d_Cf, G_R, P_R, h.n_tau, h.spin, h.c_symmetric);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_last_error(std::string("k_polarizability_f32: ") + cudaGetErrorString(e)); return GW_ERR_CUDA; }
   return GW_OK;
@@ -220,7 +224,10 @@ gw_status mixed_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_e
   if (!m.ready) { set_last_error("mixed path not initialised"); return GW_ERR_ARG; }
   if (m.tc_s_ready) return tc_self_energy(m, h, d_ent, G_R, Wt_R, Sig_R, d_status, st);
   dim3 grid(h.n_entries(), h.n_tau);
-  k_self_energy_f32<<<grid, 256, m.smem_S, st>>>(d_ent, m.d_Cf, G_R, Wt_R, Sig_R, h.n_tau);
+  {
+    gw::TimedLaunch tl_("k_self_energy_f32", st);
+    k_self_energy_f32<<<grid, 256, m.smem_S, st>>>(d_ent, m.d_Cf, G_R, Wt_R, Sig_R, h.n_tau);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_last_error(std::string("k_self_energy_f32: ") + cudaGetErrorString(e)); return GW_ERR_CUDA; }
   return GW_OK;

@@ -16,6 +16,7 @@
 #include "kernels.h"
 #include "smem_limit.h"
 #include "mixed.h"
+#include "ktimer.h"
 #include "umma.h"
 
 namespace gw {
@@ -538,8 +539,11 @@ gw_status tc_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent,
                          const double2* Wt_R, double2* Sig_R, int* d_status, cudaStream_t st) {
   const int per = 4;
   dim3 grid(h.n_entries(), (h.n_tau + per - 1) / per);
-  k_self_energy_tc<<<grid, 256, m.smem_tc_s, st>>>(d_ent, m.d_Cf, m.d_BsplitT, m.d_BsplitT_off, m.d_species, G_R,
-                                                   Wt_R, Sig_R, h.n_tau, per, d_status);
+  {
+    gw::TimedLaunch tl_("k_self_energy_tc", st);
+    k_self_energy_tc<<<grid, 256, m.smem_tc_s, st>>>(d_ent, m.d_Cf, m.d_BsplitT, m.d_BsplitT_off, m.d_species, G_R,
+                                                     Wt_R, Sig_R, h.n_tau, per, d_status);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(std::string("k_self_energy_tc: ") + cudaGetErrorString(e));
@@ -568,8 +572,11 @@ gw_status tc_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* d_e
   const int n_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
   const int per = 4;
   dim3 grid(h.n_entries(), (n_eff + per - 1) / per);
-  k_polarizability_tc<<<grid, 256, m.smem_tc, st>>>(d_ent, m.d_Cf, m.d_Bsplit, m.d_Bsplit_off, m.d_species, G_R, P_R,
-                                                    h.n_tau, n_eff, per, h.spin, h.c_symmetric, d_status);
+  {
+    gw::TimedLaunch tl_("k_polarizability_tc", st);
+    k_polarizability_tc<<<grid, 256, m.smem_tc, st>>>(d_ent, m.d_Cf, m.d_Bsplit, m.d_Bsplit_off, m.d_species, G_R, P_R,
+                                                      h.n_tau, n_eff, per, h.spin, h.c_symmetric, d_status);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(std::string("k_polarizability_tc: ") + cudaGetErrorString(e));

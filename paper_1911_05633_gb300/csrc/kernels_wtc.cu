@@ -3,12 +3,13 @@
 // residual I - A X evaluated to FP64 accuracy on tcgen05 from exact BF16 slices of A
 // and X (an Ozaki-type splitting): after a power-of-two scaling per row of A and per
 // column of X, every entry is a sum of slices a_s = alpha_s 2^-7(s+1), |alpha_s| <= 128,
-// each exact in BF16.  The products a_s x_t with s + t = L are multiples of 2^-7(L+2)
-// whose sums over K = N <= 384 terms stay below 2^24 units in these accumulators:
-// levels 0, 1, 2 (Re: ArXr - AiXi, Im: ArXi + AiXr together), level 3 (one product
-// type per accumulator); levels >= 4 share one FP32 accumulator whose rounding stays
-// at 2^-52 kappa of |A||X|.  The epilogue adds the levels in FP64.  Two refinements
-// take the FP32 inverse (error ~ kappa 1e-7) to ~1e-12 for kappa ~ 2e3.
+// each exact in BF16.  The products a_s x_t with s + t = L are multiples of 2^-7(L+2).
+// For K = N <= 384 terms their sums stay below 2^24 such units in these accumulators,
+// so FP32 accumulation is exact: levels 0, 1, 2 (Re: ArXr - AiXi, Im: ArXi + AiXr
+// together), levels 3 and 4 (one product type per accumulator).  The levels >= 5 share
+// one FP32 accumulator, whose rounding is ~2^-60 N of |A||X|.  The epilogue adds the
+// levels in FP64, level 0 first against the identity.  Two refinements take the FP32
+// inverse (error ~ kappa 1e-7) to ~1e-13 for kappa ~ 2e3.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -16,6 +17,7 @@
 #include "smem_limit.h"
 #include "umma.h"
 #include "wtc.h"
+#include "ktimer.h"
 
 namespace gw {
 
@@ -169,12 +171,6 @@ using namespace umma;
 
 constexpr uint64_t kWaitNs = 500ull * 1000ull * 1000ull;
 
-__device__ __forceinline__ uint16_t bf16_bits(double v) {
-  // v is exactly representable in BF16 (<= 8 significant bits): take the top half of its FP32 form
-  const float f = (float)v;
-  return (uint16_t)(__float_as_uint(f) >> 16);
-}
-
 // scale exponent e with max |x| < 2^e (0 for an all-zero row / column)
 __device__ __forceinline__ int scale_exponent(double m) { return m > 0.0 ? ilogb(m) + 1 : 0; }
 
@@ -212,69 +208,175 @@ __global__ void k_col_exponent(const T* __restrict__ X, int* __restrict__ eX, in
   eX[(long long)b * N + j] = scale_exponent(m);
 }
 
-// A operand slices: element (i, k) of matrix b -> kWSA slices of Re and Im in the
-// K-major tile layout, one contiguous chunk per (matrix, 128-row block, 16-column step).
+// Signed base-2^7 digits of one scaled entry: m = round(v 2^56) for |v| < 1, then
+// digit s = round(m / 2^(49 - 7 s)) taken from the top, so that v = sum_s d_s 2^-7(s+1)
+// up to 2^-57 with |d_0| <= 128 and |d_s| <= 64 after it; every d_s 2^-7(s+1) is exact
+// in BF16 (at most 8 significant bits).  Integer arithmetic only after one FP64 scaling.
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  // x 2^(56 - e) with |x| < 2^e; the power of two is built from its exponent bits
+  const double p = __longlong_as_double((long long)(1023 + 56 - e) << 52);
+  return __double2ll_rn(x * p);
+}
+__device__ __forceinline__ int next_digit(long long& m, int s) {
+  const int sh = 49 - 7 * s;
+  const long long d = sh > 0 ? (m + (1ll << (sh - 1))) >> sh : m;
+  m -= d << sh;
+  return (int)d;
+}
+// bits of d 2^-7(s+1) in BF16 (exact)
+__device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
+  const float sc = __int_as_float((127 - 7 * (s + 1)) << 23);
+  return __float_as_uint((float)d * sc) >> 16;
+}
+
+// A operand slices.  Element (i, k) of matrix b -> kWSA digits of Re and Im in the
+// K-major tile layout, one contiguous chunk per (matrix, 128-row block, 16-column step)
+// holding 2 kWSA planes of 128 x 16.  One thread per (row i, 8 consecutive k): it reads
+// 128 contiguous bytes and writes one 16-byte row of a core matrix per plane; the 32
+// lanes of a warp (i % 8, k half, (i / 8) % 2) fill 512 contiguous bytes of each plane.
 __global__ void k_slice_A(const double2* __restrict__ A, const int* __restrict__ eA, uint16_t* __restrict__ Asl,
                           int N, long long n_total) {
   const int NKS = N / 16, NIB = N / 128;
-  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_total; x += (long long)gridDim.x * blockDim.x) {
-    const long long b = x / ((long long)N * N);
-    const int r = (int)(x - b * N * N);
-    const int i = r / N, k = r - (r / N) * N;
-    const double2 z = A[x];
+  const long long n_thr = n_total / 8;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;  // (b, ib, ks, row group pair)
+    const int gp = (int)(w % 8); w /= 8;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int ib = (int)(w % NIB);
+    const long long b = w / NIB;
+    const int h = (lane >> 3) & 1;
+    const int il = (lane & 7) + 8 * ((lane >> 4) + 2 * gp);  // row within the 128-row block
+    const int i = ib * 128 + il;
+    const int k0 = ks * 16 + 8 * h;
     const int e = eA[b * N + i];
-    const long long chunk = ((b * NIB + i / 128) * NKS + k / 16) * (long long)(kWAChunk / 2);
-    const uint32_t off = kmajor_offset(128, i & 127, k & 15) / 2;
-    double v[2] = {ldexp(z.x, -e), ldexp(z.y, -e)};
-    for (int c = 0; c < 2; ++c) {
-      double rres = v[c];
-      for (int s = 0; s < kWSA; ++s) {
-        const double sc = ldexp(1.0, 7 * (s + 1));
-        const double a = rint(rres * sc) / sc;  // alpha_s 2^-7(s+1)
-        rres -= a;
-        Asl[chunk + (long long)(s * 2 + c) * (128 * 16) + off] = bf16_bits(a);
+    const double2* src = A + (b * N + i) * (long long)N + k0;
+    long long mr[8], mi[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 z = src[u];
+      mr[u] = fixed56(z.x, e);
+      mi[u] = fixed56(z.y, e);
+    }
+    uint16_t* chunk = Asl + ((b * NIB + ib) * NKS + ks) * (long long)(kWAChunk / 2);
+    const uint32_t off = kmajor_offset(128, il, 8 * h) / 2;
+#pragma unroll
+    for (int s = 0; s < kWSA; ++s) {
+      uint32_t pr[4], pi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t r0 = digit_bf16(next_digit(mr[2 * u], s), s), r1 = digit_bf16(next_digit(mr[2 * u + 1], s), s);
+        const uint32_t i0 = digit_bf16(next_digit(mi[2 * u], s), s), i1 = digit_bf16(next_digit(mi[2 * u + 1], s), s);
+        pr[u] = r0 | (r1 << 16);
+        pi[u] = i0 | (i1 << 16);
       }
+      *reinterpret_cast<uint4*>(chunk + (s * 2 + 0) * (128 * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (s * 2 + 1) * (128 * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
     }
   }
 }
 
-// X operand slices: element X[k][j] of matrix b (k = reduction index) -> SX slices of
+// X operand slices.  Element X[k][j] of matrix b (k = reduction index) -> SX digits of
 // Re and Im in the K-major layout of the B operand (rows j), one chunk per (matrix,
-// kWTN-column block, 16-row step).
+// kWTN-column block, 16-row step).  One thread per (column j, 8 consecutive k); lanes
+// (j % 8, k half, (j / 8) % 2) read 128-byte row segments and fill 512 contiguous bytes
+// of each plane.
 template <typename T, int SX>
 __global__ void k_slice_X(const T* __restrict__ X, const int* __restrict__ eX, uint16_t* __restrict__ Xsl, int N,
                           long long n_total) {
+  static_assert(kWTN == 32, "two 16-column halves per column block");
   const int NKS = N / 16, NJB = N / kWTN;
-  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_total; x += (long long)gridDim.x * blockDim.x) {
-    const long long b = x / ((long long)N * N);
-    const int r = (int)(x - b * N * N);
-    const int k = r / N, j = r - (r / N) * N;
-    const T z = X[x];
+  const long long n_thr = n_total / 8;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;  // (b, jb, ks, column half)
+    const int jh = (int)(w & 1); w >>= 1;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int jb = (int)(w % NJB);
+    const long long b = w / NJB;
+    const int h = (lane >> 3) & 1;
+    const int jl = (lane & 7) + 8 * ((lane >> 4) + 2 * jh);  // column within the block
+    const int j = jb * kWTN + jl;
+    const int k0 = ks * 16 + 8 * h;
     const int e = eX[b * N + j];
-    const long long chunk = ((b * NJB + j / kWTN) * NKS + k / 16) * (long long)(wx_chunk(SX) / 2);
-    const uint32_t off = kmajor_offset(kWTN, j % kWTN, k & 15) / 2;
-    double v[2] = {ldexp((double)z.x, -e), ldexp((double)z.y, -e)};
-    for (int c = 0; c < 2; ++c) {
-      double rres = v[c];
-      for (int t = 0; t < SX; ++t) {
-        const double sc = ldexp(1.0, 7 * (t + 1));
-        const double a = rint(rres * sc) / sc;
-        rres -= a;
-        Xsl[chunk + (long long)(t * 2 + c) * (kWTN * 16) + off] = bf16_bits(a);
+    const T* src = X + (b * N + k0) * (long long)N + j;
+    long long mr[8], mi[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T z = src[(long long)u * N];
+      mr[u] = fixed56((double)z.x, e);
+      mi[u] = fixed56((double)z.y, e);
+    }
+    uint16_t* chunk = Xsl + ((b * NJB + jb) * NKS + ks) * (long long)(wx_chunk(SX) / 2);
+    const uint32_t off = kmajor_offset(kWTN, jl, 8 * h) / 2;
+#pragma unroll
+    for (int t = 0; t < SX; ++t) {
+      uint32_t pr[4], pi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t r0 = digit_bf16(next_digit(mr[2 * u], t), t), r1 = digit_bf16(next_digit(mr[2 * u + 1], t), t);
+        const uint32_t i0 = digit_bf16(next_digit(mi[2 * u], t), t), i1 = digit_bf16(next_digit(mi[2 * u + 1], t), t);
+        pr[u] = r0 | (r1 << 16);
+        pi[u] = i0 | (i1 << 16);
+      }
+      *reinterpret_cast<uint4*>(chunk + (t * 2 + 0) * (kWTN * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (t * 2 + 1) * (kWTN * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+    }
+  }
+}
+
+// Accumulator (columns q kWTN) of the products a_s x_t, s + t = L: Re 0..7, Im 8..15;
+// `neg` selects Ai Xi (subtracted from Re), `imag` the Im products.
+__host__ __device__ constexpr int ozaki_bucket(int L, bool second_type, bool imag) {
+  return (imag ? 8 : 0) + (L <= 2 ? L : L == 3 ? (second_type ? 4 : 3) : L == 4 ? (second_type ? 6 : 5) : 7);
+}
+
+// The 4 x (number of (s, t) pairs) MMAs of one 16-wide K step.  Fully unrolled, so the
+// accumulator indices, shared-memory offsets and first-use flags are constants.
+template <int SX, int LMAX, bool FIRST>
+__device__ __forceinline__ void ozaki_issue_step(uint32_t tm, uint64_t da0, uint64_t dx0, uint32_t id, uint32_t idn) {
+  constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;  // bytes per A / X plane
+  uint32_t used = 0;
+#pragma unroll
+  for (int t = 0; t < SX; ++t) {
+#pragma unroll
+    for (int s = 0; s < kWSA; ++s) {
+      if (s + t <= LMAX) {
+        const int L = s + t;
+        const int r1 = ozaki_bucket(L, false, false), r2 = ozaki_bucket(L, true, false);
+        const int i1 = ozaki_bucket(L, false, true), i2 = ozaki_bucket(L, true, true);
+        // descriptor start addresses are in 16-byte units in the low bits
+        const uint64_t dar = da0 + (uint64_t)(((s * 2 + 0) * PA) >> 4);
+        const uint64_t dai = da0 + (uint64_t)(((s * 2 + 1) * PA) >> 4);
+        const uint64_t dxr = dx0 + (uint64_t)(((t * 2 + 0) * PX) >> 4);
+        const uint64_t dxi = dx0 + (uint64_t)(((t * 2 + 1) * PX) >> 4);
+        // Re += Ar Xr - Ai Xi ; Im += Ar Xi + Ai Xr
+        mma_bf16(tm + (uint32_t)r1 * kWTN, dar, dxr, id, FIRST ? (used >> r1) & 1u : 1u);
+        used |= 1u << r1;
+        mma_bf16(tm + (uint32_t)r2 * kWTN, dai, dxi, idn, FIRST ? (used >> r2) & 1u : 1u);
+        used |= 1u << r2;
+        mma_bf16(tm + (uint32_t)i1 * kWTN, dar, dxi, id, FIRST ? (used >> i1) & 1u : 1u);
+        used |= 1u << i1;
+        mma_bf16(tm + (uint32_t)i2 * kWTN, dai, dxr, id, FIRST ? (used >> i2) & 1u : 1u);
+        used |= 1u << i2;
       }
     }
   }
 }
 
-// R[b] = I - A[b] X[b] for one 128 x kWTN output tile per block (128 threads).  Twelve
-// FP32 accumulators of kWTN columns in tensor memory: for Re and Im, the levels 0, 1, 2
-// (both product types), level 3 (one accumulator per product type) and levels >= 4.
-template <int SX>
+// R[b] = I - A[b] X[b] for one 128 x kWTN output tile per block (128 threads), from the
+// A slices s <= LMAX and SX slices of X, products with s + t <= LMAX.  Sixteen FP32
+// accumulators of kWTN columns fill the 512 tensor-memory columns: for Re and Im, the
+// levels 0, 1, 2 (both product types together), levels 3 and 4 (one accumulator per
+// product type) and the levels >= 5.  Two shared-memory stages: while the products of
+// K step ks run, the stage of step ks - 1 is refilled with step ks + 1.
+template <int SX, int LMAX>
 __global__ void __launch_bounds__(128, 1)
 k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ Xsl, const int* __restrict__ eA,
                  const int* __restrict__ eX, double2* __restrict__ R, int N, int* status) {
+  static_assert(LMAX >= 5 && LMAX < kWSA, "every accumulator receives a product; A has kWSA slices");
   constexpr uint32_t XC = wx_chunk(SX);
-  constexpr uint32_t PX = kWTN * 16 * 2;  // bytes per X plane
+  constexpr uint32_t AC = wa_bytes(LMAX);  // the leading planes s <= LMAX of each A chunk
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t full[2];
@@ -300,52 +402,35 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
   const uint32_t tm = tmem_base;
   const unsigned char* Abase = reinterpret_cast<const unsigned char*>(Asl) + ((b * NIB + ib) * NKS) * (long long)kWAChunk;
   const unsigned char* Xbase = reinterpret_cast<const unsigned char*>(Xsl) + ((b * NJB + jb) * NKS) * (long long)XC;
-  unsigned char* stage[2] = {sm, sm + kWAChunk + XC};
+  unsigned char* const stage0 = sm;
+  unsigned char* const stage1 = sm + AC + XC;
   bool ok = true;
   if (tid == 0) {
     const uint32_t id = idesc_bf16_f32(128, kWTN), idn = idesc_bf16_f32_negA(128, kWTN);
+    const uint64_t da0 = smem_desc(smem_u32(stage0), 128, 256), da1 = smem_desc(smem_u32(stage1), 128, 256);
+    const uint64_t dx0 = smem_desc(smem_u32(stage0) + AC, 128, 256), dx1 = smem_desc(smem_u32(stage1) + AC, 128, 256);
     for (int s = 0; s < 2 && s < NKS; ++s) {
-      mbar_arrive_expect_tx(&full[s], kWAChunk + XC);
-      bulk_g2s(stage[s], Abase + (long long)s * kWAChunk, kWAChunk, &full[s]);
-      bulk_g2s(stage[s] + kWAChunk, Xbase + (long long)s * XC, XC, &full[s]);
+      unsigned char* const dst = s ? stage1 : stage0;
+      mbar_arrive_expect_tx(&full[s], AC + XC);
+      bulk_g2s(dst, Abase + (long long)s * kWAChunk, AC, &full[s]);
+      bulk_g2s(dst + AC, Xbase + (long long)s * XC, XC, &full[s]);
     }
-    uint32_t used = 0;  // accumulator initialised (bit per accumulator)
-    for (int ks = 0; ks < NKS && ok; ++ks) {
+    for (int ks = 0; ks < NKS; ++ks) {
       const int st = ks & 1;
-      const uint32_t par = (uint32_t)(ks >> 1) & 1u;
-      if (!mbar_wait(&full[st], par, kWaitNs, status)) { ok = false; break; }
+      if (!mbar_wait(&full[st], (uint32_t)(ks >> 1) & 1u, kWaitNs, status)) { ok = false; break; }
       fence_after_sync();
-      const uint32_t aB = smem_u32(stage[st]), xB = aB + kWAChunk;
-      for (int t = 0; t < SX; ++t) {
-        for (int s = 0; s < kWSA && s + t <= kWLmax; ++s) {
-          const int L = s + t;
-          // accumulators (columns q * kWTN): Re 0..5, Im 6..11
-          int r1, r2, i1, i2;
-          if (L <= 2) { r1 = r2 = L; i1 = i2 = 6 + L; }
-          else if (L == 3) { r1 = 3; r2 = 4; i1 = 9; i2 = 10; }
-          else { r1 = r2 = 5; i1 = i2 = 11; }
-          const uint64_t dar = smem_desc(aB + (uint32_t)(s * 2 + 0) * 4096u, 128, 256);
-          const uint64_t dai = smem_desc(aB + (uint32_t)(s * 2 + 1) * 4096u, 128, 256);
-          const uint64_t dxr = smem_desc(xB + (uint32_t)(t * 2 + 0) * PX, 128, 256);
-          const uint64_t dxi = smem_desc(xB + (uint32_t)(t * 2 + 1) * PX, 128, 256);
-          // Re += Ar Xr - Ai Xi ; Im += Ar Xi + Ai Xr
-          mma_bf16(tm + (uint32_t)r1 * kWTN, dar, dxr, id, (used >> r1) & 1u);
-          used |= 1u << r1;
-          mma_bf16(tm + (uint32_t)r2 * kWTN, dai, dxi, idn, (used >> r2) & 1u);
-          used |= 1u << r2;
-          mma_bf16(tm + (uint32_t)i1 * kWTN, dar, dxi, id, (used >> i1) & 1u);
-          used |= 1u << i1;
-          mma_bf16(tm + (uint32_t)i2 * kWTN, dai, dxr, id, (used >> i2) & 1u);
-          used |= 1u << i2;
-        }
-      }
+      const uint64_t da = st ? da1 : da0, dx = st ? dx1 : dx0;
+      if (ks == 0) ozaki_issue_step<SX, LMAX, true>(tm, da, dx, id, idn);
+      else ozaki_issue_step<SX, LMAX, false>(tm, da, dx, id, idn);
       mma_commit(&mmad[st]);
-      if (ks + 2 < NKS) {
-        // refill this stage once its products are done
-        if (!mbar_wait(&mmad[st], par, kWaitNs, status)) { ok = false; break; }
-        mbar_arrive_expect_tx(&full[st], kWAChunk + XC);
-        bulk_g2s(stage[st], Abase + (long long)(ks + 2) * kWAChunk, kWAChunk, &full[st]);
-        bulk_g2s(stage[st] + kWAChunk, Xbase + (long long)(ks + 2) * XC, XC, &full[st]);
+      if (ks >= 1 && ks + 1 < NKS) {
+        // the products of step ks - 1 are done once its commit arrives: refill its stage
+        const int so = st ^ 1;
+        if (!mbar_wait(&mmad[so], (uint32_t)((ks - 1) >> 1) & 1u, kWaitNs, status)) { ok = false; break; }
+        unsigned char* const dst = so ? stage1 : stage0;
+        mbar_arrive_expect_tx(&full[so], AC + XC);
+        bulk_g2s(dst, Abase + (long long)(ks + 1) * kWAChunk, AC, &full[so]);
+        bulk_g2s(dst + AC, Xbase + (long long)(ks + 1) * XC, XC, &full[so]);
       }
     }
   }
@@ -361,20 +446,32 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
     const int i = ib * 128 + r;
     const int ea = eA[b * N + i];
     double2* Ro = R + (b * N + i) * (long long)N;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     for (int c0 = 0; c0 < kWTN; c0 += 16) {
-      float v[12][16];
+      // level 0 exactly against the identity, then the smaller levels added from the bottom
+      double re[16], im[16];
+      float v[16];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)(q * kWTN + c0), v[q]);
+      for (int c = 0; c < 16; ++c) { re[c] = 0.0; im[c] = 0.0; }
+#pragma unroll 1
+      for (int q = 7; q >= 1; --q) {
+        tmem_ld16(tm + lane_base + (uint32_t)(q * kWTN + c0), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) re[c] += (double)v[c];
+        tmem_ld16(tm + lane_base + (uint32_t)((8 + q) * kWTN + c0), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) im[c] += (double)v[c];
+      }
+      float v0r[16], v0i[16];
+      tmem_ld16(tm + lane_base + (uint32_t)c0, v0r);
+      tmem_ld16(tm + lane_base + (uint32_t)(8 * kWTN + c0), v0i);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int j = jb * kWTN + c0 + c;
         const double sc = ldexp(1.0, ea + eX[b * N + j]);
-        double re = 0.0, im = 0.0;
-#pragma unroll
-        for (int q = 5; q >= 0; --q) re += (double)v[q][c];
-#pragma unroll
-        for (int q = 11; q >= 6; --q) im += (double)v[q][c];
-        Ro[j] = make_double2((i == j ? 1.0 : 0.0) - sc * re, -sc * im);
+        const double r0 = (i == j ? 1.0 : 0.0) - sc * (double)v0r[c];
+        const double i0 = -sc * (double)v0i[c];
+        Ro[j] = make_double2(r0 - sc * re[c], i0 - sc * im[c]);
       }
     }
   }
@@ -436,8 +533,8 @@ k_refine_update(const T* __restrict__ X0, const double2* __restrict__ R, double2
 
 cudaError_t wtc_setup(size_t smem_gj32) {
   cudaError_t e = raise_smem_limit(k_gj_inverse_blocked_f32, smem_gj32);
-  if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX0>, w_residual_smem(kWSX0));
-  if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX1>, w_residual_smem(kWSX1));
+  if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX0, kWL0>, w_residual_smem(kWSX0, kWL0));
+  if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX1, kWLmax>, w_residual_smem(kWSX1, kWLmax));
   return e;
 }
 
@@ -445,25 +542,65 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
   const long long NN = (long long)N * N;
   const long long tot = (long long)batch * NN;
   const unsigned g1 = (unsigned)((tot + 255) / 256 < 65535LL * 8 ? (tot + 255) / 256 : 65535LL * 8);
+  const long long t8 = tot / 8;  // slicing threads: one per 8 consecutive elements
+  const unsigned g8 = (unsigned)((t8 + 255) / 256 < 65535LL * 8 ? (t8 + 255) / 256 : 65535LL * 8);
   const dim3 gcol((unsigned)((N + 127) / 128), (unsigned)batch);
   const dim3 gres((unsigned)(N / kWTN), (unsigned)(N / 128), (unsigned)batch);
   const dim3 gupd((unsigned)(N / 64), (unsigned)(N / 64), (unsigned)batch);
   // X0: FP32 Gauss-Jordan
-  k_to_f32<<<g1, 256, 0, st>>>(mats, w.X32, tot);
-  k_gj_inverse_blocked_f32<<<batch, 512, smem_gj32, st>>>(w.X32, w.perm, N, NN, w.status);
+  {
+    gw::TimedLaunch tl_("k_to_f32", st);
+    k_to_f32<<<g1, 256, 0, st>>>(mats, w.X32, tot);
+  }
+  {
+    gw::TimedLaunch tl_("k_gj_inverse_blocked_f32", st);
+    k_gj_inverse_blocked_f32<<<batch, 512, smem_gj32, st>>>(w.X32, w.perm, N, NN, w.status);
+  }
   // slices of A (kept for both residuals)
-  k_row_exponent<<<(unsigned)((batch * (long long)N + 7) / 8), 256, 0, st>>>(mats, w.eA, N, batch);
-  k_slice_A<<<g1, 256, 0, st>>>(mats, w.eA, w.Asl, N, tot);
+  {
+    gw::TimedLaunch tl_("k_row_exponent", st);
+    k_row_exponent<<<(unsigned)((batch * (long long)N + 7) / 8), 256, 0, st>>>(mats, w.eA, N, batch);
+  }
+  {
+    gw::TimedLaunch tl_("k_slice_A", st);
+    k_slice_A<<<g8, 256, 0, st>>>(mats, w.eA, w.Asl, N, tot);
+  }
   // X1 = X0 + X0 (I - A X0)
-  k_col_exponent<float2><<<gcol, 128, 0, st>>>(w.X32, w.eX, N);
-  k_slice_X<float2, kWSX0><<<g1, 256, 0, st>>>(w.X32, w.eX, w.Xsl, N, tot);
-  k_ozaki_residual<kWSX0><<<gres, 128, w_residual_smem(kWSX0), st>>>(w.Asl, w.Xsl, w.eA, w.eX, w.R, N, w.status);
-  k_refine_update<float2><<<gupd, 256, 0, st>>>(w.X32, w.R, w.X1, N);
+  {
+    gw::TimedLaunch tl_("k_col_exponent", st);
+    k_col_exponent<float2><<<gcol, 128, 0, st>>>(w.X32, w.eX, N);
+  }
+  {
+    gw::TimedLaunch tl_("k_slice_X<float2>", st);
+    k_slice_X<float2, kWSX0><<<g8, 256, 0, st>>>(w.X32, w.eX, w.Xsl, N, tot);
+  }
+  {
+    gw::TimedLaunch tl_("k_ozaki_residual<first>", st);
+    k_ozaki_residual<kWSX0, kWL0><<<gres, 128, w_residual_smem(kWSX0, kWL0), st>>>(w.Asl, w.Xsl, w.eA, w.eX, w.R, N,
+                                                                                  w.status);
+  }
+  {
+    gw::TimedLaunch tl_("k_refine_update<float2>", st);
+    k_refine_update<float2><<<gupd, 256, 0, st>>>(w.X32, w.R, w.X1, N);
+  }
   // X2 = X1 + X1 (I - A X1), written over A
-  k_col_exponent<double2><<<gcol, 128, 0, st>>>(w.X1, w.eX, N);
-  k_slice_X<double2, kWSX1><<<g1, 256, 0, st>>>(w.X1, w.eX, w.Xsl, N, tot);
-  k_ozaki_residual<kWSX1><<<gres, 128, w_residual_smem(kWSX1), st>>>(w.Asl, w.Xsl, w.eA, w.eX, w.R, N, w.status);
-  k_refine_update<double2><<<gupd, 256, 0, st>>>(w.X1, w.R, mats, N);
+  {
+    gw::TimedLaunch tl_("k_col_exponent", st);
+    k_col_exponent<double2><<<gcol, 128, 0, st>>>(w.X1, w.eX, N);
+  }
+  {
+    gw::TimedLaunch tl_("k_slice_X<double2>", st);
+    k_slice_X<double2, kWSX1><<<g8, 256, 0, st>>>(w.X1, w.eX, w.Xsl, N, tot);
+  }
+  {
+    gw::TimedLaunch tl_("k_ozaki_residual<second>", st);
+    k_ozaki_residual<kWSX1, kWLmax><<<gres, 128, w_residual_smem(kWSX1, kWLmax), st>>>(w.Asl, w.Xsl, w.eA, w.eX, w.R,
+                                                                                      N, w.status);
+  }
+  {
+    gw::TimedLaunch tl_("k_refine_update<double2>", st);
+    k_refine_update<double2><<<gupd, 256, 0, st>>>(w.X1, w.R, mats, N);
+  }
 }
 
 }  // namespace gw

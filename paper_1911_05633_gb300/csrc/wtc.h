@@ -1,4 +1,4 @@
-// Tensor-core W inverse: FP32 Gauss-Jordan + one refinement with an exactly sliced
+// Tensor-core W inverse: FP32 Gauss-Jordan + two refinements with an exactly sliced
 // (BF16) residual on tcgen05.  Kernels in kernels_wtc.cu.
 #pragma once
 
@@ -8,13 +8,21 @@
 namespace gw {
 
 constexpr int kWSA = 8;      // slices of the FP64 matrix (7 bits each)
-constexpr int kWSX0 = 6;     // slices of the FP32 first inverse
+constexpr int kWSX0 = 5;     // slices of the FP32 first inverse
+constexpr int kWL0 = 5;      // first residual: products a_s x_t with s + t <= kWL0
 constexpr int kWSX1 = 8;     // slices of the once-refined FP64 inverse
-constexpr int kWLmax = 7;    // products a_s x_t with s + t <= kWLmax
+constexpr int kWLmax = 7;    // second residual: products a_s x_t with s + t <= kWLmax
 constexpr int kWTN = 32;     // output columns per residual block
+constexpr int kWNmax = 384;  // largest N whose level sums stay exact in FP32
 constexpr uint32_t kWAChunk = kWSA * 2 * 128 * 16 * 2;  // bytes per (row block, K step)
+// bytes of the A planes s <= lmax (the leading part of a chunk)
+__host__ __device__ constexpr uint32_t wa_bytes(int lmax) {
+  return (uint32_t)((lmax + 1 < kWSA ? lmax + 1 : kWSA) * 2 * 128 * 16 * 2);
+}
 __host__ __device__ constexpr uint32_t wx_chunk(int SX) { return (uint32_t)SX * 2 * kWTN * 16 * 2; }
-__host__ __device__ constexpr size_t w_residual_smem(int SX) { return 2 * (size_t)(kWAChunk + wx_chunk(SX)); }
+__host__ __device__ constexpr size_t w_residual_smem(int SX, int lmax) {
+  return 2 * (size_t)(wa_bytes(lmax) + wx_chunk(SX));
+}
 
 __global__ void k_gj_inverse_blocked_f32(float2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
                                          int* status);

@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgw.so")
 
+GW_OK = 0
 GW_FP64, GW_MIXED = 0, 1
 GW_FERMION, GW_BOSON = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU = 0, 1
@@ -31,6 +32,7 @@ EXPORTED = [
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak",
+    "gw_timing_enable", "gw_timing_read", "gw_timing_reset",
 ]
 
 
@@ -97,6 +99,10 @@ def load_library(path: str = LIB_PATH):
     lib.gw_self_energy_tau.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, vp]
     lib.gw_fourier_R_to_k.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_sync.argtypes = [vp, vp]
+    lib.gw_timing_enable.argtypes = [vp, C.c_int]
+    lib.gw_timing_read.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_longlong)]
+    lib.gw_timing_reset.argtypes = [vp]
     lib.gw_fp_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.gw_status_string.argtypes = [C.c_int]
     lib.gw_status_string.restype = C.c_char_p
@@ -303,6 +309,23 @@ class Plan:
 
     def sync(self, stream=None):
         _check(self._lib.gw_sync(self._h, self._stream(stream)), "gw_sync")
+
+    # ---- per-kernel event timing -----------------------------------------------------
+    def timing_enable(self, on: bool = True):
+        _check(self._lib.gw_timing_enable(self._h, 1 if on else 0), "gw_timing_enable")
+
+    def timing_reset(self):
+        _check(self._lib.gw_timing_reset(self._h), "gw_timing_reset")
+
+    def timing_read(self) -> dict:
+        """{kernel name: (total device ms, launches)} since the last reset."""
+        out = {}
+        name, ms, n = C.c_char_p(), C.c_double(), C.c_longlong()
+        i = 0
+        while self._lib.gw_timing_read(self._h, i, C.byref(name), C.byref(ms), C.byref(n)) == GW_OK:
+            out[name.value.decode()] = (ms.value, n.value)
+            i += 1
+        return out
 
     # ---- ragged layout helpers (host side) ------------------------------------------
     def block_shape(self, e: int, kind: str):

@@ -54,8 +54,9 @@ class Sys:
         from paper_1911_05633_gb300 import gw
         self.cell = cell
         self.plan = gw.Plan.from_cell(cell, **plan_kw)
-        # N_PB a multiple of 128 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
-        assert self.plan.info["w_tensor"] == int(cell.n_pb_total % 128 == 0 and plan_kw.get("w_solver") != "gauss_jordan")
+        # N_PB of 128, 256 or 384 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
+        n = cell.n_pb_total
+        assert self.plan.info["w_tensor"] == int(n % 128 == 0 and n <= 384 and plan_kw.get("w_solver") != "gauss_jordan")
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
         self.G_k = cell.green_k_tau()

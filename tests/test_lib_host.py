@@ -130,3 +130,21 @@ def test_w_solve_mode(gwlib):
     ns = synth.mixed_species_cell(symmetric_C=False, n_tau=10)
     p = gw.Plan.from_cell(ns, host_only=True)
     assert p.info["c_symmetric"] == 0 and p.info["w_symmetric"] == 0
+
+
+def test_w_solver_choice(gwlib):
+    """The tensor-core inverse is chosen for N_PB in {128, 256, 384} only (the range in
+    which its FP32 level sums are exact); Gauss-Jordan otherwise or when asked for."""
+    from paper_1911_05633_gb300 import gw
+    c1 = synth.make_config(1, build=False)
+    c1._draw_basis(np.random.default_rng(0))
+    assert c1.n_pb_total == 384
+    assert gw.Plan.from_cell(c1, host_only=True).info["w_tensor"] == 1
+    assert gw.Plan.from_cell(c1, host_only=True, w_solver="gauss_jordan").info["w_tensor"] == 0
+    c2 = synth.make_config(2, atoms=8, build=False)
+    c2._draw_basis(np.random.default_rng(0))
+    assert c2.n_pb_total == 512
+    assert gw.Plan.from_cell(c2, host_only=True).info["w_tensor"] == 0
+    mixed = synth.mixed_species_cell(n_tau=10)
+    assert mixed.n_pb_total % 128 != 0
+    assert gw.Plan.from_cell(mixed, host_only=True).info["w_tensor"] == 0
