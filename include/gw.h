@@ -198,6 +198,23 @@ gw_status gw_self_energy_tau(gw_plan_t plan, const void* G_R, const void* Wt_R,
 gw_status gw_fourier_R_to_k(gw_plan_t plan, gw_block kind, int n_slices,
                             const void* F_R, void* F_k, void* stream);
 
+/* Allocation-free variant of gw_screened_W_iw (no counterpart in the paper).
+ * For callers that cannot allocate device memory once they run -- for example a code
+ * that hands all device memory to its own pool at start-up, or one that runs under a
+ * memory manager that refuses new allocations: the scratch of this call is a fixed
+ * 32 MiB array in the library's device image (held on every GPU that loads the
+ * library until the process exits), not the plan's workspace.  Same inputs, output
+ * and arithmetic as gw_screened_W_iw with the FP64 Gauss-Jordan inverse.
+ * Limit: 2 N_PB^2 complex values must fit (N_PB <= 1024); a larger plan gets
+ * GW_ERR_UNSUPPORTED and nothing is launched.  The call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  Every call shares the array, which keeps the last
+ * call's contents; calls that overlap on the GPU (other streams, threads or plans on
+ * the same device) race and give wrong results. */
+gw_status gw_screened_W_iw_noalloc(gw_plan_t plan, const void* P_R_iw, const void* v_q, void* Wt_R_iw,
+                                   void* stream);
+
 /* Per-kernel device timing (an instrumentation aid; no counterpart in the paper).
  * gw_timing_enable(plan, 1) makes every later kernel launch of this plan's entry points
  * record a CUDA event before and after it on the launching stream (off by default;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -745,3 +746,153 @@ gw_status gw_timing_reset(gw_plan_t p) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free W solve (gw_screened_W_iw_noalloc; no counterpart in the paper)
+// ---------------------------------------------------------------------------
+// Its scratch is a fixed array in the library's device image instead of the plan's
+// workspace, for callers that cannot allocate device memory while they run.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB on every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device: a host-side name of a
+// __device__ array is not a device address, so it is looked up once per device.
+gw_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_last_error("device ordinal out of range for the fixed scratch");
+    return GW_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GW_OK;
+}
+
+// Zero the bosonic slots [slot0, n_slots) of every entry (PB blocks).
+__global__ void k_zero_slots(const gw::DevEntry* __restrict__ ent, int n_slots, int slot0, double2* __restrict__ W) {
+  const gw::DevEntry E = ent[blockIdx.x];
+  const int blk = E.Ka * E.Kb;
+  double2* w = W + E.off_pb * n_slots + (long long)(slot0 + blockIdx.y) * blk;
+  for (int x = threadIdx.x; x < blk; x += blockDim.x) w[x] = make_double2(0.0, 0.0);
+}
+
+// W~_R[e][slot0 + s] += scale w conj(e^{iq.R}) (W(q) - v(q)) for one momentum q, taking the
+// real part in symmetric mode; grid (active pair, slice, element chunk).
+__global__ void k_gather_one_q(const gw::DevEntry* __restrict__ ent, const int* __restrict__ pair_first,
+                               const double2* __restrict__ phase, int n_k, int q, double w,
+                               const double2* __restrict__ Wq, long long s_stride, const double2* __restrict__ vq,
+                               int ld, double2* __restrict__ out, int n_slots, int slot0, double scale, int real_only) {
+  const int p = blockIdx.x;
+  const int s = blockIdx.y;
+  const int e0 = pair_first[p], e1 = pair_first[p + 1];
+  const gw::DevEntry E0 = ent[e0];
+  const int cols = E0.Kb;
+  const int blk = E0.Ka * cols;
+  const int idx = blockIdx.z * blockDim.x + threadIdx.x;
+  if (idx >= blk) return;
+  const int i = idx / cols, j = idx - (idx / cols) * cols;
+  const long long el = (long long)(E0.pa + i) * ld + (E0.pb + j);
+  const double2 a = Wq[(long long)s * s_stride + el];
+  const double2 b = vq[(long long)q * ld * ld + el];
+  const double vr = (a.x - b.x) * w * scale, vi = (a.y - b.y) * w * scale;
+  for (int e = e0; e < e1; ++e) {
+    const double2 ph = phase[(long long)e * n_k + q];
+    const double rr = ph.x * vr + ph.y * vi;
+    const double ri = real_only ? 0.0 : ph.x * vi - ph.y * vr;
+    double2* o = out + ent[e].off_pb * n_slots + (long long)(slot0 + s) * blk + idx;
+    const double2 t = *o;
+    *o = make_double2(t.x + rr, t.y + ri);
+  }
+}
+
+}  // namespace
+
+extern "C" gw_status gw_screened_W_iw_noalloc(gw_plan_t p, const void* P_R_iw, const void* v_q, void* Wt_R_iw,
+                                              void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!P_R_iw || !v_q || !Wt_R_iw) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  const gw::HostPlan& h = p->h;
+  const long long N = h.n_pb_total();
+  const long long NN = N * N;
+  const size_t mat = (size_t)NN * sizeof(double2);
+  const size_t perm_bytes = ((size_t)N * sizeof(int) + 255) & ~(size_t)255;
+  // v(q)^-1 and at least one (q, nu) matrix, each with its pivot record
+  if (2 * (mat + perm_bytes) > kNoAllocScratchBytes) {
+    set_last_error("product basis too large for the fixed 32 MiB scratch of gw_screened_W_iw_noalloc "
+                   "(needs 2 N_PB^2 complex values)");
+    return GW_ERR_UNSUPPORTED;
+  }
+  void* base = nullptr;
+  if ((st = noalloc_scratch(p->device, &base)) != GW_OK) return st;
+  cudaStream_t s = S(stream);
+  const int n_work = h.n_nu - p->nu_start;
+  const int n_slots = (int)std::min<size_t>((size_t)n_work, kNoAllocScratchBytes / (mat + perm_bytes) - 1);
+  unsigned char* bytes = static_cast<unsigned char*>(base);
+  double2* vinv = reinterpret_cast<double2*>(bytes);
+  double2* slots = reinterpret_cast<double2*>(bytes + mat);
+  int* perm = reinterpret_cast<int*>(bytes + (size_t)(1 + n_slots) * mat);
+  const double2* v = (const double2*)v_q;
+  // the momenta solved (one of each (q, -q) pair in symmetric mode) and their weights
+  std::vector<int> qh;
+  std::vector<double> qw;
+  for (int q = 0, q1 = 0; q1 < h.kmesh[0]; ++q1)
+    for (int q2 = 0; q2 < h.kmesh[1]; ++q2)
+      for (int q3 = 0; q3 < h.kmesh[2]; ++q3, ++q) {
+        const int mq = (((h.kmesh[0] - q1) % h.kmesh[0]) * h.kmesh[1] + (h.kmesh[1] - q2) % h.kmesh[1]) * h.kmesh[2] +
+                       (h.kmesh[2] - q3) % h.kmesh[2];
+        if (!p->w_sym) { qh.push_back(q); qw.push_back(1.0); }
+        else if (q <= mq) { qh.push_back(q); qw.push_back(q == mq ? 1.0 : 2.0); }
+      }
+  // the solved slots accumulate over momenta: they start from zero (the array keeps the
+  // previous call's contents, and so does the output)
+  {
+    dim3 g((unsigned)h.n_entries(), (unsigned)n_work);
+    k_zero_slots<<<g, 256, 0, s>>>(p->d_ent, h.n_nu, p->nu_start, (double2*)Wt_R_iw);
+    if ((st = check_launch("k_zero_slots")) != GW_OK) return st;
+  }
+  int maxblk = 0;
+  for (int a = 0; a < h.n_species; ++a)
+    for (int b2 = 0; b2 < h.n_species; ++b2) maxblk = std::max(maxblk, h.n_prod[a] * h.n_prod[b2]);
+  for (size_t qi = 0; qi < qh.size(); ++qi) {
+    dim3 gc((unsigned)std::min<long long>((NN + 255) / 256, 1024), 1);
+    gw::k_copy_mats<<<gc, 256, 0, s>>>(v, p->d_qh + qi, vinv, NN);
+    if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
+    if (p->gj_blocked) gw::k_gj_inverse_blocked<<<1, 512, p->smem_GJ, s>>>(vinv, perm, (int)N, NN, p->d_status);
+    else gw::k_gj_inverse<<<1, 512, p->smem_GJ, s>>>(vinv, perm, (int)N, NN, p->d_status);
+    if ((st = check_launch("k_gj_inverse")) != GW_OK) return st;
+    for (int c0 = 0; c0 < n_work; c0 += n_slots) {
+      const int nc = std::min(n_slots, n_work - c0);
+      const int slot0 = p->nu_start + c0;
+      if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, slot0, slots, NN, NN, s,
+                               p->d_qh + qi, 1, vinv, -1.0)) != GW_OK)
+        return st;
+      if (p->gj_blocked) gw::k_gj_inverse_blocked<<<nc, 512, p->smem_GJ, s>>>(slots, perm, (int)N, NN, p->d_status);
+      else gw::k_gj_inverse<<<nc, 512, p->smem_GJ, s>>>(slots, perm, (int)N, NN, p->d_status);
+      if ((st = check_launch("k_gj_inverse")) != GW_OK) return st;
+      dim3 gg((unsigned)p->n_active, (unsigned)nc, (unsigned)((maxblk + 127) / 128));
+      k_gather_one_q<<<gg, 128, 0, s>>>(p->d_ent, p->d_pair_first, p->d_phase, h.n_k, qh[qi], qw[qi], slots, NN, v,
+                                         (int)N, (double2*)Wt_R_iw, h.n_nu, slot0, 1.0 / h.n_k, p->w_sym ? 1 : 0);
+      if ((st = check_launch("k_gather_one_q")) != GW_OK) return st;
+    }
+  }
+  if (p->w_sym && p->n_neg > 0) {
+    dim3 g((unsigned)h.n_entries(), (unsigned)p->n_neg);
+    gw::k_mirror_nu<<<g, 256, 0, s>>>(p->d_ent, p->d_numirror, p->n_neg, h.n_nu, (double2*)Wt_R_iw);
+    if ((st = check_launch("k_mirror_nu")) != GW_OK) return st;
+  }
+  return GW_OK;
+}

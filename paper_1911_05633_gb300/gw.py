@@ -31,7 +31,7 @@ EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
-    "gw_status_string", "gw_last_error", "gw_fp_peak",
+    "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
     "gw_timing_enable", "gw_timing_read", "gw_timing_reset",
 ]
 
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_polarizability_tau.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.gw_transform_tau_iw.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_screened_W_iw.argtypes = [vp, vp, vp, vp, vp]
+    lib.gw_screened_W_iw_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.gw_self_energy_tau.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, vp]
     lib.gw_fourier_R_to_k.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_sync.argtypes = [vp, vp]
@@ -281,6 +282,16 @@ class Plan:
         _check(self._lib.gw_screened_W_iw(self._h, self._in(P_R_iw, self.len("pb", nn), "P_R_iw"),
                                           self._in(v_q, self.info["n_k"] * N * N, "v_q"),
                                           C.c_void_p(Wt_R_iw.data_ptr()), self._stream(stream)), "gw_screened_W_iw")
+        return Wt_R_iw
+
+    def screened_W_iw_noalloc(self, P_R_iw, v_q, Wt_R_iw, stream=None):
+        """gw_screened_W_iw_noalloc: the W solve with the library's fixed 32 MiB scratch
+        (for callers that cannot allocate device memory while they run); Wt_R_iw must be given."""
+        nn, N = self.info["n_nu"], self.dense_n("pb")
+        _check(self._lib.gw_screened_W_iw_noalloc(self._h, self._in(P_R_iw, self.len("pb", nn), "P_R_iw"),
+                                                  self._in(v_q, self.info["n_k"] * N * N, "v_q"),
+                                                  self._in(Wt_R_iw, self.len("pb", nn), "Wt_R_iw"),
+                                                  self._stream(stream)), "gw_screened_W_iw_noalloc")
         return Wt_R_iw
 
     def self_energy_tau(self, G_R, Wt_R, v_R=None, Sig_R=None, Sigx_R=None, precision: str = "fp64",
