@@ -98,6 +98,41 @@ def contraction_flops(cell, entries) -> float:
     return f * cell.n_tau
 
 
+def kernel_work(name: str, cell, info, entries):
+    """Algorithmic work of one sweep for the kernels that can dominate it: (bound,
+    work, kind, units) with flops for "alu"/"tensor" (real flops) and bytes for "hbm",
+    and `units` the matrices (W solve) or pair entries the sweep processes; None for
+    the others.  Per launch = this / launches per sweep."""
+    N = cell.n_pb_total
+    nq = info["n_q_solved"]
+    nnu = int((cell.nu_idx >= 0).sum()) if info["w_symmetric"] else cell.nu_idx.size
+    n_inv = nq * (nnu + 1)  # v(q) once, then every solved (q, nu)
+    gj = 8.0 * N ** 3 * n_inv  # complex Gauss-Jordan inverse, or one complex N^3 product
+    nt, nn, nw = info["n_tau"], info["n_nu"], info["n_omega"]
+    if name in ("k_gj_inverse_blocked", "k_gj_inverse"):
+        return "alu", gj, "fp64", n_inv
+    if name == "k_gj_inverse_f32":
+        return "alu", gj, "fp32", n_inv
+    if name in ("k_refine_tc<first>", "k_refine_tc<final>"):  # 6 term pairs x 4 real products of 2 N^3
+        return "tensor", 4 * 6 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
+    if name == "k_ozaki_residual<first>":  # 20 slice pairs x 4 real products of 2 N^3
+        return "tensor", 4 * 20 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
+    if name == "k_ozaki_residual<second>":  # 36 slice pairs
+        return "tensor", 4 * 36 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
+    if name == "k_polarizability_fp64":
+        return "alu", contraction_flops(cell, entries) / (2 if info["c_symmetric"] else 1), "fp64", len(entries)
+    if name == "k_self_energy_fp64":  # dynamic part and the one-slice exchange term
+        return "alu", contraction_flops(cell, entries) * (1 + 1.0 / nt), "fp64", len(entries)
+    if name == "k_transform":  # real flops per block element: 8 n_out n_in (general), 2 n_out ceil(n_in / 2)
+        # (mirror-paired input), 4 n_out n_in (real input)
+        fP = 2 * nn * ((nt + 1) // 2) if info["c_symmetric"] else 8 * nn * nt
+        fW = 4 * nt * nn if info["w_symmetric"] else 8 * nt * nn
+        return "alu", float((fP + fW) * info["len_pb"] + 8 * nw * nt * info["len_orb"]), "fp64", 3 * len(entries)
+    if name == "k_slice_A":  # FP64 in, 8 x 2 BF16 digits out per element
+        return "hbm", (16 + 32) * N * N * n_inv, "bytes", n_inv
+    return None
+
+
 def wsolve_flops(cell, info) -> float:
     """Gauss-Jordan inverses of v(q) and of v(q)^{-1} - P(q, i nu): 8 N^3 real flops
     each, over the momenta and frequencies the plan actually solves."""
@@ -209,9 +244,11 @@ class Sweep:
         calls = [
             lambda: p.green_k_to_R(self.G_k, self.G_R, stream=s),
             lambda: p.polarizability_tau(self.G_R, self.P_R, precision=self.prec, stream=s),
-            lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s),
+            lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s,
+                                       structure="mirror" if inf["c_symmetric"] else "general"),
             lambda: p.screened_W_iw(self.P_iw, self.v_q, self.W_iw, stream=s),
-            lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s),
+            lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s,
+                                       structure="real" if inf["w_symmetric"] else "general"),
             lambda: p.fourier_k_to_R("pb", 1, self.v_q, self.v_R, stream=s),
             lambda: p.self_energy_tau(self.G_R, self.W_R, v_R=self.v_R, Sig_R=self.S_R, Sigx_R=self.Sx_R,
                                       precision=self.prec, stream=s),
@@ -231,22 +268,23 @@ class Sweep:
         inf = self.plan.info
         nnu = int((self.cell.nu_idx >= 0).sum()) if inf["w_symmetric"] else inf["n_nu"]
         nchunks = -(-nnu // inf["nu_chunk"])
-        inv = 12 if inf["w_tensor"] else 1  # launches per batched inverse
+        inv = 15 if inf["w_tensor"] else 1  # launches per batched inverse
         # copy of v, inverse of v, per chunk (scatter, inverse, gather), mirror
         w = 1 + inv + nchunks * (2 + inv) + (1 if inf["w_symmetric"] else 0)
         return 1 + 1 + 1 + w + 1 + 1 + 2 + 1 + 2
 
 
-def traffic_of(stage: str):
-    """DRAM bytes per launch of the stage's dominant kernel from a committed ncu
-    capture, or None when there is none or its source has changed since."""
+def traffic_of(kernel: str, units_per_launch: float):
+    """DRAM bytes per launch of `kernel` from a committed ncu capture (bytes per unit
+    there x units in this launch), or None when there is none or when the kernel's
+    source has changed since the capture."""
     import hashlib
-    t = TRAFFIC.get(stage)
+    t = TRAFFIC.get(kernel)
     if not t:
         return None
     src = os.path.join(ROOT, "paper_1911_05633_gb300", "csrc", t["file"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return t["bytes_per_launch"] if sha == t["src_sha"] else None
+    return round(t["bytes_per_unit"] * units_per_launch) if sha == t["src_sha"] else None
 
 
 def flush_l2(buf):
@@ -276,6 +314,8 @@ def run_ours(args, rank, world, local):
     nst = len(Sweep.STAGES)
     ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nst)] for _ in range(args.steps)]
     clocks = Clocks(local)
+    sw.plan.timing_reset()
+    sw.plan.timing_enable(True)  # one CUDA event pair around each library launch
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -289,36 +329,63 @@ def run_ours(args, rank, world, local):
     wall = time.perf_counter() - t0
     barrier(world)
     clk = clocks.stop()
+    ktimes = sw.plan.timing_read()
+    sw.plan.timing_enable(False)
     stage_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nst)] for k in range(args.steps)])
     step_ms = float(stage_ms.sum(axis=1).mean())
     step_ms_max = max_over_ranks(step_ms, world)
     value = world * 1000.0 / step_ms_max
     stage_mean = stage_ms.mean(axis=0)
 
-    # roofline of the dominant stage
+    # roofline of the dominant kernel, timed live by the library's event pairs
     ent = sw.plan.entries
-    fl_P = contraction_flops(cell, ent) / (2 if sw.plan.info["c_symmetric"] else 1)  # mirrored nodes not computed
-    fl_S = contraction_flops(cell, ent)
-    fl_W = wsolve_flops(cell, sw.plan.info)
-    work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
-    dom = int(np.argmax(stage_mean))
-    dom_name = Sweep.STAGES[dom]
+    inf = sw.plan.info
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    tot_k = sum(v[0] for v in ktimes.values()) or 1.0
+    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] / args.steps,
+                   "share": round(v[0] / tot_k, 4)} for k, v in sorted(ktimes.items(), key=lambda x: -x[1][0])}
     roof = None
-    if dom_name == "W_solve" or (dom_name in work and args.precision == "fp64"):
-        ach = work[dom_name] / (stage_mean[dom] * 1e-3) / 1e12
-        peak, src = fp64_peak, "FP64 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
-        if not peak:
-            peak, src = FP64_NOMINAL_TFLOPS, "nominal FP64 (probe unavailable)"
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_of(dom_name),
-                "peak_source": src}
+    if ktimes:
+        dom_k = max(ktimes, key=lambda k: ktimes[k][0])
+        ms_tot, nl = ktimes[dom_k]
+        w = kernel_work(dom_k, cell, inf, ent)
+        if w is not None:
+            bound, work, kind, units = w
+            per_launch = work * args.steps / nl
+            dur = ms_tot * 1e-3 / nl
+            if bound == "hbm":
+                ach, unit = per_launch / dur / 1e9, "GB/s"
+                peak, src = peaks.get("hbm_gbs"), "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)"
+            elif bound == "tensor":
+                ach, unit = per_launch / dur / 1e12, "TFLOP/s"
+                peak, src = peaks.get("bf16_tflops"), "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)"
+            else:
+                ach, unit = per_launch / dur / 1e12, "TFLOP/s"
+                if kind == "fp64":
+                    peak, src = fp64_peak, "FP64 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
+                else:
+                    peak, src = fp32_peak, "FP32 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
+            roof = {"kernel": dom_k, "bound": bound, "achieved": round(ach, 4),
+                    "peak": round(peak, 4) if peak else None, "unit": unit,
+                    "frac": round(ach / peak, 4) if peak else None,
+                    "traffic": traffic_of(dom_k, units * args.steps / nl), "peak_source": src,
+                    "work_per_launch": per_launch, "launch_ms": round(dur * 1e3, 4)}
+    fl_P = contraction_flops(cell, ent) / (2 if inf["c_symmetric"] else 1)  # mirrored nodes not computed
+    fl_S = contraction_flops(cell, ent)
+    fl_W = wsolve_flops(cell, inf)
+    work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
     contraction_tflops = {k: round(work[k] / (stage_mean[Sweep.STAGES.index(k)] * 1e-3) / 1e12, 4)
                           for k in ("P", "Sigma", "W_solve")}
+
+    # the P + Sigma sweep without the W solve (rows a1-a4, a6-a8; a5 timed on its own)
+    ps_ms = float(stage_mean.sum() - stage_mean[Sweep.STAGES.index("W_solve")])
+    p_sigma = {"value": round(world * 1000.0 / ps_ms, 4), "unit": "sweep/s", "ms_per_sweep": round(ps_ms, 4),
+               "w_solve_ms": round(float(stage_mean[Sweep.STAGES.index("W_solve")]), 4),
+               "stages": "every row except the W solve, which is timed on its own"}
 
     e2e = None
     if not args.no_e2e:
@@ -333,12 +400,14 @@ def run_ours(args, rank, world, local):
                    "precision": args.precision, "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}"},
         "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
+        "p_sigma_sweep": p_sigma,
         "tflops": contraction_tflops,
         "fp64_peak_tflops_measured": fp64_peak, "fp32_peak_tflops_measured": fp32_peak,
         "wall_s": round(wall, 3),
         "clocks": clk,
         "gpu_launches": sw.kernel_launches() * args.steps,
         "roofline": roof,
+        "kernels": kernels,
         "e2e": e2e,
     }
     return out, cell

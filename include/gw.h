@@ -166,6 +166,24 @@ gw_status gw_polarizability_tau(gw_plan_t plan, const void* G_R, void* P_R,
 gw_status gw_transform_tau_iw(gw_plan_t plan, gw_statistics st, gw_direction dir,
                               gw_block kind, const void* in, void* out, void* stream);
 
+/* Input structure for gw_transform_tau_iw_ex.
+ * GW_IN_MIRROR: in(tau_{N-1-i}) = conj(in(tau_i)) for every block element, i.e. F(beta - tau)
+ *   = F(tau)* on the mirror-symmetric grid (P from gw_polarizability_tau when the plan
+ *   reports c_symmetric).  Bosonic tau -> i nu only: the output is real (F(i nu) =
+ *   sum over mirror pairs of 2 Re(T F)), so only the nodes i < ceil(N_tau / 2) are read,
+ *   the imaginary parts are written as 0, and it takes a quarter of the general flops.
+ * GW_IN_REAL: the imaginary parts of `in` are zero (W~(R, i nu) from gw_screened_W_iw when
+ *   the plan reports w_symmetric); they are not read, and it takes half the flops. */
+enum { GW_IN_GENERAL = 0, GW_IN_MIRROR = 1, GW_IN_REAL = 2 };
+
+/* gw_transform_tau_iw for inputs of a known structure (the symmetries of the tau grid
+ * and of Eq. P_MM with symmetric product coefficients).  GW_ERR_ARG for an unknown
+ * `structure`; GW_ERR_UNSUPPORTED for GW_IN_MIRROR with fermionic statistics or the
+ * i omega -> tau direction.  The input is trusted to have the stated structure. */
+gw_status gw_transform_tau_iw_ex(gw_plan_t plan, gw_statistics st, gw_direction dir,
+                                 gw_block kind, int structure, const void* in, void* out,
+                                 void* stream);
+
 /* W~(R, i nu) on the kept entries from P(R, i nu) (Eq. W_1 with W = v + W~):
  * P(q) = sum_{kept R} e^{iq.R} P(R); W(q) = (I - v(q) P(q))^{-1} v(q), computed as
  * (v(q)^{-1} - P(q))^{-1}, each inverse either by FP64 Gauss-Jordan with partial

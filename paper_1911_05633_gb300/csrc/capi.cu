@@ -32,6 +32,7 @@ struct gw_plan_s {
   double2* d_Tf_fwd = nullptr;
   double2* d_Tf_inv = nullptr;
   double2* d_Tb_fwd = nullptr;
+  double2* d_Tb_mirror = nullptr;  // [n_nu][ceil(N_tau/2)] mirror-pair coefficients
   double2* d_Tb_inv = nullptr;
   // W solve: momenta and frequencies solved, and scratch
   bool w_sym = false;
@@ -53,8 +54,9 @@ struct gw_plan_s {
   bool w_tensor = false;
   size_t smem_GJ32 = 0;
   float2* t_X32 = nullptr;
-  double2* t_X1 = nullptr;
-  double2* t_R = nullptr;
+  float2* t_lo = nullptr;
+  float2* t_R = nullptr;
+  uint16_t* t_PX = nullptr;
   uint16_t* t_Asl = nullptr;
   uint16_t* t_Xsl = nullptr;
   int* t_eA = nullptr;
@@ -116,8 +118,8 @@ gw_status upload(T** dst, const void* src, size_t bytes) {
 
 void free_device(gw_plan_s* p) {
   void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_phase,
-                  p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_inv, p->d_qh, p->d_qw,
-                  p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_X1, p->t_R, p->t_Asl,
+                  p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_mirror, p->d_Tb_inv, p->d_qh, p->d_qw,
+                  p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_lo, p->t_R, p->t_PX, p->t_Asl,
                   p->t_Xsl, p->t_eA, p->t_eX};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -185,8 +187,9 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
 gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_R, int in_n_slices,
                          int in_slice0, double2* F_k, long long k_stride, long long s_stride, cudaStream_t st,
                          const int* k_list = nullptr, int n_k_out = -1, const double2* base = nullptr,
-                         double coef = 1.0) {
+                         double coef = 1.0, bool real_in = false) {
   gw::ScatterArgs g{};
+  g.real_in = real_in ? 1 : 0;
   g.ent = p->d_ent;
   g.pair_start = p->d_pair_start;
   g.row_off = kind == GW_BLOCK_PB ? p->d_pb_off : p->d_orb_off;
@@ -232,7 +235,16 @@ gw_status launch_gj(gw_plan_s* p, double2* mats, int batch, long long N, cudaStr
 
 // In place: mats[b] (FP64, N x N) -> its inverse by the tensor-core refinement (kernels_wtc.cu).
 gw_status launch_tensor_inverse(gw_plan_s* p, double2* mats, int batch, long long N, cudaStream_t st) {
-  gw::WtcBuffers w{p->t_X32, p->t_X1, p->t_R, p->t_Asl, p->t_Xsl, p->t_eA, p->t_eX, p->d_perm, p->d_status};
+  gw::WtcBuffers w{};  // by name: the buffers differ in size per element
+  w.X32 = p->t_X32;
+  w.lo = p->t_lo;
+  w.R = p->t_R;
+  w.Asl = p->t_Asl;
+  w.Xsl = p->t_Xsl;
+  w.PX = p->t_PX;
+  w.eA = p->t_eA;
+  w.eX = p->t_eX;
+  w.status = p->d_status;
   gw::wtc_inverse(w, mats, batch, (int)N, p->smem_GJ32, st);
   return check_launch("tensor-core inverse");
 }
@@ -361,6 +373,7 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_Tf_fwd, h.Tf_fwd.data(), h.Tf_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tf_inv, h.Tf_inv.data(), h.Tf_inv.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tb_fwd, h.Tb_fwd.data(), h.Tb_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
+  if ((st = upload(&p->d_Tb_mirror, h.Tb_mirror.data(), h.Tb_mirror.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tb_inv, h.Tb_inv.data(), h.Tb_inv.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_status, nullptr, 16)) != GW_OK) return fail(st);
   if (cudaMemset(p->d_status, 0, 16) != cudaSuccess) return fail(GW_ERR_CUDA);
@@ -371,10 +384,11 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_qw, qw.data(), qw.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
   const size_t mat = npb * npb * sizeof(double2);
-  // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) FP32 copy, residual,
-  // the BF16 slices of both operands and the scale exponents
+  // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) the FP32 inverse,
+  // its correction and the residual, the BF16 digit planes of both operands, the term
+  // planes of X0 and the scale exponents
   const size_t per_mat = mat + npb * sizeof(int) +
-                         (p->w_tensor ? npb * npb * (sizeof(float2) + 2 * sizeof(double2) + 2 * (gw::kWSA + gw::kWSX1) * 2) +
+                         (p->w_tensor ? npb * npb * (3 * sizeof(float2) + 2 * (gw::kWSA + gw::kWSX1) * 2 + 6 * 2) +
                                             2 * npb * sizeof(int)
                                       : 0);
   const size_t per_nu = (size_t)p->n_qh * per_mat;
@@ -391,13 +405,14 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if (p->w_tensor) {
     const size_t nm = (size_t)nch * p->n_qh;
     if ((st = upload(&p->t_X32, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_X1, nullptr, nm * npb * npb * sizeof(double2))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_R, nullptr, nm * npb * npb * sizeof(double2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_lo, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_R, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
+    if ((st = upload(&p->t_PX, nullptr, nm * npb * npb * 6 * 2)) != GW_OK) return fail(st);
     if ((st = upload(&p->t_Asl, nullptr, nm * npb * npb * 2 * gw::kWSA * 2)) != GW_OK) return fail(st);
     if ((st = upload(&p->t_Xsl, nullptr, nm * npb * npb * 2 * gw::kWSX1 * 2)) != GW_OK) return fail(st);
     if ((st = upload(&p->t_eA, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
     if ((st = upload(&p->t_eX, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
-    p->smem_GJ32 = (2 * npb * gw::kGJB + npb) * sizeof(float2);
+    p->smem_GJ32 = gw::gj32_smem((int)npb);
     if (gw::wtc_setup(p->smem_GJ32) != cudaSuccess) {
       cudaError_t e = cudaGetLastError();
       set_last_error(std::string("cudaFuncSetAttribute (tensor W): ") + cudaGetErrorString(e));
@@ -518,11 +533,19 @@ gw_status gw_fourier_R_to_k(gw_plan_t p, gw_block kind, int n_slices, const void
                         (long long)n_slices * N * N, N * N, S(stream));
 }
 
-gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, gw_block kind, const void* in,
-                              void* out, void* stream) {
+gw_status gw_transform_tau_iw_ex(gw_plan_t p, gw_statistics stt, gw_direction dir, gw_block kind, int structure,
+                                 const void* in, void* out, void* stream) {
   gw_status st = need_device(p);
   if (st != GW_OK) return st;
   if (!in || !out) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  if (structure != 0 && structure != GW_IN_MIRROR && structure != GW_IN_REAL) {
+    set_last_error("unknown input structure");
+    return GW_ERR_ARG;
+  }
+  if (structure == GW_IN_MIRROR && !(stt == GW_BOSON && dir == GW_TAU_TO_IW)) {
+    set_last_error("GW_IN_MIRROR applies to the bosonic tau -> i nu transform only");
+    return GW_ERR_UNSUPPORTED;
+  }
   DeviceGuard guard(p->device);
   gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
@@ -538,6 +561,15 @@ gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, 
     g.n_in = nfreq;
     g.n_out = h.n_tau;
   }
+  g.in_stride = g.n_in;
+  g.mode = 0;
+  if (structure == GW_IN_MIRROR) {
+    g.T = p->d_Tb_mirror;
+    g.n_in = (h.n_tau + 1) / 2;
+    g.mode = 1;
+  } else if (structure == GW_IN_REAL) {
+    g.mode = 2;
+  }
   g.pb = kind == GW_BLOCK_PB;
   g.in = (const double2*)in;
   g.out = (double2*)out;
@@ -552,6 +584,11 @@ gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, 
     gw::k_transform<<<grid, block, (size_t)g.n_in * 32 * sizeof(double2), S(stream)>>>(g);
   }
   return check_launch("k_transform");
+}
+
+gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, gw_block kind, const void* in,
+                              void* out, void* stream) {
+  return gw_transform_tau_iw_ex(p, stt, dir, kind, 0, in, out, stream);
 }
 
 gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_precision prec, void* stream) {
@@ -670,8 +707,9 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     const int nc = std::min(p->nu_chunk, n_work - c0);
     const int slot0 = p->nu_start + c0;
     // A = v(q)^{-1} - P(q, nu) for the chunk, [nu][q][N][N]
+    // symmetric mode: P(R, i nu) is real (the imaginary parts are not read)
     if ((st = launch_scatter(p, GW_BLOCK_PB, nc, (const double2*)P_R_iw, h.n_nu, slot0, p->d_wsA, NN,
-                             (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0)) != GW_OK)
+                             (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0, p->w_sym)) != GW_OK)
       return st;
     if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsA, nc * nq, N, s);
     else st = launch_gj(p, p->d_wsA, nc * nq, N, s);

@@ -53,6 +53,9 @@ struct HostPlan {
   std::vector<int> mirror;                // [E]
   std::vector<double> phase;              // [E][N_k] complex e^{+i k.R}
   std::vector<double> Tf_fwd, Tf_inv, Tb_fwd, Tb_inv;  // complex matrices
+  // bosonic tau -> i nu for inputs with F(beta - tau) = conj(F(tau)): coefficients
+  // (a, b) per (frequency, node i < ceil(N_tau / 2)) with Re out = sum a Re F + b Im F
+  std::vector<double> Tb_mirror;
   std::vector<int> c_off;                 // per species offset into packed C
   std::vector<double> C_packed;
   int kmesh_required[3] = {0, 0, 0};

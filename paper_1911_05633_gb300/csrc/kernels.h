@@ -38,6 +38,7 @@ struct ScatterArgs {
   int n_k_out;
   const double2* base;     // optional dense [n_k_out][N][N] added to the result
   double coef;             // result = base + coef * sum
+  int real_in;             // imaginary parts of F_R are zero: not read
   const double2* F_R;      // entry layout input
   int in_n_slices, in_slice0;
   int pb;
@@ -53,6 +54,10 @@ struct TransformArgs {
   int pb;
   const double2* in;
   double2* out;
+  // 0: general complex; 1: mirror-paired input, n_in = the first ceil(N/2) nodes of an
+  // in-stride of in_stride slices, T = (a, b) coefficients, real output; 2: real input
+  int mode;
+  int in_stride;
 };
 
 struct ContractArgs {

@@ -70,9 +70,18 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
         v.x *= wk;
         v.y *= wk;
       }
+      if (g.real_only) {  // Re(conj(ph) v) only
 #pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m)
-        if (m < ne) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
+        for (int m = 0; m < kGatherEnt; ++m)
+          if (m < ne) {
+            const double2 ph = g.phase[(long long)(eb + m) * g.n_k + k];
+            acc[m].x = fma(ph.x, v.x, fma(ph.y, v.y, acc[m].x));
+          }
+      } else {
+#pragma unroll
+        for (int m = 0; m < kGatherEnt; ++m)
+          if (m < ne) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
+      }
     }
 #pragma unroll
     for (int m = 0; m < kGatherEnt; ++m) {
@@ -117,9 +126,15 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
     for (int kk = 0; kk < g.n_k_out; ++kk) {
       const int k = g.k_list ? g.k_list[kk] : kk;
       double2 acc = make_double2(0.0, 0.0);
+      if (g.real_in) {  // ph * Re(v)
 #pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m)
-        if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
+        for (int m = 0; m < kGatherEnt; ++m)
+          if (m < ne) acc = rfma(v[m].x, g.phase[(long long)(eb + m) * g.n_k + k], acc);
+      } else {
+#pragma unroll
+        for (int m = 0; m < kGatherEnt; ++m)
+          if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
+      }
       acc.x *= g.coef;
       acc.y *= g.coef;
       double2* o = g.F_k + (long long)kk * g.k_stride + (long long)s * g.s_stride + out_el;
@@ -149,7 +164,7 @@ __global__ void k_transform(TransformArgs g) {
   if (c0 >= blk) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = c0 + tx;
-  const double2* in = g.in + off * g.n_in;
+  const double2* in = g.in + off * g.in_stride;
   double2* out = g.out + off * g.n_out;
   for (int i = ty; i < g.n_in; i += blockDim.y)
     tile[i * 32 + tx] = (c < blk) ? in[(long long)i * blk + c] : make_double2(0.0, 0.0);
@@ -158,7 +173,21 @@ __global__ void k_transform(TransformArgs g) {
   for (int m = ty; m < g.n_out; m += blockDim.y) {
     const double2* Tm = g.T + (long long)m * g.n_in;
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < g.n_in; ++i) acc = cfma(Tm[i], tile[i * 32 + tx], acc);
+    if (g.mode == 1) {  // Re out = sum a Re F + b Im F over the paired nodes; Im out = 0
+      for (int i = 0; i < g.n_in; ++i) {
+        const double2 t = Tm[i], f = tile[i * 32 + tx];
+        acc.x = fma(t.x, f.x, fma(t.y, f.y, acc.x));
+      }
+    } else if (g.mode == 2) {  // real input
+      for (int i = 0; i < g.n_in; ++i) {
+        const double2 t = Tm[i];
+        const double f = tile[i * 32 + tx].x;
+        acc.x = fma(t.x, f, acc.x);
+        acc.y = fma(t.y, f, acc.y);
+      }
+    } else {
+      for (int i = 0; i < g.n_in; ++i) acc = cfma(Tm[i], tile[i * 32 + tx], acc);
+    }
     out[(long long)m * blk + c] = acc;
   }
 }

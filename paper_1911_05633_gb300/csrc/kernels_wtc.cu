@@ -32,38 +32,46 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
 
 }  // namespace
 
-// In-place FP32 Gauss-Jordan inverse, the FP32 form of k_gj_inverse_blocked.
-__global__ void k_gj_inverse_blocked_f32(float2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
-                                     int* status) {
-  extern __shared__ unsigned char smraw[];
-  float2* Pan = reinterpret_cast<float2*>(smraw);  // [N][kGJB] panel columns
-  float2* Prow = Pan + (size_t)N * kGJB;            // [kGJB][N] pivot rows (pre-update)
-  float2* colk = Prow + (size_t)N * kGJB;           // [N]
-  __shared__ float2 rowk[kGJB];
-  __shared__ int pmk[kGJB];
-  __shared__ float rv[32];
-  __shared__ int ri[32];
-  const int b = blockIdx.x;
-  float2* M = A + (long long)b * mat_stride;
-  int* pm = perm + (long long)b * N;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int k0 = 0; k0 < N; k0 += kGJB) {
-    const int bb = min(kGJB, N - k0);
-    // load the panel
-    for (int x = tid; x < N * bb; x += nt) {
-      const int i = x / bb, m = x - (x / bb) * bb;
-      Pan[i * kGJB + m] = M[(long long)i * N + k0 + m];
-    }
+// In-place FP32 Gauss-Jordan inverse with partial pivoting, one 512-thread block per
+// matrix (N a multiple of kGJ32B, at most 512).  Panels of kGJ32B columns are reduced
+// in shared memory; the row exchanges and the rank-kGJ32B update of the other columns,
+// A[:, T] += (Pan - I[:, panel]) Prow (Prow: the pivot rows before the update), run
+// per chunk of kGJ32C columns with 4 x 4 complex register blocks per thread.  At the
+// end the columns are permuted back by the composite of the pivot swaps.
+__global__ void __launch_bounds__(512, 1)
+k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __restrict__ status) {
+  constexpr int B = kGJ32B, C = kGJ32C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* Pan = reinterpret_cast<float2*>(smraw);  // [N][B]
+  float2* Buf = Pan + (size_t)N * B;               // Prow [B][C] / exchange staging [2B][C] / rows [16][N]
+  float2* colk = Buf + gj32_buf_elems(N);          // [N]
+  float2* rowk = colk + N;                         // [B]
+  float2* oldk = rowk + B;                         // [B]
+  int* pm = reinterpret_cast<int*>(oldk + B);      // [N] pivot row chosen for each column
+  int* srcmap = pm + N;                            // [N]
+  int* xdst = srcmap + N;                          // [2B]
+  int* xsrc = xdst + 2 * B;                        // [2B]
+  __shared__ float rv[16];
+  __shared__ int ri[16];
+  __shared__ int nx;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (N % C != 0 || N > 512) {
+    if (tid == 0) atomicExch(status, 3);
+    return;
+  }
+  float2* M = A + (long long)blockIdx.x * mat_stride;
+  for (int k0 = 0; k0 < N; k0 += B) {
+    for (int x = tid; x < N * B; x += 512) Pan[x] = M[(long long)(x / B) * N + k0 + (x % B)];
     __syncthreads();
-    for (int m = 0; m < bb; ++m) {
+    for (int m = 0; m < B; ++m) {
       const int k = k0 + m;
+      // pivot among rows k .. N-1 (at most one candidate per thread)
       float best = -1.0f;
-      int bi = k;
-      for (int i = k + tid; i < N; i += nt) {
-        const float2 z = Pan[i * kGJB + m];
-        const float a = fabsf(z.x) + fabsf(z.y);
-        if (a > best) { best = a; bi = i; }
+      int bi = N;
+      if (k + tid < N) {
+        const float2 z = Pan[(k + tid) * B + m];
+        best = fabsf(z.x) + fabsf(z.y);
+        bi = k + tid;
       }
       for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -73,95 +81,129 @@ __global__ void k_gj_inverse_blocked_f32(float2* __restrict__ A, int* __restrict
       if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
       __syncthreads();
       if (wid == 0) {
-        best = (lane < nw) ? rv[lane] : -1.0f;
-        bi = (lane < nw) ? ri[lane] : N;
+        best = lane < 16 ? rv[lane] : -1.0f;
+        bi = lane < 16 ? ri[lane] : N;
         for (int o = 16; o > 0; o >>= 1) {
           const float ob = __shfl_down_sync(0xffffffffu, best, o);
           const int oi = __shfl_down_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         if (lane == 0) {
-          ri[0] = bi;
-          pm[k] = bi;
-          pmk[m] = bi;
+          pm[k] = bi < N ? bi : k;
           if (!(best > 0.0f)) atomicExch(status, 1);
         }
       }
       __syncthreads();
-      const int p = ri[0];
-      if (p != k && tid < bb) {
-        const float2 t = Pan[k * kGJB + tid];
-        Pan[k * kGJB + tid] = Pan[p * kGJB + tid];
-        Pan[p * kGJB + tid] = t;
-      }
-      __syncthreads();
-      const float2 d = Pan[k * kGJB + m];
+      const int p = pm[k];
+      // phase A: pivot row (scaled), old row k, column m as it reads after the swap
+      const float2 d = Pan[p * B + m];
       const float den = d.x * d.x + d.y * d.y;
-      const float2 inv = (den > 0.0f) ? make_float2(d.x / den, -d.y / den) : make_float2(0.0f, 0.0f);
-      for (int i = tid; i < N; i += nt) colk[i] = (i == k) ? make_float2(0.0f, 0.0f) : Pan[i * kGJB + m];
-      if (tid < bb) rowk[tid] = (tid == m) ? inv : cmul(Pan[k * kGJB + tid], inv);
+      const float2 inv = den > 0.0f ? make_float2(d.x / den, -d.y / den) : make_float2(0.0f, 0.0f);
+      if (tid < B) {
+        rowk[tid] = tid == m ? inv : cmul(Pan[p * B + tid], inv);
+        oldk[tid] = Pan[k * B + tid];
+      }
+      for (int i = tid; i < N; i += 512)
+        colk[i] = i == k ? make_float2(0.0f, 0.0f) : (i == p ? Pan[k * B + m] : Pan[i * B + m]);
       __syncthreads();
-      for (int x = tid; x < N * bb; x += nt) {
-        const int i = x / bb, j = x - (x / bb) * bb;
+      // phase B: rows k and p exchanged and the panel updated, each thread on its own elements
+      for (int x = tid; x < N * B; x += 512) {
+        const int i = x / B, j = x % B;
+        float2 v;
         if (i == k) {
-          Pan[i * kGJB + j] = rowk[j];
+          v = rowk[j];
         } else {
+          const float2 src = j == m ? make_float2(0.0f, 0.0f) : (i == p ? oldk[j] : Pan[x]);
           const float2 f = colk[i];
-          const float2 z = (j == m) ? make_float2(0.0f, 0.0f) : Pan[i * kGJB + j];
-          Pan[i * kGJB + j] = cfma(make_float2(-f.x, -f.y), rowk[j], z);
+          v = cfma(make_float2(-f.x, -f.y), rowk[j], src);
         }
+        Pan[x] = v;
       }
       __syncthreads();
     }
-    // row exchanges on the other columns, then the pivot rows (pre-update) to shared memory
-    for (int j = tid; j < N; j += nt) {
-      if (j >= k0 && j < k0 + bb) continue;
-      for (int m = 0; m < bb; ++m) {
-        const int k = k0 + m, p = pmk[m];
-        if (p != k) {
-          const float2 t = M[(long long)k * N + j];
-          M[(long long)k * N + j] = M[(long long)p * N + j];
-          M[(long long)p * N + j] = t;
-        }
+    // composite row exchange of this panel: new row r = old row srcmap[r]
+    for (int i = tid; i < N; i += 512) srcmap[i] = i;
+    __syncthreads();
+    if (tid == 0) {
+      for (int m = 0; m < B; ++m) {
+        const int k = k0 + m, p = pm[k];
+        if (p != k) { const int t = srcmap[k]; srcmap[k] = srcmap[p]; srcmap[p] = t; }
       }
-      for (int m = 0; m < bb; ++m) Prow[m * N + j] = M[(long long)(k0 + m) * N + j];
+      int n = 0;
+      for (int r = k0; r < N && n < 2 * B; ++r)
+        if (srcmap[r] != r) { xdst[n] = r; xsrc[n] = srcmap[r]; ++n; }
+      nx = n;
     }
     __syncthreads();
-    // A[:, T] += (Pan - I[:, panel]) Prow   (one warp per row, lanes along j)
-    for (int i = wid; i < N; i += nw) {
-      float2 z[kGJB];
-#pragma unroll
-      for (int m = 0; m < kGJB; ++m) {
-        z[m] = (m < bb) ? Pan[i * kGJB + m] : make_float2(0.0f, 0.0f);
-        if (i == k0 + m) z[m].x -= 1.0f;
+    const int n = nx;
+    for (int c0 = 0; c0 < N; c0 += C) {
+      const bool has_panel = k0 >= c0 && k0 < c0 + C;
+      // (a) the row exchange on this chunk's other columns, staged through shared memory
+      for (int x = tid; x < n * C; x += 512) {
+        const int e = x / C, j = c0 + (x % C);
+        if (!(j >= k0 && j < k0 + B)) Buf[x] = M[(long long)xsrc[e] * N + j];
       }
-      float2* Mi = M + (long long)i * N;
-      for (int j = lane; j < N; j += 32) {
-        if (j >= k0 && j < k0 + bb) continue;
-        float2 acc = Mi[j];
-#pragma unroll
-        for (int m = 0; m < kGJB; ++m)
-          if (m < bb) acc = cfma(z[m], Prow[m * N + j], acc);
-        Mi[j] = acc;
+      __syncthreads();
+      for (int x = tid; x < n * C; x += 512) {
+        const int e = x / C, j = c0 + (x % C);
+        if (!(j >= k0 && j < k0 + B)) M[(long long)xdst[e] * N + j] = Buf[x];
       }
+      __syncthreads();
+      // (b) the pivot rows of this chunk before the update
+      for (int x = tid; x < B * C; x += 512) Buf[x] = M[(long long)(k0 + x / C) * N + c0 + (x % C)];
+      __syncthreads();
+      // (c) rows i0 .. i0 + 3, columns c0 + lane + 32 q
+      for (int i0 = 4 * wid; i0 < N; i0 += 4 * 16) {
+        float2 acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = M[(long long)(i0 + r) * N + c0 + lane + 32 * q];
+#pragma unroll 4
+        for (int m = 0; m < B; ++m) {
+          float2 z[4], pv[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            z[r] = Pan[(i0 + r) * B + m];
+            if (i0 + r == k0 + m) z[r].x -= 1.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) pv[q] = Buf[m * C + lane + 32 * q];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = cfma(z[r], pv[q], acc[r][q]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            if (!has_panel || !(j >= k0 && j < k0 + B)) M[(long long)(i0 + r) * N + j] = acc[r][q];
+          }
+      }
+      __syncthreads();
     }
-    // the panel itself
-    for (int x = tid; x < N * bb; x += nt) {
-      const int i = x / bb, m = x - (x / bb) * bb;
-      M[(long long)i * N + k0 + m] = Pan[i * kGJB + m];
-    }
+    for (int x = tid; x < N * B; x += 512) M[(long long)(x / B) * N + k0 + (x % B)] = Pan[x];
     __syncthreads();
   }
-  for (int k = N - 1; k >= 0; --k) {
-    const int p = pm[k];
-    if (p != k) {
-      for (int i = tid; i < N; i += nt) {
-        const float2 t = M[(long long)i * N + k];
-        M[(long long)i * N + k] = M[(long long)i * N + p];
-        M[(long long)i * N + p] = t;
-      }
+  // undo the pivoting on the columns: new column j = old column srcmap[j], the composite
+  // of the swaps (k, pm[k]) for k = N-1 down to 0
+  for (int i = tid; i < N; i += 512) srcmap[i] = i;
+  __syncthreads();
+  if (tid == 0)
+    for (int k = N - 1; k >= 0; --k) {
+      const int p = pm[k];
+      if (p != k) { const int t = srcmap[k]; srcmap[k] = srcmap[p]; srcmap[p] = t; }
     }
-    __syncthreads();
+  __syncthreads();
+  float2* rb = Buf + (size_t)wid * N;
+  for (int i = wid; i < N; i += 16) {
+    float2* Mi = M + (long long)i * N;
+    for (int j = lane; j < N; j += 32) rb[j] = Mi[j];
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) Mi[j] = rb[srcmap[j]];
+    __syncwarp();
   }
 }
 
@@ -196,15 +238,20 @@ __global__ void k_row_exponent(const double2* __restrict__ A, int* __restrict__ 
   if (lane == 0) eA[row] = scale_exponent(m);
 }
 
-// one thread per column j: eX[b][j] with max_k max(|Re|, |Im|) X[b][k][j] < 2^eX
-template <typename T>
-__global__ void k_col_exponent(const T* __restrict__ X, int* __restrict__ eX, int N) {
+// one thread per column j: eX[b][j] with max_k max(|Re|, |Im|) (hi + lo)[b][k][j] < 2^eX
+// (lo may be null); |hi| + |lo| bounds |hi + lo| from above
+__global__ void k_col_exponent(const float2* __restrict__ hi, const float2* __restrict__ lo, int* __restrict__ eX,
+                               int N) {
   const int b = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  const T* x = X + (long long)b * N * N;
+  const long long base = (long long)b * N * N + j;
   double m = 0.0;
-  for (int k = 0; k < N; ++k) m = fmax(m, fmax(fabs((double)x[(long long)k * N + j].x), fabs((double)x[(long long)k * N + j].y)));
+  for (int k = 0; k < N; ++k) {
+    const float2 h = hi[base + (long long)k * N];
+    const float2 l = lo ? lo[base + (long long)k * N] : make_float2(0.0f, 0.0f);
+    m = fmax(m, fmax(fabs((double)h.x) + fabs((double)l.x), fabs((double)h.y) + fabs((double)l.y)));
+  }
   eX[(long long)b * N + j] = scale_exponent(m);
 }
 
@@ -276,14 +323,14 @@ __global__ void k_slice_A(const double2* __restrict__ A, const int* __restrict__
   }
 }
 
-// X operand slices.  Element X[k][j] of matrix b (k = reduction index) -> SX digits of
-// Re and Im in the K-major layout of the B operand (rows j), one chunk per (matrix,
-// kWTN-column block, 16-row step).  One thread per (column j, 8 consecutive k); lanes
+// X operand slices.  Element X[k][j] = hi + lo of matrix b (k = reduction index; lo may
+// be null) -> SX digits of Re and Im in the K-major layout of the B operand (rows j), one
+// chunk per (matrix, kWTN-column block, 16-row step).  One thread per (column j, 8 consecutive k); lanes
 // (j % 8, k half, (j / 8) % 2) read 128-byte row segments and fill 512 contiguous bytes
 // of each plane.
-template <typename T, int SX>
-__global__ void k_slice_X(const T* __restrict__ X, const int* __restrict__ eX, uint16_t* __restrict__ Xsl, int N,
-                          long long n_total) {
+template <int SX>
+__global__ void k_slice_X(const float2* __restrict__ hi, const float2* __restrict__ lo, const int* __restrict__ eX,
+                          uint16_t* __restrict__ Xsl, int N, long long n_total) {
   static_assert(kWTN == 32, "two 16-column halves per column block");
   const int NKS = N / 16, NJB = N / kWTN;
   const long long n_thr = n_total / 8;
@@ -299,13 +346,18 @@ __global__ void k_slice_X(const T* __restrict__ X, const int* __restrict__ eX, u
     const int j = jb * kWTN + jl;
     const int k0 = ks * 16 + 8 * h;
     const int e = eX[b * N + j];
-    const T* src = X + (b * N + k0) * (long long)N + j;
+    const long long o0 = (b * N + k0) * (long long)N + j;
     long long mr[8], mi[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const T z = src[(long long)u * N];
+      const float2 z = hi[o0 + (long long)u * N];
       mr[u] = fixed56((double)z.x, e);
       mi[u] = fixed56((double)z.y, e);
+      if (lo) {  // each part rounds to 2^-56 of the column scale
+        const float2 l = lo[o0 + (long long)u * N];
+        mr[u] += fixed56((double)l.x, e);
+        mi[u] += fixed56((double)l.y, e);
+      }
     }
     uint16_t* chunk = Xsl + ((b * NJB + jb) * NKS + ks) * (long long)(wx_chunk(SX) / 2);
     const uint32_t off = kmajor_offset(kWTN, jl, 8 * h) / 2;
@@ -322,6 +374,23 @@ __global__ void k_slice_X(const T* __restrict__ X, const int* __restrict__ eX, u
       *reinterpret_cast<uint4*>(chunk + (t * 2 + 0) * (kWTN * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
       *reinterpret_cast<uint4*>(chunk + (t * 2 + 1) * (kWTN * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
     }
+  }
+}
+
+// Accumulator q (0..7) of one residual entry in units of 2^-52.  Accumulators 0..6
+// hold exact multiples of 2^-14, 2^-21, 2^-28, 2^-35, 2^-35, 2^-42, 2^-42 below 2^24
+// such units, so the scaled value is an exact integer (level 0 below 2^62); accumulator
+// 7 (levels >= 5) is rounded to 2^-52.
+__device__ __forceinline__ long long level_units52(float v, int q) {
+  switch (q) {
+    case 0: return (long long)__float2int_rn(v * 0x1p14f) << 38;
+    case 1: return (long long)__float2int_rn(v * 0x1p21f) << 31;
+    case 2: return (long long)__float2int_rn(v * 0x1p28f) << 24;
+    case 3:
+    case 4: return (long long)__float2int_rn(v * 0x1p35f) << 17;
+    case 5:
+    case 6: return (long long)__float2int_rn(v * 0x1p42f) << 10;
+    default: return __float2ll_rn(v * 0x1p52f);
   }
 }
 
@@ -373,7 +442,7 @@ __device__ __forceinline__ void ozaki_issue_step(uint32_t tm, uint64_t da0, uint
 template <int SX, int LMAX>
 __global__ void __launch_bounds__(128, 1)
 k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ Xsl, const int* __restrict__ eA,
-                 const int* __restrict__ eX, double2* __restrict__ R, int N, int* status) {
+                 const int* __restrict__ eX, float2* __restrict__ R, int N, int* status) {
   static_assert(LMAX >= 5 && LMAX < kWSA, "every accumulator receives a product; A has kWSA slices");
   constexpr uint32_t XC = wx_chunk(SX);
   constexpr uint32_t AC = wa_bytes(LMAX);  // the leading planes s <= LMAX of each A chunk
@@ -445,96 +514,245 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
     const int r = 32 * warp + lane;
     const int i = ib * 128 + r;
     const int ea = eA[b * N + i];
-    double2* Ro = R + (b * N + i) * (long long)N;
+    float2* Ro = R + (b * N + i) * (long long)N;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    bool range_ok = true;
     for (int c0 = 0; c0 < kWTN; c0 += 16) {
-      // level 0 exactly against the identity, then the smaller levels added from the bottom
-      double re[16], im[16];
+      // all levels as one exact 64-bit integer in units of 2^-52 (the levels cancel
+      // each other, so they are combined before any rounding), the identity subtracted
+      // in the same units, then one rounding to FP32: R is small and FP32 keeps it to
+      // 2^-24 of itself
+      long long sr[16], si[16];
       float v[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) { re[c] = 0.0; im[c] = 0.0; }
+      for (int c = 0; c < 16; ++c) { sr[c] = 0; si[c] = 0; }
 #pragma unroll 1
-      for (int q = 7; q >= 1; --q) {
+      for (int q = 0; q <= 7; ++q) {
         tmem_ld16(tm + lane_base + (uint32_t)(q * kWTN + c0), v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) re[c] += (double)v[c];
+        for (int c = 0; c < 16; ++c) sr[c] += level_units52(v[c], q);
         tmem_ld16(tm + lane_base + (uint32_t)((8 + q) * kWTN + c0), v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) im[c] += (double)v[c];
+        for (int c = 0; c < 16; ++c) si[c] += level_units52(v[c], q);
       }
-      float v0r[16], v0i[16];
-      tmem_ld16(tm + lane_base + (uint32_t)c0, v0r);
-      tmem_ld16(tm + lane_base + (uint32_t)(8 * kWTN + c0), v0i);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int j = jb * kWTN + c0 + c;
-        const double sc = ldexp(1.0, ea + eX[b * N + j]);
-        const double r0 = (i == j ? 1.0 : 0.0) - sc * (double)v0r[c];
-        const double i0 = -sc * (double)v0i[c];
-        Ro[j] = make_double2(r0 - sc * re[c], i0 - sc * im[c]);
+        const int e = ea + eX[b * N + j];  // (A X)_ij = 2^e sum
+        long long re = sr[c];
+        if (i == j) {
+          if (e < -10 || e > 52) range_ok = false;
+          else re -= 1ll << (52 - e);  // 1 = 2^(52 - e) units of 2^(e - 52)
+        }
+        if (e < -126 || e > 126) range_ok = false;
+        const float sc = __int_as_float((127 + min(max(e, -126), 126)) << 23);  // 2^e
+        Ro[j] = make_float2(-sc * ((float)re * 0x1p-52f), -sc * ((float)si[c] * 0x1p-52f));
       }
     }
+    if (!range_ok) atomicExch(status, 4);  // scale outside the FP32 exponent range
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
-// X1[b] = X0[b] + X0[b] R[b] with the product in FP32 arithmetic (R is small), written as
-// FP64.  64 x 64 output tile per block, 256 threads, 4 x 4 outputs per thread.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_refine_update(const T* __restrict__ X0, const double2* __restrict__ R, double2* __restrict__ X1, int N) {
-  __shared__ float2 Xs[16][64 + 1];
-  __shared__ float2 Rs[16][64 + 1];
-  const long long b = blockIdx.z;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  const T* X = X0 + b * (long long)N * N;
-  const double2* Rb = R + b * (long long)N * N;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float2 acc[4][4];
+// Three BF16 terms of an FP32 value, v = hi + mid + lo to 2^-24 of |v| (each
+// remainder is exact in FP32); bits of term s.
+__device__ __forceinline__ void split3_bits(float v, uint32_t* t) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(m);
+  const __nv_bfloat16 l = __float2bfloat16_rn(r2);
+  t[0] = __bfloat16_as_ushort(h);
+  t[1] = __bfloat16_as_ushort(m);
+  t[2] = __bfloat16_as_ushort(l);
+}
+
+// 8 consecutive K elements of one operand row -> one 16-byte core-matrix row in each of
+// the 6 planes (term s, Re/Im) of a kRefChunk chunk.
+__device__ __forceinline__ void split3_store8(const float2* z, uint16_t* chunk, uint32_t off) {
+  uint32_t tr[8][3], ti[8][3];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int w = 0; w < 4; ++w) acc[u][w] = make_float2(0.f, 0.f);
-  for (int k0 = 0; k0 < N; k0 += 16) {
-    for (int x = threadIdx.x; x < 64 * 16; x += 256) {
-      const int r = x / 16, c = x - (x / 16) * 16;  // X tile: rows i0 + r, cols k0 + c
-      const T xv = X[(long long)(i0 + r) * N + k0 + c];
-      Xs[c][r] = make_float2((float)xv.x, (float)xv.y);
-      const int r2 = x / 64, c2 = x - (x / 64) * 64;  // R tile: rows k0 + r2, cols j0 + c2
-      const double2 z = Rb[(long long)(k0 + r2) * N + j0 + c2];
-      Rs[r2][c2] = make_float2((float)z.x, (float)z.y);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < 16; ++k) {
-      float2 a[4], bb[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = Xs[k][ty + 16 * u];
-#pragma unroll
-      for (int w = 0; w < 4; ++w) bb[w] = Rs[k][tx + 16 * w];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = cfma(a[u], bb[w], acc[u][w]);
-    }
-    __syncthreads();
+  for (int u = 0; u < 8; ++u) {
+    split3_bits(z[u].x, tr[u]);
+    split3_bits(z[u].y, ti[u]);
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int s = 0; s < 3; ++s) {
+    uint4 pr, pi;
+    pr.x = tr[0][s] | (tr[1][s] << 16); pr.y = tr[2][s] | (tr[3][s] << 16);
+    pr.z = tr[4][s] | (tr[5][s] << 16); pr.w = tr[6][s] | (tr[7][s] << 16);
+    pi.x = ti[0][s] | (ti[1][s] << 16); pi.y = ti[2][s] | (ti[3][s] << 16);
+    pi.z = ti[4][s] | (ti[5][s] << 16); pi.w = ti[6][s] | (ti[7][s] << 16);
+    *reinterpret_cast<uint4*>(chunk + (s * 2 + 0) * (128 * 16) + off) = pr;
+    *reinterpret_cast<uint4*>(chunk + (s * 2 + 1) * (128 * 16) + off) = pi;
+  }
+}
+
+// BF16x3 operand planes of a row-major FP32 complex matrix M[b][r][k] (rows r = the MMA's
+// M or N rows, k = reduction index): one kRefChunk chunk per (matrix, 128-row block,
+// 16-wide K step).  Thread mapping as in k_slice_A.
+__global__ void k_split3_rows(const float2* __restrict__ M, uint16_t* __restrict__ P, int N, long long n_total) {
+  const int NKS = N / 16, NRB = N / 128;
+  const long long n_thr = n_total / 8;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;
+    const int gp = (int)(w % 8); w /= 8;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int rb = (int)(w % NRB);
+    const long long b = w / NRB;
+    const int h = (lane >> 3) & 1;
+    const int rl = (lane & 7) + 8 * ((lane >> 4) + 2 * gp);
+    const float2* src = M + (b * N + rb * 128 + rl) * (long long)N + ks * 16 + 8 * h;
+    float2 z[8];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const long long o = b * (long long)N * N + (long long)(i0 + ty + 16 * u) * N + j0 + tx + 16 * w;
-      const T x0 = X0[o];
-      X1[o] = make_double2((double)x0.x + (double)acc[u][w].x, (double)x0.y + (double)acc[u][w].y);
+    for (int u = 0; u < 8; ++u) z[u] = src[u];
+    split3_store8(z, P + ((b * NRB + rb) * NKS + ks) * (long long)(kRefChunk / 2), kmajor_offset(128, rl, 8 * h) / 2);
+  }
+}
+
+// The same planes for the transpose: element M[b][k][r] goes to row r (for the B operand
+// of X R, whose rows are the columns of R).  Thread mapping as in k_slice_X.
+__global__ void k_split3_cols(const float2* __restrict__ M, uint16_t* __restrict__ P, int N, long long n_total) {
+  const int NKS = N / 16, NRB = N / 128;
+  const long long n_thr = n_total / 8;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;
+    const int gp = (int)(w % 8); w /= 8;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int rb = (int)(w % NRB);
+    const long long b = w / NRB;
+    const int h = (lane >> 3) & 1;
+    const int rl = (lane & 7) + 8 * ((lane >> 4) + 2 * gp);
+    const float2* src = M + (b * N + ks * 16 + 8 * h) * (long long)N + rb * 128 + rl;
+    float2 z[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) z[u] = src[(long long)u * N];
+    split3_store8(z, P + ((b * NRB + rb) * NKS + ks) * (long long)(kRefChunk / 2), kmajor_offset(128, rl, 8 * h) / 2);
+  }
+}
+
+// D = X R for one 128 x 128 tile per block (128 threads) on tcgen05, from the BF16x3
+// planes of X (A operand, rows i) and of R (B operand, rows j = columns of R): the six
+// term products with s + t <= 2 for each of Re = Xr Rr - Xi Ri and Im = Xr Ri + Xi Rr,
+// accumulated in FP32 in two 128-column tensor-memory accumulators.  R is small, so the
+// product is needed to 2^-24 of itself only.  kRefStages shared-memory stages; while step
+// ks runs, the stage of step ks - 1 is refilled with step ks - 1 + kRefStages.
+//   FINAL = false: lo[b] = D (X1 = X0 + lo is kept as the unevaluated FP32 pair)
+//   FINAL = true:  out[b] = hi + lo + D in FP64
+template <bool FINAL>
+__global__ void __launch_bounds__(128, 1)
+k_refine_tc(const uint16_t* __restrict__ PX, const uint16_t* __restrict__ PR, const float2* __restrict__ hi,
+            float2* __restrict__ lo, double2* __restrict__ out, int N, int* status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t full[kRefStages];
+  __shared__ __align__(8) uint64_t mmad[kRefStages];
+  const int jb = blockIdx.x, ib = blockIdx.y;
+  const long long b = blockIdx.z;
+  const int NKS = N / 16, NRB = N / 128;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 256);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kRefStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&mmad[s], 1);
     }
+    fence_mbar_init();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tm = tmem_base;
+  const unsigned char* Abase = reinterpret_cast<const unsigned char*>(PX) + ((b * NRB + ib) * NKS) * (long long)kRefChunk;
+  const unsigned char* Bbase = reinterpret_cast<const unsigned char*>(PR) + ((b * NRB + jb) * NKS) * (long long)kRefChunk;
+  constexpr uint32_t SB = 2 * kRefChunk;  // bytes per stage
+  constexpr uint32_t PL = 128 * 16 * 2;   // bytes per plane
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t id = idesc_bf16_f32(128, 128), idn = idesc_bf16_f32_negA(128, 128);
+    const uint32_t s0 = smem_u32(sm);
+    for (int s = 0; s < kRefStages && s < NKS; ++s) {
+      mbar_arrive_expect_tx(&full[s], SB);
+      bulk_g2s(sm + s * SB, Abase + (long long)s * kRefChunk, kRefChunk, &full[s]);
+      bulk_g2s(sm + s * SB + kRefChunk, Bbase + (long long)s * kRefChunk, kRefChunk, &full[s]);
+    }
+    for (int ks = 0; ks < NKS; ++ks) {
+      const int st = ks % kRefStages;
+      if (!mbar_wait(&full[st], (uint32_t)(ks / kRefStages) & 1u, kWaitNs, status)) { ok = false; break; }
+      fence_after_sync();
+      const uint64_t da0 = smem_desc(s0 + st * SB, 128, 256), db0 = smem_desc(s0 + st * SB + kRefChunk, 128, 256);
+      bool first = ks == 0;
+#pragma unroll
+      for (int sa = 0; sa < 3; ++sa) {
+#pragma unroll
+        for (int sb = 0; sb < 3; ++sb) {
+          if (sa + sb <= 2) {
+            const uint64_t dar = da0 + (uint64_t)(((sa * 2 + 0) * PL) >> 4), dai = da0 + (uint64_t)(((sa * 2 + 1) * PL) >> 4);
+            const uint64_t dbr = db0 + (uint64_t)(((sb * 2 + 0) * PL) >> 4), dbi = db0 + (uint64_t)(((sb * 2 + 1) * PL) >> 4);
+            const uint32_t acc = first ? 0u : 1u;
+            mma_bf16(tm, dar, dbr, id, acc);          // Re += Xr Rr
+            mma_bf16(tm, dai, dbi, idn, 1u);          // Re -= Xi Ri
+            mma_bf16(tm + 128, dar, dbi, id, acc);    // Im += Xr Ri
+            mma_bf16(tm + 128, dai, dbr, id, 1u);     // Im += Xi Rr
+            first = false;
+          }
+        }
+      }
+      mma_commit(&mmad[st]);
+      if (ks >= 1 && ks - 1 + kRefStages < NKS) {
+        const int so = (ks - 1) % kRefStages;
+        if (!mbar_wait(&mmad[so], (uint32_t)((ks - 1) / kRefStages) & 1u, kWaitNs, status)) { ok = false; break; }
+        const int kn = ks - 1 + kRefStages;
+        mbar_arrive_expect_tx(&full[so], SB);
+        bulk_g2s(sm + so * SB, Abase + (long long)kn * kRefChunk, kRefChunk, &full[so]);
+        bulk_g2s(sm + so * SB + kRefChunk, Bbase + (long long)kn * kRefChunk, kRefChunk, &full[so]);
+      }
+    }
+  }
+  const int last = NKS - 1;
+  const bool done = ok && mbar_wait(&mmad[last % kRefStages], (uint32_t)(last / kRefStages) & 1u, kWaitNs, status);
+  ok = __syncthreads_and(done ? 1 : 0) != 0;
+  fence_after_sync();
+  if (!ok) {
+    if (tid == 0) atomicExch(status, 2);
+  } else {
+    const int i = ib * 128 + 32 * warp + lane;
+    const long long row = (b * N + i) * (long long)N + jb * 128;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      float re[16], im[16];
+      tmem_ld16(tm + lane_base + (uint32_t)c0, re);
+      tmem_ld16(tm + lane_base + (uint32_t)(128 + c0), im);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const long long o = row + c0 + c;
+        if (FINAL) {
+          const float2 h = hi[o], l = lo[o];
+          out[o] = make_double2((double)h.x + (double)l.x + (double)re[c], (double)h.y + (double)l.y + (double)im[c]);
+        } else {
+          lo[o] = make_float2(re[c], im[c]);
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 256);
 }
 
 cudaError_t wtc_setup(size_t smem_gj32) {
-  cudaError_t e = raise_smem_limit(k_gj_inverse_blocked_f32, smem_gj32);
+  cudaError_t e = raise_smem_limit(k_gj_inverse_f32, smem_gj32);
   if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX0, kWL0>, w_residual_smem(kWSX0, kWL0));
   if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX1, kWLmax>, w_residual_smem(kWSX1, kWLmax));
+  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<false>, w_refine_smem());
+  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<true>, w_refine_smem());
   return e;
 }
 
@@ -546,17 +764,17 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
   const unsigned g8 = (unsigned)((t8 + 255) / 256 < 65535LL * 8 ? (t8 + 255) / 256 : 65535LL * 8);
   const dim3 gcol((unsigned)((N + 127) / 128), (unsigned)batch);
   const dim3 gres((unsigned)(N / kWTN), (unsigned)(N / 128), (unsigned)batch);
-  const dim3 gupd((unsigned)(N / 64), (unsigned)(N / 64), (unsigned)batch);
+  const dim3 gref((unsigned)(N / 128), (unsigned)(N / 128), (unsigned)batch);
   // X0: FP32 Gauss-Jordan
   {
     gw::TimedLaunch tl_("k_to_f32", st);
     k_to_f32<<<g1, 256, 0, st>>>(mats, w.X32, tot);
   }
   {
-    gw::TimedLaunch tl_("k_gj_inverse_blocked_f32", st);
-    k_gj_inverse_blocked_f32<<<batch, 512, smem_gj32, st>>>(w.X32, w.perm, N, NN, w.status);
+    gw::TimedLaunch tl_("k_gj_inverse_f32", st);
+    k_gj_inverse_f32<<<batch, 512, smem_gj32, st>>>(w.X32, N, NN, w.status);
   }
-  // slices of A (kept for both residuals)
+  // digits of A (kept for both residuals)
   {
     gw::TimedLaunch tl_("k_row_exponent", st);
     k_row_exponent<<<(unsigned)((batch * (long long)N + 7) / 8), 256, 0, st>>>(mats, w.eA, N, batch);
@@ -565,14 +783,14 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
     gw::TimedLaunch tl_("k_slice_A", st);
     k_slice_A<<<g8, 256, 0, st>>>(mats, w.eA, w.Asl, N, tot);
   }
-  // X1 = X0 + X0 (I - A X0)
+  // R0 = I - A X0 (FP32), lo = X0 R0: X1 = X0 + lo
   {
     gw::TimedLaunch tl_("k_col_exponent", st);
-    k_col_exponent<float2><<<gcol, 128, 0, st>>>(w.X32, w.eX, N);
+    k_col_exponent<<<gcol, 128, 0, st>>>(w.X32, nullptr, w.eX, N);
   }
   {
-    gw::TimedLaunch tl_("k_slice_X<float2>", st);
-    k_slice_X<float2, kWSX0><<<g8, 256, 0, st>>>(w.X32, w.eX, w.Xsl, N, tot);
+    gw::TimedLaunch tl_("k_slice_X", st);
+    k_slice_X<kWSX0><<<g8, 256, 0, st>>>(w.X32, nullptr, w.eX, w.Xsl, N, tot);
   }
   {
     gw::TimedLaunch tl_("k_ozaki_residual<first>", st);
@@ -580,17 +798,25 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
                                                                                   w.status);
   }
   {
-    gw::TimedLaunch tl_("k_refine_update<float2>", st);
-    k_refine_update<float2><<<gupd, 256, 0, st>>>(w.X32, w.R, w.X1, N);
+    gw::TimedLaunch tl_("k_split3_rows", st);
+    k_split3_rows<<<g8, 256, 0, st>>>(w.X32, w.PX, N, tot);
   }
-  // X2 = X1 + X1 (I - A X1), written over A
+  {
+    gw::TimedLaunch tl_("k_split3_cols", st);
+    k_split3_cols<<<g8, 256, 0, st>>>(w.R, w.Xsl, N, tot);  // the X digits are no longer needed
+  }
+  {
+    gw::TimedLaunch tl_("k_refine_tc<first>", st);
+    k_refine_tc<false><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, nullptr, N, w.status);
+  }
+  // R1 = I - A X1 (FP32), X2 = X1 + X0 R1 in FP64, written over A
   {
     gw::TimedLaunch tl_("k_col_exponent", st);
-    k_col_exponent<double2><<<gcol, 128, 0, st>>>(w.X1, w.eX, N);
+    k_col_exponent<<<gcol, 128, 0, st>>>(w.X32, w.lo, w.eX, N);
   }
   {
-    gw::TimedLaunch tl_("k_slice_X<double2>", st);
-    k_slice_X<double2, kWSX1><<<g8, 256, 0, st>>>(w.X1, w.eX, w.Xsl, N, tot);
+    gw::TimedLaunch tl_("k_slice_X", st);
+    k_slice_X<kWSX1><<<g8, 256, 0, st>>>(w.X32, w.lo, w.eX, w.Xsl, N, tot);
   }
   {
     gw::TimedLaunch tl_("k_ozaki_residual<second>", st);
@@ -598,8 +824,12 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
                                                                                       N, w.status);
   }
   {
-    gw::TimedLaunch tl_("k_refine_update<double2>", st);
-    k_refine_update<double2><<<gupd, 256, 0, st>>>(w.X1, w.R, mats, N);
+    gw::TimedLaunch tl_("k_split3_cols", st);
+    k_split3_cols<<<g8, 256, 0, st>>>(w.R, w.Xsl, N, tot);
+  }
+  {
+    gw::TimedLaunch tl_("k_refine_tc<final>", st);
+    k_refine_tc<true><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, mats, N, w.status);
   }
 }
 

@@ -432,6 +432,18 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   hp.Tf_inv = to_interleaved(Uf);
   hp.Tb_fwd = to_interleaved(Tb);
   hp.Tb_inv = to_interleaved(Ub);
+  // F(tau_{N-1-i}) = conj(F(tau_i)) pairs node i with its mirror: T F + T' conj(F) has the
+  // real part (Re T + Re T') Re F + (Im T' - Im T) Im F; the self-mirrored middle node of
+  // an odd grid keeps (Re T, -Im T).  The imaginary part vanishes for bosonic frequencies.
+  const int nh = (N + 1) / 2;
+  hp.Tb_mirror.assign((size_t)2 * hp.n_nu * nh, 0.0);
+  for (int m = 0; m < hp.n_nu; ++m)
+    for (int i = 0; i < nh; ++i) {
+      const cd t = Tb[(size_t)m * N + i], tm = Tb[(size_t)m * N + (N - 1 - i)];
+      const bool mid = (N - 1 - i) == i;
+      hp.Tb_mirror[2 * ((size_t)m * nh + i)] = mid ? t.real() : t.real() + tm.real();
+      hp.Tb_mirror[2 * ((size_t)m * nh + i) + 1] = mid ? -t.imag() : tm.imag() - t.imag();
+    }
   return GW_OK;
 }
 

@@ -24,24 +24,40 @@ __host__ __device__ constexpr size_t w_residual_smem(int SX, int lmax) {
   return 2 * (size_t)(wa_bytes(lmax) + wx_chunk(SX));
 }
 
-__global__ void k_gj_inverse_blocked_f32(float2* __restrict__ A, int* __restrict__ perm, int N, long long mat_stride,
-                                         int* status);
+constexpr int kGJ32B = 32;    // panel width of the FP32 Gauss-Jordan inverse
+constexpr int kGJ32C = 128;   // column chunk of its trailing update
+// float2 elements of the multi-use buffer (pivot rows, exchange staging, row copies)
+__host__ __device__ constexpr size_t gj32_buf_elems(int N) {
+  return (size_t)2 * kGJ32B * kGJ32C > (size_t)16 * N ? (size_t)2 * kGJ32B * kGJ32C : (size_t)16 * N;
+}
+// dynamic shared memory of k_gj_inverse_f32
+__host__ __device__ constexpr size_t gj32_smem(int N) {
+  return ((size_t)N * kGJ32B + gj32_buf_elems(N) + N + 2 * kGJ32B) * 8 + ((size_t)2 * N + 4 * kGJ32B) * 4;
+}
+__global__ void k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __restrict__ status);
 __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ dst, long long n);
 __global__ void k_row_exponent(const double2* __restrict__ A, int* __restrict__ eA, int N, int batch);
 
 __global__ void k_slice_A(const double2* __restrict__ A, const int* __restrict__ eA, uint16_t* __restrict__ Asl,
                           int N, long long n_total);
-// Scratch of one batch of tensor-core inverses (sizes per matrix: N^2 FP32 and three
-// N^2 FP64 arrays, 2 kWSA and 2 kWSX1 BF16 slices per element, 2 N exponents, N pivots).
+// Refinement products X R on the tensor cores: BF16x3 planes, 6 planes of 128 x 16 per
+// (128-row block, 16-wide K step) chunk, kRefStages pipeline stages of 2 chunks.
+constexpr uint32_t kRefChunk = 6 * 128 * 16 * 2;
+constexpr int kRefStages = 4;
+__host__ __device__ constexpr size_t w_refine_smem() { return (size_t)kRefStages * 2 * kRefChunk; }
+
+// Scratch of one batch of tensor-core inverses (per matrix: three N^2 FP32 complex
+// arrays, 2 kWSA and 2 kWSX1 BF16 digit planes and 6 BF16 term planes per element,
+// 2 N exponents).
 struct WtcBuffers {
-  float2* X32;
-  double2* X1;
-  double2* R;
-  uint16_t* Asl;
-  uint16_t* Xsl;
+  float2* X32;    // FP32 inverse X0 (the high part of X1)
+  float2* lo;     // X1 - X0
+  float2* R;      // residual I - A X (FP32)
+  uint16_t* Asl;  // digits of A
+  uint16_t* Xsl;  // digits of X, then the term planes of R
+  uint16_t* PX;   // term planes of X0
   int* eA;
   int* eX;
-  int* perm;
   int* status;
 };
 

@@ -26,13 +26,14 @@ _PREC = {"fp64": GW_FP64, "mixed": GW_MIXED}
 _STAT = {"F": GW_FERMION, "B": GW_BOSON, "fermion": GW_FERMION, "boson": GW_BOSON}
 _DIR = {"tau_to_iw": GW_TAU_TO_IW, "iw_to_tau": GW_IW_TO_TAU}
 _BLK = {"orb": GW_BLOCK_ORB, "pb": GW_BLOCK_PB}
+_STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
-    "gw_timing_enable", "gw_timing_read", "gw_timing_reset",
+    "gw_timing_enable", "gw_timing_read", "gw_timing_reset", "gw_transform_tau_iw_ex",
 ]
 
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_green_k_to_R.argtypes = [vp, vp, vp, vp]
     lib.gw_polarizability_tau.argtypes = [vp, vp, vp, C.c_int, vp]
     lib.gw_transform_tau_iw.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+    lib.gw_transform_tau_iw_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_screened_W_iw.argtypes = [vp, vp, vp, vp, vp]
     lib.gw_screened_W_iw_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.gw_self_energy_tau.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, vp]
@@ -266,14 +268,18 @@ class Plan:
                "gw_polarizability_tau")
         return P_R
 
-    def transform_tau_iw(self, stat: str, direction: str, kind: str, inp, out=None, stream=None):
+    def transform_tau_iw(self, stat: str, direction: str, kind: str, inp, out=None, stream=None,
+                         structure: str = "general"):
+        """gw_transform_tau_iw, or gw_transform_tau_iw_ex when `structure` is "mirror"
+        (input with F(beta - tau) = F(tau)*) or "real" (input with zero imaginary parts)."""
         nt = self.info["n_tau"]
         nf = self.info["n_omega"] if _STAT[stat] == GW_FERMION else self.info["n_nu"]
         n_in, n_out = (nt, nf) if _DIR[direction] == GW_TAU_TO_IW else (nf, nt)
         out = self._buf(out, self.len(kind, n_out), "out")
-        _check(self._lib.gw_transform_tau_iw(self._h, _STAT[stat], _DIR[direction], _BLK[kind],
-                                             self._in(inp, self.len(kind, n_in), "in"),
-                                             C.c_void_p(out.data_ptr()), self._stream(stream)), "gw_transform_tau_iw")
+        _check(self._lib.gw_transform_tau_iw_ex(self._h, _STAT[stat], _DIR[direction], _BLK[kind],
+                                                _STRUCT[structure], self._in(inp, self.len(kind, n_in), "in"),
+                                                C.c_void_p(out.data_ptr()), self._stream(stream)),
+               "gw_transform_tau_iw_ex")
         return out
 
     def screened_W_iw(self, P_R_iw, v_q, Wt_R_iw=None, stream=None):

@@ -133,6 +133,29 @@ def test_transform(name, st, direction, kind):
     assert rel(out, pack(ref)) < TOL
 
 
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5", "c1"])
+def test_transform_structured_inputs(name):
+    """gw_transform_tau_iw_ex: P(R, tau) with P(beta - tau) = P(tau)* (symmetric C) through
+    the mirror-paired bosonic transform, and a real W~(R, i nu) through the real-input
+    inverse, against the oracle's general transform."""
+    s = system(name)
+    assert s.plan.info["c_symmetric"] == 1
+    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    ref = oracle.transform(s.orc.B_fwd, PR)
+    out = host(s.plan.transform_tau_iw("B", "tau_to_iw", "pb", dev(pack(PR)), structure="mirror"))
+    assert rel(out, pack(ref)) < TOL
+    assert np.all(out.imag == 0.0)
+    rng = np.random.default_rng(11)
+    nn = s.cell.nu_idx.size
+    Wr = [rng.standard_normal((nn,) + blk.shape[1:]) + 0j for blk in PR]
+    ref = oracle.transform(s.orc.B_inv, Wr)
+    out = host(s.plan.transform_tau_iw("B", "iw_to_tau", "pb", dev(pack(Wr)), structure="real"))
+    assert rel(out, pack(ref)) < TOL
+    from paper_1911_05633_gb300 import gw
+    with pytest.raises(gw.GwError):
+        s.plan.transform_tau_iw("F", "tau_to_iw", "orb", dev(pack(s.G_R())), structure="mirror")
+
+
 @pytest.mark.parametrize("name", SMALL + ["c0_nosym", "c1_cut5_gj"])
 def test_screened_W(name):
     s = system(name)
@@ -214,9 +237,11 @@ def test_whole_sweep(name):
     r = s.orc.sweep(s.G_k, s.v_q, s.v_class)
     GR = p.green_k_to_R(dev(s.G_k))
     PR = p.polarizability_tau(GR)
-    Piw = p.transform_tau_iw("B", "tau_to_iw", "pb", PR)
+    # the structured transforms where the plan's symmetries provide them (as bench.py runs)
+    inf = p.info
+    Piw = p.transform_tau_iw("B", "tau_to_iw", "pb", PR, structure="mirror" if inf["c_symmetric"] else "general")
     Wiw = p.screened_W_iw(Piw, dev(s.v_q))
-    WR = p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw)
+    WR = p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw, structure="real" if inf["w_symmetric"] else "general")
     vR = p.fourier_k_to_R("pb", 1, dev(s.v_q))
     Sig, Sigx = p.self_energy_tau(GR, WR, v_R=vR)
     Siw = p.transform_tau_iw("F", "tau_to_iw", "orb", Sig)
