@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="the small profiling case instead of the bench workload")
     return ap.parse_args()
 
 
@@ -81,10 +82,14 @@ def max_over_ranks(x, world):
 # workload and its algorithmic work
 # --------------------------------------------------------------------------------------
 
-def workload(cfg: int):
+def workload(cfg: int, small: bool = False):
+    """The bench workload, or with `small` the 8-atom cell on a 2x2x2 mesh with 12 tau
+    nodes and a 5-bohr cutoff (N_PB = 384, 64 W-solve matrices): a case small enough for
+    full ncu captures of single kernels."""
     import synth
-    cell = synth.make_config(cfg)
-    return cell
+    if small:
+        return synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2))
+    return synth.make_config(cfg)
 
 
 def contraction_flops(cell, entries) -> float:
@@ -294,7 +299,7 @@ def flush_l2(buf):
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
-    cell = workload(args.config)
+    cell = workload(args.config, args.small)
     sw = Sweep(cell, args.precision, device=local)
     Gk = cell.green_k_tau()
     vq, _ = cell.coulomb()
@@ -493,7 +498,7 @@ def cpu_cores():
 
 
 def run_reference(args, rank, world):
-    cell = workload(args.config)
+    cell = workload(args.config, args.small)
     if rank != 0:
         return None
     secs = []

@@ -213,8 +213,8 @@ using namespace umma;
 
 constexpr uint64_t kWaitNs = 500ull * 1000ull * 1000ull;
 
-// scale exponent e with max |x| < 2^e (0 for an all-zero row / column)
-__device__ __forceinline__ int scale_exponent(double m) { return m > 0.0 ? ilogb(m) + 1 : 0; }
+__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+__device__ __forceinline__ int exp_field(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
 
 }  // namespace
 
@@ -225,45 +225,70 @@ __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ d
   }
 }
 
-// one warp per row: eA[b][i] with max_k max(|Re|, |Im|) A[b][i][k] < 2^eA
+// Scale exponents e with |x| < 2^e for every entry of a row of A (FP64) or of a column
+// of X (FP32, or the unevaluated pair hi + lo), from the exponent fields alone: a normal
+// x of biased exponent E has |x| < 2^(E - bias + 1).  0 for an all-zero row or column
+// (subnormal entries count as zero).
+
+// one warp per row
 __global__ void k_row_exponent(const double2* __restrict__ A, int* __restrict__ eA, int N, int batch) {
   const int warps = blockDim.x >> 5;
   const long long row = (long long)blockIdx.x * warps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= (long long)batch * N) return;
   const double2* a = A + row * N;
-  double m = 0.0;
-  for (int k = lane; k < N; k += 32) m = fmax(m, fmax(fabs(a[k].x), fabs(a[k].y)));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) eA[row] = scale_exponent(m);
+  int m = 0;
+  for (int k = lane; k < N; k += 32) m = max(m, max(exp_field(a[k].x), exp_field(a[k].y)));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) eA[row] = m > 0 ? m - 1022 : 0;
 }
 
-// one thread per column j: eX[b][j] with max_k max(|Re|, |Im|) (hi + lo)[b][k][j] < 2^eX
-// (lo may be null); |hi| + |lo| bounds |hi + lo| from above
+// one thread per column j (lo may be null): |hi|, |lo| < 2^(m - 126), so |hi + lo| < 2^(m - 125)
 __global__ void k_col_exponent(const float2* __restrict__ hi, const float2* __restrict__ lo, int* __restrict__ eX,
                                int N) {
   const int b = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
   const long long base = (long long)b * N * N + j;
-  double m = 0.0;
+  int m = 0;
   for (int k = 0; k < N; ++k) {
     const float2 h = hi[base + (long long)k * N];
-    const float2 l = lo ? lo[base + (long long)k * N] : make_float2(0.0f, 0.0f);
-    m = fmax(m, fmax(fabs((double)h.x) + fabs((double)l.x), fabs((double)h.y) + fabs((double)l.y)));
+    m = max(m, max(exp_field(h.x), exp_field(h.y)));
+    if (lo) {
+      const float2 l = lo[base + (long long)k * N];
+      m = max(m, max(exp_field(l.x), exp_field(l.y)));
+    }
   }
-  eX[(long long)b * N + j] = scale_exponent(m);
+  eX[(long long)b * N + j] = m > 0 ? m - (lo ? 125 : 126) : 0;
+}
+
+// round(x 2^(56 - e)) for |x| < 2^e as a 64-bit integer, from the bits of x: the
+// significand shifted by its exponent relative to 2^(e - 56), rounded half up when
+// shifted right.  |result| < 2^56; subnormal x gives 0.
+__device__ __forceinline__ long long shift_round(long long m, int sh) {
+  if (sh >= 0) return m << sh;
+  if (sh > -63) return (m + (1ll << (-sh - 1))) >> (-sh);
+  return 0;
+}
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long r = shift_round((long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull), E - 1019 - e);  // <= 3
+  return (u >> 63) ? -r : r;
+}
+__device__ __forceinline__ long long fixed56(float x, int e) {
+  const uint32_t u = __float_as_uint(x);
+  const int E = (int)((u >> 23) & 0xFF);
+  if (E == 0) return 0;
+  const long long r = shift_round((long long)((u & 0x7FFFFFu) | 0x800000u), E - 94 - e);  // <= 32
+  return (u >> 31) ? -r : r;
 }
 
 // Signed base-2^7 digits of one scaled entry: m = round(v 2^56) for |v| < 1, then
 // digit s = round(m / 2^(49 - 7 s)) taken from the top, so that v = sum_s d_s 2^-7(s+1)
 // up to 2^-57 with |d_0| <= 128 and |d_s| <= 64 after it; every d_s 2^-7(s+1) is exact
-// in BF16 (at most 8 significant bits).  Integer arithmetic only after one FP64 scaling.
-__device__ __forceinline__ long long fixed56(double x, int e) {
-  // x 2^(56 - e) with |x| < 2^e; the power of two is built from its exponent bits
-  const double p = __longlong_as_double((long long)(1023 + 56 - e) << 52);
-  return __double2ll_rn(x * p);
-}
+// in BF16 (at most 8 significant bits).
 __device__ __forceinline__ int next_digit(long long& m, int s) {
   const int sh = 49 - 7 * s;
   const long long d = sh > 0 ? (m + (1ll << (sh - 1))) >> sh : m;
@@ -276,11 +301,12 @@ __device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
   return __float_as_uint((float)d * sc) >> 16;
 }
 
-// A operand slices.  Element (i, k) of matrix b -> kWSA digits of Re and Im in the
-// K-major tile layout, one contiguous chunk per (matrix, 128-row block, 16-column step)
-// holding 2 kWSA planes of 128 x 16.  One thread per (row i, 8 consecutive k): it reads
-// 128 contiguous bytes and writes one 16-byte row of a core matrix per plane; the 32
-// lanes of a warp (i % 8, k half, (i / 8) % 2) fill 512 contiguous bytes of each plane.
+// A operand digits.  Element (i, k) of matrix b -> kWSA digits of Re and of Im in the
+// K-major tile layout, one chunk per (matrix, 128-row block, 16-wide K step) holding
+// the 2 kWSA planes of 128 x 16 in the order (Re digits 0 .. kWSA-1, Im digits ...).
+// One thread per (row i, 8 consecutive k): it reads 128 contiguous bytes and writes one
+// 16-byte row of a core matrix per plane; the 32 lanes of a warp (i % 8, k half,
+// (i / 8) % 2) fill 512 contiguous bytes of each plane.
 __global__ void k_slice_A(const double2* __restrict__ A, const int* __restrict__ eA, uint16_t* __restrict__ Asl,
                           int N, long long n_total) {
   const int NKS = N / 16, NIB = N / 128;
@@ -317,32 +343,33 @@ __global__ void k_slice_A(const double2* __restrict__ A, const int* __restrict__
         pr[u] = r0 | (r1 << 16);
         pi[u] = i0 | (i1 << 16);
       }
-      *reinterpret_cast<uint4*>(chunk + (s * 2 + 0) * (128 * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-      *reinterpret_cast<uint4*>(chunk + (s * 2 + 1) * (128 * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+      *reinterpret_cast<uint4*>(chunk + (0 * kWSA + s) * (128 * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (1 * kWSA + s) * (128 * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
     }
   }
 }
 
-// X operand slices.  Element X[k][j] = hi + lo of matrix b (k = reduction index; lo may
-// be null) -> SX digits of Re and Im in the K-major layout of the B operand (rows j), one
-// chunk per (matrix, kWTN-column block, 16-row step).  One thread per (column j, 8 consecutive k); lanes
-// (j % 8, k half, (j / 8) % 2) read 128-byte row segments and fill 512 contiguous bytes
-// of each plane.
+// X operand digits.  Element X[k][j] = hi + lo of matrix b (k = reduction index; lo may
+// be null) -> SX digits of Re and of Im in the K-major layout of the B operand (rows j),
+// one chunk per (matrix, kWTN-column block, 16-wide K step) holding the 2 SX planes of
+// kWTN x 16 in the order (Re digits, Im digits).  One thread per (column j, 8
+// consecutive k); lanes (j % 8, k half, (j / 8) % 2) read 128-byte row segments and fill
+// 512 contiguous bytes of each plane.
 template <int SX>
 __global__ void k_slice_X(const float2* __restrict__ hi, const float2* __restrict__ lo, const int* __restrict__ eX,
                           uint16_t* __restrict__ Xsl, int N, long long n_total) {
-  static_assert(kWTN == 32, "two 16-column halves per column block");
+  constexpr int JG = kWTN / 16;  // 16-column groups per block
   const int NKS = N / 16, NJB = N / kWTN;
   const long long n_thr = n_total / 8;
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
     const int lane = (int)(x & 31);
-    long long w = x >> 5;  // (b, jb, ks, column half)
-    const int jh = (int)(w & 1); w >>= 1;
+    long long w = x >> 5;  // (b, jb, ks, column group)
+    const int jg = (int)(w % JG); w /= JG;
     const int ks = (int)(w % NKS); w /= NKS;
     const int jb = (int)(w % NJB);
     const long long b = w / NJB;
     const int h = (lane >> 3) & 1;
-    const int jl = (lane & 7) + 8 * ((lane >> 4) + 2 * jh);  // column within the block
+    const int jl = (lane & 7) + 8 * ((lane >> 4) + 2 * jg);  // column within the block
     const int j = jb * kWTN + jl;
     const int k0 = ks * 16 + 8 * h;
     const int e = eX[b * N + j];
@@ -351,12 +378,12 @@ __global__ void k_slice_X(const float2* __restrict__ hi, const float2* __restric
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float2 z = hi[o0 + (long long)u * N];
-      mr[u] = fixed56((double)z.x, e);
-      mi[u] = fixed56((double)z.y, e);
+      mr[u] = fixed56(z.x, e);
+      mi[u] = fixed56(z.y, e);
       if (lo) {  // each part rounds to 2^-56 of the column scale
         const float2 l = lo[o0 + (long long)u * N];
-        mr[u] += fixed56((double)l.x, e);
-        mi[u] += fixed56((double)l.y, e);
+        mr[u] += fixed56(l.x, e);
+        mi[u] += fixed56(l.y, e);
       }
     }
     uint16_t* chunk = Xsl + ((b * NJB + jb) * NKS + ks) * (long long)(wx_chunk(SX) / 2);
@@ -371,8 +398,8 @@ __global__ void k_slice_X(const float2* __restrict__ hi, const float2* __restric
         pr[u] = r0 | (r1 << 16);
         pi[u] = i0 | (i1 << 16);
       }
-      *reinterpret_cast<uint4*>(chunk + (t * 2 + 0) * (kWTN * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-      *reinterpret_cast<uint4*>(chunk + (t * 2 + 1) * (kWTN * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+      *reinterpret_cast<uint4*>(chunk + (0 * SX + t) * (kWTN * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (1 * SX + t) * (kWTN * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
     }
   }
 }
@@ -394,75 +421,76 @@ __device__ __forceinline__ long long level_units52(float v, int q) {
   }
 }
 
-// Accumulator (columns q kWTN) of the products a_s x_t, s + t = L: Re 0..7, Im 8..15;
-// `neg` selects Ai Xi (subtracted from Re), `imag` the Im products.
-__host__ __device__ constexpr int ozaki_bucket(int L, bool second_type, bool imag) {
-  return (imag ? 8 : 0) + (L <= 2 ? L : L == 3 ? (second_type ? 4 : 3) : L == 4 ? (second_type ? 6 : 5) : 7);
+// The residual as a real product of twice the length: the Re rows of A X are
+// [Ar, -Ai] [Xr; Xi] and the Im rows [Ai, Ar] [Xr; Xi], so one output row (Re or Im)
+// accumulates over 2N terms from one digit plane of A and one of X per 16-wide K step
+// (-Ai through the negate-A bit of the instruction descriptor).  The products a_s x_t of
+// level L = s + t go to accumulator q(L, half): levels 0, 1, 2 each one accumulator over
+// both halves of K (<= 2 N terms), levels 3 and 4 one accumulator per half (<= N terms),
+// levels >= 5 one accumulator.
+__host__ __device__ constexpr int ozaki_bucket(int L, int half) {
+  return L <= 2 ? L : L == 3 ? 3 + half : L == 4 ? 5 + half : 7;
 }
 
-// The 4 x (number of (s, t) pairs) MMAs of one 16-wide K step.  Fully unrolled, so the
-// accumulator indices, shared-memory offsets and first-use flags are constants.
-template <int SX, int LMAX, bool FIRST>
-__device__ __forceinline__ void ozaki_issue_step(uint32_t tm, uint64_t da0, uint64_t dx0, uint32_t id, uint32_t idn) {
+// The MMAs of one 16-wide K step, fully unrolled.  `fresh` marks the accumulators whose
+// first product of the whole K loop is in this step (written, not added).
+template <int SX, int NA, int LMAX>
+__device__ __forceinline__ void ozaki_issue_step(uint32_t tm, uint64_t da0, uint64_t dx0, uint32_t id, int half,
+                                                 uint32_t fresh) {
   constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;  // bytes per A / X plane
   uint32_t used = 0;
 #pragma unroll
   for (int t = 0; t < SX; ++t) {
 #pragma unroll
-    for (int s = 0; s < kWSA; ++s) {
+    for (int s = 0; s < NA; ++s) {
       if (s + t <= LMAX) {
-        const int L = s + t;
-        const int r1 = ozaki_bucket(L, false, false), r2 = ozaki_bucket(L, true, false);
-        const int i1 = ozaki_bucket(L, false, true), i2 = ozaki_bucket(L, true, true);
+        const int q = ozaki_bucket(s + t, half);
+        const uint32_t acc = (((fresh & ~used) >> q) & 1u) ? 0u : 1u;
+        used |= 1u << q;
         // descriptor start addresses are in 16-byte units in the low bits
-        const uint64_t dar = da0 + (uint64_t)(((s * 2 + 0) * PA) >> 4);
-        const uint64_t dai = da0 + (uint64_t)(((s * 2 + 1) * PA) >> 4);
-        const uint64_t dxr = dx0 + (uint64_t)(((t * 2 + 0) * PX) >> 4);
-        const uint64_t dxi = dx0 + (uint64_t)(((t * 2 + 1) * PX) >> 4);
-        // Re += Ar Xr - Ai Xi ; Im += Ar Xi + Ai Xr
-        mma_bf16(tm + (uint32_t)r1 * kWTN, dar, dxr, id, FIRST ? (used >> r1) & 1u : 1u);
-        used |= 1u << r1;
-        mma_bf16(tm + (uint32_t)r2 * kWTN, dai, dxi, idn, FIRST ? (used >> r2) & 1u : 1u);
-        used |= 1u << r2;
-        mma_bf16(tm + (uint32_t)i1 * kWTN, dar, dxi, id, FIRST ? (used >> i1) & 1u : 1u);
-        used |= 1u << i1;
-        mma_bf16(tm + (uint32_t)i2 * kWTN, dai, dxr, id, FIRST ? (used >> i2) & 1u : 1u);
-        used |= 1u << i2;
+        mma_bf16(tm + (uint32_t)q * kWTN, da0 + (uint64_t)((s * PA) >> 4), dx0 + (uint64_t)((t * PX) >> 4), id, acc);
       }
     }
   }
 }
 
-// R[b] = I - A[b] X[b] for one 128 x kWTN output tile per block (128 threads), from the
-// A slices s <= LMAX and SX slices of X, products with s + t <= LMAX.  Sixteen FP32
-// accumulators of kWTN columns fill the 512 tensor-memory columns: for Re and Im, the
-// levels 0, 1, 2 (both product types together), levels 3 and 4 (one accumulator per
-// product type) and the levels >= 5.  Two shared-memory stages: while the products of
-// K step ks run, the stage of step ks - 1 is refilled with step ks + 1.
+// R[b] = I - A[b] X[b] for one block of 128 output rows (Re rows for blockIdx.y < N/128,
+// else Im rows) x kWTN columns per block (128 threads), from the A digits s <= LMAX and
+// SX digits of X, products with s + t <= LMAX.  Eight FP32 accumulators of kWTN columns
+// fill the 512 tensor-memory columns.  kWStages shared-memory stages; while step kk runs,
+// the stage of step kk - 1 is refilled with step kk - 1 + kWStages.  The epilogue adds all
+// levels and the identity as one exact 64-bit integer in units of 2^-52 (the levels
+// cancel each other, so they are combined before any rounding), then rounds once to FP32
+// (R is small; FP32 keeps it to 2^-24 of itself) into the Re or Im part of R.
 template <int SX, int LMAX>
 __global__ void __launch_bounds__(128, 1)
 k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ Xsl, const int* __restrict__ eA,
                  const int* __restrict__ eX, float2* __restrict__ R, int N, int* status) {
-  static_assert(LMAX >= 5 && LMAX < kWSA, "every accumulator receives a product; A has kWSA slices");
+  static_assert(LMAX >= 5 && LMAX < kWSA, "every accumulator receives a product; A has kWSA digits");
+  constexpr int NA = LMAX + 1;                            // A digits used
+  constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;
+  constexpr uint32_t AB = NA * PA, XB = SX * PX, SB = AB + XB;  // bytes per stage
   constexpr uint32_t XC = wx_chunk(SX);
-  constexpr uint32_t AC = wa_bytes(LMAX);  // the leading planes s <= LMAX of each A chunk
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t full[2];
-  __shared__ __align__(8) uint64_t mmad[2];
-  const int jb = blockIdx.x, ib = blockIdx.y;
-  const long long b = blockIdx.z;
+  __shared__ __align__(8) uint64_t full[kWStages];
+  __shared__ __align__(8) uint64_t mmad[kWStages];
+  const int jb = blockIdx.x;
   const int NKS = N / 16, NIB = N / 128, NJB = N / kWTN;
+  const bool imrow = (int)blockIdx.y >= NIB;
+  const int ib = imrow ? (int)blockIdx.y - NIB : (int)blockIdx.y;
+  const long long b = blockIdx.z;
+  const int NK2 = 2 * NKS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&mmad[0], 1);
-    mbar_init(&mmad[1], 1);
+    for (int s = 0; s < kWStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&mmad[s], 1);
+    }
     fence_mbar_init();
   }
   fence_before_sync();
@@ -471,41 +499,41 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
   const uint32_t tm = tmem_base;
   const unsigned char* Abase = reinterpret_cast<const unsigned char*>(Asl) + ((b * NIB + ib) * NKS) * (long long)kWAChunk;
   const unsigned char* Xbase = reinterpret_cast<const unsigned char*>(Xsl) + ((b * NJB + jb) * NKS) * (long long)XC;
-  unsigned char* const stage0 = sm;
-  unsigned char* const stage1 = sm + AC + XC;
+  // step kk: half 0 takes (Ar | Ai for Im rows) with Xr, half 1 (Ai negated | Ar) with Xi
+  auto load = [&](int kk, int st) {
+    const int half = kk >= NKS ? 1 : 0, ks = kk - half * NKS;
+    const int cA = imrow ? 1 - half : half;
+    unsigned char* dst = sm + st * SB;
+    mbar_arrive_expect_tx(&full[st], SB);
+    bulk_g2s(dst, Abase + (long long)ks * kWAChunk + (long long)cA * kWSA * PA, AB, &full[st]);
+    bulk_g2s(dst + AB, Xbase + (long long)ks * XC + (long long)half * SX * PX, XB, &full[st]);
+  };
   bool ok = true;
   if (tid == 0) {
     const uint32_t id = idesc_bf16_f32(128, kWTN), idn = idesc_bf16_f32_negA(128, kWTN);
-    const uint64_t da0 = smem_desc(smem_u32(stage0), 128, 256), da1 = smem_desc(smem_u32(stage1), 128, 256);
-    const uint64_t dx0 = smem_desc(smem_u32(stage0) + AC, 128, 256), dx1 = smem_desc(smem_u32(stage1) + AC, 128, 256);
-    for (int s = 0; s < 2 && s < NKS; ++s) {
-      unsigned char* const dst = s ? stage1 : stage0;
-      mbar_arrive_expect_tx(&full[s], AC + XC);
-      bulk_g2s(dst, Abase + (long long)s * kWAChunk, AC, &full[s]);
-      bulk_g2s(dst + AC, Xbase + (long long)s * XC, XC, &full[s]);
-    }
-    for (int ks = 0; ks < NKS; ++ks) {
-      const int st = ks & 1;
-      if (!mbar_wait(&full[st], (uint32_t)(ks >> 1) & 1u, kWaitNs, status)) { ok = false; break; }
+    const uint32_t s0 = smem_u32(sm);
+    for (int s = 0; s < kWStages && s < NK2; ++s) load(s, s);
+    for (int kk = 0; kk < NK2; ++kk) {
+      const int st = kk % kWStages;
+      if (!mbar_wait(&full[st], (uint32_t)(kk / kWStages) & 1u, kWaitNs, status)) { ok = false; break; }
       fence_after_sync();
-      const uint64_t da = st ? da1 : da0, dx = st ? dx1 : dx0;
-      if (ks == 0) ozaki_issue_step<SX, LMAX, true>(tm, da, dx, id, idn);
-      else ozaki_issue_step<SX, LMAX, false>(tm, da, dx, id, idn);
+      const int half = kk >= NKS ? 1 : 0;
+      // first products: every accumulator at kk = 0, the second-half ones of levels 3, 4 at kk = NKS
+      const uint32_t fresh = kk == 0 ? 0xFFu : (kk == NKS ? ((1u << 4) | (1u << 6)) : 0u);
+      ozaki_issue_step<SX, NA, LMAX>(tm, smem_desc(s0 + st * SB, 128, 256), smem_desc(s0 + st * SB + AB, 128, 256),
+                                     (!imrow && half) ? idn : id, half, fresh);
       mma_commit(&mmad[st]);
-      if (ks >= 1 && ks + 1 < NKS) {
-        // the products of step ks - 1 are done once its commit arrives: refill its stage
-        const int so = st ^ 1;
-        if (!mbar_wait(&mmad[so], (uint32_t)((ks - 1) >> 1) & 1u, kWaitNs, status)) { ok = false; break; }
-        unsigned char* const dst = so ? stage1 : stage0;
-        mbar_arrive_expect_tx(&full[so], AC + XC);
-        bulk_g2s(dst, Abase + (long long)(ks + 1) * kWAChunk, AC, &full[so]);
-        bulk_g2s(dst + AC, Xbase + (long long)(ks + 1) * XC, XC, &full[so]);
+      if (kk >= 1 && kk - 1 + kWStages < NK2) {
+        // the products of step kk - 1 are done once its commit arrives: refill its stage
+        const int so = (kk - 1) % kWStages;
+        if (!mbar_wait(&mmad[so], (uint32_t)((kk - 1) / kWStages) & 1u, kWaitNs, status)) { ok = false; break; }
+        load(kk - 1 + kWStages, so);
       }
     }
   }
   // every thread waits for the last products; one verdict for the block
-  const int last = NKS - 1;
-  const bool done = ok && mbar_wait(&mmad[last & 1], (uint32_t)(last >> 1) & 1u, kWaitNs, status);
+  const int last = NK2 - 1;
+  const bool done = ok && mbar_wait(&mmad[last % kWStages], (uint32_t)(last / kWStages) & 1u, kWaitNs, status);
   ok = __syncthreads_and(done ? 1 : 0) != 0;
   fence_after_sync();
   if (!ok) {
@@ -514,39 +542,32 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
     const int r = 32 * warp + lane;
     const int i = ib * 128 + r;
     const int ea = eA[b * N + i];
-    float2* Ro = R + (b * N + i) * (long long)N;
+    float* Ro = reinterpret_cast<float*>(R + (b * N + i) * (long long)N) + (imrow ? 1 : 0);
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     bool range_ok = true;
     for (int c0 = 0; c0 < kWTN; c0 += 16) {
-      // all levels as one exact 64-bit integer in units of 2^-52 (the levels cancel
-      // each other, so they are combined before any rounding), the identity subtracted
-      // in the same units, then one rounding to FP32: R is small and FP32 keeps it to
-      // 2^-24 of itself
-      long long sr[16], si[16];
+      long long sum[16];
       float v[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) { sr[c] = 0; si[c] = 0; }
+      for (int c = 0; c < 16; ++c) sum[c] = 0;
 #pragma unroll 1
-      for (int q = 0; q <= 7; ++q) {
+      for (int q = 0; q < 8; ++q) {
         tmem_ld16(tm + lane_base + (uint32_t)(q * kWTN + c0), v);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) sr[c] += level_units52(v[c], q);
-        tmem_ld16(tm + lane_base + (uint32_t)((8 + q) * kWTN + c0), v);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) si[c] += level_units52(v[c], q);
+        for (int c = 0; c < 16; ++c) sum[c] += level_units52(v[c], q);
       }
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int j = jb * kWTN + c0 + c;
         const int e = ea + eX[b * N + j];  // (A X)_ij = 2^e sum
-        long long re = sr[c];
-        if (i == j) {
+        long long val = sum[c];
+        if (!imrow && i == j) {
           if (e < -10 || e > 52) range_ok = false;
-          else re -= 1ll << (52 - e);  // 1 = 2^(52 - e) units of 2^(e - 52)
+          else val -= 1ll << (52 - e);  // 1 = 2^(52 - e) units of 2^(e - 52)
         }
         if (e < -126 || e > 126) range_ok = false;
         const float sc = __int_as_float((127 + min(max(e, -126), 126)) << 23);  // 2^e
-        Ro[j] = make_float2(-sc * ((float)re * 0x1p-52f), -sc * ((float)si[c] * 0x1p-52f));
+        Ro[2 * (long long)j] = -sc * ((float)val * 0x1p-52f);
       }
     }
     if (!range_ok) atomicExch(status, 4);  // scale outside the FP32 exponent range
@@ -763,7 +784,7 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
   const long long t8 = tot / 8;  // slicing threads: one per 8 consecutive elements
   const unsigned g8 = (unsigned)((t8 + 255) / 256 < 65535LL * 8 ? (t8 + 255) / 256 : 65535LL * 8);
   const dim3 gcol((unsigned)((N + 127) / 128), (unsigned)batch);
-  const dim3 gres((unsigned)(N / kWTN), (unsigned)(N / 128), (unsigned)batch);
+  const dim3 gres((unsigned)(N / kWTN), (unsigned)(2 * (N / 128)), (unsigned)batch);  // Re rows, then Im rows
   const dim3 gref((unsigned)(N / 128), (unsigned)(N / 128), (unsigned)batch);
   // X0: FP32 Gauss-Jordan
   {

@@ -12,16 +12,15 @@ constexpr int kWSX0 = 5;     // slices of the FP32 first inverse
 constexpr int kWL0 = 5;      // first residual: products a_s x_t with s + t <= kWL0
 constexpr int kWSX1 = 8;     // slices of the once-refined FP64 inverse
 constexpr int kWLmax = 7;    // second residual: products a_s x_t with s + t <= kWLmax
-constexpr int kWTN = 32;     // output columns per residual block
+constexpr int kWTN = 64;     // output columns per residual block
 constexpr int kWNmax = 384;  // largest N whose level sums stay exact in FP32
-constexpr uint32_t kWAChunk = kWSA * 2 * 128 * 16 * 2;  // bytes per (row block, K step)
-// bytes of the A planes s <= lmax (the leading part of a chunk)
-__host__ __device__ constexpr uint32_t wa_bytes(int lmax) {
-  return (uint32_t)((lmax + 1 < kWSA ? lmax + 1 : kWSA) * 2 * 128 * 16 * 2);
-}
+constexpr int kWStages = 4;  // shared-memory stages of the residual
+constexpr uint32_t kWAChunk = kWSA * 2 * 128 * 16 * 2;  // bytes per (row block, K step): Re then Im digits
 __host__ __device__ constexpr uint32_t wx_chunk(int SX) { return (uint32_t)SX * 2 * kWTN * 16 * 2; }
+// dynamic shared memory of the residual: per stage the A digits s <= lmax of one
+// component (128 x 16 each) and the SX digits of one component of X (kWTN x 16 each)
 __host__ __device__ constexpr size_t w_residual_smem(int SX, int lmax) {
-  return 2 * (size_t)(wa_bytes(lmax) + wx_chunk(SX));
+  return (size_t)kWStages * ((size_t)(lmax + 1) * 128 * 16 * 2 + (size_t)SX * kWTN * 16 * 2);
 }
 
 constexpr int kGJ32B = 32;    // panel width of the FP32 Gauss-Jordan inverse
