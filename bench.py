@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="the small profiling case instead of the bench workload")
+    ap.add_argument("--w-solver", default="auto", choices=["auto", "gauss_jordan"],
+                    help="inverse of the W solve: tensor-core refinement where supported, or FP64 Gauss-Jordan")
     return ap.parse_args()
 
 
@@ -211,13 +213,13 @@ class Sweep:
     STAGES = ["G_k_to_R", "P", "P_tau_to_nu", "W_solve", "W_nu_to_tau", "v_k_to_R", "Sigma", "Sigma_tau_to_omega",
               "Sigma_R_to_k"]
 
-    def __init__(self, cell, precision: str, device: int = 0):
+    def __init__(self, cell, precision: str, device: int = 0, w_solver: str = "auto"):
         import torch
         from paper_1911_05633_gb300 import gw
         self.torch = torch
         self.cell = cell
         self.prec = precision
-        self.plan = gw.Plan.from_cell(cell, device=device)
+        self.plan = gw.Plan.from_cell(cell, device=device, w_solver=w_solver)
         p = self.plan
         inf = p.info
         self.dev = torch.device("cuda", device)
@@ -300,7 +302,7 @@ def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
     cell = workload(args.config, args.small)
-    sw = Sweep(cell, args.precision, device=local)
+    sw = Sweep(cell, args.precision, device=local, w_solver=args.w_solver)
     Gk = cell.green_k_tau()
     vq, _ = cell.coulomb()
     sw.load_inputs(Gk, vq)
@@ -403,6 +405,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": cell.name + f": {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k,"
                    f" {cell.n_tau} tau, cutoff {cell.cutoff} bohr, {len(ent)} pair entries",
                    "precision": args.precision, "l2": "256 MB buffer written between timed steps",
+                   "w_inverse": ("FP32 Gauss-Jordan + two residual refinements on the tensor cores (FP64-accurate)"
+                                 if inf["w_tensor"] else "FP64 Gauss-Jordan"),
                    "parallelism": f"replicas x{world}"},
         "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
         "p_sigma_sweep": p_sigma,

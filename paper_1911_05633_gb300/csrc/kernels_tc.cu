@@ -18,6 +18,7 @@
 #include "mixed.h"
 #include "ktimer.h"
 #include "umma.h"
+#include "fpbits.h"
 
 namespace gw {
 
@@ -57,8 +58,8 @@ __host__ __device__ inline TcLayout tc_layout(int na, int nb, int Ka, int Kb) {
   return L;
 }
 
-// grid (entry, tau chunk); 256 threads.  taus: the computed nodes it = 0 .. n_eff-1.
-__global__ void __launch_bounds__(256, 1)
+// grid (entry, tau chunk); 512 threads.  taus: the computed nodes it = 0 .. n_eff-1.
+__global__ void __launch_bounds__(512, 1)
 k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, const uint16_t* __restrict__ Bsplit,
                     const int* __restrict__ Bsplit_off, const int* __restrict__ species_of_atom,
                     const double2* __restrict__ G, double2* __restrict__ out, int n_tau, int n_eff, int tau_per_cta,
@@ -108,7 +109,7 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
   const float* Ca = C + E.ca;
   const double2* Gin = G + E.off_orb * n_tau;
   double2* Pout = out + E.off_pb * n_tau;
-  const double ms = -(double)spin;
+  const float msf = -(float)spin;
   const int t0 = blockIdx.y * tau_per_cta;
   const int t1 = min(n_eff, t0 + tau_per_cta);
   bool ok = true;
@@ -118,8 +119,8 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
     for (int x = tid; x < na * nb; x += blockDim.x) {
       const double2 g1 = Gin[(long long)it * na * nb + x];
       const double2 g2 = Gin[(long long)im * na * nb + x];
-      G1[x] = make_float2((float)g1.x, (float)g1.y);
-      G2[x] = make_float2((float)g2.x, (float)g2.y);
+      G1[x] = make_float2(d2f(g1.x), d2f(g1.y));
+      G2[x] = make_float2(d2f(g2.x), d2f(g2.y));
     }
     __syncthreads();
     // stage 1: X[K][L''][L']
@@ -138,31 +139,50 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
       X[x] = make_float2(ax, ay);
     }
     __syncthreads();
-    // stage 2 + split: rows K (Re) and Ka + K (Im), column j = L' nb + L'''
-    for (int x = tid; x < Ka * nb * nb; x += blockDim.x) {
-      const int K = x / (nb * nb);
-      const int j = x - K * nb * nb;
-      const int L1 = j / nb, L3 = j - L1 * nb;
+    // stage 2 + split: rows K (Re) and Ka + K (Im), columns j = L' nb + L''' in groups of
+    // 8 (one 16-byte core-matrix row per plane; the padding columns j >= nb^2 are zeros)
+    const int ngj = L.KD / 8;
+    for (int x = tid; x < Ka * ngj; x += blockDim.x) {
+      const int K = x / ngj;
+      const int j0 = (x - K * ngj) * 8;
       const float2* xk = X + K * na * nb;
-      float yr = 0.f, yi = 0.f;
-      for (int L2 = 0; L2 < na; ++L2) {
-        const float2 a = xk[L2 * nb + L1];
-        const float2 b = G2[L2 * nb + L3];
-        // a * conj(b)
-        yr = fmaf(a.x, b.x, fmaf(a.y, b.y, yr));
-        yi = fmaf(a.y, b.x, fmaf(-a.x, b.y, yi));
+      uint32_t pk[6][4];  // (hi, mid, lo) x (Re, Im), 8 BF16 each
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) pk[q][w] = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u;
+        float yr = 0.f, yi = 0.f;
+        if (j < nb * nb) {
+          const int L1 = j / nb, L3 = j - L1 * nb;
+          for (int L2 = 0; L2 < na; ++L2) {
+            const float2 a = xk[L2 * nb + L1];
+            const float2 b = G2[L2 * nb + L3];
+            // a * conj(b)
+            yr = fmaf(a.x, b.x, fmaf(a.y, b.y, yr));
+            yi = fmaf(a.y, b.x, fmaf(-a.x, b.y, yi));
+          }
+        }
+        __nv_bfloat16 h, m, l;
+        const uint32_t sh = (uint32_t)(u & 1) * 16u;
+        split3(yr, h, m, l);
+        pk[0][u >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << sh;
+        pk[1][u >> 1] |= (uint32_t)__bfloat16_as_ushort(m) << sh;
+        pk[2][u >> 1] |= (uint32_t)__bfloat16_as_ushort(l) << sh;
+        split3(yi, h, m, l);
+        pk[3][u >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << sh;
+        pk[4][u >> 1] |= (uint32_t)__bfloat16_as_ushort(m) << sh;
+        pk[5][u >> 1] |= (uint32_t)__bfloat16_as_ushort(l) << sh;
       }
-      __nv_bfloat16 h, m, l;
-      split3(yr, h, m, l);
-      uint32_t o = kmajor_offset(128, K, j);
-      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
-      split3(yi, h, m, l);
-      o = kmajor_offset(128, Ka + K, j);
-      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+      const uint32_t o_r = kmajor_offset(128, K, j0), o_i = kmajor_offset(128, Ka + K, j0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        *reinterpret_cast<uint4*>(Ap + q * aPlane + o_r) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+        *reinterpret_cast<uint4*>(Ap + q * aPlane + o_i) =
+            make_uint4(pk[3 + q][0], pk[3 + q][1], pk[3 + q][2], pk[3 + q][3]);
+      }
     }
     fence_smem_to_async();
     fence_before_sync();
@@ -217,9 +237,9 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
     const bool mirror = mirror_tau && (im != it);
     for (int x = tid; x < Ka * Kb; x += blockDim.x) {
       const float2 p = Ps[x];
-      const double2 z = make_double2(ms * (double)p.x, ms * (double)p.y);
-      Pout[(long long)it * Ka * Kb + x] = z;
-      if (mirror) Pout[(long long)im * Ka * Kb + x] = make_double2(z.x, -z.y);
+      const float zr = msf * p.x, zi = msf * p.y;  // -s is a power of two: exact in FP32
+      Pout[(long long)it * Ka * Kb + x] = make_double2(f2d(zr), f2d(zi));
+      if (mirror) Pout[(long long)im * Ka * Kb + x] = make_double2(f2d(zr), f2d(-zi));
     }
     __syncthreads();
   }
@@ -231,8 +251,10 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
 struct TcLayoutS {
   int KK;      // padded reduction length (K_b rounded up to 16)
   int NJ;      // padded N (n_b^2 rounded up to 16)
-  uint32_t offA, offB, offBm, offD, offG, offBar, total;
+  uint32_t offA, offB, offBm, offD, offG, offRed, offBar, total;
 };
+
+constexpr int kSGroups = 8;  // thread groups splitting the K sum of stage C
 
 __host__ __device__ inline TcLayoutS tc_layout_s(int na, int nb, int Ka, int Kb) {
   TcLayoutS L;
@@ -244,6 +266,7 @@ __host__ __device__ inline TcLayoutS tc_layout_s(int na, int nb, int Ka, int Kb)
   L.offBm = o; o += (uint32_t)Ka * nb * nb * 8u;
   L.offD = o; o += (uint32_t)Ka * na * nb * 8u;
   L.offG = o; o += (uint32_t)na * nb * 8u;
+  L.offRed = o; o += (uint32_t)kSGroups * na * nb * 8u;
   o = (o + 15u) & ~15u;
   L.offBar = o; o += 16u;
   L.total = o;
@@ -255,8 +278,8 @@ __host__ __device__ inline TcLayoutS tc_layout_s(int na, int nb, int Ka, int Kb)
 // BF16 terms, B = (C^b)^T split likewise, six products); stages B and C in FP32:
 //   D[K][L2][L1]  = sum_L3 G[L2][L3] Bm[K][L1 nb + L3]
 //   Sigma[L][L1]  = -sum_{K, L2} C^a[K][L][L2] D[K][L2][L1]
-// grid (entry, tau chunk); 256 threads.
-__global__ void __launch_bounds__(256, 1)
+// grid (entry, tau chunk); 512 threads.
+__global__ void __launch_bounds__(512, 1)
 k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, const uint16_t* __restrict__ BsplitT,
                  const int* __restrict__ BsplitT_off, const int* __restrict__ species_of_atom,
                  const double2* __restrict__ G, const double2* __restrict__ W, double2* __restrict__ out, int n_tau,
@@ -272,6 +295,7 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
   float2* Bm = reinterpret_cast<float2*>(sm + L.offBm);
   float2* D = reinterpret_cast<float2*>(sm + L.offD);
   float2* Gs = reinterpret_cast<float2*>(sm + L.offG);
+  float2* Red = reinterpret_cast<float2*>(sm + L.offRed);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.offBar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint32_t ncols = 32;
@@ -309,23 +333,42 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
     const double2* Win = W + E.off_pb * n_tau + (long long)it * Ka * Kb;
     for (int x = tid; x < na * nb; x += blockDim.x) {
       const double2 g = Gin[x];
-      Gs[x] = make_float2((float)g.x, (float)g.y);
+      Gs[x] = make_float2(d2f(g.x), d2f(g.y));
     }
-    // A operand: rows K (Re W~) and Ka + K (Im W~), reduction index K2
-    for (int x = tid; x < Ka * Kb; x += blockDim.x) {
-      const int K = x / Kb, Kp = x - (x / Kb) * Kb;
-      const double2 w = Win[x];
-      __nv_bfloat16 h, m, l;
-      split3((float)w.x, h, m, l);
-      uint32_t o = kmajor_offset(128, K, Kp);
-      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
-      split3((float)w.y, h, m, l);
-      o = kmajor_offset(128, Ka + K, Kp);
-      *reinterpret_cast<__nv_bfloat16*>(Ap + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + aPlane + o) = m;
-      *reinterpret_cast<__nv_bfloat16*>(Ap + 2 * aPlane + o) = l;
+    // A operand: rows K (Re W~) and Ka + K (Im W~), reduction index K2 in groups of 8
+    // (one 16-byte core-matrix row per plane; the padding K2 >= Kb stays zero)
+    const int ngk = (Kb + 7) / 8;
+    for (int x = tid; x < Ka * ngk; x += blockDim.x) {
+      const int K = x / ngk;
+      const int k0 = (x - K * ngk) * 8;
+      uint32_t pk[6][4];
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) pk[q][w] = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (k0 + u < Kb) {
+          const double2 w = Win[(long long)K * Kb + k0 + u];
+          const uint32_t sh = (uint32_t)(u & 1) * 16u;
+          __nv_bfloat16 h, m, l;
+          split3(d2f(w.x), h, m, l);
+          pk[0][u >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << sh;
+          pk[1][u >> 1] |= (uint32_t)__bfloat16_as_ushort(m) << sh;
+          pk[2][u >> 1] |= (uint32_t)__bfloat16_as_ushort(l) << sh;
+          split3(d2f(w.y), h, m, l);
+          pk[3][u >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << sh;
+          pk[4][u >> 1] |= (uint32_t)__bfloat16_as_ushort(m) << sh;
+          pk[5][u >> 1] |= (uint32_t)__bfloat16_as_ushort(l) << sh;
+        }
+      }
+      const uint32_t o_r = kmajor_offset(128, K, k0), o_i = kmajor_offset(128, Ka + K, k0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        *reinterpret_cast<uint4*>(Ap + q * aPlane + o_r) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+        *reinterpret_cast<uint4*>(Ap + q * aPlane + o_i) =
+            make_uint4(pk[3 + q][0], pk[3 + q][1], pk[3 + q][2], pk[3 + q][3]);
+      }
     }
     fence_smem_to_async();
     fence_before_sync();
@@ -389,22 +432,39 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
       D[x] = make_float2(tx, ty);
     }
     __syncthreads();
-    // stage C: one output (L, L1) per thread
-    if (tid < na * nb) {
-      const int Lr = tid / nb, L1 = tid - (tid / nb) * nb;
-      float ax = 0.f, ay = 0.f;
-      for (int K = 0; K < Ka; ++K) {
-        const float* c = Ca + (long long)K * na * na + Lr * na;
-        const float2* dk = D + K * na * nb;
-        for (int L2 = 0; L2 < na; ++L2) {
-          const float cv = c[L2];
-          const float2 d = dk[L2 * nb + L1];
-          ax = fmaf(cv, d.x, ax);
-          ay = fmaf(cv, d.y, ay);
+    // stage C: output (L, L1) summed over K in kSGroups slices of the threads, then reduced
+    {
+      const int no = na * nb;
+      const int per_g = blockDim.x / kSGroups;
+      const int g = tid / per_g, t = tid - g * per_g;
+      const int kchunk = (Ka + kSGroups - 1) / kSGroups;
+      const int K0 = g * kchunk, K1 = min(Ka, K0 + kchunk);
+      for (int o = t; o < no; o += per_g) {
+        const int Lr = o / nb, L1 = o - (o / nb) * nb;
+        float ax = 0.f, ay = 0.f;
+        for (int K = K0; K < K1; ++K) {
+          const float* c = Ca + (long long)K * na * na + Lr * na;
+          const float2* dk = D + K * na * nb;
+          for (int L2 = 0; L2 < na; ++L2) {
+            const float cv = c[L2];
+            const float2 d = dk[L2 * nb + L1];
+            ax = fmaf(cv, d.x, ax);
+            ay = fmaf(cv, d.y, ay);
+          }
         }
+        Red[g * no + o] = make_float2(ax, ay);
       }
-      double2* o = out + E.off_orb * n_tau + (long long)it * na * nb;
-      o[tid] = make_double2(-(double)ax, -(double)ay);
+    }
+    __syncthreads();
+    for (int o = tid; o < na * nb; o += blockDim.x) {
+      float ax = 0.f, ay = 0.f;
+      for (int g = 0; g < kSGroups; ++g) {
+        const float2 r2 = Red[g * na * nb + o];
+        ax += r2.x;
+        ay += r2.y;
+      }
+      double2* op = out + E.off_orb * n_tau + (long long)it * na * nb;
+      op[o] = make_double2(f2d(-ax), f2d(-ay));
     }
     __syncthreads();
   }
@@ -541,7 +601,7 @@ gw_status tc_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent,
   dim3 grid(h.n_entries(), (h.n_tau + per - 1) / per);
   {
     gw::TimedLaunch tl_("k_self_energy_tc", st);
-    k_self_energy_tc<<<grid, 256, m.smem_tc_s, st>>>(d_ent, m.d_Cf, m.d_BsplitT, m.d_BsplitT_off, m.d_species, G_R,
+    k_self_energy_tc<<<grid, 512, m.smem_tc_s, st>>>(d_ent, m.d_Cf, m.d_BsplitT, m.d_BsplitT_off, m.d_species, G_R,
                                                      Wt_R, Sig_R, h.n_tau, per, d_status);
   }
   cudaError_t e = cudaGetLastError();
@@ -574,7 +634,7 @@ gw_status tc_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* d_e
   dim3 grid(h.n_entries(), (n_eff + per - 1) / per);
   {
     gw::TimedLaunch tl_("k_polarizability_tc", st);
-    k_polarizability_tc<<<grid, 256, m.smem_tc, st>>>(d_ent, m.d_Cf, m.d_Bsplit, m.d_Bsplit_off, m.d_species, G_R, P_R,
+    k_polarizability_tc<<<grid, 512, m.smem_tc, st>>>(d_ent, m.d_Cf, m.d_Bsplit, m.d_Bsplit_off, m.d_species, G_R, P_R,
                                                       h.n_tau, n_eff, per, h.spin, h.c_symmetric, d_status);
   }
   cudaError_t e = cudaGetLastError();

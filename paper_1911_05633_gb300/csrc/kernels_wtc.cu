@@ -16,6 +16,7 @@
 #include "kernels.h"
 #include "smem_limit.h"
 #include "umma.h"
+#include "fpbits.h"
 #include "wtc.h"
 #include "ktimer.h"
 
@@ -121,6 +122,8 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
       }
       __syncthreads();
     }
+    // the trailing update below uses Pan - I on the panel's diagonal
+    if (tid < B) Pan[(k0 + tid) * B + tid].x -= 1.0f;
     // composite row exchange of this panel: new row r = old row srcmap[r]
     for (int i = tid; i < N; i += 512) srcmap[i] = i;
     __syncthreads();
@@ -152,30 +155,28 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
       // (b) the pivot rows of this chunk before the update
       for (int x = tid; x < B * C; x += 512) Buf[x] = M[(long long)(k0 + x / C) * N + c0 + (x % C)];
       __syncthreads();
-      // (c) rows i0 .. i0 + 3, columns c0 + lane + 32 q
-      for (int i0 = 4 * wid; i0 < N; i0 += 4 * 16) {
-        float2 acc[4][4];
+      // (c) rows i0 .. i0 + 7, columns c0 + lane + 32 q: 32 independent loads in flight per
+      // thread, then 8 x 4 complex FMAs per pair of shared-memory vectors (z, pv)
+      for (int i0 = 8 * wid; i0 < N; i0 += 8 * 16) {
+        float2 acc[8][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[r][q] = M[(long long)(i0 + r) * N + c0 + lane + 32 * q];
-#pragma unroll 4
+#pragma unroll 2
         for (int m = 0; m < B; ++m) {
-          float2 z[4], pv[4];
+          float2 z[8], pv[4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            z[r] = Pan[(i0 + r) * B + m];
-            if (i0 + r == k0 + m) z[r].x -= 1.0f;
-          }
+          for (int r = 0; r < 8; ++r) z[r] = Pan[(i0 + r) * B + m];
 #pragma unroll
           for (int q = 0; q < 4; ++q) pv[q] = Buf[m * C + lane + 32 * q];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[r][q] = cfma(z[r], pv[q], acc[r][q]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 8; ++r)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int j = c0 + lane + 32 * q;
@@ -184,6 +185,8 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
       }
       __syncthreads();
     }
+    if (tid < B) Pan[(k0 + tid) * B + tid].x += 1.0f;
+    __syncthreads();
     for (int x = tid; x < N * B; x += 512) M[(long long)(x / B) * N + k0 + (x % B)] = Pan[x];
     __syncthreads();
   }
@@ -756,7 +759,7 @@ k_refine_tc(const uint16_t* __restrict__ PX, const uint16_t* __restrict__ PR, co
         const long long o = row + c0 + c;
         if (FINAL) {
           const float2 h = hi[o], l = lo[o];
-          out[o] = make_double2((double)h.x + (double)l.x + (double)re[c], (double)h.y + (double)l.y + (double)im[c]);
+          out[o] = make_double2(f2d(h.x) + f2d(l.x) + f2d(re[c]), f2d(h.y) + f2d(l.y) + f2d(im[c]));
         } else {
           lo[o] = make_float2(re[c], im[c]);
         }
