@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="the small profiling case instead of the bench workload")
     ap.add_argument("--w-solver", default="auto", choices=["auto", "gauss_jordan"],
                     help="inverse of the W solve: tensor-core refinement where supported, or FP64 Gauss-Jordan")
+    ap.add_argument("--fp64-products", default="auto", choices=["auto", "fp64"],
+                    help="FP64 Sigma: its W~ C^b stage as FP64-accurate tensor-core products, or FP64 arithmetic")
     return ap.parse_args()
 
 
@@ -136,8 +138,12 @@ def kernel_work(name: str, cell, info, entries):
         return "tensor", 4 * 36 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
     if name == "k_polarizability_fp64":
         return "alu", contraction_flops(cell, entries) / (2 if info["c_symmetric"] else 1), "fp64", len(entries)
-    if name == "k_self_energy_fp64":  # dynamic part and the one-slice exchange term
-        return "alu", contraction_flops(cell, entries) * (1 + 1.0 / nt), "fp64", len(entries)
+    if name == "k_self_energy_fp64":  # dynamic part (stages B, C only when stage A runs on the tensor cores)
+        full = contraction_flops(cell, entries)      # and the one-slice exchange term (all stages)
+        dyn = stage_bc_flops(cell, entries) if info["sigma_tensor"] else full
+        return "alu", dyn + full / nt, "fp64", len(entries)
+    if name == "k_oz_gemm":  # 36 digit pairs x 2 flops x rows (entry, tau, K, Re/Im) x padded K x padded N
+        return "tensor", oz_gemm_flops(cell, entries), "bf16", len(entries)
     if name == "k_transform":  # real flops per block element: 8 n_out n_in (general), 2 n_out ceil(n_in / 2)
         # (mirror-paired input), 4 n_out n_in (real input)
         fP = 2 * nn * ((nt + 1) // 2) if info["c_symmetric"] else 8 * nn * nt
@@ -146,6 +152,33 @@ def kernel_work(name: str, cell, info, entries):
     if name == "k_slice_A":  # FP64 in, 8 x 2 BF16 digits out per element
         return "hbm", (16 + 32) * N * N * n_inv, "bytes", n_inv
     return None
+
+
+def stage_bc_flops(cell, entries) -> float:
+    """Real flops of stages B and C of the Sigma contraction (after B = W~ C^b):
+    2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2) per (entry, tau)."""
+    f = 0.0
+    for a, b in entries[:, :2]:
+        na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
+        Ka = cell.n_prod_of(int(a))
+        f += 2.0 * (2 * Ka * na * na * nb + 4 * Ka * na * nb * nb)
+    return f * cell.n_tau
+
+
+def oz_gemm_flops(cell, entries) -> float:
+    """Tensor flops of the FP64-accurate W~ C^b products: per (entry, tau) 2 K_a rows
+    x 36 digit pairs x 2 x (K_b padded to 16) x (n_b^2 padded to the column tile)."""
+    nb2max = max(cell.n_orb_of(i) ** 2 for i in range(cell.n_atoms))
+    NT, best = 16, 1 << 30
+    for c in range(16, 81, 16):
+        padded = -(-nb2max // c) * c
+        if padded <= best:
+            best, NT = padded, c
+    f = 0.0
+    for a, b in entries[:, :2]:
+        nb, Ka, Kb = cell.n_orb_of(int(b)), cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
+        f += 2 * Ka * 36 * 2.0 * (-(-Kb // 16) * 16) * (-(-nb * nb // NT) * NT)
+    return f * cell.n_tau
 
 
 def wsolve_flops(cell, info) -> float:
@@ -221,13 +254,13 @@ class Sweep:
     STAGES = ["G_k_to_R", "P", "P_tau_to_nu", "W_solve", "W_nu_to_tau", "v_k_to_R", "Sigma", "Sigma_tau_to_omega",
               "Sigma_R_to_k"]
 
-    def __init__(self, cell, precision: str, device: int = 0, w_solver: str = "auto"):
+    def __init__(self, cell, precision: str, device: int = 0, w_solver: str = "auto", fp64_products: str = "auto"):
         import torch
         from paper_1911_05633_gb300 import gw
         self.torch = torch
         self.cell = cell
         self.prec = precision
-        self.plan = gw.Plan.from_cell(cell, device=device, w_solver=w_solver)
+        self.plan = gw.Plan.from_cell(cell, device=device, w_solver=w_solver, fp64_products=fp64_products)
         p = self.plan
         inf = p.info
         self.dev = torch.device("cuda", device)
@@ -278,15 +311,6 @@ class Sweep:
             if events is not None:
                 events[i][1].record(stream)
 
-    def kernel_launches(self) -> int:
-        """Kernels this library launches per sweep (counted from the launch code)."""
-        inf = self.plan.info
-        nnu = int((self.cell.nu_idx >= 0).sum()) if inf["w_symmetric"] else inf["n_nu"]
-        nchunks = -(-nnu // inf["nu_chunk"])
-        inv = 15 if inf["w_tensor"] else 1  # launches per batched inverse
-        # copy of v, inverse of v, per chunk (scatter, inverse, gather), mirror
-        w = 1 + inv + nchunks * (2 + inv) + (1 if inf["w_symmetric"] else 0)
-        return 1 + 1 + 1 + w + 1 + 1 + 2 + 1 + 2
 
 
 def traffic_of(kernel: str, units_per_launch: float):
@@ -310,7 +334,7 @@ def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
     cell = workload(args.config, args.small)
-    sw = Sweep(cell, args.precision, device=local, w_solver=args.w_solver)
+    sw = Sweep(cell, args.precision, device=local, w_solver=args.w_solver, fp64_products=args.fp64_products)
     Gk = cell.green_k_tau()
     vq, _ = cell.coulomb()
     sw.load_inputs(Gk, vq)
@@ -413,6 +437,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": cell.name + f": {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k,"
                    f" {cell.n_tau} tau, cutoff {cell.cutoff} bohr, {len(ent)} pair entries",
                    "precision": args.precision, "l2": "256 MB buffer written between timed steps",
+                   "sigma_stage_a": ("FP64-accurate digit products on the tensor cores" if inf["sigma_tensor"]
+                                     else "FP64 arithmetic"),
                    "w_inverse": ("FP32 Gauss-Jordan + two residual refinements on the tensor cores (FP64-accurate)"
                                  if inf["w_tensor"] else "FP64 Gauss-Jordan"),
                    "parallelism": f"replicas x{world}"},
@@ -422,7 +448,8 @@ def run_ours(args, rank, world, local):
         "fp64_peak_tflops_measured": fp64_peak, "fp32_peak_tflops_measured": fp32_peak,
         "wall_s": round(wall, 3),
         "clocks": clk,
-        "gpu_launches": sw.kernel_launches() * args.steps,
+        # the library's kernel launches in the timed region, counted by its event timer
+        "gpu_launches": int(sum(v[1] for v in ktimes.values())),
         "roofline": roof,
         "kernels": kernels,
         "e2e": e2e,

@@ -96,6 +96,9 @@ typedef struct {
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
   int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384),
                              1: FP64 Gauss-Jordan inverse always */
+  int fp64_products;      /* GW_FP64 Sigma: 0 automatic (its W~ C^b stage as FP64-accurate
+                             digit products on the tensor cores when every K <= 64),
+                             1: FP64 arithmetic only */
 } gw_options;
 
 typedef struct {
@@ -112,7 +115,8 @@ typedef struct {
   double cond_boson;
   int w_symmetric;            /* the W solve runs on nu >= 0 and half of the q mesh (see gw_screened_W_iw) */
   int n_q_solved;             /* momenta solved per frequency */
-  int w_tensor;               /* inverses by FP32 Gauss-Jordan + one tensor-core refinement */
+  int w_tensor;               /* inverses by FP32 Gauss-Jordan + two tensor-core refinements */
+  int sigma_tensor;           /* GW_FP64 Sigma: stage W~ C^b by FP64-accurate tensor-core products */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */

@@ -15,6 +15,7 @@
 #include "smem_limit.h"
 #include "mixed.h"
 #include "wtc.h"
+#include "oz.h"
 #include "ktimer.h"
 
 struct gw_plan_s {
@@ -62,6 +63,8 @@ struct gw_plan_s {
   int* t_eA = nullptr;
   int* t_eX = nullptr;
   gw::MixedPlan mixed;
+  bool sigma_tensor = false;  // FP64 Sigma stage A by tensor-core digit products
+  gw::OzSigma oz;
   gw::KernelTimer timer;  // optional per-kernel event timing (gw_timing_*)
 };
 
@@ -124,6 +127,7 @@ void free_device(gw_plan_s* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
+  gw::oz_sigma_free(p->oz);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -344,6 +348,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     // FP32 level accumulators of the residual are exact)
     const size_t n = (size_t)hh.n_pb_total();
     p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 && n <= (size_t)gw::kWNmax;
+    bool k_ok = true;  // the tensor-core Sigma stage keeps a reduction of K_b <= 64 resident
+    for (int s = 0; s < hh.n_species; ++s) k_ok = k_ok && hh.n_prod[s] <= 16 * gw::kOzMaxKS;
+    p->sigma_tensor = !(opt && opt->fp64_products == 1) && k_ok;
   }
   p->device = opt ? opt->device : 0;
   if (p->host_only) {
@@ -440,6 +447,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     return fail(GW_ERR_UNSUPPORTED);
   }
   if ((st = gw::mixed_init(p->mixed, h, de)) != GW_OK) return fail(st);
+  if (p->sigma_tensor) {
+    if ((st = gw::oz_sigma_init(p->oz, h, (size_t)4 << 30)) != GW_OK) return fail(st);
+    p->sigma_tensor = p->oz.ready;
+  }
   *out = p;
   return GW_OK;
 }
@@ -480,6 +491,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->cond_boson = h.cond_b;
   info->w_symmetric = p->w_sym ? 1 : 0;
   info->w_tensor = p->w_tensor ? 1 : 0;
+  info->sigma_tensor = p->sigma_tensor ? 1 : 0;
   info->n_q_solved = p->n_qh;
   return GW_OK;
 }
@@ -644,12 +656,32 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
     g.w_n_slices = h.n_tau;
     g.out_n_slices = h.n_tau;
     g.sign = -1.0;
-    dim3 grid(h.n_entries(), h.n_tau);
-    {
-      gw::TimedLaunch tl_("k_self_energy_fp64", S(stream));
-      gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+    if (p->sigma_tensor) {
+      // stage A (W~ C^b) on the tensor cores per pass of tau slices, stages B and C in FP64
+      for (int s0 = 0; s0 < h.n_tau; s0 += p->oz.tau_c) {
+        const int te = std::min(p->oz.tau_c, h.n_tau - s0);
+        if ((st = gw::oz_sigma_stage_a(p->oz, h, p->d_ent, (const double2*)Wt_R, s0, te, p->d_status, S(stream))) !=
+            GW_OK)
+          return st;
+        g.Bpre = p->oz.d_Bpre;
+        g.offB = p->oz.d_offB;
+        g.tau_c = p->oz.tau_c;
+        g.s0 = s0;
+        dim3 grid(h.n_entries(), te);
+        {
+          gw::TimedLaunch tl_("k_self_energy_fp64", S(stream));
+          gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+        }
+        if ((st = check_launch("k_self_energy_fp64")) != GW_OK) return st;
+      }
+    } else {
+      dim3 grid(h.n_entries(), h.n_tau);
+      {
+        gw::TimedLaunch tl_("k_self_energy_fp64", S(stream));
+        gw::k_self_energy_fp64<<<grid, 256, p->smem_S, S(stream)>>>(g);
+      }
+      if ((st = check_launch("k_self_energy_fp64")) != GW_OK) return st;
     }
-    if ((st = check_launch("k_self_energy_fp64")) != GW_OK) return st;
   } else {
     set_last_error("unknown precision");
     return GW_ERR_ARG;

@@ -73,6 +73,11 @@ struct ContractArgs {
   int w_n_slices;
   int out_n_slices;
   double sign;
+  // Sigma with stage A precomputed (B[e][sl][K][j] at Bpre + offB[e] tau_c + (sl K_a + K) n_b^2 + j):
+  // block y = sl is slice s0 + sl of G and of the output
+  const double2* Bpre;
+  const long long* offB;
+  int tau_c, s0;
 };
 
 __global__ void k_gather_k_to_R(GatherArgs g);

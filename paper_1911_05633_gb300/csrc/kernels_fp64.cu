@@ -278,7 +278,8 @@ __global__ void k_self_energy_fp64(ContractArgs g) {
   double2* Gs = sm;                  // [na][nb]
   double2* B = Gs + na * nb;         // [kKC][nb][nb]
   double2* D = B + kKC * nb * nb;    // [kKC][na][nb]
-  const int gs = (g.g_slice >= 0) ? g.g_slice : s;
+  const int so = g.Bpre ? g.s0 + s : s;  // slice of G and of the output
+  const int gs = (g.g_slice >= 0) ? g.g_slice : so;
   const double2* Gin = g.G + E.off_orb * g.g_n_slices + (long long)gs * na * nb;
   for (int x = threadIdx.x; x < na * nb; x += blockDim.x) Gs[x] = Gin[x];
   const double2* W = g.W + E.off_pb * g.w_n_slices + (long long)s * Ka * Kb;
@@ -289,13 +290,18 @@ __global__ void k_self_energy_fp64(ContractArgs g) {
   __syncthreads();
   for (int k0 = 0; k0 < Ka; k0 += kKC) {
     const int kc = min(kKC, Ka - k0);
-    for (int x = threadIdx.x; x < kc * nb * nb; x += blockDim.x) {
-      const int K = x / (nb * nb);
-      const int j = x - K * nb * nb;
-      const double2* w = W + (long long)(k0 + K) * Kb;
-      double2 t = make_double2(0.0, 0.0);
-      for (int Kp = 0; Kp < Kb; ++Kp) t = rfma(Cb[(long long)Kp * nb * nb + j], w[Kp], t);
-      B[x] = t;
+    if (g.Bpre) {  // stage A done on the tensor cores
+      const double2* bp = g.Bpre + g.offB[e] * g.tau_c + ((long long)s * Ka + k0) * nb * nb;
+      for (int x = threadIdx.x; x < kc * nb * nb; x += blockDim.x) B[x] = bp[x];
+    } else {
+      for (int x = threadIdx.x; x < kc * nb * nb; x += blockDim.x) {
+        const int K = x / (nb * nb);
+        const int j = x - K * nb * nb;
+        const double2* w = W + (long long)(k0 + K) * Kb;
+        double2 t = make_double2(0.0, 0.0);
+        for (int Kp = 0; Kp < Kb; ++Kp) t = rfma(Cb[(long long)Kp * nb * nb + j], w[Kp], t);
+        B[x] = t;
+      }
     }
     __syncthreads();
     for (int x = threadIdx.x; x < kc * na * nb; x += blockDim.x) {
@@ -319,7 +325,7 @@ __global__ void k_self_energy_fp64(ContractArgs g) {
     __syncthreads();
   }
   if (own < na * nb) {
-    double2* o = g.out + E.off_orb * g.out_n_slices + (long long)s * na * nb;
+    double2* o = g.out + E.off_orb * g.out_n_slices + (long long)so * na * nb;
     o[own] = make_double2(g.sign * acc.x, g.sign * acc.y);
   }
 }

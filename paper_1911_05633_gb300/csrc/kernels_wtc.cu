@@ -17,6 +17,7 @@
 #include "smem_limit.h"
 #include "umma.h"
 #include "fpbits.h"
+#include "ozaki.h"
 #include "wtc.h"
 #include "ktimer.h"
 
@@ -216,9 +217,6 @@ using namespace umma;
 
 constexpr uint64_t kWaitNs = 500ull * 1000ull * 1000ull;
 
-__device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
-__device__ __forceinline__ int exp_field(float x) { return (int)((__float_as_uint(x) >> 23) & 0xFF); }
-
 }  // namespace
 
 __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ dst, long long n) {
@@ -263,45 +261,6 @@ __global__ void k_col_exponent(const float2* __restrict__ hi, const float2* __re
     }
   }
   eX[(long long)b * N + j] = m > 0 ? m - (lo ? 125 : 126) : 0;
-}
-
-// round(x 2^(56 - e)) for |x| < 2^e as a 64-bit integer, from the bits of x: the
-// significand shifted by its exponent relative to 2^(e - 56), rounded half up when
-// shifted right.  |result| < 2^56; subnormal x gives 0.
-__device__ __forceinline__ long long shift_round(long long m, int sh) {
-  if (sh >= 0) return m << sh;
-  if (sh > -63) return (m + (1ll << (-sh - 1))) >> (-sh);
-  return 0;
-}
-__device__ __forceinline__ long long fixed56(double x, int e) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((u >> 52) & 0x7FF);
-  if (E == 0) return 0;
-  const long long r = shift_round((long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull), E - 1019 - e);  // <= 3
-  return (u >> 63) ? -r : r;
-}
-__device__ __forceinline__ long long fixed56(float x, int e) {
-  const uint32_t u = __float_as_uint(x);
-  const int E = (int)((u >> 23) & 0xFF);
-  if (E == 0) return 0;
-  const long long r = shift_round((long long)((u & 0x7FFFFFu) | 0x800000u), E - 94 - e);  // <= 32
-  return (u >> 31) ? -r : r;
-}
-
-// Signed base-2^7 digits of one scaled entry: m = round(v 2^56) for |v| < 1, then
-// digit s = round(m / 2^(49 - 7 s)) taken from the top, so that v = sum_s d_s 2^-7(s+1)
-// up to 2^-57 with |d_0| <= 128 and |d_s| <= 64 after it; every d_s 2^-7(s+1) is exact
-// in BF16 (at most 8 significant bits).
-__device__ __forceinline__ int next_digit(long long& m, int s) {
-  const int sh = 49 - 7 * s;
-  const long long d = sh > 0 ? (m + (1ll << (sh - 1))) >> sh : m;
-  m -= d << sh;
-  return (int)d;
-}
-// bits of d 2^-7(s+1) in BF16 (exact)
-__device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
-  const float sc = __int_as_float((127 - 7 * (s + 1)) << 23);
-  return __float_as_uint((float)d * sc) >> 16;
 }
 
 // A operand digits.  Element (i, k) of matrix b -> kWSA digits of Re and of Im in the

@@ -1,0 +1,54 @@
+// FP64-accurate stage A of the Sigma contraction (Eq. S_MM) on the tensor cores:
+//   B[e][tau][K][j] = sum_K2 W~[e][tau][K][K2] C^b[K2][j],  j = (L', L''')
+// as a row GEMM over rows (entry, tau, K, Re/Im) from exact BF16 digits of W~ (sliced
+// per call) and of C^b (sliced once per plan).  Kernels in kernels_oz.cu; stages B and C
+// of the contraction then run in FP64 on B (k_self_energy_fp64 with Bpre set).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace gw {
+
+constexpr int kOzDigits = 8;   // base-2^7 digits per value
+constexpr int kOzLmax = 7;     // digit products a_s b_t with s + t <= kOzLmax
+constexpr int kOzBuckets = 6;  // accumulators: levels 0 .. 4 exactly, levels >= 5 together
+constexpr int kOzMaxKS = 4;    // reduction length up to 64 (K steps of 16) kept in shared memory
+constexpr uint32_t kOzAChunk = kOzDigits * 128 * 16 * 2;  // bytes of A digits per (row tile, K step)
+__host__ __device__ constexpr uint32_t oz_bchunk(int NT) { return (uint32_t)kOzDigits * NT * 16 * 2; }
+
+struct OzSigma {
+  bool ready = false;
+  int KS = 0;          // K steps: max over species of ceil(K_b / 16)
+  int NT = 0;          // output columns per tile (multiple of 16)
+  int max_nt = 0;      // column tiles of the widest n_b^2
+  int tau_c = 0;       // tau slices per pass
+  int n_tiles = 0;     // 128-row tiles per pass
+  size_t smem = 0;     // dynamic shared memory of the product kernel
+  int* d_tile_e = nullptr;        // [n_tiles] entry of the tile
+  int* d_tile_r0 = nullptr;       // [n_tiles] first row of the tile within its entry
+  uint16_t* d_Adig = nullptr;     // [n_tiles][KS] chunks of kOzDigits planes of 128 x 16
+  int* d_eA = nullptr;            // [n_tiles][128] row scale exponents
+  uint16_t* d_Bdig = nullptr;     // per species [nt][KS] chunks of kOzDigits planes of NT x 16
+  long long* d_Boff = nullptr;    // [n_species] offset of a species in d_Bdig (uint16 units)
+  int* d_eB = nullptr;            // per species [nt * NT] column scale exponents
+  int* d_eBoff = nullptr;         // [n_species]
+  int* d_species = nullptr;       // [n_atoms]
+  double2* d_Bpre = nullptr;      // [sum_e K_a n_b^2][tau_c]: stage A of one pass
+  long long* d_offB = nullptr;    // [E] prefix sums of K_a n_b^2
+  size_t bytes = 0;               // device memory held
+};
+
+// Plans the tensor-core stage A when every species fits (K_b <= 64) and allocates its
+// scratch within `cap` bytes; leaves o.ready false otherwise.
+gw_status oz_sigma_init(OzSigma& o, const HostPlan& h, size_t cap);
+void oz_sigma_free(OzSigma& o);
+// Stage A for slices s0 .. s0 + tau_eff - 1 of W~ (PB entry layout, n_tau slices) into o.d_Bpre.
+gw_status oz_sigma_stage_a(OzSigma& o, const HostPlan& h, const DevEntry* d_ent, const double2* W, int s0,
+                           int tau_eff, int* d_status, cudaStream_t st);
+
+}  // namespace gw

@@ -55,7 +55,8 @@ class GwGrid(C.Structure):
 
 class GwOptions(C.Structure):
     _fields_ = [("spin", C.c_int), ("strict_kmesh", C.c_int), ("host_only", C.c_int), ("device", C.c_int),
-                ("workspace_bytes", C.c_size_t), ("no_symmetry", C.c_int), ("w_solver", C.c_int)]
+                ("workspace_bytes", C.c_size_t), ("no_symmetry", C.c_int), ("w_solver", C.c_int),
+                ("fp64_products", C.c_int)]
 
 
 class GwPlanInfo(C.Structure):
@@ -64,7 +65,8 @@ class GwPlanInfo(C.Structure):
                 ("kmesh", C.c_int * 3), ("kmesh_required", C.c_int * 3), ("c_symmetric", C.c_int),
                 ("len_orb", C.c_int64), ("len_pb", C.c_int64), ("workspace_bytes", C.c_size_t),
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
-                ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int)]
+                ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
+                ("sigma_tensor", C.c_int)]
 
 
 class GwError(RuntimeError):
@@ -141,7 +143,7 @@ class Plan:
     def __init__(self, lattice, frac, species, n_orb: Sequence[int], n_prod: Sequence[int], C_list,
                  kmesh, beta: float, tau, omega_idx, nu_idx, cutoff: float, spin: int = 2,
                  strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0,
-                 no_symmetry: bool = False, w_solver: str = "auto"):
+                 no_symmetry: bool = False, w_solver: str = "auto", fp64_products: str = "auto"):
         lib = load_library()
         self._lib = lib
         self._keep = []
@@ -161,7 +163,8 @@ class Plan:
         grid = GwGrid(float(beta), len(tau), _ptr(tau, C.c_double), len(om), _ptr(om, C.c_int),
                       len(nu), _ptr(nu, C.c_int))
         opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes),
-                        int(bool(no_symmetry)), {"auto": 0, "gauss_jordan": 1}[w_solver])
+                        int(bool(no_symmetry)), {"auto": 0, "gauss_jordan": 1}[w_solver],
+                        {"auto": 0, "fp64": 1}[fp64_products])
         km = (C.c_int * 3)(*[int(x) for x in kmesh])
         h = C.c_void_p()
         _check(lib.gw_plan_create(C.byref(cell), C.byref(basis), km, C.byref(grid), float(cutoff),

@@ -57,6 +57,10 @@ class Sys:
         # N_PB of 128, 256 or 384 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
         n = cell.n_pb_total
         assert self.plan.info["w_tensor"] == int(n % 128 == 0 and n <= 384 and plan_kw.get("w_solver") != "gauss_jordan")
+        # the FP64 Sigma takes its W~ C^b stage from the tensor cores for K <= 64 unless the plan
+        # asks for FP64 only
+        kmax = max(sp.n_prod for sp in cell.species)
+        assert self.plan.info["sigma_tensor"] == int(plan_kw.get("fp64_products") != "fp64" and kmax <= 64)
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
         self.G_k = cell.green_k_tau()
@@ -89,6 +93,10 @@ def system(name):
             _CACHE[name] = Sys(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)))
         elif name == "c1_cut5_gj":
             _CACHE[name] = Sys(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)), w_solver="gauss_jordan")
+        elif name == "c0_fp64":
+            _CACHE[name] = Sys(synth.make_config(0), fp64_products="fp64")
+        elif name == "c1_fp64":
+            _CACHE[name] = Sys(synth.make_config(1), fp64_products="fp64")
         else:
             raise KeyError(name)
     return _CACHE[name]
@@ -197,7 +205,7 @@ def _random_W(s, seed=23):
     return out
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1"])
+@pytest.mark.parametrize("name", SMALL + ["c1", "c0_fp64", "c1_fp64"])
 def test_self_energy_and_exchange(name):
     s = system(name)
     WR = _random_W(s)
