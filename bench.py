@@ -142,12 +142,24 @@ def kernel_work(name: str, cell, info, entries):
         full = contraction_flops(cell, entries)      # and the one-slice exchange term (all stages)
         dyn = stage_bc_flops(cell, entries) if info["sigma_tensor"] else full
         return "alu", dyn + full / nt, "fp64", len(entries)
-    if name == "k_oz_gemm":  # 36 digit pairs x 2 flops x rows (entry, tau, K, Re/Im) x padded K x padded N
-        return "tensor", oz_gemm_flops(cell, entries), "bf16", len(entries)
+    if name == "k_oz_gemm":  # 36 digit pairs x 2 flops x rows x padded K x padded N, every use in a sweep
+        f = oz_gemm_flops(cell, entries) if info["sigma_tensor"] else 0.0
+        pad = lambda x, m: -(-x // m) * m
+        rows = info["len_pb"]
+        if info["transform_tensor"] & 1 and info["w_symmetric"]:  # W~ i nu -> tau, real input
+            f += rows * 36 * 2.0 * pad(nn, 16) * pad(2 * nt, oz_nt(2 * nt))
+        if info["transform_tensor"] & 2 and info["c_symmetric"]:  # P tau -> i nu, mirror pairs
+            nh = (nt + 1) // 2
+            f += rows * 36 * 2.0 * pad(2 * nh, 16) * pad(nn, oz_nt(nn))
+        return "tensor", f, "bf16", len(entries)
     if name == "k_transform":  # real flops per block element: 8 n_out n_in (general), 2 n_out ceil(n_in / 2)
         # (mirror-paired input), 4 n_out n_in (real input)
         fP = 2 * nn * ((nt + 1) // 2) if info["c_symmetric"] else 8 * nn * nt
         fW = 4 * nt * nn if info["w_symmetric"] else 8 * nt * nn
+        if info["c_symmetric"] and info["transform_tensor"] & 2:  # done by k_oz_gemm instead
+            fP = 0
+        if info["w_symmetric"] and info["transform_tensor"] & 1:
+            fW = 0
         return "alu", float((fP + fW) * info["len_pb"] + 8 * nw * nt * info["len_orb"]), "fp64", 3 * len(entries)
     if name == "k_slice_A":  # FP64 in, 8 x 2 BF16 digits out per element
         return "hbm", (16 + 32) * N * N * n_inv, "bytes", n_inv
@@ -165,15 +177,21 @@ def stage_bc_flops(cell, entries) -> float:
     return f * cell.n_tau
 
 
+def oz_nt(n_cols: int) -> int:
+    """Column tile of the digit-product GEMM: the multiple of 16 up to 80 with the least
+    padding of n_cols, the wider on ties."""
+    NT, best = 16, 1 << 30
+    for c in range(16, 81, 16):
+        padded = -(-n_cols // c) * c
+        if padded <= best:
+            best, NT = padded, c
+    return NT
+
+
 def oz_gemm_flops(cell, entries) -> float:
     """Tensor flops of the FP64-accurate W~ C^b products: per (entry, tau) 2 K_a rows
     x 36 digit pairs x 2 x (K_b padded to 16) x (n_b^2 padded to the column tile)."""
-    nb2max = max(cell.n_orb_of(i) ** 2 for i in range(cell.n_atoms))
-    NT, best = 16, 1 << 30
-    for c in range(16, 81, 16):
-        padded = -(-nb2max // c) * c
-        if padded <= best:
-            best, NT = padded, c
+    NT = oz_nt(max(cell.n_orb_of(i) ** 2 for i in range(cell.n_atoms)))
     f = 0.0
     for a, b in entries[:, :2]:
         nb, Ka, Kb = cell.n_orb_of(int(b)), cell.n_prod_of(int(a)), cell.n_prod_of(int(b))

@@ -65,6 +65,7 @@ struct gw_plan_s {
   gw::MixedPlan mixed;
   bool sigma_tensor = false;  // FP64 Sigma stage A by tensor-core digit products
   gw::OzSigma oz;
+  gw::OzTransform ozt;  // FP64-accurate structured transforms on the tensor cores
   gw::KernelTimer timer;  // optional per-kernel event timing (gw_timing_*)
 };
 
@@ -128,6 +129,7 @@ void free_device(gw_plan_s* p) {
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
   gw::oz_sigma_free(p->oz);
+  gw::oz_transform_free(p->ozt);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -451,6 +453,8 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     if ((st = gw::oz_sigma_init(p->oz, h, (size_t)4 << 30)) != GW_OK) return fail(st);
     p->sigma_tensor = p->oz.ready;
   }
+  if (!(opt && opt->fp64_products == 1))
+    if ((st = gw::oz_transform_init(p->ozt, h)) != GW_OK) return fail(st);
   *out = p;
   return GW_OK;
 }
@@ -492,6 +496,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->w_symmetric = p->w_sym ? 1 : 0;
   info->w_tensor = p->w_tensor ? 1 : 0;
   info->sigma_tensor = p->sigma_tensor ? 1 : 0;
+  info->transform_tensor = (p->ozt.ready_w ? 1 : 0) | (p->ozt.ready_p ? 2 : 0);
   info->n_q_solved = p->n_qh;
   return GW_OK;
 }
@@ -561,6 +566,11 @@ gw_status gw_transform_tau_iw_ex(gw_plan_t p, gw_statistics stt, gw_direction di
   DeviceGuard guard(p->device);
   gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
+  if (kind == GW_BLOCK_PB && stt == GW_BOSON &&
+      ((structure == GW_IN_REAL && dir == GW_IW_TO_TAU && p->ozt.ready_w) ||
+       (structure == GW_IN_MIRROR && p->ozt.ready_p)))
+    return gw::oz_transform(p->ozt, h, p->d_ent, structure, (const double2*)in, (double2*)out, p->d_status,
+                            S(stream));
   gw::TransformArgs g{};
   g.ent = p->d_ent;
   const int nfreq = (stt == GW_FERMION) ? h.n_omega : h.n_nu;

@@ -82,22 +82,19 @@ __host__ __device__ constexpr int oz_bucket(int L) { return L < kOzBuckets - 1 ?
 
 // One 128-row tile x NT columns per block (128 threads): all K steps of both operands
 // are loaded into shared memory by two bulk copies, then one thread issues the digit
-// products; the epilogue writes B to FP64.
-__global__ void __launch_bounds__(128, 1)
-k_oz_gemm(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, const int* __restrict__ tile_r0,
-          const int* __restrict__ species, const uint16_t* __restrict__ Adig, const int* __restrict__ eA,
-          const uint16_t* __restrict__ Bdig, const long long* __restrict__ Boff, const int* __restrict__ eB,
-          const int* __restrict__ eBoff, int KS, int NT, int tau_c, int tau_eff, double2* __restrict__ Bpre,
-          const long long* __restrict__ offB, int* status) {
+// products; the epilogue writes the FP64 result where the mode puts it.
+__global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
   __shared__ __align__(8) uint64_t bar;
   const int t = blockIdx.x, nt = blockIdx.y;
-  const int e = tile_e[t];
-  const DevEntry E = ent[e];
-  const int nb2 = E.nb * E.nb;
-  if (nt * NT >= nb2) return;  // this entry has fewer column tiles (uniform over the block)
-  const int sb = species[E.b];
+  const int e = g.tile_e[t];
+  const DevEntry E = g.ent[e];
+  const int NT = g.NT, KS = g.KS;
+  // columns of this entry's output rows
+  const int ncols = g.mode == kOzOutSigmaB ? E.nb * E.nb : (g.mode == kOzOutRealToComplex ? 2 * g.n_out : g.n_out);
+  if (nt * NT >= ncols) return;  // this entry has fewer column tiles (uniform over the block)
+  const int sb = g.species ? g.species[E.b] : 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     tmem_alloc(&tmem_base, 512);
@@ -115,9 +112,9 @@ k_oz_gemm(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, cons
   bool ok = true;
   if (tid == 0) {
     mbar_arrive_expect_tx(&bar, AB + BB);
-    bulk_g2s(sm, reinterpret_cast<const unsigned char*>(Adig) + (long long)t * AB, AB, &bar);
-    bulk_g2s(sm + AB, reinterpret_cast<const unsigned char*>(Bdig + Boff[sb]) + (long long)nt * BB, BB, &bar);
-    ok = mbar_wait(&bar, 0, kWaitNs, status);
+    bulk_g2s(sm, reinterpret_cast<const unsigned char*>(g.Adig) + (long long)t * AB, AB, &bar);
+    bulk_g2s(sm + AB, reinterpret_cast<const unsigned char*>(g.Bdig + g.Boff[sb]) + (long long)nt * BB, BB, &bar);
+    ok = mbar_wait(&bar, 0, kWaitNs, g.status);
     if (ok) {
       fence_after_sync();
       const uint32_t id = idesc_bf16_f32(128, NT);
@@ -136,21 +133,35 @@ k_oz_gemm(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, cons
       mma_commit(&bar);
     }
   }
-  const bool done = __syncthreads_and(ok ? 1 : 0) != 0 && mbar_wait(&bar, 1, kWaitNs, status);
+  const bool done = __syncthreads_and(ok ? 1 : 0) != 0 && mbar_wait(&bar, 1, kWaitNs, g.status);
   ok = __syncthreads_and(done ? 1 : 0) != 0;
   fence_after_sync();
   if (!ok) {
-    if (tid == 0) atomicExch(status, 2);
+    if (tid == 0) atomicExch(g.status, 2);
   } else {
-    const int Ka = E.Ka;
     const int r = 32 * warp + lane;
-    const int rho = tile_r0[t] + r;
-    const bool valid = rho < tau_eff * Ka * 2;
-    const int c = rho & 1, q = rho >> 1;
-    const int sl = q / Ka, K = q - (q / Ka) * Ka;
-    const int ea = eA[t * 128 + r];
-    double* orow = reinterpret_cast<double*>(Bpre + offB[e] * tau_c + ((long long)sl * Ka + K) * nb2) + c;
-    const int* eb = eB + eBoff[sb] + nt * NT;
+    const int rho = g.tile_r0[t] + r;
+    const int ea = g.eA[t * 128 + r];
+    const int* eb = g.eB + g.eBoff[sb] + nt * NT;
+    // the destination of this row: one double per column, at stride `cstride` doubles
+    bool valid;
+    double* orow;
+    long long cstride;
+    bool zero_im = false;
+    if (g.mode == kOzOutSigmaB) {
+      const int Ka = E.Ka, nb2 = E.nb * E.nb;
+      valid = rho < g.tau_eff * Ka * 2;
+      const int c = rho & 1, q = rho >> 1;
+      const int sl = q / Ka, K = q - (q / Ka) * Ka;
+      orow = reinterpret_cast<double*>(g.out + g.offB[e] * g.tau_c + ((long long)sl * Ka + K) * nb2) + c;
+      cstride = 2;
+    } else {
+      const int blk = E.Ka * E.Kb;  // transforms on the product-basis layout
+      valid = rho < blk;
+      orow = reinterpret_cast<double*>(g.out + E.off_pb * g.n_out + rho);
+      cstride = 2LL * blk;  // next output slice (tau or nu) of the same element
+      zero_im = g.mode == kOzOutReal;
+    }
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     for (int n0 = 0; n0 < NT; n0 += 16) {
       long long S[16];
@@ -171,7 +182,17 @@ k_oz_gemm(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, cons
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = nt * NT + n0 + i;
-          if (j < nb2) orow[2 * (long long)j] = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
+          if (j >= ncols) continue;
+          const double val = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
+          if (g.mode == kOzOutRealToComplex) {
+            // columns 0 .. n_out-1: Re of slice j; n_out .. 2 n_out-1: Im of slice j - n_out
+            const int sl = j < g.n_out ? j : j - g.n_out;
+            orow[(long long)sl * cstride + (j < g.n_out ? 0 : 1)] = val;
+          } else if (zero_im) {
+            reinterpret_cast<double2*>(orow)[(long long)j * (cstride / 2)] = make_double2(val, 0.0);
+          } else {
+            orow[(long long)j * cstride] = val;
+          }
         }
       }
     }
@@ -179,6 +200,51 @@ k_oz_gemm(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, cons
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+// Digits of the rows of a tau <-> i nu transform input on the product-basis layout: row x
+// of entry e (x < K_a K_b), value k from slice k (GW_IN_REAL: Re in[k]) or, for the
+// mirror-paired form, Re in[k] for k < nh and Im in[k - nh] for nh <= k < 2 nh.
+__global__ void __launch_bounds__(128)
+k_oz_slice_elem(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, const int* __restrict__ tile_r0,
+                const double2* __restrict__ in, int n_slices, int K, int nh, int KS, uint16_t* __restrict__ Adig,
+                int* __restrict__ eA) {
+  const int t = blockIdx.x, r = threadIdx.x;
+  const DevEntry E = ent[tile_e[t]];
+  const int blk = E.Ka * E.Kb;
+  const int x = tile_r0[t] + r;
+  const bool valid = x < blk;
+  const double* base = reinterpret_cast<const double*>(in + E.off_pb * n_slices + x);
+  auto value = [&](int k) -> double {
+    if (nh > 0 && k >= nh) return base[2LL * (k - nh) * blk + 1];
+    return base[2LL * k * blk];
+  };
+  int m = 0;
+  if (valid)
+    for (int k = 0; k < K; ++k) m = max(m, exp_field(value(k)));
+  const int e = m > 0 ? m - 1022 : 0;
+  eA[t * 128 + r] = e;
+  uint16_t* tile = Adig + (long long)t * KS * (kOzAChunk / 2);
+  for (int ks = 0; ks < KS; ++ks) {
+    for (int h = 0; h < 2; ++h) {
+      long long mv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = ks * 16 + 8 * h + u;
+        mv[u] = (valid && k < K) ? fixed56(value(k), e) : 0ll;
+      }
+      uint16_t* chunk = tile + (long long)ks * (kOzAChunk / 2);
+      const uint32_t off = kmajor_offset(128, r, 8 * h) / 2;
+#pragma unroll
+      for (int s = 0; s < kOzDigits; ++s) {
+        uint32_t p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          p[u] = digit_bf16(next_digit(mv[2 * u], s), s) | (digit_bf16(next_digit(mv[2 * u + 1], s), s) << 16);
+        *reinterpret_cast<uint4*>(chunk + s * (128 * 16) + off) = make_uint4(p[0], p[1], p[2], p[3]);
+      }
+    }
+  }
 }
 
 // Host digits with the device's rules (scale exponent from the exponent field, rounding
@@ -212,6 +278,48 @@ uint16_t host_digit_bf16(long long& m, int s) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
   return (uint16_t)(u >> 16);
+}
+
+// Digit chunks [nt][KS] of kOzDigits planes of NT x 16 and the column exponents of a
+// column operand B[n][k] (n < n_cols, k < K) given by value(n, k).
+struct OzMatrix {
+  int NT = 0, n_nt = 0, KS = 0;
+  std::vector<uint16_t> dig;
+  std::vector<int> e;
+};
+template <typename F>
+OzMatrix oz_matrix(int n_cols, int K, int NT, int KS, F value) {
+  OzMatrix m;
+  m.NT = NT;
+  m.KS = KS;
+  m.n_nt = (n_cols + NT - 1) / NT;
+  m.dig.assign((size_t)m.n_nt * KS * (oz_bchunk(NT) / 2), 0);
+  for (int n = 0; n < m.n_nt * NT; ++n) {
+    int mx = 0;
+    if (n < n_cols)
+      for (int k = 0; k < K; ++k) mx = std::max(mx, host_exp_field(value(n, k)));
+    const int e = mx > 0 ? mx - 1022 : 0;
+    m.e.push_back(e);
+    if (n >= n_cols) continue;
+    const int ntile = n / NT, nl = n % NT;
+    for (int k = 0; k < K; ++k) {
+      long long mv = host_fixed56(value(n, k), e);
+      const size_t chunk = ((size_t)ntile * KS + k / 16) * (oz_bchunk(NT) / 2);
+      const uint32_t off = umma::kmajor_offset(NT, nl, k % 16) / 2;
+      for (int d = 0; d < kOzDigits; ++d) m.dig[chunk + (size_t)d * NT * 16 + off] = host_digit_bf16(mv, d);
+    }
+  }
+  return m;
+}
+// The multiple of 16 up to 80 (six accumulators fit the 512 tensor-memory columns) with
+// the least padding of n_cols, the wider on ties.
+int oz_pick_nt(int n_cols) {
+  int NT = 16, best = 1 << 30;
+  for (int c = 16; c <= 80; c += 16) {
+    const int padded = ((n_cols + c - 1) / c) * c;
+    if (padded <= best) { best = padded; NT = c; }
+  }
+  return NT;
 }
 
 }  // namespace
@@ -335,14 +443,145 @@ gw_status oz_sigma_stage_a(OzSigma& o, const HostPlan& h, const DevEntry* d_ent,
                                            o.d_eA);
   }
   {
+    OzGemmArgs g{};
+    g.ent = d_ent;
+    g.tile_e = o.d_tile_e;
+    g.tile_r0 = o.d_tile_r0;
+    g.Adig = o.d_Adig;
+    g.eA = o.d_eA;
+    g.KS = o.KS;
+    g.Bdig = o.d_Bdig;
+    g.Boff = o.d_Boff;
+    g.eB = o.d_eB;
+    g.eBoff = o.d_eBoff;
+    g.species = o.d_species;
+    g.NT = o.NT;
+    g.mode = kOzOutSigmaB;
+    g.out = o.d_Bpre;
+    g.offB = o.d_offB;
+    g.tau_c = o.tau_c;
+    g.tau_eff = tau_eff;
+    g.status = d_status;
     TimedLaunch tl_("k_oz_gemm", st);
-    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)o.max_nt), 128, o.smem, st>>>(
-        d_ent, o.d_tile_e, o.d_tile_r0, o.d_species, o.d_Adig, o.d_eA, o.d_Bdig, o.d_Boff, o.d_eB, o.d_eBoff, o.KS,
-        o.NT, o.tau_c, tau_eff, o.d_Bpre, o.d_offB, d_status);
+    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)o.max_nt), 128, o.smem, st>>>(g);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core Sigma stage: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
+}
+
+gw_status oz_transform_init(OzTransform& o, const HostPlan& h) {
+  o = OzTransform{};
+  const int N = h.n_tau, nh = (N + 1) / 2, nn = h.n_nu;
+  const bool w_ok = nn <= 16 * kOzMaxKS;      // reduction over the nu slices
+  const bool p_ok = 2 * nh <= 16 * kOzMaxKS;  // reduction over (Re, Im) of the paired nodes
+  if (!w_ok && !p_ok) return GW_OK;
+  // row tiles: the K_a K_b elements of every entry, 128 per tile
+  std::vector<int> te, tr;
+  for (int e = 0; e < h.n_entries(); ++e) {
+    const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
+    const int blk = h.n_prod[h.species[a]] * h.n_prod[h.species[b]];
+    for (int r0 = 0; r0 < blk; r0 += 128) {
+      te.push_back(e);
+      tr.push_back(r0);
+    }
+  }
+  o.n_tiles = (int)te.size();
+  // W: B[n][k] = Re T_inv[n][k] (n < N), Im T_inv[n - N][k]; P: B[m][k] = a (k < nh), b (k >= nh)
+  o.KS_w = (nn + 15) / 16;
+  o.KS_p = (2 * nh + 15) / 16;
+  o.NT_w = oz_pick_nt(2 * N);
+  o.NT_p = oz_pick_nt(nn);
+  const std::vector<double>& Ti = h.Tb_inv;  // [N][nn] complex
+  const std::vector<double>& Tm = h.Tb_mirror;  // [nn][nh] (a, b)
+  OzMatrix mw = oz_matrix(2 * N, nn, o.NT_w, o.KS_w, [&](int n, int k) {
+    return n < N ? Ti[2 * ((size_t)n * nn + k)] : Ti[2 * ((size_t)(n - N) * nn + k) + 1];
+  });
+  OzMatrix mp = oz_matrix(nn, 2 * nh, o.NT_p, o.KS_p, [&](int n, int k) {
+    return k < nh ? Tm[2 * ((size_t)n * nh + k)] : Tm[2 * ((size_t)n * nh + (k - nh)) + 1];
+  });
+  o.nt_w = mw.n_nt;
+  o.nt_p = mp.n_nt;
+  o.KSmax = std::max(w_ok ? o.KS_w : 0, p_ok ? o.KS_p : 0);
+  const long long zero64 = 0;
+  const int zero32 = 0;
+  auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    o.bytes += bytes;
+    return !src || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  const bool good = up((void**)&o.d_tile_e, te.data(), te.size() * sizeof(int)) &&
+                    up((void**)&o.d_tile_r0, tr.data(), tr.size() * sizeof(int)) &&
+                    up((void**)&o.d_Adig, nullptr, (size_t)o.n_tiles * o.KSmax * kOzAChunk) &&
+                    up((void**)&o.d_eA, nullptr, (size_t)o.n_tiles * 128 * sizeof(int)) &&
+                    up((void**)&o.d_Bw, mw.dig.data(), mw.dig.size() * sizeof(uint16_t)) &&
+                    up((void**)&o.d_ew, mw.e.data(), mw.e.size() * sizeof(int)) &&
+                    up((void**)&o.d_Bp, mp.dig.data(), mp.dig.size() * sizeof(uint16_t)) &&
+                    up((void**)&o.d_ep, mp.e.data(), mp.e.size() * sizeof(int)) &&
+                    up((void**)&o.d_zero64, &zero64, sizeof(long long)) &&
+                    up((void**)&o.d_zero32, &zero32, sizeof(int));
+  if (!good) {
+    set_last_error("device allocation for the tensor-core transforms failed");
+    oz_transform_free(o);
+    return GW_ERR_OOM;
+  }
+  o.smem = std::max(w_ok ? (size_t)o.KS_w * (kOzAChunk + oz_bchunk(o.NT_w)) : 0,
+                    p_ok ? (size_t)o.KS_p * (kOzAChunk + oz_bchunk(o.NT_p)) : 0);
+  if (raise_smem_limit(k_oz_gemm, o.smem) != cudaSuccess) {
+    set_last_error("cudaFuncSetAttribute (tensor-core transforms)");
+    oz_transform_free(o);
+    return GW_ERR_UNSUPPORTED;
+  }
+  o.ready_w = w_ok;
+  o.ready_p = p_ok;
+  return GW_OK;
+}
+
+void oz_transform_free(OzTransform& o) {
+  void* ptrs[] = {o.d_tile_e, o.d_tile_r0, o.d_Adig, o.d_eA, o.d_Bw, o.d_ew, o.d_Bp, o.d_ep, o.d_zero64, o.d_zero32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  o = OzTransform{};
+}
+
+gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
+                       double2* out, int* d_status, cudaStream_t st) {
+  const bool w = structure == GW_IN_REAL;
+  const int N = h.n_tau, nh = (N + 1) / 2, nn = h.n_nu;
+  const int KS = w ? o.KS_w : o.KS_p, NT = w ? o.NT_w : o.NT_p, nts = w ? o.nt_w : o.nt_p;
+  {
+    TimedLaunch tl_("k_oz_slice_elem", st);
+    k_oz_slice_elem<<<o.n_tiles, 128, 0, st>>>(d_ent, o.d_tile_e, o.d_tile_r0, in, w ? nn : N, w ? nn : 2 * nh,
+                                               w ? 0 : nh, KS, o.d_Adig, o.d_eA);
+  }
+  {
+    OzGemmArgs g{};
+    g.ent = d_ent;
+    g.tile_e = o.d_tile_e;
+    g.tile_r0 = o.d_tile_r0;
+    g.Adig = o.d_Adig;
+    g.eA = o.d_eA;
+    g.KS = KS;
+    g.Bdig = w ? o.d_Bw : o.d_Bp;
+    g.Boff = o.d_zero64;
+    g.eB = w ? o.d_ew : o.d_ep;
+    g.eBoff = o.d_zero32;
+    g.species = nullptr;
+    g.NT = NT;
+    g.mode = w ? kOzOutRealToComplex : kOzOutReal;
+    g.out = out;
+    g.n_out = w ? N : nn;
+    g.status = d_status;
+    TimedLaunch tl_("k_oz_gemm", st);
+    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)nts), 128, (size_t)KS * (kOzAChunk + oz_bchunk(NT)), st>>>(g);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("tensor-core transform: ") + cudaGetErrorString(e));
     return GW_ERR_CUDA;
   }
   return GW_OK;

@@ -21,6 +21,61 @@ constexpr int kOzMaxKS = 4;    // reduction length up to 64 (K steps of 16) kept
 constexpr uint32_t kOzAChunk = kOzDigits * 128 * 16 * 2;  // bytes of A digits per (row tile, K step)
 __host__ __device__ constexpr uint32_t oz_bchunk(int NT) { return (uint32_t)kOzDigits * NT * 16 * 2; }
 
+// Where k_oz_gemm writes its rows: Sigma stage A (B of one pass of tau slices), or a
+// tau <-> i nu transform on the product-basis layout with a real input (columns:
+// Re then Im of each output slice) or a real output (imaginary parts written as 0).
+constexpr int kOzOutSigmaB = 0;
+constexpr int kOzOutRealToComplex = 1;
+constexpr int kOzOutReal = 2;
+
+struct OzGemmArgs {
+  const DevEntry* ent;
+  const int* tile_e;       // [tiles] entry of a 128-row tile
+  const int* tile_r0;      // [tiles] its first row within the entry
+  const uint16_t* Adig;    // [tiles][KS] digit chunks of the rows
+  const int* eA;           // [tiles][128] row scale exponents
+  int KS;                  // 16-wide K steps
+  const uint16_t* Bdig;    // digit chunks of the column operand, [nt][KS] per matrix
+  const long long* Boff;   // offset of each matrix in Bdig (uint16 units)
+  const int* eB;           // column scale exponents
+  const int* eBoff;        // offset of each matrix in eB
+  const int* species;      // Sigma: species of each atom selects the matrix (else matrix 0)
+  int NT;                  // columns per tile
+  int mode;                // kOzOut*
+  double2* out;
+  const long long* offB;   // Sigma: [E] prefix sums of K_a n_b^2
+  int tau_c, tau_eff;      // Sigma: slices per pass, slices in this pass
+  int n_out;               // transforms: output slices
+  int* status;
+};
+
+// FP64-accurate structured tau <-> i nu transforms of the product-basis layout.
+struct OzTransform {
+  bool ready_w = false;  // bosonic i nu -> tau of a real input
+  bool ready_p = false;  // bosonic tau -> i nu of a mirror-paired input
+  int n_tiles = 0, KSmax = 0;
+  int* d_tile_e = nullptr;
+  int* d_tile_r0 = nullptr;
+  uint16_t* d_Adig = nullptr;
+  int* d_eA = nullptr;
+  // the two column operands
+  int KS_w = 0, NT_w = 0, nt_w = 0, KS_p = 0, NT_p = 0, nt_p = 0;
+  uint16_t* d_Bw = nullptr;
+  int* d_ew = nullptr;
+  uint16_t* d_Bp = nullptr;
+  int* d_ep = nullptr;
+  long long* d_zero64 = nullptr;  // {0}: offset of the single matrix
+  int* d_zero32 = nullptr;
+  size_t smem = 0;
+  size_t bytes = 0;
+};
+
+gw_status oz_transform_init(OzTransform& o, const HostPlan& h);
+void oz_transform_free(OzTransform& o);
+// structure: GW_IN_REAL (bosonic i nu -> tau) or GW_IN_MIRROR (bosonic tau -> i nu)
+gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
+                       double2* out, int* d_status, cudaStream_t st);
+
 struct OzSigma {
   bool ready = false;
   int KS = 0;          // K steps: max over species of ceil(K_b / 16)

@@ -61,6 +61,9 @@ class Sys:
         # asks for FP64 only
         kmax = max(sp.n_prod for sp in cell.species)
         assert self.plan.info["sigma_tensor"] == int(plan_kw.get("fp64_products") != "fp64" and kmax <= 64)
+        nn, nh = cell.nu_idx.size, (cell.n_tau + 1) // 2
+        want = 0 if plan_kw.get("fp64_products") == "fp64" else int(nn <= 64) | (2 * int(2 * nh <= 64))
+        assert self.plan.info["transform_tensor"] == want
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
         self.G_k = cell.green_k_tau()
@@ -141,7 +144,7 @@ def test_transform(name, st, direction, kind):
     assert rel(out, pack(ref)) < TOL
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5", "c1"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5", "c1", "c0_fp64", "c1_fp64"])
 def test_transform_structured_inputs(name):
     """gw_transform_tau_iw_ex: P(R, tau) with P(beta - tau) = P(tau)* (symmetric C) through
     the mirror-paired bosonic transform, and a real W~(R, i nu) through the real-input
