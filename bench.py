@@ -136,8 +136,9 @@ def kernel_work(name: str, cell, info, entries):
         return "tensor", 4 * 20 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
     if name == "k_ozaki_residual<second>":  # 36 slice pairs
         return "tensor", 4 * 36 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
-    if name == "k_polarizability_fp64":
-        return "alu", contraction_flops(cell, entries) / (2 if info["c_symmetric"] else 1), "fp64", len(entries)
+    if name == "k_polarizability_fp64":  # stages 1 and 2 only when stage 3 runs on the tensor cores
+        f = stage_bc_flops(cell, entries) if info["p_tensor"] else contraction_flops(cell, entries)
+        return "alu", f / (2 if info["c_symmetric"] else 1), "fp64", len(entries)
     if name == "k_self_energy_fp64":  # dynamic part (stages B, C only when stage A runs on the tensor cores)
         full = contraction_flops(cell, entries)      # and the one-slice exchange term (all stages)
         dyn = stage_bc_flops(cell, entries) if info["sigma_tensor"] else full
@@ -146,6 +147,12 @@ def kernel_work(name: str, cell, info, entries):
         f = oz_gemm_flops(cell, entries) if info["sigma_tensor"] else 0.0
         pad = lambda x, m: -(-x // m) * m
         rows = info["len_pb"]
+        if info["p_tensor"]:  # P stage 3: 2 K_a rows per (entry, computed node), K = n_b^2, N = K_b
+            ntp = oz_nt(max(cell.n_prod_of(i) for i in range(cell.n_atoms)))
+            ne = (nt + 1) // 2 if info["c_symmetric"] else nt
+            for a, b in entries[:, :2]:
+                nb, Ka, Kb = cell.n_orb_of(int(b)), cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
+                f += ne * 2 * Ka * 36 * 2.0 * pad(nb * nb, 16) * pad(Kb, ntp)
         if info["transform_tensor"] & 1 and info["w_symmetric"]:  # W~ i nu -> tau, real input
             f += rows * 36 * 2.0 * pad(nn, 16) * pad(2 * nt, oz_nt(2 * nt))
         if info["transform_tensor"] & 2 and info["c_symmetric"]:  # P tau -> i nu, mirror pairs
@@ -167,8 +174,8 @@ def kernel_work(name: str, cell, info, entries):
 
 
 def stage_bc_flops(cell, entries) -> float:
-    """Real flops of stages B and C of the Sigma contraction (after B = W~ C^b):
-    2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2) per (entry, tau)."""
+    """Real flops of the two small stages of a contraction (Sigma after B = W~ C^b, or P
+    before Y C^b): 2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2) per (entry, tau)."""
     f = 0.0
     for a, b in entries[:, :2]:
         na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))

@@ -97,8 +97,9 @@ typedef struct {
   int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384),
                              1: FP64 Gauss-Jordan inverse always */
   int fp64_products;      /* 0 automatic: FP64-accurate digit products on the tensor cores for
-                             the W~ C^b stage of the GW_FP64 Sigma (every K <= 64) and the
-                             structured bosonic transforms (reduction <= 64);
+                             the W~ C^b stage of the GW_FP64 Sigma (every K <= 384), the Y C^b
+                             stage of the GW_FP64 P (every n^2 <= 384) and the structured
+                             bosonic transforms (reduction <= 384);
                              1: FP64 arithmetic only */
 } gw_options;
 
@@ -118,6 +119,7 @@ typedef struct {
   int n_q_solved;             /* momenta solved per frequency */
   int w_tensor;               /* inverses by FP32 Gauss-Jordan + two tensor-core refinements */
   int sigma_tensor;           /* GW_FP64 Sigma: stage W~ C^b by FP64-accurate tensor-core products */
+  int p_tensor;               /* GW_FP64 P: stage Y C^b by FP64-accurate tensor-core products (device plans) */
   int transform_tensor;       /* bit 0: GW_IN_REAL bosonic i nu -> tau, bit 1: GW_IN_MIRROR bosonic
                                  tau -> i nu of the product-basis layout by FP64-accurate
                                  tensor-core products (device plans) */

@@ -66,6 +66,7 @@ struct gw_plan_s {
   bool sigma_tensor = false;  // FP64 Sigma stage A by tensor-core digit products
   gw::OzSigma oz;
   gw::OzTransform ozt;  // FP64-accurate structured transforms on the tensor cores
+  gw::OzPol ozp;        // FP64-accurate stage 3 of P on the tensor cores
   gw::KernelTimer timer;  // optional per-kernel event timing (gw_timing_*)
 };
 
@@ -130,6 +131,7 @@ void free_device(gw_plan_s* p) {
   gw::mixed_free(p->mixed);
   gw::oz_sigma_free(p->oz);
   gw::oz_transform_free(p->ozt);
+  gw::oz_pol_free(p->ozp);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -350,7 +352,7 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     // FP32 level accumulators of the residual are exact)
     const size_t n = (size_t)hh.n_pb_total();
     p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 && n <= (size_t)gw::kWNmax;
-    bool k_ok = true;  // the tensor-core Sigma stage keeps a reduction of K_b <= 64 resident
+    bool k_ok = true;  // the tensor-core Sigma stage sums levels 0-4 exactly for K_b <= 384
     for (int s = 0; s < hh.n_species; ++s) k_ok = k_ok && hh.n_prod[s] <= 16 * gw::kOzMaxKS;
     p->sigma_tensor = !(opt && opt->fp64_products == 1) && k_ok;
   }
@@ -453,8 +455,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     if ((st = gw::oz_sigma_init(p->oz, h, (size_t)4 << 30)) != GW_OK) return fail(st);
     p->sigma_tensor = p->oz.ready;
   }
-  if (!(opt && opt->fp64_products == 1))
+  if (!(opt && opt->fp64_products == 1)) {
     if ((st = gw::oz_transform_init(p->ozt, h)) != GW_OK) return fail(st);
+    if ((st = gw::oz_pol_init(p->ozp, h, (size_t)4 << 30)) != GW_OK) return fail(st);
+  }
   *out = p;
   return GW_OK;
 }
@@ -496,6 +500,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->w_symmetric = p->w_sym ? 1 : 0;
   info->w_tensor = p->w_tensor ? 1 : 0;
   info->sigma_tensor = p->sigma_tensor ? 1 : 0;
+  info->p_tensor = p->ozp.ready ? 1 : 0;
   info->transform_tensor = (p->ozt.ready_w ? 1 : 0) | (p->ozt.ready_p ? 2 : 0);
   info->n_q_solved = p->n_qh;
   return GW_OK;
@@ -633,6 +638,24 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   g.spin = h.spin;
   g.mirror_tau = h.c_symmetric;
   const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
+  if (p->ozp.ready) {
+    // stages 1 and 2 in FP64 (Y to the pass buffer), stage 3 on the tensor cores, per pass
+    for (int s0 = 0; s0 < nt_eff; s0 += p->ozp.tau_c) {
+      const int te = std::min(p->ozp.tau_c, nt_eff - s0);
+      g.Ypre = p->ozp.d_Ypre;
+      g.offB = p->ozp.d_offB;
+      g.tau_c = p->ozp.tau_c;
+      g.s0 = s0;
+      {
+        gw::TimedLaunch tl_("k_polarizability_fp64", S(stream));
+        gw::k_polarizability_fp64<<<dim3(h.n_entries(), te), 256, p->smem_P, S(stream)>>>(g);
+      }
+      if ((st = check_launch("k_polarizability_fp64")) != GW_OK) return st;
+      if ((st = gw::oz_pol_stage3(p->ozp, h, p->d_ent, s0, te, (double2*)P_R, p->d_status, S(stream))) != GW_OK)
+        return st;
+    }
+    return GW_OK;
+  }
   dim3 grid(h.n_entries(), nt_eff);
   {
     gw::TimedLaunch tl_("k_polarizability_fp64", S(stream));

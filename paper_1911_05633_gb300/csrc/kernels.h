@@ -78,6 +78,9 @@ struct ContractArgs {
   const double2* Bpre;
   const long long* offB;
   int tau_c, s0;
+  // P with stage 3 on the tensor cores: block y = sl is computed node s0 + sl; stage 2 (Y)
+  // goes to Ypre + offB[e] tau_c + (sl K_a + K) n_b^2 + j instead of stage 3
+  double2* Ypre;
 };
 
 __global__ void k_gather_k_to_R(GatherArgs g);

@@ -204,7 +204,7 @@ constexpr int kKC = 16;  // product functions of atom a per pass
 __global__ void k_polarizability_fp64(ContractArgs g) {
   extern __shared__ double2 sm[];
   const int e = blockIdx.x;
-  const int it = blockIdx.y;
+  const int it = g.Ypre ? g.s0 + (int)blockIdx.y : (int)blockIdx.y;
   const DevEntry E = g.ent[e];
   const int na = E.na, nb = E.nb, Ka = E.Ka, Kb = E.Kb;
   const int N = g.n_tau;
@@ -244,8 +244,11 @@ __global__ void k_polarizability_fp64(ContractArgs g) {
       double2 acc = make_double2(0.0, 0.0);
       for (int L2 = 0; L2 < na; ++L2) acc = cfmac(xk[L2 * nb + L1], G2[L2 * nb + L3], acc);
       Y[x] = acc;
+      if (g.Ypre)  // stage 3 runs on the tensor cores
+        g.Ypre[g.offB[e] * g.tau_c + ((long long)blockIdx.y * Ka + k0) * nb * nb + x] = acc;
     }
     __syncthreads();
+    if (g.Ypre) continue;
     for (int x = threadIdx.x; x < kc * Kb; x += blockDim.x) {
       const int K = x / Kb, Kp = x - (x / Kb) * Kb;
       const double2* y = Y + K * nb * nb;

@@ -80,19 +80,24 @@ k_oz_slice_w(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, c
 // Accumulator of level L (levels >= 5 together).
 __host__ __device__ constexpr int oz_bucket(int L) { return L < kOzBuckets - 1 ? L : kOzBuckets - 1; }
 
-// One 128-row tile x NT columns per block (128 threads): all K steps of both operands
-// are loaded into shared memory by two bulk copies, then one thread issues the digit
-// products; the epilogue writes the FP64 result where the mode puts it.
+// One 128-row tile x NT columns per block (128 threads).  The K steps of both operands
+// pass through kOzStages shared-memory stages (one bulk copy of each per step; while
+// step ks runs, the stage of step ks - 1 is refilled with step ks - 1 + kOzStages); one
+// thread issues the digit products; the epilogue writes the FP64 result where the mode
+// puts it.
 __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t full[kOzStages];
+  __shared__ __align__(8) uint64_t mmad[kOzStages];
   const int t = blockIdx.x, nt = blockIdx.y;
   const int e = g.tile_e[t];
   const DevEntry E = g.ent[e];
   const int NT = g.NT, KS = g.KS;
   // columns of this entry's output rows
-  const int ncols = g.mode == kOzOutSigmaB ? E.nb * E.nb : (g.mode == kOzOutRealToComplex ? 2 * g.n_out : g.n_out);
+  const int ncols = g.mode == kOzOutSigmaB ? E.nb * E.nb
+                    : g.mode == kOzOutP    ? E.Kb
+                    : (g.mode == kOzOutRealToComplex ? 2 * g.n_out : g.n_out);
   if (nt * NT >= ncols) return;  // this entry has fewer column tiles (uniform over the block)
   const int sb = g.species ? g.species[E.b] : 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -101,39 +106,56 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int st = 0; st < kOzStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&mmad[st], 1);
+    }
     fence_mbar_init();
   }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tm = tmem_base;
-  const uint32_t AB = (uint32_t)KS * kOzAChunk, BB = (uint32_t)KS * oz_bchunk(NT);
+  const uint32_t BC = oz_bchunk(NT), SB = kOzAChunk + BC;  // bytes per stage
+  const unsigned char* Ab = reinterpret_cast<const unsigned char*>(g.Adig) + (long long)t * KS * kOzAChunk;
+  const unsigned char* Bb = reinterpret_cast<const unsigned char*>(g.Bdig + g.Boff[sb]) + (long long)nt * KS * BC;
+  auto load = [&](int ks, int st) {
+    mbar_arrive_expect_tx(&full[st], SB);
+    bulk_g2s(sm + st * SB, Ab + (long long)ks * kOzAChunk, kOzAChunk, &full[st]);
+    bulk_g2s(sm + st * SB + kOzAChunk, Bb + (long long)ks * BC, BC, &full[st]);
+  };
   bool ok = true;
   if (tid == 0) {
-    mbar_arrive_expect_tx(&bar, AB + BB);
-    bulk_g2s(sm, reinterpret_cast<const unsigned char*>(g.Adig) + (long long)t * AB, AB, &bar);
-    bulk_g2s(sm + AB, reinterpret_cast<const unsigned char*>(g.Bdig + g.Boff[sb]) + (long long)nt * BB, BB, &bar);
-    ok = mbar_wait(&bar, 0, kWaitNs, g.status);
-    if (ok) {
+    const uint32_t id = idesc_bf16_f32(128, NT);
+    const uint32_t s0 = smem_u32(sm);
+    const uint32_t PA = 128 * 16 * 2, PB = (uint32_t)NT * 16 * 2;
+    for (int st = 0; st < kOzStages && st < KS; ++st) load(st, st);
+    uint32_t used = 0;
+    for (int ks = 0; ks < KS; ++ks) {
+      const int st = ks % kOzStages;
+      if (!mbar_wait(&full[st], (uint32_t)(ks / kOzStages) & 1u, kWaitNs, g.status)) { ok = false; break; }
       fence_after_sync();
-      const uint32_t id = idesc_bf16_f32(128, NT);
-      const uint32_t a0 = smem_u32(sm), b0 = a0 + AB;
-      const uint32_t PA = 128 * 16 * 2, PB = (uint32_t)NT * 16 * 2;
-      uint32_t used = 0;
-      for (int ks = 0; ks < KS; ++ks)
-        for (int tt = 0; tt < kOzDigits; ++tt)
-          for (int s = 0; s + tt <= kOzLmax && s < kOzDigits; ++s) {
-            const int q = oz_bucket(s + tt);
-            const uint32_t acc = (used >> q) & 1u;
-            used |= 1u << q;
-            mma_bf16(tm + (uint32_t)(q * NT), smem_desc(a0 + ks * kOzAChunk + s * PA, 128, 256),
-                     smem_desc(b0 + ks * oz_bchunk(NT) + tt * PB, 128, 256), id, acc);
-          }
-      mma_commit(&bar);
+      const uint32_t a0 = s0 + st * SB, b0 = a0 + kOzAChunk;
+      for (int tt = 0; tt < kOzDigits; ++tt)
+        for (int s = 0; s + tt <= kOzLmax && s < kOzDigits; ++s) {
+          const int q = oz_bucket(s + tt);
+          const uint32_t acc = (used >> q) & 1u;
+          used |= 1u << q;
+          mma_bf16(tm + (uint32_t)(q * NT), smem_desc(a0 + s * PA, 128, 256), smem_desc(b0 + tt * PB, 128, 256), id,
+                   acc);
+        }
+      mma_commit(&mmad[st]);
+      if (ks >= 1 && ks - 1 + kOzStages < KS) {
+        // the products of step ks - 1 are done once its commit arrives: refill its stage
+        const int so = (ks - 1) % kOzStages;
+        if (!mbar_wait(&mmad[so], (uint32_t)((ks - 1) / kOzStages) & 1u, kWaitNs, g.status)) { ok = false; break; }
+        load(ks - 1 + kOzStages, so);
+      }
     }
   }
-  const bool done = __syncthreads_and(ok ? 1 : 0) != 0 && mbar_wait(&bar, 1, kWaitNs, g.status);
+  const int last = KS - 1;
+  const bool done = __syncthreads_and(ok ? 1 : 0) != 0 &&
+                    mbar_wait(&mmad[last % kOzStages], (uint32_t)(last / kOzStages) & 1u, kWaitNs, g.status);
   ok = __syncthreads_and(done ? 1 : 0) != 0;
   fence_after_sync();
   if (!ok) {
@@ -148,6 +170,8 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
     double* orow;
     long long cstride;
     bool zero_im = false;
+    long long moff = 0;  // P: offset of the mirrored node (0: none)
+    double msign = 1.0;
     if (g.mode == kOzOutSigmaB) {
       const int Ka = E.Ka, nb2 = E.nb * E.nb;
       valid = rho < g.tau_eff * Ka * 2;
@@ -155,6 +179,18 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
       const int sl = q / Ka, K = q - (q / Ka) * Ka;
       orow = reinterpret_cast<double*>(g.out + g.offB[e] * g.tau_c + ((long long)sl * Ka + K) * nb2) + c;
       cstride = 2;
+    } else if (g.mode == kOzOutP) {
+      const int Ka = E.Ka, Kb = E.Kb;
+      valid = rho < g.tau_eff * Ka * 2;
+      const int c = rho & 1, q = rho >> 1;
+      const int sl = q / Ka, K = q - (q / Ka) * Ka;
+      const int it = g.s0 + sl, im = g.n_tau - 1 - it;
+      orow = reinterpret_cast<double*>(g.out + E.off_pb * g.n_tau + ((long long)it * Ka + K) * Kb) + c;
+      cstride = 2;
+      if (g.mirror && im != it) {  // the mirrored node is the conjugate
+        moff = 2LL * (im - it) * Ka * Kb;
+        msign = c ? -1.0 : 1.0;
+      }
     } else {
       const int blk = E.Ka * E.Kb;  // transforms on the product-basis layout
       valid = rho < blk;
@@ -184,7 +220,11 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
           const int j = nt * NT + n0 + i;
           if (j >= ncols) continue;
           const double val = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
-          if (g.mode == kOzOutRealToComplex) {
+          if (g.mode == kOzOutP) {
+            const double pv = g.ms * val;  // -s is a power of two: exact
+            orow[(long long)j * cstride] = pv;
+            if (moff) orow[(long long)j * cstride + moff] = msign * pv;
+          } else if (g.mode == kOzOutRealToComplex) {
             // columns 0 .. n_out-1: Re of slice j; n_out .. 2 n_out-1: Im of slice j - n_out
             const int sl = j < g.n_out ? j : j - g.n_out;
             orow[(long long)sl * cstride + (j < g.n_out ? 0 : 1)] = val;
@@ -200,6 +240,53 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+// Digits of Y (stage 2 of the P contraction).  One thread per row of a 128-row tile:
+// row rho = (sl K_a + K) 2 + c of the tile's entry, values Y[sl][K][j].c for j < n_b^2
+// from the pass buffer (entry e at offB[e] tau_c, [sl][K_a][n_b^2] complex).
+__global__ void __launch_bounds__(128)
+k_oz_slice_y(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e, const int* __restrict__ tile_r0,
+             const double2* __restrict__ Y, const long long* __restrict__ offB, int tau_c, int tau_eff, int KS,
+             uint16_t* __restrict__ Adig, int* __restrict__ eA) {
+  const int t = blockIdx.x, r = threadIdx.x;
+  const int ei = tile_e[t];
+  const DevEntry E = ent[ei];
+  const int Ka = E.Ka, nb2 = E.nb * E.nb;
+  const int rho = tile_r0[t] + r;
+  const bool valid = rho < tau_eff * Ka * 2;
+  const double* src = nullptr;
+  if (valid) {
+    const int c = rho & 1, q = rho >> 1;
+    const int sl = q / Ka, K = q - (q / Ka) * Ka;
+    src = reinterpret_cast<const double*>(Y + offB[ei] * tau_c + ((long long)sl * Ka + K) * nb2) + c;
+  }
+  int m = 0;
+  if (valid)
+    for (int k = 0; k < nb2; ++k) m = max(m, exp_field(src[2 * k]));
+  const int e = m > 0 ? m - 1022 : 0;
+  eA[t * 128 + r] = e;
+  uint16_t* tile = Adig + (long long)t * KS * (kOzAChunk / 2);
+  for (int ks = 0; ks < KS; ++ks) {
+    for (int h = 0; h < 2; ++h) {
+      long long mv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = ks * 16 + 8 * h + u;
+        mv[u] = (valid && k < nb2) ? fixed56(src[2 * k], e) : 0ll;
+      }
+      uint16_t* chunk = tile + (long long)ks * (kOzAChunk / 2);
+      const uint32_t off = kmajor_offset(128, r, 8 * h) / 2;
+#pragma unroll
+      for (int s = 0; s < kOzDigits; ++s) {
+        uint32_t p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          p[u] = digit_bf16(next_digit(mv[2 * u], s), s) | (digit_bf16(next_digit(mv[2 * u + 1], s), s) << 16);
+        *reinterpret_cast<uint4*>(chunk + s * (128 * 16) + off) = make_uint4(p[0], p[1], p[2], p[3]);
+      }
+    }
+  }
 }
 
 // Digits of the rows of a tau <-> i nu transform input on the product-basis layout: row x
@@ -328,7 +415,7 @@ gw_status oz_sigma_init(OzSigma& o, const HostPlan& h, size_t cap) {
   o.ready = false;
   int KS = 0, max_nb2 = 0;
   for (int s = 0; s < h.n_species; ++s) {
-    if (h.n_prod[s] > 16 * kOzMaxKS) return GW_OK;  // reduction too long for the resident design
+    if (h.n_prod[s] > 16 * kOzMaxKS) return GW_OK;  // levels 0-4 exact up to 384 terms only
     KS = std::max(KS, (h.n_prod[s] + 15) / 16);
     max_nb2 = std::max(max_nb2, h.n_orb[s] * h.n_orb[s]);
   }
@@ -342,7 +429,7 @@ gw_status oz_sigma_init(OzSigma& o, const HostPlan& h, size_t cap) {
   o.KS = KS;
   o.NT = NT;
   o.max_nt = (max_nb2 + NT - 1) / NT;
-  o.smem = (size_t)KS * kOzAChunk + (size_t)KS * oz_bchunk(NT);
+  o.smem = oz_smem(KS, NT);
   const int E = h.n_entries();
   // stage-A output per tau slice and entry: K_a n_b^2 complex values
   std::vector<long long> offB(E + 1, 0);
@@ -529,8 +616,7 @@ gw_status oz_transform_init(OzTransform& o, const HostPlan& h) {
     oz_transform_free(o);
     return GW_ERR_OOM;
   }
-  o.smem = std::max(w_ok ? (size_t)o.KS_w * (kOzAChunk + oz_bchunk(o.NT_w)) : 0,
-                    p_ok ? (size_t)o.KS_p * (kOzAChunk + oz_bchunk(o.NT_p)) : 0);
+  o.smem = std::max(w_ok ? oz_smem(o.KS_w, o.NT_w) : 0, p_ok ? oz_smem(o.KS_p, o.NT_p) : 0);
   if (raise_smem_limit(k_oz_gemm, o.smem) != cudaSuccess) {
     set_last_error("cudaFuncSetAttribute (tensor-core transforms)");
     oz_transform_free(o);
@@ -577,11 +663,138 @@ gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent,
     g.n_out = w ? N : nn;
     g.status = d_status;
     TimedLaunch tl_("k_oz_gemm", st);
-    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)nts), 128, (size_t)KS * (kOzAChunk + oz_bchunk(NT)), st>>>(g);
+    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)nts), 128, oz_smem(KS, NT), st>>>(g);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core transform: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
+}
+
+gw_status oz_pol_init(OzPol& o, const HostPlan& h, size_t cap) {
+  o = OzPol{};
+  int KS = 0, max_Kb = 0;
+  for (int s = 0; s < h.n_species; ++s) {
+    const int nb2 = h.n_orb[s] * h.n_orb[s];
+    if (nb2 > 16 * kOzMaxKS) return GW_OK;  // levels 0-4 exact up to 384 terms only
+    KS = std::max(KS, (nb2 + 15) / 16);
+    max_Kb = std::max(max_Kb, h.n_prod[s]);
+  }
+  const int NT = oz_pick_nt(max_Kb);
+  o.KS = KS;
+  o.NT = NT;
+  o.max_nt = (max_Kb + NT - 1) / NT;
+  o.smem = oz_smem(KS, NT);
+  const int E = h.n_entries();
+  const int n_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
+  std::vector<long long> offB(E + 1, 0);
+  std::vector<int> rows1(E);
+  long long rows_all = 0;
+  for (int e = 0; e < E; ++e) {
+    const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
+    const int Ka = h.n_prod[h.species[a]], nb = h.n_orb[h.species[b]];
+    offB[e + 1] = offB[e] + (long long)Ka * nb * nb;
+    rows1[e] = 2 * Ka;
+    rows_all += rows1[e];
+  }
+  const double per_slice = (double)offB[E] * 16.0 + (double)rows_all * KS * 16 * kOzDigits * 2.0;
+  o.tau_c = std::max(1, std::min(n_eff, (int)((double)cap / std::max(per_slice, 1.0))));
+  std::vector<int> te, tr;
+  for (int e = 0; e < E; ++e)
+    for (int r0 = 0; r0 < o.tau_c * rows1[e]; r0 += 128) {
+      te.push_back(e);
+      tr.push_back(r0);
+    }
+  o.n_tiles = (int)te.size();
+  std::vector<uint16_t> bd;
+  std::vector<long long> boff;
+  std::vector<int> eb, eboff;
+  for (int s = 0; s < h.n_species; ++s) {
+    const int nb2 = h.n_orb[s] * h.n_orb[s], Kb = h.n_prod[s];
+    const std::vector<double>& C = h.C[s];  // [K'][j]
+    OzMatrix m = oz_matrix(Kb, nb2, NT, KS, [&](int n, int k) { return C[(size_t)n * nb2 + k]; });
+    boff.push_back((long long)bd.size());
+    eboff.push_back((int)eb.size());
+    bd.insert(bd.end(), m.dig.begin(), m.dig.end());
+    eb.insert(eb.end(), m.e.begin(), m.e.end());
+  }
+  auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+    o.bytes += bytes;
+    return !src || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  const bool good =
+      up((void**)&o.d_tile_e, te.data(), te.size() * sizeof(int)) &&
+      up((void**)&o.d_tile_r0, tr.data(), tr.size() * sizeof(int)) &&
+      up((void**)&o.d_Adig, nullptr, (size_t)o.n_tiles * KS * kOzAChunk) &&
+      up((void**)&o.d_eA, nullptr, (size_t)o.n_tiles * 128 * sizeof(int)) &&
+      up((void**)&o.d_Bdig, bd.data(), bd.size() * sizeof(uint16_t)) &&
+      up((void**)&o.d_Boff, boff.data(), boff.size() * sizeof(long long)) &&
+      up((void**)&o.d_eB, eb.data(), eb.size() * sizeof(int)) &&
+      up((void**)&o.d_eBoff, eboff.data(), eboff.size() * sizeof(int)) &&
+      up((void**)&o.d_species, h.species.data(), h.species.size() * sizeof(int)) &&
+      up((void**)&o.d_Ypre, nullptr, (size_t)offB[E] * o.tau_c * sizeof(double2)) &&
+      up((void**)&o.d_offB, offB.data(), offB.size() * sizeof(long long));
+  if (!good) {
+    set_last_error("device allocation for the tensor-core P stage failed");
+    oz_pol_free(o);
+    return GW_ERR_OOM;
+  }
+  if (raise_smem_limit(k_oz_gemm, o.smem) != cudaSuccess) {
+    set_last_error("cudaFuncSetAttribute (tensor-core P stage)");
+    oz_pol_free(o);
+    return GW_ERR_UNSUPPORTED;
+  }
+  o.ready = true;
+  return GW_OK;
+}
+
+void oz_pol_free(OzPol& o) {
+  void* ptrs[] = {o.d_tile_e, o.d_tile_r0, o.d_Adig, o.d_eA, o.d_Bdig, o.d_Boff, o.d_eB,
+                  o.d_eBoff, o.d_species, o.d_Ypre, o.d_offB};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  o = OzPol{};
+}
+
+gw_status oz_pol_stage3(OzPol& o, const HostPlan& h, const DevEntry* d_ent, int s0, int tau_eff, double2* P_R,
+                        int* d_status, cudaStream_t st) {
+  {
+    TimedLaunch tl_("k_oz_slice_y", st);
+    k_oz_slice_y<<<o.n_tiles, 128, 0, st>>>(d_ent, o.d_tile_e, o.d_tile_r0, o.d_Ypre, o.d_offB, o.tau_c, tau_eff,
+                                            o.KS, o.d_Adig, o.d_eA);
+  }
+  {
+    OzGemmArgs g{};
+    g.ent = d_ent;
+    g.tile_e = o.d_tile_e;
+    g.tile_r0 = o.d_tile_r0;
+    g.Adig = o.d_Adig;
+    g.eA = o.d_eA;
+    g.KS = o.KS;
+    g.Bdig = o.d_Bdig;
+    g.Boff = o.d_Boff;
+    g.eB = o.d_eB;
+    g.eBoff = o.d_eBoff;
+    g.species = o.d_species;
+    g.NT = o.NT;
+    g.mode = kOzOutP;
+    g.out = P_R;
+    g.tau_eff = tau_eff;
+    g.s0 = s0;
+    g.n_tau = h.n_tau;
+    g.mirror = h.c_symmetric;
+    g.ms = -(double)h.spin;
+    g.status = d_status;
+    TimedLaunch tl_("k_oz_gemm", st);
+    k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)o.max_nt), 128, o.smem, st>>>(g);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("tensor-core P stage: ") + cudaGetErrorString(e));
     return GW_ERR_CUDA;
   }
   return GW_OK;

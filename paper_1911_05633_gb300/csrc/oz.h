@@ -17,9 +17,14 @@ namespace gw {
 constexpr int kOzDigits = 8;   // base-2^7 digits per value
 constexpr int kOzLmax = 7;     // digit products a_s b_t with s + t <= kOzLmax
 constexpr int kOzBuckets = 6;  // accumulators: levels 0 .. 4 exactly, levels >= 5 together
-constexpr int kOzMaxKS = 4;    // reduction length up to 64 (K steps of 16) kept in shared memory
+constexpr int kOzMaxKS = 24;   // reduction length up to 384 (K steps of 16): levels 0-4 stay exact
+constexpr int kOzStages = 4;   // shared-memory stages of one K step of both operands
 constexpr uint32_t kOzAChunk = kOzDigits * 128 * 16 * 2;  // bytes of A digits per (row tile, K step)
 __host__ __device__ constexpr uint32_t oz_bchunk(int NT) { return (uint32_t)kOzDigits * NT * 16 * 2; }
+// dynamic shared memory of k_oz_gemm for KS K steps and NT columns
+__host__ __device__ constexpr size_t oz_smem(int KS, int NT) {
+  return (size_t)(KS < kOzStages ? KS : kOzStages) * (kOzAChunk + oz_bchunk(NT));
+}
 
 // Where k_oz_gemm writes its rows: Sigma stage A (B of one pass of tau slices), or a
 // tau <-> i nu transform on the product-basis layout with a real input (columns:
@@ -27,6 +32,7 @@ __host__ __device__ constexpr uint32_t oz_bchunk(int NT) { return (uint32_t)kOzD
 constexpr int kOzOutSigmaB = 0;
 constexpr int kOzOutRealToComplex = 1;
 constexpr int kOzOutReal = 2;
+constexpr int kOzOutP = 3;  // P stage 3: P[e][s0 + sl][K][K'] = -s value (and the mirrored node)
 
 struct OzGemmArgs {
   const DevEntry* ent;
@@ -46,6 +52,8 @@ struct OzGemmArgs {
   const long long* offB;   // Sigma: [E] prefix sums of K_a n_b^2
   int tau_c, tau_eff;      // Sigma: slices per pass, slices in this pass
   int n_out;               // transforms: output slices
+  int s0, n_tau, mirror;   // P: first computed node of the pass, N_tau, write the mirrored nodes
+  double ms;               // P: -s
   int* status;
 };
 
@@ -75,6 +83,34 @@ void oz_transform_free(OzTransform& o);
 // structure: GW_IN_REAL (bosonic i nu -> tau) or GW_IN_MIRROR (bosonic tau -> i nu)
 gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st);
+
+// FP64-accurate stage 3 of the P contraction (Eq. P_MM) on the tensor cores:
+//   P[e][tau][K][K'] = -s sum_j Y[e][tau][K][j] C^b[K'][j],  j = (L', L''')
+// with Y from the FP64 stages 1 and 2 (k_polarizability_fp64 with Ypre set).
+struct OzPol {
+  bool ready = false;
+  int KS = 0, NT = 0, max_nt = 0;
+  int tau_c = 0;       // computed nodes per pass
+  int n_tiles = 0;
+  size_t smem = 0;
+  int* d_tile_e = nullptr;
+  int* d_tile_r0 = nullptr;
+  uint16_t* d_Adig = nullptr;
+  int* d_eA = nullptr;
+  uint16_t* d_Bdig = nullptr;   // per species: B[K'][j] = C[K'][j]
+  long long* d_Boff = nullptr;
+  int* d_eB = nullptr;
+  int* d_eBoff = nullptr;
+  int* d_species = nullptr;
+  double2* d_Ypre = nullptr;    // [sum_e K_a n_b^2][tau_c]
+  long long* d_offB = nullptr;  // [E] prefix sums of K_a n_b^2
+  size_t bytes = 0;
+};
+gw_status oz_pol_init(OzPol& o, const HostPlan& h, size_t cap);
+void oz_pol_free(OzPol& o);
+// Stage 3 for the computed nodes s0 .. s0 + tau_eff - 1, Y in o.d_Ypre, into P_R (PB layout).
+gw_status oz_pol_stage3(OzPol& o, const HostPlan& h, const DevEntry* d_ent, int s0, int tau_eff, double2* P_R,
+                        int* d_status, cudaStream_t st);
 
 struct OzSigma {
   bool ready = false;

@@ -66,7 +66,7 @@ class GwPlanInfo(C.Structure):
                 ("len_orb", C.c_int64), ("len_pb", C.c_int64), ("workspace_bytes", C.c_size_t),
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
                 ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
-                ("sigma_tensor", C.c_int), ("transform_tensor", C.c_int)]
+                ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int)]
 
 
 class GwError(RuntimeError):

@@ -59,10 +59,15 @@ class Sys:
         assert self.plan.info["w_tensor"] == int(n % 128 == 0 and n <= 384 and plan_kw.get("w_solver") != "gauss_jordan")
         # the FP64 Sigma takes its W~ C^b stage from the tensor cores for K <= 64 unless the plan
         # asks for FP64 only
+        # FP64-accurate tensor-core products (reductions up to 384 terms) unless the plan asks
+        # for FP64 arithmetic only
+        on = plan_kw.get("fp64_products") != "fp64"
         kmax = max(sp.n_prod for sp in cell.species)
-        assert self.plan.info["sigma_tensor"] == int(plan_kw.get("fp64_products") != "fp64" and kmax <= 64)
+        nmax = max(sp.n_orb for sp in cell.species)
+        assert self.plan.info["sigma_tensor"] == int(on and kmax <= 384)
+        assert self.plan.info["p_tensor"] == int(on and nmax * nmax <= 384)
         nn, nh = cell.nu_idx.size, (cell.n_tau + 1) // 2
-        want = 0 if plan_kw.get("fp64_products") == "fp64" else int(nn <= 64) | (2 * int(2 * nh <= 64))
+        want = int(on) * (int(nn <= 384) | (2 * int(2 * nh <= 384)))
         assert self.plan.info["transform_tensor"] == want
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
@@ -115,7 +120,7 @@ def test_green_k_to_R(name):
     assert rel(GR, pack(s.G_R())) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1"])
+@pytest.mark.parametrize("name", SMALL + ["c1", "c0_fp64", "c1_fp64"])
 def test_polarizability(name):
     s = system(name)
     ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
