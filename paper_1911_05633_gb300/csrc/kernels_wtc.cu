@@ -65,15 +65,15 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
   for (int k0 = 0; k0 < N; k0 += B) {
     for (int x = tid; x < N * B; x += 512) Pan[x] = M[(long long)(x / B) * N + k0 + (x % B)];
     __syncthreads();
-    for (int m = 0; m < B; ++m) {
-      const int k = k0 + m;
-      // pivot among rows k .. N-1 (at most one candidate per thread)
+    // pivot candidates of the panel's first column (at most one row per thread); those of
+    // the later columns are gathered while the previous column is applied
+    {
       float best = -1.0f;
       int bi = N;
-      if (k + tid < N) {
-        const float2 z = Pan[(k + tid) * B + m];
+      if (k0 + tid < N) {
+        const float2 z = Pan[(k0 + tid) * B];
         best = fabsf(z.x) + fabsf(z.y);
-        bi = k + tid;
+        bi = k0 + tid;
       }
       for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -81,10 +81,14 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
-      __syncthreads();
+    }
+    __syncthreads();
+    for (int m = 0; m < B; ++m) {
+      const int k = k0 + m;
+      // pivot of column m from the 16 warp candidates
       if (wid == 0) {
-        best = lane < 16 ? rv[lane] : -1.0f;
-        bi = lane < 16 ? ri[lane] : N;
+        float best = lane < 16 ? rv[lane] : -1.0f;
+        int bi = lane < 16 ? ri[lane] : N;
         for (int o = 16; o > 0; o >>= 1) {
           const float ob = __shfl_down_sync(0xffffffffu, best, o);
           const int oi = __shfl_down_sync(0xffffffffu, bi, o);
@@ -108,7 +112,11 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
       for (int i = tid; i < N; i += 512)
         colk[i] = i == k ? make_float2(0.0f, 0.0f) : (i == p ? Pan[k * B + m] : Pan[i * B + m]);
       __syncthreads();
-      // phase B: rows k and p exchanged and the panel updated, each thread on its own elements
+      // phase B: rows k and p exchanged and the panel updated, each thread on its own
+      // elements (warp w on rows w, w + 16, ..., lane = column); lane m + 1 keeps the
+      // pivot candidates of the next column among rows below k
+      float best = -1.0f;
+      int bi = N;
       for (int x = tid; x < N * B; x += 512) {
         const int i = x / B, j = x % B;
         float2 v;
@@ -120,7 +128,12 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
           v = cfma(make_float2(-f.x, -f.y), rowk[j], src);
         }
         Pan[x] = v;
+        if (j == m + 1 && i > k) {
+          const float a = fabsf(v.x) + fabsf(v.y);
+          if (a > best) { best = a; bi = i; }
+        }
       }
+      if (m + 1 < B && lane == m + 1) { rv[wid] = best; ri[wid] = bi; }
       __syncthreads();
     }
     // the trailing update below uses Pan - I on the panel's diagonal
