@@ -35,26 +35,24 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
 }  // namespace
 
 // In-place FP32 Gauss-Jordan inverse with partial pivoting, one 512-thread block per
-// matrix (N a multiple of kGJ32B, at most 512).  Panels of kGJ32B columns are reduced
-// in shared memory; the row exchanges and the rank-kGJ32B update of the other columns,
-// A[:, T] += (Pan - I[:, panel]) Prow (Prow: the pivot rows before the update), run
-// per chunk of kGJ32C columns with 4 x 4 complex register blocks per thread.  At the
-// end the columns are permuted back by the composite of the pivot swaps.
+// matrix (N a multiple of kGJ32C, at most 512).  Panels of kGJ32B columns are reduced
+// in shared memory, each warp owning every 16th row with one column per lane, two
+// block barriers per column; the row exchanges and the rank-kGJ32B update of the other
+// columns, A[:, T] += (Pan - I[:, panel]) Prow (Prow: the pivot rows before the
+// update), run per chunk of kGJ32C columns with 8 x 4 complex register blocks per
+// thread.  At the end the columns are permuted back by the composite of the pivot swaps.
 __global__ void __launch_bounds__(512, 1)
 k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __restrict__ status) {
   constexpr int B = kGJ32B, C = kGJ32C;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* Pan = reinterpret_cast<float2*>(smraw);  // [N][B]
   float2* Buf = Pan + (size_t)N * B;               // Prow [B][C] / exchange staging [2B][C] / rows [16][N]
-  float2* colk = Buf + gj32_buf_elems(N);          // [N]
-  float2* rowk = colk + N;                         // [B]
-  float2* oldk = rowk + B;                         // [B]
-  int* pm = reinterpret_cast<int*>(oldk + B);      // [N] pivot row chosen for each column
+  int* pm = reinterpret_cast<int*>(Buf + gj32_buf_elems(N));  // [N] pivot row chosen for each column
   int* srcmap = pm + N;                            // [N]
   int* xdst = srcmap + N;                          // [2B]
   int* xsrc = xdst + 2 * B;                        // [2B]
-  __shared__ float rv[16];
-  __shared__ int ri[16];
+  __shared__ float rv[2][16];  // pivot candidates per warp, by column parity
+  __shared__ int ri[2][16];
   __shared__ int nx;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (N % C != 0 || N > 512) {
@@ -80,60 +78,52 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+      if (lane == 0) { rv[0][wid] = best; ri[0][wid] = bi; }
     }
     __syncthreads();
     for (int m = 0; m < B; ++m) {
-      const int k = k0 + m;
-      // pivot of column m from the 16 warp candidates
-      if (wid == 0) {
-        float best = lane < 16 ? rv[lane] : -1.0f;
-        int bi = lane < 16 ? ri[lane] : N;
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) {
-          pm[k] = bi < N ? bi : k;
-          if (!(best > 0.0f)) atomicExch(status, 1);
-        }
+      const int k = k0 + m, par = m & 1;
+      // every warp reduces the 16 candidates of column m itself (no barrier for the pivot)
+      float best = lane < 16 ? rv[par][lane] : -1.0f;
+      int bi = lane < 16 ? ri[par][lane] : N;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      __syncthreads();
-      const int p = pm[k];
-      // phase A: pivot row (scaled), old row k, column m as it reads after the swap
+      const int p = bi < N ? bi : k;
+      if (tid == 0) {
+        pm[k] = p;
+        if (!(best > 0.0f)) atomicExch(status, 1);
+      }
+      // lane j holds column j of the pivot row (scaled) and of the old row k
       const float2 d = Pan[p * B + m];
       const float den = d.x * d.x + d.y * d.y;
       const float2 inv = den > 0.0f ? make_float2(d.x / den, -d.y / den) : make_float2(0.0f, 0.0f);
-      if (tid < B) {
-        rowk[tid] = tid == m ? inv : cmul(Pan[p * B + tid], inv);
-        oldk[tid] = Pan[k * B + tid];
-      }
-      for (int i = tid; i < N; i += 512)
-        colk[i] = i == k ? make_float2(0.0f, 0.0f) : (i == p ? Pan[k * B + m] : Pan[i * B + m]);
-      __syncthreads();
-      // phase B: rows k and p exchanged and the panel updated, each thread on its own
-      // elements (warp w on rows w, w + 16, ..., lane = column); lane m + 1 keeps the
-      // pivot candidates of the next column among rows below k
-      float best = -1.0f;
-      int bi = N;
-      for (int x = tid; x < N * B; x += 512) {
-        const int i = x / B, j = x % B;
+      const float2 rowk = lane == m ? inv : cmul(Pan[p * B + lane], inv);
+      const float2 oldk = Pan[k * B + lane];
+      __syncthreads();  // rows p and k are read by every warp before their owners rewrite them
+      // rows k and p exchanged and every row updated: warp w owns rows w, w + 16, ..., lane
+      // = column; lane m + 1 keeps the pivot candidates of the next column below row k
+      best = -1.0f;
+      bi = N;
+#pragma unroll 4
+      for (int i = wid; i < N; i += 16) {
+        const float2 cur = i == p ? oldk : Pan[i * B + lane];
         float2 v;
         if (i == k) {
-          v = rowk[j];
+          v = rowk;
         } else {
-          const float2 src = j == m ? make_float2(0.0f, 0.0f) : (i == p ? oldk[j] : Pan[x]);
-          const float2 f = colk[i];
-          v = cfma(make_float2(-f.x, -f.y), rowk[j], src);
+          const float2 f = make_float2(__shfl_sync(0xffffffffu, cur.x, m), __shfl_sync(0xffffffffu, cur.y, m));
+          v = cfma(make_float2(-f.x, -f.y), rowk, lane == m ? make_float2(0.0f, 0.0f) : cur);
         }
-        Pan[x] = v;
-        if (j == m + 1 && i > k) {
+        Pan[i * B + lane] = v;
+        if (lane == m + 1 && i > k) {
           const float a = fabsf(v.x) + fabsf(v.y);
           if (a > best) { best = a; bi = i; }
         }
       }
-      if (m + 1 < B && lane == m + 1) { rv[wid] = best; ri[wid] = bi; }
+      if (m + 1 < B && lane == m + 1) { rv[par ^ 1][wid] = best; ri[par ^ 1][wid] = bi; }
       __syncthreads();
     }
     // the trailing update below uses Pan - I on the panel's diagonal
@@ -141,15 +131,24 @@ k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __res
     // composite row exchange of this panel: new row r = old row srcmap[r]
     for (int i = tid; i < N; i += 512) srcmap[i] = i;
     __syncthreads();
-    if (tid == 0) {
-      for (int m = 0; m < B; ++m) {
-        const int k = k0 + m, p = pm[k];
-        if (p != k) { const int t = srcmap[k]; srcmap[k] = srcmap[p]; srcmap[p] = t; }
-      }
+    if (wid == 0) {
+      if (lane == 0)
+        for (int m = 0; m < B; ++m) {
+          const int k = k0 + m, p = pm[k];
+          if (p != k) { const int t = srcmap[k]; srcmap[k] = srcmap[p]; srcmap[p] = t; }
+        }
+      __syncwarp();
+      // the moved rows (at most 2B), compacted in row order
       int n = 0;
-      for (int r = k0; r < N && n < 2 * B; ++r)
-        if (srcmap[r] != r) { xdst[n] = r; xsrc[n] = srcmap[r]; ++n; }
-      nx = n;
+      for (int r0 = k0; r0 < N; r0 += 32) {
+        const int r = r0 + lane;
+        const bool mv = r < N && srcmap[r] != r;
+        const unsigned bal = __ballot_sync(0xffffffffu, mv);
+        const int pos = n + __popc(bal & ((1u << lane) - 1u));
+        if (mv && pos < 2 * B) { xdst[pos] = r; xsrc[pos] = srcmap[r]; }
+        n += __popc(bal);
+      }
+      if (lane == 0) nx = min(n, 2 * B);
     }
     __syncthreads();
     const int n = nx;
@@ -514,36 +513,40 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
   if (!ok) {
     if (tid == 0) atomicExch(status, 2);
   } else {
-    const int r = 32 * warp + lane;
-    const int i = ib * 128 + r;
+    const int i = ib * 128 + 32 * warp + lane;
     const int ea = eA[b * N + i];
-    float* Ro = reinterpret_cast<float*>(R + (b * N + i) * (long long)N) + (imrow ? 1 : 0);
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    // The pipeline stages are free now: each warp stages its 32 x 16 results there, so
+    // that one store instruction covers two rows of 16 columns instead of 32 rows.
+    float* stg = reinterpret_cast<float*>(sm) + warp * (32 * 17);
+    float* Rw = reinterpret_cast<float*>(R + (b * N + ib * 128 + 32 * warp) * (long long)N) + (imrow ? 1 : 0);
     bool range_ok = true;
     for (int c0 = 0; c0 < kWTN; c0 += 16) {
-      long long sum[16];
-      float v[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) sum[c] = 0;
-#pragma unroll 1
-      for (int q = 0; q < 8; ++q) {
-        tmem_ld16(tm + lane_base + (uint32_t)(q * kWTN + c0), v);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) sum[c] += level_units52(v[c], q);
-      }
+      float v[128];  // accumulator q, column c at v[16 q + c]
+      tmem_ld16x4(tm + lane_base + (uint32_t)c0, kWTN, v);
+      tmem_ld16x4(tm + lane_base + (uint32_t)(4 * kWTN + c0), kWTN, v + 64);
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
+        long long val = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) val += level_units52(v[16 * q + c], q);
         const int j = jb * kWTN + c0 + c;
         const int e = ea + eX[b * N + j];  // (A X)_ij = 2^e sum
-        long long val = sum[c];
         if (!imrow && i == j) {
           if (e < -10 || e > 52) range_ok = false;
           else val -= 1ll << (52 - e);  // 1 = 2^(52 - e) units of 2^(e - 52)
         }
         if (e < -126 || e > 126) range_ok = false;
         const float sc = __int_as_float((127 + min(max(e, -126), 126)) << 23);  // 2^e
-        Ro[2 * (long long)j] = -sc * ((float)val * 0x1p-52f);
+        stg[lane * 17 + c] = -sc * ((float)val * 0x1p-52f);
       }
+      __syncwarp();
+#pragma unroll 4
+      for (int t = 0; t < 16; ++t) {
+        const int rr = 2 * t + (lane >> 4), cc = lane & 15;
+        Rw[2 * ((long long)rr * N + jb * kWTN + c0 + cc)] = stg[rr * 17 + cc];
+      }
+      __syncwarp();
     }
     if (!range_ok) atomicExch(status, 4);  // scale outside the FP32 exponent range
   }
@@ -719,23 +722,31 @@ k_refine_tc(const uint16_t* __restrict__ PX, const uint16_t* __restrict__ PR, co
   if (!ok) {
     if (tid == 0) atomicExch(status, 2);
   } else {
-    const int i = ib * 128 + 32 * warp + lane;
-    const long long row = (b * N + i) * (long long)N + jb * 128;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    for (int c0 = 0; c0 < 128; c0 += 16) {
-      float re[16], im[16];
-      tmem_ld16(tm + lane_base + (uint32_t)c0, re);
-      tmem_ld16(tm + lane_base + (uint32_t)(128 + c0), im);
+    // The pipeline stages are free now: each warp stages its 32 rows x 64 columns there,
+    // so that its loads and stores run along rows (32 consecutive columns per instruction).
+    float2* stg = reinterpret_cast<float2*>(sm) + warp * (32 * 65);
+    const long long row0 = (b * N + ib * 128 + 32 * warp) * (long long)N + jb * 128;
+    for (int c0 = 0; c0 < 128; c0 += 64) {
+      float re[64], im[64];
+      tmem_ld16x4(tm + lane_base + (uint32_t)c0, 16, re);
+      tmem_ld16x4(tm + lane_base + (uint32_t)(128 + c0), 16, im);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const long long o = row + c0 + c;
+      for (int c = 0; c < 64; ++c) stg[lane * 65 + c] = make_float2(re[c], im[c]);
+      __syncwarp();
+#pragma unroll 4
+      for (int t = 0; t < 64; ++t) {
+        const int rr = t >> 1, cc = 32 * (t & 1) + lane;
+        const float2 z = stg[rr * 65 + cc];
+        const long long o = row0 + (long long)rr * N + c0 + cc;
         if (FINAL) {
           const float2 h = hi[o], l = lo[o];
-          out[o] = make_double2(f2d(h.x) + f2d(l.x) + f2d(re[c]), f2d(h.y) + f2d(l.y) + f2d(im[c]));
+          out[o] = make_double2(f2d(h.x) + f2d(l.x) + f2d(z.x), f2d(h.y) + f2d(l.y) + f2d(z.y));
         } else {
-          lo[o] = make_float2(re[c], im[c]);
+          lo[o] = z;
         }
       }
+      __syncwarp();
     }
   }
   fence_before_sync();

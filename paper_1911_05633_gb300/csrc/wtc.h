@@ -31,7 +31,7 @@ __host__ __device__ constexpr size_t gj32_buf_elems(int N) {
 }
 // dynamic shared memory of k_gj_inverse_f32
 __host__ __device__ constexpr size_t gj32_smem(int N) {
-  return ((size_t)N * kGJ32B + gj32_buf_elems(N) + N + 2 * kGJ32B) * 8 + ((size_t)2 * N + 4 * kGJ32B) * 4;
+  return ((size_t)N * kGJ32B + gj32_buf_elems(N)) * 8 + ((size_t)2 * N + 4 * kGJ32B) * 4;
 }
 __global__ void k_gj_inverse_f32(float2* __restrict__ A, int N, long long mat_stride, int* __restrict__ status);
 __global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ dst, long long n);
