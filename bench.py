@@ -60,6 +60,10 @@ def parse():
                     help="inverse of the W solve: tensor-core refinement where supported, or FP64 Gauss-Jordan")
     ap.add_argument("--fp64-products", default="auto", choices=["auto", "fp64"],
                     help="FP64 Sigma: its W~ C^b stage as FP64-accurate tensor-core products, or FP64 arithmetic")
+    ap.add_argument("--r-b", type=float, default=0.0,
+                    help="radius of sphere B (bohr): pairs beyond it keep --n-prod-far product functions (Sec. 2)")
+    ap.add_argument("--n-prod-far", type=int, nargs="+", default=None,
+                    help="product functions per species kept by pairs beyond sphere B")
     return ap.parse_args()
 
 
@@ -94,28 +98,35 @@ def max_over_ranks(x, world):
 # workload and its algorithmic work
 # --------------------------------------------------------------------------------------
 
-def workload(cfg: int, small: bool = False):
+def workload(cfg: int, small: bool = False, r_b: float = 0.0, n_prod_far=None):
     """The bench workload, or with `small` the 8-atom cell on a 2x2x2 mesh with 12 tau
     nodes and a 5-bohr cutoff (N_PB = 384, 64 W-solve matrices): a case small enough for
-    full ncu captures of single kernels."""
+    full ncu captures of single kernels.  r_b > 0: pairs beyond sphere B keep n_prod_far
+    product functions per species (the reduced basis of Sec. 2)."""
     import synth
-    if small:
-        return synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2))
-    return synth.make_config(cfg)
+    cell = synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)) if small else synth.make_config(cfg)
+    if r_b > 0:
+        synth.with_far_basis(cell, r_b, n_prod_far or [max(1, sp.n_prod // 4) for sp in cell.species])
+    return cell
 
 
-def contraction_flops(cell, entries) -> float:
+def pb_dims(plan):
+    """(K_a(e), K_b(e)) of every entry, as the plan lays them out."""
+    return [plan.block_shape(e, "pb") for e in range(len(plan.entries))]
+
+
+def contraction_flops(cell, entries, kdims) -> float:
     """Real flops of one P (or Sigma) contraction over all entries and tau nodes:
-    2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2 + 2 K_a K_b n_b^2) per (entry, tau)."""
+    2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2 + 2 K_a K_b n_b^2) per (entry, tau), K_a and K_b
+    the entry's product-basis sizes."""
     f = 0.0
-    for a, b in entries[:, :2]:
+    for (a, b), (Ka, Kb) in zip(entries[:, :2], kdims):
         na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
-        Ka, Kb = cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
         f += 2.0 * (2 * Ka * na * na * nb + 4 * Ka * na * nb * nb + 2 * Ka * Kb * nb * nb)
     return f * cell.n_tau
 
 
-def kernel_work(name: str, cell, info, entries):
+def kernel_work(name: str, cell, info, entries, kdims):
     """Algorithmic work of one sweep for the kernels that can dominate it: (bound,
     work, kind, units) with flops for "alu"/"tensor" (real flops) and bytes for "hbm",
     and `units` the matrices (W solve) or pair entries the sweep processes; None for
@@ -137,21 +148,21 @@ def kernel_work(name: str, cell, info, entries):
     if name == "k_ozaki_residual<second>":  # 36 slice pairs
         return "tensor", 4 * 36 * 2.0 * N ** 3 * n_inv, "bf16", n_inv
     if name == "k_polarizability_fp64":  # stages 1 and 2 only when stage 3 runs on the tensor cores
-        f = stage_bc_flops(cell, entries) if info["p_tensor"] else contraction_flops(cell, entries)
+        f = stage_bc_flops(cell, entries, kdims) if info["p_tensor"] else contraction_flops(cell, entries, kdims)
         return "alu", f / (2 if info["c_symmetric"] else 1), "fp64", len(entries)
     if name == "k_self_energy_fp64":  # dynamic part (stages B, C only when stage A runs on the tensor cores)
-        full = contraction_flops(cell, entries)      # and the one-slice exchange term (all stages)
-        dyn = stage_bc_flops(cell, entries) if info["sigma_tensor"] else full
+        full = contraction_flops(cell, entries, kdims)  # and the one-slice exchange term (all stages)
+        dyn = stage_bc_flops(cell, entries, kdims) if info["sigma_tensor"] else full
         return "alu", dyn + full / nt, "fp64", len(entries)
     if name == "k_oz_gemm":  # 36 digit pairs x 2 flops x rows x padded K x padded N, every use in a sweep
-        f = oz_gemm_flops(cell, entries) if info["sigma_tensor"] else 0.0
+        f = oz_gemm_flops(cell, entries, kdims) if info["sigma_tensor"] else 0.0
         pad = lambda x, m: -(-x // m) * m
         rows = info["len_pb"]
         if info["p_tensor"]:  # P stage 3: 2 K_a rows per (entry, computed node), K = n_b^2, N = K_b
             ntp = oz_nt(max(cell.n_prod_of(i) for i in range(cell.n_atoms)))
             ne = (nt + 1) // 2 if info["c_symmetric"] else nt
-            for a, b in entries[:, :2]:
-                nb, Ka, Kb = cell.n_orb_of(int(b)), cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
+            for (a, b), (Ka, Kb) in zip(entries[:, :2], kdims):
+                nb = cell.n_orb_of(int(b))
                 f += ne * 2 * Ka * 36 * 2.0 * pad(nb * nb, 16) * pad(Kb, ntp)
         if info["transform_tensor"] & 1 and info["w_symmetric"]:  # W~ i nu -> tau, real input
             f += rows * 36 * 2.0 * pad(nn, 16) * pad(2 * nt, oz_nt(2 * nt))
@@ -173,13 +184,12 @@ def kernel_work(name: str, cell, info, entries):
     return None
 
 
-def stage_bc_flops(cell, entries) -> float:
+def stage_bc_flops(cell, entries, kdims) -> float:
     """Real flops of the two small stages of a contraction (Sigma after B = W~ C^b, or P
     before Y C^b): 2 (2 K_a n_a^2 n_b + 4 K_a n_a n_b^2) per (entry, tau)."""
     f = 0.0
-    for a, b in entries[:, :2]:
+    for (a, b), (Ka, _) in zip(entries[:, :2], kdims):
         na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
-        Ka = cell.n_prod_of(int(a))
         f += 2.0 * (2 * Ka * na * na * nb + 4 * Ka * na * nb * nb)
     return f * cell.n_tau
 
@@ -195,13 +205,14 @@ def oz_nt(n_cols: int) -> int:
     return NT
 
 
-def oz_gemm_flops(cell, entries) -> float:
+def oz_gemm_flops(cell, entries, kdims) -> float:
     """Tensor flops of the FP64-accurate W~ C^b products: per (entry, tau) 2 K_a rows
-    x 36 digit pairs x 2 x (K_b padded to 16) x (n_b^2 padded to the column tile)."""
+    x 36 digit pairs x 2 x (the entry's K_b padded to 16) x (n_b^2 padded to the column
+    tile)."""
     NT = oz_nt(max(cell.n_orb_of(i) ** 2 for i in range(cell.n_atoms)))
     f = 0.0
-    for a, b in entries[:, :2]:
-        nb, Ka, Kb = cell.n_orb_of(int(b)), cell.n_prod_of(int(a)), cell.n_prod_of(int(b))
+    for (a, b), (Ka, Kb) in zip(entries[:, :2], kdims):
+        nb = cell.n_orb_of(int(b))
         f += 2 * Ka * 36 * 2.0 * (-(-Kb // 16) * 16) * (-(-nb * nb // NT) * NT)
     return f * cell.n_tau
 
@@ -358,7 +369,7 @@ def flush_l2(buf):
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
-    cell = workload(args.config, args.small)
+    cell = workload(args.config, args.small, args.r_b, args.n_prod_far)
     sw = Sweep(cell, args.precision, device=local, w_solver=args.w_solver, fp64_products=args.fp64_products)
     Gk = cell.green_k_tau()
     vq, _ = cell.coulomb()
@@ -404,6 +415,7 @@ def run_ours(args, rank, world, local):
     # roofline of the dominant kernel, timed live by the library's event pairs
     ent = sw.plan.entries
     inf = sw.plan.info
+    kd = pb_dims(sw.plan)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -416,7 +428,7 @@ def run_ours(args, rank, world, local):
     if ktimes:
         dom_k = max(ktimes, key=lambda k: ktimes[k][0])
         ms_tot, nl = ktimes[dom_k]
-        w = kernel_work(dom_k, cell, inf, ent)
+        w = kernel_work(dom_k, cell, inf, ent, kd)
         if w is not None:
             bound, work, kind, units = w
             per_launch = work * args.steps / nl
@@ -438,8 +450,8 @@ def run_ours(args, rank, world, local):
                     "frac": round(ach / peak, 4) if peak else None,
                     "traffic": traffic_of(dom_k, units * args.steps / nl), "peak_source": src,
                     "work_per_launch": per_launch, "launch_ms": round(dur * 1e3, 4)}
-    fl_P = contraction_flops(cell, ent) / (2 if inf["c_symmetric"] else 1)  # mirrored nodes not computed
-    fl_S = contraction_flops(cell, ent)
+    fl_P = contraction_flops(cell, ent, kd) / (2 if inf["c_symmetric"] else 1)  # mirrored nodes not computed
+    fl_S = contraction_flops(cell, ent, kd)
     fl_W = wsolve_flops(cell, inf)
     work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
     contraction_tflops = {k: round(work[k] / (stage_mean[Sweep.STAGES.index(k)] * 1e-3) / 1e12, 4)
@@ -451,6 +463,7 @@ def run_ours(args, rank, world, local):
                "w_solve_ms": round(float(stage_mean[Sweep.STAGES.index("W_solve")]), 4),
                "stages": "every row except the W solve, which is timed on its own"}
 
+    mixed_err = mixed_vs_fp64(sw, stream) if args.precision == "mixed" else None
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(sw, Gk, vq, stream, args)
@@ -466,6 +479,9 @@ def run_ours(args, rank, world, local):
                                      else "FP64 arithmetic"),
                    "w_inverse": ("FP32 Gauss-Jordan + two residual refinements on the tensor cores (FP64-accurate)"
                                  if inf["w_tensor"] else "FP64 Gauss-Jordan"),
+                   "far_basis": ({"r_b_bohr": cell.r_b, "n_prod_far": [sp.n_prod_far for sp in cell.species],
+                                  "entries_far": inf["n_entries_far"], "len_pb": inf["len_pb"]}
+                                 if inf["n_entries_far"] else None),
                    "parallelism": f"replicas x{world}"},
         "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
         "p_sigma_sweep": p_sigma,
@@ -479,7 +495,42 @@ def run_ours(args, rank, world, local):
         "kernels": kernels,
         "e2e": e2e,
     }
+    if mixed_err is not None:
+        out["mixed_vs_fp64"] = mixed_err
     return out, cell
+
+
+def mixed_vs_fp64(sw, stream):
+    """Relative Frobenius errors of the mixed path against the FP64 GPU path of the same
+    plan on the same inputs (after the timed region): the P contraction (same G(R)), the
+    Sigma contraction (same G(R) and W~(R)), and the whole sweep's Sigma(R, tau) and
+    Sigma(k, i omega), whose W~ comes from the mixed P through the W solve."""
+    torch = sw.torch
+    outs = {}
+    for prec in ("mixed", "fp64"):
+        sw.prec = prec
+        with torch.cuda.stream(stream):
+            sw.run(stream)
+        sw.plan.sync(stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        outs[prec] = {"P": sw.P_R.clone(), "Sigma_chain": sw.S_R.clone(), "Sigma_k_chain": sw.S_k.clone()}
+    # the Sigma contraction alone, in mixed precision on the FP64 sweep's G(R) and W~(R)
+    S_mix, Sx = torch.empty_like(sw.S_R), torch.empty_like(sw.Sx_R)
+    with torch.cuda.stream(stream):
+        sw.plan.self_energy_tau(sw.G_R, sw.W_R, v_R=sw.v_R, Sig_R=S_mix, Sigx_R=Sx, precision="mixed",
+                                stream=stream.cuda_stream)
+    sw.plan.sync(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    outs["mixed"]["Sigma_contraction"] = S_mix
+    outs["fp64"]["Sigma_contraction"] = outs["fp64"]["Sigma_chain"]
+    sw.prec = "mixed"
+    keys = ("P", "Sigma_contraction", "Sigma_chain", "Sigma_k_chain")
+    rel = {k: float(torch.linalg.vector_norm(outs["mixed"][k] - outs["fp64"][k]) /
+                    torch.linalg.vector_norm(outs["fp64"][k])) for k in keys}
+    del outs
+    return {**{k: float(f"{v:.3e}") for k, v in rel.items()}, "tolerance_contractions": 1e-6,
+            "reference": "the FP64 GPU path, same plan and inputs",
+            "note": "the chain values carry the W solve's amplification of P's error"}
 
 
 def run_e2e(sw, Gk, vq, stream, args):
@@ -528,7 +579,7 @@ def oracle_sample(cell, n_nu_sample: int = 3):
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     GR = oracle.fourier_k_to_R(Gk, orc.entries, orc.kmesh, cell.orb_offsets, cell.orb_offsets)
-    PR = oracle.polarizability_R(GR, orc.entries, orc.C_atom, cell.spin)
+    PR = oracle.polarizability_R(GR, orc.entries, orc.C_atom, cell.spin, orc.kdims)
     Piw = oracle.transform(orc.B_fwd, PR)
     t_a = time.perf_counter() - t0
     nn = cell.nu_idx.size
@@ -562,7 +613,7 @@ def cpu_cores():
 
 
 def run_reference(args, rank, world):
-    cell = workload(args.config, args.small)
+    cell = workload(args.config, args.small, args.r_b, args.n_prod_far)
     if rank != 0:
         return None
     secs = []

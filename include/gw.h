@@ -21,7 +21,12 @@
  * block starting at element n_slices * off[e], where off[] is the prefix sum
  * of rows_e * cols_e returned by gw_plan_offsets():
  *   GW_BLOCK_ORB: rows_e = n_a, cols_e = n_b   (G, Sigma)
- *   GW_BLOCK_PB : rows_e = K_a, cols_e = K_b   (P, W~, v)
+ *   GW_BLOCK_PB : rows_e = K_a(e), cols_e = K_b(e)   (P, W~, v)
+ * K_a(e) is the product-basis size of atom a for entry e: n_prod of its species,
+ * or n_prod_far for an entry beyond the radius r_b of sphere B (the reduced
+ * basis of distant pairs, Sec. 2, Fig. 2); those entries keep the FIRST
+ * n_prod_far product functions of each atom.  gw_plan_entry_dims() returns the
+ * per-entry shapes.
  * Dense k-space buffers are [N_k][n_slices][N][N] with N = total orbitals
  * (ORB) or total product functions (PB), atoms in order.
  */
@@ -73,6 +78,9 @@ typedef struct {
   const int* n_orb;       /* host [n_species], 1..16 */
   const int* n_prod;      /* host [n_species], 1..128 */
   const double* const* C; /* host [n_species] pointers */
+  const int* n_prod_far;  /* host [n_species], 1..n_prod, or NULL: product functions kept for
+                             pair entries beyond gw_options.r_b (Sec. 2, the pairs between
+                             spheres B and C); NULL keeps n_prod for every entry */
 } gw_basis;
 
 /* Imaginary-time nodes and sampled Matsubara indices (Appendix A grid).
@@ -101,6 +109,10 @@ typedef struct {
                              stage of the GW_FP64 P (every n^2 <= 384) and the structured
                              bosonic transforms (reduction <= 384);
                              1: FP64 arithmetic only */
+  double r_b;             /* radius of sphere B in bohr (Sec. 2, Fig. 2): an entry whose
+                             minimum-image distance |R + t_b - t_a| exceeds r_b by more than
+                             1e-9 bohr^2 in the square keeps n_prod_far product functions per
+                             atom; <= 0 (or n_prod_far NULL): every entry keeps n_prod */
 } gw_options;
 
 typedef struct {
@@ -123,6 +135,7 @@ typedef struct {
   int transform_tensor;       /* bit 0: GW_IN_REAL bosonic i nu -> tau, bit 1: GW_IN_MIRROR bosonic
                                  tau -> i nu of the product-basis layout by FP64-accurate
                                  tensor-core products (device plans) */
+  int n_entries_far;          /* entries with the reduced product basis (beyond r_b) */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */
@@ -147,6 +160,10 @@ gw_status gw_plan_entries(gw_plan_t plan, int64_t* rows);
 
 /* Host copy of the per-entry block offsets, [n_entries + 1] int64 (see the layout note). */
 gw_status gw_plan_offsets(gw_plan_t plan, gw_block kind, int64_t* off);
+
+/* Host copy of the per-entry block shapes, rows[e] x cols[e] ([n_entries] int32 each):
+ * (n_a, n_b) for GW_BLOCK_ORB, (K_a(e), K_b(e)) for GW_BLOCK_PB (see the layout note). */
+gw_status gw_plan_entry_dims(gw_plan_t plan, gw_block kind, int32_t* rows, int32_t* cols);
 
 /* Host copy of a transform matrix, complex [n_out][n_in] interleaved doubles:
  * (FERMION, TAU_TO_IW) n_omega x n_tau, (FERMION, IW_TO_TAU) n_tau x n_omega,

@@ -11,6 +11,10 @@ Every function follows one statement of the paper, cited in its docstring:
 * Sec. 2, "basic approximation" (Fig. 1): two-point functions F^R_{rr'} are kept
   only for |R + r - r'| <= R_max, and the k-mesh must be at least the number of
   cells the R_max sphere encloses or crosses.  -> ``kmesh_rule``, ``pair_list``
+* Sec. 2, the reduced basis of distant pairs (Fig. 2): a pair farther apart than
+  the radius of sphere B keeps a smaller product basis (the first n_prod_far
+  functions of each atom here) -> ``entry_far``, ``entry_pb_dims``; every
+  product-basis function below takes its block shapes from its inputs
 * Sec. 2, transformations between R and k spaces over the kept pairs
   -> ``fourier_k_to_R``, ``fourier_R_to_k``
 * Eq. P_MM with the sign and the tau pairing of Eq. P_II -> ``polarizability_R``
@@ -42,6 +46,8 @@ from numpy.polynomial.legendre import leggauss
 __all__ = [
     "kmesh_rule",
     "pair_list",
+    "entry_far",
+    "entry_pb_dims",
     "green0_k_tau",
     "fourier_k_to_R",
     "fourier_R_to_k",
@@ -151,10 +157,38 @@ def _occ_factor(xi: np.ndarray, t: float, beta: float) -> np.ndarray:
 # Sec. 2: R <-> k transforms restricted to the kept entries
 # ----------------------------------------------------------------------------
 
-def fourier_k_to_R(F_k: np.ndarray, entries: np.ndarray, kmesh, row_off, col_off) -> List[np.ndarray]:
+def entry_far(lattice: np.ndarray, frac: np.ndarray, entries: np.ndarray, r_b: float) -> np.ndarray:
+    """Entries beyond sphere B (Sec. 2, Fig. 2): the minimum-image distance
+    |R + t_b - t_a| of the entry exceeds r_b (its square by more than 1e-9 bohr^2).
+    r_b <= 0: no entry is far."""
+    A = np.asarray(lattice, dtype=np.float64)
+    frac = np.asarray(frac, dtype=np.float64)
+    far = np.zeros(len(entries), dtype=bool)
+    if r_b <= 0.0:
+        return far
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        x = (np.asarray(row[5:8], dtype=np.float64) + frac[b] - frac[a]) @ A
+        far[e] = float(x @ x) > r_b * r_b + 1e-9
+    return far
+
+
+def entry_pb_dims(entries: np.ndarray, far: np.ndarray, n_prod_atom, n_prod_far_atom) -> List[Tuple[int, int]]:
+    """(K_a(e), K_b(e)) per entry: the full product basis of each atom, or its reduced
+    size n_prod_far for an entry beyond sphere B (the first functions are kept)."""
+    out = []
+    for e, row in enumerate(entries):
+        a, b = int(row[0]), int(row[1])
+        src = n_prod_far_atom if far[e] else n_prod_atom
+        out.append((int(src[a]), int(src[b])))
+    return out
+
+
+def fourier_k_to_R(F_k: np.ndarray, entries: np.ndarray, kmesh, row_off, col_off, dims=None) -> List[np.ndarray]:
     """F_ab(R) = (1/N_k) sum_k e^{-i k.R} F_ab(k) for each kept entry (brute force).
 
-    F_k: [N_k][n_slices][N][N].  Returns a list over entries of [n_slices][n_a][n_b].
+    F_k: [N_k][n_slices][N][N].  Returns a list over entries of [n_slices][rows][cols]:
+    the atoms' full blocks, or the top-left dims[e] of them (an entry beyond sphere B).
     """
     kint = np.array(list(np.ndindex(*kmesh)), dtype=np.int64)
     ph = _class_phase(kint, kmesh, entries[:, 2:5])  # [N_k][E]
@@ -162,7 +196,8 @@ def fourier_k_to_R(F_k: np.ndarray, entries: np.ndarray, kmesh, row_off, col_off
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        blk = F_k[:, :, row_off[a]:row_off[a + 1], col_off[b]:col_off[b + 1]]
+        r, c = (row_off[a + 1] - row_off[a], col_off[b + 1] - col_off[b]) if dims is None else dims[e]
+        blk = F_k[:, :, row_off[a]:row_off[a] + r, col_off[b]:col_off[b] + c]
         out.append(np.einsum("k,ksij->sij", np.conj(ph[:, e]), blk) / nk)
     return out
 
@@ -175,7 +210,8 @@ def fourier_R_to_k(F_R: Sequence[np.ndarray], entries: np.ndarray, kmesh, row_of
     out = np.zeros((len(kint), ns, row_off[-1], col_off[-1]), np.complex128)
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        out[:, :, row_off[a]:row_off[a + 1], col_off[b]:col_off[b + 1]] += (
+        r, c = F_R[e].shape[1:]  # the full block, or the kept top-left part of it
+        out[:, :, row_off[a]:row_off[a] + r, col_off[b]:col_off[b] + c] += (
             ph[:, e][:, None, None, None] * F_R[e][None])
     return out
 
@@ -185,17 +221,19 @@ def fourier_R_to_k(F_R: Sequence[np.ndarray], entries: np.ndarray, kmesh, row_of
 # ----------------------------------------------------------------------------
 
 def polarizability_R(G_R: Sequence[np.ndarray], entries: np.ndarray, C_atom: Sequence[np.ndarray],
-                     spin: int = 2) -> List[np.ndarray]:
+                     spin: int = 2, kdims=None) -> List[np.ndarray]:
     """P_{aK, bK'}(R, tau_i) per kept entry (Eq. P_MM, sign and pairing of Eq. P_II).
 
     P = -s sum_{L L'' L' L'''} C^a_{K; L L''} G_{aL, bL'}(R, tau_i)
             conj(G_{aL'', bL'''}(R, beta - tau_i)) C^b_{K'; L' L'''},
-    beta - tau_i being the mirrored node tau_{N-1-i}.
+    beta - tau_i being the mirrored node tau_{N-1-i}; K < K_a(e), K' < K_b(e) when
+    kdims gives the entry's product-basis sizes (the reduced basis beyond sphere B).
     """
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        out.append(-spin * _p_block(C_atom[a], G_R[e], np.conj(G_R[e][::-1]), C_atom[b]))
+        Ka, Kb = (len(C_atom[a]), len(C_atom[b])) if kdims is None else kdims[e]
+        out.append(-spin * _p_block(C_atom[a][:Ka], G_R[e], np.conj(G_R[e][::-1]), C_atom[b][:Kb]))
     return out
 
 
@@ -329,6 +367,7 @@ def screened_W(P_R_iw: Sequence[np.ndarray], entries: np.ndarray, v_q: np.ndarra
     """
     nk = v_q.shape[0]
     n_nu = P_R_iw[0].shape[0]
+    dims = [blk.shape[1:] for blk in P_R_iw]  # the entries' product-basis blocks
     P_q = fourier_R_to_k(P_R_iw, entries, kmesh, pb_off, pb_off)  # [N_k][N_nu][N][N]
     I = np.eye(v_q.shape[1])
     if q_subset is not None or nu_subset is not None:
@@ -339,7 +378,7 @@ def screened_W(P_R_iw: Sequence[np.ndarray], entries: np.ndarray, v_q: np.ndarra
     for q in range(nk):
         for n in range(n_nu):
             Wt_q[q, n] = np.linalg.solve(I - v_q[q] @ P_q[q, n], v_q[q]) - v_q[q]
-    return fourier_k_to_R(Wt_q, entries, kmesh, pb_off, pb_off), Wt_q
+    return fourier_k_to_R(Wt_q, entries, kmesh, pb_off, pb_off, dims), Wt_q
 
 
 # ----------------------------------------------------------------------------
@@ -348,11 +387,13 @@ def screened_W(P_R_iw: Sequence[np.ndarray], entries: np.ndarray, v_q: np.ndarra
 
 def self_energy_R(G_R, Wt_R, entries, C_atom) -> List[np.ndarray]:
     """Sigma_{aL, bL'}(R, tau_i) = -sum C^a_{K; L L''} G_{aL'', bL'''}(R, tau_i)
-    W~_{aK, bK'}(R, tau_i) C^b_{K'; L' L'''}  (Eq. S_MM, indices as read above)."""
+    W~_{aK, bK'}(R, tau_i) C^b_{K'; L' L'''}  (Eq. S_MM, indices as read above), K and K'
+    over the entry's product basis (the shape of its W~ block)."""
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        out.append(-_s_block(C_atom[a], G_R[e], Wt_R[e], C_atom[b]))
+        Ka, Kb = Wt_R[e].shape[1:]
+        out.append(-_s_block(C_atom[a][:Ka], G_R[e], Wt_R[e], C_atom[b][:Kb]))
     return out
 
 
@@ -362,7 +403,8 @@ def exchange_R(G_R, v_R, entries, C_atom) -> List[np.ndarray]:
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        out.append(_s_block(C_atom[a], G_R[e][-1:], v_R[e][None], C_atom[b])[0])
+        Ka, Kb = v_R[e].shape
+        out.append(_s_block(C_atom[a][:Ka], G_R[e][-1:], v_R[e][None], C_atom[b][:Kb])[0])
     return out
 
 
@@ -408,21 +450,27 @@ class OracleSystem:
         self.B_fwd = fourier_matrix(cell.beta, self.tau, cell.nu_idx, "B")
         self.F_inv = inverse_matrix(self.F_fwd)
         self.B_inv = inverse_matrix(self.B_fwd)
+        # the reduced product basis beyond sphere B (Sec. 2, Fig. 2), when the cell has one
+        r_b = float(getattr(cell, "r_b", 0.0) or 0.0)
+        self.far = entry_far(cell.lattice, cell.frac, self.entries, r_b)
+        n_full = [len(C) for C in self.C_atom]
+        n_far = [cell.species[s].n_prod_far or cell.species[s].n_prod for s in cell.species_of_atom] \
+            if r_b > 0 else n_full
+        self.kdims = entry_pb_dims(self.entries, self.far, n_full, n_far)
 
     def v_R(self, v_class: np.ndarray) -> List[np.ndarray]:
         out = []
-        for row in self.entries:
+        for e, row in enumerate(self.entries):
             a, b = int(row[0]), int(row[1])
             c = int(np.ravel_multi_index(tuple(row[2:5]), self.kmesh))
-            Ka = self.pb_off[a + 1] - self.pb_off[a]
-            Kb = self.pb_off[b + 1] - self.pb_off[b]
+            Ka, Kb = self.kdims[e]
             out.append(v_class[a, b, c, :Ka, :Kb].astype(np.complex128))
         return out
 
     def sweep(self, G_k: np.ndarray, v_q: np.ndarray, v_class: np.ndarray) -> dict:
         r = {}
         r["G_R"] = fourier_k_to_R(G_k, self.entries, self.kmesh, self.orb_off, self.orb_off)
-        r["P_R"] = polarizability_R(r["G_R"], self.entries, self.C_atom, self.spin)
+        r["P_R"] = polarizability_R(r["G_R"], self.entries, self.C_atom, self.spin, self.kdims)
         r["P_iw"] = transform(self.B_fwd, r["P_R"])
         r["Wt_iw"], r["Wt_q"] = screened_W(r["P_iw"], self.entries, v_q, self.kmesh, self.pb_off)
         r["Wt_R"] = transform(self.B_inv, r["Wt_iw"])

@@ -172,6 +172,7 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
   g.s_stride = s_stride;
   g.ld = dense_n(p, kind);
   g.pb = kind == GW_BLOCK_PB;
+  g.row_off = kind == GW_BLOCK_PB ? p->d_pb_off : p->d_orb_off;
   g.F_sub = F_sub;
   g.sub_k_stride = sub_k_stride;
   g.sub_s_stride = sub_s_stride;
@@ -493,6 +494,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->c_symmetric = h.c_symmetric;
   info->len_orb = h.off_orb.back();
   info->len_pb = h.off_pb.back();
+  info->n_entries_far = h.n_far;
   info->workspace_bytes = p->ws_bytes;
   info->nu_chunk = p->nu_chunk;
   info->cond_fermion = h.cond_f;
@@ -516,6 +518,21 @@ gw_status gw_plan_offsets(gw_plan_t p, gw_block kind, int64_t* off) {
   if (!p || !off) { set_last_error("null argument"); return GW_ERR_ARG; }
   const std::vector<int64_t>& v = (kind == GW_BLOCK_PB) ? p->h.off_pb : p->h.off_orb;
   std::memcpy(off, v.data(), v.size() * sizeof(int64_t));
+  return GW_OK;
+}
+
+gw_status gw_plan_entry_dims(gw_plan_t p, gw_block kind, int32_t* rows, int32_t* cols) {
+  if (!p || !rows || !cols) { set_last_error("null argument"); return GW_ERR_ARG; }
+  const gw::HostPlan& h = p->h;
+  for (int e = 0; e < h.n_entries(); ++e) {
+    if (kind == GW_BLOCK_PB) {
+      rows[e] = h.Ka_e[e];
+      cols[e] = h.Kb_e[e];
+    } else {
+      rows[e] = h.n_orb[h.species[h.entries[8 * e]]];
+      cols[e] = h.n_orb[h.species[h.entries[8 * e + 1]]];
+    }
+  }
   return GW_OK;
 }
 
@@ -894,15 +911,17 @@ __global__ void k_zero_slots(const gw::DevEntry* __restrict__ ent, int n_slots, 
 // W~_R[e][slot0 + s] += scale w conj(e^{iq.R}) (W(q) - v(q)) for one momentum q, taking the
 // real part in symmetric mode; grid (active pair, slice, element chunk).
 __global__ void k_gather_one_q(const gw::DevEntry* __restrict__ ent, const int* __restrict__ pair_first,
-                               const double2* __restrict__ phase, int n_k, int q, double w,
-                               const double2* __restrict__ Wq, long long s_stride, const double2* __restrict__ vq,
-                               int ld, double2* __restrict__ out, int n_slots, int slot0, double scale, int real_only) {
+                               const int* __restrict__ pb_off, const double2* __restrict__ phase, int n_k, int q,
+                               double w, const double2* __restrict__ Wq, long long s_stride,
+                               const double2* __restrict__ vq, int ld, double2* __restrict__ out, int n_slots,
+                               int slot0, double scale, int real_only) {
   const int p = blockIdx.x;
   const int s = blockIdx.y;
   const int e0 = pair_first[p], e1 = pair_first[p + 1];
   const gw::DevEntry E0 = ent[e0];
-  const int cols = E0.Kb;
-  const int blk = E0.Ka * cols;
+  // the pair's full block; an entry beyond sphere B keeps its top-left K_a(e) x K_b(e)
+  const int cols = pb_off[E0.b + 1] - pb_off[E0.b];
+  const int blk = (pb_off[E0.a + 1] - pb_off[E0.a]) * cols;
   const int idx = blockIdx.z * blockDim.x + threadIdx.x;
   if (idx >= blk) return;
   const int i = idx / cols, j = idx - (idx / cols) * cols;
@@ -911,10 +930,12 @@ __global__ void k_gather_one_q(const gw::DevEntry* __restrict__ ent, const int* 
   const double2 b = vq[(long long)q * ld * ld + el];
   const double vr = (a.x - b.x) * w * scale, vi = (a.y - b.y) * w * scale;
   for (int e = e0; e < e1; ++e) {
+    const gw::DevEntry& E = ent[e];
+    if (i >= E.Ka || j >= E.Kb) continue;
     const double2 ph = phase[(long long)e * n_k + q];
     const double rr = ph.x * vr + ph.y * vi;
     const double ri = real_only ? 0.0 : ph.x * vi - ph.y * vr;
-    double2* o = out + ent[e].off_pb * n_slots + (long long)(slot0 + s) * blk + idx;
+    double2* o = out + E.off_pb * n_slots + (long long)(slot0 + s) * E.Ka * E.Kb + i * E.Kb + j;
     const double2 t = *o;
     *o = make_double2(t.x + rr, t.y + ri);
   }
@@ -987,7 +1008,7 @@ extern "C" gw_status gw_screened_W_iw_noalloc(gw_plan_t p, const void* P_R_iw, c
       else gw::k_gj_inverse<<<nc, 512, p->smem_GJ, s>>>(slots, perm, (int)N, NN, p->d_status);
       if ((st = check_launch("k_gj_inverse")) != GW_OK) return st;
       dim3 gg((unsigned)p->n_active, (unsigned)nc, (unsigned)((maxblk + 127) / 128));
-      k_gather_one_q<<<gg, 128, 0, s>>>(p->d_ent, p->d_pair_first, p->d_phase, h.n_k, qh[qi], qw[qi], slots, NN, v,
+      k_gather_one_q<<<gg, 128, 0, s>>>(p->d_ent, p->d_pair_first, p->d_pb_off, p->d_phase, h.n_k, qh[qi], qw[qi], slots, NN, v,
                                          (int)N, (double2*)Wt_R_iw, h.n_nu, slot0, 1.0 / h.n_k, p->w_sym ? 1 : 0);
       if ((st = check_launch("k_gather_one_q")) != GW_OK) return st;
     }

@@ -20,6 +20,7 @@ struct GatherArgs {
   long long k_stride, s_stride;
   int ld;
   int pb;                  // 1: product-basis blocks, 0: orbital blocks
+  const int* row_off;      // [n_atoms + 1] orbital or product offsets (the full pair block)
   const double2* F_sub;    // optional dense input subtracted from F_k
   long long sub_k_stride, sub_s_stride;
   double2* F_R;            // entry layout output

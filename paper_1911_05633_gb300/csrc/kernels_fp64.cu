@@ -33,7 +33,8 @@ __device__ __forceinline__ double2 rfma(double r, double2 b, double2 c) {
 
 // ---------------------------------------------------------------------------
 // k -> R gather:  F_R[e][s][i][j] = scale * sum_k conj(ph[e][k]) (F_k - F_sub)[k][s][oa+i][ob+j]
-// grid: (active pair, slice, element chunk of blockDim.x)
+// grid: (active pair, slice, element chunk of blockDim.x) over the pair's full block; an
+// entry with a reduced product basis (beyond sphere B) keeps its top-left K_a(e) x K_b(e).
 // ---------------------------------------------------------------------------
 constexpr int kGatherEnt = 8;
 
@@ -43,8 +44,8 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
   const int e0 = g.pair_first[p];
   const int e1 = g.pair_first[p + 1];
   const DevEntry E0 = g.ent[e0];
-  const int rows = g.pb ? E0.Ka : E0.na;
-  const int cols = g.pb ? E0.Kb : E0.nb;
+  const int rows = g.row_off[E0.a + 1] - g.row_off[E0.a];
+  const int cols = g.row_off[E0.b + 1] - g.row_off[E0.b];
   const int ro = g.pb ? E0.pa : E0.oa;
   const int co = g.pb ? E0.pb : E0.ob;
   const int blk = rows * cols;
@@ -54,6 +55,15 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
   const long long in_el = (long long)(ro + i) * g.ld + (co + j);
   for (int eb = e0; eb < e1; eb += kGatherEnt) {
     const int ne = min(kGatherEnt, e1 - eb);
+    // the entries of this chunk whose kept block holds (i, j)
+    unsigned need = 0;
+#pragma unroll
+    for (int m = 0; m < kGatherEnt; ++m)
+      if (m < ne) {
+        const DevEntry& E = g.ent[eb + m];
+        if (i < (g.pb ? E.Ka : E.na) && j < (g.pb ? E.Kb : E.nb)) need |= 1u << m;
+      }
+    if (!need) continue;
     double2 acc[kGatherEnt];
 #pragma unroll
     for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
@@ -73,23 +83,24 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
       if (g.real_only) {  // Re(conj(ph) v) only
 #pragma unroll
         for (int m = 0; m < kGatherEnt; ++m)
-          if (m < ne) {
+          if ((need >> m) & 1u) {
             const double2 ph = g.phase[(long long)(eb + m) * g.n_k + k];
             acc[m].x = fma(ph.x, v.x, fma(ph.y, v.y, acc[m].x));
           }
       } else {
 #pragma unroll
         for (int m = 0; m < kGatherEnt; ++m)
-          if (m < ne) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
+          if ((need >> m) & 1u) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
       }
     }
 #pragma unroll
     for (int m = 0; m < kGatherEnt; ++m) {
-      if (m < ne) {
+      if ((need >> m) & 1u) {
         const DevEntry& E = g.ent[eb + m];
         const long long off = g.pb ? E.off_pb : E.off_orb;
+        const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
         double2 r = make_double2(acc[m].x * g.scale, g.real_only ? 0.0 : acc[m].y * g.scale);
-        g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * blk + idx] = r;
+        g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] = r;
       }
     }
   }
@@ -118,9 +129,11 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
     for (int m = 0; m < kGatherEnt; ++m) {
       v[m] = make_double2(0.0, 0.0);
       if (m < ne) {
+        // an entry with a reduced product basis holds only the top-left K_a(e) x K_b(e)
         const DevEntry& E = g.ent[eb + m];
         const long long off = g.pb ? E.off_pb : E.off_orb;
-        v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * blk + idx];
+        const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+        if (i < re && j < ce) v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
       }
     }
     for (int kk = 0; kk < g.n_k_out; ++kk) {

@@ -435,8 +435,8 @@ gw_status oz_sigma_init(OzSigma& o, const HostPlan& h, size_t cap) {
   std::vector<long long> offB(E + 1, 0);
   std::vector<int> Ka(E), rows1(E);
   for (int e = 0; e < E; ++e) {
-    const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
-    Ka[e] = h.n_prod[h.species[a]];
+    const int b = (int)h.entries[8 * e + 1];
+    Ka[e] = h.Ka_e[e];  // product functions of a kept by this entry
     const int nb = h.n_orb[h.species[b]];
     offB[e + 1] = offB[e] + (long long)Ka[e] * nb * nb;
     rows1[e] = 2 * Ka[e];
@@ -569,8 +569,7 @@ gw_status oz_transform_init(OzTransform& o, const HostPlan& h) {
   // row tiles: the K_a K_b elements of every entry, 128 per tile
   std::vector<int> te, tr;
   for (int e = 0; e < h.n_entries(); ++e) {
-    const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
-    const int blk = h.n_prod[h.species[a]] * h.n_prod[h.species[b]];
+    const int blk = h.Ka_e[e] * h.Kb_e[e];
     for (int r0 = 0; r0 < blk; r0 += 128) {
       te.push_back(e);
       tr.push_back(r0);
@@ -693,8 +692,8 @@ gw_status oz_pol_init(OzPol& o, const HostPlan& h, size_t cap) {
   std::vector<int> rows1(E);
   long long rows_all = 0;
   for (int e = 0; e < E; ++e) {
-    const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
-    const int Ka = h.n_prod[h.species[a]], nb = h.n_orb[h.species[b]];
+    const int b = (int)h.entries[8 * e + 1];
+    const int Ka = h.Ka_e[e], nb = h.n_orb[h.species[b]];
     offB[e + 1] = offB[e] + (long long)Ka * nb * nb;
     rows1[e] = 2 * Ka;
     rows_all += rows1[e];

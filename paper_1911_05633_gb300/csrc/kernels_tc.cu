@@ -92,7 +92,8 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
   }
   // B operand (C^b split in three planes, canonical layout) and a zeroed A operand
   const int sb = species_of_atom[E.b];
-  const uint4* bsrc = reinterpret_cast<const uint4*>(Bsplit + Bsplit_off[sb]);
+  // the planes of C^b for this entry's product-basis size (full, or reduced beyond sphere B)
+  const uint4* bsrc = reinterpret_cast<const uint4*>(Bsplit + Bsplit_off[2 * sb + E.far]);
   uint4* bdst = reinterpret_cast<uint4*>(Bp);
   const int nb16 = (int)(3u * L.NP * L.KD * 2u / 16u);
   for (int x = tid; x < nb16; x += blockDim.x) bdst[x] = bsrc[x];
@@ -309,7 +310,7 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
     fence_mbar_init();
   }
   const int sb = species_of_atom[E.b];
-  const uint4* bsrc = reinterpret_cast<const uint4*>(BsplitT + BsplitT_off[sb]);
+  const uint4* bsrc = reinterpret_cast<const uint4*>(BsplitT + BsplitT_off[2 * sb + E.far]);
   uint4* bdst = reinterpret_cast<uint4*>(Bp);
   const int nb16 = (int)(3u * L.NJ * L.KK * 2u / 16u);
   for (int x = tid; x < nb16; x += blockDim.x) bdst[x] = bsrc[x];
@@ -519,11 +520,13 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
   m.tc_ready = false;
   size_t smem = 0;
   if (!tc_eligible(h, &smem)) return GW_OK;
-  // C^b in three BF16 planes per species, canonical K-major layout of an NP x KD operand
+  // C^b in three BF16 planes per species and product-basis size (full, then the reduced
+  // size of entries beyond sphere B), canonical K-major layout of an NP x KD operand
   std::vector<uint16_t> planes;
   std::vector<int> off;
-  for (int s = 0; s < h.n_species; ++s) {
-    const int nb = h.n_orb[s], Kb = h.n_prod[s];
+  for (int sv = 0; sv < 2 * h.n_species; ++sv) {
+    const int s = sv / 2;
+    const int nb = h.n_orb[s], Kb = (sv & 1) ? h.n_prod_far[s] : h.n_prod[s];
     const TcLayout L = tc_layout(nb, nb, Kb, Kb);
     off.push_back((int)planes.size());
     const size_t plane = (size_t)L.NP * L.KD;
@@ -556,13 +559,15 @@ gw_status tc_init(MixedPlan& m, const HostPlan& h) {
   m.smem_tc = smem;
   m.tc_ready = true;
 
-  // Sigma: (C^b)^T, rows j = (L1, L3), reduction K2, three BF16 planes per species
+  // Sigma: (C^b)^T, rows j = (L1, L3), reduction K2, three BF16 planes per species and
+  // product-basis size as above
   size_t smem_s = 0;
   if (!tc_eligible_s(h, &smem_s)) return GW_OK;
   std::vector<uint16_t> tplanes;
   std::vector<int> toff;
-  for (int s = 0; s < h.n_species; ++s) {
-    const int nb = h.n_orb[s], Kb = h.n_prod[s];
+  for (int sv = 0; sv < 2 * h.n_species; ++sv) {
+    const int s = sv / 2;
+    const int nb = h.n_orb[s], Kb = (sv & 1) ? h.n_prod_far[s] : h.n_prod[s];
     const TcLayoutS L = tc_layout_s(nb, nb, Kb, Kb);
     toff.push_back((int)tplanes.size());
     const size_t plane = (size_t)L.NJ * L.KK;

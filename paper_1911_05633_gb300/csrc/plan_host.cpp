@@ -291,6 +291,15 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   hp.nu_idx.assign(grid->nu_idx, grid->nu_idx + grid->n_nu);
   hp.cutoff = cutoff;
   hp.spin = opt ? opt->spin : 2;
+  // reduced product basis beyond sphere B (Sec. 2, Fig. 2)
+  hp.r_b = (opt && basis->n_prod_far) ? opt->r_b : 0.0;
+  hp.n_prod_far = hp.n_prod;
+  if (hp.r_b > 0)
+    for (int s = 0; s < hp.n_species; ++s) {
+      const int f = basis->n_prod_far[s];
+      if (f < 1 || f > hp.n_prod[s]) { err = "n_prod_far must be in [1, n_prod]"; return GW_ERR_ARG; }
+      hp.n_prod_far[s] = f;
+    }
   if (hp.spin != 1 && hp.spin != 2) { err = "spin must be 1 or 2"; return GW_ERR_ARG; }
 
   // tau grid: ascending, ends at 0 and beta, mirror symmetric
@@ -325,6 +334,7 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
 
   // pair list: minimum image per class, ties to the lexicographically smallest R
   const double* A = hp.lat;
+  std::vector<double> dist2;  // squared minimum-image distance of each kept entry
   hp.entries.clear();
   hp.pair_start.assign((size_t)hp.n_atoms * hp.n_atoms + 1, 0);
   for (int a = 0; a < hp.n_atoms; ++a) {
@@ -357,6 +367,7 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
             if (cutoff <= 0 || std::sqrt(best) <= cutoff) {
               int64_t row[8] = {a, b, c1, c2, c3, bR[0], bR[1], bR[2]};
               hp.entries.insert(hp.entries.end(), row, row + 8);
+              dist2.push_back(best);
             }
           }
     }
@@ -365,13 +376,27 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   const int E = hp.n_entries();
   if (E == 0) { err = "no pair entry inside the cutoff"; return GW_ERR_ARG; }
 
+  // product functions per entry: the first n_prod_far of each atom beyond sphere B
+  hp.Ka_e.assign(E, 0);
+  hp.Kb_e.assign(E, 0);
+  hp.far_e.assign(E, 0);
+  hp.n_far = 0;
+  for (int e = 0; e < E; ++e) {
+    const int sa = hp.species[hp.entries[8 * e]], sb = hp.species[hp.entries[8 * e + 1]];
+    const bool far = hp.r_b > 0 && dist2[e] > hp.r_b * hp.r_b + 1e-9;
+    hp.Ka_e[e] = far ? hp.n_prod_far[sa] : hp.n_prod[sa];
+    hp.Kb_e[e] = far ? hp.n_prod_far[sb] : hp.n_prod[sb];
+    hp.far_e[e] = far ? 1 : 0;
+    hp.n_far += far ? 1 : 0;
+  }
+
   // block offsets
   hp.off_orb.assign(E + 1, 0);
   hp.off_pb.assign(E + 1, 0);
   for (int e = 0; e < E; ++e) {
     int sa = hp.species[hp.entries[8 * e]], sb = hp.species[hp.entries[8 * e + 1]];
     hp.off_orb[e + 1] = hp.off_orb[e] + (int64_t)hp.n_orb[sa] * hp.n_orb[sb];
-    hp.off_pb[e + 1] = hp.off_pb[e] + (int64_t)hp.n_prod[sa] * hp.n_prod[sb];
+    hp.off_pb[e + 1] = hp.off_pb[e] + (int64_t)hp.Ka_e[e] * hp.Kb_e[e];
   }
 
   // mirror entry (b, a, -R mod N)
@@ -457,8 +482,8 @@ std::vector<DevEntry> make_dev_entries(const HostPlan& hp) {
     int sa = hp.species[d.a], sb = hp.species[d.b];
     d.na = hp.n_orb[sa];
     d.nb = hp.n_orb[sb];
-    d.Ka = hp.n_prod[sa];
-    d.Kb = hp.n_prod[sb];
+    d.Ka = hp.Ka_e[e];
+    d.Kb = hp.Kb_e[e];
     d.oa = hp.orb_off[d.a];
     d.ob = hp.orb_off[d.b];
     d.pa = hp.pb_off[d.a];
@@ -468,6 +493,7 @@ std::vector<DevEntry> make_dev_entries(const HostPlan& hp) {
     d.off_orb = hp.off_orb[e];
     d.off_pb = hp.off_pb[e];
     d.mirror = hp.mirror[e];
+    d.far = hp.far_e[e];
     out[e] = d;
   }
   return out;

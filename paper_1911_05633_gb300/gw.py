@@ -29,7 +29,7 @@ _BLK = {"orb": GW_BLOCK_ORB, "pb": GW_BLOCK_PB}
 _STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
-    "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets",
+    "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
@@ -44,7 +44,7 @@ class GwCell(C.Structure):
 
 class GwBasis(C.Structure):
     _fields_ = [("n_species", C.c_int), ("n_orb", C.POINTER(C.c_int)), ("n_prod", C.POINTER(C.c_int)),
-                ("C", C.POINTER(C.POINTER(C.c_double)))]
+                ("C", C.POINTER(C.POINTER(C.c_double))), ("n_prod_far", C.POINTER(C.c_int))]
 
 
 class GwGrid(C.Structure):
@@ -56,7 +56,7 @@ class GwGrid(C.Structure):
 class GwOptions(C.Structure):
     _fields_ = [("spin", C.c_int), ("strict_kmesh", C.c_int), ("host_only", C.c_int), ("device", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("no_symmetry", C.c_int), ("w_solver", C.c_int),
-                ("fp64_products", C.c_int)]
+                ("fp64_products", C.c_int), ("r_b", C.c_double)]
 
 
 class GwPlanInfo(C.Structure):
@@ -66,7 +66,8 @@ class GwPlanInfo(C.Structure):
                 ("len_orb", C.c_int64), ("len_pb", C.c_int64), ("workspace_bytes", C.c_size_t),
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
                 ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
-                ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int)]
+                ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int),
+                ("n_entries_far", C.c_int)]
 
 
 class GwError(RuntimeError):
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_plan_query.argtypes = [vp, C.POINTER(GwPlanInfo)]
     lib.gw_plan_entries.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.gw_plan_offsets.argtypes = [vp, C.c_int, C.POINTER(C.c_int64)]
+    lib.gw_plan_entry_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.gw_plan_transform_matrix.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.gw_fourier_k_to_R.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_green_k_to_R.argtypes = [vp, vp, vp, vp]
@@ -143,7 +145,8 @@ class Plan:
     def __init__(self, lattice, frac, species, n_orb: Sequence[int], n_prod: Sequence[int], C_list,
                  kmesh, beta: float, tau, omega_idx, nu_idx, cutoff: float, spin: int = 2,
                  strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0,
-                 no_symmetry: bool = False, w_solver: str = "auto", fp64_products: str = "auto"):
+                 no_symmetry: bool = False, w_solver: str = "auto", fp64_products: str = "auto",
+                 n_prod_far: Sequence[int] = None, r_b: float = 0.0):
         lib = load_library()
         self._lib = lib
         self._keep = []
@@ -157,14 +160,16 @@ class Plan:
         tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float64))
         om = np.ascontiguousarray(np.asarray(omega_idx, dtype=np.int32))
         nu = np.ascontiguousarray(np.asarray(nu_idx, dtype=np.int32))
-        self._keep += [lat, frac, species, n_orb, n_prod, Cs, Cptr, tau, om, nu]
+        far = None if n_prod_far is None else np.ascontiguousarray(np.asarray(n_prod_far, dtype=np.int32))
+        self._keep += [lat, frac, species, n_orb, n_prod, Cs, Cptr, tau, om, nu, far]
         cell = GwCell((C.c_double * 9)(*lat), len(frac), _ptr(frac, C.c_double), _ptr(species, C.c_int))
-        basis = GwBasis(len(Cs), _ptr(n_orb, C.c_int), _ptr(n_prod, C.c_int), Cptr)
+        basis = GwBasis(len(Cs), _ptr(n_orb, C.c_int), _ptr(n_prod, C.c_int), Cptr,
+                        _ptr(far, C.c_int) if far is not None else C.POINTER(C.c_int)())
         grid = GwGrid(float(beta), len(tau), _ptr(tau, C.c_double), len(om), _ptr(om, C.c_int),
                       len(nu), _ptr(nu, C.c_int))
         opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes),
                         int(bool(no_symmetry)), {"auto": 0, "gauss_jordan": 1}[w_solver],
-                        {"auto": 0, "fp64": 1}[fp64_products])
+                        {"auto": 0, "fp64": 1}[fp64_products], float(r_b))
         km = (C.c_int * 3)(*[int(x) for x in kmesh])
         h = C.c_void_p()
         _check(lib.gw_plan_create(C.byref(cell), C.byref(basis), km, C.byref(grid), float(cutoff),
@@ -184,10 +189,18 @@ class Plan:
         self.off_pb = np.empty(E + 1, np.int64)
         _check(lib.gw_plan_offsets(h, GW_BLOCK_ORB, _ptr(self.off_orb, C.c_int64)), "gw_plan_offsets")
         _check(lib.gw_plan_offsets(h, GW_BLOCK_PB, _ptr(self.off_pb, C.c_int64)), "gw_plan_offsets")
+        self._dims = {}
+        for kind, code in (("orb", GW_BLOCK_ORB), ("pb", GW_BLOCK_PB)):
+            r, c = np.empty(E, np.int32), np.empty(E, np.int32)
+            _check(lib.gw_plan_entry_dims(h, code, _ptr(r, C.c_int32), _ptr(c, C.c_int32)), "gw_plan_entry_dims")
+            self._dims[kind] = (r, c)
 
     @classmethod
     def from_cell(cls, cell, **kw) -> "Plan":
-        """Plan for a synthetic cell object (geometry, basis and grids are read from it)."""
+        """Plan for a synthetic cell object (geometry, basis and grids are read from it,
+        with its reduced basis beyond sphere B when it has one)."""
+        if getattr(cell, "r_b", 0.0) > 0 and "r_b" not in kw:
+            kw = dict(kw, r_b=cell.r_b, n_prod_far=[s.n_prod_far for s in cell.species])
         return cls(cell.lattice, cell.frac, cell.species_of_atom, [s.n_orb for s in cell.species],
                    [s.n_prod for s in cell.species], [s.C for s in cell.species], cell.kmesh, cell.beta,
                    cell.tau, cell.omega_idx, cell.nu_idx, cell.cutoff, spin=cell.spin, **kw)
@@ -349,11 +362,9 @@ class Plan:
 
     # ---- ragged layout helpers (host side) ------------------------------------------
     def block_shape(self, e: int, kind: str):
-        a, b = int(self.entries[e, 0]), int(self.entries[e, 1])
-        return self._dims[kind][a], self._dims[kind][b]
-
-    def set_dims(self, n_orb_atom, n_prod_atom):
-        self._dims = {"orb": list(n_orb_atom), "pb": list(n_prod_atom)}
+        """(rows, cols) of entry e's block: (n_a, n_b) or (K_a(e), K_b(e))."""
+        r, c = self._dims[kind]
+        return int(r[e]), int(c[e])
 
     def unpack(self, flat: np.ndarray, kind: str, n_slices: int):
         """Entry-layout vector -> list of [n_slices][rows][cols] arrays."""

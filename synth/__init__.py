@@ -52,6 +52,7 @@ class Species:
     n_orb: int
     n_prod: int
     C: np.ndarray  # [n_prod][n_orb][n_orb] float64, symmetric in the last two
+    n_prod_far: Optional[int] = None  # product functions kept by pairs beyond sphere B
 
 
 @dataclasses.dataclass
@@ -71,6 +72,7 @@ class SynthCell:
     gap: Optional[float] = None  # target on-mesh gap (Ha) or None
     hop_cutoff: float = 10.0
     spin: int = 2
+    r_b: float = 0.0             # radius of sphere B (bohr); <= 0: one product basis for every pair
     # filled by build()
     hoppings: Optional[list] = None
     H_k: Optional[np.ndarray] = None
@@ -459,6 +461,16 @@ def make_config(idx: int, atoms: Optional[int] = None, build: bool = True, **ove
     for k, v in over.items():
         setattr(cell, k, v)
     return cell.build() if build else cell
+
+
+def with_far_basis(cell: SynthCell, r_b: float, n_prod_far: Sequence[int]) -> SynthCell:
+    """The same cell with a reduced product basis for pairs beyond a sphere of radius
+    r_b (bohr): n_prod_far[s] functions per atom of species s (inputs only)."""
+    cell.r_b = float(r_b)
+    for sp, f in zip(cell.species, n_prod_far):
+        sp.n_prod_far = int(f)
+    cell.name = f"{cell.name}-rb{r_b:g}-K" + "/".join(str(int(f)) for f in n_prod_far)
+    return cell
 
 
 def chain_cell(n_cells_k: int = 8, t_hop: float = 0.25, beta: float = 20.0, n_tau: int = 24,

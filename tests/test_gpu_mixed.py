@@ -12,16 +12,16 @@ pytestmark = pytest.mark.gpu
 TOL_MIXED = 1e-6
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "mixed_nonsym", "c1"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "mixed_nonsym", "c1", "c1_cut5_far", "mixed_far"])
 def test_polarizability_mixed(name):
     s = system(name)
-    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
     P = host(s.plan.polarizability_tau(dev(pack(s.G_R())), precision="mixed"))
     err = rel(P, pack(ref))
     assert err < TOL_MIXED, err
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "c1"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1", "c1_cut5_far", "mixed_far"])
 def test_self_energy_mixed(name):
     s = system(name)
     WR = _random_W(s)
@@ -37,7 +37,7 @@ def test_self_energy_mixed(name):
 TOL_CHAIN = 1e-3
 
 
-@pytest.mark.parametrize("name", ["c0", "c1_cut5"])
+@pytest.mark.parametrize("name", ["c0", "c1_cut5", "c1_cut5_far"])
 def test_whole_sweep_mixed(name):
     s = system(name)
     p = s.plan

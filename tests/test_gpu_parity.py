@@ -71,6 +71,9 @@ class Sys:
         assert self.plan.info["transform_tensor"] == want
         self.orc = oracle.OracleSystem(cell)
         assert np.array_equal(self.plan.entries, self.orc.entries)
+        # the product-basis block of every entry (reduced beyond sphere B) as the oracle has it
+        assert [self.plan.block_shape(e, "pb") for e in range(len(self.orc.entries))] == self.orc.kdims
+        assert self.plan.info["n_entries_far"] == int(self.orc.far.sum())
         self.G_k = cell.green_k_tau()
         self.v_q, self.v_class = cell.coulomb()
         self.nt = cell.n_tau
@@ -105,12 +108,21 @@ def system(name):
             _CACHE[name] = Sys(synth.make_config(0), fp64_products="fp64")
         elif name == "c1_fp64":
             _CACHE[name] = Sys(synth.make_config(1), fp64_products="fp64")
+        elif name == "c1_cut5_far":  # 24 of 48 product functions beyond the nearest neighbours
+            _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
+                                                    4.0, [24]))
+        elif name == "mixed_far":  # every pair but the onsite ones reduced: K 8 -> 5, 19 -> 11
+            _CACHE[name] = Sys(synth.with_far_basis(synth.mixed_species_cell(), 4.0, [5, 11]))
+        elif name == "c1_far_fp64":
+            _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
+                                                    4.0, [24]), fp64_products="fp64")
         else:
             raise KeyError(name)
     return _CACHE[name]
 
 
 SMALL = ["c0", "mixed", "mixed_nonsym", "c1_cut5"]
+FAR = ["c1_cut5_far", "mixed_far"]  # reduced product basis beyond sphere B (Sec. 2, Fig. 2)
 
 
 @pytest.mark.parametrize("name", SMALL + ["c1"])
@@ -120,15 +132,15 @@ def test_green_k_to_R(name):
     assert rel(GR, pack(s.G_R())) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1", "c0_fp64", "c1_fp64"])
+@pytest.mark.parametrize("name", SMALL + FAR + ["c1", "c0_fp64", "c1_fp64", "c1_far_fp64"])
 def test_polarizability(name):
     s = system(name)
-    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
     P = host(s.plan.polarizability_tau(dev(pack(s.G_R()))))
     assert rel(P, pack(ref)) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1"])
+@pytest.mark.parametrize("name", SMALL + FAR + ["c1"])
 @pytest.mark.parametrize("st,direction,kind", [("B", "tau_to_iw", "pb"), ("B", "iw_to_tau", "pb"),
                                                ("F", "tau_to_iw", "orb"), ("F", "iw_to_tau", "orb")])
 def test_transform(name, st, direction, kind):
@@ -139,24 +151,23 @@ def test_transform(name, st, direction, kind):
         T = s.orc.B_inv if st == "B" else s.orc.F_inv
     n_in = T.shape[1]
     blocks = []
-    for row in s.orc.entries:
+    for e, row in enumerate(s.orc.entries):
         a, b = int(row[0]), int(row[1])
-        r = s.cell.n_prod_of(a) if kind == "pb" else s.cell.n_orb_of(a)
-        c = s.cell.n_prod_of(b) if kind == "pb" else s.cell.n_orb_of(b)
+        r, c = s.orc.kdims[e] if kind == "pb" else (s.cell.n_orb_of(a), s.cell.n_orb_of(b))
         blocks.append(rng.standard_normal((n_in, r, c)) + 1j * rng.standard_normal((n_in, r, c)))
     ref = oracle.transform(T, blocks)
     out = host(s.plan.transform_tau_iw(st, direction, kind, dev(pack(blocks))))
     assert rel(out, pack(ref)) < TOL
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5", "c1", "c0_fp64", "c1_fp64"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5", "c1", "c0_fp64", "c1_fp64"] + FAR)
 def test_transform_structured_inputs(name):
     """gw_transform_tau_iw_ex: P(R, tau) with P(beta - tau) = P(tau)* (symmetric C) through
     the mirror-paired bosonic transform, and a real W~(R, i nu) through the real-input
     inverse, against the oracle's general transform."""
     s = system(name)
     assert s.plan.info["c_symmetric"] == 1
-    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
     ref = oracle.transform(s.orc.B_fwd, PR)
     out = host(s.plan.transform_tau_iw("B", "tau_to_iw", "pb", dev(pack(PR)), structure="mirror"))
     assert rel(out, pack(ref)) < TOL
@@ -172,10 +183,10 @@ def test_transform_structured_inputs(name):
         s.plan.transform_tau_iw("F", "tau_to_iw", "orb", dev(pack(s.G_R())), structure="mirror")
 
 
-@pytest.mark.parametrize("name", SMALL + ["c0_nosym", "c1_cut5_gj"])
+@pytest.mark.parametrize("name", SMALL + FAR + ["c0_nosym", "c1_cut5_gj"])
 def test_screened_W(name):
     s = system(name)
-    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin)
+    PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
     Piw = oracle.transform(s.orc.B_fwd, PR)
     ref, _ = oracle.screened_W(Piw, s.orc.entries, s.v_q, s.orc.kmesh, s.cell.pb_offsets)
     W = host(s.plan.screened_W_iw(dev(pack(Piw)), dev(s.v_q)))
@@ -206,14 +217,13 @@ def test_screened_W_sampled_full_size():
 def _random_W(s, seed=23):
     rng = np.random.default_rng(seed)
     out = []
-    for row in s.orc.entries:
-        a, b = int(row[0]), int(row[1])
-        Ka, Kb = s.cell.n_prod_of(a), s.cell.n_prod_of(b)
+    for e, row in enumerate(s.orc.entries):
+        Ka, Kb = s.orc.kdims[e]
         out.append(rng.standard_normal((s.nt, Ka, Kb)) + 1j * rng.standard_normal((s.nt, Ka, Kb)))
     return out
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1", "c0_fp64", "c1_fp64"])
+@pytest.mark.parametrize("name", SMALL + FAR + ["c1", "c0_fp64", "c1_fp64", "c1_far_fp64"])
 def test_self_energy_and_exchange(name):
     s = system(name)
     WR = _random_W(s)
@@ -225,7 +235,7 @@ def test_self_energy_and_exchange(name):
     assert rel(host(Sigx), pack(refx)) < TOL
 
 
-@pytest.mark.parametrize("name", SMALL + ["c1"])
+@pytest.mark.parametrize("name", SMALL + FAR + ["c1"])
 def test_fourier_R_to_k(name):
     s = system(name)
     rng = np.random.default_rng(5)
@@ -245,7 +255,7 @@ def test_fourier_R_to_k(name):
     assert rel(vq, refv.reshape(-1)) < TOL
 
 
-@pytest.mark.parametrize("name", ["c0", "c0_nosym", "mixed", "mixed_nonsym", "c1_cut5", "c1_cut5_gj"])
+@pytest.mark.parametrize("name", ["c0", "c0_nosym", "mixed", "mixed_nonsym", "c1_cut5", "c1_cut5_gj"] + FAR)
 def test_whole_sweep(name):
     """All rows chained on the device from G(k, tau) and v(q); every stage vs the oracle."""
     s = system(name)

@@ -158,3 +158,49 @@ def test_sigma_stage_choice(gwlib):
     c1._draw_basis(np.random.default_rng(0))
     assert gw.Plan.from_cell(c1, host_only=True).info["sigma_tensor"] == 1
     assert gw.Plan.from_cell(c1, host_only=True, fp64_products="fp64").info["sigma_tensor"] == 0
+
+
+@pytest.mark.parametrize("which", ["c1_cut5", "mixed", "c2_16"])
+def test_far_basis_tables_match_oracle(gwlib, which):
+    """Reduced product basis beyond sphere B (Sec. 2, Fig. 2): the plan's per-entry
+    product-basis blocks, tier count and offsets against the oracle's own tier rule."""
+    from paper_1911_05633_gb300 import gw
+    if which == "c1_cut5":
+        cell = synth.make_config(1, build=False, cutoff=5.0, kmesh=(2, 2, 2))
+        r_b, far = 4.0, [24]
+    elif which == "mixed":
+        cell = synth.mixed_species_cell()
+        r_b, far = 4.4, [5, 11]   # A-B at 4.33 bohr stay full, A-A and B-B at 5 bohr reduced
+    else:
+        cell = synth.make_config(2, atoms=16, build=False)
+        r_b, far = 7.5, [16]
+    if cell.species[0].C is None:
+        cell._draw_basis(np.random.default_rng(0))
+    synth.with_far_basis(cell, r_b, far)
+    p = gw.Plan.from_cell(cell, host_only=True)
+    ent = oracle.pair_list(cell.lattice, cell.frac, cell.kmesh, cell.cutoff)
+    assert np.array_equal(p.entries, ent)
+    is_far = oracle.entry_far(cell.lattice, cell.frac, ent, r_b)
+    assert 0 < is_far.sum() < len(ent)
+    full = [cell.n_prod_of(a) for a in range(cell.n_atoms)]
+    red = [cell.species[s].n_prod_far for s in cell.species_of_atom]
+    dims = oracle.entry_pb_dims(ent, is_far, full, red)
+    assert p.info["n_entries_far"] == int(is_far.sum())
+    assert [p.block_shape(e, "pb") for e in range(len(ent))] == dims
+    assert np.array_equal(p.off_pb, np.concatenate([[0], np.cumsum([ka * kb for ka, kb in dims])]))
+    assert p.info["len_pb"] == sum(ka * kb for ka, kb in dims)
+    # the orbital blocks are not reduced
+    no = [cell.n_orb_of(int(a)) * cell.n_orb_of(int(b)) for a, b in ent[:, :2]]
+    assert np.array_equal(p.off_orb, np.concatenate([[0], np.cumsum(no)]))
+    # r_b beyond every kept distance: one basis for every entry
+    q = gw.Plan.from_cell(cell, host_only=True, r_b=1e3, n_prod_far=far)
+    assert q.info["n_entries_far"] == 0
+    assert q.info["len_pb"] == sum(full[int(a)] * full[int(b)] for a, b in ent[:, :2])
+
+
+def test_far_basis_rejects_bad_sizes(gwlib):
+    from paper_1911_05633_gb300 import gw
+    cell = synth.make_config(0)
+    for bad in ([0], [9]):  # n_prod = 8
+        with pytest.raises(gw.GwError):
+            gw.Plan.from_cell(cell, host_only=True, r_b=4.0, n_prod_far=bad)

@@ -449,3 +449,97 @@ def test_w_solve_amplifies_errors_of_p():
     a, b = w_tau(PRn), w_tau(PR)
     amp = np.linalg.norm(a - b) / np.linalg.norm(b) / 1e-7
     assert 10.0 < amp < 1e4, amp
+
+
+# ----------------------------------------------------------------------------
+# Reduced product basis beyond sphere B (Sec. 2, Fig. 2; worked values in Sec. 3)
+# ----------------------------------------------------------------------------
+
+def _far_cells(r_b=4.0, n_far=3):
+    """cell0 twice from the same seed: with the reduced basis beyond r_b, and without."""
+    full = synth.make_config(0)
+    tier = synth.with_far_basis(synth.make_config(0), r_b, [n_far])
+    assert np.array_equal(full.species[0].C, tier.species[0].C)
+    return full, tier
+
+
+def test_far_basis_storage_ratio_printed_in_sec3():
+    row = [l.split() for l in open(os.path.join(GOLDEN, "far_basis_ratios.txt")) if l.strip() and not l.startswith("#")]
+    r_b, r_c, shell, l_b, l_c, storage = (float(x) for x in row[0])
+    assert abs((r_c ** 3 - r_b ** 3) / r_b ** 3 - shell) < 0.5
+    # product functions per atom ~ (L + 1)^2: a near and a far entry of one atom pair
+    ent = np.array([[0, 0, 0, 0, 0, 0, 0, 0], [0, 0, 1, 0, 0, 1, 0, 0]], np.int64)
+    dims = oracle.entry_pb_dims(ent, np.array([False, True]), [int((l_b + 1) ** 2)], [int((l_c + 1) ** 2)])
+    ratio = (dims[0][0] * dims[0][1]) / (dims[1][0] * dims[1][1])
+    assert math.isclose(ratio, ((l_b + 1) / (l_c + 1)) ** 4, rel_tol=1e-15)
+    assert abs(ratio - storage) < 0.5
+
+
+def test_far_basis_tiers_by_distance():
+    full, tier = _far_cells()
+    orc = oracle.OracleSystem(tier)
+    ent = orc.entries
+    # sc a = 5 with atoms at 0 and the cube centre: onsite 0, A-B 4.33, A-A' 5 bohr
+    for e, row in enumerate(ent):
+        onsite = row[0] == row[1] and not row[5:8].any()
+        assert orc.far[e] == (not onsite)
+        assert orc.kdims[e] == ((8, 8) if onsite else (3, 3))
+    assert not oracle.OracleSystem(full).far.any()
+
+
+def test_far_basis_equals_masked_full_basis():
+    """The reduced basis against a second route: the full-basis oracle with every
+    dropped row and column of P, W~ and v set to zero (Sec. 2: the two-point functions
+    of distant pairs live in the smaller basis)."""
+    full, tier = _far_cells()
+    of, ot = oracle.OracleSystem(full), oracle.OracleSystem(tier)
+    Gk = full.green_k_tau()
+    vq, vcls = full.coulomb()
+    ent, po = of.entries, full.pb_offsets
+    GR = oracle.fourier_k_to_R(Gk, ent, of.kmesh, full.orb_offsets, full.orb_offsets)
+
+    def mask(blocks):
+        out = []
+        for e, b in enumerate(blocks):
+            m = np.zeros_like(b)
+            ka, kb = ot.kdims[e]
+            m[..., :ka, :kb] = b[..., :ka, :kb]
+            out.append(m)
+        return out
+
+    Pf = oracle.polarizability_R(GR, ent, of.C_atom, full.spin)
+    Pt = oracle.polarizability_R(GR, ent, ot.C_atom, tier.spin, ot.kdims)
+    for e in range(len(ent)):
+        ka, kb = ot.kdims[e]
+        assert Pt[e].shape[1:] == (ka, kb)
+        assert np.abs(Pt[e] - Pf[e][:, :ka, :kb]).max() <= 1e-14 * np.abs(Pf[e]).max()
+    Wt_iw, Wq_t = oracle.screened_W(oracle.transform(ot.B_fwd, Pt), ent, vq, ot.kmesh, po)
+    Wm_iw, Wq_m = oracle.screened_W(oracle.transform(of.B_fwd, mask(Pf)), ent, vq, of.kmesh, po)
+    assert np.abs(Wq_t - Wq_m).max() <= 1e-12 * np.abs(Wq_m).max()
+    for e in range(len(ent)):
+        ka, kb = ot.kdims[e]
+        assert np.abs(Wt_iw[e] - Wm_iw[e][:, :ka, :kb]).max() <= 1e-12 * np.abs(Wm_iw[e]).max()
+    WtR = oracle.transform(ot.B_inv, Wt_iw)
+    WmR = mask(oracle.transform(of.B_inv, Wm_iw))
+    St = oracle.self_energy_R(GR, WtR, ent, ot.C_atom)
+    Sm = oracle.self_energy_R(GR, WmR, ent, of.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(St, Sm)) <= 1e-12 * max(np.abs(b).max() for b in Sm)
+    Xt = oracle.exchange_R(GR, ot.v_R(vcls), ent, ot.C_atom)
+    Xm = oracle.exchange_R(GR, mask(of.v_R(vcls)), ent, of.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(Xt, Xm)) <= 1e-12 * max(np.abs(b).max() for b in Xm)
+    # and the reduction changes the answer (the test would be empty otherwise)
+    Sf = oracle.self_energy_R(GR, oracle.transform(of.B_inv, oracle.screened_W(
+        oracle.transform(of.B_fwd, Pf), ent, vq, of.kmesh, po)[0]), ent, of.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(St, Sf)) > 1e-6 * max(np.abs(b).max() for b in Sf)
+
+
+def test_far_basis_beyond_every_distance_is_the_full_basis():
+    full = synth.make_config(0)
+    tier = synth.with_far_basis(synth.make_config(0), 1e3, [3])
+    Gk = full.green_k_tau()
+    vq, vcls = full.coulomb()
+    rf = oracle.OracleSystem(full).sweep(Gk, vq, vcls)
+    rt = oracle.OracleSystem(tier).sweep(Gk, vq, vcls)
+    for key in ("P_R", "Wt_R", "Sig_R", "Sigx_R"):
+        for a, b in zip(rf[key], rt[key]):
+            assert a.shape == b.shape and np.array_equal(a, b)
