@@ -64,6 +64,9 @@ def parse():
                     help="radius of sphere B (bohr): pairs beyond it keep --n-prod-far product functions (Sec. 2)")
     ap.add_argument("--n-prod-far", type=int, nargs="+", default=None,
                     help="product functions per species kept by pairs beyond sphere B")
+    ap.add_argument("--scaling", type=int, nargs="*", default=None,
+                    help="time the P+Sigma rows (no W solve) of the 64-function diamond series at these atom "
+                         "counts (default 8 16 32 48 72), FP64 and mixed; one JSON line")
     return ap.parse_args()
 
 
@@ -632,8 +635,92 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_scaling(args, local):
+    """P + Sigma rows (a1-a4 and a6-a8; the W solve is timed apart by the metric) of the
+    diamond supercell series with 9 orbitals and 64 product functions per atom, a 2x2x2
+    mesh, 64 tau nodes and a 12-bohr cutoff (8, 16, 32, 48, 72 atoms), in FP64 and in
+    mixed precision.  W~(R, i nu) and v(R) are seeded random inputs of the plan's shapes:
+    the W solve of N_PB = 64 x atoms is not part of this step.  Per size: ms per sweep
+    over the rows, per pair entry, and the contraction TFLOP/s."""
+    import torch
+    import synth
+    from paper_1911_05633_gb300 import gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = args.scaling or [8, 16, 32, 48, 72]
+    stream = torch.cuda.Stream(device=local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rows = []
+    for nat in sizes:
+        cell = synth.make_config(2, atoms=nat)
+        plan = gw.Plan.from_cell(cell, device=local)
+        inf = plan.info
+        nt, nn, nw, No, nk = inf["n_tau"], inf["n_nu"], inf["n_omega"], inf["n_orb_total"], inf["n_k"]
+        z = lambda n: torch.empty(n, dtype=torch.complex128, device=dev)
+        G_k = torch.from_numpy(cell.green_k_tau().reshape(-1)).to(dev)
+        gen = torch.Generator(device=dev).manual_seed(nat)
+        W_iw = torch.randn(plan.len("pb", nn), dtype=torch.float64, device=dev, generator=gen).to(torch.complex128)
+        v_R = torch.randn(plan.len("pb", 1), dtype=torch.float64, device=dev, generator=gen).to(torch.complex128)
+        G_R, P_R, P_iw, W_R = z(plan.len("orb", nt)), z(plan.len("pb", nt)), z(plan.len("pb", nn)), z(plan.len("pb", nt))
+        S_R, Sx_R, S_iw = z(plan.len("orb", nt)), z(plan.len("orb", 1)), z(plan.len("orb", nw))
+        S_k = z(nk * nw * No * No)
+        kd = pb_dims(plan)
+        ent = plan.entries
+        flops = contraction_flops(cell, ent, kd)
+        row = {"atoms": nat, "entries": len(ent), "n_pb": inf["n_pb_total"]}
+        for prec in ("fp64", "mixed"):
+            def sweep():
+                sp = stream.cuda_stream
+                plan.green_k_to_R(G_k, G_R, stream=sp)
+                plan.polarizability_tau(G_R, P_R, precision=prec, stream=sp)
+                plan.transform_tau_iw("B", "tau_to_iw", "pb", P_R, P_iw, stream=sp,
+                                      structure="mirror" if inf["c_symmetric"] else "general")
+                plan.transform_tau_iw("B", "iw_to_tau", "pb", W_iw, W_R, stream=sp, structure="real")
+                plan.self_energy_tau(G_R, W_R, v_R=v_R, Sig_R=S_R, Sigx_R=Sx_R, precision=prec, stream=sp)
+                plan.transform_tau_iw("F", "tau_to_iw", "orb", S_R, S_iw, stream=sp)
+                plan.fourier_R_to_k("orb", nw, S_iw, S_k, stream=sp)
+            with torch.cuda.stream(stream):
+                for _ in range(max(3, args.warmup)):
+                    sweep()
+            plan.sync(stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush_l2(flush)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sweep()
+                    e1.record(stream)
+                plan.sync(stream=stream.cuda_stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.mean(ts))
+            row[prec] = {"ms_per_sweep": round(ms, 3), "us_per_entry": round(1000.0 * ms / len(ent), 3),
+                         "contraction_tflops": round(2 * flops / (ms * 1e-3) / 1e12, 3)}
+        rows.append(row)
+        del G_k, W_iw, v_R, G_R, P_R, P_iw, W_R, S_R, Sx_R, S_iw, S_k
+        plan.close()
+        torch.cuda.empty_cache()
+    base = rows[0]
+    for r in rows:  # time per entry relative to the smallest cell: 1.0 is linear scaling
+        for prec in ("fp64", "mixed"):
+            r[prec]["per_entry_vs_smallest"] = round(r[prec]["us_per_entry"] / base[prec]["us_per_entry"], 3)
+    return {"metric": "P+Sigma sweep time vs atom count (W solve excluded)", "unit": "ms per sweep",
+            "steps": args.steps, "warmup": max(3, args.warmup), "data": "synthetic",
+            "config": {"workload": "diamond supercells, 9 orbitals and 64 product functions per atom, 2x2x2 k, "
+                                   "64 tau, cutoff 12 bohr; W~(R, i nu) and v(R) seeded random",
+                       "l2": "256 MB buffer written before each timed sweep"},
+            "series": rows}
+
+
 def main():
     args = parse()
+    if args.scaling is not None:
+        rank, world, local = dist_init(args)
+        if rank == 0:
+            print(json.dumps(run_scaling(args, local)), flush=True)
+        return
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
