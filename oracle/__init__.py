@@ -26,6 +26,9 @@ Every function follows one statement of the paper, cited in its docstring:
 * Appendix A, the sparse Matsubara grid: tau <-> i omega transforms, read as
   exact Fourier integrals of the polynomial that interpolates the tau nodes
   -> ``fourier_matrix``, ``inverse_matrix``
+* Eq. G_1 (Dyson equation) with the Hartree G0, the particle number from
+  G(beta-) and the chemical potential by bisection -> ``dyson_green_iw``,
+  ``green_iw_to_tau``, ``particle_number``, ``chemical_potential``
 
 Readings where the paper is silent or garbled (each listed in the design notes):
 P(x, x'; tau) = -s G(x, x'; tau) G(x', x; beta - tau) and G(x', x) = G(x, x')^*;
@@ -60,6 +63,10 @@ __all__ = [
     "self_energy_R",
     "exchange_R",
     "self_energy_k_kspace",
+    "dyson_green_iw",
+    "green_iw_to_tau",
+    "particle_number",
+    "chemical_potential",
     "OracleSystem",
 ]
 
@@ -427,6 +434,69 @@ def self_energy_k_kspace(G_k: np.ndarray, Wt_q_tau: np.ndarray, C_atom, orb_off,
                     out[ik, :, orb_off[a]:orb_off[a + 1], orb_off[b]:orb_off[b + 1]] -= _s_block(
                         C_atom[a], G, W, C_atom[b])
     return out / nk
+
+
+# ----------------------------------------------------------------------------
+# Eq. G_1 (Dyson equation), the particle number and the chemical potential
+# ----------------------------------------------------------------------------
+
+def dyson_green_iw(H_k: np.ndarray, Sigx_k: np.ndarray, Sig_k_iw, mu: float, beta: float, omega_idx) -> np.ndarray:
+    """G(k, i w_n) from Eq. G_1, G = G0 + G0 Sigma G, with G0 = (i w_n + mu - H)^{-1} the
+    Green function of the fixed (Hartree) Hamiltonian H and Sigma = Sigma_x + Sigma_c:
+    one inverse G = [(i w_n + mu) I - H(k) - Sigma_x(k) - Sigma_c(k, i w_n)]^{-1} per
+    (k, n), w_n = (2n + 1) pi / beta.  H_k, Sigx_k: [N_k][N][N]; Sig_k_iw: [N_k][n_w][N][N]
+    or None (Sigma_c = 0).  Returns [N_k][n_w][N][N]."""
+    nk, N = H_k.shape[0], H_k.shape[1]
+    w = (2 * np.asarray(omega_idx, dtype=np.float64) + 1) * np.pi / beta
+    I = np.eye(N)
+    out = np.empty((nk, len(w), N, N), np.complex128)
+    for k in range(nk):
+        for n, wn in enumerate(w):
+            S = Sigx_k[k] + (Sig_k_iw[k, n] if Sig_k_iw is not None else 0.0)
+            out[k, n] = np.linalg.inv((1j * wn + mu) * I - H_k[k] - S)
+    return out
+
+
+def green_iw_to_tau(G_iw: np.ndarray, H_k: np.ndarray, Sigx_k: np.ndarray, mu: float, beta: float, tau,
+                    omega_idx, F_inv: np.ndarray) -> np.ndarray:
+    """G(k, tau_i) from G(k, i w_n) by the inverse transform of Appendix A.  The two leading
+    terms of G at large frequency, 1/(i w) and M1/(i w)^2 with M1 = H + Sigma_x - mu, are
+    taken out before the transform and added back as their tau functions over [0, beta]:
+    -1/2 and M1 (2 tau - beta)/4 (each the function whose fermionic Matsubara integral is
+    that term).  Returns [N_k][N_tau][N][N]."""
+    w = (2 * np.asarray(omega_idx, dtype=np.float64) + 1) * np.pi / beta
+    N = G_iw.shape[-1]
+    I = np.eye(N)
+    M1 = H_k + Sigx_k - mu * I
+    iw = 1j * w
+    rem = G_iw - I[None, None] / iw[None, :, None, None] - M1[:, None] / (iw * iw)[None, :, None, None]
+    out = np.einsum("tn,knij->ktij", F_inv, rem)
+    t = np.asarray(tau, dtype=np.float64)
+    return out - 0.5 * I[None, None] + M1[:, None] * ((2.0 * t - beta) / 4.0)[None, :, None, None]
+
+
+def particle_number(G_k_tau: np.ndarray, spin: int = 2) -> float:
+    """Electrons per cell, N = s (1/N_k) sum_k Tr[-G(k, beta-)] (the last tau node):
+    -G(beta-) is the one-particle density matrix."""
+    return float(spin * np.real(np.trace(-G_k_tau[:, -1], axis1=1, axis2=2)).sum() / G_k_tau.shape[0])
+
+
+def chemical_potential(H_k, Sigx_k, Sig_k_iw, n_electrons: float, beta: float, tau, omega_idx, F_inv,
+                       spin: int = 2, lo: float = -5.0, hi: float = 5.0, tol: float = 1e-12):
+    """mu with N(mu) = n_electrons, by bisection on [lo, hi] (N grows with mu); N(mu)
+    from G(k, beta-) of Eq. G_1 through the inverse transform above.  Returns (mu, N(mu))."""
+    def count(m):
+        G = green_iw_to_tau(dyson_green_iw(H_k, Sigx_k, Sig_k_iw, m, beta, omega_idx), H_k, Sigx_k, m, beta,
+                            tau, omega_idx, F_inv)
+        return particle_number(G, spin)
+    while hi - lo > tol:
+        mid = 0.5 * (lo + hi)
+        if count(mid) < n_electrons:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return mu, count(mu)
 
 
 # ----------------------------------------------------------------------------

@@ -543,3 +543,83 @@ def test_far_basis_beyond_every_distance_is_the_full_basis():
     for key in ("P_R", "Wt_R", "Sig_R", "Sigx_R"):
         for a, b in zip(rf[key], rt[key]):
             assert a.shape == b.shape and np.array_equal(a, b)
+
+
+# ----------------------------------------------------------------------------
+# Eq. G_1: Dyson equation, particle number, chemical potential
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cell_dense():
+    """Configuration 0 at beta = 10 with 48 nodes: the transforms are accurate to ~1e-13."""
+    c = synth.make_config(0, beta=10.0, n_tau=48)
+    return c, oracle.OracleSystem(c)
+
+
+def _static_hermitian(rng, nk, n, scale=0.05):
+    x = rng.standard_normal((nk, n, n)) + 1j * rng.standard_normal((nk, n, n))
+    return scale * (x + np.conj(np.transpose(x, (0, 2, 1))))
+
+
+def test_dyson_without_self_energy_is_g0(cell_dense):
+    c, orc = cell_dense
+    Z = np.zeros_like(c.H_k)
+    G = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, Z, None, c.mu, c.beta, c.omega_idx), c.H_k, Z, c.mu,
+                               c.beta, c.tau, c.omega_idx, orc.F_inv)
+    G0 = oracle.green0_k_tau(c.H_k, c.mu, c.beta, c.tau)
+    assert np.abs(G - G0).max() < 1e-11
+
+
+def test_dyson_static_exchange_is_hartree_fock(cell_dense):
+    """A static Hermitian Sigma_x and Sigma_c = 0: G is the closed-form G0 of H + Sigma_x."""
+    c, orc = cell_dense
+    Sx = _static_hermitian(np.random.default_rng(4), c.n_k, c.n_orb_total)
+    G = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, Sx, None, c.mu, c.beta, c.omega_idx), c.H_k, Sx, c.mu,
+                               c.beta, c.tau, c.omega_idx, orc.F_inv)
+    GHF = oracle.green0_k_tau(c.H_k + Sx, c.mu, c.beta, c.tau)
+    assert np.abs(G - GHF).max() < 1e-11
+
+
+def test_dyson_inverse_equals_eq_G1_as_printed(cell0):
+    """G = G0 + G0 Sigma G solved as the linear system (I - G0 Sigma) G = G0 per (k, n)."""
+    c = cell0
+    rng = np.random.default_rng(8)
+    nk, nw, N = c.n_k, c.omega_idx.size, c.n_orb_total
+    Sx = _static_hermitian(rng, nk, N)
+    Sc = 0.05 * (rng.standard_normal((nk, nw, N, N)) + 1j * rng.standard_normal((nk, nw, N, N)))
+    G = oracle.dyson_green_iw(c.H_k, Sx, Sc, c.mu, c.beta, c.omega_idx)
+    w = (2 * c.omega_idx + 1) * np.pi / c.beta
+    I = np.eye(N)
+    for k in range(nk):
+        for n in range(nw):
+            G0 = np.linalg.inv((1j * w[n] + c.mu) * I - c.H_k[k])
+            ref = np.linalg.solve(I - G0 @ (Sx[k] + Sc[k, n]), G0)
+            assert np.abs(G[k, n] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_green_tail_terms_are_exact_matsubara_integrals(cell_dense):
+    """-1/2 and (2 tau - beta)/4 are polynomials, so the forward transform of Appendix A
+    maps them exactly to 1/(i w) and 1/(i w)^2: the tail added back is the tail taken out."""
+    c, orc = cell_dense
+    w = (2 * c.omega_idx + 1) * np.pi / c.beta
+    f0 = np.full(c.n_tau, -0.5, np.complex128)
+    f1 = ((2 * c.tau - c.beta) / 4).astype(np.complex128)
+    assert np.abs(orc.F_fwd @ f0 - 1 / (1j * w)).max() < 1e-13
+    assert np.abs(orc.F_fwd @ f1 - 1 / (1j * w) ** 2).max() < 1e-13 * c.beta
+
+
+def test_chemical_potential_reproduces_fermi_filling(cell_dense):
+    """Sigma = 0: the bisection on N(mu) from G(beta-) finds the mu of the Fermi sum over
+    the band energies at half filling (the generator's own bisection on eigenvalues)."""
+    c, orc = cell_dense
+    Z = np.zeros_like(c.H_k)
+    e = np.linalg.eigvalsh(c.H_k)
+    mu, n = oracle.chemical_potential(c.H_k, Z, None, float(c.n_orb_total), c.beta, c.tau, c.omega_idx, orc.F_inv,
+                                      c.spin, lo=float(e.min()) - 1, hi=float(e.max()) + 1, tol=1e-13)
+    assert abs(n - c.n_orb_total) < 1e-9
+    assert abs(mu - c.mu) < 1e-9
+    # and N(mu) itself against the Fermi sum at a shifted mu
+    G = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, Z, None, c.mu + 0.1, c.beta, c.omega_idx), c.H_k, Z,
+                               c.mu + 0.1, c.beta, c.tau, c.omega_idx, orc.F_inv)
+    ref = c.spin * synth.fermi(e - c.mu - 0.1, c.beta).sum() / c.n_k
+    assert abs(oracle.particle_number(G, c.spin) - ref) < 1e-10
