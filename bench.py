@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dyson", action="store_true", help="skip the Eq. G_1 step timed after the sweep")
     ap.add_argument("--small", action="store_true", help="the small profiling case instead of the bench workload")
     ap.add_argument("--w-solver", default="auto", choices=["auto", "gauss_jordan"],
                     help="inverse of the W solve: tensor-core refinement where supported, or FP64 Gauss-Jordan")
@@ -466,6 +467,7 @@ def run_ours(args, rank, world, local):
                "w_solve_ms": round(float(stage_mean[Sweep.STAGES.index("W_solve")]), 4),
                "stages": "every row except the W solve, which is timed on its own"}
 
+    dyson = None if args.no_dyson else run_dyson(sw, cell, stream, args)
     mixed_err = mixed_vs_fp64(sw, stream) if args.precision == "mixed" else None
     e2e = None
     if not args.no_e2e:
@@ -500,7 +502,46 @@ def run_ours(args, rank, world, local):
     }
     if mixed_err is not None:
         out["mixed_vs_fp64"] = mixed_err
+    if dyson is not None:
+        out["dyson"] = dyson
     return out, cell
+
+
+def run_dyson(sw, cell, stream, args):
+    """Eq. G_1 after the sweep (the next step of an iteration, not part of `value`): the
+    device Dyson solve G(k, tau) from the sweep's Sigma(k, i w) and Sigma_x(k), timed with
+    CUDA events over `steps` calls, and the chemical potential at half filling by bisection
+    (wall clock; one Dyson solve per step)."""
+    torch = sw.torch
+    p = sw.plan
+    H = torch.from_numpy(cell.H_k.reshape(-1)).to(sw.dev)
+    G = torch.empty(p.info["n_k"] * p.info["n_tau"] * p.dense_n("orb") ** 2, dtype=torch.complex128, device=sw.dev)
+    ss = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        p.dyson_green_tau(H, cell.mu, Sigx_k=sw.Sx_k, Sig_k_iw=sw.S_k, G_k_tau=G, stream=ss)  # allocates its scratch
+    p.sync(stream=ss)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            p.dyson_green_tau(H, cell.mu, Sigx_k=sw.Sx_k, Sig_k_iw=sw.S_k, G_k_tau=G, stream=ss)
+            b.record(stream)
+    p.sync(stream=ss)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    sx = sw.Sx_k.cpu().numpy().reshape(cell.H_k.shape)
+    e = np.linalg.eigvalsh(cell.H_k + 0.5 * (sx + np.conj(np.transpose(sx, (0, 2, 1)))))  # the static levels
+    lo, hi, tol = float(e.min()) - 2.0, float(e.max()) + 2.0, 1e-10
+    t0 = time.perf_counter()
+    mu, n = p.chemical_potential(H, float(cell.n_orb_total), lo, hi, tol=tol, Sigx_k=sw.Sx_k, Sig_k_iw=sw.S_k,
+                                 stream=ss)
+    t_mu = time.perf_counter() - t0
+    N, nk, nw = p.dense_n("orb"), p.info["n_k"], p.info["n_omega"]
+    return {"green_tau_ms": round(ms, 3), "inverses": nk * nw, "n_orb": N,
+            "inverse_tflops": round(8.0 * N ** 3 * nk * nw / (ms * 1e-3) / 1e12, 3),
+            "mu_search_s": round(t_mu, 3), "mu_steps": int(np.ceil(np.log2((hi - lo) / tol))) + 1,
+            "mu": mu, "n_electrons": n, "note": "Eq. G_1 with the sweep's Sigma; not part of value"}
 
 
 def mixed_vs_fp64(sw, stream):

@@ -279,6 +279,34 @@ const char* gw_status_string(gw_status s);
 /* Text of the last error on this thread (empty if none). */
 const char* gw_last_error(void);
 
+/* ---- Eq. G_1: the Dyson equation and the chemical potential ------------------- */
+
+/* G(k, tau) from Eq. G_1, G = G0 + G0 Sigma G with G0 = (i w + mu - H)^{-1} the Green
+ * function of the fixed (Hartree) Hamiltonian: per momentum k and sampled fermionic
+ * frequency w_n (the plan's omega indices), the FP64 inverse
+ *   G(k, i w_n) = [(i w_n + mu) I - H(k) - Sigma_x(k) - Sigma_c(k, i w_n)]^{-1},
+ * then G(k, tau_i) = sum_n T[i][n] (G - 1/(i w_n) - M1/(i w_n)^2) - I/2 + M1 (2 tau_i - beta)/4
+ * with T the inverse fermionic transform of Appendix A (gw_plan_transform_matrix) and
+ * M1 = H + Sigma_x - mu: the two leading terms of G at large frequency are taken out
+ * before the transform and added back as their exact tau functions.
+ * H_k, Sigx_k: device [N_k][N][N] (N = total orbitals; Sigx_k NULL reads as zero);
+ * Sig_k_iw: device [N_k][n_omega][N][N] (the layout gw_fourier_R_to_k writes) or NULL;
+ * G_k_tau: device [N_k][n_tau][N][N], the layout gw_green_k_to_R reads.  The plan
+ * allocates N_k n_omega N^2 complex values of scratch on the first call.  A zero pivot
+ * is reported by gw_sync (GW_ERR_SINGULAR). */
+gw_status gw_dyson_green_tau(gw_plan_t plan, const void* H_k, const void* Sigx_k, const void* Sig_k_iw, double mu,
+                             void* G_k_tau, void* stream);
+
+/* The chemical potential mu in [mu_lo, mu_hi] at which the electrons per cell,
+ * N(mu) = s (1/N_k) sum_k Re Tr[-G(k, beta-)] with G from gw_dyson_green_tau at tau = beta-,
+ * equal n_electrons: bisection until the bracket is narrower than tol (at most 200
+ * steps; N grows with mu).  Each step is one Dyson solve on the device; the call is
+ * synchronous on `stream`.  Writes mu and, if n_out is not NULL, N(mu).  Returns
+ * GW_ERR_ARG for mu_lo >= mu_hi or tol <= 0, GW_ERR_SINGULAR for a zero pivot. */
+gw_status gw_chemical_potential(gw_plan_t plan, const void* H_k, const void* Sigx_k, const void* Sig_k_iw,
+                                double n_electrons, double mu_lo, double mu_hi, double tol, double* mu_out,
+                                double* n_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

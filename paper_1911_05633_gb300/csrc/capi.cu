@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -17,6 +18,7 @@
 #include "wtc.h"
 #include "oz.h"
 #include "ktimer.h"
+#include "dyson.h"
 
 struct gw_plan_s {
   gw::HostPlan h;
@@ -68,6 +70,7 @@ struct gw_plan_s {
   gw::OzTransform ozt;  // FP64-accurate structured transforms on the tensor cores
   gw::OzPol ozp;        // FP64-accurate stage 3 of P on the tensor cores
   gw::KernelTimer timer;  // optional per-kernel event timing (gw_timing_*)
+  gw::DysonPlan dyson;    // Eq. G_1 scratch, allocated by the first Dyson call
 };
 
 namespace gw {
@@ -132,6 +135,7 @@ void free_device(gw_plan_s* p) {
   gw::oz_sigma_free(p->oz);
   gw::oz_transform_free(p->ozt);
   gw::oz_pol_free(p->ozp);
+  gw::dyson_free(p->dyson);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -862,6 +866,72 @@ gw_status gw_timing_reset(gw_plan_t p) {
   } else {
     p->timer.totals.clear();
   }
+  return GW_OK;
+}
+
+gw_status gw_dyson_green_tau(gw_plan_t p, const void* H_k, const void* Sigx_k, const void* Sig_k_iw, double mu,
+                             void* G_k_tau, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!H_k || !G_k_tau || !std::isfinite(mu)) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  gw::ActiveTimer at_(&p->timer);
+  if ((st = gw::dyson_init(p->dyson, p->h)) != GW_OK) return st;
+  cudaStream_t s = S(stream);
+  const double2* H = (const double2*)H_k;
+  const double2* Sx = (const double2*)Sigx_k;
+  if ((st = gw::dyson_solve(p->dyson, p->h, H, Sx, (const double2*)Sig_k_iw, mu, p->d_status, s)) != GW_OK) return st;
+  return gw::dyson_to_tau(p->dyson, p->h, H, Sx, mu, p->d_Tf_inv, (double2*)G_k_tau, s);
+}
+
+gw_status gw_chemical_potential(gw_plan_t p, const void* H_k, const void* Sigx_k, const void* Sig_k_iw,
+                                double n_electrons, double mu_lo, double mu_hi, double tol, double* mu_out,
+                                double* n_out, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!H_k || !mu_out || !(mu_lo < mu_hi) || !(tol > 0.0) || !std::isfinite(n_electrons)) {
+    set_last_error("bad argument");
+    return GW_ERR_ARG;
+  }
+  DeviceGuard guard(p->device);
+  gw::ActiveTimer at_(&p->timer);
+  if ((st = gw::dyson_init(p->dyson, p->h)) != GW_OK) return st;
+  const gw::HostPlan& h = p->h;
+  cudaStream_t s = S(stream);
+  const double2* H = (const double2*)H_k;
+  const double2* Sx = (const double2*)Sigx_k;
+  const double2* Tlast = p->d_Tf_inv + (size_t)(h.n_tau - 1) * h.n_omega;  // the row of tau = beta-
+  std::vector<double> part(h.n_k);
+  // N(mu) = s (1/N_k) sum_k Re Tr[-G(k, beta-)], one Dyson solve per evaluation
+  auto count = [&](double mu, double* n) -> gw_status {
+    gw_status e = gw::dyson_solve(p->dyson, h, H, Sx, (const double2*)Sig_k_iw, mu, p->d_status, s);
+    if (e == GW_OK) e = gw::dyson_density(p->dyson, h, H, Sx, mu, Tlast, s);
+    if (e != GW_OK) return e;
+    GW_CUDA(cudaMemcpyAsync(part.data(), p->dyson.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
+    int flag = 0;
+    GW_CUDA(cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      cudaMemset(p->d_status, 0, sizeof(int));
+      set_last_error("zero pivot in the Dyson solve");
+      return GW_ERR_SINGULAR;
+    }
+    double t = 0.0;
+    for (double v : part) t += v;
+    *n = h.spin * t / h.n_k;
+    return GW_OK;
+  };
+  double lo = mu_lo, hi = mu_hi, n = 0.0;
+  for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if ((st = count(mid, &n)) != GW_OK) return st;
+    if (n < n_electrons) lo = mid;
+    else hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  if ((st = count(mu, &n)) != GW_OK) return st;
+  *mu_out = mu;
+  if (n_out) *n_out = n;
   return GW_OK;
 }
 

@@ -1,0 +1,36 @@
+// Eq. G_1 on the device: G(k, i w_n) = [(i w_n + mu) I - H(k) - Sigma_x(k) - Sigma_c(k, i w_n)]^{-1}
+// for the sampled fermionic frequencies, G(k, tau) through the inverse transform of
+// Appendix A with the two leading tail terms taken out, and the particle number from
+// G(k, beta-).  Kernels in kernels_dyson.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gw {
+
+struct DysonPlan {
+  bool ready = false;
+  int N = 0, n_w = 0, n_k = 0, n_tau = 0;
+  double2* M = nullptr;    // [n_k][n_w][N][N]: the matrices, then G(k, i w_n)
+  int* perm = nullptr;     // [n_k * n_w][N] pivot rows of the inverse
+  double* w = nullptr;     // [n_w] w_n = (2n + 1) pi / beta
+  double* tau = nullptr;   // [n_tau]
+  double* part = nullptr;  // [n_k] per-k traces for the particle number
+  size_t bytes = 0;
+};
+
+gw_status dyson_init(DysonPlan& d, const HostPlan& h);
+void dyson_free(DysonPlan& d);
+// G(k, i w_n) into d.M (H, Sigx: [n_k][N][N]; Sigc: [n_k][n_w][N][N]; Sigx and Sigc may be null).
+gw_status dyson_solve(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx, const double2* Sigc,
+                      double mu, int* d_status, cudaStream_t st);
+// G(k, tau) [n_k][n_tau][N][N] from d.M; T: the inverse fermionic transform [n_tau][n_w].
+gw_status dyson_to_tau(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx, double mu,
+                       const double2* T, double2* G_tau, cudaStream_t st);
+// d.part[k] = Re Tr[-G(k, beta-)] from d.M; Tlast: the last row of the inverse transform.
+gw_status dyson_density(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx, double mu,
+                        const double2* Tlast, cudaStream_t st);
+
+}  // namespace gw

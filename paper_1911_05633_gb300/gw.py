@@ -30,6 +30,7 @@ _STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
+    "gw_dyson_green_tau", "gw_chemical_potential",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
@@ -95,6 +96,9 @@ def load_library(path: str = LIB_PATH):
     lib.gw_plan_entries.argtypes = [vp, C.POINTER(C.c_int64)]
     lib.gw_plan_offsets.argtypes = [vp, C.c_int, C.POINTER(C.c_int64)]
     lib.gw_plan_entry_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.gw_dyson_green_tau.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
+    lib.gw_chemical_potential.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.gw_plan_transform_matrix.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.gw_fourier_k_to_R.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
     lib.gw_green_k_to_R.argtypes = [vp, vp, vp, vp]
@@ -339,6 +343,34 @@ class Plan:
                                            self._in(F_R, self.len(kind, n_slices), "F_R"),
                                            C.c_void_p(F_k.data_ptr()), self._stream(stream)), "gw_fourier_R_to_k")
         return F_k
+
+    # ---- Eq. G_1 -------------------------------------------------------------------------
+    def _dyson_inputs(self, H_k, Sigx_k, Sig_k_iw):
+        nk, N, nw = self.info["n_k"], self.dense_n("orb"), self.info["n_omega"]
+        h = self._in(H_k, nk * N * N, "H_k")
+        x = self._in(Sigx_k, nk * N * N, "Sigx_k") if Sigx_k is not None else C.c_void_p(0)
+        c = self._in(Sig_k_iw, nk * nw * N * N, "Sig_k_iw") if Sig_k_iw is not None else C.c_void_p(0)
+        return h, x, c
+
+    def dyson_green_tau(self, H_k, mu: float, Sigx_k=None, Sig_k_iw=None, G_k_tau=None, stream=None):
+        """gw_dyson_green_tau: G(k, tau) [N_k][N_tau][N][N] from Eq. G_1 with Sigma_x(k) and
+        Sigma_c(k, i w) (None: zero)."""
+        nk, N, nt = self.info["n_k"], self.dense_n("orb"), self.info["n_tau"]
+        G_k_tau = self._buf(G_k_tau, nk * nt * N * N, "G_k_tau")
+        h, x, c = self._dyson_inputs(H_k, Sigx_k, Sig_k_iw)
+        _check(self._lib.gw_dyson_green_tau(self._h, h, x, c, float(mu), C.c_void_p(G_k_tau.data_ptr()),
+                                            self._stream(stream)), "gw_dyson_green_tau")
+        return G_k_tau
+
+    def chemical_potential(self, H_k, n_electrons: float, lo: float, hi: float, tol: float = 1e-12,
+                           Sigx_k=None, Sig_k_iw=None, stream=None):
+        """gw_chemical_potential: (mu, N(mu)) with N(mu) = n_electrons by bisection on [lo, hi]."""
+        h, x, c = self._dyson_inputs(H_k, Sigx_k, Sig_k_iw)
+        mu, n = C.c_double(), C.c_double()
+        _check(self._lib.gw_chemical_potential(self._h, h, x, c, float(n_electrons), float(lo), float(hi), float(tol),
+                                               C.byref(mu), C.byref(n), self._stream(stream)),
+               "gw_chemical_potential")
+        return mu.value, n.value
 
     def sync(self, stream=None):
         _check(self._lib.gw_sync(self._h, self._stream(stream)), "gw_sync")

@@ -1,0 +1,83 @@
+"""Eq. G_1 on the device against the oracle: G(k, tau) from the Dyson solve with a static
+Sigma_x and a frequency-dependent Sigma_c, the chemical potential by bisection on the
+particle number, and the Dyson step fed by the device sweep's own Sigma (FP64, 1e-10)."""
+import numpy as np
+import pytest
+
+import oracle
+from test_gpu_parity import TOL, dev, host, rel, system
+
+pytestmark = pytest.mark.gpu
+
+
+def _sigmas(cell, seed):
+    """A static Hermitian Sigma_x(k) and a Sigma_c(k, i w) with Sigma_c(-i w) = Sigma_c(i w)^dagger."""
+    rng = np.random.default_rng(seed)
+    nk, N, idx = cell.n_k, cell.n_orb_total, cell.omega_idx
+    x = rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N))
+    Sx = 0.05 * (x + np.conj(np.transpose(x, (0, 2, 1))))
+    pos = {int(n): i for i, n in enumerate(idx)}
+    Sc = np.zeros((nk, len(idx), N, N), np.complex128)
+    for i, n in enumerate(idx):
+        if n >= 0:
+            c = 0.02 * (rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N)))
+            Sc[:, i] = c
+            j = pos.get(-int(n) - 1)  # w_{-n-1} = -w_n
+            if j is not None:
+                Sc[:, j] = np.conj(np.transpose(c, (0, 2, 1)))
+    return Sx, Sc
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5"])
+def test_dyson_green_tau(name):
+    s = system(name)
+    c = s.cell
+    Sx, Sc = _sigmas(c, 3)
+    ref = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, Sx, Sc, c.mu, c.beta, c.omega_idx), c.H_k, Sx, c.mu,
+                                 c.beta, c.tau, c.omega_idx, s.orc.F_inv)
+    G = host(s.plan.dyson_green_tau(dev(c.H_k), c.mu, Sigx_k=dev(Sx), Sig_k_iw=dev(Sc)))
+    s.plan.sync()
+    assert rel(G, ref.reshape(-1)) < TOL
+    # no self-energy: G0 of H through the same transform
+    Z = np.zeros_like(c.H_k)
+    ref0 = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, Z, None, c.mu, c.beta, c.omega_idx), c.H_k, Z, c.mu,
+                                  c.beta, c.tau, c.omega_idx, s.orc.F_inv)
+    G0 = host(s.plan.dyson_green_tau(dev(c.H_k), c.mu))
+    s.plan.sync()
+    assert rel(G0, ref0.reshape(-1)) < TOL
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed"])
+def test_chemical_potential(name):
+    s = system(name)
+    c = s.cell
+    Sx, Sc = _sigmas(c, 5)
+    target = float(c.n_orb_total)  # half filling, s = 2
+    e = np.linalg.eigvalsh(c.H_k)
+    lo, hi = float(e.min()) - 1.0, float(e.max()) + 1.0
+    mu_o, n_o = oracle.chemical_potential(c.H_k, Sx, Sc, target, c.beta, c.tau, c.omega_idx, s.orc.F_inv, c.spin,
+                                          lo, hi, tol=1e-11)
+    mu_g, n_g = s.plan.chemical_potential(dev(c.H_k), target, lo, hi, tol=1e-11, Sigx_k=dev(Sx), Sig_k_iw=dev(Sc))
+    assert abs(n_o - target) < 1e-8
+    assert abs(mu_g - mu_o) < 1e-9
+    assert abs(n_g - n_o) < 1e-9
+
+
+def test_dyson_after_the_device_sweep():
+    """Sigma(k, i w) and Sigma_x(k) from the whole device sweep feed the Dyson step: the
+    next iteration's G(k, tau) against the oracle's sweep and Dyson step."""
+    s = system("c0")
+    p, c = s.plan, s.cell
+    r = s.orc.sweep(s.G_k, s.v_q, s.v_class)
+    GR = p.green_k_to_R(dev(s.G_k))
+    PR = p.polarizability_tau(GR)
+    Wiw = p.screened_W_iw(p.transform_tau_iw("B", "tau_to_iw", "pb", PR), dev(s.v_q))
+    WR = p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw)
+    Sig, Sigx = p.self_energy_tau(GR, WR, v_R=p.fourier_k_to_R("pb", 1, dev(s.v_q)))
+    Sk = p.fourier_R_to_k("orb", c.omega_idx.size, p.transform_tau_iw("F", "tau_to_iw", "orb", Sig))
+    Sxk = p.fourier_R_to_k("orb", 1, Sigx)
+    G = host(p.dyson_green_tau(dev(c.H_k), c.mu, Sigx_k=Sxk, Sig_k_iw=Sk))
+    p.sync()
+    ref = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, r["Sigx_k"], r["Sig_k"], c.mu, c.beta, c.omega_idx),
+                                 c.H_k, r["Sigx_k"], c.mu, c.beta, c.tau, c.omega_idx, s.orc.F_inv)
+    assert rel(G, ref.reshape(-1)) < TOL
