@@ -29,6 +29,8 @@ Every function follows one statement of the paper, cited in its docstring:
 * Eq. G_1 (Dyson equation) with the Hartree G0, the particle number from
   G(beta-) and the chemical potential by bisection -> ``dyson_green_iw``,
   ``green_iw_to_tau``, ``particle_number``, ``chemical_potential``
+* the linearisation of Sigma at zero frequency behind the paper's band plots
+  (quasiparticle energies) -> ``qp_energies``
 
 Readings where the paper is silent or garbled (each listed in the design notes):
 P(x, x'; tau) = -s G(x, x'; tau) G(x', x; beta - tau) and G(x', x) = G(x, x')^*;
@@ -67,6 +69,7 @@ __all__ = [
     "green_iw_to_tau",
     "particle_number",
     "chemical_potential",
+    "qp_energies",
     "OracleSystem",
 ]
 
@@ -497,6 +500,35 @@ def chemical_potential(H_k, Sigx_k, Sig_k_iw, n_electrons: float, beta: float, t
             hi = mid
     mu = 0.5 * (lo + hi)
     return mu, count(mu)
+
+
+def qp_energies(H_k: np.ndarray, Sigx_k: np.ndarray, Sig_k_iw, mu: float, beta: float, omega_idx) -> np.ndarray:
+    """Linearised quasiparticle energies (the procedure the paper uses for its band
+    plots: the value and the frequency derivative of Sigma at zero frequency).  Through
+    the two lowest positive fermionic frequencies w_0 = pi/beta and w_1 = 3 pi/beta,
+    Sigma_c(i w) ~ S0 + i w S1 with S1 = (Sigma_c(i w_1) - Sigma_c(i w_0)) / (i (w_1 - w_0)) and
+    S0 = Sigma_c(i w_0) - i w_0 S1.  The poles of [i w (I - S1) - (H + Sigma_x + S0 - mu)]^{-1}
+    continued to the real axis, with Hermitian parts (h), are the eigenvalues of
+    A^{-1} (H + Sigma_x^h + S0^h - mu) A^{-1} with A = (I - S1^h)^{1/2}, plus mu.
+    Returns [N_k][N] ascending."""
+    idx = [int(n) for n in omega_idx]
+    i0, i1 = idx.index(0), idx.index(1)
+    w0, w1 = np.pi / beta, 3.0 * np.pi / beta
+    nk, N = H_k.shape[0], H_k.shape[1]
+    I = np.eye(N)
+    herm = lambda M: 0.5 * (M + M.conj().T)
+    out = np.empty((nk, N))
+    for k in range(nk):
+        if Sig_k_iw is None:
+            S0 = S1 = np.zeros((N, N), np.complex128)
+        else:
+            S1 = (Sig_k_iw[k, i1] - Sig_k_iw[k, i0]) / (1j * (w1 - w0))
+            S0 = Sig_k_iw[k, i0] - 1j * w0 * S1
+        lam, U = np.linalg.eigh(I - herm(S1))
+        Ainv = (U / np.sqrt(lam)) @ U.conj().T
+        X = herm(H_k[k]) + herm(Sigx_k[k]) + herm(S0) - mu * I
+        out[k] = np.linalg.eigvalsh(herm(Ainv @ X @ Ainv)) + mu
+    return out
 
 
 # ----------------------------------------------------------------------------

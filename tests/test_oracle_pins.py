@@ -623,3 +623,36 @@ def test_chemical_potential_reproduces_fermi_filling(cell_dense):
                                c.mu + 0.1, c.beta, c.tau, c.omega_idx, orc.F_inv)
     ref = c.spin * synth.fermi(e - c.mu - 0.1, c.beta).sum() / c.n_k
     assert abs(oracle.particle_number(G, c.spin) - ref) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Linearised quasiparticle energies
+# ----------------------------------------------------------------------------
+
+def test_qp_energies_without_correlation_are_hartree_fock(cell0):
+    c = cell0
+    rng = np.random.default_rng(12)
+    Sx = _static_hermitian(rng, c.n_k, c.n_orb_total)
+    E = oracle.qp_energies(c.H_k, Sx, None, c.mu, c.beta, c.omega_idx)
+    assert np.abs(E - np.linalg.eigvalsh(c.H_k + Sx)).max() < 1e-12
+
+
+def test_qp_energies_of_a_linear_self_energy_solve_the_generalised_problem(cell0):
+    """Sigma_c(i w) = S0 + i w S1 exactly (Hermitian S0, negative semidefinite S1): the
+    energies are the generalised eigenvalues of (H + Sigma_x + S0 - mu, I - S1) plus mu
+    (SciPy's generalised Hermitian-definite solver)."""
+    from scipy.linalg import eigh
+    c = cell0
+    rng = np.random.default_rng(13)
+    nk, N = c.n_k, c.n_orb_total
+    Sx = _static_hermitian(rng, nk, N)
+    S0 = _static_hermitian(rng, nk, N)
+    B = rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N))
+    S1 = -0.1 * np.einsum("kij,klj->kil", B, B.conj())  # -B B^dagger
+    w = (2 * c.omega_idx + 1) * np.pi / c.beta
+    Sc = S0[:, None] + 1j * w[None, :, None, None] * S1[:, None]
+    E = oracle.qp_energies(c.H_k, Sx, Sc, c.mu, c.beta, c.omega_idx)
+    I = np.eye(N)
+    for k in range(nk):
+        ref = eigh(c.H_k[k] + Sx[k] + S0[k] - c.mu * I, I - S1[k], eigvals_only=True) + c.mu
+        assert np.abs(E[k] - ref).max() < 1e-11
