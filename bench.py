@@ -468,7 +468,7 @@ def run_ours(args, rank, world, local):
                "stages": "every row except the W solve, which is timed on its own"}
 
     dyson = None if args.no_dyson else run_dyson(sw, cell, stream, args)
-    mixed_err = mixed_vs_fp64(sw, stream) if args.precision == "mixed" else None
+    mixed_err = mixed_vs_fp64(sw, stream, cell) if args.precision == "mixed" else None
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(sw, Gk, vq, stream, args)
@@ -544,12 +544,15 @@ def run_dyson(sw, cell, stream, args):
             "mu": mu, "n_electrons": n, "note": "Eq. G_1 with the sweep's Sigma; not part of value"}
 
 
-def mixed_vs_fp64(sw, stream):
+def mixed_vs_fp64(sw, stream, cell):
     """Relative Frobenius errors of the mixed path against the FP64 GPU path of the same
     plan on the same inputs (after the timed region): the P contraction (same G(R)), the
     Sigma contraction (same G(R) and W~(R)), and the whole sweep's Sigma(R, tau) and
-    Sigma(k, i omega), whose W~ comes from the mixed P through the W solve."""
+    Sigma(k, i omega), whose W~ comes from the mixed P through the W solve, and the
+    linearised quasiparticle energies from each sweep's Sigma (max |difference| in meV)."""
     torch = sw.torch
+    H = torch.from_numpy(cell.H_k.reshape(-1)).to(sw.dev)
+    qp = {}
     outs = {}
     for prec in ("mixed", "fp64"):
         sw.prec = prec
@@ -572,9 +575,62 @@ def mixed_vs_fp64(sw, stream):
     rel = {k: float(torch.linalg.vector_norm(outs["mixed"][k] - outs["fp64"][k]) /
                     torch.linalg.vector_norm(outs["fp64"][k])) for k in keys}
     del outs
+    qp = qp_compare(sw, stream, cell)
+    # the same on the two-atom configuration (beta = 50), where the linearisation is well conditioned
+    import synth
+    c0 = synth.make_config(0)
+    sw0 = Sweep(c0, "mixed", device=sw.dev.index)
+    sw0.load_inputs(c0.green_k_tau(), c0.coulomb()[0])
+    qp0 = qp_compare(sw0, stream, c0)
+    sw0.plan.close()
     return {**{k: float(f"{v:.3e}") for k, v in rel.items()}, "tolerance_contractions": 1e-6,
+            "qp_energies": qp, "qp_energies_two_atom_cell": qp0, "tolerance_qp_meV": 1.0,
             "reference": "the FP64 GPU path, same plan and inputs",
             "note": "the chain values carry the W solve's amplification of P's error"}
+
+
+def qp_compare(sw, stream, cell):
+    """Linearised quasiparticle energies (gw_qp_energies) from the mixed and from the FP64
+    sweep of the same inputs: their largest difference in meV, next to the problem's own
+    sensitivity (the largest shift of the FP64 energies when Sigma(k, i w) is scaled
+    elementwise by 1 + 1e-6 x seeded normal numbers) and the smallest eigenvalue of
+    I - S1^h (the frequency slope of Sigma at zero, whose inverse square root scales the
+    energies)."""
+    torch = sw.torch
+    H = torch.from_numpy(cell.H_k.reshape(-1)).to(sw.dev)
+    ss = stream.cuda_stream
+    E, Sk = {}, None
+    for prec in ("mixed", "fp64"):
+        sw.prec = prec
+        with torch.cuda.stream(stream):
+            sw.run(stream)
+            E[prec] = sw.plan.qp_energies(H, cell.mu, Sigx_k=sw.Sx_k, Sig_k_iw=sw.S_k, stream=ss)
+        sw.plan.sync(stream=ss)
+        torch.cuda.synchronize()
+        E[prec] = E[prec].cpu().numpy()
+    sw.prec = "mixed"
+    gen = torch.Generator(device=sw.dev).manual_seed(7)
+    noise = torch.randn(sw.S_k.shape, dtype=torch.float64, device=sw.dev, generator=gen)
+    Sp = sw.S_k * (1.0 + 1e-6 * noise)
+    with torch.cuda.stream(stream):
+        Ep = sw.plan.qp_energies(H, cell.mu, Sigx_k=sw.Sx_k, Sig_k_iw=Sp, stream=ss)
+    sw.plan.sync(stream=ss)
+    torch.cuda.synchronize()
+    Ep = Ep.cpu().numpy()
+    # slope of Sigma at zero frequency from the two lowest sampled frequencies (host)
+    inf = sw.plan.info
+    N, nk, nw = sw.plan.dense_n("orb"), inf["n_k"], inf["n_omega"]
+    idx = [int(n) for n in cell.omega_idx]
+    Sk = sw.S_k.view(nk, nw, N, N)
+    d = (Sk[:, idx.index(1)] - Sk[:, idx.index(0)]).cpu().numpy() / (1j * 2.0 * np.pi / cell.beta)
+    dh = 0.5 * (d + np.conj(np.transpose(d, (0, 2, 1))))
+    lam = float(np.linalg.eigvalsh(np.eye(N)[None] - dh).min())
+    mev = 27211.386245988
+    return {"max_abs_meV": float(f"{np.abs(E['mixed'] - E['fp64']).max() * mev:.3e}"),
+            "sensitivity_meV_per_1e-6_sigma": float(f"{np.abs(Ep - E['fp64']).max() * mev:.3e}"),
+            "min_eig_I_minus_S1h": float(f"{lam:.3e}"),
+            "energy_range_Ha": [float(f"{E['fp64'].min():.4f}"), float(f"{E['fp64'].max():.4f}")],
+            "workload": cell.name, "beta": cell.beta}
 
 
 def run_e2e(sw, Gk, vq, stream, args):

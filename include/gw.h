@@ -307,6 +307,18 @@ gw_status gw_chemical_potential(gw_plan_t plan, const void* H_k, const void* Sig
                                 double n_electrons, double mu_lo, double mu_hi, double tol, double* mu_out,
                                 double* n_out, void* stream);
 
+/* Linearised quasiparticle energies (the procedure behind the paper's band plots: the
+ * value and the frequency derivative of Sigma at zero frequency).  Sigma_c(i w) ~ S0 + i w S1
+ * through the sampled frequencies n = 0 and n = 1 (w_0 = pi/beta, w_1 = 3 pi/beta); with
+ * Hermitian parts (h) and A = (I - S1^h)^{1/2}, E(k) are the eigenvalues of
+ * A^{-1} (H(k) + Sigma_x^h(k) + S0^h - mu) A^{-1}, plus mu, in ascending order.
+ * H_k, Sigx_k, Sig_k_iw as for gw_dyson_green_tau (Sigx_k, Sig_k_iw may be NULL);
+ * E_k: device double [N_k][N].  FP64 throughout (Hermitian eigenproblems by cyclic
+ * Jacobi, one block per momentum).  GW_ERR_ARG if the sampled set lacks n = 0 or 1,
+ * GW_ERR_UNSUPPORTED for more than 80 orbitals in total. */
+gw_status gw_qp_energies(gw_plan_t plan, const void* H_k, const void* Sigx_k, const void* Sig_k_iw, double mu,
+                         void* E_k, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

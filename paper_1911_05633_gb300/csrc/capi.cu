@@ -935,6 +935,18 @@ gw_status gw_chemical_potential(gw_plan_t p, const void* H_k, const void* Sigx_k
   return GW_OK;
 }
 
+gw_status gw_qp_energies(gw_plan_t p, const void* H_k, const void* Sigx_k, const void* Sig_k_iw, double mu,
+                         void* E_k, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!H_k || !E_k || !std::isfinite(mu)) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(p->device);
+  gw::ActiveTimer at_(&p->timer);
+  if ((st = gw::dyson_init(p->dyson, p->h)) != GW_OK) return st;
+  return gw::qp_energies(p->h, (const double2*)H_k, (const double2*)Sigx_k, (const double2*)Sig_k_iw, mu,
+                         p->dyson.ainv, (double*)E_k, S(stream));
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -18,6 +18,7 @@ struct DysonPlan {
   double* w = nullptr;     // [n_w] w_n = (2n + 1) pi / beta
   double* tau = nullptr;   // [n_tau]
   double* part = nullptr;  // [n_k] per-k traces for the particle number
+  double2* ainv = nullptr;  // [n_k][N][N] scratch of the quasiparticle energies
   size_t bytes = 0;
 };
 
@@ -32,5 +33,11 @@ gw_status dyson_to_tau(DysonPlan& d, const HostPlan& h, const double2* H, const 
 // d.part[k] = Re Tr[-G(k, beta-)] from d.M; Tlast: the last row of the inverse transform.
 gw_status dyson_density(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx, double mu,
                         const double2* Tlast, cudaStream_t st);
+
+// Linearised quasiparticle energies E [n_k][N] ascending (kernels_qp.cu): Sigma_c from
+// the sampled frequencies n = 0 and n = 1; ainv_scratch: [n_k][N][N] complex.  N <= kQpMaxN.
+constexpr int kQpMaxN = 80;
+gw_status qp_energies(const HostPlan& h, const double2* H, const double2* Sigx, const double2* Sigc, double mu,
+                      double2* ainv_scratch, double* E, cudaStream_t st);
 
 }  // namespace gw

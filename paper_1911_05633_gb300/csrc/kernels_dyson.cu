@@ -151,7 +151,8 @@ gw_status dyson_init(DysonPlan& d, const HostPlan& h) {
                     up((void**)&d.perm, nullptr, nb * d.N * sizeof(int)) &&
                     up((void**)&d.w, w.data(), w.size() * sizeof(double)) &&
                     up((void**)&d.tau, h.tau.data(), h.tau.size() * sizeof(double)) &&
-                    up((void**)&d.part, nullptr, (size_t)d.n_k * sizeof(double));
+                    up((void**)&d.part, nullptr, (size_t)d.n_k * sizeof(double)) &&
+                    up((void**)&d.ainv, nullptr, (size_t)d.n_k * d.N * d.N * sizeof(double2));
   if (!good) {
     dyson_free(d);
     set_last_error("Dyson scratch allocation failed");
@@ -168,7 +169,7 @@ gw_status dyson_init(DysonPlan& d, const HostPlan& h) {
 }
 
 void dyson_free(DysonPlan& d) {
-  void* ptrs[] = {d.M, d.perm, d.w, d.tau, d.part};
+  void* ptrs[] = {d.M, d.perm, d.w, d.tau, d.part, d.ainv};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   d = DysonPlan{};

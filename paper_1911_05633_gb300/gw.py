@@ -30,7 +30,7 @@ _STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
-    "gw_dyson_green_tau", "gw_chemical_potential",
+    "gw_dyson_green_tau", "gw_chemical_potential", "gw_qp_energies",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_plan_offsets.argtypes = [vp, C.c_int, C.POINTER(C.c_int64)]
     lib.gw_plan_entry_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.gw_dyson_green_tau.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
+    lib.gw_qp_energies.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     lib.gw_chemical_potential.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.gw_plan_transform_matrix.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]
@@ -371,6 +372,19 @@ class Plan:
                                                C.byref(mu), C.byref(n), self._stream(stream)),
                "gw_chemical_potential")
         return mu.value, n.value
+
+    def qp_energies(self, H_k, mu: float, Sigx_k=None, Sig_k_iw=None, E_k=None, stream=None):
+        """gw_qp_energies: linearised quasiparticle energies [N_k][N] (float64, ascending)."""
+        torch = self._torch()
+        nk, N = self.info["n_k"], self.dense_n("orb")
+        if E_k is None:
+            E_k = torch.empty(nk * N, dtype=torch.float64, device=self._dev())
+        elif E_k.dtype != torch.float64 or not E_k.is_contiguous() or E_k.numel() != nk * N:
+            raise ValueError(f"E_k: need a contiguous float64 tensor of {nk * N} elements")
+        h, x, c = self._dyson_inputs(H_k, Sigx_k, Sig_k_iw)
+        _check(self._lib.gw_qp_energies(self._h, h, x, c, float(mu), C.c_void_p(E_k.data_ptr()),
+                                        self._stream(stream)), "gw_qp_energies")
+        return E_k
 
     def sync(self, stream=None):
         _check(self._lib.gw_sync(self._h, self._stream(stream)), "gw_sync")

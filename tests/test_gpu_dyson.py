@@ -81,3 +81,48 @@ def test_dyson_after_the_device_sweep():
     ref = oracle.green_iw_to_tau(oracle.dyson_green_iw(c.H_k, r["Sigx_k"], r["Sig_k"], c.mu, c.beta, c.omega_idx),
                                  c.H_k, r["Sigx_k"], c.mu, c.beta, c.tau, c.omega_idx, s.orc.F_inv)
     assert rel(G, ref.reshape(-1)) < TOL
+
+
+def _linear_sigma(cell, seed):
+    """Sigma_c(i w) = S0 + i w S1 with Hermitian S0 and negative semidefinite S1, and a
+    static Hermitian Sigma_x."""
+    rng = np.random.default_rng(seed)
+    nk, N = cell.n_k, cell.n_orb_total
+    herm = lambda x: 0.5 * (x + np.conj(np.transpose(x, (0, 2, 1))))
+    Sx = 0.1 * herm(rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N)))
+    S0 = 0.05 * herm(rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N)))
+    B = rng.standard_normal((nk, N, N)) + 1j * rng.standard_normal((nk, N, N))
+    S1 = -0.2 / N * np.einsum("kij,klj->kil", B, B.conj())
+    w = (2 * cell.omega_idx + 1) * np.pi / cell.beta
+    return Sx, S0[:, None] + 1j * w[None, :, None, None] * S1[:, None]
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1_cut5"])
+def test_qp_energies(name):
+    s = system(name)
+    c = s.cell
+    Sx, Sc = _linear_sigma(c, 21)
+    ref = oracle.qp_energies(c.H_k, Sx, Sc, c.mu, c.beta, c.omega_idx)
+    E = s.plan.qp_energies(dev(c.H_k), c.mu, Sigx_k=dev(Sx), Sig_k_iw=dev(Sc))
+    s.plan.sync()
+    E = E.cpu().numpy().reshape(ref.shape)
+    assert np.abs(E - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
+    # without correlation: the Hartree-Fock levels
+    E0 = s.plan.qp_energies(dev(c.H_k), c.mu, Sigx_k=dev(Sx)).cpu().numpy().reshape(ref.shape)
+    assert np.abs(E0 - np.linalg.eigvalsh(c.H_k + Sx)).max() < 1e-10 * max(1.0, np.abs(E0).max())
+
+
+def test_qp_energies_after_the_device_sweep():
+    s = system("c0")
+    p, c = s.plan, s.cell
+    r = s.orc.sweep(s.G_k, s.v_q, s.v_class)
+    GR = p.green_k_to_R(dev(s.G_k))
+    Wiw = p.screened_W_iw(p.transform_tau_iw("B", "tau_to_iw", "pb", p.polarizability_tau(GR)), dev(s.v_q))
+    Sig, Sigx = p.self_energy_tau(GR, p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw),
+                                  v_R=p.fourier_k_to_R("pb", 1, dev(s.v_q)))
+    Sk = p.fourier_R_to_k("orb", c.omega_idx.size, p.transform_tau_iw("F", "tau_to_iw", "orb", Sig))
+    Sxk = p.fourier_R_to_k("orb", 1, Sigx)
+    E = p.qp_energies(dev(c.H_k), c.mu, Sigx_k=Sxk, Sig_k_iw=Sk)
+    p.sync()
+    ref = oracle.qp_energies(c.H_k, r["Sigx_k"], r["Sig_k"], c.mu, c.beta, c.omega_idx)
+    assert np.abs(E.cpu().numpy().reshape(ref.shape) - ref).max() < 1e-10
