@@ -65,6 +65,8 @@ def parse():
                     help="radius of sphere B (bohr): pairs beyond it keep --n-prod-far product functions (Sec. 2)")
     ap.add_argument("--n-prod-far", type=int, nargs="+", default=None,
                     help="product functions per species kept by pairs beyond sphere B")
+    ap.add_argument("--serve", action="store_true",
+                    help="Poisson request stream of whole GW iterations on four small systems: p50/p99 latency")
     ap.add_argument("--scaling", type=int, nargs="*", default=None,
                     help="time the P+Sigma rows (no W solve) of the 64-function diamond series at these atom "
                          "counts (default 8 16 32 48 72), FP64 and mixed; one JSON line")
@@ -811,8 +813,55 @@ def run_scaling(args, local):
             "series": rows}
 
 
+def run_serve(args, local):
+    """Serving: a Poisson stream of whole GW iterations (G -> P -> W -> Sigma -> Dyson -> G)
+    on four systems of different sizes, continuous batching across systems
+    (paper_1911_05633_gb300.serve), the arrival rate swept to saturation.  Per rate:
+    p50 / p99 latency (arrival to completion) and throughput."""
+    import torch
+    import synth
+    from paper_1911_05633_gb300.serve import Server, System, latency_stats, poisson_arrivals
+    torch.cuda.set_device(local)
+    cells = {"sc2-n4-K8": synth.make_config(0), "mixed2-n4/5-K8/19": synth.mixed_species_cell(),
+             "diamond8-cut5": synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
+             "diamond8-cut5-far": synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
+                                                       4.0, [24])}
+    systems = {n: System(n, c, device=local, precision=args.precision) for n, c in cells.items()}
+    names = list(systems)
+    server = Server(systems, mem_cap_bytes=sum(s.footprint for s in systems.values()))
+    for _ in range(max(1, args.warmup)):  # warm-up: every system once
+        server.run([(0.0, n) for n in names])
+    alone = {}
+    for n in names:  # service time of each system alone
+        lat = [server.run([(0.0, n)])[0].latency for _ in range(3)]
+        alone[n] = round(1e3 * float(np.median(lat)), 3)
+    mean_service = float(np.mean(list(alone.values()))) / 1e3
+    series = []
+    for f in (0.25, 0.5, 1.0, 2.0, 4.0):  # offered load relative to one system at a time
+        rate = f / mean_service
+        for s in systems.values():
+            s.reset()
+        reqs = server.run(poisson_arrivals(rate, 40 * max(1, args.steps // 5), names, seed=int(f * 100)))
+        series.append({"offered_per_s": round(rate, 2), "load_vs_serial": f, **latency_stats(reqs)})
+    for s in systems.values():
+        s.close()
+    return {"metric": "serve p50/p99 latency of whole GW iterations (continuous batching)", "unit": "ms",
+            "precision": args.precision, "data": "synthetic",
+            "config": {"systems": {n: {"atoms": c.n_atoms, "orbitals": c.n_orb_total, "n_pb": c.n_pb_total,
+                                       "k": int(np.prod(c.kmesh)), "tau": c.n_tau} for n, c in cells.items()},
+                       "request": "one iteration: G(k,tau) -> G(R) -> P -> P(i nu) -> W~ -> W~(tau) -> Sigma, "
+                                  "Sigma_x -> Sigma(k, i w) -> Dyson -> G(k,tau)",
+                       "admission": "arrival order; a system runs one request at a time; memory cap = all systems"},
+            "alone_ms": alone, "series": series}
+
+
 def main():
     args = parse()
+    if args.serve:
+        rank, world, local = dist_init(args)
+        if rank == 0:
+            print(json.dumps(run_serve(args, local)), flush=True)
+        return
     if args.scaling is not None:
         rank, world, local = dist_init(args)
         if rank == 0:
