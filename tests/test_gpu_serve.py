@@ -48,12 +48,18 @@ def test_result_alone_equals_result_in_the_mix(systems):
     assert all(r.done is not None and r.done >= r.admitted >= r.arrival - 1e-9 for r in mix)
 
 
-def test_memory_cap_serialises(systems):
-    """A cap that holds one system at a time: no two requests overlap."""
+def test_memory_cap_bounds_what_runs_at_once(systems):
+    """A cap equal to the largest system's footprint: that system never runs beside
+    another, and the footprints of the requests running at any moment fit the cap."""
     from paper_1911_05633_gb300.serve import Server
-    server = Server(systems, mem_cap_bytes=max(s.footprint for s in systems.values()))
+    cap = max(s.footprint for s in systems.values())
+    big = max(systems, key=lambda n: systems[n].footprint)
+    server = Server(systems, mem_cap_bytes=cap)
     for s in systems.values():
         s.reset()
-    reqs = server.run([(0.0, n) for n in ("c0", "mixed", "c1_cut5", "c0")])
-    spans = sorted((r.admitted, r.done) for r in reqs)
-    assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))
+    reqs = server.run([(0.0, n) for n in ("c0", "mixed", "c1_cut5", "c0", "mixed", "c1_cut5")])
+    for r in reqs:
+        during = [q for q in reqs if q is not r and q.admitted < r.done and r.admitted < q.done]
+        assert sum(systems[q.system].footprint for q in during) + systems[r.system].footprint <= cap
+        if r.system == big:
+            assert not during
