@@ -100,6 +100,14 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def aggregate(step_ms: float, world: int):
+    """Whole-job figures of a replicated run (every rank sweeps its own copy of the
+    workload): the slowest rank's ms per step and the sweeps per second of all ranks
+    together, world / that time."""
+    step_ms_max = max_over_ranks(step_ms, world)
+    return step_ms_max, world * 1000.0 / step_ms_max
+
+
 # --------------------------------------------------------------------------------------
 # workload and its algorithmic work
 # --------------------------------------------------------------------------------------
@@ -414,8 +422,7 @@ def run_ours(args, rank, world, local):
     sw.plan.timing_enable(False)
     stage_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nst)] for k in range(args.steps)])
     step_ms = float(stage_ms.sum(axis=1).mean())
-    step_ms_max = max_over_ranks(step_ms, world)
-    value = world * 1000.0 / step_ms_max
+    step_ms_max, value = aggregate(step_ms, world)
     stage_mean = stage_ms.mean(axis=0)
 
     # roofline of the dominant kernel, timed live by the library's event pairs
