@@ -79,9 +79,14 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.offBar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // tensor-memory accumulator: 128 lanes x NP columns (allocation: power of two >= 32)
+  // tensor-memory accumulators: one of 128 lanes x NP columns per 16-wide K step when they
+  // fit the 512 columns (the tensor core truncates as it accumulates, so fewer additions
+  // per accumulator keep the sum closer; the epilogue adds them with rounding to nearest),
+  // else one for all (allocation: power of two >= 32)
+  const int nks = L.KD / 16;
+  const bool per_step = nks * L.NP <= 512;
   uint32_t ncols = 32;
-  while ((int)ncols < L.NP) ncols <<= 1;
+  while ((int)ncols < (per_step ? nks * L.NP : L.NP)) ncols <<= 1;
   if (warp == 0) {
     tmem_alloc(&tmem_base, ncols);
     tmem_relinquish();
@@ -190,17 +195,18 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
     __syncthreads();
     fence_after_sync();
     if (tid == 0) {
-      const int nks = L.KD / 16;
       uint32_t acc = 0;
       for (int s = 0; s < nks; ++s) {
         const uint32_t ao = (uint32_t)s * 128u * 32u, bo = (uint32_t)s * (uint32_t)L.NP * 32u;
+        const uint32_t td = tm + (per_step ? (uint32_t)(s * L.NP) : 0u);
+        if (per_step) acc = 0;
         // the six split products with i + j <= 2 (0 = hi, 1 = mid, 2 = lo)
         const int pa[6] = {0, 0, 1, 0, 1, 2};
         const int pb[6] = {0, 1, 0, 2, 1, 0};
         for (int q = 0; q < 6; ++q) {
           const uint64_t da = smem_desc(aBase + pa[q] * aPlane + ao, 128, 256);
           const uint64_t db = smem_desc(bBase + pb[q] * bPlane + bo, 128, 256);
-          mma_bf16(tm, da, db, idesc, acc);
+          mma_bf16(td, da, db, idesc, acc);
           acc = 1;
         }
       }
@@ -221,8 +227,13 @@ k_polarizability_tc(const DevEntry* __restrict__ ent, const float* __restrict__ 
     if (warp < 4) {
       const int r = 32 * warp + lane;
       for (int c0 = 0; c0 < L.NP; c0 += 16) {
-        float v[16];
+        float v[16], t[16];
         tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        for (int s = 1; per_step && s < nks; ++s) {
+          tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * L.NP + c0), t);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += t[i];
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int Kp = c0 + i;
