@@ -310,8 +310,12 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
   float2* Red = reinterpret_cast<float2*>(sm + L.offRed);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.offBar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // one accumulator of NJ columns per 16-wide K step when they fit the 512 columns (as in
+  // the P kernel: fewer truncating additions per accumulator), else one for all
+  const int nks = L.KK / 16;
+  const bool per_step = nks * L.NJ <= 512;
   uint32_t ncols = 32;
-  while ((int)ncols < L.NJ) ncols <<= 1;
+  while ((int)ncols < (per_step ? nks * L.NJ : L.NJ)) ncols <<= 1;
   if (warp == 0) {
     tmem_alloc(&tmem_base, ncols);
     tmem_relinquish();
@@ -387,16 +391,17 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
     __syncthreads();
     fence_after_sync();
     if (tid == 0) {
-      const int nks = L.KK / 16;
       uint32_t acc = 0;
       const int pa[6] = {0, 0, 1, 0, 1, 2};
       const int pb[6] = {0, 1, 0, 2, 1, 0};
       for (int s2 = 0; s2 < nks; ++s2) {
         const uint32_t ao = (uint32_t)s2 * 128u * 32u, bo = (uint32_t)s2 * (uint32_t)L.NJ * 32u;
+        const uint32_t td = tm + (per_step ? (uint32_t)(s2 * L.NJ) : 0u);
+        if (per_step) acc = 0;
         for (int q = 0; q < 6; ++q) {
           const uint64_t da = smem_desc(aBase + pa[q] * aPlane + ao, 128, 256);
           const uint64_t db = smem_desc(bBase + pb[q] * bPlane + bo, 128, 256);
-          mma_bf16(tm, da, db, idesc, acc);
+          mma_bf16(td, da, db, idesc, acc);
           acc = 1;
         }
       }
@@ -414,8 +419,13 @@ k_self_energy_tc(const DevEntry* __restrict__ ent, const float* __restrict__ C, 
     if (warp < 4) {
       const int r = 32 * warp + lane;
       for (int c0 = 0; c0 < L.NJ; c0 += 16) {
-        float v[16];
+        float v[16], t[16];
         tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        for (int s2 = 1; per_step && s2 < nks; ++s2) {
+          tmem_ld16(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s2 * L.NJ + c0), t);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += t[i];
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = c0 + i;
