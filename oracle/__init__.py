@@ -31,6 +31,9 @@ Every function follows one statement of the paper, cited in its docstring:
   ``green_iw_to_tau``, ``particle_number``, ``chemical_potential``
 * the linearisation of Sigma at zero frequency behind the paper's band plots
   (quasiparticle energies) -> ``qp_energies``
+* Eq. sf_9, the continued fraction through Sigma on the stored Matsubara grid
+  (analytic continuation to w + i delta) -> ``continued_fraction_coefficients``,
+  ``continued_fraction_value``, ``continue_sigma``
 
 Readings where the paper is silent or garbled (each listed in the design notes):
 P(x, x'; tau) = -s G(x, x'; tau) G(x', x; beta - tau) and G(x', x) = G(x, x')^*;
@@ -70,6 +73,9 @@ __all__ = [
     "particle_number",
     "chemical_potential",
     "qp_energies",
+    "continued_fraction_coefficients",
+    "continued_fraction_value",
+    "continue_sigma",
     "OracleSystem",
 ]
 
@@ -528,6 +534,54 @@ def qp_energies(H_k: np.ndarray, Sigx_k: np.ndarray, Sig_k_iw, mu: float, beta: 
         Ainv = (U / np.sqrt(lam)) @ U.conj().T
         X = herm(H_k[k]) + herm(Sigx_k[k]) + herm(S0) - mu * I
         out[k] = np.linalg.eigvalsh(herm(Ainv @ X @ Ainv)) + mu
+    return out
+
+
+def continued_fraction_coefficients(z: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Coefficients a_0..a_M of the continued fraction of Eq. sf_9 through the points
+    (z_i, f_i), i = 0..M (the recursion of its reference, Vidberg and Serene): g_0(z_i) = f_i,
+    g_p(z_i) = (g_{p-1}(z_{p-1}) - g_{p-1}(z_i)) / ((z_i - z_{p-1}) g_{p-1}(z_i)) for i >= p,
+    a_p = g_p(z_p).  f: [M+1][...] (any trailing shape, one fraction per element)."""
+    z = np.asarray(z, dtype=np.complex128)
+    g = np.array(f, dtype=np.complex128, copy=True)
+    a = np.empty_like(g)
+    a[0] = g[0]
+    shape = (-1,) + (1,) * (g.ndim - 1)
+    for p in range(1, len(z)):
+        g[p:] = (g[p - 1] - g[p:]) / ((z[p:] - z[p - 1]).reshape(shape) * g[p:])
+        a[p] = g[p]
+    return a
+
+
+def continued_fraction_value(a: np.ndarray, z: np.ndarray, w) -> np.ndarray:
+    """Eq. sf_9 at the complex frequencies w: a_0 / (1 + a_1 (w - z_0) / (1 + ... a_M (w - z_{M-1}) / 1)),
+    evaluated from the innermost level out.  Returns [len(w)][...]."""
+    z = np.asarray(z, dtype=np.complex128)
+    w = np.asarray(w, dtype=np.complex128)
+    M = len(z) - 1
+    out = []
+    for x in w:
+        A = np.ones_like(a[0])
+        for p in range(M, 0, -1):
+            A = 1.0 + a[p] * (x - z[p - 1]) / A
+        out.append(a[0] / A)
+    return np.array(out)
+
+
+def continue_sigma(Sig_k_iw: np.ndarray, omega_idx, beta: float, w_real, delta: float) -> np.ndarray:
+    """Sigma(k, w + i delta) per element from Sigma(k, i w_n) on the stored grid's non-negative
+    sampled frequencies (the paper feeds the continuation the self-consistent grid itself),
+    by the continued fraction of Eq. sf_9.  Sig_k_iw: [N_k][n_w][N][N]; returns
+    [N_k][len(w_real)][N][N]."""
+    idx = np.asarray(omega_idx)
+    pos = np.nonzero(idx >= 0)[0]
+    pos = pos[np.argsort(idx[pos])]
+    z = 1j * (2 * idx[pos] + 1) * np.pi / beta
+    w = np.asarray(w_real, dtype=np.float64) + 1j * delta
+    out = np.empty((Sig_k_iw.shape[0], len(w)) + Sig_k_iw.shape[2:], np.complex128)
+    for k in range(Sig_k_iw.shape[0]):
+        a = continued_fraction_coefficients(z, Sig_k_iw[k, pos])
+        out[k] = continued_fraction_value(a, z, w)
     return out
 
 

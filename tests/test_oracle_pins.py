@@ -656,3 +656,55 @@ def test_qp_energies_of_a_linear_self_energy_solve_the_generalised_problem(cell0
     for k in range(nk):
         ref = eigh(c.H_k[k] + Sx[k] + S0[k] - c.mu * I, I - S1[k], eigvals_only=True) + c.mu
         assert np.abs(E[k] - ref).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------
+# Eq. sf_9: continued-fraction continuation
+# ----------------------------------------------------------------------------
+
+def test_continued_fraction_reproduces_a_pole_sum():
+    """f(z) = sum_j A_j / (z - p_j) with J poles is a rational function the fraction through
+    2J points represents exactly: the continuation to the real axis is f itself."""
+    rng = np.random.default_rng(3)
+    J = 4
+    A = rng.uniform(0.1, 1.0, J)
+    p = rng.uniform(-2.0, 2.0, J) - 0.05j
+    f = lambda z: (A[None, :] / (np.asarray(z)[:, None] - p[None, :])).sum(axis=1)
+    z = 1j * (2 * np.arange(2 * J) + 1) * np.pi / 20.0
+    a = oracle.continued_fraction_coefficients(z, f(z))
+    w = np.linspace(-3.0, 3.0, 41) + 0.01j
+    # continuing from the imaginary axis to poles 0.05 below the real one is ill-conditioned:
+    # rounding reaches ~1e-9 here, while one point too few leaves errors of order one
+    assert np.abs(oracle.continued_fraction_value(a, z, w) - f(w)).max() < 1e-7 * np.abs(f(w)).max()
+    a7 = oracle.continued_fraction_coefficients(z[:-1], f(z[:-1]))
+    assert np.abs(oracle.continued_fraction_value(a7, z[:-1], w) - f(w)).max() > 1e-2 * np.abs(f(w)).max()
+
+
+def test_continued_fraction_interpolates_its_points():
+    rng = np.random.default_rng(4)
+    z = 1j * (2 * np.sort(rng.choice(60, 12, replace=False)) + 1) * np.pi / 30.0
+    f = rng.standard_normal((12, 3, 3)) + 1j * rng.standard_normal((12, 3, 3))
+    a = oracle.continued_fraction_coefficients(z, f)
+    assert np.abs(oracle.continued_fraction_value(a, z, z) - f).max() < 1e-9 * np.abs(f).max()
+
+
+def test_continue_sigma_of_a_single_pole_self_energy(cell0):
+    """A self-energy made of one pole per element, sampled on the stored grid of
+    configuration 0: the continuation through the grid's 2 lowest non-negative
+    frequencies returns it on the real axis (the rest of the grid carries the same
+    rational function, so every level beyond the second vanishes)."""
+    c = cell0
+    idx = np.asarray(c.omega_idx)
+    keep = idx[(idx >= 0)]
+    keep = np.sort(keep)[:2]
+    mask = np.isin(idx, keep)
+    rng = np.random.default_rng(5)
+    nk, N = c.n_k, c.n_orb_total
+    A = rng.uniform(0.1, 1.0, (nk, N, N))
+    P = rng.uniform(-1.0, 1.0, (nk, N, N)) - 0.1j
+    w = (2 * idx[mask] + 1) * np.pi / c.beta
+    S = A[:, None] / (1j * w[None, :, None, None] - P[:, None])
+    wr = np.linspace(-1.0, 1.0, 9)
+    out = oracle.continue_sigma(S, idx[mask], c.beta, wr, 0.02)
+    ref = A[:, None] / ((wr + 0.02j)[None, :, None, None] - P[:, None])
+    assert np.abs(out - ref).max() < 1e-10 * np.abs(ref).max()
