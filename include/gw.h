@@ -319,6 +319,18 @@ gw_status gw_chemical_potential(gw_plan_t plan, const void* H_k, const void* Sig
 gw_status gw_qp_energies(gw_plan_t plan, const void* H_k, const void* Sigx_k, const void* Sig_k_iw, double mu,
                          void* E_k, void* stream);
 
+/* Eq. sf_9: the continued fraction through Sigma on the stored Matsubara grid, per
+ * element, continued to the real frequencies w_r + i delta (w measured from mu):
+ *   Sigma(w) = a_0 / (1 + a_1 (w - z_0) / (1 + ... a_M (w - z_{M-1}) / 1)),
+ * with z_i = i w_i the non-negative sampled fermionic frequencies of the plan (ascending,
+ * at most 64) and a_p from the recursion of the fraction's reference (Vidberg and Serene).
+ * Sig_k_iw: device [N_k][n_omega][N][N]; w_real: HOST [n_real]; Sig_k_w: device
+ * [N_k][n_real][N][N].  The continuation from the imaginary axis is ill-conditioned by
+ * nature: results near poles close to the real axis carry rounding amplified accordingly.
+ * Synchronous with respect to the copy of w_real; the kernel is asynchronous. */
+gw_status gw_continue_sigma(gw_plan_t plan, const void* Sig_k_iw, int n_real, const double* w_real, double delta,
+                            void* Sig_k_w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

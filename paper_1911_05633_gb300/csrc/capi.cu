@@ -947,6 +947,21 @@ gw_status gw_qp_energies(gw_plan_t p, const void* H_k, const void* Sigx_k, const
                          p->dyson.ainv, (double*)E_k, S(stream));
 }
 
+gw_status gw_continue_sigma(gw_plan_t p, const void* Sig_k_iw, int n_real, const double* w_real, double delta,
+                            void* Sig_k_w, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!Sig_k_iw || !Sig_k_w || !w_real || n_real < 1 || !(delta >= 0.0)) {
+    set_last_error("bad argument");
+    return GW_ERR_ARG;
+  }
+  DeviceGuard guard(p->device);
+  gw::ActiveTimer at_(&p->timer);
+  if ((st = gw::dyson_init(p->dyson, p->h)) != GW_OK) return st;
+  return gw::continue_sigma(p->dyson, p->h, (const double2*)Sig_k_iw, n_real, w_real, delta, (double2*)Sig_k_w,
+                            S(stream));
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,8 @@ struct DysonPlan {
   double* tau = nullptr;   // [n_tau]
   double* part = nullptr;  // [n_k] per-k traces for the particle number
   double2* ainv = nullptr;  // [n_k][N][N] scratch of the quasiparticle energies
+  void* cont = nullptr;      // small tables of the continued fraction
+  size_t cont_bytes = 0;
   size_t bytes = 0;
 };
 
@@ -39,5 +41,11 @@ gw_status dyson_density(DysonPlan& d, const HostPlan& h, const double2* H, const
 constexpr int kQpMaxN = 80;
 gw_status qp_energies(const HostPlan& h, const double2* H, const double2* Sigx, const double2* Sigc, double mu,
                       double2* ainv_scratch, double* E, cudaStream_t st);
+
+// Eq. sf_9: Sigma(k, w_r + i delta) [n_k][n_real][N][N] from Sigma(k, i w_n) [n_k][n_w][N][N]
+// through the non-negative sampled frequencies (kernels_cont.cu); w_real on the host.
+constexpr int kContMax = 64;
+gw_status continue_sigma(DysonPlan& d, const HostPlan& h, const double2* S, int n_real, const double* w_real_host,
+                         double delta, double2* out, cudaStream_t st);
 
 }  // namespace gw

@@ -30,7 +30,7 @@ _STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
-    "gw_dyson_green_tau", "gw_chemical_potential", "gw_qp_energies",
+    "gw_dyson_green_tau", "gw_chemical_potential", "gw_qp_energies", "gw_continue_sigma",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.gw_plan_entry_dims.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.gw_dyson_green_tau.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     lib.gw_qp_energies.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
+    lib.gw_continue_sigma.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double), C.c_double, vp, vp]
     lib.gw_chemical_potential.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.gw_plan_transform_matrix.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]
@@ -385,6 +386,17 @@ class Plan:
         _check(self._lib.gw_qp_energies(self._h, h, x, c, float(mu), C.c_void_p(E_k.data_ptr()),
                                         self._stream(stream)), "gw_qp_energies")
         return E_k
+
+    def continue_sigma(self, Sig_k_iw, w_real, delta: float, Sig_k_w=None, stream=None):
+        """gw_continue_sigma: Sigma(k, w + i delta) [N_k][len(w_real)][N][N] by the continued
+        fraction of Eq. sf_9 through the non-negative sampled frequencies."""
+        nk, N, nw = self.info["n_k"], self.dense_n("orb"), self.info["n_omega"]
+        wr = np.ascontiguousarray(np.asarray(w_real, dtype=np.float64))
+        Sig_k_w = self._buf(Sig_k_w, nk * len(wr) * N * N, "Sig_k_w")
+        _check(self._lib.gw_continue_sigma(self._h, self._in(Sig_k_iw, nk * nw * N * N, "Sig_k_iw"), len(wr),
+                                           _ptr(wr, C.c_double), float(delta), C.c_void_p(Sig_k_w.data_ptr()),
+                                           self._stream(stream)), "gw_continue_sigma")
+        return Sig_k_w
 
     def sync(self, stream=None):
         _check(self._lib.gw_sync(self._h, self._stream(stream)), "gw_sync")

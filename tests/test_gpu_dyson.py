@@ -126,3 +126,44 @@ def test_qp_energies_after_the_device_sweep():
     p.sync()
     ref = oracle.qp_energies(c.H_k, r["Sigx_k"], r["Sig_k"], c.mu, c.beta, c.omega_idx)
     assert np.abs(E.cpu().numpy().reshape(ref.shape) - ref).max() < 1e-10
+
+
+def _pole_sigma(cell, seed, n_poles=10):
+    """Sigma(k, i w) of n_poles poles per element below the real axis, on the stored grid."""
+    rng = np.random.default_rng(seed)
+    nk, N = cell.n_k, cell.n_orb_total
+    A = rng.uniform(0.05, 0.5, (n_poles, nk, N, N))
+    P = rng.uniform(-1.5, 1.5, (n_poles, nk, N, N)) - 1j * rng.uniform(0.1, 0.5, (n_poles, nk, N, N))
+    z = 1j * (2 * cell.omega_idx + 1) * np.pi / cell.beta
+    return (A[:, :, None] / (z[None, None, :, None, None] - P[:, :, None])).sum(axis=0)
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed"])
+def test_continue_sigma(name):
+    """Eq. sf_9 on the device against the oracle's continued fraction, same inputs."""
+    s = system(name)
+    c = s.cell
+    S = _pole_sigma(c, 31)
+    wr = np.linspace(-1.0, 1.0, 7)
+    ref = oracle.continue_sigma(S, c.omega_idx, c.beta, wr, 0.05)
+    out = host(s.plan.continue_sigma(dev(S), wr, 0.05)).reshape(ref.shape)
+    s.plan.sync()
+    assert np.isfinite(ref).all()
+    assert np.abs(out - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_continue_sigma_of_the_device_sweep():
+    s = system("c0")
+    p, c = s.plan, s.cell
+    GR = p.green_k_to_R(dev(s.G_k))
+    Wiw = p.screened_W_iw(p.transform_tau_iw("B", "tau_to_iw", "pb", p.polarizability_tau(GR)), dev(s.v_q))
+    Sig = p.self_energy_tau(GR, p.transform_tau_iw("B", "iw_to_tau", "pb", Wiw))
+    Sk = p.fourier_R_to_k("orb", c.omega_idx.size, p.transform_tau_iw("F", "tau_to_iw", "orb", Sig))
+    wr = np.linspace(-0.5, 0.5, 5)
+    out = host(p.continue_sigma(Sk, wr, 0.02))
+    p.sync()
+    ref = oracle.continue_sigma(host(Sk).reshape(c.n_k, c.omega_idx.size, c.n_orb_total, c.n_orb_total),
+                                c.omega_idx, c.beta, wr, 0.02)
+    ok = np.isfinite(ref)
+    assert ok.mean() > 0.99
+    assert np.abs(out.reshape(ref.shape)[ok] - ref[ok]).max() <= 1e-6 * np.abs(ref[ok]).max()
