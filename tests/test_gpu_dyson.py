@@ -138,18 +138,35 @@ def _pole_sigma(cell, seed, n_poles=10):
     return (A[:, :, None] / (z[None, None, :, None, None] - P[:, :, None])).sum(axis=0)
 
 
+def _rounding_envelope(S, idx, beta, wr, delta, seeds=(0, 1, 2)):
+    """How far the oracle's own continuation moves, element by element, when its input is
+    perturbed at the level of FP64 rounding (1e-16 relative): continuing from the
+    imaginary axis amplifies rounding, and two correct FP64 evaluations that round
+    differently differ by about this much."""
+    ref = oracle.continue_sigma(S, idx, beta, wr, delta)
+    env = np.zeros(ref.shape)
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        Sp = S * (1 + 1e-16 * (rng.standard_normal(S.shape) + 1j * rng.standard_normal(S.shape)))
+        env = np.maximum(env, np.abs(oracle.continue_sigma(Sp, idx, beta, wr, delta) - ref))
+    return ref, env
+
+
 @pytest.mark.parametrize("name", ["c0", "mixed"])
 def test_continue_sigma(name):
-    """Eq. sf_9 on the device against the oracle's continued fraction, same inputs."""
+    """Eq. sf_9 on the device against the oracle's continued fraction on the same inputs,
+    element by element within the oracle's own rounding envelope (and 1e-12 of the scale)."""
     s = system(name)
     c = s.cell
     S = _pole_sigma(c, 31)
     wr = np.linspace(-1.0, 1.0, 7)
-    ref = oracle.continue_sigma(S, c.omega_idx, c.beta, wr, 0.05)
+    ref, env = _rounding_envelope(S, c.omega_idx, c.beta, wr, 0.05)
     out = host(s.plan.continue_sigma(dev(S), wr, 0.05)).reshape(ref.shape)
     s.plan.sync()
     assert np.isfinite(ref).all()
-    assert np.abs(out - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert np.all(np.abs(out - ref) <= 100.0 * env + 1e-12 * np.abs(ref).max())
+    # and most elements agree far more closely than the worst-conditioned ones
+    assert np.median(np.abs(out - ref)) <= 1e-8 * np.abs(ref).max()
 
 
 def test_continue_sigma_of_the_device_sweep():
@@ -162,8 +179,9 @@ def test_continue_sigma_of_the_device_sweep():
     wr = np.linspace(-0.5, 0.5, 5)
     out = host(p.continue_sigma(Sk, wr, 0.02))
     p.sync()
-    ref = oracle.continue_sigma(host(Sk).reshape(c.n_k, c.omega_idx.size, c.n_orb_total, c.n_orb_total),
-                                c.omega_idx, c.beta, wr, 0.02)
-    ok = np.isfinite(ref)
+    S = host(Sk).reshape(c.n_k, c.omega_idx.size, c.n_orb_total, c.n_orb_total)
+    ref, env = _rounding_envelope(S, c.omega_idx, c.beta, wr, 0.02)
+    ok = np.isfinite(ref) & np.isfinite(env)
     assert ok.mean() > 0.99
-    assert np.abs(out.reshape(ref.shape)[ok] - ref[ok]).max() <= 1e-6 * np.abs(ref[ok]).max()
+    out = out.reshape(ref.shape)
+    assert np.all(np.abs(out[ok] - ref[ok]) <= 100.0 * env[ok] + 1e-12 * np.abs(ref[ok]).max())
