@@ -331,6 +331,16 @@ gw_status gw_qp_energies(gw_plan_t plan, const void* H_k, const void* Sigx_k, co
 gw_status gw_continue_sigma(gw_plan_t plan, const void* Sig_k_iw, int n_real, const double* w_real, double delta,
                             void* Sig_k_w, void* stream);
 
+/* Eqs. sf_1 and sf_7: the k-resolved spectral function A(k, w) = -(1/pi) Im Tr G^R(k, w) with
+ *   G^R = [(w + i delta + mu) I - H(k) - Sigma_x(k) - Sigma_c(k, w)]^{-1}
+ * (Eq. sf_7 in the band states of H + Sigma_x; the trace is basis independent), FP64
+ * inverses on the device.  Sig_k_w: device [N_k][n_real][N][N], e.g. from
+ * gw_continue_sigma with the same w_real and delta, or NULL; H_k, Sigx_k as for
+ * gw_dyson_green_tau; w_real: HOST [n_real] (from mu); delta > 0; A_kw: device double
+ * [N_k][n_real].  Allocates N_k n_real N^2 complex values of scratch on first use (kept). */
+gw_status gw_spectral_function(gw_plan_t plan, const void* H_k, const void* Sigx_k, const void* Sig_k_w, int n_real,
+                               const double* w_real, double delta, double mu, void* A_kw, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,7 @@ Every function follows one statement of the paper, cited in its docstring:
 * Eq. sf_9, the continued fraction through Sigma on the stored Matsubara grid
   (analytic continuation to w + i delta) -> ``continued_fraction_coefficients``,
   ``continued_fraction_value``, ``continue_sigma``
+* Eqs. sf_1 and sf_7, the spectral function from the retarded G -> ``spectral_function``
 
 Readings where the paper is silent or garbled (each listed in the design notes):
 P(x, x'; tau) = -s G(x, x'; tau) G(x', x; beta - tau) and G(x', x) = G(x, x')^*;
@@ -76,6 +77,7 @@ __all__ = [
     "continued_fraction_coefficients",
     "continued_fraction_value",
     "continue_sigma",
+    "spectral_function",
     "OracleSystem",
 ]
 
@@ -582,6 +584,22 @@ def continue_sigma(Sig_k_iw: np.ndarray, omega_idx, beta: float, w_real, delta: 
     for k in range(Sig_k_iw.shape[0]):
         a = continued_fraction_coefficients(z, Sig_k_iw[k, pos])
         out[k] = continued_fraction_value(a, z, w)
+    return out
+
+
+def spectral_function(H_k: np.ndarray, Sigx_k: np.ndarray, Sig_k_w, mu: float, w_real, delta: float) -> np.ndarray:
+    """Eq. sf_1 with the retarded Green function of Eq. sf_7: A(k, w) = -(1/pi) Im Tr G^R(k, w),
+    G^R = [(w + i delta + mu) I - H - Sigma_x - Sigma_c^R(w)]^{-1}.  Eq. sf_7 writes it in the
+    band states of H + Sigma_x (its eigenvalues on the diagonal); the trace is the same in
+    any basis.  Sig_k_w: [N_k][n_w][N][N] continued Sigma_c (or None); returns [N_k][n_w]."""
+    nk, N = H_k.shape[0], H_k.shape[1]
+    w = np.asarray(w_real, dtype=np.float64)
+    I = np.eye(N)
+    out = np.empty((nk, len(w)))
+    for k in range(nk):
+        for r, x in enumerate(w):
+            S = Sigx_k[k] + (Sig_k_w[k, r] if Sig_k_w is not None else 0.0)
+            out[k, r] = -np.trace(np.linalg.inv((x + 1j * delta + mu) * I - H_k[k] - S)).imag / np.pi
     return out
 
 

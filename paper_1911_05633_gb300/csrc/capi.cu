@@ -962,6 +962,21 @@ gw_status gw_continue_sigma(gw_plan_t p, const void* Sig_k_iw, int n_real, const
                             S(stream));
 }
 
+gw_status gw_spectral_function(gw_plan_t p, const void* H_k, const void* Sigx_k, const void* Sig_k_w, int n_real,
+                               const double* w_real, double delta, double mu, void* A_kw, void* stream) {
+  gw_status st = need_device(p);
+  if (st != GW_OK) return st;
+  if (!H_k || !A_kw || !w_real || n_real < 1 || !(delta > 0.0) || !std::isfinite(mu)) {
+    set_last_error("bad argument");
+    return GW_ERR_ARG;
+  }
+  DeviceGuard guard(p->device);
+  gw::ActiveTimer at_(&p->timer);
+  if ((st = gw::dyson_init(p->dyson, p->h)) != GW_OK) return st;
+  return gw::spectral_function(p->dyson, p->h, (const double2*)H_k, (const double2*)Sigx_k, (const double2*)Sig_k_w,
+                               n_real, w_real, delta, mu, (double*)A_kw, p->d_status, S(stream));
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,8 @@ struct DysonPlan {
   double2* ainv = nullptr;  // [n_k][N][N] scratch of the quasiparticle energies
   void* cont = nullptr;      // small tables of the continued fraction
   size_t cont_bytes = 0;
+  void* spec = nullptr;      // matrices, pivots and frequencies of the spectral function
+  size_t spec_bytes = 0;
   size_t bytes = 0;
 };
 
@@ -47,5 +49,11 @@ gw_status qp_energies(const HostPlan& h, const double2* H, const double2* Sigx, 
 constexpr int kContMax = 64;
 gw_status continue_sigma(DysonPlan& d, const HostPlan& h, const double2* S, int n_real, const double* w_real_host,
                          double delta, double2* out, cudaStream_t st);
+
+// Eqs. sf_1, sf_7: A [n_k][n_real] = -(1/pi) Im Tr [(w + i delta + mu) - H - Sigma_x - Sigma_c(w)]^{-1}
+// (kernels_cont.cu); Sigc_w [n_k][n_real][N][N] or null; w_real on the host.
+gw_status spectral_function(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx,
+                            const double2* Sigc_w, int n_real, const double* w_real_host, double delta, double mu,
+                            double* A, int* d_status, cudaStream_t st);
 
 }  // namespace gw

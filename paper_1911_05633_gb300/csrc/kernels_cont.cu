@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "dyson.h"
+#include "kernels.h"
 #include "ktimer.h"
 
 namespace gw {
@@ -57,7 +58,93 @@ __global__ void k_continue_sigma(const double2* __restrict__ S, const int* __res
   }
 }
 
+// [(w_r + i delta + mu) I - H(k) - Sigma_x(k) - Sigma_c(k, w_r)] for block b = k n_real + r.
+__global__ void k_retarded_build(const double2* __restrict__ H, const double2* __restrict__ Sx,
+                                 const double2* __restrict__ Sc, const double* __restrict__ wr, double delta,
+                                 double mu, int N, int n_real, double2* __restrict__ M) {
+  const long long b = blockIdx.x;
+  const long long k = b / n_real;
+  const int r = (int)(b - k * n_real);
+  const long long NN = (long long)N * N;
+  for (long long x = threadIdx.x; x < NN; x += blockDim.x) {
+    const double2 h = H[k * NN + x];
+    double re = -h.x, im = -h.y;
+    if (Sx) {
+      const double2 s = Sx[k * NN + x];
+      re -= s.x;
+      im -= s.y;
+    }
+    if (Sc) {
+      const double2 c = Sc[b * NN + x];
+      re -= c.x;
+      im -= c.y;
+    }
+    if (x / N == x % N) {
+      re += wr[r] + mu;
+      im += delta;
+    }
+    M[b * NN + x] = make_double2(re, im);
+  }
+}
+
+// A[b] = -(1/pi) Im Tr M_b^{-1}, one warp per block b.
+__global__ void k_trace_spectral(const double2* __restrict__ G, int N, long long n_b, double* __restrict__ A) {
+  const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= n_b) return;
+  const int lane = threadIdx.x & 31;
+  const long long NN = (long long)N * N;
+  double t = 0.0;
+  for (int i = lane; i < N; i += 32) t += G[b * NN + (long long)i * N + i].y;
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) A[b] = -t / M_PI;
+}
+
 }  // namespace
+
+gw_status spectral_function(DysonPlan& d, const HostPlan& h, const double2* H, const double2* Sigx,
+                            const double2* Sigc_w, int n_real, const double* w_real_host, double delta, double mu,
+                            double* A, int* d_status, cudaStream_t st) {
+  const int N = h.n_orb_total();
+  const long long nb = (long long)h.n_k * n_real, NN = (long long)N * N;
+  const size_t need = (size_t)nb * NN * sizeof(double2) + (size_t)nb * N * sizeof(int) + (size_t)n_real * sizeof(double) + 256;
+  if (need > d.spec_bytes) {
+    if (d.spec) cudaFree(d.spec);
+    d.spec = nullptr;
+    d.spec_bytes = 0;
+    if (cudaMalloc(&d.spec, need) != cudaSuccess) {
+      set_last_error("spectral function: scratch allocation failed");
+      return GW_ERR_OOM;
+    }
+    d.spec_bytes = need;
+  }
+  double2* M = static_cast<double2*>(d.spec);
+  int* perm = reinterpret_cast<int*>(M + nb * NN);
+  double* d_wr = reinterpret_cast<double*>(perm + nb * N + (((nb * N) & 1) ? 1 : 0));
+  cudaError_t e = cudaMemcpyAsync(d_wr, w_real_host, n_real * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // w_real is the caller's host memory
+  if (e != cudaSuccess) {
+    set_last_error(std::string("spectral function: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  {
+    TimedLaunch tl_("k_retarded_build", st);
+    k_retarded_build<<<(unsigned)nb, 256, 0, st>>>(H, Sigx, Sigc_w, d_wr, delta, mu, N, n_real, M);
+  }
+  {
+    TimedLaunch tl_("k_gj_inverse", st);
+    k_gj_inverse<<<(unsigned)nb, 512, 2 * (size_t)N * sizeof(double2), st>>>(M, perm, N, NN, d_status);
+  }
+  {
+    TimedLaunch tl_("k_trace_spectral", st);
+    k_trace_spectral<<<(unsigned)((nb + 7) / 8), 256, 0, st>>>(M, N, nb, A);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("spectral function: ") + cudaGetErrorString(e));
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
+}
 
 gw_status continue_sigma(DysonPlan& d, const HostPlan& h, const double2* S, int n_real, const double* w_real_host,
                          double delta, double2* out, cudaStream_t st) {

@@ -169,7 +169,7 @@ gw_status dyson_init(DysonPlan& d, const HostPlan& h) {
 }
 
 void dyson_free(DysonPlan& d) {
-  void* ptrs[] = {d.M, d.perm, d.w, d.tau, d.part, d.ainv, d.cont};
+  void* ptrs[] = {d.M, d.perm, d.w, d.tau, d.part, d.ainv, d.cont, d.spec};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   d = DysonPlan{};

@@ -30,7 +30,7 @@ _STRUCT = {"general": 0, "mirror": 1, "real": 2}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
-    "gw_dyson_green_tau", "gw_chemical_potential", "gw_qp_energies", "gw_continue_sigma",
+    "gw_dyson_green_tau", "gw_chemical_potential", "gw_qp_energies", "gw_continue_sigma", "gw_spectral_function",
     "gw_plan_transform_matrix", "gw_fourier_k_to_R", "gw_green_k_to_R", "gw_polarizability_tau",
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     lib.gw_dyson_green_tau.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     lib.gw_qp_energies.argtypes = [vp, vp, vp, vp, C.c_double, vp, vp]
     lib.gw_continue_sigma.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_double), C.c_double, vp, vp]
+    lib.gw_spectral_function.argtypes = [vp, vp, vp, vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_double,
+                                         vp, vp]
     lib.gw_chemical_potential.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.gw_plan_transform_matrix.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_double)]
@@ -397,6 +399,19 @@ class Plan:
                                            _ptr(wr, C.c_double), float(delta), C.c_void_p(Sig_k_w.data_ptr()),
                                            self._stream(stream)), "gw_continue_sigma")
         return Sig_k_w
+
+    def spectral_function(self, H_k, w_real, delta: float, mu: float, Sigx_k=None, Sig_k_w=None, stream=None):
+        """gw_spectral_function: A(k, w) [N_k][len(w_real)] (float64) from the retarded G."""
+        torch = self._torch()
+        nk, N = self.info["n_k"], self.dense_n("orb")
+        wr = np.ascontiguousarray(np.asarray(w_real, dtype=np.float64))
+        A = torch.empty(nk * len(wr), dtype=torch.float64, device=self._dev())
+        h = self._in(H_k, nk * N * N, "H_k")
+        x = self._in(Sigx_k, nk * N * N, "Sigx_k") if Sigx_k is not None else C.c_void_p(0)
+        c = self._in(Sig_k_w, nk * len(wr) * N * N, "Sig_k_w") if Sig_k_w is not None else C.c_void_p(0)
+        _check(self._lib.gw_spectral_function(self._h, h, x, c, len(wr), _ptr(wr, C.c_double), float(delta), float(mu),
+                                              C.c_void_p(A.data_ptr()), self._stream(stream)), "gw_spectral_function")
+        return A
 
     def sync(self, stream=None):
         _check(self._lib.gw_sync(self._h, self._stream(stream)), "gw_sync")

@@ -185,3 +185,24 @@ def test_continue_sigma_of_the_device_sweep():
     assert ok.mean() > 0.99
     out = out.reshape(ref.shape)
     assert np.all(np.abs(out[ok] - ref[ok]) <= 100.0 * env[ok] + 1e-12 * np.abs(ref[ok]).max())
+
+
+@pytest.mark.parametrize("name", ["c0", "mixed"])
+def test_spectral_function(name):
+    """Eqs. sf_1, sf_7 on the device: A(k, w) from a continued Sigma (the device's own,
+    handed to the oracle as well) and, without correlation, the Lorentzians of H + Sigma_x."""
+    s = system(name)
+    c = s.cell
+    nk, N = c.n_k, c.n_orb_total
+    Sx, _ = _sigmas(c, 3)
+    wr = np.linspace(-1.0, 1.0, 7)
+    Sw = s.plan.continue_sigma(dev(_pole_sigma(c, 31)), wr, 0.05)
+    A = host(s.plan.spectral_function(dev(c.H_k), wr, 0.05, c.mu, Sigx_k=dev(Sx), Sig_k_w=Sw))
+    s.plan.sync()
+    ref = oracle.spectral_function(c.H_k, Sx, host(Sw).reshape(nk, len(wr), N, N), c.mu, wr, 0.05)
+    assert np.abs(A.reshape(ref.shape) - ref).max() <= 1e-10 * np.abs(ref).max()
+    A0 = host(s.plan.spectral_function(dev(c.H_k), wr, 0.05, c.mu, Sigx_k=dev(Sx))).reshape(ref.shape)
+    s.plan.sync()
+    e = np.linalg.eigvalsh(c.H_k + Sx)
+    ref0 = (0.05 / np.pi / ((wr[None, :, None] + c.mu - e[:, None, :]) ** 2 + 0.05 ** 2)).sum(axis=2)
+    assert np.abs(A0 - ref0).max() <= 1e-10 * np.abs(ref0).max()

@@ -708,3 +708,18 @@ def test_continue_sigma_of_a_single_pole_self_energy(cell0):
     out = oracle.continue_sigma(S, idx[mask], c.beta, wr, 0.02)
     ref = A[:, None] / ((wr + 0.02j)[None, :, None, None] - P[:, None])
     assert np.abs(out - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_spectral_function_without_correlation_is_a_sum_of_lorentzians(cell0):
+    """Sigma_c = 0: A(k, w) = sum over the levels e of H + Sigma_x of
+    (delta/pi) / ((w + mu - e)^2 + delta^2), and it integrates to the number of levels."""
+    c = cell0
+    Sx = _static_hermitian(np.random.default_rng(14), c.n_k, c.n_orb_total)
+    w = np.linspace(-3.0, 3.0, 61)
+    A = oracle.spectral_function(c.H_k, Sx, None, c.mu, w, 0.05)
+    e = np.linalg.eigvalsh(c.H_k + Sx)
+    ref = (0.05 / np.pi / ((w[None, :, None] + c.mu - e[:, None, :]) ** 2 + 0.05 ** 2)).sum(axis=2)
+    assert np.abs(A - ref).max() < 1e-12 * np.abs(ref).max()
+    wd = np.linspace(-400.0, 400.0, 400001)
+    Ad = oracle.spectral_function(c.H_k[:1], Sx[:1], None, c.mu, wd, 0.05)
+    assert abs(np.trapezoid(Ad[0], wd) - c.n_orb_total) < 1e-3
