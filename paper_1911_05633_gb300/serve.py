@@ -91,6 +91,20 @@ class System:
         p.fourier_R_to_k("orb", 1, self.Sx_R, self.Sx_k, stream=s)
         p.dyson_green_tau(self.H_k, self.cell.mu, Sigx_k=self.Sx_k, Sig_k_iw=self.S_k, G_k_tau=self.G_k, stream=s)
 
+    def submit(self, keep_sigma: bool = False):
+        """Enqueue one iteration; returns (event, copy of Sigma(k, i w) or None).  The event
+        answers query() once the device has finished it."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.enqueue_iteration()
+            sig = self.S_k.clone() if keep_sigma else None
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        return ev, sig
+
+    def finish(self):
+        self.plan.sync(stream=self.stream.cuda_stream)
+
     def close(self):
         self.plan.close()
 
@@ -108,7 +122,6 @@ class Server:
     def run(self, arrivals: Sequence[tuple], keep_sigma: bool = False, poll_s: float = 20e-6) -> List[Request]:
         """Serve `arrivals` = [(seconds after start, system name), ...] (any order); returns
         the requests with their admission and completion times."""
-        import torch
         reqs = [Request(i, name, float(t)) for i, (t, name) in enumerate(sorted(arrivals, key=lambda a: a[0]))]
         pending = collections.deque(reqs)
         queue: collections.deque = collections.deque()
@@ -126,12 +139,7 @@ class Server:
                     continue
                 queue.remove(r)
                 r.admitted = time.perf_counter() - t0
-                with torch.cuda.stream(sysm.stream):
-                    sysm.enqueue_iteration()
-                    if keep_sigma:
-                        r.sigma_k = sysm.S_k.clone()
-                    r.event = torch.cuda.Event()
-                    r.event.record(sysm.stream)
+                r.event, r.sigma_k = sysm.submit(keep_sigma)
                 running[r.system] = r
                 used += sysm.footprint
             for name, r in list(running.items()):
@@ -144,7 +152,7 @@ class Server:
             elif running:
                 time.sleep(poll_s)
         for s in self.systems.values():
-            s.plan.sync(stream=s.stream.cuda_stream)
+            s.finish()
         return reqs
 
 

@@ -58,8 +58,10 @@ def test_memory_cap_bounds_what_runs_at_once(systems):
     for s in systems.values():
         s.reset()
     reqs = server.run([(0.0, n) for n in ("c0", "mixed", "c1_cut5", "c0", "mixed", "c1_cut5")])
+    # footprint only grows at admissions: at each one, what runs then fits the cap
     for r in reqs:
-        during = [q for q in reqs if q is not r and q.admitted < r.done and r.admitted < q.done]
-        assert sum(systems[q.system].footprint for q in during) + systems[r.system].footprint <= cap
+        t = r.admitted
+        running = [q for q in reqs if q.admitted <= t < q.done]
+        assert sum(systems[q.system].footprint for q in running) <= cap
         if r.system == big:
-            assert not during
+            assert not [q for q in reqs if q is not r and q.admitted < r.done and r.admitted < q.done]
