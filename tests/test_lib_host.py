@@ -204,3 +204,32 @@ def test_far_basis_rejects_bad_sizes(gwlib):
     for bad in ([0], [9]):  # n_prod = 8
         with pytest.raises(gw.GwError):
             gw.Plan.from_cell(cell, host_only=True, r_b=4.0, n_prod_far=bad)
+
+
+def test_every_compute_call_refuses_a_host_only_plan(gwlib):
+    """GW_ERR_NO_DEVICE (9) from each device entry point of a host-only plan, before any
+    pointer is touched (the pointers given here are not valid memory)."""
+    from paper_1911_05633_gb300 import gw
+    p = gw.Plan.from_cell(synth.make_config(0), host_only=True)
+    lib = gw.load_library()
+    h, q = p._h, ctypes.c_void_p(16)
+    d = ctypes.c_double(0.0)
+    w = (ctypes.c_double * 2)(0.0, 0.1)
+    calls = {
+        "gw_fourier_k_to_R": lambda: lib.gw_fourier_k_to_R(h, 1, 1, q, q, None),
+        "gw_polarizability_tau": lambda: lib.gw_polarizability_tau(h, q, q, 0, None),
+        "gw_transform_tau_iw": lambda: lib.gw_transform_tau_iw(h, 0, 0, 0, q, q, None),
+        "gw_screened_W_iw": lambda: lib.gw_screened_W_iw(h, q, q, q, None),
+        "gw_screened_W_iw_noalloc": lambda: lib.gw_screened_W_iw_noalloc(h, q, q, q, None),
+        "gw_self_energy_tau": lambda: lib.gw_self_energy_tau(h, q, q, None, q, None, 0, None),
+        "gw_fourier_R_to_k": lambda: lib.gw_fourier_R_to_k(h, 0, 1, q, q, None),
+        "gw_dyson_green_tau": lambda: lib.gw_dyson_green_tau(h, q, None, None, 0.0, q, None),
+        "gw_chemical_potential": lambda: lib.gw_chemical_potential(h, q, None, None, 8.0, -1.0, 1.0, 1e-9,
+                                                                   ctypes.byref(d), None, None),
+        "gw_qp_energies": lambda: lib.gw_qp_energies(h, q, None, None, 0.0, q, None),
+        "gw_continue_sigma": lambda: lib.gw_continue_sigma(h, q, 2, w, 0.01, q, None),
+        "gw_spectral_function": lambda: lib.gw_spectral_function(h, q, None, None, 2, w, 0.01, 0.0, q, None),
+        "gw_sync": lambda: lib.gw_sync(h, None),
+    }
+    for name, call in calls.items():
+        assert call() == 9, name
