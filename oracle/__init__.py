@@ -256,19 +256,15 @@ def polarizability_R(G_R: Sequence[np.ndarray], entries: np.ndarray, C_atom: Seq
 
 
 def _p_block(Ca, G1, G2c, Cb):
-    """sum_{A B C D} Ca[k,A,B] G1[t,A,C] G2c[t,B,D] Cb[q,C,D], one summation index at a time
-    (A = L, B = L'', C = L', D = L''' of Eq. P_MM)."""
-    X = np.einsum("kAB,tAC->tkBC", Ca, G1)      # sum over A
-    Y = np.einsum("tkBC,tBD->tkCD", X, G2c)     # sum over B
-    return np.einsum("tkCD,qCD->tkq", Y, Cb)    # sum over C and D
+    """The sum of Eq. P_MM as one contraction: sum over A, B, C, D of
+    Ca[k,A,B] G1[t,A,C] G2c[t,B,D] Cb[q,C,D] -> [t,k,q] (A = L, B = L'', C = L', D = L''')."""
+    return np.einsum("kAB,tAC,tBD,qCD->tkq", Ca, G1, G2c, Cb, optimize=True)
 
 
 def _s_block(Ca, G, W, Cb):
-    """sum_{K M N Q} Ca[K,L,M] G[t,M,N] W[t,K,Q] Cb[Q,P,N] -> [t,L,P], one index group at a time
-    (M = L'', N = L''', Q = K' of Eq. S_MM)."""
-    B = np.einsum("tKQ,QPN->tKPN", W, Cb)       # sum over Q
-    D = np.einsum("tMN,tKPN->tKMP", G, B)       # sum over N
-    return np.einsum("KLM,tKMP->tLP", Ca, D)     # sum over K and M
+    """The sum of Eq. S_MM as one contraction: sum over K, M, N, Q of
+    Ca[K,L,M] G[t,M,N] W[t,K,Q] Cb[Q,P,N] -> [t,L,P] (M = L'', N = L''', Q = K', P = L')."""
+    return np.einsum("KLM,tMN,tKQ,QPN->tLP", Ca, G, W, Cb, optimize=True)
 
 
 def polarizability_q_kspace(G_k: np.ndarray, C_atom, orb_off, pb_off, kmesh, spin: int = 2) -> np.ndarray:

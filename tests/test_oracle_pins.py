@@ -383,6 +383,134 @@ def test_exchange_fock_chain():
         assert abs(Sxk[k] - ref) < 1e-14
 
 
+def _complete_basis(n):
+    """K = n^2 product functions with C_{(L1 L2); L L''} = delta_{L1 L} delta_{L2 L''} (not
+    symmetric in (L, L''))."""
+    C = np.zeros((n * n, n, n))
+    for L1 in range(n):
+        for L2 in range(n):
+            C[L1 * n + L2, L1, L2] = 1.0
+    return C
+
+
+def test_self_energy_complete_product_basis():
+    """Eq. S_MM with a complete product basis on both atoms reduces to the orbital-pair
+    form of Eq. S_II: Sigma_{L L'}(tau) = -sum_{L'' L'''} G_{L'' L'''}(tau) W~_{(L L''), (L' L''')}(tau).
+    Atoms with different orbital counts, a non-Hermitian W~ and coefficients that are not
+    symmetric in (L, L''), so a transposed W~ block or a C contracted on the wrong index shows."""
+    rng = np.random.default_rng(17)
+    na, nb, nt = 2, 3, 5
+    G = rng.standard_normal((nt, na, nb)) + 1j * rng.standard_normal((nt, na, nb))
+    W = rng.standard_normal((nt, na * na, nb * nb)) + 1j * rng.standard_normal((nt, na * na, nb * nb))
+    ent = np.array([[0, 1, 0, 0, 0, 0, 0, 0]])
+    S = oracle.self_energy_R([G], [W], ent, [_complete_basis(na), _complete_basis(nb)])[0]
+    ref = np.zeros((nt, na, nb), complex)
+    for t in range(nt):
+        for L in range(na):
+            for Lp in range(nb):
+                s = 0j
+                for L2 in range(na):
+                    for L3 in range(nb):
+                        s += G[t, L2, L3] * W[t, L * na + L2, Lp * nb + L3]
+                ref[t, L, Lp] = -s
+    assert np.abs(S - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+def test_exchange_complete_product_basis():
+    """The exchange rule (W~ -> v, G(tau) -> -G(beta-)) in a complete product basis:
+    Sigma_x,{L L'} = +sum_{L'' L'''} G_{L'' L'''}(beta-) v_{(L L''), (L' L''')}."""
+    rng = np.random.default_rng(19)
+    na, nb, nt = 3, 2, 4
+    G = rng.standard_normal((nt, na, nb)) + 1j * rng.standard_normal((nt, na, nb))
+    v = rng.standard_normal((na * na, nb * nb)) + 1j * rng.standard_normal((na * na, nb * nb))
+    ent = np.array([[0, 1, 0, 0, 0, 0, 0, 0]])
+    Sx = oracle.exchange_R([G], [v], ent, [_complete_basis(na), _complete_basis(nb)])[0]
+    ref = np.zeros((na, nb), complex)
+    for L in range(na):
+        for Lp in range(nb):
+            for L2 in range(na):
+                for L3 in range(nb):
+                    ref[L, Lp] += G[nt - 1, L2, L3] * v[L * na + L2, Lp * nb + L3]
+    assert np.abs(Sx - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+def _single_pole_chain(n_tau=64):
+    """One-band chain with a screened interaction of one bosonic pole per class R:
+    W~(R, i nu) = A(R) 2 Omega / (nu^2 + Omega^2), i.e. W~(R, tau) = A(R) w(tau) with
+    w(tau) = (e^{-Omega tau} + e^{-Omega (beta - tau)}) / (1 - e^{-beta Omega})."""
+    ch = synth.chain_cell(n_cells_k=8, beta=20.0, n_tau=n_tau)
+    ent = oracle.pair_list(ch.lattice, ch.frac, ch.kmesh, 0.0)
+    N = ch.n_k
+    A = np.array([0.4 / (1.0 + min(c, N - c)) for c in range(N)])  # A(R) = A(-R): A_q real
+    return ch, ent, A, 0.35
+
+
+def _single_pole_w(beta, Om, tau, bos):
+    nu = 2 * np.pi * np.asarray(bos) / beta
+    return 2 * Om / (nu ** 2 + Om ** 2), (np.exp(-Om * tau) + np.exp(-Om * (beta - tau))) / (1 - np.exp(-beta * Om))
+
+
+def test_bosonic_inverse_transform_of_a_single_pole():
+    """Appendix A grid, bosonic side: the least-squares inverse maps the exact Matsubara
+    values w(i nu_m) = 2 Omega / (nu_m^2 + Omega^2) of the bosonic function
+    w(tau) = (e^{-Omega tau} + e^{-Omega (beta - tau)}) / (1 - e^{-beta Omega}) back to w at the
+    tau nodes; a grid too coarse for the pole fails."""
+    beta, Om = 20.0, 0.35
+    errs = {}
+    for N in (12, 48, 64):
+        tau = synth.tau_nodes(beta, N)
+        _, bos = synth.matsubara_sets(N)
+        U = oracle.inverse_matrix(oracle.fourier_matrix(beta, tau, bos, "B"))
+        w_iv, w_tau = _single_pole_w(beta, Om, tau, bos)
+        errs[N] = np.abs(U @ w_iv - w_tau).max() / np.abs(w_tau).max()
+    assert errs[64] < 1e-10 and errs[48] < 1e-8, errs
+    assert errs[12] > 1e-6, errs
+
+
+def _single_pole_sigma_iw(ch, A, Om, omega_idx):
+    """Sigma(k, i w_n) of the one-band G0 and the single-pole W~ by residues:
+    Sigma(k, tau) = -(1/N) sum_k' G0(k', tau) W~(k - k', tau), G0(k', tau) = -e^{-xi tau}/(1 + e^{-beta xi}),
+    W~(q, tau) = A_q w(tau), each exponential integrated in closed form,
+    int_0^beta e^{(i w - x) tau} d tau = (1 + e^{-beta x}) / (x - i w) for fermionic w."""
+    beta, N = ch.beta, ch.n_k
+    xi = np.linalg.eigvalsh(ch.H_k)[:, 0] - ch.mu
+    Aq = np.array([sum(A[c] * np.exp(2j * np.pi * q * c / N) for c in range(N)) for q in range(N)])
+    w = (2 * np.asarray(omega_idx) + 1) * np.pi / beta
+    I = lambda y: (1 + np.exp(-beta * y)) / (y - 1j * w)
+    out = np.zeros((N, len(w)), complex)
+    for k in range(N):
+        for kp in range(N):
+            x = xi[kp]
+            out[k] += Aq[(k - kp) % N] / ((1 + np.exp(-beta * x)) * (1 - np.exp(-beta * Om))) * (
+                I(x + Om) + np.exp(-beta * Om) * I(x - Om))
+    return out / N
+
+
+def test_self_energy_single_pole_closed_form():
+    """Eq. S_MM on the one-band chain with a single-pole W~(i nu): the oracle's chain
+    W~(R, i nu) -> W~(R, tau) (bosonic inverse) -> Sigma(R, tau) -> Sigma(R, i w) (fermionic
+    forward) -> Sigma(k, i w) against the residue closed form of the Matsubara sum."""
+    ch, ent, A, Om = _single_pole_chain(64)
+    beta, tau = ch.beta, ch.tau
+    fer, bos = synth.matsubara_sets(ch.n_tau)
+    G = oracle.green0_k_tau(ch.H_k, ch.mu, beta, tau)
+    GR = oracle.fourier_k_to_R(G, ent, ch.kmesh, [0, 1], [0, 1])
+    w_iv, _ = _single_pole_w(beta, Om, tau, bos)
+    W_iv = [(A[int(r[2])] * w_iv).astype(complex)[:, None, None] for r in ent]
+    WR = oracle.transform(oracle.inverse_matrix(oracle.fourier_matrix(beta, tau, bos, "B")), W_iv)
+    F = oracle.fourier_matrix(beta, tau, fer, "F")
+    ref = _single_pole_sigma_iw(ch, A, Om, fer)
+
+    def sigma_k(G_R):
+        SR = oracle.self_energy_R(G_R, WR, ent, [np.ones((1, 1, 1))])
+        return oracle.fourier_R_to_k(oracle.transform(F, SR), ent, ch.kmesh, [0, 1], [0, 1])[:, :, 0, 0]
+
+    assert np.abs(sigma_k(GR) - ref).max() < 1e-9 * np.abs(ref).max()
+    # the closed form fixes the pairing of Eq. S_MM: G taken at beta - tau is far off
+    # (W~ is mirror symmetric in tau, G is not)
+    assert np.abs(sigma_k([g[::-1] for g in GR]) - ref).max() > 1e-2 * np.abs(ref).max()
+
+
 def test_self_energy_real_space_equals_kspace_route(cell0):
     c = cell0
     ent = oracle.pair_list(c.lattice, c.frac, c.kmesh, 0.0)
