@@ -255,16 +255,24 @@ def polarizability_R(G_R: Sequence[np.ndarray], entries: np.ndarray, C_atom: Seq
     return out
 
 
+def _contract(spec, *ops):
+    """np.einsum of the whole sum, with the pairwise order that NumPy's own path search
+    picks when intermediates may be as large as 2^27 elements (its default limit, the size
+    of the largest operand, would leave a loop over all indices at once)."""
+    path = np.einsum_path(spec, *ops, optimize=("greedy", 2 ** 27))[0]
+    return np.einsum(spec, *ops, optimize=path)
+
+
 def _p_block(Ca, G1, G2c, Cb):
     """The sum of Eq. P_MM as one contraction: sum over A, B, C, D of
     Ca[k,A,B] G1[t,A,C] G2c[t,B,D] Cb[q,C,D] -> [t,k,q] (A = L, B = L'', C = L', D = L''')."""
-    return np.einsum("kAB,tAC,tBD,qCD->tkq", Ca, G1, G2c, Cb, optimize=True)
+    return _contract("kAB,tAC,tBD,qCD->tkq", Ca, G1, G2c, Cb)
 
 
 def _s_block(Ca, G, W, Cb):
     """The sum of Eq. S_MM as one contraction: sum over K, M, N, Q of
     Ca[K,L,M] G[t,M,N] W[t,K,Q] Cb[Q,P,N] -> [t,L,P] (M = L'', N = L''', Q = K', P = L')."""
-    return np.einsum("KLM,tMN,tKQ,QPN->tLP", Ca, G, W, Cb, optimize=True)
+    return _contract("KLM,tMN,tKQ,QPN->tLP", Ca, G, W, Cb)
 
 
 def polarizability_q_kspace(G_k: np.ndarray, C_atom, orb_off, pb_off, kmesh, spin: int = 2) -> np.ndarray:
