@@ -169,6 +169,32 @@ def test_continue_sigma(name):
     assert np.median(np.abs(out - ref)) <= 1e-8 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("name", ["c0", "mixed"])
+def test_continue_sigma_well_conditioned(name):
+    """Eq. sf_9 where the continuation is well conditioned: two poles per element at least
+    0.5 Ha below the real axis (a rational function the fraction through the stored points
+    reproduces exactly).  Every element, no exclusions, against the oracle and against the
+    pole sum itself at a fixed 1e-9 of the scale (the oracle's own rounding envelope here
+    is ~1e-13 of the scale)."""
+    s = system(name)
+    c = s.cell
+    nk, N = c.n_k, c.n_orb_total
+    rng = np.random.default_rng(41)
+    A = rng.uniform(0.05, 0.5, (2, nk, N, N))
+    P = rng.uniform(-1.5, 1.5, (2, nk, N, N)) - 1j * rng.uniform(0.5, 1.0, (2, nk, N, N))
+    z = 1j * (2 * c.omega_idx + 1) * np.pi / c.beta
+    S = (A[:, :, None] / (z[None, None, :, None, None] - P[:, :, None])).sum(axis=0)
+    wr = np.linspace(-1.0, 1.0, 7)
+    ref = oracle.continue_sigma(S, c.omega_idx, c.beta, wr, 0.05)
+    exact = (A[:, :, None] / ((wr + 0.05j)[None, None, :, None, None] - P[:, :, None])).sum(axis=0)
+    out = host(s.plan.continue_sigma(dev(S), wr, 0.05)).reshape(ref.shape)
+    s.plan.sync()
+    scale = np.abs(exact).max()
+    assert np.isfinite(out).all()
+    assert np.abs(out - ref).max() <= 1e-9 * scale
+    assert np.abs(out - exact).max() <= 1e-9 * scale
+
+
 def test_continue_sigma_of_the_device_sweep():
     s = system("c0")
     p, c = s.plan, s.cell

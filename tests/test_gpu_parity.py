@@ -47,6 +47,24 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def rel_blocks(a, b, off, n_slices, floor=1e-6):
+    """Largest relative error over the (entry, slice) blocks of an entry-layout buffer: each
+    block's error against its own norm, so that a wrong block of small magnitude (a far entry,
+    a distant pair, the middle of the tau grid) cannot hide under the global norm.
+    floor = x: blocks smaller than x times the largest block are measured against that floor
+    (stages computed block by block from exact inputs, whose rounding is relative per block);
+    floor = "rms": against the root-mean-square block norm (stages downstream of the W solve,
+    whose rounding is relative to the whole dense matrix of each (q, nu), not to each block)."""
+    blocks = []
+    for e in range(len(off) - 1):
+        A = a[n_slices * off[e]: n_slices * off[e + 1]].reshape(n_slices, -1)
+        B = b[n_slices * off[e]: n_slices * off[e + 1]].reshape(n_slices, -1)
+        blocks.append((np.linalg.norm(A - B, axis=1), np.linalg.norm(B, axis=1)))
+    nbs = np.concatenate([nb for _, nb in blocks])
+    ref = float(np.sqrt(np.mean(nbs ** 2))) if floor == "rms" else floor * float(nbs.max())
+    return max(float((d / np.maximum(nb, ref)).max()) for d, nb in blocks)
+
+
 class Sys:
     """One synthetic system: the plan, the oracle and the seeded inputs."""
 
@@ -138,6 +156,7 @@ def test_polarizability(name):
     ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
     P = host(s.plan.polarizability_tau(dev(pack(s.G_R()))))
     assert rel(P, pack(ref)) < TOL
+    assert rel_blocks(P, pack(ref), s.plan.off_pb, s.nt) < TOL
 
 
 @pytest.mark.parametrize("name", SMALL + FAR + ["c1"])
@@ -233,6 +252,8 @@ def test_self_energy_and_exchange(name):
     Sig, Sigx = s.plan.self_energy_tau(dev(pack(s.G_R())), dev(pack(WR)), v_R=dev(pack(vR)))
     assert rel(host(Sig), pack(ref)) < TOL
     assert rel(host(Sigx), pack(refx)) < TOL
+    assert rel_blocks(host(Sig), pack(ref), s.plan.off_orb, s.nt) < TOL
+    assert rel_blocks(host(Sigx), pack(refx), s.plan.off_orb, 1) < TOL
 
 
 @pytest.mark.parametrize("name", SMALL + FAR + ["c1"])
@@ -284,6 +305,14 @@ def test_whole_sweep(name):
     assert rel(host(Sigx), pack(r["Sigx_R"])) < TOL
     assert rel(host(Sk), r["Sig_k"].reshape(-1)) < TOL
     assert rel(host(Sxk), r["Sigx_k"].reshape(-1)) < TOL
+    # block by block for every entry-layout stage (the far entries and the middle of the tau grid included)
+    nt, nn, nw = s.nt, s.cell.nu_idx.size, s.cell.omega_idx.size
+    oo, op = p.off_orb, p.off_pb
+    for got, ref, off, ns, fl in ((GR, r["G_R"], oo, nt, 1e-6), (PR, r["P_R"], op, nt, 1e-6),
+                                  (Piw, r["P_iw"], op, nn, "rms"), (Wiw, r["Wt_iw"], op, nn, "rms"),
+                                  (WR, r["Wt_R"], op, nt, "rms"), (Sig, r["Sig_R"], oo, nt, "rms"),
+                                  (Sigx, r["Sigx_R"], oo, 1, 1e-6)):
+        assert rel_blocks(host(got), pack(ref), off, ns, fl) < TOL
 
 
 def test_largest_blocks():
