@@ -1,16 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the real-space / imaginary-time GW sweep on one GB300 per rank.
 
-One step = one pass of every row of the sweep over the 8-atom diamond-like
-workload (n = 9 orbitals, K = 48 product functions per atom, 4x4x4 k-mesh,
-beta = 1000, 48 tau nodes, 12-bohr cutoff: 376 pair entries):
-  G(k,tau) -> G(R,tau) -> P(R,tau) -> P(R,i nu) -> [P(q) -> W solve -> W~(R)] (i nu)
-  -> W~(R,tau) -> Sigma(R,tau) + Sigma_x -> Sigma(R,i omega) -> Sigma(k,i omega).
-Inputs G(k,tau) and v(q) are resident in HBM when the timed region starts.
+One step = one pass of the P + Sigma rows of the sweep over the 72-atom diamond-like
+supercell (3x3x1 of the 8-atom cell; n = 9 orbitals, K = 64 product functions per
+atom, 2x2x2 k-mesh, beta = 1000, 64 tau nodes, 12-bohr cutoff: 3312 pair entries):
+  G(k,tau) -> G(R,tau) -> P(R,tau) -> P(R,i nu)            (rows a1, a2, a3)
+  W~(R,i nu) -> W~(R,tau) -> Sigma(R,tau) + Sigma_x        (rows a6, a7)
+  -> Sigma(R,i omega) -> Sigma(k,i omega), Sigma_x(k)      (row a8)
+The W solve between P(R,i nu) and W~(R,i nu) (Eq. W_1, with the dense momentum-space
+halves of rows a4 and a6 that stream inside it) is timed apart, as the metric states;
+at this size (N_PB = 4608) W~(R,i nu) and v(R) are seeded inputs of the plan's shapes.
+Inputs G(k,tau), W~(R,i nu) and v(R) are resident in HBM when the timed region starts.
 
-`value` is sweeps per second summed over ranks (weak scaling: each rank runs its
-own replica; the sweep does not shard).  `--impl reference` times the FP64 CPU
-oracle on a bounded sample of the same workload on the host cores.
+`value` is P+Sigma sweeps per second in mixed precision (BF16x3 contractions with FP32
+accumulation, FP64-accurate transforms), summed over ranks (weak scaling: each rank
+runs its own replica; the sweep does not shard).  The FP64 path of the same rows is
+timed beside it (`fp64`), and the 8-atom workload's whole sweep with its W solve is
+kept as `full_sweep_8_atoms`.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -30,31 +37,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "P+Σ sweep time & TFLOP/s vs peak; serve p50/p99; mixed vs FP64 at 1e-6 rel err"
 UNIT = "sweep/s"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (used only if the live probe fails)
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), valid
-# only while the kernel's source file is unchanged since the capture.
+# DRAM traffic per launch of a kernel from an ncu capture (profiles/), valid only while
+# the kernel's source file is unchanged since the capture: bytes per unit there x units
+# in this launch.
 TRAFFIC = {
     # bench.py --small captures (56 matrices of N_PB = 384 per launch): DRAM read + write / 56
     "k_gj_inverse_f32": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
                          "bytes_per_unit": (66.10e6 + 254.12e6) / 56},
-    "k_ozaki_residual<second>": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
-                                 "bytes_per_unit": (536.13e6 + 59.19e6) / 56},
-    "k_refine_tc<final>": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
-                           "bytes_per_unit": (334.96e6 + 101.09e6) / 56},
 }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="precision of `value` (the other one is timed beside it)")
+    ap.add_argument("--config", type=int, default=2,
+                    help="2: P+Sigma rows of the 72-atom cell (default); 1: the 8-atom whole sweep with its W solve")
+    ap.add_argument("--atoms", type=int, default=72, help="configuration 2 series: 8, 16, 32, 48 or 72 atoms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 8-atom whole sweep and its error report")
     ap.add_argument("--no-dyson", action="store_true", help="skip the Eq. G_1 step timed after the sweep")
     ap.add_argument("--small", action="store_true", help="the small profiling case instead of the bench workload")
     ap.add_argument("--w-solver", default="auto", choices=["auto", "gauss_jordan"],
@@ -66,7 +73,7 @@ def parse():
     ap.add_argument("--n-prod-far", type=int, nargs="+", default=None,
                     help="product functions per species kept by pairs beyond sphere B")
     ap.add_argument("--serve", action="store_true",
-                    help="Poisson request stream of whole GW iterations on four small systems: p50/p99 latency")
+                    help="Poisson request stream of whole GW iterations: p50/p99 latency")
     ap.add_argument("--scaling", type=int, nargs="*", default=None,
                     help="time the P+Sigma rows (no W solve) of the 64-function diamond series at these atom "
                          "counts (default 8 16 32 48 72), FP64 and mixed; one JSON line")
@@ -112,13 +119,19 @@ def aggregate(step_ms: float, world: int):
 # workload and its algorithmic work
 # --------------------------------------------------------------------------------------
 
-def workload(cfg: int, small: bool = False, r_b: float = 0.0, n_prod_far=None):
-    """The bench workload, or with `small` the 8-atom cell on a 2x2x2 mesh with 12 tau
-    nodes and a 5-bohr cutoff (N_PB = 384, 64 W-solve matrices): a case small enough for
-    full ncu captures of single kernels.  r_b > 0: pairs beyond sphere B keep n_prod_far
-    product functions per species (the reduced basis of Sec. 2)."""
+def workload(cfg: int, small: bool = False, r_b: float = 0.0, n_prod_far=None, atoms: int = 72):
+    """The bench workload: configuration 2 (the diamond supercell series, 72 atoms by
+    default), configuration 1 (the 8-atom cell), or with `small` the 8-atom cell on a 2x2x2
+    mesh with 12 tau nodes and a 5-bohr cutoff (N_PB = 384, 64 W-solve matrices): a case
+    small enough for full ncu captures of single kernels.  r_b > 0: pairs beyond sphere B
+    keep n_prod_far product functions per species (the reduced basis of Sec. 2)."""
     import synth
-    cell = synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)) if small else synth.make_config(cfg)
+    if small:
+        cell = synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2))
+    elif cfg == 2:
+        cell = synth.make_config(2, atoms=atoms)
+    else:
+        cell = synth.make_config(cfg)
     if r_b > 0:
         synth.with_far_basis(cell, r_b, n_prod_far or [max(1, sp.n_prod // 4) for sp in cell.species])
     return cell
@@ -206,6 +219,77 @@ def stage_bc_flops(cell, entries, kdims) -> float:
         na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
         f += 2.0 * (2 * Ka * na * na * nb + 4 * Ka * na * nb * nb)
     return f * cell.n_tau
+
+
+def stage3_flops(cell, entries, kdims, row: str) -> float:
+    """Real flops of the dense stage of a contraction per tau node, summed over entries:
+    Y C^b of P or W~ C^b of Sigma, 2 x 2 K_a K_b n_b^2 per (entry, tau)."""
+    f = 0.0
+    for (a, b), (Ka, Kb) in zip(entries[:, :2], kdims):
+        nb = cell.n_orb_of(int(b))
+        f += 2.0 * 2 * Ka * Kb * nb * nb
+    return f
+
+
+def row_work(cell, entries, kdims, row: str, c_symmetric: int):
+    """Algorithmic work of one contraction row over one sweep: (real flops, DRAM bytes,
+    BF16x3 tensor flops of its dense stage, FP32 flops of its small stages).
+    P: the computed tau nodes (half of them, the mirrored ones written as conjugates, when C is
+    symmetric), reading G(tau) and G(beta - tau) once and writing every P(tau) slice.
+    Sigma: every tau node, reading G and W~ and writing Sigma (the one-slice exchange apart)."""
+    nt = cell.n_tau
+    ne = (nt + 1) // 2 if (row == "P" and c_symmetric) else nt
+    fl = contraction_flops(cell, entries, kdims) * ne / nt
+    dense = stage3_flops(cell, entries, kdims, row) * ne
+    small = fl - dense
+    byt = 0.0
+    for (a, b), (Ka, Kb) in zip(entries[:, :2], kdims):
+        na, nb = cell.n_orb_of(int(a)), cell.n_orb_of(int(b))
+        if row == "P":
+            byt += nt * 16.0 * (na * nb + Ka * Kb)
+        else:
+            byt += nt * 16.0 * (2 * na * nb + Ka * Kb)
+    return fl, byt, 6.0 * dense, small
+
+
+def contraction_roofline(kernel, ms_per_step, launches_per_step, work, peaks, fp32_peak, fp64_peak, mixed):
+    """Roofline of one contraction kernel from its live event times.  The floors: its
+    algorithmic DRAM bytes at the measured HBM peak, and its arithmetic at the peak of the
+    unit that runs it (mixed: BF16x3 tensor flops of the dense stage at the sustained BF16
+    peak, the small stages at the FP32 peak; FP64: all flops at the FP64 peak).  `bound` is
+    the largest floor; `achieved` is the algorithmic work of that bound per launch over the
+    mean launch time."""
+    fl, byt, tens, small = work
+    dur = ms_per_step * 1e-3 / launches_per_step
+    hbm = peaks.get("hbm_gbs")
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    floors = {"hbm": byt / launches_per_step / (hbm * 1e9) if hbm else 0.0}
+    if mixed:
+        floors["tensor"] = tens / launches_per_step / (bf16 * 1e12) if bf16 else 0.0
+        floors["alu"] = small / launches_per_step / (fp32_peak * 1e12) if fp32_peak else 0.0
+    else:
+        floors["alu"] = fl / launches_per_step / (fp64_peak * 1e12) if fp64_peak else 0.0
+    bound = max(floors, key=floors.get)
+    if bound == "hbm":
+        ach, peak, unit, src = byt / launches_per_step / dur / 1e9, hbm, "GB/s", "measured HBM copy (hbm_gbs)"
+    elif bound == "tensor":
+        ach, peak, unit = tens / launches_per_step / dur / 1e12, bf16, "TFLOP/s"
+        src = "measured cuBLAS BF16 sustained (bf16_tflops_sustained); achieved counts the BF16x3 products"
+    elif mixed:
+        ach, peak, unit = small / launches_per_step / dur / 1e12, fp32_peak, "TFLOP/s"
+        src = "FP32 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
+    else:
+        ach, peak, unit = fl / launches_per_step / dur / 1e12, fp64_peak, "TFLOP/s"
+        src = "FP64 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
+    return {"kernel": kernel, "bound": bound, "achieved": round(ach, 4), "peak": round(peak, 4) if peak else None,
+            "unit": unit, "frac": round(ach / peak, 4) if peak else None, "traffic": None, "peak_source": src,
+            "launch_ms": round(dur * 1e3, 4), "algorithmic_bytes_per_launch": byt / launches_per_step,
+            "algorithmic_flops_per_launch": fl / launches_per_step,
+            "algorithmic_tflops": round(fl / launches_per_step / dur / 1e12, 4),
+            "emulation": ({"bf16x3_tensor_flops_per_launch": tens / launches_per_step,
+                           "tensor_frac_of_bf16_sustained": round(tens / launches_per_step / dur / 1e12 / bf16, 4)
+                           if bf16 else None} if mixed else None),
+            "floors_ms": {k: round(v * 1e3, 4) for k, v in floors.items()}}
 
 
 def oz_nt(n_cols: int) -> int:
@@ -298,8 +382,267 @@ class Clocks:
 # our arm
 # --------------------------------------------------------------------------------------
 
+# --------------------------------------------------------------------------------------
+# our arm, main line: the P + Sigma rows of configuration 2
+# --------------------------------------------------------------------------------------
+
+class RowSweep:
+    """Device buffers and the ordered calls of the P + Sigma rows (the W solve apart):
+    G(k,tau) -> G(R,tau) -> P(R,tau) -> P(R,i nu); W~(R,i nu) -> W~(R,tau) -> Sigma(R,tau)
+    + Sigma_x -> Sigma(R,i w) -> Sigma(k,i w), Sigma_x(k)."""
+
+    STAGES = ["G_k_to_R", "P", "P_tau_to_nu", "W_nu_to_tau", "Sigma", "Sigma_tau_to_omega", "Sigma_R_to_k"]
+
+    def __init__(self, cell, device: int = 0, seed: int = 0):
+        import torch
+        from paper_1911_05633_gb300 import gw
+        self.torch = torch
+        self.cell = cell
+        self.prec = "mixed"
+        self.plan = gw.Plan.from_cell(cell, device=device)
+        p, inf = self.plan, self.plan.info
+        self.dev = torch.device("cuda", device)
+        z = lambda n: torch.empty(n, dtype=torch.complex128, device=self.dev)
+        nt, nn, nw, No, nk = inf["n_tau"], inf["n_nu"], inf["n_omega"], inf["n_orb_total"], inf["n_k"]
+        self.G_k = z(nk * nt * No * No)
+        self.G_R, self.P_R, self.P_iw = z(p.len("orb", nt)), z(p.len("pb", nt)), z(p.len("pb", nn))
+        self.W_iw, self.W_R, self.v_R = z(p.len("pb", nn)), z(p.len("pb", nt)), z(p.len("pb", 1))
+        self.S_R, self.Sx_R, self.S_iw = z(p.len("orb", nt)), z(p.len("orb", 1)), z(p.len("orb", nw))
+        self.S_k, self.Sx_k = z(nk * nw * No * No), z(nk * No * No)
+        # seeded stand-ins for the W solve's output (real: the plan's symmetric W mode) and v(R)
+        gen = torch.Generator(device=self.dev).manual_seed(seed)
+        self.W_iw.copy_(torch.randn(self.W_iw.numel(), dtype=torch.float64, device=self.dev, generator=gen))
+        self.v_R.copy_(torch.randn(self.v_R.numel(), dtype=torch.float64, device=self.dev, generator=gen))
+
+    def load_G(self, G_k_host):
+        self.G_k.copy_(self.torch.from_numpy(G_k_host.reshape(-1)))
+
+    def run(self, stream, events=None):
+        p, s = self.plan, stream.cuda_stream
+        inf = p.info
+        calls = [
+            lambda: p.green_k_to_R(self.G_k, self.G_R, stream=s),
+            lambda: p.polarizability_tau(self.G_R, self.P_R, precision=self.prec, stream=s),
+            lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s,
+                                       structure="mirror" if inf["c_symmetric"] else "general"),
+            lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s,
+                                       structure="real" if inf["w_symmetric"] else "general"),
+            lambda: p.self_energy_tau(self.G_R, self.W_R, v_R=self.v_R, Sig_R=self.S_R, Sigx_R=self.Sx_R,
+                                      precision=self.prec, stream=s),
+            lambda: p.transform_tau_iw("F", "tau_to_iw", "orb", self.S_R, self.S_iw, stream=s),
+            lambda: (p.fourier_R_to_k("orb", inf["n_omega"], self.S_iw, self.S_k, stream=s),
+                     p.fourier_R_to_k("orb", 1, self.Sx_R, self.Sx_k, stream=s)),
+        ]
+        for i, c in enumerate(calls):
+            if events is not None:
+                events[i][0].record(stream)
+            c()
+            if events is not None:
+                events[i][1].record(stream)
+
+
+def time_rows(sw, stream, flush, steps, warmup, clocks=None):
+    """Warm-up, then `steps` sweeps, each after an L2 flush, with a CUDA event pair around
+    every row on the launching stream and the library's event pair around every kernel.
+    Returns (ms per sweep, ms per row, {kernel: (total ms, launches)}, clocks)."""
+    torch = sw.torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            sw.run(stream)
+    sw.plan.sync(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    nst = len(sw.STAGES)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nst)] for _ in range(steps)]
+    sw.plan.timing_reset()
+    sw.plan.timing_enable(True)
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush_l2(flush)
+            sw.run(stream, ev[k])
+    sw.plan.sync(stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    kt = sw.plan.timing_read()
+    sw.plan.timing_enable(False)
+    stage_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nst)] for k in range(steps)])
+    return float(stage_ms.sum(axis=1).mean()), stage_ms.mean(axis=0), kt, clk
+
+
+def kernels_table(kt, steps):
+    tot = sum(v[0] for v in kt.values()) or 1.0
+    return {k: {"ms_per_step": round(v[0] / steps, 4), "launches_per_step": v[1] / steps, "share": round(v[0] / tot, 4)}
+            for k, v in sorted(kt.items(), key=lambda x: -x[1][0])}
+
+
+# the contraction kernels of rows a2 (P) and a7 (Sigma) by precision
+CONTRACTION_KERNELS = {
+    "k_polarizability_tc": ("P", True), "k_polarizability_f32": ("P", True),
+    "k_self_energy_tc": ("S", True), "k_self_energy_f32": ("S", True),
+    "k_contract_p_tc": ("P", True), "k_contract_s_tc": ("S", True),
+    "k_polarizability_fp64": ("P", False), "k_self_energy_fp64": ("S", False),
+}
+
+
+def dominant_contraction_roofline(kt, steps, cell, plan, peaks, fp32_peak, fp64_peak):
+    """The roofline of the contraction kernel with the most device time (rows a2, a7)."""
+    cands = {k: v for k, v in kt.items() if k in CONTRACTION_KERNELS}
+    if not cands:
+        return None
+    k = max(cands, key=lambda x: cands[x][0])
+    row, mixed = CONTRACTION_KERNELS[k]
+    ent, kd, inf = plan.entries, pb_dims(plan), plan.info
+    if mixed:
+        work = row_work(cell, ent, kd, row, inf["c_symmetric"])
+    else:  # the FP64 kernel does the small stages; its dense stage runs as digit GEMMs
+        w = kernel_work(k, cell, inf, ent, kd)
+        fl = w[1]
+        byt = row_work(cell, ent, kd, row, inf["c_symmetric"])[1]
+        work = (fl, byt, 0.0, fl)
+    ms, nl = cands[k]
+    roof = contraction_roofline(k, ms / steps, nl / steps, work, peaks, fp32_peak, fp64_peak, mixed)
+    roof["row"] = {"P": "a2 (Eq. P_MM)", "S": "a7 (Eq. S_MM)"}[row]
+    return roof
+
+
+def run_rows(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    cell = workload(2, False, args.r_b, args.n_prod_far, atoms=args.atoms)
+    sw = RowSweep(cell, device=local)
+    Gk = cell.green_k_tau()
+    sw.load_G(Gk)
+    stream = torch.cuda.Stream(device=local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=sw.dev)  # 256 MB > L2
+    try:
+        from paper_1911_05633_gb300 import gw
+        fp64_peak, fp32_peak = gw.fp_peak(local)
+    except Exception:
+        fp64_peak, fp32_peak = None, None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    res = {}
+    for prec in (other, args.precision):  # the headline precision last, under the clock sampler
+        sw.prec = prec
+        barrier(world)
+        clocks = Clocks(local) if prec == args.precision else None
+        ms, stage_ms, kt, clk = time_rows(sw, stream, flush, args.steps, args.warmup, clocks)
+        res[prec] = {"ms": ms, "stage_ms": stage_ms, "kt": kt, "clk": clk}
+    main_ = res[args.precision]
+    step_ms_max, value = aggregate(main_["ms"], world)
+    ent, inf, kd = sw.plan.entries, sw.plan.info, pb_dims(sw.plan)
+    wP = row_work(cell, ent, kd, "P", inf["c_symmetric"])
+    wS = row_work(cell, ent, kd, "S", inf["c_symmetric"])
+
+    def block(r, prec):
+        st = dict(zip(RowSweep.STAGES, r["stage_ms"]))
+        return {"value": round(world * 1000.0 / r["ms"], 6), "unit": UNIT, "ms_per_sweep": round(r["ms"], 4),
+                "stage_ms": {n: round(float(t), 4) for n, t in st.items()},
+                "contraction_tflops": {"P": round(wP[0] / (st["P"] * 1e-3) / 1e12, 4),
+                                       "Sigma": round(wS[0] / (st["Sigma"] * 1e-3) / 1e12, 4)},
+                "kernels": kernels_table(r["kt"], args.steps),
+                "roofline": dominant_contraction_roofline(r["kt"], args.steps, cell, sw.plan, peaks, fp32_peak,
+                                                          fp64_peak)}
+
+    b_main, b_other = block(main_, args.precision), block(res[other], other)
+    errs = rows_mixed_vs_fp64(sw, stream, cell)
+    e2e = None if args.no_e2e else run_e2e_rows(sw, Gk, stream, flush, args)
+    out = {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16x3-f32acc contractions + f64 transforms" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": rows_config(cell, len(ent), inf["n_pb_total"], args.precision, world),
+        "stage_ms": b_main["stage_ms"],
+        "contraction_tflops": b_main["contraction_tflops"],
+        "clocks": main_["clk"],
+        # the library's kernel launches in the timed region, counted by its event timer
+        "gpu_launches": int(sum(v[1] for v in main_["kt"].values())),
+        "roofline": b_main["roofline"],
+        "kernels": b_main["kernels"],
+        other: {**b_other, "speedup_of_" + args.precision: round(res[other]["ms"] / main_["ms"], 3)},
+        "mixed_vs_fp64": errs,
+        "fp64_peak_tflops_measured": fp64_peak, "fp32_peak_tflops_measured": fp32_peak,
+        "e2e": e2e,
+    }
+    del sw
+    torch.cuda.empty_cache()
+    return out, cell
+
+
+def rows_mixed_vs_fp64(sw, stream, cell):
+    """Relative Frobenius errors of the mixed rows against the FP64 rows of the same plan
+    and inputs (the FP64 rows equal the oracle to 1e-10 on sampled entries of this workload:
+    tests/test_gpu_parity.py::test_full_size_72_atoms_sampled): P(R, tau) and Sigma(R, tau),
+    Sigma(k, i w) on the same W~."""
+    torch = sw.torch
+    outs = {}
+    for prec in ("mixed", "fp64"):
+        sw.prec = prec
+        with torch.cuda.stream(stream):
+            sw.run(stream)
+        sw.plan.sync(stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        outs[prec] = {"P": sw.P_R.clone(), "Sigma": sw.S_R.clone(), "Sigma_k": sw.S_k.clone()}
+    sw.prec = "mixed"
+    rel = {k: float(f"{float(torch.linalg.vector_norm(outs['mixed'][k] - outs['fp64'][k]) / torch.linalg.vector_norm(outs['fp64'][k])):.3e}")
+           for k in ("P", "Sigma", "Sigma_k")}
+    del outs
+    torch.cuda.empty_cache()
+    return {**rel, "tolerance": 1e-6, "reference": "the FP64 GPU rows, same plan and inputs"}
+
+
+def run_e2e_rows(sw, Gk, stream, flush, args):
+    """The same rows through the C ABI with host buffers: per step, H2D of G(k,tau),
+    W~(R,i nu) and v(R) from pinned memory and D2H of Sigma(k,i w) and Sigma_x(k), inside
+    the timed region; the same steps and L2 flush as `value`."""
+    torch = sw.torch
+    Gk_h = torch.from_numpy(Gk.reshape(-1)).pin_memory()
+    W_h = sw.W_iw.cpu().pin_memory()
+    v_h = sw.v_R.cpu().pin_memory()
+    Sk_h = torch.empty(sw.S_k.numel(), dtype=torch.complex128).pin_memory()
+    Sxk_h = torch.empty(sw.Sx_k.numel(), dtype=torch.complex128).pin_memory()
+    sw.prec = args.precision
+
+    def step():
+        sw.G_k.copy_(Gk_h, non_blocking=True)
+        sw.W_iw.copy_(W_h, non_blocking=True)
+        sw.v_R.copy_(v_h, non_blocking=True)
+        sw.run(stream)
+        Sk_h.copy_(sw.S_k, non_blocking=True)
+        Sxk_h.copy_(sw.Sx_k, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush_l2(flush)
+            a.record(stream)
+            step()
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    return {"value": round(1000.0 / ms, 6), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int((Gk_h.numel() + W_h.numel() + v_h.numel()) * 16),
+            "d2h_bytes_per_step": int((Sk_h.numel() + Sxk_h.numel()) * 16), "steps": args.steps,
+            "l2": "256 MB buffer written before each step"}
+
+
+# --------------------------------------------------------------------------------------
+# the 8-atom workload's whole sweep (configuration 1, W solve included)
+# --------------------------------------------------------------------------------------
+
 class Sweep:
-    """Device buffers and the ordered calls of one sweep."""
+    """Device buffers and the ordered calls of one whole sweep, the W solve included."""
 
     STAGES = ["G_k_to_R", "P", "P_tau_to_nu", "W_solve", "W_nu_to_tau", "v_k_to_R", "Sigma", "Sigma_tau_to_omega",
               "Sigma_R_to_k"]
@@ -330,7 +673,6 @@ class Sweep:
         self.S_iw = z(p.len("orb", nw))
         self.S_k = z(inf["n_k"] * nw * No * No)
         self.Sx_k = z(inf["n_k"] * No * No)
-        self.launches_per_step = None
 
     def load_inputs(self, G_k_host, v_q_host):
         self.G_k.copy_(self.torch.from_numpy(G_k_host.reshape(-1)))
@@ -362,7 +704,6 @@ class Sweep:
                 events[i][1].record(stream)
 
 
-
 def traffic_of(kernel: str, units_per_launch: float):
     """DRAM bytes per launch of `kernel` from a committed ncu capture (bytes per unit
     there x units in this launch), or None when there is none or when the kernel's
@@ -380,139 +721,74 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def run_ours(args, rank, world, local):
+def dominant_kernel_roofline(kt, steps, cell, plan, peaks, fp32_peak, fp64_peak):
+    """The roofline of the kernel with the most device time in a whole sweep."""
+    if not kt:
+        return None
+    dom_k = max(kt, key=lambda k: kt[k][0])
+    ms_tot, nl = kt[dom_k]
+    w = kernel_work(dom_k, cell, plan.info, plan.entries, pb_dims(plan))
+    if w is None:
+        return {"kernel": dom_k, "bound": None}
+    bound, work, kind, units = w
+    per_launch = work * steps / nl
+    dur = ms_tot * 1e-3 / nl
+    if bound == "hbm":
+        ach, unit, peak = per_launch / dur / 1e9, "GB/s", peaks.get("hbm_gbs")
+    elif bound == "tensor":
+        ach, unit, peak = per_launch / dur / 1e12, "TFLOP/s", peaks.get("bf16_tflops_sustained")
+    else:
+        ach, unit = per_launch / dur / 1e12, "TFLOP/s"
+        peak = fp64_peak if kind == "fp64" else fp32_peak
+    return {"kernel": dom_k, "bound": bound, "achieved": round(ach, 4), "peak": round(peak, 4) if peak else None,
+            "unit": unit, "frac": round(ach / peak, 4) if peak else None,
+            "traffic": traffic_of(dom_k, units * steps / nl), "launch_ms": round(dur * 1e3, 4)}
+
+
+def run_full(args, local, with_errors: bool = True):
+    """The 8-atom workload's whole sweep (W solve included) in FP64 and in mixed precision,
+    and the mixed-vs-FP64 errors of P, Sigma and the quasiparticle energies."""
     import torch
     torch.cuda.set_device(local)
-    cell = workload(args.config, args.small, args.r_b, args.n_prod_far)
-    sw = Sweep(cell, args.precision, device=local, w_solver=args.w_solver, fp64_products=args.fp64_products)
+    cell = workload(1, args.small, args.r_b if args.config == 1 else 0.0, args.n_prod_far)
+    sw = Sweep(cell, "fp64", device=local, w_solver=args.w_solver, fp64_products=args.fp64_products)
     Gk = cell.green_k_tau()
     vq, _ = cell.coulomb()
     sw.load_inputs(Gk, vq)
     stream = torch.cuda.Stream(device=local)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=sw.dev)  # 256 MB > L2
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=sw.dev)
     try:
         from paper_1911_05633_gb300 import gw
         fp64_peak, fp32_peak = gw.fp_peak(local)
     except Exception:
         fp64_peak, fp32_peak = None, None
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            sw.run(stream)
-        sw.plan.sync(stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    nst = len(Sweep.STAGES)
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nst)] for _ in range(args.steps)]
-    clocks = Clocks(local)
-    sw.plan.timing_reset()
-    sw.plan.timing_enable(True)  # one CUDA event pair around each library launch
-    barrier(world)
-    torch.cuda.synchronize()
-    clocks.start()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush_l2(flush)
-            sw.run(stream, ev[k])
-    sw.plan.sync(stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    barrier(world)
-    clk = clocks.stop()
-    ktimes = sw.plan.timing_read()
-    sw.plan.timing_enable(False)
-    stage_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(nst)] for k in range(args.steps)])
-    step_ms = float(stage_ms.sum(axis=1).mean())
-    step_ms_max, value = aggregate(step_ms, world)
-    stage_mean = stage_ms.mean(axis=0)
-
-    # roofline of the dominant kernel, timed live by the library's event pairs
-    ent = sw.plan.entries
-    inf = sw.plan.info
-    kd = pb_dims(sw.plan)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    tot_k = sum(v[0] for v in ktimes.values()) or 1.0
-    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches_per_step": v[1] / args.steps,
-                   "share": round(v[0] / tot_k, 4)} for k, v in sorted(ktimes.items(), key=lambda x: -x[1][0])}
-    roof = None
-    if ktimes:
-        dom_k = max(ktimes, key=lambda k: ktimes[k][0])
-        ms_tot, nl = ktimes[dom_k]
-        w = kernel_work(dom_k, cell, inf, ent, kd)
-        if w is not None:
-            bound, work, kind, units = w
-            per_launch = work * args.steps / nl
-            dur = ms_tot * 1e-3 / nl
-            if bound == "hbm":
-                ach, unit = per_launch / dur / 1e9, "GB/s"
-                peak, src = peaks.get("hbm_gbs"), "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)"
-            elif bound == "tensor":
-                ach, unit = per_launch / dur / 1e12, "TFLOP/s"
-                peak, src = peaks.get("bf16_tflops"), "measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops)"
-            else:
-                ach, unit = per_launch / dur / 1e12, "TFLOP/s"
-                if kind == "fp64":
-                    peak, src = fp64_peak, "FP64 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
-                else:
-                    peak, src = fp32_peak, "FP32 FMA-chain probe (gw_fp_peak) on this GPU before the timed region"
-            roof = {"kernel": dom_k, "bound": bound, "achieved": round(ach, 4),
-                    "peak": round(peak, 4) if peak else None, "unit": unit,
-                    "frac": round(ach / peak, 4) if peak else None,
-                    "traffic": traffic_of(dom_k, units * args.steps / nl), "peak_source": src,
-                    "work_per_launch": per_launch, "launch_ms": round(dur * 1e3, 4)}
-    fl_P = contraction_flops(cell, ent, kd) / (2 if inf["c_symmetric"] else 1)  # mirrored nodes not computed
-    fl_S = contraction_flops(cell, ent, kd)
-    fl_W = wsolve_flops(cell, inf)
-    work = {"P": fl_P, "Sigma": fl_S, "W_solve": fl_W}
-    contraction_tflops = {k: round(work[k] / (stage_mean[Sweep.STAGES.index(k)] * 1e-3) / 1e12, 4)
-                          for k in ("P", "Sigma", "W_solve")}
-
-    # the P + Sigma sweep without the W solve (rows a1-a4, a6-a8; a5 timed on its own)
-    ps_ms = float(stage_mean.sum() - stage_mean[Sweep.STAGES.index("W_solve")])
-    p_sigma = {"value": round(world * 1000.0 / ps_ms, 4), "unit": "sweep/s", "ms_per_sweep": round(ps_ms, 4),
-               "w_solve_ms": round(float(stage_mean[Sweep.STAGES.index("W_solve")]), 4),
-               "stages": "every row except the W solve, which is timed on its own"}
-
-    dyson = None if args.no_dyson else run_dyson(sw, cell, stream, args)
-    mixed_err = mixed_vs_fp64(sw, stream, cell) if args.precision == "mixed" else None
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(sw, Gk, vq, stream, args)
-    out = {
-        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(step_ms_max, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x3/f32-acc + f64",
-        "data": "synthetic",
-        "config": {"workload": cell.name + f": {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k,"
-                   f" {cell.n_tau} tau, cutoff {cell.cutoff} bohr, {len(ent)} pair entries",
-                   "precision": args.precision, "l2": "256 MB buffer written between timed steps",
-                   "sigma_stage_a": ("FP64-accurate digit products on the tensor cores" if inf["sigma_tensor"]
-                                     else "FP64 arithmetic"),
-                   "w_inverse": ("FP32 Gauss-Jordan + two residual refinements on the tensor cores (FP64-accurate)"
-                                 if inf["w_tensor"] else "FP64 Gauss-Jordan"),
-                   "far_basis": ({"r_b_bohr": cell.r_b, "n_prod_far": [sp.n_prod_far for sp in cell.species],
-                                  "entries_far": inf["n_entries_far"], "len_pb": inf["len_pb"]}
-                                 if inf["n_entries_far"] else None),
-                   "parallelism": f"replicas x{world}"},
-        "stage_ms": {n: round(float(t), 4) for n, t in zip(Sweep.STAGES, stage_mean)},
-        "p_sigma_sweep": p_sigma,
-        "tflops": contraction_tflops,
-        "fp64_peak_tflops_measured": fp64_peak, "fp32_peak_tflops_measured": fp32_peak,
-        "wall_s": round(wall, 3),
-        "clocks": clk,
-        # the library's kernel launches in the timed region, counted by its event timer
-        "gpu_launches": int(sum(v[1] for v in ktimes.values())),
-        "roofline": roof,
-        "kernels": kernels,
-        "e2e": e2e,
-    }
-    if mixed_err is not None:
-        out["mixed_vs_fp64"] = mixed_err
-    if dyson is not None:
-        out["dyson"] = dyson
+    out = {"workload": f"{cell.name}: {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k, "
+                       f"{cell.n_tau} tau, cutoff {cell.cutoff} bohr, {len(sw.plan.entries)} pair entries, N_PB "
+                       f"{cell.n_pb_total}"}
+    for prec in ("fp64", "mixed"):
+        sw.prec = prec
+        ms, stage_ms, kt, _ = time_rows(sw, stream, flush, args.steps, args.warmup)
+        st = dict(zip(Sweep.STAGES, stage_ms))
+        ps = ms - st["W_solve"]
+        out[prec] = {"value": round(1000.0 / ms, 6), "unit": UNIT, "ms_per_sweep": round(ms, 4),
+                     "p_sigma_rows_ms": round(ps, 4), "w_solve_ms": round(st["W_solve"], 4),
+                     "stage_ms": {n: round(float(t), 4) for n, t in st.items()},
+                     "roofline_dominant_kernel": dominant_kernel_roofline(kt, args.steps, cell, sw.plan, peaks,
+                                                                         fp32_peak, fp64_peak),
+                     "kernels": kernels_table(kt, args.steps)}
+    sw.prec = "mixed"
+    if with_errors:
+        out["mixed_vs_fp64"] = mixed_vs_fp64(sw, stream, cell)
+    if not args.no_dyson:
+        out["dyson"] = run_dyson(sw, cell, stream, args)
+    sw.plan.close()
+    del sw
+    torch.cuda.empty_cache()
     return out, cell
 
 
@@ -642,73 +918,62 @@ def qp_compare(sw, stream, cell):
             "workload": cell.name, "beta": cell.beta}
 
 
-def run_e2e(sw, Gk, vq, stream, args):
-    """Same sweep through the public API with host buffers: H2D of G(k,tau) and v(q)
-    from pinned memory and D2H of Sigma(k, i omega) and Sigma_x(k) inside the timed region."""
-    import torch
-    Gk_h = torch.from_numpy(Gk.reshape(-1)).pin_memory()
-    vq_h = torch.from_numpy(vq.reshape(-1)).pin_memory()
-    Sk_h = torch.empty(sw.S_k.numel(), dtype=torch.complex128).pin_memory()
-    Sxk_h = torch.empty(sw.Sx_k.numel(), dtype=torch.complex128).pin_memory()
-    steps = max(1, min(args.steps, 3))
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        sw.G_k.copy_(Gk_h, non_blocking=True)
-        sw.v_q.copy_(vq_h, non_blocking=True)
-        sw.run(stream)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(steps):
-            sw.G_k.copy_(Gk_h, non_blocking=True)
-            sw.v_q.copy_(vq_h, non_blocking=True)
-            sw.run(stream)
-            Sk_h.copy_(sw.S_k, non_blocking=True)
-            Sxk_h.copy_(sw.Sx_k, non_blocking=True)
-        ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
-    return {"value": round(1000.0 / ms, 6), "unit": UNIT, "ms_per_step": round(ms, 4),
-            "h2d_bytes_per_step": int(Gk_h.numel() * 16 + vq_h.numel() * 16),
-            "d2h_bytes_per_step": int(Sk_h.numel() * 16 + Sxk_h.numel() * 16), "steps": steps}
-
-
 # --------------------------------------------------------------------------------------
 # the oracle on the host cores (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------------------
 
-def oracle_sample(cell, n_nu_sample: int = 3):
-    """Time one oracle sweep with the W solve on `n_nu_sample` of the bosonic
-    frequencies; the W time is scaled to all of them.  Returns (seconds per sweep, note)."""
-    import oracle
-    t0 = time.perf_counter()
-    orc = oracle.OracleSystem(cell)
-    Gk = cell.green_k_tau()
-    vq, vc = cell.coulomb()
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    GR = oracle.fourier_k_to_R(Gk, orc.entries, orc.kmesh, cell.orb_offsets, cell.orb_offsets)
-    PR = oracle.polarizability_R(GR, orc.entries, orc.C_atom, cell.spin, orc.kdims)
-    Piw = oracle.transform(orc.B_fwd, PR)
-    t_a = time.perf_counter() - t0
-    nn = cell.nu_idx.size
-    sel = list(range(min(n_nu_sample, nn)))
-    t0 = time.perf_counter()
-    oracle.screened_W([x[sel] for x in Piw], orc.entries, vq, orc.kmesh, cell.pb_offsets)
-    t_w = (time.perf_counter() - t0) * nn / len(sel)
-    t0 = time.perf_counter()
-    rng = np.random.default_rng(0)
-    WR = [rng.standard_normal(p.shape) + 0j for p in PR]  # W~(R, tau) has P's shapes
-    vR = orc.v_R(vc)
-    SR = oracle.self_energy_R(GR, WR, orc.entries, orc.C_atom)
-    oracle.exchange_R(GR, vR, orc.entries, orc.C_atom)
-    Siw = oracle.transform(orc.F_fwd, SR)
-    oracle.fourier_R_to_k(Siw, orc.entries, orc.kmesh, cell.orb_offsets, cell.orb_offsets)
-    t_b = time.perf_counter() - t0
-    total = t_a + t_w + t_b
-    note = (f"full oracle sweep except the W solve, which ran on {len(sel)} of {nn} bosonic frequencies "
-            f"({t_w * len(sel) / nn:.2f} s) and is scaled x{nn / len(sel):.1f}; input setup {t_setup:.1f} s not counted")
-    return total, note
+class OracleRows:
+    """The FP64 oracle's P + Sigma rows on a fixed sample of the workload's pair entries
+    (every E/n-th entry, all tau nodes), with the same seeded stand-in for W~(R, i nu);
+    one timed pass is scaled by E/n to a whole sweep (every row's cost is a sum over
+    entries).  Setup (the cell, G(k, tau), the transform matrices) is not timed."""
+
+    def __init__(self, cell, n_sample: int = 24):
+        import oracle
+        self.oracle = oracle
+        self.cell = cell
+        self.orc = oracle.OracleSystem(cell)
+        E = len(self.orc.entries)
+        self.sel = np.unique(np.linspace(0, E - 1, min(n_sample, E)).astype(int))
+        self.scale = E / len(self.sel)
+        self.ent = self.orc.entries[self.sel]
+        self.kdims = [self.orc.kdims[e] for e in self.sel]
+        self.Gk = cell.green_k_tau()
+        rng = np.random.default_rng(0)
+        nn = cell.nu_idx.size
+        self.Wiw = [rng.standard_normal((nn, Ka, Kb)) + 0j for Ka, Kb in self.kdims]
+        self.vR = [rng.standard_normal((Ka, Kb)) + 0j for Ka, Kb in self.kdims]
+        self.note = (f"P+Sigma rows (a1, a2, a3, a6, a7, a8) on {len(self.sel)} of {E} pair entries (every "
+                     f"{E // len(self.sel)}th, all {cell.n_tau} tau nodes), scaled x{self.scale:.1f}; W~(R, i nu) "
+                     f"seeded as on the GPU; setup not counted")
+
+    def time_one(self) -> float:
+        o, c, orc = self.oracle, self.cell, self.orc
+        oo = c.orb_offsets
+        # the R -> k sum of the sample into the blocks of the atoms it touches (the dense
+        # output of the whole cell is allocated once per sweep, timed apart and not scaled)
+        used = sorted(set(int(x) for x in self.ent[:, 0]) | set(int(x) for x in self.ent[:, 1]))
+        ren = {a: i for i, a in enumerate(used)}
+        ent_c = self.ent.copy()
+        ent_c[:, 0] = [ren[int(a)] for a in self.ent[:, 0]]
+        ent_c[:, 1] = [ren[int(b)] for b in self.ent[:, 1]]
+        oo_c = np.concatenate([[0], np.cumsum([c.n_orb_of(a) for a in used])])
+        t0 = time.perf_counter()
+        GR = o.fourier_k_to_R(self.Gk, self.ent, orc.kmesh, oo, oo)
+        PR = o.polarizability_R(GR, self.ent, orc.C_atom, c.spin, self.kdims)
+        o.transform(orc.B_fwd, PR)
+        WR = o.transform(orc.B_inv, self.Wiw)
+        SR = o.self_energy_R(GR, WR, self.ent, orc.C_atom)
+        o.exchange_R(GR, self.vR, self.ent, orc.C_atom)
+        Siw = o.transform(orc.F_fwd, SR)
+        o.fourier_R_to_k(Siw, ent_c, orc.kmesh, oo_c, oo_c)
+        t_sample = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        out = np.zeros((c.n_k, c.omega_idx.size, c.n_orb_total, c.n_orb_total), np.complex128)
+        out[0, 0, 0, 0] = 1.0
+        t_alloc = time.perf_counter() - t0
+        del out
+        return t_sample * self.scale + t_alloc
 
 
 def cpu_cores():
@@ -721,23 +986,34 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def rows_config(cell, n_entries, n_pb, precision, world):
+    """The `config` of the P + Sigma rows line (the same dict in both arms)."""
+    return {"workload": f"{cell.name}: {cell.n_atoms} atoms, {cell.kmesh[0]}x{cell.kmesh[1]}x{cell.kmesh[2]} k,"
+                        f" {cell.n_tau} tau, cutoff {cell.cutoff} bohr, {n_entries} pair entries, N_PB {n_pb}",
+            "rows": "a1 G k->R, a2 P, a3 P tau->i nu, a6 W~ i nu->tau, a7 Sigma + Sigma_x, a8 Sigma tau->i w "
+                    "and R->k; the W solve (Eq. W_1, with the dense q-space halves of a4/a6) timed apart",
+            "inputs": "G(k,tau) of the seeded tight-binding cell; W~(R,i nu) and v(R) seeded (the W solve's "
+                      "output and the bare interaction, in the plan's shapes)",
+            "precision": precision, "l2": "256 MB buffer written between timed steps (inputs > L2)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
-    cell = workload(args.config, args.small, args.r_b, args.n_prod_far)
     if rank != 0:
         return None
-    secs = []
-    note = ""
-    for _ in range(max(1, args.steps)):
-        s, note = oracle_sample(cell)
-        secs.append(s)
+    cell = workload(2, False, args.r_b, args.n_prod_far, atoms=args.atoms)
+    orc = OracleRows(cell)
+    for _ in range(args.warmup):
+        orc.time_one()
+    secs = [orc.time_one() for _ in range(max(1, args.steps))]
     ms = 1000.0 * float(np.mean(secs))
     v = 1000.0 / ms
+    cfg = rows_config(cell, len(orc.orc.entries), cell.n_pb_total, args.precision, world)
     return {"impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cell.name, "precision": "fp64 (oracle, NumPy/LAPACK)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": round(v, 8), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                             "sample": note},
+                             "sample": orc.note},
             "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -864,28 +1140,42 @@ def run_serve(args, local):
 
 def main():
     args = parse()
+    rank, world, local = dist_init(args)
     if args.serve:
-        rank, world, local = dist_init(args)
         if rank == 0:
             print(json.dumps(run_serve(args, local)), flush=True)
         return
     if args.scaling is not None:
-        rank, world, local = dist_init(args)
         if rank == 0:
             print(json.dumps(run_scaling(args, local)), flush=True)
         return
-    rank, world, local = dist_init(args)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return
-    out, cell = run_ours(args, rank, world, local)
+    if args.config == 1 or args.small:  # the 8-atom whole sweep as the main line
+        full, cell = run_full(args, local)
+        m = full[args.precision]
+        step_ms_max, value = aggregate(m["ms_per_sweep"], world)
+        out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(step_ms_max, 4), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x3-f32acc",
+               "data": "synthetic", "config": {"workload": full["workload"], "precision": args.precision},
+               "roofline": m["roofline_dominant_kernel"], "gpu_launches": None, "full_sweep": full}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
+    out, cell = run_rows(args, rank, world, local)
+    if not args.no_extra:
+        full, _ = run_full(args, local)
+        out["full_sweep_8_atoms"] = full
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            s, note = oracle_sample(cell)
+            orc = OracleRows(cell)
+            s = orc.time_one()
             out["cpu_baseline"] = {"value": round(1.0 / s, 8), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                   "sample": note}
+                                   "sample": orc.note}
         print(json.dumps(out), flush=True)
 
 

@@ -136,6 +136,8 @@ typedef struct {
                                  tau -> i nu of the product-basis layout by FP64-accurate
                                  tensor-core products (device plans) */
   int n_entries_far;          /* entries with the reduced product basis (beyond r_b) */
+  int mixed_queue;            /* GW_MIXED contractions as persistent tensor-core kernels over a queue
+                                 of (entry, tau) units: bit 0 P, bit 1 Sigma (device plans) */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */
@@ -278,6 +280,53 @@ gw_status gw_sync(gw_plan_t plan, void* stream);
 const char* gw_status_string(gw_status s);
 /* Text of the last error on this thread (empty if none). */
 const char* gw_last_error(void);
+
+/* ---- batches of systems of uneven sizes in one launch -------------------------- */
+
+/* A batch of up to GW_BATCH_MAX plans (device plans on one device, each within the
+ * contraction kernels' limits: n_orb <= 16, n_prod <= 128) whose GW_MIXED P and Sigma
+ * contractions (Eqs. P_MM and S_MM) run as ONE persistent launch each: a queue of
+ * (system, pair entry, tau node) units drained by one resident block per SM, so that
+ * systems with different atom counts, pair lists and basis sizes share the GPU without
+ * one launch per system.  The batch holds its unit queue and launch configuration; the
+ * plans must outlive it.  Results are those of gw_polarizability_tau and
+ * gw_self_energy_tau (without exchange) with GW_MIXED on each plan alone. */
+#define GW_BATCH_MAX 24
+typedef struct gw_batch_s* gw_batch_t;
+
+typedef struct {
+  int n_plans;
+  long long n_units_p, n_units_s;  /* queue lengths */
+  int groups_p, groups_s;          /* thread groups per block */
+  int kc_p, kc_s;                  /* reduction chunk (product-basis or orbital-pair columns) */
+  int order_p, order_s;            /* unit order: 0 by shape class, 1 heaviest first */
+  int tuned;                       /* 1 after gw_batch_tune */
+} gw_batch_info;
+
+/* GW_ERR_ARG for n_plans outside [1, GW_BATCH_MAX], plans on different devices or host-only
+ * plans; GW_ERR_UNSUPPORTED for a plan outside the kernels' limits. */
+gw_status gw_batch_create(const gw_plan_t* plans, int n_plans, gw_batch_t* out);
+gw_status gw_batch_destroy(gw_batch_t b);
+gw_status gw_batch_query(gw_batch_t b, gw_batch_info* info);
+
+/* P of every plan of the batch in one launch.  G_R, P_R: HOST arrays of n_plans DEVICE
+ * pointers, each in the layout of gw_polarizability_tau for its plan.  Asynchronous;
+ * capturable in a CUDA graph (no host-to-device copy, no allocation). */
+gw_status gw_batch_polarizability_tau(gw_batch_t b, const void* const* G_R, void* const* P_R, void* stream);
+
+/* The dynamic Sigma of every plan in one launch (layouts of gw_self_energy_tau). */
+gw_status gw_batch_self_energy_tau(gw_batch_t b, const void* const* G_R, const void* const* Wt_R,
+                                   void* const* Sig_R, void* stream);
+
+/* Autotuner: times each candidate launch configuration (thread groups per block, reduction
+ * chunk, unit order) of both contractions on these buffers with CUDA events on `stream`,
+ * `reps` launches per candidate, and keeps the fastest.  Overwrites P_R and Sig_R;
+ * synchronous.  Call before capturing the batch's launches in a graph. */
+gw_status gw_batch_tune(gw_batch_t b, const void* const* G_R, void* const* P_R, const void* const* Wt_R,
+                        void* const* Sig_R, int reps, void* stream);
+
+/* Wait for the stream and report a deferred device error of the batch's launches. */
+gw_status gw_batch_sync(gw_batch_t b, void* stream);
 
 /* ---- Eq. G_1: the Dyson equation and the chemical potential ------------------- */
 

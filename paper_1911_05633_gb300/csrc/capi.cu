@@ -15,6 +15,7 @@
 #include "kernels.h"
 #include "smem_limit.h"
 #include "mixed.h"
+#include "contract.h"
 #include "wtc.h"
 #include "oz.h"
 #include "ktimer.h"
@@ -30,6 +31,8 @@ struct gw_plan_s {
   int n_active = 0;
   int* d_orb_off = nullptr;
   int* d_pb_off = nullptr;
+  int* d_orb_atom = nullptr;  // [N_orb] atom of each orbital row / column
+  int* d_pb_atom = nullptr;   // [N_PB] atom of each product-basis row / column
   double2* d_phase = nullptr;
   double* d_C = nullptr;
   double2* d_Tf_fwd = nullptr;
@@ -65,6 +68,14 @@ struct gw_plan_s {
   int* t_eA = nullptr;
   int* t_eX = nullptr;
   gw::MixedPlan mixed;
+  // mixed-precision contractions as persistent tensor-core kernels over a unit queue
+  gw::CTables ct;
+  gw::CConfig cfgP, cfgS;
+  bool contract_p = false, contract_s = false;
+  gw::CUnit* d_unitsP = nullptr;
+  gw::CUnit* d_unitsS = nullptr;
+  int n_unitsP = 0, n_unitsS = 0;
+  int* d_counter = nullptr;
   bool sigma_tensor = false;  // FP64 Sigma stage A by tensor-core digit products
   gw::OzSigma oz;
   gw::OzTransform ozt;  // FP64-accurate structured transforms on the tensor cores
@@ -125,13 +136,15 @@ gw_status upload(T** dst, const void* src, size_t bytes) {
 }
 
 void free_device(gw_plan_s* p) {
-  void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_phase,
+  void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_orb_atom,
+                  p->d_pb_atom, p->d_phase,
                   p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_mirror, p->d_Tb_inv, p->d_qh, p->d_qw,
                   p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_lo, p->t_R, p->t_PX, p->t_Asl,
-                  p->t_Xsl, p->t_eA, p->t_eX};
+                  p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_counter};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
+  gw::ctables_free(p->ct);
   gw::oz_sigma_free(p->oz);
   gw::oz_transform_free(p->ozt);
   gw::oz_pol_free(p->ozp);
@@ -164,7 +177,9 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
                         int real_only = 0) {
   gw::GatherArgs g{};
   g.ent = p->d_ent;
-  g.pair_first = p->d_pair_first;
+  g.pair_start = p->d_pair_start;
+  g.col_atom = kind == GW_BLOCK_PB ? p->d_pb_atom : p->d_orb_atom;
+  g.n_atoms = p->h.n_atoms;
   g.phase = p->d_phase;
   g.n_k = p->h.n_k;
   g.k_list = k_list;
@@ -184,15 +199,10 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
   g.out_n_slices = out_n_slices;
   g.out_slice0 = out_slice0;
   g.scale = scale;
-  int maxblk = 0;
-  for (int s = 0; s < p->h.n_species; ++s)
-    for (int t = 0; t < p->h.n_species; ++t)
-      maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
-  const int threads = 128;
-  dim3 grid(p->n_active, n_slices, (maxblk + threads - 1) / threads);
+  dim3 grid(p->h.n_atoms, n_slices);
   {
     gw::TimedLaunch tl_("k_gather_k_to_R", st);
-    gw::k_gather_k_to_R<<<grid, threads, 0, st>>>(g);
+    gw::k_gather_k_to_R<<<grid, 256, 0, st>>>(g);
   }
   return check_launch("k_gather_k_to_R");
 }
@@ -205,6 +215,7 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   g.real_in = real_in ? 1 : 0;
   g.ent = p->d_ent;
   g.pair_start = p->d_pair_start;
+  g.col_atom = kind == GW_BLOCK_PB ? p->d_pb_atom : p->d_orb_atom;
   g.row_off = kind == GW_BLOCK_PB ? p->d_pb_off : p->d_orb_off;
   g.n_atoms = p->h.n_atoms;
   g.phase = p->d_phase;
@@ -221,15 +232,10 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   g.k_stride = k_stride;
   g.s_stride = s_stride;
   g.ld = dense_n(p, kind);
-  int maxblk = 0;
-  for (int s = 0; s < p->h.n_species; ++s)
-    for (int t = 0; t < p->h.n_species; ++t)
-      maxblk = std::max(maxblk, kind == GW_BLOCK_PB ? p->h.n_prod[s] * p->h.n_prod[t] : p->h.n_orb[s] * p->h.n_orb[t]);
-  const int threads = 128;
-  dim3 grid(p->h.n_atoms * p->h.n_atoms, n_slices, (maxblk + threads - 1) / threads);
+  dim3 grid(p->h.n_atoms, n_slices);
   {
     gw::TimedLaunch tl_("k_scatter_R_to_k", st);
-    gw::k_scatter_R_to_k<<<grid, threads, 0, st>>>(g);
+    gw::k_scatter_R_to_k<<<grid, 256, 0, st>>>(g);
   }
   return check_launch("k_scatter_R_to_k");
 }
@@ -384,6 +390,15 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_pair_first, pair_first.data(), pair_first.size() * sizeof(int))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_orb_off, h.orb_off.data(), h.orb_off.size() * sizeof(int))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_pb_off, h.pb_off.data(), h.pb_off.size() * sizeof(int))) != GW_OK) return fail(st);
+  {
+    std::vector<int> oa(h.n_orb_total()), pa(h.n_pb_total());
+    for (int a = 0; a < h.n_atoms; ++a) {
+      for (int i = h.orb_off[a]; i < h.orb_off[a + 1]; ++i) oa[i] = a;
+      for (int i = h.pb_off[a]; i < h.pb_off[a + 1]; ++i) pa[i] = a;
+    }
+    if ((st = upload(&p->d_orb_atom, oa.data(), oa.size() * sizeof(int))) != GW_OK) return fail(st);
+    if ((st = upload(&p->d_pb_atom, pa.data(), pa.size() * sizeof(int))) != GW_OK) return fail(st);
+  }
   if ((st = upload(&p->d_phase, h.phase.data(), h.phase.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_C, h.C_packed.data(), h.C_packed.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tf_fwd, h.Tf_fwd.data(), h.Tf_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
@@ -456,6 +471,20 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     return fail(GW_ERR_UNSUPPORTED);
   }
   if ((st = gw::mixed_init(p->mixed, h, de)) != GW_OK) return fail(st);
+  if ((st = gw::ctables_init(p->ct, h)) != GW_OK) return fail(st);
+  if (p->ct.ready) {
+    // the queue kernels where their configuration fits this device; otherwise the
+    // mixed path keeps its per-entry kernels
+    p->contract_p = gw::contract_config(false, p->ct.np_max, p->ct.kd_max, p->cfgP, p->device) == GW_OK;
+    p->contract_s = gw::contract_config(true, p->ct.nj_max, p->ct.kds_max, p->cfgS, p->device) == GW_OK;
+    const std::vector<gw::CUnit> uP = gw::contract_units(h, 0, false), uS = gw::contract_units(h, 0, true);
+    p->n_unitsP = (int)uP.size();
+    p->n_unitsS = (int)uS.size();
+    if ((st = upload(&p->d_unitsP, uP.data(), uP.size() * sizeof(gw::CUnit))) != GW_OK) return fail(st);
+    if ((st = upload(&p->d_unitsS, uS.data(), uS.size() * sizeof(gw::CUnit))) != GW_OK) return fail(st);
+    if ((st = upload(&p->d_counter, nullptr, 16)) != GW_OK) return fail(st);
+    gw::set_last_error("");
+  }
   if (p->sigma_tensor) {
     if ((st = gw::oz_sigma_init(p->oz, h, (size_t)4 << 30)) != GW_OK) return fail(st);
     p->sigma_tensor = p->oz.ready;
@@ -507,6 +536,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->w_tensor = p->w_tensor ? 1 : 0;
   info->sigma_tensor = p->sigma_tensor ? 1 : 0;
   info->p_tensor = p->ozp.ready ? 1 : 0;
+  info->mixed_queue = (p->contract_p ? 1 : 0) | (p->contract_s ? 2 : 0);
   info->transform_tensor = (p->ozt.ready_w ? 1 : 0) | (p->ozt.ready_p ? 2 : 0);
   info->n_q_solved = p->n_qh;
   return GW_OK;
@@ -639,6 +669,25 @@ gw_status gw_transform_tau_iw(gw_plan_t p, gw_statistics stt, gw_direction dir, 
   return gw_transform_tau_iw_ex(p, stt, dir, kind, 0, in, out, stream);
 }
 
+// One plan's entry in a queue launch of the contraction kernels.
+static gw::CSys contract_sys(const gw_plan_s* p, const double2* G, const double2* W, double2* out) {
+  gw::CSys s{};
+  s.ent = p->d_ent;
+  s.Cp = p->ct.d_Cp;
+  s.cp_off = p->ct.d_cp_off;
+  s.cp_ld = p->ct.d_cp_ld;
+  s.Bp = W ? p->ct.d_BpS : p->ct.d_BpP;
+  s.bp_off = W ? p->ct.d_bpS_off : p->ct.d_bpP_off;
+  s.species = p->ct.d_species;
+  s.G = G;
+  s.W = W;
+  s.out = out;
+  s.n_tau = p->h.n_tau;
+  s.spin = p->h.spin;
+  s.mirror = p->h.c_symmetric;
+  return s;
+}
+
 gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_precision prec, void* stream) {
   gw_status st = need_device(p);
   if (st != GW_OK) return st;
@@ -646,9 +695,16 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   DeviceGuard guard(p->device);
   gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
-  if (prec == GW_MIXED)
+  if (prec == GW_MIXED) {
+    if (p->contract_p) {
+      gw::CBatch b{};
+      b.n = 1;
+      b.s[0] = contract_sys(p, (const double2*)G_R, nullptr, (double2*)P_R);
+      return gw::contract_launch(false, p->cfgP, b, p->d_unitsP, p->n_unitsP, p->d_counter, p->d_status, S(stream));
+    }
     return gw::mixed_polarizability(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (double2*)P_R, p->d_status,
                                     S(stream));
+  }
   if (prec != GW_FP64) { set_last_error("unknown precision"); return GW_ERR_ARG; }
   gw::ContractArgs g{};
   g.ent = p->d_ent;
@@ -694,8 +750,15 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
   gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   if (prec == GW_MIXED) {
-    st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
-                               (double2*)Sig_R, p->d_status, S(stream));
+    if (p->contract_s) {
+      gw::CBatch b{};
+      b.n = 1;
+      b.s[0] = contract_sys(p, (const double2*)G_R, (const double2*)Wt_R, (double2*)Sig_R);
+      st = gw::contract_launch(true, p->cfgS, b, p->d_unitsS, p->n_unitsS, p->d_counter, p->d_status, S(stream));
+    } else {
+      st = gw::mixed_self_energy(p->mixed, h, p->d_ent, p->d_C, (const double2*)G_R, (const double2*)Wt_R,
+                                 (double2*)Sig_R, p->d_status, S(stream));
+    }
     if (st != GW_OK) return st;
   } else if (prec == GW_FP64) {
     gw::ContractArgs g{};
@@ -824,9 +887,12 @@ gw_status gw_sync(gw_plan_t p, void* stream) {
   DeviceGuard guard(p->device);
   GW_CUDA(cudaStreamSynchronize(S(stream)));
   int flag = 0;
-  GW_CUDA(cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  GW_CUDA(cudaMemcpyAsync(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+  GW_CUDA(cudaStreamSynchronize(S(stream)));
   if (flag) {
-    cudaMemset(p->d_status, 0, sizeof(int));
+    // cleared on the caller's stream, ordered before any later launch on it
+    GW_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), S(stream)));
+    GW_CUDA(cudaStreamSynchronize(S(stream)));
     if (flag == 2) {
       set_last_error("a tensor-core wait gave up (bounded wait)");
       return GW_ERR_TIMEOUT;
@@ -910,9 +976,11 @@ gw_status gw_chemical_potential(gw_plan_t p, const void* H_k, const void* Sigx_k
     GW_CUDA(cudaMemcpyAsync(part.data(), p->dyson.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GW_CUDA(cudaStreamSynchronize(s));
     int flag = 0;
-    GW_CUDA(cudaMemcpy(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    GW_CUDA(cudaMemcpyAsync(&flag, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GW_CUDA(cudaStreamSynchronize(s));
     if (flag) {
-      cudaMemset(p->d_status, 0, sizeof(int));
+      GW_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+      GW_CUDA(cudaStreamSynchronize(s));
       set_last_error("zero pivot in the Dyson solve");
       return GW_ERR_SINGULAR;
     }
@@ -1131,4 +1199,246 @@ extern "C" gw_status gw_screened_W_iw_noalloc(gw_plan_t p, const void* P_R_iw, c
     if ((st = check_launch("k_mirror_nu")) != GW_OK) return st;
   }
   return GW_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches of systems: the GW_MIXED contractions of several plans in one queue launch
+// ---------------------------------------------------------------------------------------
+
+struct gw_batch_s {
+  std::vector<gw_plan_s*> plans;
+  int device = 0;
+  int ncols_p = 0, kd_p = 0, ncols_s = 0, kd_s = 0;
+  gw::CConfig cfgP, cfgS;
+  int orderP = 0, orderS = 0;
+  gw::CUnit* d_unitsP = nullptr;
+  gw::CUnit* d_unitsS = nullptr;
+  int nP = 0, nS = 0;
+  int* d_counter = nullptr;
+  int* d_status = nullptr;
+  bool tuned = false;
+};
+
+namespace {
+
+// The batch's units of one contraction in the given order: 0 grouped by shape class
+// (species pair and basis size, so that consecutive units share their B operand), 1 the
+// heaviest first (so that the queue's tail is made of light units).
+std::vector<gw::CUnit> batch_units(const gw_batch_s* b, bool sigma, int order) {
+  std::vector<gw::CUnit> u;
+  std::vector<long long> key;
+  for (int i = 0; i < (int)b->plans.size(); ++i) {
+    const gw::HostPlan& h = b->plans[i]->h;
+    for (const gw::CUnit& x : gw::contract_units(h, i, sigma)) {
+      u.push_back(x);
+      if (order == 1) {
+        key.push_back(-gw::contract_unit_cost(h, x.e, sigma));
+      } else {
+        const int a = (int)h.entries[8 * x.e], bb = (int)h.entries[8 * x.e + 1];
+        const long long na = h.n_orb[h.species[a]], nb = h.n_orb[h.species[bb]];
+        key.push_back((((na * 32 + nb) * 256 + h.Ka_e[x.e]) * 256 + h.Kb_e[x.e]) * 32 + i);
+      }
+    }
+  }
+  std::vector<size_t> idx(u.size());
+  for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return key[x] < key[y]; });
+  std::vector<gw::CUnit> out(u.size());
+  for (size_t k = 0; k < idx.size(); ++k) out[k] = u[idx[k]];
+  return out;
+}
+
+gw_status batch_upload_units(gw_batch_s* b, bool sigma, int order) {
+  const std::vector<gw::CUnit> u = batch_units(b, sigma, order);
+  gw::CUnit*& d = sigma ? b->d_unitsS : b->d_unitsP;
+  if (!d) {
+    gw_status st = upload(&d, nullptr, u.size() * sizeof(gw::CUnit));
+    if (st != GW_OK) return st;
+  }
+  GW_CUDA(cudaMemcpy(d, u.data(), u.size() * sizeof(gw::CUnit), cudaMemcpyHostToDevice));
+  (sigma ? b->nS : b->nP) = (int)u.size();
+  (sigma ? b->orderS : b->orderP) = order;
+  return GW_OK;
+}
+
+gw::CBatch batch_systems(const gw_batch_s* b, const void* const* G_R, const void* const* Wt_R, void* const* out) {
+  gw::CBatch cb{};
+  cb.n = (int)b->plans.size();
+  for (int i = 0; i < cb.n; ++i)
+    cb.s[i] = contract_sys(b->plans[i], (const double2*)G_R[i], Wt_R ? (const double2*)Wt_R[i] : nullptr,
+                           (double2*)out[i]);
+  return cb;
+}
+
+}  // namespace
+
+gw_status gw_batch_create(const gw_plan_t* plans, int n_plans, gw_batch_t* out) {
+  if (!plans || !out || n_plans < 1 || n_plans > GW_BATCH_MAX) {
+    set_last_error("gw_batch_create: need 1 .. GW_BATCH_MAX plans");
+    return GW_ERR_ARG;
+  }
+  *out = nullptr;
+  gw_batch_s* b = new (std::nothrow) gw_batch_s();
+  if (!b) return GW_ERR_OOM;
+  for (int i = 0; i < n_plans; ++i) {
+    gw_plan_s* p = plans[i];
+    if (!p || p->host_only || (i > 0 && p->device != plans[0]->device)) {
+      delete b;
+      set_last_error("gw_batch_create: device plans on one device only");
+      return GW_ERR_ARG;
+    }
+    if (!p->ct.ready) {
+      delete b;
+      set_last_error("gw_batch_create: a plan is outside the contraction kernels' limits");
+      return GW_ERR_UNSUPPORTED;
+    }
+    b->plans.push_back(p);
+    b->ncols_p = std::max(b->ncols_p, p->ct.np_max);
+    b->kd_p = std::max(b->kd_p, p->ct.kd_max);
+    b->ncols_s = std::max(b->ncols_s, p->ct.nj_max);
+    b->kd_s = std::max(b->kd_s, p->ct.kds_max);
+  }
+  b->device = plans[0]->device;
+  DeviceGuard guard(b->device);
+  gw_status st = gw::contract_config(false, b->ncols_p, b->kd_p, b->cfgP, b->device);
+  if (st == GW_OK) st = gw::contract_config(true, b->ncols_s, b->kd_s, b->cfgS, b->device);
+  if (st == GW_OK) st = batch_upload_units(b, false, 0);
+  if (st == GW_OK) st = batch_upload_units(b, true, 0);
+  if (st == GW_OK) st = upload(&b->d_counter, nullptr, 16);
+  if (st == GW_OK) st = upload(&b->d_status, nullptr, 16);
+  if (st == GW_OK && cudaMemset(b->d_status, 0, 16) != cudaSuccess) st = GW_ERR_CUDA;
+  if (st != GW_OK) {
+    gw_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return GW_OK;
+}
+
+gw_status gw_batch_destroy(gw_batch_t b) {
+  if (!b) return GW_OK;
+  {
+    DeviceGuard guard(b->device);
+    cudaFree(b->d_unitsP);
+    cudaFree(b->d_unitsS);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_status);
+  }
+  delete b;
+  return GW_OK;
+}
+
+gw_status gw_batch_query(gw_batch_t b, gw_batch_info* info) {
+  if (!b || !info) return GW_ERR_ARG;
+  info->n_plans = (int)b->plans.size();
+  info->n_units_p = b->nP;
+  info->n_units_s = b->nS;
+  info->groups_p = b->cfgP.groups;
+  info->groups_s = b->cfgS.groups;
+  info->kc_p = b->cfgP.kc;
+  info->kc_s = b->cfgS.kc;
+  info->order_p = b->orderP;
+  info->order_s = b->orderS;
+  info->tuned = b->tuned ? 1 : 0;
+  return GW_OK;
+}
+
+gw_status gw_batch_polarizability_tau(gw_batch_t b, const void* const* G_R, void* const* P_R, void* stream) {
+  if (!b || !G_R || !P_R) return GW_ERR_ARG;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (!G_R[i] || !P_R[i]) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(b->device);
+  gw::ActiveTimer timing(&b->plans[0]->timer);
+  const gw::CBatch cb = batch_systems(b, G_R, nullptr, P_R);
+  return gw::contract_launch(false, b->cfgP, cb, b->d_unitsP, b->nP, b->d_counter, b->d_status, S(stream));
+}
+
+gw_status gw_batch_self_energy_tau(gw_batch_t b, const void* const* G_R, const void* const* Wt_R,
+                                   void* const* Sig_R, void* stream) {
+  if (!b || !G_R || !Wt_R || !Sig_R) return GW_ERR_ARG;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (!G_R[i] || !Wt_R[i] || !Sig_R[i]) { set_last_error("bad argument"); return GW_ERR_ARG; }
+  DeviceGuard guard(b->device);
+  gw::ActiveTimer timing(&b->plans[0]->timer);
+  const gw::CBatch cb = batch_systems(b, G_R, Wt_R, Sig_R);
+  return gw::contract_launch(true, b->cfgS, cb, b->d_unitsS, b->nS, b->d_counter, b->d_status, S(stream));
+}
+
+gw_status gw_batch_sync(gw_batch_t b, void* stream) {
+  if (!b) return GW_ERR_ARG;
+  DeviceGuard guard(b->device);
+  GW_CUDA(cudaStreamSynchronize(S(stream)));
+  int flag = 0;
+  GW_CUDA(cudaMemcpyAsync(&flag, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+  GW_CUDA(cudaStreamSynchronize(S(stream)));
+  if (flag) {
+    GW_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int), S(stream)));
+    GW_CUDA(cudaStreamSynchronize(S(stream)));
+    set_last_error("a tensor-core wait gave up (bounded wait)");
+    return GW_ERR_TIMEOUT;
+  }
+  return GW_OK;
+}
+
+gw_status gw_batch_tune(gw_batch_t b, const void* const* G_R, void* const* P_R, const void* const* Wt_R,
+                        void* const* Sig_R, int reps, void* stream) {
+  if (!b || !G_R || !P_R || !Wt_R || !Sig_R || reps < 1) return GW_ERR_ARG;
+  DeviceGuard guard(b->device);
+  cudaStream_t st = S(stream);
+  cudaEvent_t e0, e1;
+  GW_CUDA(cudaEventCreate(&e0));
+  GW_CUDA(cudaEventCreate(&e1));
+  gw_status result = GW_OK;
+  for (int sig = 0; sig < 2 && result == GW_OK; ++sig) {
+    const bool sigma = sig == 1;
+    const gw::CBatch cb = sigma ? batch_systems(b, G_R, Wt_R, Sig_R) : batch_systems(b, G_R, nullptr, P_R);
+    const int ncols = sigma ? b->ncols_s : b->ncols_p, kd = sigma ? b->kd_s : b->kd_p;
+    float best = 1e30f;
+    gw::CConfig best_cfg = sigma ? b->cfgS : b->cfgP;
+    int best_order = 0;
+    for (int order = 0; order < 2 && result == GW_OK; ++order) {
+      if ((result = batch_upload_units(b, sigma, order)) != GW_OK) break;
+      for (int groups = 1; groups <= 2; ++groups) {
+        // the longest chunk that fits, and half of it
+        for (int half = 0; half < 2; ++half) {
+          gw::CConfig c;
+          if (gw::contract_config(sigma, ncols, kd, c, b->device, groups) != GW_OK || c.groups != groups) continue;
+          if (half) {
+            const int kc2 = (c.kc / 2) & ~15;
+            gw::CConfig c2;
+            if (kc2 < 16 || gw::contract_config(sigma, ncols, kd, c2, b->device, groups, kc2) != GW_OK ||
+                c2.kc == c.kc)
+              continue;
+            c = c2;
+          }
+          const gw::CUnit* du = sigma ? b->d_unitsS : b->d_unitsP;
+          const int nu = sigma ? b->nS : b->nP;
+          if ((result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st)) != GW_OK) break;
+          GW_CUDA(cudaEventRecord(e0, st));
+          for (int r = 0; r < reps && result == GW_OK; ++r)
+            result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st);
+          GW_CUDA(cudaEventRecord(e1, st));
+          GW_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          GW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (result == GW_OK && ms < best) {
+            best = ms;
+            best_cfg = c;
+            best_order = order;
+          }
+        }
+      }
+    }
+    if (result != GW_OK) break;
+    (sigma ? b->cfgS : b->cfgP) = best_cfg;
+    // the chosen configuration's shared-memory opt-in (raised for every candidate already)
+    result = batch_upload_units(b, sigma, best_order);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result == GW_OK) {
+    b->tuned = true;
+    result = gw_batch_sync(b, stream);
+  }
+  return result;
 }

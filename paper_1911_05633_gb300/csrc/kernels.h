@@ -9,7 +9,9 @@ namespace gw {
 
 struct GatherArgs {
   const DevEntry* ent;
-  const int* pair_first;   // [n_active + 1] entry range of each active atom pair
+  const int* pair_start;   // [n_atoms^2 + 1] entry range of each ordered atom pair
+  const int* col_atom;     // [N] atom of each dense row / column
+  int n_atoms;
   const double2* phase;    // [E][N_k] e^{+i k.R}
   int n_k;                 // mesh size (phase row length)
   const int* k_list;       // optional: input k index kk -> mesh k (n_k_in entries)
@@ -31,6 +33,7 @@ struct GatherArgs {
 struct ScatterArgs {
   const DevEntry* ent;
   const int* pair_start;   // [n_atoms^2 + 1]
+  const int* col_atom;     // [N] atom of each dense row / column
   const int* row_off;      // [n_atoms + 1] orbital or product offsets
   int n_atoms;
   const double2* phase;

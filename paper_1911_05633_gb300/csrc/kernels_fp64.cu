@@ -3,7 +3,7 @@
 // contractions of Eqs. P_MM and S_MM, and the batched W solve of Eq. W_1.
 //
 // Complex numbers are double2 (re, im).  Every kernel is bounds-checked against
-// the sizes it is given; launch shapes are computed in launch_fp64.cu.
+// the sizes it is given; launch shapes are computed by the C ABI in capi.cu.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -33,74 +33,75 @@ __device__ __forceinline__ double2 rfma(double r, double2 b, double2 c) {
 
 // ---------------------------------------------------------------------------
 // k -> R gather:  F_R[e][s][i][j] = scale * sum_k conj(ph[e][k]) (F_k - F_sub)[k][s][oa+i][ob+j]
-// grid: (active pair, slice, element chunk of blockDim.x) over the pair's full block; an
-// entry with a reduced product basis (beyond sphere B) keeps its top-left K_a(e) x K_b(e).
+// grid: (row atom a, slice); the block sweeps the band of rows of atom a across every
+// column of the dense matrix, so that consecutive threads read consecutive columns; an
+// element whose atom pair has no entry is skipped; an entry with a reduced product basis
+// (beyond sphere B) keeps its top-left K_a(e) x K_b(e).
 // ---------------------------------------------------------------------------
 constexpr int kGatherEnt = 8;
 
 __global__ void k_gather_k_to_R(GatherArgs g) {
-  const int p = blockIdx.x;
-  const int s = blockIdx.y;
-  const int e0 = g.pair_first[p];
-  const int e1 = g.pair_first[p + 1];
-  const DevEntry E0 = g.ent[e0];
-  const int rows = g.row_off[E0.a + 1] - g.row_off[E0.a];
-  const int cols = g.row_off[E0.b + 1] - g.row_off[E0.b];
-  const int ro = g.pb ? E0.pa : E0.oa;
-  const int co = g.pb ? E0.pb : E0.ob;
-  const int blk = rows * cols;
-  const int idx = blockIdx.z * blockDim.x + threadIdx.x;
-  if (idx >= blk) return;
-  const int i = idx / cols, j = idx - i * cols;
-  const long long in_el = (long long)(ro + i) * g.ld + (co + j);
-  for (int eb = e0; eb < e1; eb += kGatherEnt) {
-    const int ne = min(kGatherEnt, e1 - eb);
-    // the entries of this chunk whose kept block holds (i, j)
-    unsigned need = 0;
+  const int a = blockIdx.x, s = blockIdx.y;
+  const int ro = g.row_off[a];
+  const int rows = g.row_off[a + 1] - ro;
+  const long long n_el = (long long)rows * g.ld;
+  for (long long x = threadIdx.x; x < n_el; x += blockDim.x) {
+    const int i = (int)(x / g.ld), col = (int)(x - (long long)i * g.ld);
+    const int b = g.col_atom[col];
+    const int j = col - g.row_off[b];
+    const int p = a * g.n_atoms + b;
+    const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
+    if (e0 == e1) continue;
+    const long long in_el = (long long)(ro + i) * g.ld + col;
+    for (int eb = e0; eb < e1; eb += kGatherEnt) {
+      const int ne = min(kGatherEnt, e1 - eb);
+      // the entries of this chunk whose kept block holds (i, j)
+      unsigned need = 0;
 #pragma unroll
-    for (int m = 0; m < kGatherEnt; ++m)
-      if (m < ne) {
-        const DevEntry& E = g.ent[eb + m];
-        if (i < (g.pb ? E.Ka : E.na) && j < (g.pb ? E.Kb : E.nb)) need |= 1u << m;
+      for (int m = 0; m < kGatherEnt; ++m)
+        if (m < ne) {
+          const DevEntry& E = g.ent[eb + m];
+          if (i < (g.pb ? E.Ka : E.na) && j < (g.pb ? E.Kb : E.nb)) need |= 1u << m;
+        }
+      if (!need) continue;
+      double2 acc[kGatherEnt];
+#pragma unroll
+      for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
+      for (int kk = 0; kk < g.n_k_in; ++kk) {
+        const int k = g.k_list ? g.k_list[kk] : kk;
+        double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
+        if (g.F_sub) {
+          double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
+          v.x -= w.x;
+          v.y -= w.y;
+        }
+        if (g.k_weight) {
+          const double wk = g.k_weight[kk];
+          v.x *= wk;
+          v.y *= wk;
+        }
+        if (g.real_only) {  // Re(conj(ph) v) only
+#pragma unroll
+          for (int m = 0; m < kGatherEnt; ++m)
+            if ((need >> m) & 1u) {
+              const double2 ph = g.phase[(long long)(eb + m) * g.n_k + k];
+              acc[m].x = fma(ph.x, v.x, fma(ph.y, v.y, acc[m].x));
+            }
+        } else {
+#pragma unroll
+          for (int m = 0; m < kGatherEnt; ++m)
+            if ((need >> m) & 1u) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
+        }
       }
-    if (!need) continue;
-    double2 acc[kGatherEnt];
 #pragma unroll
-    for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
-    for (int kk = 0; kk < g.n_k_in; ++kk) {
-      const int k = g.k_list ? g.k_list[kk] : kk;
-      double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
-      if (g.F_sub) {
-        double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
-        v.x -= w.x;
-        v.y -= w.y;
-      }
-      if (g.k_weight) {
-        const double wk = g.k_weight[kk];
-        v.x *= wk;
-        v.y *= wk;
-      }
-      if (g.real_only) {  // Re(conj(ph) v) only
-#pragma unroll
-        for (int m = 0; m < kGatherEnt; ++m)
-          if ((need >> m) & 1u) {
-            const double2 ph = g.phase[(long long)(eb + m) * g.n_k + k];
-            acc[m].x = fma(ph.x, v.x, fma(ph.y, v.y, acc[m].x));
-          }
-      } else {
-#pragma unroll
-        for (int m = 0; m < kGatherEnt; ++m)
-          if ((need >> m) & 1u) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < kGatherEnt; ++m) {
-      if ((need >> m) & 1u) {
-        const DevEntry& E = g.ent[eb + m];
-        const long long off = g.pb ? E.off_pb : E.off_orb;
-        const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
-        double2 r = make_double2(acc[m].x * g.scale, g.real_only ? 0.0 : acc[m].y * g.scale);
-        g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] = r;
+      for (int m = 0; m < kGatherEnt; ++m) {
+        if ((need >> m) & 1u) {
+          const DevEntry& E = g.ent[eb + m];
+          const long long off = g.pb ? E.off_pb : E.off_orb;
+          const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
+          double2 r = make_double2(acc[m].x * g.scale, g.real_only ? 0.0 : acc[m].y * g.scale);
+          g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] = r;
+        }
       }
     }
   }
@@ -108,58 +109,61 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
 
 // ---------------------------------------------------------------------------
 // R -> k scatter:  F_k[k][s][oa+i][ob+j] = sum_{e in (a,b)} ph[e][k] F_R[e][s][i][j]
-// grid: (ordered atom pair a*n_atoms+b, slice, element chunk)
+// grid: (row atom a, slice); the block writes the band of rows of atom a across every
+// column (zeros where the atom pair has no entry), consecutive threads on consecutive
+// columns.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter_R_to_k(ScatterArgs g) {
-  const int p = blockIdx.x;
-  const int s = blockIdx.y;
-  const int a = p / g.n_atoms, b = p - (p / g.n_atoms) * g.n_atoms;
-  const int ro = g.row_off[a], co = g.row_off[b];
-  const int rows = g.row_off[a + 1] - ro, cols = g.row_off[b + 1] - co;
-  const int blk = rows * cols;
-  const int idx = blockIdx.z * blockDim.x + threadIdx.x;
-  if (idx >= blk) return;
-  const int i = idx / cols, j = idx - i * cols;
-  const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
-  const long long out_el = (long long)(ro + i) * g.ld + (co + j);
-  for (int eb = e0; eb < e1 || eb == e0; eb += kGatherEnt) {
-    const int ne = max(0, min(kGatherEnt, e1 - eb));
-    double2 v[kGatherEnt];
+  const int a = blockIdx.x, s = blockIdx.y;
+  const int ro = g.row_off[a];
+  const int rows = g.row_off[a + 1] - ro;
+  const long long n_el = (long long)rows * g.ld;
+  for (long long x = threadIdx.x; x < n_el; x += blockDim.x) {
+    const int i = (int)(x / g.ld), col = (int)(x - (long long)i * g.ld);
+    const int b = g.col_atom[col];
+    const int j = col - g.row_off[b];
+    const int p = a * g.n_atoms + b;
+    const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
+    const long long out_el = (long long)(ro + i) * g.ld + col;
+    for (int eb = e0; eb < e1 || eb == e0; eb += kGatherEnt) {
+      const int ne = max(0, min(kGatherEnt, e1 - eb));
+      double2 v[kGatherEnt];
 #pragma unroll
-    for (int m = 0; m < kGatherEnt; ++m) {
-      v[m] = make_double2(0.0, 0.0);
-      if (m < ne) {
-        // an entry with a reduced product basis holds only the top-left K_a(e) x K_b(e)
-        const DevEntry& E = g.ent[eb + m];
-        const long long off = g.pb ? E.off_pb : E.off_orb;
-        const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
-        if (i < re && j < ce) v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+      for (int m = 0; m < kGatherEnt; ++m) {
+        v[m] = make_double2(0.0, 0.0);
+        if (m < ne) {
+          // an entry with a reduced product basis holds only the top-left K_a(e) x K_b(e)
+          const DevEntry& E = g.ent[eb + m];
+          const long long off = g.pb ? E.off_pb : E.off_orb;
+          const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+          if (i < re && j < ce) v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+        }
       }
+      for (int kk = 0; kk < g.n_k_out; ++kk) {
+        const int k = g.k_list ? g.k_list[kk] : kk;
+        double2 acc = make_double2(0.0, 0.0);
+        if (g.real_in) {  // ph * Re(v)
+#pragma unroll
+          for (int m = 0; m < kGatherEnt; ++m)
+            if (m < ne) acc = rfma(v[m].x, g.phase[(long long)(eb + m) * g.n_k + k], acc);
+        } else {
+#pragma unroll
+          for (int m = 0; m < kGatherEnt; ++m)
+            if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
+        }
+        acc.x *= g.coef;
+        acc.y *= g.coef;
+        double2* o = g.F_k + (long long)kk * g.k_stride + (long long)s * g.s_stride + out_el;
+        if (eb == e0) {
+          if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
+          *o = acc;
+        } else {
+          double2 t = *o;
+          *o = cadd(t, acc);
+        }
+      }
+      if (e1 <= e0) break;
     }
-    for (int kk = 0; kk < g.n_k_out; ++kk) {
-      const int k = g.k_list ? g.k_list[kk] : kk;
-      double2 acc = make_double2(0.0, 0.0);
-      if (g.real_in) {  // ph * Re(v)
-#pragma unroll
-        for (int m = 0; m < kGatherEnt; ++m)
-          if (m < ne) acc = rfma(v[m].x, g.phase[(long long)(eb + m) * g.n_k + k], acc);
-      } else {
-#pragma unroll
-        for (int m = 0; m < kGatherEnt; ++m)
-          if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
-      }
-      acc.x *= g.coef;
-      acc.y *= g.coef;
-      double2* o = g.F_k + (long long)kk * g.k_stride + (long long)s * g.s_stride + out_el;
-      if (eb == e0) {
-        if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
-        *o = acc;
-      } else {
-        double2 t = *o;
-        *o = cadd(t, acc);
-      }
-    }
-    if (e1 <= e0) break;
   }
 }
 

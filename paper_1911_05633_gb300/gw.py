@@ -35,6 +35,8 @@ EXPORTED = [
     "gw_transform_tau_iw", "gw_screened_W_iw", "gw_self_energy_tau", "gw_fourier_R_to_k", "gw_sync",
     "gw_status_string", "gw_last_error", "gw_fp_peak", "gw_screened_W_iw_noalloc",
     "gw_timing_enable", "gw_timing_read", "gw_timing_reset", "gw_transform_tau_iw_ex",
+    "gw_batch_create", "gw_batch_destroy", "gw_batch_query", "gw_batch_polarizability_tau",
+    "gw_batch_self_energy_tau", "gw_batch_tune", "gw_batch_sync",
 ]
 
 
@@ -68,7 +70,13 @@ class GwPlanInfo(C.Structure):
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
                 ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
                 ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int),
-                ("n_entries_far", C.c_int)]
+                ("n_entries_far", C.c_int), ("mixed_queue", C.c_int)]
+
+
+class GwBatchInfo(C.Structure):
+    _fields_ = [("n_plans", C.c_int), ("n_units_p", C.c_longlong), ("n_units_s", C.c_longlong),
+                ("groups_p", C.c_int), ("groups_s", C.c_int), ("kc_p", C.c_int), ("kc_s", C.c_int),
+                ("order_p", C.c_int), ("order_s", C.c_int), ("tuned", C.c_int)]
 
 
 class GwError(RuntimeError):
@@ -119,6 +127,14 @@ def load_library(path: str = LIB_PATH):
                                    C.POINTER(C.c_longlong)]
     lib.gw_timing_reset.argtypes = [vp]
     lib.gw_fp_peak.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    vpp = C.POINTER(C.c_void_p)
+    lib.gw_batch_create.argtypes = [vpp, C.c_int, C.POINTER(vp)]
+    lib.gw_batch_destroy.argtypes = [vp]
+    lib.gw_batch_query.argtypes = [vp, C.POINTER(GwBatchInfo)]
+    lib.gw_batch_polarizability_tau.argtypes = [vp, vpp, vpp, vp]
+    lib.gw_batch_self_energy_tau.argtypes = [vp, vpp, vpp, vpp, vp]
+    lib.gw_batch_tune.argtypes = [vp, vpp, vpp, vpp, vpp, C.c_int, vp]
+    lib.gw_batch_sync.argtypes = [vp, vp]
     lib.gw_status_string.argtypes = [C.c_int]
     lib.gw_status_string.restype = C.c_char_p
     lib.gw_last_error.restype = C.c_char_p
@@ -450,3 +466,73 @@ class Plan:
 
     def pack(self, blocks, kind: str) -> np.ndarray:
         return np.concatenate([np.ascontiguousarray(b).reshape(-1) for b in blocks]).astype(np.complex128)
+
+
+class Batch:
+    """A gw_batch_t: the GW_MIXED P and Sigma contractions of several plans (systems of
+    uneven sizes) in one persistent launch each."""
+
+    def __init__(self, plans: Sequence[Plan]):
+        lib = load_library()
+        self._lib = lib
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = C.c_void_p()
+        _check(lib.gw_batch_create(arr, len(self.plans), C.byref(h)), "gw_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gw_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        inf = GwBatchInfo()
+        _check(self._lib.gw_batch_query(self._h, C.byref(inf)), "gw_batch_query")
+        return {f: getattr(inf, f) for f, _ in GwBatchInfo._fields_}
+
+    def _ptrs(self, ts, kind, n_slices, name, create=False):
+        out = []
+        for p, t in zip(self.plans, ts if ts is not None else [None] * len(self.plans)):
+            out.append(p._buf(t, p.len(kind, n_slices(p)), name) if create else p._buf(t, p.len(kind, n_slices(p)),
+                                                                                       name))
+        return out, (C.c_void_p * len(out))(*[t.data_ptr() for t in out])
+
+    def _stream(self, stream):
+        return self.plans[0]._stream(stream)
+
+    def polarizability_tau(self, G_R, P_R=None, stream=None):
+        nt = lambda p: p.info["n_tau"]
+        G, gp = self._ptrs(G_R, "orb", nt, "G_R")
+        P, pp = self._ptrs(P_R, "pb", nt, "P_R", create=True)
+        _check(self._lib.gw_batch_polarizability_tau(self._h, gp, pp, self._stream(stream)),
+               "gw_batch_polarizability_tau")
+        return P
+
+    def self_energy_tau(self, G_R, Wt_R, Sig_R=None, stream=None):
+        nt = lambda p: p.info["n_tau"]
+        G, gp = self._ptrs(G_R, "orb", nt, "G_R")
+        W, wp = self._ptrs(Wt_R, "pb", nt, "Wt_R")
+        S, sp = self._ptrs(Sig_R, "orb", nt, "Sig_R", create=True)
+        _check(self._lib.gw_batch_self_energy_tau(self._h, gp, wp, sp, self._stream(stream)),
+               "gw_batch_self_energy_tau")
+        return S
+
+    def tune(self, G_R, P_R, Wt_R, Sig_R, reps: int = 3, stream=None):
+        nt = lambda p: p.info["n_tau"]
+        _, gp = self._ptrs(G_R, "orb", nt, "G_R")
+        _, pp = self._ptrs(P_R, "pb", nt, "P_R")
+        _, wp = self._ptrs(Wt_R, "pb", nt, "Wt_R")
+        _, sp = self._ptrs(Sig_R, "orb", nt, "Sig_R")
+        _check(self._lib.gw_batch_tune(self._h, gp, pp, wp, sp, int(reps), self._stream(stream)), "gw_batch_tune")
+        return self.info
+
+    def sync(self, stream=None):
+        _check(self._lib.gw_batch_sync(self._h, self._stream(stream)), "gw_batch_sync")

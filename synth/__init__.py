@@ -31,6 +31,9 @@ __all__ = [
     "Species",
     "SynthCell",
     "make_config",
+    "batch_family",
+    "perovskite_cell",
+    "f_rich_cell",
     "chain_cell",
     "mixed_species_cell",
     "tau_nodes",
@@ -461,6 +464,87 @@ def make_config(idx: int, atoms: Optional[int] = None, build: bool = True, **ove
     for k, v in over.items():
         setattr(cell, k, v)
     return cell.build() if build else cell
+
+
+# the layered perovskite of the large-cell runs (K2NiF4 type, as La2CuO4): body-centred
+# tetragonal conventional cell of 14 atoms, a = 7.14 bohr, c = 24.85 bohr
+_K2NIF4_14 = np.array([
+    [0.0, 0.0, 0.0], [0.5, 0.5, 0.5],                                        # transition-metal sites
+    [0.5, 0.0, 0.0], [0.0, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5],      # in-plane anions
+    [0.0, 0.0, 0.182], [0.0, 0.0, 0.818], [0.5, 0.5, 0.318], [0.5, 0.5, 0.682],  # apical anions
+    [0.0, 0.0, 0.362], [0.0, 0.0, 0.638], [0.5, 0.5, 0.138], [0.5, 0.5, 0.862],  # A-site cations
+])
+_K2NIF4_SPECIES = np.array([0, 0, 2, 2, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1], np.int32)
+
+
+def perovskite_cell(mult=(2, 2, 1), kmesh=(2, 2, 2), n_tau: int = 48, cutoff: float = 12.0, seed: int = 3000,
+                    beta: float = 1000.0) -> SynthCell:
+    """Layered perovskite-like cell (K2NiF4 type, the structure of La2CuO4): 14 atoms per
+    conventional cell, `mult` cells (2x2x1: 56 atoms).  Species: transition-metal sites with
+    14 orbitals (s, p, d and a second d-like shell) and 96 product functions, A-site cations
+    with 9 orbitals and 64, anions with 9 orbitals and 40."""
+    m = np.array(mult)
+    frac, spec = [], []
+    for sft in np.ndindex(*m):
+        for f, sp in zip(_K2NIF4_14, _K2NIF4_SPECIES):
+            frac.append((f + np.array(sft)) / m)
+            spec.append(sp)
+    lat = np.diag([7.14 * m[0], 7.14 * m[1], 24.85 * m[2]])
+    sp = [Species("tm", 14, 96, None), Species("a", 9, 64, None), Species("x", 9, 40, None)]
+    n = len(frac)
+    return SynthCell(f"perovskite{n}-n14/9-K96/64/40", lat, np.array(frac), np.array(spec, np.int32), sp,
+                     tuple(kmesh), beta, n_tau, cutoff, seed=seed, gap=None, hop_cutoff=cutoff).build()
+
+
+def f_rich_cell(kmesh=(2, 2, 2), n_tau: int = 48, cutoff: float = 10.0, seed: int = 4000,
+                beta: float = 1000.0) -> SynthCell:
+    """Cubic cell of 64 atoms rich in f orbitals (as the SmB6 runs): 8 heavy sites on a 2x2x2
+    simple-cubic sublattice with 16 orbitals (s, p, d and f shells: 1 + 3 + 5 + 7) and 112
+    product functions, and 56 light atoms with 9 orbitals and 48 (an octahedron of six around
+    each cube centre and eight on the x-edge midpoints of the heavy sublattice)."""
+    a = 7.8  # bohr per heavy-atom cube
+    frac = []
+    for c in np.ndindex(2, 2, 2):
+        frac.append(np.array(c) / 2.0)
+    spec = [0] * 8
+    u = 0.2
+    for c in np.ndindex(2, 2, 2):
+        ctr = (np.array(c) + 0.5) / 2.0
+        for d in np.vstack([np.eye(3), -np.eye(3)]):
+            frac.append(ctr + u * d / 2.0)
+            spec.append(1)
+    for c in np.ndindex(2, 2, 2):  # the x-edge midpoints of the heavy sublattice
+        frac.append(np.array([0.25 + c[0] / 2.0, c[1] / 2.0, c[2] / 2.0]))
+        spec.append(1)
+    frac = np.mod(np.array(frac), 1.0)
+    lat = np.eye(3) * 2 * a
+    sp = [Species("f", 16, 112, None), Species("light", 9, 48, None)]
+    return SynthCell("frich64-n16/9-K112/48", lat, frac, np.array(spec, np.int32), sp, tuple(kmesh), beta, n_tau,
+                     cutoff, seed=seed, gap=None, hop_cutoff=cutoff).build()
+
+
+# the batch of uneven systems: (diamond multiples, k-mesh, cutoff) and the perovskite
+_BATCH3 = [((1, 1, 1), (4, 4, 4), 12.0), ((1, 1, 1), (3, 3, 3), 10.0), ((2, 1, 1), (2, 2, 2), 12.0),
+           ((2, 1, 1), (3, 3, 3), 14.0), ((3, 1, 1), (2, 2, 2), 10.0), ((1, 1, 1), (4, 4, 4), 14.0),
+           ((2, 2, 1), (2, 2, 2), 12.0), ((3, 1, 1), (3, 3, 3), 12.0), ((4, 1, 1), (2, 2, 2), 10.0),
+           ((2, 1, 1), (4, 4, 4), 10.0), ((5, 1, 1), (2, 2, 2), 12.0), ((3, 2, 1), (2, 2, 2), 10.0),
+           ((2, 2, 1), (3, 3, 3), 14.0), ((6, 1, 1), (2, 2, 2), 10.0), ((7, 1, 1), (2, 2, 2), 12.0)]
+
+
+def batch_family(n: int = 16, n_tau: int = 48) -> List[SynthCell]:
+    """The batch of uneven systems: 15 diamond-like supercells of 8 to 56 atoms (9 orbitals,
+    48 product functions per atom; k-meshes 2x2x2 to 4x4x4, cutoffs 10 to 14 bohr) and the
+    56-atom layered perovskite-like cell (perovskite_cell).  Seeds 3000 + index."""
+    cells = []
+    for i, (mult, km, rc) in enumerate(_BATCH3[:max(0, n - 1)]):
+        lat, frac = _diamond_supercell(mult)
+        sp = [Species("spd", 9, 48, None)]
+        cells.append(SynthCell(f"diamond{len(frac)}-n9-K48-k{km[0]}-rc{rc:g}", lat, frac,
+                               np.zeros(len(frac), np.int32), sp, km, 1000.0, n_tau, rc, seed=3000 + i, gap=None,
+                               hop_cutoff=rc).build())
+    if n >= 16:
+        cells.append(perovskite_cell(n_tau=n_tau, seed=3015))
+    return cells
 
 
 def with_far_basis(cell: SynthCell, r_b: float, n_prod_far: Sequence[int]) -> SynthCell:
