@@ -72,6 +72,8 @@ def parse():
                     help="radius of sphere B (bohr): pairs beyond it keep --n-prod-far product functions (Sec. 2)")
     ap.add_argument("--n-prod-far", type=int, nargs="+", default=None,
                     help="product functions per species kept by pairs beyond sphere B")
+    ap.add_argument("--batch", action="store_true",
+                    help="only the batched uneven systems (the 16-system family in one launch per contraction)")
     ap.add_argument("--serve", action="store_true",
                     help="Poisson request stream of whole GW iterations: p50/p99 latency")
     ap.add_argument("--scaling", type=int, nargs="*", default=None,
@@ -1017,6 +1019,114 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# --------------------------------------------------------------------------------------
+# batched uneven systems (configuration 3): one persistent launch per contraction
+# --------------------------------------------------------------------------------------
+
+def run_batch3(args, local, peaks):
+    """The mixed P and Sigma contractions of the 16-system batch family (15 diamond-like
+    supercells of 8 to 56 atoms with different meshes and cutoffs, and the 56-atom layered
+    perovskite-like cell) as one persistent launch each (gw_batch_*), autotuned, captured in
+    a CUDA graph and replayed; beside it the same contractions launched system by system.
+    Inputs: G(R, tau) from each cell's G(k, tau), W~(R, tau) seeded.  Checks that every
+    system's result is the same bits in the batch and alone."""
+    import torch
+    import synth
+    from paper_1911_05633_gb300 import gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_setup = time.perf_counter()
+    cells = synth.batch_family()
+    plans, G, W, P, S = [], [], [], [], []
+    gen = torch.Generator(device=dev).manual_seed(3)
+    for c in cells:
+        p = gw.Plan.from_cell(c, device=local)
+        nt = p.info["n_tau"]
+        Gk = torch.from_numpy(c.green_k_tau().reshape(-1)).to(dev)
+        G.append(p.green_k_to_R(Gk))
+        del Gk
+        W.append(torch.randn(p.len("pb", nt), dtype=torch.complex128, device=dev, generator=gen))
+        P.append(torch.empty(p.len("pb", nt), dtype=torch.complex128, device=dev))
+        S.append(torch.empty(p.len("orb", nt), dtype=torch.complex128, device=dev))
+        plans.append(p)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    b = gw.Batch(plans)
+    stream = torch.cuda.Stream(device=local)
+    ss = stream.cuda_stream
+    t0 = time.perf_counter()
+    info = b.tune(G, P, W, S, reps=2, stream=ss)
+    t_tune = time.perf_counter() - t0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def batched():
+        b.polarizability_tau(G, P, stream=ss)
+        b.self_energy_tau(G, W, S, stream=ss)
+
+    def alone(outP, outS):
+        for p, g, w, op, os_ in zip(plans, G, W, outP, outS):
+            p.polarizability_tau(g, op, precision="mixed", stream=ss)
+            p.self_energy_tau(g, w, Sig_R=os_, precision="mixed", stream=ss)
+
+    with torch.cuda.stream(stream):
+        batched()
+    b.sync(stream=ss)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batched()
+
+    def time_it(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for a, e in ev:
+                flush_l2(flush)
+                a.record(stream)
+                fn()
+                e.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(e) for a, e in ev]))
+
+    ms_batch = time_it(graph.replay)
+    P2 = [torch.empty_like(x) for x in P]
+    S2 = [torch.empty_like(x) for x in S]
+    ms_alone = time_it(lambda: alone(P2, S2))
+    b.sync(stream=ss)
+    same = all(torch.equal(x, y) for x, y in zip(P + S, P2 + S2))
+    # algorithmic work and bytes of both contractions over every system
+    fl = byt = 0.0
+    for c, p in zip(cells, plans):
+        kd = pb_dims(p)
+        for row in ("P", "S"):
+            w = row_work(c, p.entries, kd, row, p.info["c_symmetric"])
+            fl += w[0]
+            byt += w[1]
+    hbm = peaks.get("hbm_gbs")
+    out = {"workload": f"{len(cells)} systems of {min(c.n_atoms for c in cells)} to {max(c.n_atoms for c in cells)} atoms "
+                       f"({sum(c.n_atoms for c in cells)} atoms, {sum(len(p.entries) for p in plans)} pair entries, "
+                       f"48 tau): diamond-like supercells (n 9, K 48) and the layered perovskite-like cell "
+                       f"(n 14/9/9, K 96/64/40)",
+           "precision": "mixed", "ms_batched_graph": round(ms_batch, 4), "ms_system_by_system": round(ms_alone, 4),
+           "speedup_batched": round(ms_alone / ms_batch, 3),
+           "contraction_tflops": round(fl / (ms_batch * 1e-3) / 1e12, 4),
+           "roofline": {"bound": "hbm", "achieved": round(byt / (ms_batch * 1e-3) / 1e9, 2), "peak": hbm,
+                        "unit": "GB/s", "frac": round(byt / (ms_batch * 1e-3) / 1e9 / hbm, 4) if hbm else None,
+                        "algorithmic_bytes": byt, "note": "P and Sigma launches together, algorithmic bytes of both"},
+           "tuned": {k: info[k] for k in ("groups_p", "groups_s", "kc_p", "kc_s", "order_p", "order_s")},
+           "tune_s": round(t_tune, 2), "setup_s": round(t_setup, 1), "batched_equals_alone_bitwise": bool(same),
+           "units": {"P": info["n_units_p"], "Sigma": info["n_units_s"]}, "steps": args.steps,
+           "l2": "256 MB buffer written before each timed step"}
+    b.close()
+    del graph, G, W, P, S, P2, S2
+    for p in plans:
+        p.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_scaling(args, local):
     """P + Sigma rows (a1-a4 and a6-a8; the W solve is timed apart by the metric) of the
     diamond supercell series with 9 orbitals and 64 product functions per atom, a 2x2x2
@@ -1097,45 +1207,59 @@ def run_scaling(args, local):
 
 
 def run_serve(args, local):
-    """Serving: a Poisson stream of whole GW iterations (G -> P -> W -> Sigma -> Dyson -> G)
-    on four systems of different sizes, continuous batching across systems
-    (paper_1911_05633_gb300.serve), the arrival rate swept to saturation.  Per rate:
-    p50 / p99 latency (arrival to completion) and throughput."""
+    """Serving (paper_1911_05633_gb300.serve): a Poisson stream of requests over 20 systems
+    of different sizes under a device-memory cap below their total -- P/Sigma evaluations on
+    the 16-system batch family and two 64-atom f-rich cells (G and W~ resident; a whole
+    iteration there would need the W solve at N_PB ~ 3000-3600), whole iterations (W solve,
+    chemical potential, Dyson step) on two small cells -- the arrival rate swept to
+    saturation.  Per rate: p50 / p99 latency (arrival to completion), throughput and the
+    systems brought in."""
     import torch
     import synth
-    from paper_1911_05633_gb300.serve import Server, System, latency_stats, poisson_arrivals
+    from paper_1911_05633_gb300.serve import Server, SystemSpec, latency_stats, poisson_arrivals
     torch.cuda.set_device(local)
-    cells = {"sc2-n4-K8": synth.make_config(0), "mixed2-n4/5-K8/19": synth.mixed_species_cell(),
-             "diamond8-cut5": synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
-             "diamond8-cut5-far": synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
-                                                       4.0, [24])}
-    systems = {n: System(n, c, device=local, precision=args.precision) for n, c in cells.items()}
-    names = list(systems)
-    server = Server(systems, mem_cap_bytes=sum(s.footprint for s in systems.values()))
-    for _ in range(max(1, args.warmup)):  # warm-up: every system once
-        server.run([(0.0, n) for n in names])
+    prec = args.precision
+    specs = {}
+    for i, c in enumerate(synth.batch_family()):
+        specs[f"b{i:02d}-{c.name}"] = SystemSpec(f"b{i:02d}", c, mode="psigma", precision=prec, w_seed=i)
+    for i in range(2):
+        c = synth.f_rich_cell(seed=4000 + i)
+        specs[f"f{i}-{c.name}"] = SystemSpec(f"f{i}", c, mode="psigma", precision=prec, w_seed=100 + i)
+    for n, c in (("it-sc2", synth.make_config(0)),
+                 ("it-diamond8-cut5", synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)))):
+        specs[n] = SystemSpec(n, c, mode="iteration", precision=prec, workspace_bytes=1 << 30)
+    t0 = time.perf_counter()
+    for sp in specs.values():
+        sp.prepare()
+    t_prep = time.perf_counter() - t0
+    total = sum(sp.footprint for sp in specs.values())
+    cap = int(0.4 * total)
+    cap = max(cap, 2 * max(sp.footprint for sp in specs.values()))
+    names = list(specs)
+    server = Server(specs, mem_cap_bytes=cap, device=local)
     alone = {}
-    for n in names:  # service time of each system alone
-        lat = [server.run([(0.0, n)])[0].latency for _ in range(3)]
+    for n in names:  # service time of each system alone, brought in and resident
+        server.run([(0.0, n)])
+        lat = [server.run([(0.0, n)])[0].latency for _ in range(2)]
         alone[n] = round(1e3 * float(np.median(lat)), 3)
     mean_service = float(np.mean(list(alone.values()))) / 1e3
     series = []
-    for f in (0.25, 0.5, 1.0, 2.0, 4.0):  # offered load relative to one system at a time
+    for f in (0.5, 1.0, 2.0, 4.0):  # offered load relative to one system at a time
         rate = f / mean_service
-        for s in systems.values():
-            s.reset()
         reqs = server.run(poisson_arrivals(rate, 40 * max(1, args.steps // 5), names, seed=int(f * 100)))
         series.append({"offered_per_s": round(rate, 2), "load_vs_serial": f, **latency_stats(reqs)})
-    for s in systems.values():
-        s.close()
-    return {"metric": "serve p50/p99 latency of whole GW iterations (continuous batching)", "unit": "ms",
-            "precision": args.precision, "data": "synthetic",
-            "config": {"systems": {n: {"atoms": c.n_atoms, "orbitals": c.n_orb_total, "n_pb": c.n_pb_total,
-                                       "k": int(np.prod(c.kmesh)), "tau": c.n_tau} for n, c in cells.items()},
-                       "request": "one iteration: G(k,tau) -> G(R) -> P -> P(i nu) -> W~ -> W~(tau) -> Sigma, "
-                                  "Sigma_x -> Sigma(k, i w) -> Dyson -> G(k,tau)",
-                       "admission": "arrival order; a system runs one request at a time; memory cap = all systems"},
-            "alone_ms": alone, "series": series}
+    evictions = sum(1 for e in server.log if e[1] == "evict")
+    server.close()
+    return {"metric": "serve p50/p99 latency of P/Sigma evaluations and whole GW iterations (continuous batching)",
+            "unit": "ms", "precision": prec, "data": "synthetic",
+            "config": {"systems": {n: {"atoms": sp.cell.n_atoms, "orbitals": sp.cell.n_orb_total,
+                                       "n_pb": sp.cell.n_pb_total, "k": int(np.prod(sp.cell.kmesh)),
+                                       "tau": sp.cell.n_tau, "request": sp.mode,
+                                       "footprint_GB": round(sp.footprint / 1e9, 2)} for n, sp in specs.items()},
+                       "mem_cap_GB": round(cap / 1e9, 1), "sum_of_footprints_GB": round(total / 1e9, 1),
+                       "admission": "arrival order; one request per system at a time; a system not resident is "
+                                    "brought in on admission, idle residents evicted least recently used first"},
+            "prepare_s": round(t_prep, 1), "alone_ms": alone, "series": series, "evictions": evictions}
 
 
 def main():
@@ -1148,6 +1272,14 @@ def main():
     if args.scaling is not None:
         if rank == 0:
             print(json.dumps(run_scaling(args, local)), flush=True)
+        return
+    if args.batch:
+        if rank == 0:
+            try:
+                peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            except Exception:
+                peaks = {}
+            print(json.dumps(run_batch3(args, local, peaks)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
@@ -1170,6 +1302,11 @@ def main():
     if not args.no_extra:
         full, _ = run_full(args, local)
         out["full_sweep_8_atoms"] = full
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            peaks = {}
+        out["batched_uneven_systems"] = run_batch3(args, local, peaks)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             orc = OracleRows(cell)

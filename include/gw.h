@@ -22,10 +22,11 @@
  * of rows_e * cols_e returned by gw_plan_offsets():
  *   GW_BLOCK_ORB: rows_e = n_a, cols_e = n_b   (G, Sigma)
  *   GW_BLOCK_PB : rows_e = K_a(e), cols_e = K_b(e)   (P, W~, v)
- * K_a(e) is the product-basis size of atom a for entry e: n_prod of its species,
- * or n_prod_far for an entry beyond the radius r_b of sphere B (the reduced
- * basis of distant pairs, Sec. 2, Fig. 2); those entries keep the FIRST
- * n_prod_far product functions of each atom.  gw_plan_entry_dims() returns the
+ * K_a(e) is the product-basis size of atom a for entry e at the entry's level of
+ * Sec. 2, Fig. 2: n_prod of its species when both arguments are in one sphere
+ * (the onsite entry, sphere A), n_prod_near for two spheres within the radius r_b
+ * of sphere B, n_prod_far beyond it; an entry keeps the FIRST K_a(e) product
+ * functions of each atom.  gw_plan_entry_dims() returns the
  * per-entry shapes.
  * Dense k-space buffers are [N_k][n_slices][N][N] with N = total orbitals
  * (ORB) or total product functions (PB), atoms in order.
@@ -81,6 +82,10 @@ typedef struct {
   const int* n_prod_far;  /* host [n_species], 1..n_prod, or NULL: product functions kept for
                              pair entries beyond gw_options.r_b (Sec. 2, the pairs between
                              spheres B and C); NULL keeps n_prod for every entry */
+  const int* n_prod_near; /* host [n_species], n_prod_far..n_prod, or NULL (n_prod): product
+                             functions kept for the entries of two distinct spheres within r_b
+                             (sphere B); the onsite entries (one sphere, sphere A) keep n_prod.
+                             Read only together with n_prod_far and r_b > 0 */
 } gw_basis;
 
 /* Imaginary-time nodes and sampled Matsubara indices (Appendix A grid).
@@ -112,7 +117,8 @@ typedef struct {
   double r_b;             /* radius of sphere B in bohr (Sec. 2, Fig. 2): an entry whose
                              minimum-image distance |R + t_b - t_a| exceeds r_b by more than
                              1e-9 bohr^2 in the square keeps n_prod_far product functions per
-                             atom; <= 0 (or n_prod_far NULL): every entry keeps n_prod */
+                             atom, an entry of two spheres within it n_prod_near, an onsite
+                             entry n_prod; <= 0 (or n_prod_far NULL): every entry keeps n_prod */
 } gw_options;
 
 typedef struct {
@@ -136,6 +142,8 @@ typedef struct {
                                  tau -> i nu of the product-basis layout by FP64-accurate
                                  tensor-core products (device plans) */
   int n_entries_far;          /* entries with the reduced product basis (beyond r_b) */
+  int n_entries_near;         /* entries of two distinct spheres within r_b that keep n_prod_near
+                                 (0 when n_prod_near is NULL) */
   int mixed_queue;            /* GW_MIXED contractions as persistent tensor-core kernels over a queue
                                  of (entry, tau) units: bit 0 P, bit 1 Sigma (device plans) */
 } gw_plan_info;
@@ -233,7 +241,8 @@ gw_status gw_screened_W_iw(gw_plan_t plan, const void* P_R_iw, const void* v_q,
  *      W~_{aK,bK'}(R, tau_i) C^b_{K';L' L'''}                     (Eq. S_MM)
  * and, when v_R and Sigx_R are both non-NULL, the static exchange of the same
  * contraction with W~ -> v and G(tau) -> -G(beta-) (the rule after Eq. P_II):
- *   Sigx = + sum C^a G(R, beta-) v(R) C^b.
+ *   Sigx = + sum C^a G(R, beta-) v(R) C^b
+ * (in the precision `prec` asks for, like the dynamic part).
  * G_R: ORB, N_tau slices; Wt_R: PB, N_tau slices; v_R: PB, 1 slice;
  * Sig_R: ORB, N_tau slices; Sigx_R: ORB, 1 slice. */
 gw_status gw_self_energy_tau(gw_plan_t plan, const void* G_R, const void* Wt_R,

@@ -11,10 +11,11 @@ Every function follows one statement of the paper, cited in its docstring:
 * Sec. 2, "basic approximation" (Fig. 1): two-point functions F^R_{rr'} are kept
   only for |R + r - r'| <= R_max, and the k-mesh must be at least the number of
   cells the R_max sphere encloses or crosses.  -> ``kmesh_rule``, ``pair_list``
-* Sec. 2, the reduced basis of distant pairs (Fig. 2): a pair farther apart than
-  the radius of sphere B keeps a smaller product basis (the first n_prod_far
-  functions of each atom here) -> ``entry_far``, ``entry_pb_dims``; every
-  product-basis function below takes its block shapes from its inputs
+* Sec. 2, the three product-basis levels (Fig. 2): both arguments in one sphere
+  (A) keep the whole basis, pairs within the radius of sphere B a smaller one, pairs
+  beyond it the smallest (the first n_prod_near / n_prod_far functions of each atom
+  here) -> ``entry_tier``, ``entry_far``, ``entry_pb_dims``; every product-basis
+  function below takes its block shapes from its inputs
 * Sec. 2, transformations between R and k spaces over the kept pairs
   -> ``fourier_k_to_R``, ``fourier_R_to_k``
 * Eq. P_MM with the sign and the tau pairing of Eq. P_II -> ``polarizability_R``
@@ -55,6 +56,7 @@ from numpy.polynomial.legendre import leggauss
 __all__ = [
     "kmesh_rule",
     "pair_list",
+    "entry_tier",
     "entry_far",
     "entry_pb_dims",
     "green0_k_tau",
@@ -175,29 +177,43 @@ def _occ_factor(xi: np.ndarray, t: float, beta: float) -> np.ndarray:
 # Sec. 2: R <-> k transforms restricted to the kept entries
 # ----------------------------------------------------------------------------
 
-def entry_far(lattice: np.ndarray, frac: np.ndarray, entries: np.ndarray, r_b: float) -> np.ndarray:
-    """Entries beyond sphere B (Sec. 2, Fig. 2): the minimum-image distance
-    |R + t_b - t_a| of the entry exceeds r_b (its square by more than 1e-9 bohr^2).
-    r_b <= 0: no entry is far."""
+def entry_tier(lattice: np.ndarray, frac: np.ndarray, entries: np.ndarray, r_b: float) -> np.ndarray:
+    """The product-basis level of each entry (Sec. 2, Fig. 2, three levels): 0 when both
+    arguments are in the same sphere (a = b and minimum-image distance 0: sphere A), 1 when
+    the distance |R + t_b - t_a| is within the radius r_b of sphere B (its square at most
+    r_b^2 + 1e-9 bohr^2), 2 beyond it (up to the cutoff, sphere C).  r_b <= 0: no level 2."""
     A = np.asarray(lattice, dtype=np.float64)
     frac = np.asarray(frac, dtype=np.float64)
-    far = np.zeros(len(entries), dtype=bool)
-    if r_b <= 0.0:
-        return far
+    tier = np.zeros(len(entries), dtype=np.int64)
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
         x = (np.asarray(row[5:8], dtype=np.float64) + frac[b] - frac[a]) @ A
-        far[e] = float(x @ x) > r_b * r_b + 1e-9
-    return far
+        d2 = float(x @ x)
+        if a == b and d2 <= 1e-9:
+            tier[e] = 0
+        elif r_b > 0.0 and d2 > r_b * r_b + 1e-9:
+            tier[e] = 2
+        else:
+            tier[e] = 1
+    return tier
 
 
-def entry_pb_dims(entries: np.ndarray, far: np.ndarray, n_prod_atom, n_prod_far_atom) -> List[Tuple[int, int]]:
-    """(K_a(e), K_b(e)) per entry: the full product basis of each atom, or its reduced
-    size n_prod_far for an entry beyond sphere B (the first functions are kept)."""
+def entry_far(lattice: np.ndarray, frac: np.ndarray, entries: np.ndarray, r_b: float) -> np.ndarray:
+    """Entries beyond sphere B (level 2 of entry_tier)."""
+    return entry_tier(lattice, frac, entries, r_b) == 2
+
+
+def entry_pb_dims(entries: np.ndarray, tier, n_prod_atom, n_prod_far_atom, n_prod_near_atom=None) \
+        -> List[Tuple[int, int]]:
+    """(K_a(e), K_b(e)) per entry: the first functions of each atom's product basis kept at
+    the entry's level -- all of them in sphere A, n_prod_near within sphere B (default: all),
+    n_prod_far beyond it.  `tier` is the level per entry (entry_tier) or a boolean "far"."""
+    near = n_prod_atom if n_prod_near_atom is None else n_prod_near_atom
     out = []
     for e, row in enumerate(entries):
         a, b = int(row[0]), int(row[1])
-        src = n_prod_far_atom if far[e] else n_prod_atom
+        t = int(tier[e]) if np.asarray(tier).dtype != bool else (2 if tier[e] else 0)
+        src = (n_prod_atom, near, n_prod_far_atom)[t]
         out.append((int(src[a]), int(src[b])))
     return out
 
@@ -628,13 +644,15 @@ class OracleSystem:
         self.B_fwd = fourier_matrix(cell.beta, self.tau, cell.nu_idx, "B")
         self.F_inv = inverse_matrix(self.F_fwd)
         self.B_inv = inverse_matrix(self.B_fwd)
-        # the reduced product basis beyond sphere B (Sec. 2, Fig. 2), when the cell has one
+        # the product-basis levels of Sec. 2, Fig. 2 (spheres A, B, C), when the cell has them
         r_b = float(getattr(cell, "r_b", 0.0) or 0.0)
-        self.far = entry_far(cell.lattice, cell.frac, self.entries, r_b)
+        self.tier = entry_tier(cell.lattice, cell.frac, self.entries, r_b)
+        self.far = self.tier == 2
         n_full = [len(C) for C in self.C_atom]
-        n_far = [cell.species[s].n_prod_far or cell.species[s].n_prod for s in cell.species_of_atom] \
-            if r_b > 0 else n_full
-        self.kdims = entry_pb_dims(self.entries, self.far, n_full, n_far)
+        sp = [cell.species[s] for s in cell.species_of_atom]
+        n_far = [x.n_prod_far or x.n_prod for x in sp] if r_b > 0 else n_full
+        n_near = [getattr(x, "n_prod_near", None) or x.n_prod for x in sp] if r_b > 0 else n_full
+        self.kdims = entry_pb_dims(self.entries, self.tier, n_full, n_far, n_near)
 
     def v_R(self, v_class: np.ndarray) -> List[np.ndarray]:
         out = []

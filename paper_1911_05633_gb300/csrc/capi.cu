@@ -74,7 +74,8 @@ struct gw_plan_s {
   bool contract_p = false, contract_s = false;
   gw::CUnit* d_unitsP = nullptr;
   gw::CUnit* d_unitsS = nullptr;
-  int n_unitsP = 0, n_unitsS = 0;
+  gw::CUnit* d_unitsX = nullptr;  // the exchange term: one node per entry
+  int n_unitsP = 0, n_unitsS = 0, n_unitsX = 0;
   int* d_counter = nullptr;
   bool sigma_tensor = false;  // FP64 Sigma stage A by tensor-core digit products
   gw::OzSigma oz;
@@ -140,7 +141,7 @@ void free_device(gw_plan_s* p) {
                   p->d_pb_atom, p->d_phase,
                   p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_mirror, p->d_Tb_inv, p->d_qh, p->d_qw,
                   p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_lo, p->t_R, p->t_PX, p->t_Asl,
-                  p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_counter};
+                  p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_unitsX, p->d_counter};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
@@ -482,6 +483,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     p->n_unitsS = (int)uS.size();
     if ((st = upload(&p->d_unitsP, uP.data(), uP.size() * sizeof(gw::CUnit))) != GW_OK) return fail(st);
     if ((st = upload(&p->d_unitsS, uS.data(), uS.size() * sizeof(gw::CUnit))) != GW_OK) return fail(st);
+    const std::vector<gw::CUnit> uX = gw::contract_units(h, 0, true, 1);
+    p->n_unitsX = (int)uX.size();
+    if ((st = upload(&p->d_unitsX, uX.data(), uX.size() * sizeof(gw::CUnit))) != GW_OK) return fail(st);
     if ((st = upload(&p->d_counter, nullptr, 16)) != GW_OK) return fail(st);
     gw::set_last_error("");
   }
@@ -528,6 +532,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->len_orb = h.off_orb.back();
   info->len_pb = h.off_pb.back();
   info->n_entries_far = h.n_far;
+  info->n_entries_near = h.n_near;
   info->workspace_bytes = p->ws_bytes;
   info->nu_chunk = p->nu_chunk;
   info->cond_fermion = h.cond_f;
@@ -683,6 +688,9 @@ static gw::CSys contract_sys(const gw_plan_s* p, const double2* G, const double2
   s.W = W;
   s.out = out;
   s.n_tau = p->h.n_tau;
+  s.g_slices = s.w_slices = s.out_slices = p->h.n_tau;
+  s.g_fixed = -1;
+  s.sign = -1.0;
   s.spin = p->h.spin;
   s.mirror = p->h.c_symmetric;
   return s;
@@ -803,8 +811,19 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
     set_last_error("unknown precision");
     return GW_ERR_ARG;
   }
+  if (v_R && Sigx_R && prec == GW_MIXED && p->contract_s) {
+    // exchange: W~ -> v, G(tau) -> -G(beta-): +C G(beta-) v C, one node per entry through the
+    // same queue kernel (reduced precision like the dynamic part)
+    gw::CBatch b{};
+    b.n = 1;
+    b.s[0] = contract_sys(p, (const double2*)G_R, (const double2*)v_R, (double2*)Sigx_R);
+    b.s[0].w_slices = b.s[0].out_slices = 1;
+    b.s[0].g_fixed = h.n_tau - 1;
+    b.s[0].sign = +1.0;
+    return gw::contract_launch(true, p->cfgS, b, p->d_unitsX, p->n_unitsX, p->d_counter, p->d_status, S(stream));
+  }
   if (v_R && Sigx_R) {
-    // exchange: W~ -> v, G(tau) -> -G(beta-): +C G(beta-) v C, always in FP64
+    // exchange: W~ -> v, G(tau) -> -G(beta-): +C G(beta-) v C in FP64
     gw::ContractArgs g{};
     g.ent = p->d_ent;
     g.C = p->d_C;

@@ -25,12 +25,17 @@ struct CSys {
   const int* cp_off;         // [n_species] first float of species s in Cp
   const int* cp_ld;          // [n_species] K stride of species s (n_prod padded to a multiple of 4)
   const uint16_t* Bp;        // BF16 three-term planes of the dense-stage B operand, per (species, size)
-  const long long* bp_off;   // [2 n_species] first element of the plane set of (species, reduced size)
+  const long long* bp_off;   // [3 n_species] first element of the plane set of (species, level)
   const int* species;        // [n_atoms]
   const double2* G;          // G(R, tau): orbital entry layout, n_tau slices
   const double2* W;          // W~(R, tau): product entry layout, n_tau slices (Sigma only)
   double2* out;              // P (product layout) or Sigma (orbital layout), n_tau slices
   int n_tau;
+  // Sigma: slices of G, W~ and the output per entry, a fixed G slice (-1: the unit's node)
+  // and the sign of the result (-1: Eq. S_MM; +1: the exchange term with W~ -> v and
+  // G(tau) -> G(beta-), one slice each of W and of the output)
+  int g_slices, w_slices, out_slices, g_fixed;
+  double sign;
   int spin;                  // P: spin degeneracy s
   int mirror;                // P: the nodes i < ceil(n_tau/2) are computed, the node n_tau-1-i written
                              // as the conjugate (C symmetric in (L, L''))
@@ -70,9 +75,10 @@ struct CTables {
 gw_status ctables_init(CTables& t, const HostPlan& h);
 void ctables_free(CTables& t);
 
-// The queue of one system's units for P (computed nodes only) or Sigma, grouped by
-// (species a, species b, reduced size) so that consecutive units share their B operand.
-std::vector<CUnit> contract_units(const HostPlan& h, int sys, bool sigma);
+// The queue of one system's units for P (computed nodes only) or Sigma (n_nodes nodes:
+// N_tau, or 1 for the exchange term), grouped by (species a, species b, reduced size) so
+// that consecutive units share their B operand.
+std::vector<CUnit> contract_units(const HostPlan& h, int sys, bool sigma, int n_nodes = -1);
 
 // Launch configuration (per batch): reduction chunk, accumulators, thread groups and
 // dynamic shared memory, from the largest shapes of the batch.

@@ -24,7 +24,7 @@ struct DevEntry {
   long long off_orb;   // prefix sum of na*nb over earlier entries
   long long off_pb;    // prefix sum of Ka*Kb over earlier entries
   int mirror;          // entry index of (b, a, -R)
-  int far;             // 1: beyond sphere B, Ka and Kb are the reduced product-basis sizes
+  int tier;            // product-basis level (Sec. 2, Fig. 2): 0 one sphere, 1 within sphere B, 2 beyond
 };
 
 // Host-side tables of a plan (no CUDA types; built by build_host_plan()).
@@ -36,6 +36,7 @@ struct HostPlan {
   int n_species = 0;
   std::vector<int> n_orb, n_prod;
   std::vector<int> n_prod_far;          // per species: product functions kept beyond r_b
+  std::vector<int> n_prod_near;         // per species: kept by two spheres within r_b
   double r_b = 0;                       // radius of sphere B (<= 0: no reduced tier)
   std::vector<std::vector<double>> C;  // per species [K][n][n]
   int kmesh[3];
@@ -52,8 +53,9 @@ struct HostPlan {
   std::vector<int64_t> entries;           // [E][8]
   std::vector<int64_t> off_orb, off_pb;   // [E + 1]
   std::vector<int> Ka_e, Kb_e;            // [E] product functions of a and b kept by entry e
-  std::vector<int> far_e;                 // [E] 1: beyond sphere B (reduced basis)
-  int n_far = 0;                          // entries with the reduced basis
+  std::vector<int> tier_e;                // [E] product-basis level: 0 sphere A, 1 B, 2 C
+  int n_far = 0;                          // entries beyond sphere B
+  int n_near = 0;                         // entries within sphere B keeping n_prod_near < n_prod
   std::vector<int> pair_start;            // [n_atoms^2 + 1] entry range per ordered atom pair
   std::vector<int> mirror;                // [E]
   std::vector<double> phase;              // [E][N_k] complex e^{+i k.R}

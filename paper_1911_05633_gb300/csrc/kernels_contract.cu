@@ -232,10 +232,10 @@ __device__ bool p_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
   const int sa = S.species[E.a], sb = S.species[E.b];
   const float* Ca = S.Cp + S.cp_off[sa];  // [L][L''][K], K fastest
   const int ldk = S.cp_ld[sa];
-  const uint16_t* bsrc = S.Bp + S.bp_off[2 * sb + E.far];
+  const uint16_t* bsrc = S.Bp + S.bp_off[3 * sb + E.tier];
   const long long plane_elems = (long long)NP * KD;
   const int n_chunks = (KD + c.kc - 1) / c.kc;
-  const int bkey = (sys << 12) | (sb << 1) | E.far;
+  const int bkey = (sys << 12) | (sb << 2) | E.tier;
   const int t = c.t;
   // G(tau) and conj(G(beta - tau)) transposed, in FP32
   float2* G1 = c.Gs;
@@ -376,20 +376,20 @@ __device__ bool p_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
 template <int NA, int NB, bool EXACT>
 __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, int sys) {
   const int na = EXACT ? NA : E.na, nb = EXACT ? NB : E.nb, Ka = E.Ka, Kb = E.Kb;
-  const int nt = S.n_tau;
   const int nbb = nb * nb;
   const int KD = (Kb + 15) & ~15, NJ = (nbb + 15) & ~15;
   const int sa = S.species[E.a], sb = S.species[E.b];
   const float* Ca = S.Cp + S.cp_off[sa];  // [L][L''][K], K fastest
   const int ldk = S.cp_ld[sa];
-  const uint16_t* bsrc = S.Bp + S.bp_off[2 * sb + E.far];
+  const uint16_t* bsrc = S.Bp + S.bp_off[3 * sb + E.tier];
   const long long plane_elems = (long long)NJ * KD;
   const int n_chunks = (KD + c.kc - 1) / c.kc;
-  const int bkey = (sys << 12) | (sb << 1) | E.far;
+  const int bkey = (sys << 12) | (sb << 2) | E.tier;
   const int t = c.t;
-  const double2* Win = S.W + E.off_pb * nt + (long long)it * Ka * Kb;
+  const double2* Win = S.W + E.off_pb * S.w_slices + (long long)it * Ka * Kb;
   {
-    const double2* Gin = S.G + E.off_orb * nt + (long long)it * na * nb;
+    const int gs = S.g_fixed >= 0 ? S.g_fixed : it;
+    const double2* Gin = S.G + E.off_orb * S.g_slices + (long long)gs * na * nb;
     for (int x = t; x < na * nb; x += kTG) {
       const double2 gv = Gin[x];
       c.Gs[x] = make_float2(d2f(gv.x), d2f(gv.y));
@@ -521,7 +521,8 @@ __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
       if (EXACT || L1 < nb) part[(Lr * nks_t + ks) * kCMaxOrb + L1] = make_float2(accr[L1], acci[L1]);
   }
   group_sync(c.g);
-  double2* op = S.out + E.off_orb * nt + (long long)it * na * nb;
+  double2* op = S.out + E.off_orb * S.out_slices + (long long)it * na * nb;
+  const float sgn = (float)S.sign;  // +-1: exact
   for (int o = t; o < na * nb; o += kTG) {
     const int L = o / nb, L1 = o - L * nb;
     float sr = 0.f, si = 0.f;
@@ -530,7 +531,7 @@ __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
       sr += p.x;
       si += p.y;
     }
-    op[o] = make_double2(f2d(-sr), f2d(-si));
+    op[o] = make_double2(f2d(sgn * sr), f2d(sgn * si));
   }
   group_sync(c.g);
   return true;
@@ -670,9 +671,9 @@ gw_status ctables_init(CTables& t, const HostPlan& h) {
   std::vector<uint16_t> bpP, bpS;
   std::vector<long long> offP, offS;
   t.np_max = t.kd_max = t.nj_max = t.kds_max = 0;
-  for (int sv = 0; sv < 2 * h.n_species; ++sv) {
-    const int s = sv / 2;
-    const int n = h.n_orb[s], K = (sv & 1) ? h.n_prod_far[s] : h.n_prod[s];
+  for (int sv = 0; sv < 3 * h.n_species; ++sv) {
+    const int s = sv / 3, tier = sv % 3;
+    const int n = h.n_orb[s], K = tier == 0 ? h.n_prod[s] : tier == 1 ? h.n_prod_near[s] : h.n_prod_far[s];
     const int nn = n * n;
     const int KD = (nn + 15) & ~15, NP = (K + 15) & ~15;
     t.np_max = std::max(t.np_max, NP);
@@ -724,14 +725,14 @@ void ctables_free(CTables& t) {
   t = CTables();
 }
 
-std::vector<CUnit> contract_units(const HostPlan& h, int sys, bool sigma) {
+std::vector<CUnit> contract_units(const HostPlan& h, int sys, bool sigma, int n_nodes) {
   const int E = h.n_entries();
-  const int ne = (!sigma && h.c_symmetric) ? (h.n_tau + 1) / 2 : h.n_tau;
+  const int ne = n_nodes > 0 ? n_nodes : (!sigma && h.c_symmetric) ? (h.n_tau + 1) / 2 : h.n_tau;
   std::vector<int> order(E);
   for (int e = 0; e < E; ++e) order[e] = e;
   auto key = [&](int e) {
     const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
-    return (h.species[b] * 2 + h.far_e[e]) * 64 + h.species[a];
+    return (h.species[b] * 3 + h.tier_e[e]) * 64 + h.species[a];
   };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key(x) < key(y); });
   std::vector<CUnit> u;

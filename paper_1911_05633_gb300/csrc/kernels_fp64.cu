@@ -38,40 +38,30 @@ __device__ __forceinline__ double2 rfma(double r, double2 b, double2 c) {
 // element whose atom pair has no entry is skipped; an entry with a reduced product basis
 // (beyond sphere B) keeps its top-left K_a(e) x K_b(e).
 // ---------------------------------------------------------------------------
-constexpr int kGatherEnt = 8;
-
 __global__ void k_gather_k_to_R(GatherArgs g) {
   const int a = blockIdx.x, s = blockIdx.y;
   const int ro = g.row_off[a];
   const int rows = g.row_off[a + 1] - ro;
-  const long long n_el = (long long)rows * g.ld;
-  for (long long x = threadIdx.x; x < n_el; x += blockDim.x) {
-    const int i = (int)(x / g.ld), col = (int)(x - (long long)i * g.ld);
+  const int n_el = rows * g.ld;
+  for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
+    const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
     const int j = col - g.row_off[b];
     const int p = a * g.n_atoms + b;
     const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
-    if (e0 == e1) continue;
     const long long in_el = (long long)(ro + i) * g.ld + col;
-    for (int eb = e0; eb < e1; eb += kGatherEnt) {
-      const int ne = min(kGatherEnt, e1 - eb);
-      // the entries of this chunk whose kept block holds (i, j)
-      unsigned need = 0;
-#pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m)
-        if (m < ne) {
-          const DevEntry& E = g.ent[eb + m];
-          if (i < (g.pb ? E.Ka : E.na) && j < (g.pb ? E.Kb : E.nb)) need |= 1u << m;
-        }
-      if (!need) continue;
-      double2 acc[kGatherEnt];
-#pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m) acc[m] = make_double2(0.0, 0.0);
+    // one FP64 sum over k per entry that keeps (i, j) (runtime loops: the FP64 work is
+    // proportional to the entries, not to a fixed unrolled count)
+    for (int e = e0; e < e1; ++e) {
+      const DevEntry& E = g.ent[e];
+      if (i >= (g.pb ? E.Ka : E.na) || j >= (g.pb ? E.Kb : E.nb)) continue;
+      const double2* ph = g.phase + (long long)e * g.n_k;
+      double2 acc = make_double2(0.0, 0.0);
       for (int kk = 0; kk < g.n_k_in; ++kk) {
         const int k = g.k_list ? g.k_list[kk] : kk;
         double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
         if (g.F_sub) {
-          double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
+          const double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
           v.x -= w.x;
           v.y -= w.y;
         }
@@ -80,29 +70,14 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
           v.x *= wk;
           v.y *= wk;
         }
-        if (g.real_only) {  // Re(conj(ph) v) only
-#pragma unroll
-          for (int m = 0; m < kGatherEnt; ++m)
-            if ((need >> m) & 1u) {
-              const double2 ph = g.phase[(long long)(eb + m) * g.n_k + k];
-              acc[m].x = fma(ph.x, v.x, fma(ph.y, v.y, acc[m].x));
-            }
-        } else {
-#pragma unroll
-          for (int m = 0; m < kGatherEnt; ++m)
-            if ((need >> m) & 1u) acc[m] = cfma_conj_a(g.phase[(long long)(eb + m) * g.n_k + k], v, acc[m]);
-        }
+        const double2 c = ph[k];
+        if (g.real_only) acc.x = fma(c.x, v.x, fma(c.y, v.y, acc.x));  // Re(conj(ph) v) only
+        else acc = cfma_conj_a(c, v, acc);
       }
-#pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m) {
-        if ((need >> m) & 1u) {
-          const DevEntry& E = g.ent[eb + m];
-          const long long off = g.pb ? E.off_pb : E.off_orb;
-          const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
-          double2 r = make_double2(acc[m].x * g.scale, g.real_only ? 0.0 : acc[m].y * g.scale);
-          g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] = r;
-        }
-      }
+      const long long off = g.pb ? E.off_pb : E.off_orb;
+      const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
+      g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] =
+          make_double2(acc.x * g.scale, g.real_only ? 0.0 : acc.y * g.scale);
     }
   }
 }
@@ -117,52 +92,34 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
   const int a = blockIdx.x, s = blockIdx.y;
   const int ro = g.row_off[a];
   const int rows = g.row_off[a + 1] - ro;
-  const long long n_el = (long long)rows * g.ld;
-  for (long long x = threadIdx.x; x < n_el; x += blockDim.x) {
-    const int i = (int)(x / g.ld), col = (int)(x - (long long)i * g.ld);
+  const int n_el = rows * g.ld;
+  for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
+    const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
     const int j = col - g.row_off[b];
     const int p = a * g.n_atoms + b;
     const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
     const long long out_el = (long long)(ro + i) * g.ld + col;
-    for (int eb = e0; eb < e1 || eb == e0; eb += kGatherEnt) {
-      const int ne = max(0, min(kGatherEnt, e1 - eb));
-      double2 v[kGatherEnt];
-#pragma unroll
-      for (int m = 0; m < kGatherEnt; ++m) {
-        v[m] = make_double2(0.0, 0.0);
-        if (m < ne) {
-          // an entry with a reduced product basis holds only the top-left K_a(e) x K_b(e)
-          const DevEntry& E = g.ent[eb + m];
-          const long long off = g.pb ? E.off_pb : E.off_orb;
-          const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
-          if (i < re && j < ce) v[m] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
-        }
+    for (int kk = 0; kk < g.n_k_out; ++kk) {
+      const int k = g.k_list ? g.k_list[kk] : kk;
+      double2 acc = make_double2(0.0, 0.0);
+      // the entries of the pair whose kept block holds (i, j); runtime loop, so the FP64 work
+      // is proportional to them
+      for (int e = e0; e < e1; ++e) {
+        const DevEntry& E = g.ent[e];
+        const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+        if (i >= re || j >= ce) continue;
+        const long long off = g.pb ? E.off_pb : E.off_orb;
+        const double2 v = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+        const double2 c = g.phase[(long long)e * g.n_k + k];
+        acc = g.real_in ? rfma(v.x, c, acc) : cfma(c, v, acc);  // ph * Re(v) for a real input
       }
-      for (int kk = 0; kk < g.n_k_out; ++kk) {
-        const int k = g.k_list ? g.k_list[kk] : kk;
-        double2 acc = make_double2(0.0, 0.0);
-        if (g.real_in) {  // ph * Re(v)
-#pragma unroll
-          for (int m = 0; m < kGatherEnt; ++m)
-            if (m < ne) acc = rfma(v[m].x, g.phase[(long long)(eb + m) * g.n_k + k], acc);
-        } else {
-#pragma unroll
-          for (int m = 0; m < kGatherEnt; ++m)
-            if (m < ne) acc = cfma(g.phase[(long long)(eb + m) * g.n_k + k], v[m], acc);
-        }
+      if (g.coef != 1.0) {
         acc.x *= g.coef;
         acc.y *= g.coef;
-        double2* o = g.F_k + (long long)kk * g.k_stride + (long long)s * g.s_stride + out_el;
-        if (eb == e0) {
-          if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
-          *o = acc;
-        } else {
-          double2 t = *o;
-          *o = cadd(t, acc);
-        }
       }
-      if (e1 <= e0) break;
+      if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
+      g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + out_el] = acc;
     }
   }
 }

@@ -194,11 +194,10 @@ gw_status mixed_init(MixedPlan& m, const HostPlan& h, const std::vector<DevEntry
     return GW_ERR_UNSUPPORTED;
   }
   m.ready = true;
-  return tc_init(m, h);
+  return GW_OK;
 }
 
 void mixed_free(MixedPlan& m) {
-  tc_free(m);
   if (m.d_Cf) cudaFree(m.d_Cf);
   m.d_Cf = nullptr;
   m.ready = false;
@@ -207,7 +206,6 @@ void mixed_free(MixedPlan& m) {
 gw_status mixed_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent, const double*,
                                const double2* G_R, double2* P_R, int* d_status, cudaStream_t st) {
   if (!m.ready) { set_last_error("mixed path not initialised"); return GW_ERR_ARG; }
-  if (m.tc_ready) return tc_polarizability(m, h, d_ent, G_R, P_R, d_status, st);
   const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
   dim3 grid(h.n_entries(), nt_eff);
   {
@@ -222,7 +220,6 @@ gw_status mixed_polarizability(MixedPlan& m, const HostPlan& h, const DevEntry* 
 gw_status mixed_self_energy(MixedPlan& m, const HostPlan& h, const DevEntry* d_ent, const double*,
                             const double2* G_R, const double2* Wt_R, double2* Sig_R, int* d_status, cudaStream_t st) {
   if (!m.ready) { set_last_error("mixed path not initialised"); return GW_ERR_ARG; }
-  if (m.tc_s_ready) return tc_self_energy(m, h, d_ent, G_R, Wt_R, Sig_R, d_status, st);
   dim3 grid(h.n_entries(), h.n_tau);
   {
     gw::TimedLaunch tl_("k_self_energy_f32", st);

@@ -294,11 +294,17 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   // reduced product basis beyond sphere B (Sec. 2, Fig. 2)
   hp.r_b = (opt && basis->n_prod_far) ? opt->r_b : 0.0;
   hp.n_prod_far = hp.n_prod;
+  hp.n_prod_near = hp.n_prod;
   if (hp.r_b > 0)
     for (int s = 0; s < hp.n_species; ++s) {
       const int f = basis->n_prod_far[s];
       if (f < 1 || f > hp.n_prod[s]) { err = "n_prod_far must be in [1, n_prod]"; return GW_ERR_ARG; }
       hp.n_prod_far[s] = f;
+      if (basis->n_prod_near) {
+        const int nr = basis->n_prod_near[s];
+        if (nr < f || nr > hp.n_prod[s]) { err = "n_prod_near must be in [n_prod_far, n_prod]"; return GW_ERR_ARG; }
+        hp.n_prod_near[s] = nr;
+      }
     }
   if (hp.spin != 1 && hp.spin != 2) { err = "spin must be 1 or 2"; return GW_ERR_ARG; }
 
@@ -376,18 +382,25 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   const int E = hp.n_entries();
   if (E == 0) { err = "no pair entry inside the cutoff"; return GW_ERR_ARG; }
 
-  // product functions per entry: the first n_prod_far of each atom beyond sphere B
+  // product functions per entry at its level (Sec. 2, Fig. 2): every function when both
+  // arguments are in one sphere (A), the first n_prod_near within sphere B, the first
+  // n_prod_far beyond it
   hp.Ka_e.assign(E, 0);
   hp.Kb_e.assign(E, 0);
-  hp.far_e.assign(E, 0);
-  hp.n_far = 0;
+  hp.tier_e.assign(E, 0);
+  hp.n_far = hp.n_near = 0;
   for (int e = 0; e < E; ++e) {
-    const int sa = hp.species[hp.entries[8 * e]], sb = hp.species[hp.entries[8 * e + 1]];
-    const bool far = hp.r_b > 0 && dist2[e] > hp.r_b * hp.r_b + 1e-9;
-    hp.Ka_e[e] = far ? hp.n_prod_far[sa] : hp.n_prod[sa];
-    hp.Kb_e[e] = far ? hp.n_prod_far[sb] : hp.n_prod[sb];
-    hp.far_e[e] = far ? 1 : 0;
-    hp.n_far += far ? 1 : 0;
+    const int a = (int)hp.entries[8 * e], b = (int)hp.entries[8 * e + 1];
+    const int sa = hp.species[a], sb = hp.species[b];
+    int tier = 1;
+    if (a == b && dist2[e] <= 1e-9) tier = 0;
+    else if (hp.r_b > 0 && dist2[e] > hp.r_b * hp.r_b + 1e-9) tier = 2;
+    const std::vector<int>& n = tier == 0 ? hp.n_prod : tier == 1 ? hp.n_prod_near : hp.n_prod_far;
+    hp.Ka_e[e] = n[sa];
+    hp.Kb_e[e] = n[sb];
+    hp.tier_e[e] = tier;
+    hp.n_far += tier == 2 ? 1 : 0;
+    hp.n_near += (tier == 1 && (n[sa] < hp.n_prod[sa] || n[sb] < hp.n_prod[sb])) ? 1 : 0;
   }
 
   // block offsets
@@ -493,7 +506,7 @@ std::vector<DevEntry> make_dev_entries(const HostPlan& hp) {
     d.off_orb = hp.off_orb[e];
     d.off_pb = hp.off_pb[e];
     d.mirror = hp.mirror[e];
-    d.far = hp.far_e[e];
+    d.tier = hp.tier_e[e];
     out[e] = d;
   }
   return out;

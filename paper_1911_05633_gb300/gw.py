@@ -47,7 +47,8 @@ class GwCell(C.Structure):
 
 class GwBasis(C.Structure):
     _fields_ = [("n_species", C.c_int), ("n_orb", C.POINTER(C.c_int)), ("n_prod", C.POINTER(C.c_int)),
-                ("C", C.POINTER(C.POINTER(C.c_double))), ("n_prod_far", C.POINTER(C.c_int))]
+                ("C", C.POINTER(C.POINTER(C.c_double))), ("n_prod_far", C.POINTER(C.c_int)),
+                ("n_prod_near", C.POINTER(C.c_int))]
 
 
 class GwGrid(C.Structure):
@@ -70,7 +71,7 @@ class GwPlanInfo(C.Structure):
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
                 ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
                 ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int),
-                ("n_entries_far", C.c_int), ("mixed_queue", C.c_int)]
+                ("n_entries_far", C.c_int), ("n_entries_near", C.c_int), ("mixed_queue", C.c_int)]
 
 
 class GwBatchInfo(C.Structure):
@@ -170,7 +171,7 @@ class Plan:
                  kmesh, beta: float, tau, omega_idx, nu_idx, cutoff: float, spin: int = 2,
                  strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0,
                  no_symmetry: bool = False, w_solver: str = "auto", fp64_products: str = "auto",
-                 n_prod_far: Sequence[int] = None, r_b: float = 0.0):
+                 n_prod_far: Sequence[int] = None, r_b: float = 0.0, n_prod_near: Sequence[int] = None):
         lib = load_library()
         self._lib = lib
         self._keep = []
@@ -185,10 +186,12 @@ class Plan:
         om = np.ascontiguousarray(np.asarray(omega_idx, dtype=np.int32))
         nu = np.ascontiguousarray(np.asarray(nu_idx, dtype=np.int32))
         far = None if n_prod_far is None else np.ascontiguousarray(np.asarray(n_prod_far, dtype=np.int32))
-        self._keep += [lat, frac, species, n_orb, n_prod, Cs, Cptr, tau, om, nu, far]
+        near = None if n_prod_near is None else np.ascontiguousarray(np.asarray(n_prod_near, dtype=np.int32))
+        self._keep += [lat, frac, species, n_orb, n_prod, Cs, Cptr, tau, om, nu, far, near]
         cell = GwCell((C.c_double * 9)(*lat), len(frac), _ptr(frac, C.c_double), _ptr(species, C.c_int))
         basis = GwBasis(len(Cs), _ptr(n_orb, C.c_int), _ptr(n_prod, C.c_int), Cptr,
-                        _ptr(far, C.c_int) if far is not None else C.POINTER(C.c_int)())
+                        _ptr(far, C.c_int) if far is not None else C.POINTER(C.c_int)(),
+                        _ptr(near, C.c_int) if near is not None else C.POINTER(C.c_int)())
         grid = GwGrid(float(beta), len(tau), _ptr(tau, C.c_double), len(om), _ptr(om, C.c_int),
                       len(nu), _ptr(nu, C.c_int))
         opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes),
@@ -225,6 +228,8 @@ class Plan:
         with its reduced basis beyond sphere B when it has one)."""
         if getattr(cell, "r_b", 0.0) > 0 and "r_b" not in kw:
             kw = dict(kw, r_b=cell.r_b, n_prod_far=[s.n_prod_far for s in cell.species])
+            if any(getattr(s, "n_prod_near", None) for s in cell.species):
+                kw["n_prod_near"] = [getattr(s, "n_prod_near", None) or s.n_prod for s in cell.species]
         return cls(cell.lattice, cell.frac, cell.species_of_atom, [s.n_orb for s in cell.species],
                    [s.n_prod for s in cell.species], [s.C for s in cell.species], cell.kmesh, cell.beta,
                    cell.tau, cell.omega_idx, cell.nu_idx, cell.cutoff, spin=cell.spin, **kw)

@@ -55,7 +55,8 @@ class Species:
     n_orb: int
     n_prod: int
     C: np.ndarray  # [n_prod][n_orb][n_orb] float64, symmetric in the last two
-    n_prod_far: Optional[int] = None  # product functions kept by pairs beyond sphere B
+    n_prod_far: Optional[int] = None   # product functions kept by pairs beyond sphere B
+    n_prod_near: Optional[int] = None  # product functions kept by other pairs within sphere B
 
 
 @dataclasses.dataclass
@@ -547,13 +548,19 @@ def batch_family(n: int = 16, n_tau: int = 48) -> List[SynthCell]:
     return cells
 
 
-def with_far_basis(cell: SynthCell, r_b: float, n_prod_far: Sequence[int]) -> SynthCell:
-    """The same cell with a reduced product basis for pairs beyond a sphere of radius
-    r_b (bohr): n_prod_far[s] functions per atom of species s (inputs only)."""
+def with_far_basis(cell: SynthCell, r_b: float, n_prod_far: Sequence[int],
+                   n_prod_near: Optional[Sequence[int]] = None) -> SynthCell:
+    """The same cell with reduced product bases for pairs of distinct spheres (inputs only):
+    n_prod_far[s] functions per atom of species s beyond a sphere of radius r_b (bohr) and,
+    when given, n_prod_near[s] within it (the onsite pairs keep every function)."""
     cell.r_b = float(r_b)
     for sp, f in zip(cell.species, n_prod_far):
         sp.n_prod_far = int(f)
-    cell.name = f"{cell.name}-rb{r_b:g}-K" + "/".join(str(int(f)) for f in n_prod_far)
+    if n_prod_near is not None:
+        for sp, f in zip(cell.species, n_prod_near):
+            sp.n_prod_near = int(f)
+    cell.name = f"{cell.name}-rb{r_b:g}-K" + "/".join(str(int(f)) for f in n_prod_far) + (
+        "" if n_prod_near is None else "-near" + "/".join(str(int(f)) for f in n_prod_near))
     return cell
 
 

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 TOL_MIXED = 1e-6
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "mixed_nonsym", "c1", "c1_cut5_far", "mixed_far"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "mixed_nonsym", "c1", "c1_cut5_far", "mixed_far", "c1_3tier"])
 def test_polarizability_mixed(name):
     s = system(name)
     assert s.plan.info["mixed_queue"] == 3  # the persistent tensor-core kernels, not a fallback
@@ -25,7 +25,7 @@ def test_polarizability_mixed(name):
     assert rel_blocks(P, pack(ref), s.plan.off_pb, s.nt) < TOL_MIXED
 
 
-@pytest.mark.parametrize("name", ["c0", "mixed", "c1", "c1_cut5_far", "mixed_far"])
+@pytest.mark.parametrize("name", ["c0", "mixed", "c1", "c1_cut5_far", "mixed_far", "c1_3tier"])
 def test_self_energy_mixed(name):
     s = system(name)
     WR = _random_W(s)
@@ -34,6 +34,12 @@ def test_self_energy_mixed(name):
     err = rel(S, pack(ref))
     assert err < TOL_MIXED, err
     assert rel_blocks(S, pack(ref), s.plan.off_orb, s.nt) < TOL_MIXED
+    # the exchange term in the same precision (W~ -> v, G(tau) -> G(beta-), opposite sign)
+    vR = s.orc.v_R(s.v_class)
+    refx = oracle.exchange_R(s.G_R(), vR, s.orc.entries, s.orc.C_atom)
+    _, Sx = s.plan.self_energy_tau(dev(pack(s.G_R())), dev(pack(WR)), v_R=dev(pack(vR)), precision="mixed")
+    assert rel(host(Sx), pack(refx)) < TOL_MIXED
+    assert rel_blocks(host(Sx), pack(refx), s.plan.off_orb, 1) < TOL_MIXED
 
 
 def _amplification():
@@ -109,8 +115,9 @@ def test_mixed_quasiparticle_energies_within_1_meV():
     assert np.abs(Em - E64).max() * hartree_meV < 1.0
 
 
-def test_mixed_largest_blocks_cuda_core_path():
-    """n = 16, K = 128 is outside the tensor-core tile limits: the FP32 CUDA-core form runs."""
+def test_mixed_largest_blocks():
+    """n = 16, K = 128 (the compiled maxima): the queue kernels with the reduction in chunks
+    (n^2 = 256 columns of P's dense stage) and one thread group for Sigma's 256-wide stage."""
     import synth
     from test_gpu_parity import Sys
     lat = np.eye(3) * 6.0
@@ -118,6 +125,7 @@ def test_mixed_largest_blocks_cuda_core_path():
     cell = synth.SynthCell("big1", lat, np.zeros((1, 3)), np.zeros(1, np.int32), sp, (2, 1, 1), 20.0, 8, 0.0,
                            seed=77, gap=None, hop_cutoff=6.5).build()
     s = Sys(cell)
+    assert s.plan.info["mixed_queue"] == 3
     ref = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, cell.spin)
     assert rel(host(s.plan.polarizability_tau(dev(pack(s.G_R())), precision="mixed")), pack(ref)) < TOL_MIXED
     WR = _random_W(s)

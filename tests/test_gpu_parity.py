@@ -92,6 +92,9 @@ class Sys:
         # the product-basis block of every entry (reduced beyond sphere B) as the oracle has it
         assert [self.plan.block_shape(e, "pb") for e in range(len(self.orc.entries))] == self.orc.kdims
         assert self.plan.info["n_entries_far"] == int(self.orc.far.sum())
+        full = [(cell.n_prod_of(int(r[0])), cell.n_prod_of(int(r[1]))) for r in self.orc.entries]
+        near = sum(1 for t, kd, fk in zip(self.orc.tier, self.orc.kdims, full) if t == 1 and kd != fk)
+        assert self.plan.info["n_entries_near"] == near
         self.G_k = cell.green_k_tau()
         self.v_q, self.v_class = cell.coulomb()
         self.nt = cell.n_tau
@@ -131,6 +134,11 @@ def system(name):
                                                     4.0, [24]))
         elif name == "mixed_far":  # every pair but the onsite ones reduced: K 8 -> 5, 19 -> 11
             _CACHE[name] = Sys(synth.with_far_basis(synth.mixed_species_cell(), 4.0, [5, 11]))
+        elif name == "c0_3tier":  # the three levels of Fig. 2: onsite 8, neighbour 5, image beyond 4.6 bohr 3
+            _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(0), 4.6, [3], n_prod_near=[5]))
+        elif name == "c1_3tier":  # 8-atom cell, cutoff 7.5: nearest neighbours 36 of 48, second ones 24
+            _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=7.5, n_tau=12, kmesh=(2, 2, 2)),
+                                                    4.6, [24], n_prod_near=[36]))
         elif name == "c1_far_fp64":
             _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
                                                     4.0, [24]), fp64_products="fp64")
@@ -140,7 +148,7 @@ def system(name):
 
 
 SMALL = ["c0", "mixed", "mixed_nonsym", "c1_cut5"]
-FAR = ["c1_cut5_far", "mixed_far"]  # reduced product basis beyond sphere B (Sec. 2, Fig. 2)
+FAR = ["c1_cut5_far", "mixed_far", "c0_3tier", "c1_3tier"]  # reduced product bases (Sec. 2, Fig. 2)
 
 
 @pytest.mark.parametrize("name", SMALL + ["c1"])

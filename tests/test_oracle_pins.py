@@ -661,6 +661,68 @@ def test_far_basis_equals_masked_full_basis():
     assert max(np.abs(a - b).max() for a, b in zip(St, Sf)) > 1e-6 * max(np.abs(b).max() for b in Sf)
 
 
+def _three_level_cells(r_b=4.6, n_near=5, n_far=3):
+    """cell0 twice from the same seed: with the three levels of Fig. 2 (onsite 8 functions,
+    the A-B neighbour at 4.33 bohr inside sphere B keeps n_near, the A-A' image at 5 bohr
+    beyond it n_far), and with the full basis everywhere."""
+    full = synth.make_config(0)
+    tier = synth.with_far_basis(synth.make_config(0), r_b, [n_far], n_prod_near=[n_near])
+    return full, tier
+
+
+def test_three_levels_by_distance():
+    full, tier = _three_level_cells()
+    orc = oracle.OracleSystem(tier)
+    for e, row in enumerate(orc.entries):
+        onsite = row[0] == row[1] and not row[5:8].any()
+        near = row[0] != row[1]  # a-b: the cube centre at 4.33 bohr (every class here)
+        assert orc.tier[e] == (0 if onsite else 1 if near else 2)
+        assert orc.kdims[e] == ((8, 8) if onsite else (5, 5) if near else (3, 3))
+    assert set(orc.tier) == {0, 1, 2}
+
+
+def test_three_levels_equal_masked_full_basis():
+    """Three basis sizes against the full-basis oracle with the dropped rows and columns of
+    P, W~ and v set to zero, level by level."""
+    full, tier = _three_level_cells()
+    of, ot = oracle.OracleSystem(full), oracle.OracleSystem(tier)
+    Gk = full.green_k_tau()
+    vq, vcls = full.coulomb()
+    ent, po = of.entries, full.pb_offsets
+    GR = oracle.fourier_k_to_R(Gk, ent, of.kmesh, full.orb_offsets, full.orb_offsets)
+
+    def mask(blocks):
+        out = []
+        for e, b in enumerate(blocks):
+            m = np.zeros_like(b)
+            ka, kb = ot.kdims[e]
+            m[..., :ka, :kb] = b[..., :ka, :kb]
+            out.append(m)
+        return out
+
+    Pf = oracle.polarizability_R(GR, ent, of.C_atom, full.spin)
+    Pt = oracle.polarizability_R(GR, ent, ot.C_atom, tier.spin, ot.kdims)
+    for e in range(len(ent)):
+        ka, kb = ot.kdims[e]
+        assert np.abs(Pt[e] - Pf[e][:, :ka, :kb]).max() <= 1e-14 * np.abs(Pf[e]).max()
+    Wt_iw, Wq_t = oracle.screened_W(oracle.transform(ot.B_fwd, Pt), ent, vq, ot.kmesh, po)
+    Wm_iw, Wq_m = oracle.screened_W(oracle.transform(of.B_fwd, mask(Pf)), ent, vq, of.kmesh, po)
+    assert np.abs(Wq_t - Wq_m).max() <= 1e-12 * np.abs(Wq_m).max()
+    St = oracle.self_energy_R(GR, oracle.transform(ot.B_inv, Wt_iw), ent, ot.C_atom)
+    Sm = oracle.self_energy_R(GR, mask(oracle.transform(of.B_inv, Wm_iw)), ent, of.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(St, Sm)) <= 1e-12 * max(np.abs(b).max() for b in Sm)
+    Xt = oracle.exchange_R(GR, ot.v_R(vcls), ent, ot.C_atom)
+    Xm = oracle.exchange_R(GR, mask(of.v_R(vcls)), ent, of.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(Xt, Xm)) <= 1e-12 * max(np.abs(b).max() for b in Xm)
+    # the middle level matters: the two-level reduction (near = full) gives another answer
+    _, two = _far_cells(r_b=4.6, n_far=3)
+    o2 = oracle.OracleSystem(two)
+    P2 = oracle.polarizability_R(GR, ent, o2.C_atom, two.spin, o2.kdims)
+    W2 = oracle.transform(o2.B_inv, oracle.screened_W(oracle.transform(o2.B_fwd, P2), ent, vq, o2.kmesh, po)[0])
+    S2 = oracle.self_energy_R(GR, W2, ent, o2.C_atom)
+    assert max(np.abs(a - b).max() for a, b in zip(St, S2)) > 1e-6 * max(np.abs(b).max() for b in S2)
+
+
 def test_far_basis_beyond_every_distance_is_the_full_basis():
     full = synth.make_config(0)
     tier = synth.with_far_basis(synth.make_config(0), 1e3, [3])
