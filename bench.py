@@ -401,7 +401,7 @@ class RowSweep:
         self.torch = torch
         self.cell = cell
         self.prec = "mixed"
-        self.plan = gw.Plan.from_cell(cell, device=device)
+        self.plan = gw.Plan.from_cell(cell, device=device, defer_scratch=True)  # no W solve here
         p, inf = self.plan, self.plan.info
         self.dev = torch.device("cuda", device)
         z = lambda n: torch.empty(n, dtype=torch.complex128, device=self.dev)
@@ -1023,6 +1023,16 @@ def run_reference(args, rank, world):
 # batched uneven systems (configuration 3): one persistent launch per contraction
 # --------------------------------------------------------------------------------------
 
+def release_device():
+    """Drop unreferenced plans and return torch's cached blocks to the device, so that the
+    next block's plans can allocate."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 def run_batch3(args, local, peaks):
     """The mixed P and Sigma contractions of the 16-system batch family (15 diamond-like
     supercells of 8 to 56 atoms with different meshes and cutoffs, and the 56-atom layered
@@ -1040,7 +1050,7 @@ def run_batch3(args, local, peaks):
     plans, G, W, P, S = [], [], [], [], []
     gen = torch.Generator(device=dev).manual_seed(3)
     for c in cells:
-        p = gw.Plan.from_cell(c, device=local)
+        p = gw.Plan.from_cell(c, device=local, defer_scratch=True)
         nt = p.info["n_tau"]
         Gk = torch.from_numpy(c.green_k_tau().reshape(-1)).to(dev)
         G.append(p.green_k_to_R(Gk))
@@ -1145,7 +1155,7 @@ def run_scaling(args, local):
     rows = []
     for nat in sizes:
         cell = synth.make_config(2, atoms=nat)
-        plan = gw.Plan.from_cell(cell, device=local)
+        plan = gw.Plan.from_cell(cell, device=local, defer_scratch=True)
         inf = plan.info
         nt, nn, nw, No, nk = inf["n_tau"], inf["n_nu"], inf["n_omega"], inf["n_orb_total"], inf["n_k"]
         z = lambda n: torch.empty(n, dtype=torch.complex128, device=dev)
@@ -1232,16 +1242,19 @@ def run_serve(args, local):
     for sp in specs.values():
         sp.prepare()
     t_prep = time.perf_counter() - t0
-    total = sum(sp.footprint for sp in specs.values())
-    cap = int(0.4 * total)
-    cap = max(cap, 2 * max(sp.footprint for sp in specs.values()))
     names = list(specs)
-    server = Server(specs, mem_cap_bytes=cap, device=local)
+    free, _ = torch.cuda.mem_get_info(local)
+    server = Server(specs, mem_cap_bytes=int(0.9 * free), device=local)
     alone = {}
-    for n in names:  # service time of each system alone, brought in and resident
+    for n in names:  # service time of each system alone, brought in and resident; measures its footprint
         server.run([(0.0, n)])
         lat = [server.run([(0.0, n)])[0].latency for _ in range(2)]
         alone[n] = round(1e3 * float(np.median(lat)), 3)
+        server.evict(n)
+    # the cap for the sweep, from the measured footprints: well below their sum
+    total = sum(sp.footprint for sp in specs.values())
+    cap = max(int(0.4 * total), int(1.5 * max(sp.footprint for sp in specs.values())))
+    server.mem_cap = cap
     mean_service = float(np.mean(list(alone.values()))) / 1e3
     series = []
     for f in (0.5, 1.0, 2.0, 4.0):  # offered load relative to one system at a time
@@ -1300,13 +1313,20 @@ def main():
         return
     out, cell = run_rows(args, rank, world, local)
     if not args.no_extra:
-        full, _ = run_full(args, local)
-        out["full_sweep_8_atoms"] = full
         try:
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             peaks = {}
-        out["batched_uneven_systems"] = run_batch3(args, local, peaks)
+        # extra blocks: each on a device emptied of the previous one's plans and buffers;
+        # a failure is recorded in the line instead of losing the line
+        for key, fn in (("full_sweep_8_atoms", lambda: run_full(args, local)[0]),
+                        ("batched_uneven_systems", lambda: run_batch3(args, local, peaks))):
+            release_device()
+            try:
+                out[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                out[key] = {"error": f"{type(e).__name__}: {e}"[:400]}
+            release_device()
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             orc = OracleRows(cell)

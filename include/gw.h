@@ -105,7 +105,7 @@ typedef struct {
   int strict_kmesh;       /* 1: reject a k-mesh below the rule of Sec. 2 */
   int host_only;          /* 1: build host tables only; compute calls fail with GW_ERR_NO_DEVICE */
   int device;             /* CUDA device ordinal used by the plan */
-  size_t workspace_bytes; /* cap on the W-solve scratch (0: 4 GiB) */
+  size_t workspace_bytes; /* cap on the W-solve scratch (0: 24 GiB for the tensor-core inverse, 4 GiB otherwise) */
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
   int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384),
                              1: FP64 Gauss-Jordan inverse always */
@@ -119,6 +119,12 @@ typedef struct {
                              1e-9 bohr^2 in the square keeps n_prod_far product functions per
                              atom, an entry of two spheres within it n_prod_near, an onsite
                              entry n_prod; <= 0 (or n_prod_far NULL): every entry keeps n_prod */
+  int defer_scratch;      /* 1: allocate the W-solve scratch (gw_screened_W_iw) and the FP64
+                             digit-product scratch (GW_FP64 gw_polarizability_tau and
+                             gw_self_energy_tau) at the first call that needs them instead of at
+                             plan creation, so that plans used for the mixed contractions alone
+                             hold none of it; such a first call allocates device memory and so
+                             must not be inside a stream capture.  0: allocate at creation */
 } gw_options;
 
 typedef struct {

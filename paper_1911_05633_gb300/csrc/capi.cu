@@ -34,6 +34,7 @@ struct gw_plan_s {
   int* d_orb_atom = nullptr;  // [N_orb] atom of each orbital row / column
   int* d_pb_atom = nullptr;   // [N_PB] atom of each product-basis row / column
   double2* d_phase = nullptr;
+  signed char* d_pcode = nullptr;  // quarter-turn codes of the phases, when every phase is one
   double* d_C = nullptr;
   double2* d_Tf_fwd = nullptr;
   double2* d_Tf_inv = nullptr;
@@ -54,6 +55,9 @@ struct gw_plan_s {
   int* d_status = nullptr;
   int nu_chunk = 0;
   size_t ws_bytes = 0;
+  size_t ws_cap = 0;            // cap on the W-solve scratch
+  // scratch left for the first call that needs it (gw_options.defer_scratch)
+  bool w_pending = false, oz_pending = false, ozp_pending = false;
   size_t smem_P = 0, smem_S = 0, smem_T = 0, smem_GJ = 0;
   bool gj_blocked = false;
   // tensor-core inverse (FP32 Gauss-Jordan + sliced FP64-accurate residual)
@@ -138,7 +142,7 @@ gw_status upload(T** dst, const void* src, size_t bytes) {
 
 void free_device(gw_plan_s* p) {
   void* ptrs[] = {p->d_ent, p->d_pair_start, p->d_pair_first, p->d_orb_off, p->d_pb_off, p->d_orb_atom,
-                  p->d_pb_atom, p->d_phase,
+                  p->d_pb_atom, p->d_phase, p->d_pcode,
                   p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_mirror, p->d_Tb_inv, p->d_qh, p->d_qw,
                   p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_lo, p->t_R, p->t_PX, p->t_Asl,
                   p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_unitsX, p->d_counter};
@@ -182,6 +186,7 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
   g.col_atom = kind == GW_BLOCK_PB ? p->d_pb_atom : p->d_orb_atom;
   g.n_atoms = p->h.n_atoms;
   g.phase = p->d_phase;
+  g.pcode = p->d_pcode;
   g.n_k = p->h.n_k;
   g.k_list = k_list;
   g.k_weight = k_weight;
@@ -220,6 +225,7 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   g.row_off = kind == GW_BLOCK_PB ? p->d_pb_off : p->d_orb_off;
   g.n_atoms = p->h.n_atoms;
   g.phase = p->d_phase;
+  g.pcode = p->d_pcode;
   g.n_k = p->h.n_k;
   g.k_list = k_list;
   g.n_k_out = n_k_out < 0 ? p->h.n_k : n_k_out;
@@ -290,6 +296,67 @@ size_t smem_sigma(const gw::HostPlan& h) {
 }
 
 }  // namespace
+
+// The W-solve scratch: v(q)^-1 of the solved momenta and a chunk of bosonic frequencies
+// sized to the cap, plus the tensor-core inverse's planes.
+static gw_status alloc_w_scratch(gw_plan_s* p) {
+  const gw::HostPlan& h = p->h;
+  const size_t npb = (size_t)h.n_pb_total();
+  const size_t mat = npb * npb * sizeof(double2);
+  // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) the FP32 inverse,
+  // its correction and the residual, the BF16 digit planes of both operands, the term
+  // planes of X0 and the scale exponents
+  const size_t per_mat = mat + npb * sizeof(int) +
+                         (p->w_tensor ? npb * npb * (3 * sizeof(float2) + 2 * (gw::kWSA + gw::kWSX1) * 2 + 6 * 2) +
+                                            2 * npb * sizeof(int)
+                                      : 0);
+  const size_t per_nu = (size_t)p->n_qh * per_mat;
+  const size_t cap = p->ws_cap;
+  const int n_work_nu = h.n_nu - p->nu_start;
+  const size_t base_bytes = (size_t)p->n_qh * mat;
+  const int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_work_nu, cap > base_bytes ? (cap - base_bytes) / per_nu : 1));
+  p->nu_chunk = nch;
+  auto up = [&](void** dst, size_t bytes) -> gw_status {
+    if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("device allocation for the W-solve scratch failed");
+      return GW_ERR_OOM;
+    }
+    return GW_OK;
+  };
+  gw_status st;
+  if ((st = up((void**)&p->d_wsV, (size_t)p->n_qh * mat)) != GW_OK) return st;
+  if ((st = up((void**)&p->d_wsA, (size_t)nch * p->n_qh * mat)) != GW_OK) return st;
+  if ((st = up((void**)&p->d_perm, (size_t)nch * p->n_qh * npb * sizeof(int))) != GW_OK) return st;
+  p->ws_bytes = (size_t)p->n_qh * mat + (size_t)nch * per_nu;
+  if (p->w_tensor) {
+    const size_t nm = (size_t)nch * p->n_qh;
+    if ((st = up((void**)&p->t_X32, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_lo, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_R, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_PX, nm * npb * npb * 6 * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_Asl, nm * npb * npb * 2 * gw::kWSA * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_Xsl, nm * npb * npb * 2 * gw::kWSX1 * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_eA, nm * npb * sizeof(int))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_eX, nm * npb * sizeof(int))) != GW_OK) return st;
+  }
+  p->w_pending = false;
+  return GW_OK;
+}
+
+// The FP64 digit-GEMM scratch of the Sigma stage W~ C^b and of the P stage Y C^b.
+static gw_status alloc_oz_sigma(gw_plan_s* p) {
+  const gw_status st = gw::oz_sigma_init(p->oz, p->h, (size_t)4 << 30);
+  p->oz_pending = false;
+  if (st != GW_OK) return st;
+  p->sigma_tensor = p->oz.ready;
+  return GW_OK;
+}
+static gw_status alloc_oz_pol(gw_plan_s* p) {
+  const gw_status st = gw::oz_pol_init(p->ozp, p->h, (size_t)4 << 30);
+  p->ozp_pending = false;
+  return st;
+}
 
 extern "C" {
 
@@ -401,6 +468,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     if ((st = upload(&p->d_pb_atom, pa.data(), pa.size() * sizeof(int))) != GW_OK) return fail(st);
   }
   if ((st = upload(&p->d_phase, h.phase.data(), h.phase.size() * sizeof(double))) != GW_OK) return fail(st);
+  if (!h.phase_code.empty() &&
+      (st = upload(&p->d_pcode, h.phase_code.data(), h.phase_code.size())) != GW_OK)
+    return fail(st);
   if ((st = upload(&p->d_C, h.C_packed.data(), h.C_packed.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tf_fwd, h.Tf_fwd.data(), h.Tf_fwd.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_Tf_inv, h.Tf_inv.data(), h.Tf_inv.size() * sizeof(double))) != GW_OK) return fail(st);
@@ -415,35 +485,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_qh, qh.data(), qh.size() * sizeof(int))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_qw, qw.data(), qw.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
-  const size_t mat = npb * npb * sizeof(double2);
-  // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) the FP32 inverse,
-  // its correction and the residual, the BF16 digit planes of both operands, the term
-  // planes of X0 and the scale exponents
-  const size_t per_mat = mat + npb * sizeof(int) +
-                         (p->w_tensor ? npb * npb * (3 * sizeof(float2) + 2 * (gw::kWSA + gw::kWSX1) * 2 + 6 * 2) +
-                                            2 * npb * sizeof(int)
-                                      : 0);
-  const size_t per_nu = (size_t)p->n_qh * per_mat;
-  const size_t cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes
-                                                    : (p->w_tensor ? ((size_t)24 << 30) : ((size_t)4 << 30));
-  const int n_work_nu = h.n_nu - p->nu_start;
-  const size_t base_bytes = (size_t)p->n_qh * mat;
-  int nch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_work_nu, cap > base_bytes ? (cap - base_bytes) / per_nu : 1));
-  p->nu_chunk = nch;
-  if ((st = upload(&p->d_wsV, nullptr, (size_t)p->n_qh * mat)) != GW_OK) return fail(st);
-  if ((st = upload(&p->d_wsA, nullptr, (size_t)nch * p->n_qh * mat)) != GW_OK) return fail(st);
-  if ((st = upload(&p->d_perm, nullptr, (size_t)nch * p->n_qh * npb * sizeof(int))) != GW_OK) return fail(st);
-  p->ws_bytes = (size_t)p->n_qh * mat + (size_t)nch * per_nu;
+  p->ws_cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes
+                                            : (p->w_tensor ? ((size_t)24 << 30) : ((size_t)4 << 30));
   if (p->w_tensor) {
-    const size_t nm = (size_t)nch * p->n_qh;
-    if ((st = upload(&p->t_X32, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_lo, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_R, nullptr, nm * npb * npb * sizeof(float2))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_PX, nullptr, nm * npb * npb * 6 * 2)) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_Asl, nullptr, nm * npb * npb * 2 * gw::kWSA * 2)) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_Xsl, nullptr, nm * npb * npb * 2 * gw::kWSX1 * 2)) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_eA, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
-    if ((st = upload(&p->t_eX, nullptr, nm * npb * sizeof(int))) != GW_OK) return fail(st);
     p->smem_GJ32 = gw::gj32_smem((int)npb);
     if (gw::wtc_setup(p->smem_GJ32) != cudaSuccess) {
       cudaError_t e = cudaGetLastError();
@@ -451,6 +495,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
       return fail(GW_ERR_UNSUPPORTED);
     }
   }
+  const bool defer = opt && opt->defer_scratch;
+  if (defer) p->w_pending = true;
+  else if ((st = alloc_w_scratch(p)) != GW_OK) return fail(st);
 
   // dynamic shared memory opt-ins
   p->smem_P = smem_polar(h);
@@ -490,12 +537,13 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     gw::set_last_error("");
   }
   if (p->sigma_tensor) {
-    if ((st = gw::oz_sigma_init(p->oz, h, (size_t)4 << 30)) != GW_OK) return fail(st);
-    p->sigma_tensor = p->oz.ready;
+    if (defer) p->oz_pending = true;
+    else if ((st = alloc_oz_sigma(p)) != GW_OK) return fail(st);
   }
   if (!(opt && opt->fp64_products == 1)) {
     if ((st = gw::oz_transform_init(p->ozt, h)) != GW_OK) return fail(st);
-    if ((st = gw::oz_pol_init(p->ozp, h, (size_t)4 << 30)) != GW_OK) return fail(st);
+    if (defer) p->ozp_pending = true;
+    else if ((st = alloc_oz_pol(p)) != GW_OK) return fail(st);
   }
   *out = p;
   return GW_OK;
@@ -540,7 +588,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->w_symmetric = p->w_sym ? 1 : 0;
   info->w_tensor = p->w_tensor ? 1 : 0;
   info->sigma_tensor = p->sigma_tensor ? 1 : 0;
-  info->p_tensor = p->ozp.ready ? 1 : 0;
+  info->p_tensor = (p->ozp.ready || p->ozp_pending) ? 1 : 0;  // pending: planned at the first call
   info->mixed_queue = (p->contract_p ? 1 : 0) | (p->contract_s ? 2 : 0);
   info->transform_tensor = (p->ozt.ready_w ? 1 : 0) | (p->ozt.ready_p ? 2 : 0);
   info->n_q_solved = p->n_qh;
@@ -632,6 +680,9 @@ gw_status gw_transform_tau_iw_ex(gw_plan_t p, gw_statistics stt, gw_direction di
        (structure == GW_IN_MIRROR && p->ozt.ready_p)))
     return gw::oz_transform(p->ozt, h, p->d_ent, structure, (const double2*)in, (double2*)out, p->d_status,
                             S(stream));
+  if (structure == 0 && gw::oz_general_ready(p->ozt, stt == GW_FERMION, dir == GW_IW_TO_TAU, kind == GW_BLOCK_PB))
+    return gw::oz_general_run(p->ozt, h, p->d_ent, stt == GW_FERMION, dir == GW_IW_TO_TAU, kind == GW_BLOCK_PB,
+                              (const double2*)in, (double2*)out, p->d_status, S(stream));
   gw::TransformArgs g{};
   g.ent = p->d_ent;
   const int nfreq = (stt == GW_FERMION) ? h.n_omega : h.n_nu;
@@ -723,6 +774,7 @@ gw_status gw_polarizability_tau(gw_plan_t p, const void* G_R, void* P_R, gw_prec
   g.spin = h.spin;
   g.mirror_tau = h.c_symmetric;
   const int nt_eff = h.c_symmetric ? (h.n_tau + 1) / 2 : h.n_tau;
+  if (p->ozp_pending && (st = alloc_oz_pol(p)) != GW_OK) return st;
   if (p->ozp.ready) {
     // stages 1 and 2 in FP64 (Y to the pass buffer), stage 3 on the tensor cores, per pass
     for (int s0 = 0; s0 < nt_eff; s0 += p->ozp.tau_c) {
@@ -781,6 +833,7 @@ gw_status gw_self_energy_tau(gw_plan_t p, const void* G_R, const void* Wt_R, con
     g.w_n_slices = h.n_tau;
     g.out_n_slices = h.n_tau;
     g.sign = -1.0;
+    if (p->oz_pending && (st = alloc_oz_sigma(p)) != GW_OK) return st;
     if (p->sigma_tensor) {
       // stage A (W~ C^b) on the tensor cores per pass of tau slices, stages B and C in FP64
       for (int s0 = 0; s0 < h.n_tau; s0 += p->oz.tau_c) {
@@ -854,6 +907,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
   gw::ActiveTimer timing(&p->timer);
   const gw::HostPlan& h = p->h;
   cudaStream_t s = S(stream);
+  if (p->w_pending && (st = alloc_w_scratch(p)) != GW_OK) return st;
   const long long N = h.n_pb_total();
   const long long NN = N * N;
   const int nq = p->n_qh;

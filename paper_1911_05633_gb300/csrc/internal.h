@@ -59,6 +59,7 @@ struct HostPlan {
   std::vector<int> pair_start;            // [n_atoms^2 + 1] entry range per ordered atom pair
   std::vector<int> mirror;                // [E]
   std::vector<double> phase;              // [E][N_k] complex e^{+i k.R}
+  std::vector<signed char> phase_code;    // [E][N_k] c with e^{+i k.R} = i^c, when every phase is one (else empty)
   std::vector<double> Tf_fwd, Tf_inv, Tb_fwd, Tb_inv;  // complex matrices
   // bosonic tau -> i nu for inputs with F(beta - tau) = conj(F(tau)): coefficients
   // (a, b) per (frequency, node i < ceil(N_tau / 2)) with Re out = sum a Re F + b Im F

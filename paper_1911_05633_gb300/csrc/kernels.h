@@ -13,6 +13,7 @@ struct GatherArgs {
   const int* col_atom;     // [N] atom of each dense row / column
   int n_atoms;
   const double2* phase;    // [E][N_k] e^{+i k.R}
+  const signed char* pcode;  // optional [E][N_k]: e^{+i k.R} = i^pcode exactly (quarter turns)
   int n_k;                 // mesh size (phase row length)
   const int* k_list;       // optional: input k index kk -> mesh k (n_k_in entries)
   const double* k_weight;  // optional: weight per input k index
@@ -37,6 +38,7 @@ struct ScatterArgs {
   const int* row_off;      // [n_atoms + 1] orbital or product offsets
   int n_atoms;
   const double2* phase;
+  const signed char* pcode;  // optional [E][N_k]: e^{+i k.R} = i^pcode exactly (quarter turns)
   int n_k;                 // mesh size (phase row length)
   const int* k_list;       // optional: output k index kk -> mesh k (n_k_out entries)
   int n_k_out;

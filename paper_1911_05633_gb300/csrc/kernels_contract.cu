@@ -64,19 +64,12 @@ __device__ __forceinline__ bool group_all(int g, bool v) {
 // block has reported a timeout (status 2).
 __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity, const volatile int* status) {
   const uint32_t a = smem_u32(mbar);
+  if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 0;; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(a), "r"(parity) : "memory");
-    if (done) return true;
-    if ((i & 63) == 63) {
-      if (status && *status == 2) return false;
-      if (global_ns() - t0 > kWaitNs) return false;
-    }
+  for (;;) {
+    if (mbar_try_wait(a, parity)) return true;
+    if (status && *status == 2) return false;
+    if (global_ns() - t0 > kWaitNs) return false;
   }
 }
 
@@ -124,6 +117,7 @@ struct GroupState {
   CUnit u;
   int bkey;  // the B operand held in the group's buffer (system, species, size), -1: none
   int stop;
+  int next;  // the unit claimed after u (its input already on its way into L2), -1: none yet
 };
 
 // What a group works with: its buffers, barriers and tensor-memory columns.
@@ -538,12 +532,39 @@ __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
 }
 
 // Take the next unit of the queue for the group (one thread fetches, the group reads).
-__device__ __forceinline__ bool next_unit(GroupState* gs, const CUnit* units, int n_units, int* counter,
-                                          const volatile int* status, int g) {
+// Bring a unit's inputs into L2 (bulk prefetches of 16-byte aligned, whole-block ranges):
+// the slices of G it reads and, for Sigma, its block of W~.
+__device__ __forceinline__ void prefetch_unit(const CBatch& batch, const CUnit& u, bool sigma) {
+  const CSys& S = batch.s[u.sys];
+  const DevEntry E = S.ent[u.e];
+  const uint32_t gb = (uint32_t)(E.na * E.nb) * 16u;
+  const int gs = S.g_fixed >= 0 ? S.g_fixed : u.tau;
+  const double2* G = S.G + E.off_orb * S.g_slices;
+  prefetch_l2(G + (long long)gs * E.na * E.nb, gb);
+  if (!sigma) {
+    prefetch_l2(G + (long long)(S.n_tau - 1 - u.tau) * E.na * E.nb, gb);
+    return;
+  }
+  const char* w = reinterpret_cast<const char*>(S.W + E.off_pb * S.w_slices + (long long)u.tau * E.Ka * E.Kb);
+  const long long wb = (long long)E.Ka * E.Kb * 16;
+  for (long long o = 0; o < wb; o += 32768) prefetch_l2(w + o, (uint32_t)min(32768ll, wb - o));
+}
+
+// The group's next unit: the one claimed on the previous call (or a fresh claim), with the
+// unit after it claimed now and prefetched, so that its input streams in during this one.
+__device__ __forceinline__ bool next_unit(GroupState* gs, const CBatch& batch, const CUnit* units, int n_units,
+                                          int* counter, const volatile int* status, int g, bool sigma) {
   if ((threadIdx.x % kTG) == 0) {
-    const int i = (*status == 2 || gs->stop) ? n_units : atomicAdd(counter, 1);
-    if (i < n_units) gs->u = units[i];
-    else gs->stop = 1;
+    int i = n_units;
+    if (!(*status == 2 || gs->stop)) i = gs->next >= 0 ? gs->next : atomicAdd(counter, 1);
+    if (i < n_units) {
+      gs->u = units[i];
+      const int j = atomicAdd(counter, 1);
+      gs->next = j;
+      if (j < n_units) prefetch_unit(batch, units[j], sigma);
+    } else {
+      gs->stop = 1;
+    }
   }
   group_sync(g);
   return !gs->stop;
@@ -591,6 +612,7 @@ k_contract(const __grid_constant__ CBatch batch, const CUnit* __restrict__ units
     fence_mbar_init();
     gst[g].bkey = -1;
     gst[g].stop = 0;
+    gst[g].next = -1;
   }
   fence_before_sync();
   __syncthreads();
@@ -598,7 +620,7 @@ k_contract(const __grid_constant__ CBatch batch, const CUnit* __restrict__ units
   const uint32_t tm = tmem_base + (512u / (uint32_t)n_groups) * (uint32_t)g;
   c.col_corr = tm;
   c.col_hh = tm + (uint32_t)n_cols;
-  while (next_unit(c.gs, units, n_units, counter, status, g)) {
+  while (next_unit(c.gs, batch, units, n_units, counter, status, g, SIGMA)) {
     const CUnit u = c.gs->u;
     const CSys& S = batch.s[u.sys];
     const DevEntry E = S.ent[u.e];

@@ -31,53 +31,95 @@ __device__ __forceinline__ double2 rfma(double r, double2 b, double2 c) {
   return make_double2(fma(r, b.x, c.x), fma(r, b.y, c.y));
 }
 
+// i^c v for a quarter-turn code c (0..3): a swap and sign flips of the bit patterns, no
+// arithmetic (c = 1: (-y, x), 2: (-x, -y), 3: (y, -x)).
+__device__ __forceinline__ double neg_if(double x, bool n) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)n << 63));
+}
+__device__ __forceinline__ double2 qmul(int c, double2 v) {
+  const bool sw = c & 1;
+  return make_double2(neg_if(sw ? v.y : v.x, c == 1 || c == 2), neg_if(sw ? v.x : v.y, c >= 2));
+}
+
+constexpr int kHoldK = 8;  // k points held in registers by the gather and scatter
+
 // ---------------------------------------------------------------------------
 // k -> R gather:  F_R[e][s][i][j] = scale * sum_k conj(ph[e][k]) (F_k - F_sub)[k][s][oa+i][ob+j]
 // grid: (row atom a, slice); the block sweeps the band of rows of atom a across every
 // column of the dense matrix, so that consecutive threads read consecutive columns; an
 // element whose atom pair has no entry is skipped; an entry with a reduced product basis
-// (beyond sphere B) keeps its top-left K_a(e) x K_b(e).
+// keeps its top-left K_a(e) x K_b(e).  With at most kHoldK k points the element's values
+// are read once for all its entries; with quarter-turn phases each term is two additions.
 // ---------------------------------------------------------------------------
 __global__ void k_gather_k_to_R(GatherArgs g) {
   const int a = blockIdx.x, s = blockIdx.y;
   const int ro = g.row_off[a];
   const int rows = g.row_off[a + 1] - ro;
   const int n_el = rows * g.ld;
+  const bool hold = g.n_k_in <= kHoldK;
   for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
     const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
     const int j = col - g.row_off[b];
     const int p = a * g.n_atoms + b;
     const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
+    if (e0 == e1) continue;
     const long long in_el = (long long)(ro + i) * g.ld + col;
-    // one FP64 sum over k per entry that keeps (i, j) (runtime loops: the FP64 work is
+    auto value = [&](int kk) -> double2 {
+      const int k = g.k_list ? g.k_list[kk] : kk;
+      double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
+      if (g.F_sub) {
+        const double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
+        v.x -= w.x;
+        v.y -= w.y;
+      }
+      if (g.k_weight) {
+        const double wk = g.k_weight[kk];
+        v.x *= wk;
+        v.y *= wk;
+      }
+      return v;
+    };
+    double2 vh[kHoldK];
+    if (hold)
+#pragma unroll
+      for (int kk = 0; kk < kHoldK; ++kk)
+        if (kk < g.n_k_in) vh[kk] = value(kk);
+    // one sum over k per entry that keeps (i, j) (runtime loops: the FP64 work is
     // proportional to the entries, not to a fixed unrolled count)
     for (int e = e0; e < e1; ++e) {
       const DevEntry& E = g.ent[e];
       if (i >= (g.pb ? E.Ka : E.na) || j >= (g.pb ? E.Kb : E.nb)) continue;
       const double2* ph = g.phase + (long long)e * g.n_k;
+      const signed char* pc = g.pcode ? g.pcode + (long long)e * g.n_k : nullptr;
       double2 acc = make_double2(0.0, 0.0);
-      for (int kk = 0; kk < g.n_k_in; ++kk) {
+      auto term = [&](int kk, double2 v) {
         const int k = g.k_list ? g.k_list[kk] : kk;
-        double2 v = g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + in_el];
-        if (g.F_sub) {
-          const double2 w = g.F_sub[(long long)k * g.sub_k_stride + (long long)s * g.sub_s_stride + in_el];
-          v.x -= w.x;
-          v.y -= w.y;
+        if (pc) {  // conj(i^c) v = i^(4 - c) v
+          const double2 t = qmul((4 - pc[k]) & 3, v);
+          acc.x += t.x;
+          if (!g.real_only) acc.y += t.y;
+        } else {
+          const double2 c = ph[k];
+          if (g.real_only) acc.x = fma(c.x, v.x, fma(c.y, v.y, acc.x));  // Re(conj(ph) v) only
+          else acc = cfma_conj_a(c, v, acc);
         }
-        if (g.k_weight) {
-          const double wk = g.k_weight[kk];
-          v.x *= wk;
-          v.y *= wk;
-        }
-        const double2 c = ph[k];
-        if (g.real_only) acc.x = fma(c.x, v.x, fma(c.y, v.y, acc.x));  // Re(conj(ph) v) only
-        else acc = cfma_conj_a(c, v, acc);
+      };
+      if (hold) {
+#pragma unroll
+        for (int kk = 0; kk < kHoldK; ++kk)
+          if (kk < g.n_k_in) term(kk, vh[kk]);
+      } else {
+        for (int kk = 0; kk < g.n_k_in; ++kk) term(kk, value(kk));
       }
       const long long off = g.pb ? E.off_pb : E.off_orb;
       const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
+      if (g.scale != 1.0) {
+        acc.x *= g.scale;
+        acc.y *= g.scale;
+      }
       g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] =
-          make_double2(acc.x * g.scale, g.real_only ? 0.0 : acc.y * g.scale);
+          make_double2(acc.x, g.real_only ? 0.0 : acc.y);
     }
   }
 }
@@ -86,13 +128,15 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
 // R -> k scatter:  F_k[k][s][oa+i][ob+j] = sum_{e in (a,b)} ph[e][k] F_R[e][s][i][j]
 // grid: (row atom a, slice); the block writes the band of rows of atom a across every
 // column (zeros where the atom pair has no entry), consecutive threads on consecutive
-// columns.
+// columns.  With at most kHoldK k points the sums of all k are kept in registers and each
+// entry's value is read once; with quarter-turn phases each term is two additions.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter_R_to_k(ScatterArgs g) {
   const int a = blockIdx.x, s = blockIdx.y;
   const int ro = g.row_off[a];
   const int rows = g.row_off[a + 1] - ro;
   const int n_el = rows * g.ld;
+  const bool hold = g.n_k_out <= kHoldK;
   for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
     const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
@@ -100,26 +144,58 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
     const int p = a * g.n_atoms + b;
     const int e0 = g.pair_start[p], e1 = g.pair_start[p + 1];
     const long long out_el = (long long)(ro + i) * g.ld + col;
-    for (int kk = 0; kk < g.n_k_out; ++kk) {
-      const int k = g.k_list ? g.k_list[kk] : kk;
-      double2 acc = make_double2(0.0, 0.0);
-      // the entries of the pair whose kept block holds (i, j); runtime loop, so the FP64 work
-      // is proportional to them
-      for (int e = e0; e < e1; ++e) {
-        const DevEntry& E = g.ent[e];
-        const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
-        if (i >= re || j >= ce) continue;
-        const long long off = g.pb ? E.off_pb : E.off_orb;
-        const double2 v = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+    // ph[e][k] v (or ph Re(v) for a real input) added to acc
+    auto term = [&](int e, int k, double2 v, double2& acc) {
+      if (g.pcode) {
+        const int c = g.pcode[(long long)e * g.n_k + k];
+        const double2 t = qmul(c, g.real_in ? make_double2(v.x, 0.0) : v);
+        acc.x += t.x;
+        acc.y += t.y;
+      } else {
         const double2 c = g.phase[(long long)e * g.n_k + k];
-        acc = g.real_in ? rfma(v.x, c, acc) : cfma(c, v, acc);  // ph * Re(v) for a real input
+        acc = g.real_in ? rfma(v.x, c, acc) : cfma(c, v, acc);
       }
+    };
+    auto finish = [&](int kk, double2 acc) {
       if (g.coef != 1.0) {
         acc.x *= g.coef;
         acc.y *= g.coef;
       }
       if (g.base) acc = cadd(acc, g.base[(long long)kk * g.ld * g.ld + out_el]);
       g.F_k[(long long)kk * g.k_stride + (long long)s * g.s_stride + out_el] = acc;
+    };
+    if (hold) {
+      double2 acc[kHoldK];
+#pragma unroll
+      for (int kk = 0; kk < kHoldK; ++kk) acc[kk] = make_double2(0.0, 0.0);
+      // the entries of the pair whose kept block holds (i, j); runtime loop, so the FP64
+      // work is proportional to them
+      for (int e = e0; e < e1; ++e) {
+        const DevEntry& E = g.ent[e];
+        const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+        if (i >= re || j >= ce) continue;
+        const long long off = g.pb ? E.off_pb : E.off_orb;
+        const double2 v = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+#pragma unroll
+        for (int kk = 0; kk < kHoldK; ++kk)
+          if (kk < g.n_k_out) term(e, g.k_list ? g.k_list[kk] : kk, v, acc[kk]);
+      }
+#pragma unroll
+      for (int kk = 0; kk < kHoldK; ++kk)
+        if (kk < g.n_k_out) finish(kk, acc[kk]);
+    } else {
+      for (int kk = 0; kk < g.n_k_out; ++kk) {
+        const int k = g.k_list ? g.k_list[kk] : kk;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int e = e0; e < e1; ++e) {
+          const DevEntry& E = g.ent[e];
+          const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+          if (i >= re || j >= ce) continue;
+          const long long off = g.pb ? E.off_pb : E.off_orb;
+          term(e, k, g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j], acc);
+        }
+        finish(kk, acc);
+      }
     }
   }
 }

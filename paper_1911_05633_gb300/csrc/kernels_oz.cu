@@ -334,23 +334,7 @@ k_oz_slice_elem(const DevEntry* __restrict__ ent, const int* __restrict__ tile_e
   }
 }
 
-// Host digits with the device's rules (scale exponent from the exponent field, rounding
-// half up at 2^-56 of the scale, top-down signed digits).
-int host_exp_field(double x) {
-  uint64_t u;
-  std::memcpy(&u, &x, 8);
-  return (int)((u >> 52) & 0x7FF);
-}
-long long host_fixed56(double x, int e) {
-  uint64_t u;
-  std::memcpy(&u, &x, 8);
-  const int E = (int)((u >> 52) & 0x7FF);
-  if (E == 0) return 0;
-  const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-  const int sh = E - 1019 - e;
-  long long r = sh >= 0 ? (m << sh) : (sh > -63 ? (m + (1ll << (-sh - 1))) >> (-sh) : 0);
-  return (u >> 63) ? -r : r;
-}
+// Host digits with the device's rules (top-down signed digits, as next_digit).
 uint16_t host_digit_bf16(long long& m, int s) {
   const int sh = 49 - 7 * s;
   long long d;
@@ -600,9 +584,43 @@ gw_status oz_transform_init(OzTransform& o, const HostPlan& h) {
     o.bytes += bytes;
     return !src || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
-  const bool good = up((void**)&o.d_tile_e, te.data(), te.size() * sizeof(int)) &&
-                    up((void**)&o.d_tile_r0, tr.data(), tr.size() * sizeof(int)) &&
-                    up((void**)&o.d_Adig, nullptr, (size_t)o.n_tiles * o.KSmax * kOzAChunk) &&
+  if (!up((void**)&o.d_tile_e, te.data(), te.size() * sizeof(int)) ||
+      !up((void**)&o.d_tile_r0, tr.data(), tr.size() * sizeof(int))) {
+    set_last_error("device allocation for the tensor-core transforms failed");
+    oz_transform_free(o);
+    return GW_ERR_OOM;
+  }
+  // row tiles of the orbital blocks, for the general transforms of the orbital layout
+  {
+    std::vector<int> te2, tr2;
+    for (int e = 0; e < h.n_entries(); ++e) {
+      const int a = (int)h.entries[8 * e], b = (int)h.entries[8 * e + 1];
+      const int blk = h.n_orb[h.species[a]] * h.n_orb[h.species[b]];
+      for (int r0 = 0; r0 < blk; r0 += 128) {
+        te2.push_back(e);
+        tr2.push_back(r0);
+      }
+    }
+    o.n_tiles_orb = (int)te2.size();
+    if (!up((void**)&o.d_tile_e_orb, te2.data(), te2.size() * sizeof(int)) ||
+        !up((void**)&o.d_tile_r0_orb, tr2.data(), tr2.size() * sizeof(int))) {
+      set_last_error("device allocation for the tensor-core transforms failed");
+      oz_transform_free(o);
+      return GW_ERR_OOM;
+    }
+  }
+  // the fused kernels need only the row tiles; the digit planes serve the forms they cannot take
+  const gw_status fs = oz_fused_init(o, h);
+  if (fs != GW_OK) {
+    oz_transform_free(o);
+    return fs;
+  }
+  if ((!w_ok || o.fw.ready) && (!p_ok || o.fp.ready)) {
+    o.ready_w = w_ok;
+    o.ready_p = p_ok;
+    return GW_OK;
+  }
+  const bool good = up((void**)&o.d_Adig, nullptr, (size_t)o.n_tiles * o.KSmax * kOzAChunk) &&
                     up((void**)&o.d_eA, nullptr, (size_t)o.n_tiles * 128 * sizeof(int)) &&
                     up((void**)&o.d_Bw, mw.dig.data(), mw.dig.size() * sizeof(uint16_t)) &&
                     up((void**)&o.d_ew, mw.e.data(), mw.e.size() * sizeof(int)) &&
@@ -627,6 +645,7 @@ gw_status oz_transform_init(OzTransform& o, const HostPlan& h) {
 }
 
 void oz_transform_free(OzTransform& o) {
+  oz_fused_free(o);
   void* ptrs[] = {o.d_tile_e, o.d_tile_r0, o.d_Adig, o.d_eA, o.d_Bw, o.d_ew, o.d_Bp, o.d_ep, o.d_zero64, o.d_zero32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -636,6 +655,7 @@ void oz_transform_free(OzTransform& o) {
 gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st) {
   const bool w = structure == GW_IN_REAL;
+  if (w ? o.fw.ready : o.fp.ready) return oz_fused_run(o, h, d_ent, structure, in, out, d_status, st);
   const int N = h.n_tau, nh = (N + 1) / 2, nn = h.n_nu;
   const int KS = w ? o.KS_w : o.KS_p, NT = w ? o.NT_w : o.NT_p, nts = w ? o.nt_w : o.nt_p;
   {

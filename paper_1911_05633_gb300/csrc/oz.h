@@ -57,6 +57,22 @@ struct OzGemmArgs {
   int* status;
 };
 
+// Column operand of the fused transform kernel (k_oz_transform, kernels_oztf.cu): balanced
+// digits d_s 2^-7s of B[n][k], [KS][kOzDigits][NT x 16] in the K-major layout, and the
+// column scale exponents.
+struct OzFused {
+  bool ready = false;
+  int K = 0, KS = 0;        // reduction length, 16-wide steps (<= 8)
+  int n_cols = 0, NT = 0;   // columns, and columns per tile (a multiple of 16, <= 80)
+  int n_ct = 0;             // column tiles
+  bool hold = false;        // the slicers keep a tile's values (KS <= 5)
+  bool wide = false;        // level sums may pass 2^22 (K > 102)
+  bool stage = false;       // the epilogue stages its sums in shared memory (KS <= 5)
+  uint16_t* d_B = nullptr;  // per column tile [KS][kOzDigits][NT x 16]
+  int* d_e = nullptr;       // [n_ct NT]
+  size_t smem = 0;          // dynamic shared memory of the kernel
+};
+
 // FP64-accurate structured tau <-> i nu transforms of the product-basis layout.
 struct OzTransform {
   bool ready_w = false;  // bosonic i nu -> tau of a real input
@@ -76,9 +92,29 @@ struct OzTransform {
   int* d_zero32 = nullptr;
   size_t smem = 0;
   size_t bytes = 0;
+  // the fused kernels (reduction <= 80 terms, <= 80 output columns); when both are ready
+  // the digit planes above are not allocated
+  OzFused fw, fp;
+  // the general complex transforms (reduction <= 128 terms, <= 256 output columns):
+  // [fermionic tau -> i w, i w -> tau, bosonic tau -> i nu, i nu -> tau]
+  OzFused fg[4];
+  int* d_tile_e_orb = nullptr;   // row tiles of the orbital blocks (n_a n_b per entry)
+  int* d_tile_r0_orb = nullptr;
+  int n_tiles_orb = 0;
+  int n_sm = 0;
 };
 
 gw_status oz_transform_init(OzTransform& o, const HostPlan& h);
+// Plans the fused kernels for the plan's grids (needs the row tiles of o); fills o.fw, o.fp.
+gw_status oz_fused_init(OzTransform& o, const HostPlan& h);
+void oz_fused_free(OzTransform& o);
+// A general (complex input) transform on the fused kernel: ready, and run.
+bool oz_general_ready(const OzTransform& o, int fermion, int to_tau, bool pb);
+gw_status oz_general_run(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int fermion, int to_tau, bool pb,
+                         const double2* in, double2* out, int* d_status, cudaStream_t st);
+// One fused transform (structure GW_IN_REAL or GW_IN_MIRROR) when its kernel is ready.
+gw_status oz_fused_run(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
+                       double2* out, int* d_status, cudaStream_t st);
 void oz_transform_free(OzTransform& o);
 // structure: GW_IN_REAL (bosonic i nu -> tau) or GW_IN_MIRROR (bosonic tau -> i nu)
 gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 namespace gw {
 
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
@@ -70,4 +72,21 @@ __device__ __forceinline__ double i2d_scaled(long long S, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// Host forms of exp_field and fixed56 with the device's rules (scale exponent from the
+// exponent field, rounding half up at 2^-56 of the scale).
+inline int host_exp_field(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  return (int)((u >> 52) & 0x7FF);
+}
+inline long long host_fixed56(double x, int e) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = E - 1019 - e;
+  long long r = sh >= 0 ? (m << sh) : (sh > -63 ? (m + (1ll << (-sh - 1))) >> (-sh) : 0);
+  return (u >> 63) ? -r : r;
+}
 }  // namespace gw

@@ -425,6 +425,10 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
   // phases e^{+i k.R} = exp(2 pi i sum_j m_j c_j / N_j), reduced exactly in integers
   const long long L = (long long)kmesh[0] * kmesh[1] * kmesh[2];
   hp.phase.assign((size_t)2 * E * hp.n_k, 0.0);
+  // when every phase is a quarter turn (4 r = 0 mod L: Gamma-centred meshes of 1, 2 or 4
+  // points per axis) it is i^code exactly, and the lattice sums need no multiplications
+  hp.phase_code.assign((size_t)E * hp.n_k, 0);
+  bool quarter = true;
   for (int e = 0; e < E; ++e) {
     int k = 0;
     for (int m1 = 0; m1 < kmesh[0]; ++m1)
@@ -437,8 +441,11 @@ gw_status build_host_plan(const gw_cell* cell, const gw_basis* basis, const int 
           long double th = 2.0L * 3.14159265358979323846264338327950288L * (long double)r / (long double)L;
           hp.phase[2 * ((size_t)e * hp.n_k + k)] = (double)std::cos(th);
           hp.phase[2 * ((size_t)e * hp.n_k + k) + 1] = (double)std::sin(th);
+          if ((4 * r) % L == 0) hp.phase_code[(size_t)e * hp.n_k + k] = (signed char)(4 * r / L);
+          else quarter = false;
         }
   }
+  if (!quarter) hp.phase_code.clear();
 
   // packed C and its (L, L'') symmetry
   hp.c_off.assign(hp.n_species + 1, 0);

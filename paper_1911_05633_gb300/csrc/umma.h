@@ -97,25 +97,32 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// One bounded test of an mbarrier phase: the thread may be suspended (not spinning, so
+// waiting warps take no issue slots from working ones) until the phase completes or
+// kSuspendNs pass.
+constexpr uint32_t kSuspendNs = 100000;
+__device__ __forceinline__ bool mbar_try_wait(uint32_t saddr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done) : "r"(saddr), "r"(parity), "r"(kSuspendNs) : "memory");
+  return done != 0;
+}
+
 // Wait for the mbarrier phase with the given parity.  Gives up and returns false
 // after `timeout_ns` of wall time, or as soon as *abort is non-zero (another block
 // already gave up), so that a failure costs one timeout, not one per block.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t timeout_ns,
                                           const volatile int* abort) {
   const uint32_t a = smem_u32(mbar);
+  if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 0;; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(a), "r"(parity) : "memory");
-    if (done) return true;
-    if ((i & 63) == 63) {
-      if (abort && *abort) return false;
-      if (global_ns() - t0 > timeout_ns) return false;
-    }
+  for (;;) {
+    if (mbar_try_wait(a, parity)) return true;
+    if (abort && *abort) return false;
+    if (global_ns() - t0 > timeout_ns) return false;
   }
 }
 

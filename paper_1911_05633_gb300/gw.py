@@ -60,7 +60,7 @@ class GwGrid(C.Structure):
 class GwOptions(C.Structure):
     _fields_ = [("spin", C.c_int), ("strict_kmesh", C.c_int), ("host_only", C.c_int), ("device", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("no_symmetry", C.c_int), ("w_solver", C.c_int),
-                ("fp64_products", C.c_int), ("r_b", C.c_double)]
+                ("fp64_products", C.c_int), ("r_b", C.c_double), ("defer_scratch", C.c_int)]
 
 
 class GwPlanInfo(C.Structure):
@@ -171,7 +171,8 @@ class Plan:
                  kmesh, beta: float, tau, omega_idx, nu_idx, cutoff: float, spin: int = 2,
                  strict_kmesh: bool = False, host_only: bool = False, device: int = 0, workspace_bytes: int = 0,
                  no_symmetry: bool = False, w_solver: str = "auto", fp64_products: str = "auto",
-                 n_prod_far: Sequence[int] = None, r_b: float = 0.0, n_prod_near: Sequence[int] = None):
+                 n_prod_far: Sequence[int] = None, r_b: float = 0.0, n_prod_near: Sequence[int] = None,
+                 defer_scratch: bool = False):
         lib = load_library()
         self._lib = lib
         self._keep = []
@@ -196,7 +197,7 @@ class Plan:
                       len(nu), _ptr(nu, C.c_int))
         opt = GwOptions(int(spin), int(bool(strict_kmesh)), int(bool(host_only)), int(device), int(workspace_bytes),
                         int(bool(no_symmetry)), {"auto": 0, "gauss_jordan": 1}[w_solver],
-                        {"auto": 0, "fp64": 1}[fp64_products], float(r_b))
+                        {"auto": 0, "fp64": 1}[fp64_products], float(r_b), int(bool(defer_scratch)))
         km = (C.c_int * 3)(*[int(x) for x in kmesh])
         h = C.c_void_p()
         _check(lib.gw_plan_create(C.byref(cell), C.byref(basis), km, C.byref(grid), float(cutoff),

@@ -66,7 +66,12 @@ class System:
         import torch
         self.name, self.cell, self.precision, self.mode = name, cell, precision, mode
         self.dev = torch.device("cuda", device)
-        self.plan = gw.Plan.from_cell(cell, device=device, workspace_bytes=workspace_bytes)
+        # a mixed-precision P/Sigma system needs neither the W-solve nor the FP64 digit-product
+        # scratch: its plan defers them (and never allocates them); every other system holds
+        # its scratch from the start, so that the footprint measured when it is brought in is
+        # all it will use
+        lean = mode == "psigma" and precision == "mixed"
+        self.plan = gw.Plan.from_cell(cell, device=device, workspace_bytes=workspace_bytes, defer_scratch=lean)
         self.stream = torch.cuda.Stream(device=device)
         p, inf = self.plan, self.plan.info
         nk, nt, nn, nw = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"]
@@ -277,9 +282,17 @@ class Server:
                         continue  # the running systems hold the memory: wait
                     self.bring_in(r.system)
                     r.brought_in = True
+                    # the measured footprint may exceed the estimate admission used: evict
+                    # more idle systems until the cap holds again
+                    idle = [n for n in self.resident if n not in running and n != r.system]
+                    while self.resident_bytes() > self.mem_cap and idle:
+                        victim = idle.pop(0)
+                        self.evict(victim)
+                        self.log.append((time.perf_counter() - t0, "evict", victim, self.resident_bytes(),
+                                         self._device_used()))
                     self.log.append((time.perf_counter() - t0, "bring_in", r.system, self.resident_bytes(),
                                      self._device_used()))
-                    if self.resident_bytes() > self.mem_cap:  # the measured footprint exceeded the estimate
+                    if self.resident_bytes() > self.mem_cap:  # the running systems and this one alone exceed it
                         raise RuntimeError(f"{r.system}: resident bytes above the cap after bringing it in")
                 self.resident.move_to_end(r.system)
                 queue.remove(r)
