@@ -233,6 +233,14 @@ def stage3_flops(cell, entries, kdims, row: str) -> float:
     return f
 
 
+def p_iw_structure(inf) -> str:
+    """How P(R, tau) goes to P(R, i nu): mirror-paired when C is symmetric, and only the
+    frequencies nu >= 0 when the W solve reads no others (a w_symmetric plan)."""
+    if not inf["c_symmetric"]:
+        return "general"
+    return "mirror_nonneg" if inf["w_symmetric"] else "mirror"
+
+
 def row_work(cell, entries, kdims, row: str, c_symmetric: int):
     """Algorithmic work of one contraction row over one sweep: (real flops, DRAM bytes,
     BF16x3 tensor flops of its dense stage, FP32 flops of its small stages).
@@ -426,7 +434,7 @@ class RowSweep:
             lambda: p.green_k_to_R(self.G_k, self.G_R, stream=s),
             lambda: p.polarizability_tau(self.G_R, self.P_R, precision=self.prec, stream=s),
             lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s,
-                                       structure="mirror" if inf["c_symmetric"] else "general"),
+                                       structure=p_iw_structure(inf)),
             lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s,
                                        structure="real" if inf["w_symmetric"] else "general"),
             lambda: p.self_energy_tau(self.G_R, self.W_R, v_R=self.v_R, Sig_R=self.S_R, Sigx_R=self.Sx_R,
@@ -687,7 +695,7 @@ class Sweep:
             lambda: p.green_k_to_R(self.G_k, self.G_R, stream=s),
             lambda: p.polarizability_tau(self.G_R, self.P_R, precision=self.prec, stream=s),
             lambda: p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s,
-                                       structure="mirror" if inf["c_symmetric"] else "general"),
+                                       structure=p_iw_structure(inf)),
             lambda: p.screened_W_iw(self.P_iw, self.v_q, self.W_iw, stream=s),
             lambda: p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s,
                                        structure="real" if inf["w_symmetric"] else "general"),
@@ -1176,7 +1184,7 @@ def run_scaling(args, local):
                 plan.green_k_to_R(G_k, G_R, stream=sp)
                 plan.polarizability_tau(G_R, P_R, precision=prec, stream=sp)
                 plan.transform_tau_iw("B", "tau_to_iw", "pb", P_R, P_iw, stream=sp,
-                                      structure="mirror" if inf["c_symmetric"] else "general")
+                                      structure=p_iw_structure(inf))
                 plan.transform_tau_iw("B", "iw_to_tau", "pb", W_iw, W_R, stream=sp, structure="real")
                 plan.self_energy_tau(G_R, W_R, v_R=v_R, Sig_R=S_R, Sigx_R=Sx_R, precision=prec, stream=sp)
                 plan.transform_tau_iw("F", "tau_to_iw", "orb", S_R, S_iw, stream=sp)

@@ -216,8 +216,13 @@ gw_status gw_transform_tau_iw(gw_plan_t plan, gw_statistics st, gw_direction dir
  *   sum over mirror pairs of 2 Re(T F)), so only the nodes i < ceil(N_tau / 2) are read,
  *   the imaginary parts are written as 0, and it takes a quarter of the general flops.
  * GW_IN_REAL: the imaginary parts of `in` are zero (W~(R, i nu) from gw_screened_W_iw when
- *   the plan reports w_symmetric); they are not read, and it takes half the flops. */
-enum { GW_IN_GENERAL = 0, GW_IN_MIRROR = 1, GW_IN_REAL = 2 };
+ *   the plan reports w_symmetric); they are not read, and it takes half the flops.
+ * GW_OUT_NONNEG (with GW_IN_MIRROR): only the output slices of the sampled frequencies
+ *   nu >= 0 are written; the others keep what they held.  With the mirror-symmetric
+ *   frequency set of a w_symmetric plan these are all gw_screened_W_iw reads (it fills the
+ *   negative ones from the mirror entries, P_ab(R, -i nu) = P_ba(-R, i nu)^T); half the
+ *   columns and half the bytes written. */
+enum { GW_IN_GENERAL = 0, GW_IN_MIRROR = 1, GW_IN_REAL = 2, GW_OUT_NONNEG = 4 };
 
 /* gw_transform_tau_iw for inputs of a known structure (the symmetries of the tau grid
  * and of Eq. P_MM with symmetric product coefficients).  GW_ERR_ARG for an unknown

@@ -664,11 +664,12 @@ gw_status gw_transform_tau_iw_ex(gw_plan_t p, gw_statistics stt, gw_direction di
   gw_status st = need_device(p);
   if (st != GW_OK) return st;
   if (!in || !out) { set_last_error("bad argument"); return GW_ERR_ARG; }
-  if (structure != 0 && structure != GW_IN_MIRROR && structure != GW_IN_REAL) {
+  if (structure != 0 && structure != GW_IN_MIRROR && structure != GW_IN_REAL &&
+      structure != (GW_IN_MIRROR | GW_OUT_NONNEG)) {
     set_last_error("unknown input structure");
     return GW_ERR_ARG;
   }
-  if (structure == GW_IN_MIRROR && !(stt == GW_BOSON && dir == GW_TAU_TO_IW)) {
+  if ((structure & GW_IN_MIRROR) && !(stt == GW_BOSON && dir == GW_TAU_TO_IW)) {
     set_last_error("GW_IN_MIRROR applies to the bosonic tau -> i nu transform only");
     return GW_ERR_UNSUPPORTED;
   }
@@ -677,13 +678,22 @@ gw_status gw_transform_tau_iw_ex(gw_plan_t p, gw_statistics stt, gw_direction di
   const gw::HostPlan& h = p->h;
   if (kind == GW_BLOCK_PB && stt == GW_BOSON &&
       ((structure == GW_IN_REAL && dir == GW_IW_TO_TAU && p->ozt.ready_w) ||
-       (structure == GW_IN_MIRROR && p->ozt.ready_p)))
+       ((structure & GW_IN_MIRROR) && p->ozt.ready_p)))
     return gw::oz_transform(p->ozt, h, p->d_ent, structure, (const double2*)in, (double2*)out, p->d_status,
                             S(stream));
+  // GW_OUT_NONNEG: the slices of the frequencies nu >= 0 only (ascending sampled indices)
+  int m_begin = 0;
+  if (structure & GW_OUT_NONNEG) {
+    bool ascending = true;
+    for (int j = 1; j < h.n_nu; ++j) ascending = ascending && h.nu_idx[j] > h.nu_idx[j - 1];
+    while (ascending && m_begin < h.n_nu && h.nu_idx[m_begin] < 0) ++m_begin;
+    structure &= ~GW_OUT_NONNEG;
+  }
   if (structure == 0 && gw::oz_general_ready(p->ozt, stt == GW_FERMION, dir == GW_IW_TO_TAU, kind == GW_BLOCK_PB))
     return gw::oz_general_run(p->ozt, h, p->d_ent, stt == GW_FERMION, dir == GW_IW_TO_TAU, kind == GW_BLOCK_PB,
                               (const double2*)in, (double2*)out, p->d_status, S(stream));
   gw::TransformArgs g{};
+  g.m_begin = m_begin;
   g.ent = p->d_ent;
   const int nfreq = (stt == GW_FERMION) ? h.n_omega : h.n_nu;
   if (dir == GW_TAU_TO_IW) {

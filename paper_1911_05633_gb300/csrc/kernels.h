@@ -64,6 +64,7 @@ struct TransformArgs {
   // in-stride of in_stride slices, T = (a, b) coefficients, real output; 2: real input
   int mode;
   int in_stride;
+  int m_begin;             // first output slice written (the ones before keep their contents)
 };
 
 struct ContractArgs {

@@ -220,7 +220,7 @@ __global__ void k_transform(TransformArgs g) {
     tile[i * 32 + tx] = (c < blk) ? in[(long long)i * blk + c] : make_double2(0.0, 0.0);
   __syncthreads();
   if (c >= blk) return;
-  for (int m = ty; m < g.n_out; m += blockDim.y) {
+  for (int m = g.m_begin + ty; m < g.n_out; m += blockDim.y) {
     const double2* Tm = g.T + (long long)m * g.n_in;
     double2 acc = make_double2(0.0, 0.0);
     if (g.mode == 1) {  // Re out = sum a Re F + b Im F over the paired nodes; Im out = 0

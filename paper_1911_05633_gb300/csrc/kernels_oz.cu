@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = nt * NT + n0 + i;
-          if (j >= ncols) continue;
+          if (j >= ncols || j < g.n_skip) continue;
           const double val = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
           if (g.mode == kOzOutP) {
             const double pv = g.ms * val;  // -s is a power of two: exact
@@ -655,7 +655,17 @@ void oz_transform_free(OzTransform& o) {
 gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st) {
   const bool w = structure == GW_IN_REAL;
-  if (w ? o.fw.ready : o.fp.ready) return oz_fused_run(o, h, d_ent, structure, in, out, d_status, st);
+  if (structure == (GW_IN_MIRROR | GW_OUT_NONNEG) && o.fph.ready)
+    return oz_fused_run(o, h, d_ent, structure, in, out, d_status, st);
+  // the forms below: GW_OUT_NONNEG skips the output slices of the negative frequencies
+  int n_skip = 0;
+  if (structure & GW_OUT_NONNEG) {
+    bool ascending = true;
+    for (int j = 1; j < h.n_nu; ++j) ascending = ascending && h.nu_idx[j] > h.nu_idx[j - 1];
+    while (ascending && n_skip < h.n_nu && h.nu_idx[n_skip] < 0) ++n_skip;
+    structure &= ~GW_OUT_NONNEG;
+  }
+  if (n_skip == 0 && (w ? o.fw.ready : o.fp.ready)) return oz_fused_run(o, h, d_ent, structure, in, out, d_status, st);
   const int N = h.n_tau, nh = (N + 1) / 2, nn = h.n_nu;
   const int KS = w ? o.KS_w : o.KS_p, NT = w ? o.NT_w : o.NT_p, nts = w ? o.nt_w : o.nt_p;
   {
@@ -680,6 +690,7 @@ gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent,
     g.mode = w ? kOzOutRealToComplex : kOzOutReal;
     g.out = out;
     g.n_out = w ? N : nn;
+    g.n_skip = w ? 0 : n_skip;
     g.status = d_status;
     TimedLaunch tl_("k_oz_gemm", st);
     k_oz_gemm<<<dim3((unsigned)o.n_tiles, (unsigned)nts), 128, oz_smem(KS, NT), st>>>(g);

@@ -76,6 +76,7 @@ struct TfArgs {
   int real_in;         // 1: value k = Re in[k]; 0: value 2i + c = component c of in[i]
   double2* out;        // output, n_out slices per entry block
   int n_out;
+  int out_slice0;      // column n (kTfOutReal) goes to output slice out_slice0 + n
   int out_mode;        // kTfOut*
   int n_cols;          // columns of the column operand (all column tiles)
   int NT;              // columns per tile and accumulator (multiple of 16)
@@ -153,6 +154,62 @@ __device__ __forceinline__ void tf_add_level_wide(long long* S, const float* v, 
     const int I = 4 * hi + (__float_as_int((x - (y - 50331648.0f)) + 12582912.0f) - 0x4B400000);
     if (l <= 5) S[j] += (long long)I << (38 - 7 * l);
     else S[j] += (long long)((I + (1 << (7 * l - 39))) >> (7 * l - 38));
+  }
+}
+
+// The digit products of one K step for columns NT wide, as a schedule fixed at compile
+// time: digit s of the rows against digits t .. t + cnt - 1 of the columns (consecutive
+// planes, one MMA cnt NT wide) into accumulators slot .. slot + cnt - 1; `init`: the MMA
+// writes (does not add to) its accumulators in the first K step of a tile.
+struct TfMma {
+  int s, t, cnt, slot, init;
+};
+template <int NT>
+struct TfSchedule {
+  TfMma m[kOzDigits * kOzDigits];
+  int n;
+  constexpr TfSchedule() : m(), n(0) {
+    const int nslot = tf_nslot(NT);
+    unsigned inited = 0;
+    for (int s = 0; s < kOzDigits; ++s)
+      for (int t = 0; t <= kOzLmax - s;) {
+        const int slot = s + t < nslot - 1 ? s + t : nslot - 1;
+        int cnt = 1;
+        while (t + cnt <= kOzLmax - s && (s + t + cnt < nslot - 1 ? s + t + cnt : nslot - 1) == slot + cnt &&
+               (cnt + 1) * NT <= 256)
+          ++cnt;
+        m[n].s = s;
+        m[n].t = t;
+        m[n].cnt = cnt;
+        m[n].slot = slot;
+        m[n].init = ((inited >> slot) & 1u) ? 0 : 1;
+        inited |= ((1u << cnt) - 1u) << slot;
+        ++n;
+        t += cnt;
+      }
+  }
+};
+
+// Issues the digit products of one K step: dA, dB the descriptors of the step's first row
+// and column digit planes (planes kTfPlane and NT x 32 bytes apart: the descriptor's address
+// field counts 16-byte units).
+template <int NT>
+__device__ __forceinline__ void tf_issue_step(uint32_t tm, uint64_t dA, uint64_t dB, bool first) {
+  constexpr TfSchedule<NT> S{};
+#pragma unroll
+  for (int i = 0; i < S.n; ++i) {
+    const TfMma m = S.m[i];
+    mma_bf16(tm + (uint32_t)(m.slot * NT), dA + (uint64_t)(m.s * (kTfPlane >> 4)),
+             dB + (uint64_t)(m.t * (NT * 32 / 16)), idesc_bf16_f32(128, m.cnt * NT), (first && m.init) ? 0u : 1u);
+  }
+}
+__device__ __forceinline__ void tf_issue(int NT, uint32_t tm, uint64_t dA, uint64_t dB, bool first) {
+  switch (NT) {
+    case 16: tf_issue_step<16>(tm, dA, dB, first); break;
+    case 32: tf_issue_step<32>(tm, dA, dB, first); break;
+    case 48: tf_issue_step<48>(tm, dA, dB, first); break;
+    case 64: tf_issue_step<64>(tm, dA, dB, first); break;
+    default: tf_issue_step<80>(tm, dA, dB, first); break;
   }
 }
 
@@ -367,28 +424,13 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_con
         }
         if (!(ok = mbar_wait(&t_empty, (uint32_t)(i & 1) ^ 1u, kTfWaitNs, g.status))) break;
         fence_after_sync();
-        uint32_t inited = 0;  // accumulators written in this tile
         for (int ks = 0; ks < KS && ok; ++ks, ++step) {
           const int st = step % kTfStages;
           ok = mbar_wait(&a_full[st], (uint32_t)((step / kTfStages) & 1), kTfWaitNs, g.status);
           if (!ok) break;
           fence_after_sync();
-          const uint32_t a0 = a_base + st * kTfAStage, b0 = b_base + ks * BK;
-          for (int s = 0; s < kOzDigits; ++s) {
-            // digit s of the rows against digits t = 0 .. kOzLmax - s of the columns, as runs
-            // of consecutive column planes that land in consecutive accumulators
-            for (int tt = 0; tt <= kOzLmax - s;) {
-              const int slot = min(s + tt, nslot - 1);
-              int cnt = 1;
-              while (tt + cnt <= kOzLmax - s && min(s + tt + cnt, nslot - 1) == slot + cnt && (cnt + 1) * NT <= 256)
-                ++cnt;
-              const uint32_t acc = (inited >> slot) & 1u;
-              inited |= ((1u << cnt) - 1u) << slot;
-              mma_bf16(tm + (uint32_t)(slot * NT), smem_desc(a0 + s * kTfPlane, 128, 256),
-                       smem_desc(b0 + (uint32_t)(tt * NT * 32), 128, 256), idesc_bf16_f32(128, cnt * NT), acc);
-              tt += cnt;
-            }
-          }
+          tf_issue(NT, tm, smem_desc(a_base + st * kTfAStage, 128, 256), smem_desc(b_base + ks * BK, 128, 256),
+                   ks == 0);
           mma_commit(&a_empty[st]);
         }
         if (ok) mma_commit(&t_full);
@@ -486,7 +528,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_con
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + j;
             if (n >= g.n_cols) break;
-            dst[(long long)n * blk] = make_double2(i2d_scaled(S[j], ea + eB_s[n] - 52), 0.0);
+            dst[(long long)(g.out_slice0 + n) * blk] = make_double2(i2d_scaled(S[j], ea + eB_s[n] - 52), 0.0);
           }
         }
       }
@@ -650,6 +692,19 @@ gw_status oz_fused_init(OzTransform& o, const HostPlan& h) {
               [&](int n, int k) { return Tm[2 * ((size_t)n * nh + (k >> 1)) + (k & 1)]; }, dig, ex);
     if ((s = upload(o.fp)) != GW_OK) return s;
   }
+  // the same for the frequencies nu >= 0 only (sampled indices ascending: the first n_neg
+  // are the negative ones)
+  int n_neg = 0;
+  while (n_neg < nn && h.nu_idx[n_neg] < 0) ++n_neg;
+  bool ascending = true;
+  for (int j = 1; j < nn; ++j) ascending = ascending && h.nu_idx[j] > h.nu_idx[j - 1];
+  o.nu_nonneg0 = n_neg;
+  if (ascending && nn - n_neg <= kTfMaxNT && 2 * nh <= 16 * kTfMaxKS && n_neg > 0) {
+    const std::vector<double>& Tm = h.Tb_mirror;
+    tf_matrix(o.fph, nn - n_neg, 2 * nh, (nn - n_neg + 15) / 16 * 16,
+              [&](int n, int k) { return Tm[2 * ((size_t)(n_neg + n) * nh + (k >> 1)) + (k & 1)]; }, dig, ex);
+    if ((s = upload(o.fph)) != GW_OK) return s;
+  }
   // the general forms: complex input and output, value 2i + c of input slice i, column
   // 2m + c' of output slice m; B[2m + c'][2i + c] from T[m][i] = tr + i ti:
   // (c', c) = (0, 0): tr, (0, 1): -ti, (1, 0): ti, (1, 1): tr
@@ -671,7 +726,7 @@ gw_status oz_fused_init(OzTransform& o, const HostPlan& h) {
 }
 
 void oz_fused_free(OzTransform& o) {
-  for (OzFused* f : {&o.fw, &o.fp, &o.fg[0], &o.fg[1], &o.fg[2], &o.fg[3]}) {
+  for (OzFused* f : {&o.fw, &o.fp, &o.fph, &o.fg[0], &o.fg[1], &o.fg[2], &o.fg[3]}) {
     if (f->d_B) cudaFree(f->d_B);
     if (f->d_e) cudaFree(f->d_e);
     *f = OzFused{};
@@ -684,7 +739,8 @@ void oz_fused_free(OzTransform& o) {
 // One fused transform: `f` the column operand, `pb` the block kind (row tiles of o), the
 // input form and where the columns go.
 static gw_status tf_run(OzTransform& o, const OzFused& f, const DevEntry* d_ent, bool pb, const double2* in, int n_in,
-                        int real_in, double2* out, int n_out, int out_mode, int* d_status, cudaStream_t st) {
+                        int real_in, double2* out, int n_out, int out_mode, int* d_status, cudaStream_t st,
+                        int out_slice0 = 0) {
   TfArgs a{};
   a.ent = d_ent;
   a.tile_e = pb ? o.d_tile_e : o.d_tile_e_orb;
@@ -699,6 +755,7 @@ static gw_status tf_run(OzTransform& o, const OzFused& f, const DevEntry* d_ent,
   a.out = out;
   a.n_out = n_out;
   a.out_mode = out_mode;
+  a.out_slice0 = out_slice0;
   a.n_cols = f.n_cols;
   a.NT = f.NT;
   a.Bdig = f.d_B;
@@ -721,6 +778,8 @@ static gw_status tf_run(OzTransform& o, const OzFused& f, const DevEntry* d_ent,
 gw_status oz_fused_run(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st) {
   const bool w = structure == GW_IN_REAL;
+  if (structure == (GW_IN_MIRROR | GW_OUT_NONNEG) && o.fph.ready)
+    return tf_run(o, o.fph, d_ent, true, in, h.n_tau, 0, out, h.n_nu, kTfOutReal, d_status, st, o.nu_nonneg0);
   const OzFused& f = w ? o.fw : o.fp;
   if (!f.ready) {
     set_last_error("fused transform not planned");

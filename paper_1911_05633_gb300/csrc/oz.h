@@ -54,6 +54,7 @@ struct OzGemmArgs {
   int n_out;               // transforms: output slices
   int s0, n_tau, mirror;   // P: first computed node of the pass, N_tau, write the mirrored nodes
   double ms;               // P: -s
+  int n_skip;              // transforms (real output): columns before it are not written
   int* status;
 };
 
@@ -95,6 +96,8 @@ struct OzTransform {
   // the fused kernels (reduction <= 80 terms, <= 80 output columns); when both are ready
   // the digit planes above are not allocated
   OzFused fw, fp;
+  OzFused fph;           // fp for the frequencies nu >= 0 only (GW_OUT_NONNEG)
+  int nu_nonneg0 = 0;    // slice of the first sampled nu >= 0
   // the general complex transforms (reduction <= 128 terms, <= 256 output columns):
   // [fermionic tau -> i w, i w -> tau, bosonic tau -> i nu, i nu -> tau]
   OzFused fg[4];
@@ -116,7 +119,8 @@ gw_status oz_general_run(OzTransform& o, const HostPlan& h, const DevEntry* d_en
 gw_status oz_fused_run(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st);
 void oz_transform_free(OzTransform& o);
-// structure: GW_IN_REAL (bosonic i nu -> tau) or GW_IN_MIRROR (bosonic tau -> i nu)
+// structure: GW_IN_REAL (bosonic i nu -> tau) or GW_IN_MIRROR (bosonic tau -> i nu), with
+// GW_OUT_NONNEG the latter for the frequencies nu >= 0 only
 gw_status oz_transform(OzTransform& o, const HostPlan& h, const DevEntry* d_ent, int structure, const double2* in,
                        double2* out, int* d_status, cudaStream_t st);
 

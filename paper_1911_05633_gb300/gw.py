@@ -26,7 +26,7 @@ _PREC = {"fp64": GW_FP64, "mixed": GW_MIXED}
 _STAT = {"F": GW_FERMION, "B": GW_BOSON, "fermion": GW_FERMION, "boson": GW_BOSON}
 _DIR = {"tau_to_iw": GW_TAU_TO_IW, "iw_to_tau": GW_IW_TO_TAU}
 _BLK = {"orb": GW_BLOCK_ORB, "pb": GW_BLOCK_PB}
-_STRUCT = {"general": 0, "mirror": 1, "real": 2}
+_STRUCT = {"general": 0, "mirror": 1, "real": 2, "mirror_nonneg": 5}
 
 EXPORTED = [
     "gw_plan_create", "gw_plan_destroy", "gw_plan_query", "gw_plan_entries", "gw_plan_offsets", "gw_plan_entry_dims",
@@ -317,7 +317,8 @@ class Plan:
     def transform_tau_iw(self, stat: str, direction: str, kind: str, inp, out=None, stream=None,
                          structure: str = "general"):
         """gw_transform_tau_iw, or gw_transform_tau_iw_ex when `structure` is "mirror"
-        (input with F(beta - tau) = F(tau)*) or "real" (input with zero imaginary parts)."""
+        (input with F(beta - tau) = F(tau)*), "mirror_nonneg" (the same, writing only the
+        slices of the frequencies nu >= 0) or "real" (input with zero imaginary parts)."""
         nt = self.info["n_tau"]
         nf = self.info["n_omega"] if _STAT[stat] == GW_FERMION else self.info["n_nu"]
         n_in, n_out = (nt, nf) if _DIR[direction] == GW_TAU_TO_IW else (nf, nt)

@@ -33,6 +33,14 @@ import numpy as np
 from . import gw
 
 
+def p_iw_structure(inf) -> str:
+    """How P(R, tau) goes to P(R, i nu): mirror-paired when C is symmetric, and only the
+    frequencies nu >= 0 when the W solve reads no others (a w_symmetric plan)."""
+    if not inf["c_symmetric"]:
+        return "general"
+    return "mirror_nonneg" if inf["w_symmetric"] else "mirror"
+
+
 @dataclasses.dataclass
 class Request:
     rid: int
@@ -117,7 +125,7 @@ class System:
         p.green_k_to_R(self.G_k, self.G_R, stream=s)
         p.polarizability_tau(self.G_R, self.P_R, precision=prec, stream=s)
         p.transform_tau_iw("B", "tau_to_iw", "pb", self.P_R, self.P_iw, stream=s,
-                           structure="mirror" if inf["c_symmetric"] else "general")
+                           structure=p_iw_structure(inf))
         if self.mode == "iteration":
             p.screened_W_iw(self.P_iw, self.v_q, self.W_iw, stream=s)
         p.transform_tau_iw("B", "iw_to_tau", "pb", self.W_iw, self.W_R, stream=s,

@@ -208,6 +208,20 @@ def test_transform_structured_inputs(name):
     from paper_1911_05633_gb300 import gw
     with pytest.raises(gw.GwError):
         s.plan.transform_tau_iw("F", "tau_to_iw", "orb", dev(pack(s.G_R())), structure="mirror")
+    # only the frequencies nu >= 0: those slices as the oracle's, the others untouched
+    ref = [b[s.cell.nu_idx >= 0] for b in oracle.transform(s.orc.B_fwd, PR)]
+    sentinel = np.full(s.plan.len("pb", nn), 7.0 - 3.0j)
+    out = dev(sentinel)
+    s.plan.transform_tau_iw("B", "tau_to_iw", "pb", dev(pack(PR)), out=out, structure="mirror_nonneg")
+    out = host(out)
+    neg = s.cell.nu_idx < 0
+    got, kept = [], []
+    for e, blk in enumerate(PR):
+        o = out[s.plan.off_pb[e] * nn:s.plan.off_pb[e + 1] * nn].reshape((nn,) + blk.shape[1:])
+        got.append(o[~neg])
+        kept.append(o[neg])
+    assert rel(pack(got), pack(ref)) < TOL
+    assert np.all(pack(kept) == 7.0 - 3.0j)
 
 
 @pytest.mark.parametrize("name", SMALL + FAR + ["c0_nosym", "c1_cut5_gj"])
