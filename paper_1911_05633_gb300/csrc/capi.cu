@@ -175,6 +175,20 @@ int dense_n(const gw_plan_s* p, gw_block kind) {
   return kind == GW_BLOCK_PB ? p->h.n_pb_total() : p->h.n_orb_total();
 }
 
+// Blocks per (atom, slice) row band of the gather and scatter: enough for about four
+// blocks per SM, and no more than one per 256 elements of the widest band.
+unsigned band_splits(const gw_plan_s* p, gw_block kind, int n_slices) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  const std::vector<int>& off = kind == GW_BLOCK_PB ? p->h.pb_off : p->h.orb_off;
+  int band = 0;
+  for (int a = 0; a < p->h.n_atoms; ++a) band = std::max(band, off[a + 1] - off[a]);
+  const long long el = (long long)band * off[p->h.n_atoms];
+  const long long base = (long long)p->h.n_atoms * std::max(1, n_slices);
+  const long long want = (4LL * std::max(1, sms) + base - 1) / base;
+  return (unsigned)std::max<long long>(1, std::min<long long>({want, (el + 255) / 256, 65535}));
+}
+
 gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2* F_k, long long k_stride,
                         long long s_stride, const double2* F_sub, long long sub_k_stride, long long sub_s_stride,
                         double2* F_R, int out_n_slices, int out_slice0, double scale, cudaStream_t st,
@@ -205,10 +219,10 @@ gw_status launch_gather(gw_plan_s* p, gw_block kind, int n_slices, const double2
   g.out_n_slices = out_n_slices;
   g.out_slice0 = out_slice0;
   g.scale = scale;
-  dim3 grid(p->h.n_atoms, n_slices);
+  dim3 grid(p->h.n_atoms, n_slices, band_splits(p, kind, n_slices));
   {
     gw::TimedLaunch tl_("k_gather_k_to_R", st);
-    gw::k_gather_k_to_R<<<grid, 256, 0, st>>>(g);
+    gw::launch_gather_kernel(grid, st, g);
   }
   return check_launch("k_gather_k_to_R");
 }
@@ -239,7 +253,7 @@ gw_status launch_scatter(gw_plan_s* p, gw_block kind, int n_slices, const double
   g.k_stride = k_stride;
   g.s_stride = s_stride;
   g.ld = dense_n(p, kind);
-  dim3 grid(p->h.n_atoms, n_slices);
+  dim3 grid(p->h.n_atoms, n_slices, band_splits(p, kind, n_slices));
   {
     gw::TimedLaunch tl_("k_scatter_R_to_k", st);
     gw::k_scatter_R_to_k<<<grid, 256, 0, st>>>(g);

@@ -90,7 +90,7 @@ struct ContractArgs {
   double2* Ypre;
 };
 
-__global__ void k_gather_k_to_R(GatherArgs g);
+void launch_gather_kernel(dim3 grid, cudaStream_t st, const GatherArgs& g);
 __global__ void k_scatter_R_to_k(ScatterArgs g);
 __global__ void k_transform(TransformArgs g);
 __global__ void k_polarizability_fp64(ContractArgs g);

@@ -348,14 +348,16 @@ __device__ bool p_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
     {
       double2* Pt = Pout + (long long)it * Ka * Kb + (long long)K0 * Kb;
       double2* Pm = Pout + (long long)im * Ka * Kb + (long long)K0 * Kb;
-      for (int x = t; x < KL * Kb; x += kTG) {
-        const int klx = x / Kb, Kp = x - klx * Kb;
-        const float2 p = Ps[klx * ldp + Kp];
-        const float zr = msf * p.x, zi = msf * p.y;  // -s is a power of two: exact
-        const double dr = f2d(zr), di = f2d(zi);
-        Pt[x] = make_double2(dr, di);
-        if (mirror) Pm[x] = make_double2(dr, -di);
-      }
+      // rows over the group's warps, columns over the lanes (consecutive stores)
+      for (int klx = t >> 5; klx < KL; klx += kTG / 32)
+        for (int Kp = t & 31; Kp < Kb; Kp += 32) {
+          const float2 p = Ps[klx * ldp + Kp];
+          const float zr = msf * p.x, zi = msf * p.y;  // -s is a power of two: exact
+          const double dr = f2d(zr), di = f2d(zi);
+          const int x = klx * Kb + Kp;
+          Pt[x] = make_double2(dr, di);
+          if (mirror) Pm[x] = make_double2(dr, -di);
+        }
     }
     // a staging wider than the A buffer overwrote the B operand
     if (t == 0 && (uint32_t)(64 * ldp * 8) > c.a_bytes) c.gs->bkey = -1;
@@ -550,23 +552,24 @@ __device__ __forceinline__ void prefetch_unit(const CBatch& batch, const CUnit& 
   for (long long o = 0; o < wb; o += 32768) prefetch_l2(w + o, (uint32_t)min(32768ll, wb - o));
 }
 
-// The group's next unit: the one claimed on the previous call (or a fresh claim), with the
-// unit after it claimed now and prefetched, so that its input streams in during this one.
+// The group's next unit: the one claimed on the previous call (or a fresh claim).  After
+// the group has it, one thread of the second warp claims the unit after it and prefetches
+// that unit's input, off the path of the others, so that it streams in during this one.
 __device__ __forceinline__ bool next_unit(GroupState* gs, const CBatch& batch, const CUnit* units, int n_units,
                                           int* counter, const volatile int* status, int g, bool sigma) {
   if ((threadIdx.x % kTG) == 0) {
     int i = n_units;
     if (!(*status == 2 || gs->stop)) i = gs->next >= 0 ? gs->next : atomicAdd(counter, 1);
-    if (i < n_units) {
-      gs->u = units[i];
-      const int j = atomicAdd(counter, 1);
-      gs->next = j;
-      if (j < n_units) prefetch_unit(batch, units[j], sigma);
-    } else {
-      gs->stop = 1;
-    }
+    if (i < n_units) gs->u = units[i];
+    else gs->stop = 1;
   }
   group_sync(g);
+  if ((threadIdx.x % kTG) == 32 && !gs->stop) {
+    // read again by thread 0 only at the next call, after this unit's group barriers
+    const int j = atomicAdd(counter, 1);
+    gs->next = j;
+    if (j < n_units) prefetch_unit(batch, units[j], sigma);
+  }
   return !gs->stop;
 }
 

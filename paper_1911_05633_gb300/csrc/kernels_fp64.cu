@@ -51,13 +51,14 @@ constexpr int kHoldK = 8;  // k points held in registers by the gather and scatt
 // keeps its top-left K_a(e) x K_b(e).  With at most kHoldK k points the element's values
 // are read once for all its entries; with quarter-turn phases each term is two additions.
 // ---------------------------------------------------------------------------
+template <bool MANY_K>
 __global__ void k_gather_k_to_R(GatherArgs g) {
   const int a = blockIdx.x, s = blockIdx.y;
   const int ro = g.row_off[a];
   const int rows = g.row_off[a + 1] - ro;
   const int n_el = rows * g.ld;
   const bool hold = g.n_k_in <= kHoldK;
-  for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
+  for (int x = threadIdx.x + blockIdx.z * blockDim.x; x < n_el; x += blockDim.x * gridDim.z) {
     const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
     const int j = col - g.row_off[b];
@@ -80,6 +81,56 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
       }
       return v;
     };
+    // conj(ph[e][k]) v added to acc (real part only for real_only)
+    auto term_e = [&](int e, int kk, double2 v, double2& acc) {
+      const int k = g.k_list ? g.k_list[kk] : kk;
+      if (g.pcode) {  // conj(i^c) v = i^(4 - c) v
+        const double2 t = qmul((4 - g.pcode[(long long)e * g.n_k + k]) & 3, v);
+        acc.x += t.x;
+        if (!g.real_only) acc.y += t.y;
+      } else {
+        const double2 c = g.phase[(long long)e * g.n_k + k];
+        if (g.real_only) acc.x = fma(c.x, v.x, fma(c.y, v.y, acc.x));
+        else acc = cfma_conj_a(c, v, acc);
+      }
+    };
+    auto store = [&](int e, double2 acc) {
+      const DevEntry& E = g.ent[e];
+      const long long off = g.pb ? E.off_pb : E.off_orb;
+      const int ce = g.pb ? E.Kb : E.nb, be = (g.pb ? E.Ka : E.na) * ce;
+      if (g.scale != 1.0) {
+        acc.x *= g.scale;
+        acc.y *= g.scale;
+      }
+      g.F_R[off * g.out_n_slices + (long long)(g.out_slice0 + s) * be + i * ce + j] =
+          make_double2(acc.x, g.real_only ? 0.0 : acc.y);
+    };
+    auto keeps = [&](int e) {
+      const DevEntry& E = g.ent[e];
+      return i < (g.pb ? E.Ka : E.na) && j < (g.pb ? E.Kb : E.nb);
+    };
+    if (MANY_K && !hold && e1 - e0 <= kHoldK) {
+      // many k points: the element's values streamed once, in chunks, for all its entries
+      double2 acc[kHoldK];
+#pragma unroll
+      for (int q = 0; q < kHoldK; ++q) acc[q] = make_double2(0.0, 0.0);
+      for (int k0 = 0; k0 < g.n_k_in; k0 += kHoldK) {
+        double2 vc[kHoldK];
+#pragma unroll
+        for (int u = 0; u < kHoldK; ++u)
+          if (k0 + u < g.n_k_in) vc[u] = value(k0 + u);
+#pragma unroll
+        for (int q = 0; q < kHoldK; ++q)
+          if (q < e1 - e0 && keeps(e0 + q))
+#pragma unroll
+            for (int u = 0; u < kHoldK; ++u)
+              if (k0 + u < g.n_k_in) term_e(e0 + q, k0 + u, vc[u], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kHoldK; ++q)
+        if (q < e1 - e0 && keeps(e0 + q)) store(e0 + q, acc[q]);
+      continue;
+    }
     double2 vh[kHoldK];
     if (hold)
 #pragma unroll
@@ -124,6 +175,13 @@ __global__ void k_gather_k_to_R(GatherArgs g) {
   }
 }
 
+// The gather on `grid` x 256 threads: the form that streams each element's values once for
+// all its entries when there are more k points than registers hold.
+void launch_gather_kernel(dim3 grid, cudaStream_t st, const GatherArgs& g) {
+  if (g.n_k_in > kHoldK) k_gather_k_to_R<true><<<grid, 256, 0, st>>>(g);
+  else k_gather_k_to_R<false><<<grid, 256, 0, st>>>(g);
+}
+
 // ---------------------------------------------------------------------------
 // R -> k scatter:  F_k[k][s][oa+i][ob+j] = sum_{e in (a,b)} ph[e][k] F_R[e][s][i][j]
 // grid: (row atom a, slice); the block writes the band of rows of atom a across every
@@ -137,7 +195,7 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
   const int rows = g.row_off[a + 1] - ro;
   const int n_el = rows * g.ld;
   const bool hold = g.n_k_out <= kHoldK;
-  for (int x = threadIdx.x; x < n_el; x += blockDim.x) {
+  for (int x = threadIdx.x + blockIdx.z * blockDim.x; x < n_el; x += blockDim.x * gridDim.z) {
     const int i = x / g.ld, col = x - i * g.ld;
     const int b = g.col_atom[col];
     const int j = col - g.row_off[b];
@@ -183,6 +241,32 @@ __global__ void k_scatter_R_to_k(ScatterArgs g) {
 #pragma unroll
       for (int kk = 0; kk < kHoldK; ++kk)
         if (kk < g.n_k_out) finish(kk, acc[kk]);
+    } else if (e1 - e0 <= kHoldK) {
+      // many k points: the entries' values read once and held
+      double2 vq[kHoldK];
+      bool on[kHoldK];
+#pragma unroll
+      for (int q = 0; q < kHoldK; ++q) {
+        on[q] = false;
+        vq[q] = make_double2(0.0, 0.0);
+        if (q < e1 - e0) {
+          const DevEntry& E = g.ent[e0 + q];
+          const int re = g.pb ? E.Ka : E.na, ce = g.pb ? E.Kb : E.nb;
+          if (i < re && j < ce) {
+            const long long off = g.pb ? E.off_pb : E.off_orb;
+            vq[q] = g.F_R[off * g.in_n_slices + (long long)(g.in_slice0 + s) * re * ce + i * ce + j];
+            on[q] = true;
+          }
+        }
+      }
+      for (int kk = 0; kk < g.n_k_out; ++kk) {
+        const int k = g.k_list ? g.k_list[kk] : kk;
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < kHoldK; ++q)
+          if (on[q]) term(e0 + q, k, vq[q], acc);
+        finish(kk, acc);
+      }
     } else {
       for (int kk = 0; kk < g.n_k_out; ++kk) {
         const int k = g.k_list ? g.k_list[kk] : kk;
