@@ -31,6 +31,7 @@
 
 #include "contract.h"
 #include "fpbits.h"
+#include "ozaki.h"
 #include "ktimer.h"
 #include "smem_limit.h"
 #include "umma.h"
@@ -356,7 +357,7 @@ __device__ bool p_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
           const double dr = f2d(zr), di = f2d(zi);
           const int x = klx * Kb + Kp;
           Pt[x] = make_double2(dr, di);
-          if (mirror) Pm[x] = make_double2(dr, -di);
+          if (mirror) Pm[x] = make_double2(dr, dneg(di));
         }
     }
     // a staging wider than the A buffer overwrote the B operand

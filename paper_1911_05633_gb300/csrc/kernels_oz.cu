@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
     long long cstride;
     bool zero_im = false;
     long long moff = 0;  // P: offset of the mirrored node (0: none)
-    double msign = 1.0;
+    bool mneg = false;  // P: the mirrored node's imaginary part changes sign
     if (g.mode == kOzOutSigmaB) {
       const int Ka = E.Ka, nb2 = E.nb * E.nb;
       valid = rho < g.tau_eff * Ka * 2;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
       cstride = 2;
       if (g.mirror && im != it) {  // the mirrored node is the conjugate
         moff = 2LL * (im - it) * Ka * Kb;
-        msign = c ? -1.0 : 1.0;
+        mneg = c != 0;
       }
     } else {
       const int blk = E.Ka * E.Kb;  // transforms on the product-basis layout
@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
       zero_im = g.mode == kOzOutReal;
     }
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int ms_shift = g.ms < -1.5 ? 1 : 0;  // P: s = 2 doubles the value
     for (int n0 = 0; n0 < NT; n0 += 16) {
       long long S[16];
       float v[16];
@@ -219,12 +220,15 @@ __global__ void __launch_bounds__(128, 1) k_oz_gemm(OzGemmArgs g) {
         for (int i = 0; i < 16; ++i) {
           const int j = nt * NT + n0 + i;
           if (j >= ncols || j < g.n_skip) continue;
-          const double val = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
           if (g.mode == kOzOutP) {
-            const double pv = g.ms * val;  // -s is a power of two: exact
+            // -s (s = 1 or 2) folded into the integer and the exponent: exact, no FP64 arithmetic
+            const double pv = i2d_scaled(-S[i], ea + eb[n0 + i] - 52 + ms_shift);
             orow[(long long)j * cstride] = pv;
-            if (moff) orow[(long long)j * cstride + moff] = msign * pv;
-          } else if (g.mode == kOzOutRealToComplex) {
+            if (moff) orow[(long long)j * cstride + moff] = mneg ? dneg(pv) : pv;
+            continue;
+          }
+          const double val = i2d_scaled(S[i], ea + eb[n0 + i] - 52);
+          if (g.mode == kOzOutRealToComplex) {
             // columns 0 .. n_out-1: Re of slice j; n_out .. 2 n_out-1: Im of slice j - n_out
             const int sl = j < g.n_out ? j : j - g.n_out;
             orow[(long long)sl * cstride + (j < g.n_out ? 0 : 1)] = val;

@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_con
             const double im = i2d_scaled(S[j + 1], ea + eB_s[n + 1] - 52);
             dst[(long long)m * blk] = make_double2(re, im);
             if (g.out_mode == kTfOutMirror && g.n_out - 1 - m != m)
-              dst[(long long)(g.n_out - 1 - m) * blk] = make_double2(re, -im);
+              dst[(long long)(g.n_out - 1 - m) * blk] = make_double2(re, dneg(im));
           }
         } else {
 #pragma unroll

@@ -55,6 +55,12 @@ __device__ __forceinline__ uint32_t digit_bf16(int d, int s) {
 }
 
 
+// -x by flipping the sign bit (an integer operation: negating a double is an FP64
+// instruction, which this chip issues at a small fraction of its other rates).
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // S 2^e as a double for a 64-bit integer S, from the bit fields: normalise, round the
 // 64-bit magnitude to 53 bits (ties to even), add e to the exponent.  |e| and |S| keep
 // the result a normal double in every use here.
