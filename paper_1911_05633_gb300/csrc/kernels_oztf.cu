@@ -236,12 +236,10 @@ __device__ __forceinline__ void tf_add_pair(long long* S, const float* v, int l)
   }
 }
 
-// HOLD: the slicers keep a tile's values in registers between the scale pass and the
-// digits (reductions up to 80 terms); otherwise they load them again per K step.
 // WIDE: level sums may exceed 2^22 (reductions beyond 102 terms).
 // STAGE: the epilogue stages its 64-bit sums in shared memory and releases the tensor
 // memory before converting and storing them (two A stages instead of three).
-template <int KS, bool HOLD, bool WIDE, bool STAGE>
+template <int KS, bool WIDE, bool STAGE>
 __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_constant__ TfArgs g) {
   constexpr int kTfStages = STAGE ? 2 : 3;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -353,23 +351,14 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_con
         fence_smem_to_async();
         mbar_arrive(&a_full[st]);
       };
-      double v[HOLD ? KS : 1][8];
+      // the scale pass, one K step at a time; the cut reads the values again (from L2)
       int mx = 0;
-      if constexpr (HOLD) {  // every load in flight at once, the values kept
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) load8(ks, v[ks]);
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks)
-#pragma unroll
-          for (int u = 0; u < 8; ++u) mx = max(mx, exp_field(v[ks][u]));
-      } else {  // one K step at a time (the second pass reads them again, from L2)
 #pragma unroll 1
-        for (int ks = 0; ks < KS; ++ks) {
-          double w[8];
-          load8(ks, w);
+      for (int ks = 0; ks < KS; ++ks) {
+        double w[8];
+        load8(ks, w);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) mx = max(mx, exp_field(w[u]));
-        }
+        for (int u = 0; u < 8; ++u) mx = max(mx, exp_field(w[u]));
       }
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
       const int e = mx > 0 ? mx - 1022 : 0;
@@ -378,24 +367,14 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_oz_transform(const __grid_con
       if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
       if (h == 0) eA_s[b][r] = e;
       mbar_arrive(&e_full[b]);
-      if constexpr (HOLD) {
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks, ++step) {
-          const int st = step % kTfStages;
-          ok = mbar_wait(&a_empty[st], (uint32_t)((step / kTfStages) & 1) ^ 1u, kTfWaitNs, g.status);
-          if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-          cut(v[ks], e, st);
-        }
-      } else {
 #pragma unroll 1
-        for (int ks = 0; ks < KS; ++ks, ++step) {
-          double w[8];
-          load8(ks, w);
-          const int st = step % kTfStages;
-          ok = mbar_wait(&a_empty[st], (uint32_t)((step / kTfStages) & 1) ^ 1u, kTfWaitNs, g.status);
-          if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-          cut(w, e, st);
-        }
+      for (int ks = 0; ks < KS; ++ks, ++step) {
+        double w[8];
+        load8(ks, w);
+        const int st = step % kTfStages;
+        ok = mbar_wait(&a_empty[st], (uint32_t)((step / kTfStages) & 1) ^ 1u, kTfWaitNs, g.status);
+        if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+        cut(w, e, st);
       }
     }
     if (!ok) atomicExch(g.status, 2);
@@ -569,7 +548,6 @@ void tf_matrix(OzFused& f, int n_cols, int K, int NT, F value, std::vector<uint1
   f.n_cols = n_cols;
   f.NT = NT;
   f.n_ct = (n_cols + NT - 1) / NT;
-  f.hold = f.KS <= kTfMaxKS;
   f.wide = f.K > 102;  // level sums may pass 2^22
   const size_t tile = (size_t)f.KS * kOzDigits * NT * 16;  // uint16 per column tile
   dig.assign(tile * f.n_ct, 0);
@@ -595,39 +573,39 @@ void tf_matrix(OzFused& f, int n_cols, int K, int NT, F value, std::vector<uint1
 
 // Raises the instance's dynamic shared-memory limit, or (static_only) reports its static
 // shared memory in *stat.
-template <int KS, bool HOLD, bool WIDE, bool STAGE>
+template <int KS, bool WIDE, bool STAGE>
 cudaError_t tf_raise(size_t smem, bool static_only, size_t* stat) {
   if (static_only) {
     cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, k_oz_transform<KS, HOLD, WIDE, STAGE>);
+    const cudaError_t e = cudaFuncGetAttributes(&a, k_oz_transform<KS, WIDE, STAGE>);
     *stat = a.sharedSizeBytes;
     return e;
   }
-  return raise_smem_limit(k_oz_transform<KS, HOLD, WIDE, STAGE>, smem);
+  return raise_smem_limit(k_oz_transform<KS, WIDE, STAGE>, smem);
 }
 cudaError_t tf_raise_ks(int KS, size_t smem, bool static_only = false, size_t* stat = nullptr) {
   switch (KS) {
-    case 1: return tf_raise<1, true, false, true>(smem, static_only, stat);
-    case 2: return tf_raise<2, true, false, true>(smem, static_only, stat);
-    case 3: return tf_raise<3, true, false, true>(smem, static_only, stat);
-    case 4: return tf_raise<4, true, false, true>(smem, static_only, stat);
-    case 5: return tf_raise<5, true, false, true>(smem, static_only, stat);
-    case 6: return tf_raise<6, false, false, false>(smem, static_only, stat);
-    case 7: return tf_raise<7, false, true, false>(smem, static_only, stat);
-    default: return tf_raise<8, false, true, false>(smem, static_only, stat);
+    case 1: return tf_raise<1, false, true>(smem, static_only, stat);
+    case 2: return tf_raise<2, false, true>(smem, static_only, stat);
+    case 3: return tf_raise<3, false, true>(smem, static_only, stat);
+    case 4: return tf_raise<4, false, true>(smem, static_only, stat);
+    case 5: return tf_raise<5, false, true>(smem, static_only, stat);
+    case 6: return tf_raise<6, false, false>(smem, static_only, stat);
+    case 7: return tf_raise<7, true, false>(smem, static_only, stat);
+    default: return tf_raise<8, true, false>(smem, static_only, stat);
   }
 }
 
 void tf_launch(int KS, unsigned grid, size_t smem, cudaStream_t st, const TfArgs& a) {
   switch (KS) {
-    case 1: k_oz_transform<1, true, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 2: k_oz_transform<2, true, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 3: k_oz_transform<3, true, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 4: k_oz_transform<4, true, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 5: k_oz_transform<5, true, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 6: k_oz_transform<6, false, false, false><<<grid, kTfThreads, smem, st>>>(a); break;
-    case 7: k_oz_transform<7, false, true, false><<<grid, kTfThreads, smem, st>>>(a); break;
-    default: k_oz_transform<8, false, true, false><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 1: k_oz_transform<1, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 2: k_oz_transform<2, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 3: k_oz_transform<3, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 4: k_oz_transform<4, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 5: k_oz_transform<5, false, true><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 6: k_oz_transform<6, false, false><<<grid, kTfThreads, smem, st>>>(a); break;
+    case 7: k_oz_transform<7, true, false><<<grid, kTfThreads, smem, st>>>(a); break;
+    default: k_oz_transform<8, true, false><<<grid, kTfThreads, smem, st>>>(a); break;
   }
 }
 

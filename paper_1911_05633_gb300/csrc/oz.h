@@ -66,7 +66,6 @@ struct OzFused {
   int K = 0, KS = 0;        // reduction length, 16-wide steps (<= 8)
   int n_cols = 0, NT = 0;   // columns, and columns per tile (a multiple of 16, <= 80)
   int n_ct = 0;             // column tiles
-  bool hold = false;        // the slicers keep a tile's values (KS <= 5)
   bool wide = false;        // level sums may pass 2^22 (K > 102)
   bool stage = false;       // the epilogue stages its sums in shared memory (KS <= 5)
   uint16_t* d_B = nullptr;  // per column tile [KS][kOzDigits][NT x 16]
