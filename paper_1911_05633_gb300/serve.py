@@ -58,6 +58,12 @@ class Request:
         return self.done - self.arrival
 
 
+def is_lean(mode: str, precision: str) -> bool:
+    """A mixed-precision P/Sigma system: its plan holds no scratch and can stay on the device
+    while the system is not resident (its tables are small next to the system's buffers)."""
+    return mode == "psigma" and precision == "mixed"
+
+
 def _bytes(*ts) -> int:
     return int(sum(t.numel() * t.element_size() for t in ts))
 
@@ -70,17 +76,26 @@ class System:
     from `w_seed` (real, as the W solve returns it for these plans)."""
 
     def __init__(self, name: str, cell, device: int = 0, precision: str = "fp64", mode: str = "iteration",
-                 workspace_bytes: int = 2 << 30, w_seed: int = 0, state: Optional[dict] = None):
+                 workspace_bytes: int = 2 << 30, w_seed: int = 0, state: Optional[dict] = None, plan=None):
         import torch
         self.name, self.cell, self.precision, self.mode = name, cell, precision, mode
         self.dev = torch.device("cuda", device)
         # a mixed-precision P/Sigma system needs neither the W-solve nor the FP64 digit-product
         # scratch: its plan defers them (and never allocates them); every other system holds
         # its scratch from the start, so that the footprint measured when it is brought in is
-        # all it will use
-        lean = mode == "psigma" and precision == "mixed"
-        self.plan = gw.Plan.from_cell(cell, device=device, workspace_bytes=workspace_bytes, defer_scratch=lean)
+        # all it will use.  `plan`: a plan kept from an earlier residency (lean systems only)
+        if plan is None:
+            plan = gw.Plan.from_cell(cell, device=device, workspace_bytes=workspace_bytes,
+                                     defer_scratch=is_lean(mode, precision))
+        self.plan = plan
         self.stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(self.stream):
+            self._setup(cell, w_seed, state)
+        # this system's own work only: other systems' requests keep running meanwhile
+        self.stream.synchronize()
+
+    def _setup(self, cell, w_seed, state):
+        import torch
         p, inf = self.plan, self.plan.info
         nk, nt, nn, nw = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"]
         No = inf["n_orb_total"]
@@ -92,7 +107,7 @@ class System:
         self.S_k, self.Sx_k = z(nk * nw * No * No), z(nk * No * No)
         bufs = [self.G_k, self.G_R, self.P_R, self.P_iw, self.W_iw, self.W_R, self.S_R, self.Sx_R, self.S_iw,
                 self.S_k, self.Sx_k]
-        if mode == "iteration":
+        if self.mode == "iteration":
             vq, _ = cell.coulomb()
             self.v_q = torch.from_numpy(vq.reshape(-1)).to(self.dev)
             self.H_k = torch.from_numpy(cell.H_k.reshape(-1)).to(self.dev)
@@ -108,16 +123,21 @@ class System:
             self.G_k.copy_(torch.from_numpy(cell.green_k_tau().reshape(-1)))
             self.mu = float(cell.mu)
         else:
-            self.G_k.copy_(state["G_k"])
+            self.G_k.copy_(state["G_k"], non_blocking=True)  # pinned host state
             self.mu = state["mu"]
-        torch.cuda.synchronize(self.dev)
         self.buffer_bytes = _bytes(*bufs)
 
-    def state(self) -> dict:
-        """The iteration state, copied to the host (for eviction)."""
+    def state(self) -> Optional[dict]:
+        """The iteration state, copied to pinned host memory (for eviction); None when it
+        cannot have changed since it was brought in (P/Sigma requests leave G alone)."""
         import torch
-        torch.cuda.synchronize(self.dev)
-        return {"G_k": self.G_k.cpu(), "mu": self.mu}
+        if self.mode != "iteration":
+            return None
+        host = torch.empty(self.G_k.numel(), dtype=self.G_k.dtype, pin_memory=True)
+        with torch.cuda.stream(self.stream):
+            host.copy_(self.G_k, non_blocking=True)
+        self.stream.synchronize()
+        return {"G_k": host, "mu": self.mu}
 
     def _rows(self):
         """The P and Sigma rows on the current G(k, tau), enqueued on this system's stream."""
@@ -143,7 +163,10 @@ class System:
         import torch
         with torch.cuda.stream(self.stream):
             self._rows()
-            sig = self.S_k.clone() if keep_sigma else None
+            sig = None
+            if keep_sigma:  # to pinned host memory: nothing outside the footprint stays on the device
+                sig = torch.empty(self.S_k.numel(), dtype=self.S_k.dtype, pin_memory=True)
+                sig.copy_(self.S_k, non_blocking=True)
             if self.mode == "iteration":
                 s = self.stream.cuda_stream
                 n_el = float(self.cell.n_orb_total)
@@ -163,9 +186,10 @@ class System:
     def finish(self):
         self.plan.sync(stream=self.stream.cuda_stream)
 
-    def close(self):
+    def close(self, keep_plan: bool = False):
         self.finish()
-        self.plan.close()
+        if not keep_plan:
+            self.plan.close()
         for k in ("G_k", "G_R", "P_R", "P_iw", "W_iw", "W_R", "S_R", "Sx_R", "S_iw", "S_k", "Sx_k", "v_q", "H_k",
                   "v_R"):
             if hasattr(self, k):
@@ -182,6 +206,7 @@ class SystemSpec:
         self.w_seed, self.workspace_bytes = w_seed, workspace_bytes
         self.state: Optional[dict] = None
         self.measured: Optional[int] = None
+        self.plan = None  # a lean system's plan, kept while the system is not resident
         hp = gw.Plan.from_cell(cell, host_only=True)
         inf = hp.info
         nk, nt, nn, nw, No = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"], inf["n_orb_total"]
@@ -202,7 +227,8 @@ class SystemSpec:
         now, so that bringing the system in later only copies it up."""
         import torch
         if self.state is None:
-            self.state = {"G_k": torch.from_numpy(self.cell.green_k_tau().reshape(-1)), "mu": float(self.cell.mu)}
+            G_k = torch.from_numpy(self.cell.green_k_tau().reshape(-1))
+            self.state = {"G_k": G_k.pin_memory() if torch.cuda.is_available() else G_k, "mu": float(self.cell.mu)}
 
 
 class Server:
@@ -231,27 +257,44 @@ class Server:
         if self.meter is not None:
             return int(self.meter())
         import torch
-        torch.cuda.synchronize(self.device)
+        # the driver's count (allocations are synchronous calls): no device synchronisation,
+        # which would wait for every request in flight
         free, total = torch.cuda.mem_get_info(self.device)
         return int(total - free)
 
     def bring_in(self, name: str):
         spec = self.specs[name]
+        # the footprint is measured once, the first time the system comes in, with the device
+        # quiet (no other request allocating or freeing meanwhile); later bring-ins reuse it
+        # and wait for nothing but their own setup
+        measure = spec.measured is None
+        if measure and self.factory is None:
+            import torch
+            torch.cuda.synchronize(self.device)
         before = self._device_used()
         if self.factory is not None:
             sysm = self.factory(spec, spec.state)
         else:
             sysm = System(name, spec.cell, device=self.device, precision=spec.precision, mode=spec.mode,
-                          workspace_bytes=spec.workspace_bytes, w_seed=spec.w_seed, state=spec.state)
-        spec.measured = max(self._device_used() - before, sysm.buffer_bytes)
+                          workspace_bytes=spec.workspace_bytes, w_seed=spec.w_seed, state=spec.state,
+                          plan=spec.plan)
+            if is_lean(spec.mode, spec.precision):
+                spec.plan = sysm.plan
+        if measure:
+            spec.measured = max(self._device_used() - before, sysm.buffer_bytes)
         self.resident[name] = sysm
         return sysm
 
     def evict(self, name: str):
         sysm = self.resident.pop(name)
         spec = self.specs[name]
-        spec.state = sysm.state()
-        sysm.close()
+        st = sysm.state()
+        if st is not None:
+            spec.state = st
+        if self.factory is None:
+            sysm.close(keep_plan=spec.plan is not None)
+        else:
+            sysm.close()
         del sysm
         if self.factory is None:
             import torch
@@ -260,7 +303,18 @@ class Server:
     def close(self):
         for n in list(self.resident):
             self.evict(n)
+        for spec in self.specs.values():
+            if getattr(spec, "plan", None) is not None:
+                spec.plan.close()
+                spec.plan = None
         self.pool.shutdown()
+
+    def _victims(self, running, queue, keep: str = "") -> List[str]:
+        """Idle resident systems in the order to evict them: those no queued request waits
+        for first, each group least recently used first."""
+        wanted = {r.system for r in queue}
+        idle = [n for n in self.resident if n not in running and n != keep]
+        return [n for n in idle if n not in wanted] + [n for n in idle if n in wanted]
 
     def run(self, arrivals: Sequence[tuple], keep_sigma: bool = False, poll_s: float = 20e-6) -> List[Request]:
         """Serve `arrivals` = [(seconds after start, system name), ...]; returns the requests
@@ -280,7 +334,7 @@ class Server:
                 spec = self.specs[r.system]
                 if r.system not in self.resident:
                     need = spec.footprint
-                    idle = [n for n in self.resident if n not in running]
+                    idle = self._victims(running, queue)
                     while self.resident_bytes() + need > self.mem_cap and idle:
                         victim = idle.pop(0)
                         self.evict(victim)
@@ -292,7 +346,7 @@ class Server:
                     r.brought_in = True
                     # the measured footprint may exceed the estimate admission used: evict
                     # more idle systems until the cap holds again
-                    idle = [n for n in self.resident if n not in running and n != r.system]
+                    idle = self._victims(running, queue, keep=r.system)
                     while self.resident_bytes() > self.mem_cap and idle:
                         victim = idle.pop(0)
                         self.evict(victim)
