@@ -45,6 +45,13 @@ TRAFFIC = {
     # bench.py --small captures (56 matrices of N_PB = 384 per launch): DRAM read + write / 56
     "k_gj_inverse_f32": {"file": "kernels_wtc.cu", "src_sha": "818f6fc1dcc6cb59",
                          "bytes_per_unit": (66.10e6 + 254.12e6) / 56},
+    # bench.py --atoms 8 captures (profiles/k_contract_diamond8_small.md): 352 entries of the
+    # same species as the 72-atom cell; units are (entry, node) pairs: 352 x 64 for Sigma,
+    # 352 x 32 computed nodes for P (each writing its node and the mirrored one)
+    "k_contract_s_tc": {"file": "kernels_contract.cu", "src_sha": "d086e265316d2289",
+                        "bytes_per_unit": (1.506191e9 + 0.031040e9) / (352 * 64)},
+    "k_contract_p_tc": {"file": "kernels_contract.cu", "src_sha": "d086e265316d2289",
+                        "bytes_per_unit": (0.029749e9 + 1.461140e9) / (352 * 32)},
 }
 
 
@@ -514,6 +521,12 @@ def dominant_contraction_roofline(kt, steps, cell, plan, peaks, fp32_peak, fp64_
     ms, nl = cands[k]
     roof = contraction_roofline(k, ms / steps, nl / steps, work, peaks, fp32_peak, fp64_peak, mixed)
     roof["row"] = {"P": "a2 (Eq. P_MM)", "S": "a7 (Eq. S_MM)"}[row]
+    if mixed:
+        # (entry, node) units of one step: Sigma every node and the exchange's one slice,
+        # P the computed nodes
+        E, nt = len(ent), cell.n_tau
+        per_step = E * (nt + 1) if row == "S" else E * ((nt + 1) // 2 if inf["c_symmetric"] else nt)
+        roof["traffic"] = traffic_of(k, per_step / (nl / steps))
     return roof
 
 
@@ -1279,7 +1292,8 @@ def run_serve(args, local):
                                        "footprint_GB": round(sp.footprint / 1e9, 2)} for n, sp in specs.items()},
                        "mem_cap_GB": round(cap / 1e9, 1), "sum_of_footprints_GB": round(total / 1e9, 1),
                        "admission": "arrival order; one request per system at a time; a system not resident is "
-                                    "brought in on admission, idle residents evicted least recently used first"},
+                                    "brought in on admission, idle residents evicted least recently used first "
+                                    "(those no queued request waits for before the others)"},
             "prepare_s": round(t_prep, 1), "alone_ms": alone, "series": series, "evictions": evictions}
 
 
