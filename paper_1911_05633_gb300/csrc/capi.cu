@@ -363,12 +363,14 @@ static gw_status alloc_oz_sigma(gw_plan_s* p) {
   const gw_status st = gw::oz_sigma_init(p->oz, p->h, (size_t)4 << 30);
   p->oz_pending = false;
   if (st != GW_OK) return st;
+  if (gw::uploads_landed() != cudaSuccess) return GW_ERR_CUDA;
   p->sigma_tensor = p->oz.ready;
   return GW_OK;
 }
 static gw_status alloc_oz_pol(gw_plan_s* p) {
   const gw_status st = gw::oz_pol_init(p->ozp, p->h, (size_t)4 << 30);
   p->ozp_pending = false;
+  if (st == GW_OK && gw::uploads_landed() != cudaSuccess) return GW_ERR_CUDA;
   return st;
 }
 
@@ -558,6 +560,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     if ((st = gw::oz_transform_init(p->ozt, h)) != GW_OK) return fail(st);
     if (defer) p->ozp_pending = true;
     else if ((st = alloc_oz_pol(p)) != GW_OK) return fail(st);
+  }
+  if (gw::uploads_landed() != cudaSuccess) {
+    set_last_error("plan tables did not reach the device");
+    return fail(GW_ERR_CUDA);
   }
   *out = p;
   return GW_OK;
@@ -1353,6 +1359,7 @@ gw_status batch_upload_units(gw_batch_s* b, bool sigma, int order) {
     if (st != GW_OK) return st;
   }
   GW_CUDA(cudaMemcpy(d, u.data(), u.size() * sizeof(gw::CUnit), cudaMemcpyHostToDevice));
+  GW_CUDA(gw::uploads_landed());
   (sigma ? b->nS : b->nP) = (int)u.size();
   (sigma ? b->orderS : b->orderP) = order;
   return GW_OK;
@@ -1404,6 +1411,7 @@ gw_status gw_batch_create(const gw_plan_t* plans, int n_plans, gw_batch_t* out) 
   if (st == GW_OK) st = upload(&b->d_counter, nullptr, 16);
   if (st == GW_OK) st = upload(&b->d_status, nullptr, 16);
   if (st == GW_OK && cudaMemset(b->d_status, 0, 16) != cudaSuccess) st = GW_ERR_CUDA;
+  if (st == GW_OK && gw::uploads_landed() != cudaSuccess) st = GW_ERR_CUDA;
   if (st != GW_OK) {
     gw_batch_destroy(b);
     return st;
@@ -1482,6 +1490,8 @@ gw_status gw_batch_tune(gw_batch_t b, const void* const* G_R, void* const* P_R, 
   if (!b || !G_R || !P_R || !Wt_R || !Sig_R || reps < 1) return GW_ERR_ARG;
   DeviceGuard guard(b->device);
   cudaStream_t st = S(stream);
+  // the unit tables are rewritten between candidates: nothing on the stream may read them
+  GW_CUDA(cudaStreamSynchronize(st));
   cudaEvent_t e0, e1;
   GW_CUDA(cudaEventCreate(&e0));
   GW_CUDA(cudaEventCreate(&e1));

@@ -7,6 +7,14 @@
 
 namespace gw {
 
+// The library's tables go up with cudaMemcpy from pageable host memory (and flags are
+// cleared with cudaMemset) on the legacy default stream.  Such a copy can return before it
+// has landed, and the callers' streams (created non-blocking) are not ordered after the
+// legacy stream: wait for it before any kernel on another stream may read what was
+// uploaded.  Called once at the end of each setup that uploads.
+inline cudaError_t uploads_landed() { return cudaStreamSynchronize(cudaStreamLegacy); }
+
+
 struct GatherArgs {
   const DevEntry* ent;
   const int* pair_start;   // [n_atoms^2 + 1] entry range of each ordered atom pair

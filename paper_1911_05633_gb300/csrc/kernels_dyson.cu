@@ -164,6 +164,11 @@ gw_status dyson_init(DysonPlan& d, const HostPlan& h) {
     set_last_error("Dyson transform: too many fermionic frequencies for shared memory");
     return GW_ERR_UNSUPPORTED;
   }
+  if (uploads_landed() != cudaSuccess) {
+    dyson_free(d);
+    set_last_error("Dyson tables did not reach the device");
+    return GW_ERR_CUDA;
+  }
   d.ready = true;
   return GW_OK;
 }
