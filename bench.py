@@ -1264,37 +1264,49 @@ def run_serve(args, local):
         sp.prepare()
     t_prep = time.perf_counter() - t0
     names = list(specs)
-    free, _ = torch.cuda.mem_get_info(local)
-    server = Server(specs, mem_cap_bytes=int(0.9 * free), device=local)
+    # the cap (the device pool the systems' buffers live in): well below the sum of the
+    # footprints, which are exact from the plans' sizes
+    total = sum(sp.footprint for sp in specs.values())
+    cap = max(int(0.4 * total), int(1.5 * max(sp.footprint for sp in specs.values())))
+    server = Server(specs, mem_cap_bytes=cap, device=local)
     alone = {}
-    for n in names:  # service time of each system alone, brought in and resident; measures its footprint
+    for n in names:  # service time of each system alone, brought in and resident; measures its plan
         server.run([(0.0, n)])
         lat = [server.run([(0.0, n)])[0].latency for _ in range(2)]
         alone[n] = round(1e3 * float(np.median(lat)), 3)
         server.evict(n)
-    # the cap for the sweep, from the measured footprints: well below their sum
-    total = sum(sp.footprint for sp in specs.values())
-    cap = max(int(0.4 * total), int(1.5 * max(sp.footprint for sp in specs.values())))
-    server.mem_cap = cap
     mean_service = float(np.mean(list(alone.values()))) / 1e3
     series = []
+    for k in ("wait_closes_s", "make_s", "make_plan_s", "close_s"):
+        server.timing[k].clear()
     for f in (0.5, 1.0, 2.0, 4.0):  # offered load relative to one system at a time
         rate = f / mean_service
         reqs = server.run(poisson_arrivals(rate, 40 * max(1, args.steps // 5), names, seed=int(f * 100)))
         series.append({"offered_per_s": round(rate, 2), "load_vs_serial": f, **latency_stats(reqs)})
     evictions = sum(1 for e in server.log if e[1] == "evict")
+    tm = server.timing
+    ms = lambda v: {"n": len(v), "mean_ms": round(1e3 * float(np.mean(v)), 2) if v else None,
+                    "p90_ms": round(1e3 * float(np.percentile(v, 90)), 2) if v else None}
+    bring = {"waiting_for_evictions": ms(tm["wait_closes_s"]), "making": ms(tm["make_s"]),
+             "making_plans": ms(tm["make_plan_s"]),
+             "evicting": ms(tm["close_s"])}
     server.close()
     return {"metric": "serve p50/p99 latency of P/Sigma evaluations and whole GW iterations (continuous batching)",
             "unit": "ms", "precision": prec, "data": "synthetic",
             "config": {"systems": {n: {"atoms": sp.cell.n_atoms, "orbitals": sp.cell.n_orb_total,
                                        "n_pb": sp.cell.n_pb_total, "k": int(np.prod(sp.cell.kmesh)),
                                        "tau": sp.cell.n_tau, "request": sp.mode,
-                                       "footprint_GB": round(sp.footprint / 1e9, 2)} for n, sp in specs.items()},
+                                       "footprint_GB": round(sp.footprint / 1e9, 2),
+                                       "plan_GB": round((sp.plan_bytes or 0) / 1e9, 3)} for n, sp in specs.items()},
                        "mem_cap_GB": round(cap / 1e9, 1), "sum_of_footprints_GB": round(total / 1e9, 1),
-                       "admission": "arrival order; one request per system at a time; a system not resident is "
-                                    "brought in on admission, idle residents evicted least recently used first "
-                                    "(those no queued request waits for before the others)"},
-            "prepare_s": round(t_prep, 1), "alone_ms": alone, "series": series, "evictions": evictions}
+                       "admission": "arrival order; one request per system at a time; the buffers of resident "
+                                    "systems in one device pool of the cap's size; a system not resident is "
+                                    "brought in on admission into a free range of the pool, idle residents "
+                                    "evicted least recently used first (those no queued request waits for "
+                                    "before the others) until one range holds it; bring-ins and evictions off "
+                                    "the request loop"},
+            "prepare_s": round(t_prep, 1), "alone_ms": alone, "series": series, "evictions": evictions,
+            "bring_in": bring}
 
 
 def main():

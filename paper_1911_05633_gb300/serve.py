@@ -11,14 +11,16 @@ Two kinds of request:
   G(R, tau), P(R, tau), P(R, i nu), W~(R, tau), Sigma(R, tau) + Sigma_x, Sigma(k, i w).
 
 A system is resident when its plan and buffers live on the device; G(k, tau) (and the
-chemical potential) carry from one iteration to the next.  A request is admitted in
-arrival order as soon as its system is idle and the resident bytes fit the cap; a
-system that is not resident is brought in on admission (its plan built, its state
-copied up), evicting idle resident systems least recently used first (their state
-copied to the host) while the cap would be exceeded.  Requests of different systems
-run concurrently, each on its system's CUDA stream (an iteration in a worker thread,
-because the chemical-potential search synchronises its stream).  Latency is
-completion minus arrival.
+chemical potential) carry from one iteration to the next.  The buffers of every resident
+system are ranges of one device pool of the cap's size, allocated once: a request is
+admitted in arrival order as soon as its system is idle and, for a system that is not
+resident, a range of the pool holds its buffers -- idle resident systems are evicted
+least recently used first (their state copied to the host) until one does.  Bringing a
+system in (its plan, its state copied up) and evicting one allocate and free nothing on
+the device, and both run off the request loop.  Requests of different systems run
+concurrently, each on its system's CUDA stream (an iteration in a worker thread, because
+the chemical-potential search synchronises its stream).  Latency is completion minus
+arrival.
 """
 from __future__ import annotations
 
@@ -58,14 +60,76 @@ class Request:
         return self.done - self.arrival
 
 
+def arena_words(inf, mode: str) -> Dict[str, int]:
+    """The complex words of each buffer of a system (plan info `inf`), in arena order."""
+    nk, nt, nn, nw = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"]
+    No, Npb, lo, lp = inf["n_orb_total"], inf["n_pb_total"], inf["len_orb"], inf["len_pb"]
+    w = {"G_k": nk * nt * No * No, "G_R": lo * nt, "P_R": lp * nt, "P_iw": lp * nn, "W_iw": lp * nn,
+         "W_R": lp * nt, "S_R": lo * nt, "Sx_R": lo, "S_iw": lo * nw, "S_k": nk * nw * No * No,
+         "Sx_k": nk * No * No, "v_R": lp}
+    if mode == "iteration":
+        w.update(v_q=nk * Npb * Npb, H_k=nk * No * No)
+    return {k: int(v) for k, v in w.items()}
+
+
+class DevicePool:
+    """One device buffer of `size` bytes handed out in ranges: first fit, aligned to
+    `align` bytes (2 MiB on a device), a freed range merged with its free neighbours.
+    With device=None it only keeps the books (no memory behind the ranges)."""
+
+    ALIGN = 2 << 20
+
+    def __init__(self, size: int, device: Optional[int] = None, align: Optional[int] = None):
+        self.align = int(align) if align is not None else (self.ALIGN if device is not None else 1)
+        self.size = int(size) - int(size) % self.align
+        self.free: List[tuple] = [(0, self.size)] if self.size > 0 else []  # (offset, bytes), by offset
+        self.buf = None
+        if device is not None:
+            import torch
+            self.buf = torch.empty(self.size, dtype=torch.uint8, device=torch.device("cuda", device))
+
+    def _round(self, n: int) -> int:
+        return -(-int(n) // self.align) * self.align
+
+    def alloc(self, n: int) -> Optional[int]:
+        """The offset of a free range of n bytes (rounded up), or None when none is free."""
+        n = self._round(n)
+        for i, (off, m) in enumerate(self.free):
+            if m >= n:
+                if m == n:
+                    del self.free[i]
+                else:
+                    self.free[i] = (off + n, m - n)
+                return off
+        return None
+
+    def release(self, off: int, n: int):
+        n = self._round(n)
+        i = 0
+        while i < len(self.free) and self.free[i][0] < off:
+            i += 1
+        if (i > 0 and self.free[i - 1][0] + self.free[i - 1][1] > off) or \
+                (i < len(self.free) and off + n > self.free[i][0]):
+            raise ValueError(f"range ({off}, {n}) overlaps a free range")
+        self.free.insert(i, (off, n))
+        if i + 1 < len(self.free) and off + n == self.free[i + 1][0]:  # merge with the next
+            self.free[i] = (off, n + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == off:  # and with the previous
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+    def free_bytes(self) -> int:
+        return sum(m for _, m in self.free)
+
+    def view(self, off: int, n: int):
+        return self.buf.narrow(0, off, n)
+
+
 def is_lean(mode: str, precision: str) -> bool:
     """A mixed-precision P/Sigma system: its plan holds no scratch and can stay on the device
     while the system is not resident (its tables are small next to the system's buffers)."""
     return mode == "psigma" and precision == "mixed"
-
-
-def _bytes(*ts) -> int:
-    return int(sum(t.numel() * t.element_size() for t in ts))
 
 
 class System:
@@ -76,56 +140,76 @@ class System:
     from `w_seed` (real, as the W solve returns it for these plans)."""
 
     def __init__(self, name: str, cell, device: int = 0, precision: str = "fp64", mode: str = "iteration",
-                 workspace_bytes: int = 2 << 30, w_seed: int = 0, state: Optional[dict] = None, plan=None):
+                 workspace_bytes: int = 2 << 30, w_seed: int = 0, state: Optional[dict] = None, plan=None,
+                 arena=None):
+        """arena: a uint8 device tensor to hold the buffers (a range of a server's pool), at
+        least 16 bytes per word of arena_words; None allocates one."""
         import torch
         self.name, self.cell, self.precision, self.mode = name, cell, precision, mode
         self.dev = torch.device("cuda", device)
         # a mixed-precision P/Sigma system needs neither the W-solve nor the FP64 digit-product
         # scratch: its plan defers them (and never allocates them); every other system holds
-        # its scratch from the start, so that the footprint measured when it is brought in is
-        # all it will use.  `plan`: a plan kept from an earlier residency (lean systems only)
+        # its scratch from the start, so that the plan bytes measured when it is first brought
+        # in are all it will use.  `plan`: a plan kept from an earlier residency (lean systems)
+        t0 = time.perf_counter()
         if plan is None:
             plan = gw.Plan.from_cell(cell, device=device, workspace_bytes=workspace_bytes,
                                      defer_scratch=is_lean(mode, precision))
         self.plan = plan
+        t1 = time.perf_counter()
         self.stream = torch.cuda.Stream(device=device)
-        with torch.cuda.stream(self.stream):
-            self._setup(cell, w_seed, state)
-        # this system's own work only: other systems' requests keep running meanwhile
-        self.stream.synchronize()
+        # the setup (one fill, the seeds, the state upload) runs on a stream of high priority,
+        # so that its few kernels start between other systems' launches instead of queueing
+        # behind them; the request stream waits for it on the device, not on the host
+        setup = torch.cuda.Stream(device=device, priority=-1)
+        with torch.cuda.stream(setup):
+            self._setup(cell, w_seed, state, arena)
+        self.stream.wait_stream(setup)
+        self._setup_stream = setup  # kept until the request stream has passed the setup
+        self.setup_s = {"plan": t1 - t0, "buffers": time.perf_counter() - t1}  # host seconds
 
-    def _setup(self, cell, w_seed, state):
+    def _setup(self, cell, w_seed, state, arena):
+        """Every buffer is a view into one arena.  The path writes every element of its
+        outputs except P(R, i nu) at nu < 0 under the nu >= 0 structure, so that buffer
+        alone is zeroed."""
         import torch
-        p, inf = self.plan, self.plan.info
-        nk, nt, nn, nw = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"]
-        No = inf["n_orb_total"]
-        z = lambda n: torch.zeros(n, dtype=torch.complex128, device=self.dev)
-        self.G_k = z(nk * nt * No * No)
-        self.G_R, self.P_R = z(p.len("orb", nt)), z(p.len("pb", nt))
-        self.P_iw, self.W_iw, self.W_R = z(p.len("pb", nn)), z(p.len("pb", nn)), z(p.len("pb", nt))
-        self.S_R, self.Sx_R, self.S_iw = z(p.len("orb", nt)), z(p.len("orb", 1)), z(p.len("orb", nw))
-        self.S_k, self.Sx_k = z(nk * nw * No * No), z(nk * No * No)
-        bufs = [self.G_k, self.G_R, self.P_R, self.P_iw, self.W_iw, self.W_R, self.S_R, self.Sx_R, self.S_iw,
-                self.S_k, self.Sx_k]
+        p = self.plan
+        sizes = arena_words(p.info, self.mode)
+        total = sum(sizes.values())
+        if arena is None:
+            arena = torch.empty(16 * total, dtype=torch.uint8, device=self.dev)
+        if arena.numel() < 16 * total:
+            raise ValueError(f"{self.name}: arena of {arena.numel()} bytes, {16 * total} needed")
+        self._arena = arena
+        flat = arena.narrow(0, 0, 16 * total).view(torch.complex128)
+        off = 0
+        for name, n in sizes.items():
+            setattr(self, name, flat.narrow(0, off, n))
+            off += n
+        self.P_iw.zero_()
         if self.mode == "iteration":
             vq, _ = cell.coulomb()
-            self.v_q = torch.from_numpy(vq.reshape(-1)).to(self.dev)
-            self.H_k = torch.from_numpy(cell.H_k.reshape(-1)).to(self.dev)
-            self.v_R = p.fourier_k_to_R("pb", 1, self.v_q)
-            bufs += [self.v_q, self.H_k, self.v_R]
+            self.v_q.copy_(torch.from_numpy(vq.reshape(-1)))
+            self.H_k.copy_(torch.from_numpy(cell.H_k.reshape(-1)))
+            p.fourier_k_to_R("pb", 1, self.v_q, self.v_R)
+            self.W_iw.zero_()
         else:
+            # W~(R, i nu) and v(R): the draws torch.randn(n, generator) gives, cut in the
+            # (still unused) P(R, tau) buffer and copied into the real parts
             gen = torch.Generator(device=self.dev).manual_seed(int(w_seed))
-            self.W_iw.copy_(torch.randn(self.W_iw.numel(), dtype=torch.float64, device=self.dev, generator=gen))
-            self.v_R = torch.randn(p.len("pb", 1), dtype=torch.float64, device=self.dev,
-                                   generator=gen).to(torch.complex128)
-            bufs += [self.v_R]
+            draw = torch.view_as_real(self.P_R).reshape(-1)
+            assert draw.numel() >= max(self.W_iw.numel(), self.v_R.numel())
+            for dst in (self.W_iw, self.v_R):
+                d = draw[:dst.numel()]
+                d.normal_(generator=gen)
+                dst.copy_(d)
         if state is None:
             self.G_k.copy_(torch.from_numpy(cell.green_k_tau().reshape(-1)))
             self.mu = float(cell.mu)
         else:
             self.G_k.copy_(state["G_k"], non_blocking=True)  # pinned host state
             self.mu = state["mu"]
-        self.buffer_bytes = _bytes(*bufs)
+        self.buffer_bytes = 16 * total
 
     def state(self) -> Optional[dict]:
         """The iteration state, copied to pinned host memory (for eviction); None when it
@@ -191,36 +275,27 @@ class System:
         if not keep_plan:
             self.plan.close()
         for k in ("G_k", "G_R", "P_R", "P_iw", "W_iw", "W_R", "S_R", "Sx_R", "S_iw", "S_k", "Sx_k", "v_q", "H_k",
-                  "v_R"):
+                  "v_R", "_arena", "_setup_stream"):
             if hasattr(self, k):
                 delattr(self, k)
 
 
 class SystemSpec:
-    """A system the server knows: its cell and mode, its footprint on the device (measured
-    when it is first made resident, estimated before), and its state while not resident."""
+    """A system the server knows: its cell and mode, its footprint in the device pool (the
+    bytes of its buffers, exact from its plan's sizes), the device bytes its plan holds
+    outside the pool (measured when it is first made resident), and its state while not
+    resident."""
 
     def __init__(self, name: str, cell, mode: str = "iteration", precision: str = "fp64", w_seed: int = 0,
                  workspace_bytes: int = 2 << 30):
         self.name, self.cell, self.mode, self.precision = name, cell, mode, precision
         self.w_seed, self.workspace_bytes = w_seed, workspace_bytes
         self.state: Optional[dict] = None
-        self.measured: Optional[int] = None
+        self.plan_bytes: Optional[int] = None
         self.plan = None  # a lean system's plan, kept while the system is not resident
         hp = gw.Plan.from_cell(cell, host_only=True)
-        inf = hp.info
-        nk, nt, nn, nw, No = inf["n_k"], inf["n_tau"], inf["n_nu"], inf["n_omega"], inf["n_orb_total"]
-        lo, lp, Npb = inf["len_orb"], inf["len_pb"], inf["n_pb_total"]
-        words = nk * nt * No * No + lo * (nt + 1 + nw) + lp * (2 * nt + 2 * nn + 1) + nk * (nw + 1) * No * No
-        if mode == "iteration":
-            words += 2 * nk * Npb * Npb + nk * No * No
+        self.footprint = 16 * sum(arena_words(hp.info, mode).values())
         hp.close()
-        # buffers, plus the plan's own tables and W-solve scratch (bounded by workspace_bytes)
-        self.estimate = int(16 * words * 1.05) + (workspace_bytes if mode == "iteration" else 0) + (64 << 20)
-
-    @property
-    def footprint(self) -> int:
-        return self.measured if self.measured is not None else self.estimate
 
     def prepare(self):
         """Compute the first state (the cell's G(k, tau) and chemical potential) on the host
@@ -232,61 +307,151 @@ class SystemSpec:
 
 
 class Server:
-    """Continuous batching over systems brought in and out of device memory under a cap."""
+    """Continuous batching over systems brought in and out of a device pool of the cap's size."""
 
     def __init__(self, specs: Dict[str, SystemSpec], mem_cap_bytes: int, device: int = 0, max_workers: int = 8,
                  factory=None, meter=None):
-        """factory(spec, state) -> a resident system (default: System on `device`); meter() ->
-        device bytes in use (default: the CUDA driver's count)."""
+        """factory(spec, state) -> a resident system (default: System on `device`, its buffers
+        in the pool; with a factory the pool only keeps the books); meter() -> device bytes
+        in use (default: the CUDA driver's count)."""
         self.specs = specs
-        self.mem_cap = int(mem_cap_bytes)
         self.device = device
         self.factory = factory
         self.meter = meter
-        too_big = [n for n, s in specs.items() if s.footprint > self.mem_cap]
-        if too_big:
-            raise ValueError(f"systems larger than the memory cap: {too_big}")
+        self._dpool: Optional[DevicePool] = None
+        self.ranges: Dict[str, tuple] = {}  # resident system -> (offset, bytes) in the pool
         self.resident: "collections.OrderedDict[str, System]" = collections.OrderedDict()  # LRU order
+        self.mem_cap = mem_cap_bytes
         self.pool = cf.ThreadPoolExecutor(max_workers=max_workers)
+        # evictions inside the request loop run here, one at a time and in order (saving an
+        # iteration's state waits for its copy to the host)
+        self.closer = cf.ThreadPoolExecutor(max_workers=1)
+        self._last_close: Optional[cf.Future] = None
+        # seconds the workers spent waiting for evictions and making systems, and the closer
+        # thread closing evicted ones
+        self.timing = {"wait_closes_s": [], "make_s": [], "make_plan_s": [], "close_s": []}
         self.log: List[tuple] = []  # (time, event, system, resident bytes after it, device bytes in use)
 
+    @property
+    def mem_cap(self) -> int:
+        return self._mem_cap
+
+    @mem_cap.setter
+    def mem_cap(self, cap: int):
+        """The pool's size; set while no system is resident (the pool is made again)."""
+        if self.resident:
+            raise RuntimeError("the memory cap changes only while no system is resident")
+        self._mem_cap = int(cap)
+        self._drop_pool()
+        align = 1 if self.factory is not None else DevicePool.ALIGN
+        too_big = [n for n, s in self.specs.items() if -(-s.footprint // align) * align > self._mem_cap]
+        if too_big:
+            raise ValueError(f"systems larger than the memory cap: {too_big}")
+
+    def _pool(self) -> DevicePool:
+        if self._dpool is None:
+            self._dpool = DevicePool(self._mem_cap, None if self.factory is not None else self.device)
+        return self._dpool
+
+    def _drop_pool(self):
+        if self._dpool is not None:
+            had = self._dpool.buf is not None
+            self._dpool = None
+            if had:
+                import torch
+                torch.cuda.empty_cache()
+
     def resident_bytes(self) -> int:
-        return sum(self.specs[n].footprint for n in self.resident)
+        return sum(self.specs[n].footprint for n in list(self.resident))  # a snapshot: workers read it too
 
     def _device_used(self) -> int:
         if self.meter is not None:
             return int(self.meter())
         import torch
-        # the driver's count (allocations are synchronous calls): no device synchronisation,
-        # which would wait for every request in flight
+        # the driver's count: no device synchronisation, which would wait for every request
+        # in flight
         free, total = torch.cuda.mem_get_info(self.device)
         return int(total - free)
 
-    def bring_in(self, name: str):
+    def _place(self, name: str) -> bool:
+        """A range of the pool for `name`'s buffers, if one is free."""
+        off = self._pool().alloc(self.specs[name].footprint)
+        if off is None:
+            return False
+        self.ranges[name] = (off, self.specs[name].footprint)
+        return True
+
+    def _make(self, name: str):
+        """A resident system for spec `name` in its range (its plan kept from an earlier
+        residency when lean)."""
         spec = self.specs[name]
-        # the footprint is measured once, the first time the system comes in, with the device
-        # quiet (no other request allocating or freeing meanwhile); later bring-ins reuse it
-        # and wait for nothing but their own setup
-        measure = spec.measured is None
+        if self.factory is not None:
+            return self.factory(spec, spec.state)
+        off, n = self.ranges[name]
+        sysm = System(name, spec.cell, device=self.device, precision=spec.precision, mode=spec.mode,
+                      workspace_bytes=spec.workspace_bytes, w_seed=spec.w_seed, state=spec.state, plan=spec.plan,
+                      arena=self._dpool.view(off, n))
+        if is_lean(spec.mode, spec.precision):
+            spec.plan = sysm.plan
+        return sysm
+
+    def _bring_and_run(self, name: str, keep_sigma: bool, closes: Optional[cf.Future]):
+        """Worker job: make the system (its range already placed) and run its request, once
+        the evictions submitted before it have saved their state (`closes`: the last of
+        them; they run in order)."""
+        t0 = time.perf_counter()
+        if closes is not None:
+            closes.result()
+        t1 = time.perf_counter()
+        sysm = self._make(name)
+        self.timing["wait_closes_s"].append(t1 - t0)
+        self.timing["make_s"].append(time.perf_counter() - t1)
+        self.timing["make_plan_s"].append(getattr(sysm, "setup_s", {}).get("plan", 0.0))
+        self.resident[name] = sysm  # replaces the reservation (one assignment)
+        return sysm.run_request(keep_sigma)
+
+    def bring_in(self, name: str):
+        """Make `name` resident now (in a free range of the pool).  The first time, with the
+        device quiet, it also measures the device bytes the system's plan holds outside the
+        pool."""
+        spec = self.specs[name]
+        if name not in self.ranges and not self._place(name):
+            raise RuntimeError(f"{name}: no free range of {spec.footprint} bytes in the pool")
+        self._wait_closes()
+        measure = spec.plan_bytes is None
         if measure and self.factory is None:
             import torch
             torch.cuda.synchronize(self.device)
         before = self._device_used()
-        if self.factory is not None:
-            sysm = self.factory(spec, spec.state)
-        else:
-            sysm = System(name, spec.cell, device=self.device, precision=spec.precision, mode=spec.mode,
-                          workspace_bytes=spec.workspace_bytes, w_seed=spec.w_seed, state=spec.state,
-                          plan=spec.plan)
-            if is_lean(spec.mode, spec.precision):
-                spec.plan = sysm.plan
+        sysm = self._make(name)
         if measure:
-            spec.measured = max(self._device_used() - before, sysm.buffer_bytes)
+            spec.plan_bytes = max(0, self._device_used() - before)
         self.resident[name] = sysm
         return sysm
 
+    def _release(self, name: str):
+        off, n = self.ranges.pop(name)
+        self._dpool.release(off, n)
+
     def evict(self, name: str):
         sysm = self.resident.pop(name)
+        self._release(name)
+        self._close(name, sysm)
+
+    def _evict_in_background(self, name: str):
+        """Take `name` off the resident set and its range back now; save its state and close
+        it on the closer thread (a system made in the range later waits for that)."""
+        sysm = self.resident.pop(name)
+        self._release(name)
+        self._last_close = self.closer.submit(self._close, name, sysm)
+
+    def _wait_closes(self):
+        if self._last_close is not None:
+            self._last_close.result()
+            self._last_close = None
+
+    def _close(self, name: str, sysm):
+        t0 = time.perf_counter()
         spec = self.specs[name]
         st = sysm.state()
         if st is not None:
@@ -296,18 +461,19 @@ class Server:
         else:
             sysm.close()
         del sysm
-        if self.factory is None:
-            import torch
-            torch.cuda.empty_cache()
+        self.timing["close_s"].append(time.perf_counter() - t0)
 
     def close(self):
+        self._wait_closes()
         for n in list(self.resident):
             self.evict(n)
         for spec in self.specs.values():
             if getattr(spec, "plan", None) is not None:
                 spec.plan.close()
                 spec.plan = None
+        self._drop_pool()
         self.pool.shutdown()
+        self.closer.shutdown()
 
     def _victims(self, running, queue, keep: str = "") -> List[str]:
         """Idle resident systems in the order to evict them: those no queued request waits
@@ -324,54 +490,84 @@ class Server:
         queue: collections.deque = collections.deque()
         running: Dict[str, Request] = {}
         t0 = time.perf_counter()
+        # the queue is scanned again only after an arrival, a completion or a system made:
+        # an idle scan would hold the interpreter lock the workers need
+        dirty = True
         while pending or queue or running:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
-            for r in list(queue):
-                if r.system in running:
-                    continue  # one request per system at a time; later requests of others may pass
+                dirty = True
+            waiting = set()  # systems with a request left in the queue in this pass
+            idle = None      # the pass's eviction candidates, listed when first needed
+            for r in (list(queue) if dirty else ()):
+                if r.system in running or r.system in waiting:
+                    # one request per system at a time, in arrival order; later requests of
+                    # other systems may pass
+                    continue
                 spec = self.specs[r.system]
                 if r.system not in self.resident:
-                    need = spec.footprint
-                    idle = self._victims(running, queue)
-                    while self.resident_bytes() + need > self.mem_cap and idle:
-                        victim = idle.pop(0)
-                        self.evict(victim)
-                        self.log.append((time.perf_counter() - t0, "evict", victim, self.resident_bytes(),
-                                         self._device_used()))
-                    if self.resident_bytes() + need > self.mem_cap:
-                        continue  # the running systems hold the memory: wait
-                    self.bring_in(r.system)
+                    first = spec.plan_bytes is None
+                    if first and any(v is None for v in self.resident.values()):
+                        waiting.add(r.system)
+                        continue  # a first bring-in measures its plan: let the pending ones finish
+                    placed = self._place(r.system)
+                    if not placed:
+                        if idle is None:
+                            idle = self._victims(running, queue)
+                        else:  # admissions earlier in the pass made some of them busy
+                            idle = [n for n in idle if n not in running and n in self.resident]
+                        while not placed and idle:
+                            victim = idle.pop(0)
+                            self._evict_in_background(victim)
+                            self.log.append((time.perf_counter() - t0, "evict", victim, self.resident_bytes(),
+                                             self._device_used()))
+                            placed = self._place(r.system)
+                        if not placed:
+                            waiting.add(r.system)
+                            continue  # the running systems hold the pool: wait
                     r.brought_in = True
-                    # the measured footprint may exceed the estimate admission used: evict
-                    # more idle systems until the cap holds again
-                    idle = self._victims(running, queue, keep=r.system)
-                    while self.resident_bytes() > self.mem_cap and idle:
-                        victim = idle.pop(0)
-                        self.evict(victim)
-                        self.log.append((time.perf_counter() - t0, "evict", victim, self.resident_bytes(),
+                    if not first:
+                        # made in the worker that runs the request, so that this loop goes on
+                        # admitting and completing others meanwhile (a reserved system is never
+                        # a victim: its request is running)
+                        self.resident[r.system] = None
+                        self.log.append((time.perf_counter() - t0, "bring_in", r.system, self.resident_bytes(),
                                          self._device_used()))
+                        queue.remove(r)
+                        r.admitted = time.perf_counter() - t0
+                        r.future = self.pool.submit(self._bring_and_run, r.system, keep_sigma, self._last_close)
+                        running[r.system] = r
+                        continue
+                    self.bring_in(r.system)
                     self.log.append((time.perf_counter() - t0, "bring_in", r.system, self.resident_bytes(),
                                      self._device_used()))
-                    if self.resident_bytes() > self.mem_cap:  # the running systems and this one alone exceed it
-                        raise RuntimeError(f"{r.system}: resident bytes above the cap after bringing it in")
                 self.resident.move_to_end(r.system)
                 queue.remove(r)
                 r.admitted = time.perf_counter() - t0
                 r.future = self.pool.submit(self.resident[r.system].run_request, keep_sigma)
                 running[r.system] = r
+            dirty = False
             for name, r in list(running.items()):
                 if r.future is not None and r.future.done():
-                    r.event, r.sigma_k = r.future.result()
+                    dirty = True
+                    try:
+                        r.event, r.sigma_k = r.future.result()
+                    except BaseException:
+                        if name in self.resident and self.resident[name] is None:
+                            del self.resident[name]  # a reservation whose system was never made
+                            self._release(name)
+                        raise
                     r.future = None
                 if r.future is None and r.event.query():
                     r.done = time.perf_counter() - t0
                     del running[name]
+                    dirty = True
             if not running and not queue and pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 1e-3)))
             elif running:
                 time.sleep(poll_s)
+        self._wait_closes()
         for sysm in self.resident.values():
             sysm.finish()
         return reqs

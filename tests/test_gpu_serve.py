@@ -1,8 +1,9 @@
 """The request loop on the device (paper_1911_05633_gb300.serve): residency under a
 memory cap below the systems' total (bring in on admission, eviction of idle systems with
 their state kept on the host), a system's result the same alone and in the mix, the state
-advancing per iteration with the chemical potential updated, and the device memory
-measured by the driver staying within the cap."""
+advancing per iteration with the chemical potential updated, every buffer in the
+server's device pool, and the device memory measured by the driver staying within the
+pool and the plans' tables."""
 import numpy as np
 import pytest
 
@@ -65,7 +66,7 @@ def test_memory_cap_binds_on_real_allocations(specs):
     torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
     baseline = total - free
-    # measured footprints from one pass with room for everything
+    # references (and each plan's bytes, measured) from one pass with room for everything
     srv = Server(specs, mem_cap_bytes=sum(s.footprint for s in specs.values()) * 2)
     ref = {n: [r.sigma_k for r in srv.run([(0.0, n), (0.0, n)], keep_sigma=True)] for n in specs}
     srv.close()
@@ -77,9 +78,20 @@ def test_memory_cap_binds_on_real_allocations(specs):
     order = ["d16", "c1_cut5", "mixed", "c0", "c1_cut5", "d16", "mixed", "c0"]
     reqs = srv.run([(0.002 * i, n) for i, n in enumerate(order)], keep_sigma=True)
     assert any(e[1] == "evict" for e in srv.log)
+    # outside the pool the device holds only the plans' tables (measured per system when it
+    # was first brought in; at most all of them at once)
+    plans = sum(s.plan_bytes for s in specs.values())
     for t, ev, name, resident, used in srv.log:
         assert resident <= cap
-        assert used - baseline <= cap + (64 << 20)  # the driver's own count, 64 MiB of slack
+        assert used - baseline <= cap + plans + (64 << 20)  # the driver's own count, 64 MiB of slack
+    # every buffer of a resident system lies in its range of the pool
+    base = srv._dpool.buf.data_ptr()
+    for n, sysm in srv.resident.items():
+        off, nb = srv.ranges[n]
+        for k in ("G_k", "G_R", "P_R", "P_iw", "W_iw", "W_R", "S_R", "Sx_R", "S_iw", "S_k", "Sx_k", "v_R"):
+            t = getattr(sysm, k)
+            lo = t.data_ptr() - base
+            assert off <= lo and lo + t.numel() * t.element_size() <= off + nb, (n, k)
     for n in specs:
         got = [r.sigma_k for r in reqs if r.system == n]
         for a, b in zip(got, ref[n]):

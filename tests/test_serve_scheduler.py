@@ -32,7 +32,7 @@ class FakeSpec:
     def __init__(self, name, footprint, service_s):
         self.name, self.footprint, self.service = name, footprint, service_s
         self.state = None
-        self.measured = None
+        self.plan_bytes = None
         self.starts = []
 
 
@@ -87,6 +87,7 @@ def test_residency_under_the_cap_with_eviction():
     system's state (its iteration count here) survives an eviction."""
     specs = [FakeSpec("big", 6, 0.01), FakeSpec("mid", 4, 0.01), FakeSpec("small", 3, 0.005)]
     srv, meter = _server(specs, 10)
+    _check_disjoint(srv)
     arrivals = [(0.0, "big"), (0.0, "mid"), (0.03, "small"), (0.05, "big"), (0.08, "mid"), (0.1, "small"),
                 (0.12, "big")]
     reqs = srv.run(arrivals, keep_sigma=True)
@@ -130,3 +131,109 @@ def test_poisson_stream_and_latency_stats():
     assert st["requests"] == 50 and 0.0 < st["p50_ms"] <= st["p99_ms"]
     assert all(r.latency >= (0.002 if r.system == "a" else 0.004) - 1e-4 for r in reqs)
     srv.close()
+
+
+class SlowClose(FakeSystem):
+    def close(self):
+        time.sleep(0.06)  # freeing device memory waits for the device to go idle
+        super().close()
+
+
+def test_later_bring_ins_do_not_hold_the_loop():
+    """A system brought in again (its footprint known) is made in the worker that runs its
+    request, after the evictions before it have freed their memory on the closer thread: a
+    request of a resident system queued behind it is admitted at once, not after the slow
+    eviction and bring-in."""
+    specs = [FakeSpec("p", 5, 0.005), FakeSpec("q", 1, 0.005), FakeSpec("r", 5, 0.005)]
+    meter = Meter()
+    made = {"p": 0}
+
+    def factory(spec, st):
+        if spec.name == "p":
+            made["p"] += 1
+            if made["p"] > 1:
+                time.sleep(0.08)  # a slow bring-in (buffers, state upload)
+        return (SlowClose if spec.name == "r" else FakeSystem)(spec, st, meter)
+
+    srv = Server({s.name: s for s in specs}, mem_cap_bytes=10, factory=factory, meter=meter)
+    reqs = srv.run([(0.0, "p"), (0.0, "q"), (0.03, "r"), (0.06, "p"), (0.06, "q")])
+    p2 = [r for r in reqs if r.system == "p"][1]
+    q2 = [r for r in reqs if r.system == "q"][1]
+    assert p2.brought_in and not q2.brought_in
+    assert made["p"] == 2
+    assert "r" in [e[2] for e in srv.log if e[1] == "evict"]
+    assert q2.admitted - p2.admitted < 0.04  # not behind r's 60 ms eviction and p's 80 ms bring-in
+    assert q2.done < p2.done
+    assert p2.done - p2.admitted > 0.14  # p was made after r had been freed
+    assert all(e[3] <= 10 and e[4] <= 10 for e in srv.log)
+    srv.close()
+    assert meter.used == 0
+
+
+def test_device_pool_first_fit_alignment_and_merging():
+    from paper_1911_05633_gb300.serve import DevicePool
+    p = DevicePool(100)
+    a, b, c = p.alloc(30), p.alloc(30), p.alloc(30)
+    assert (a, b, c) == (0, 30, 60) and p.alloc(20) is None and p.free_bytes() == 10
+    p.release(b, 30)
+    assert p.alloc(40) is None            # 30 + 10 free, not in one range
+    p.release(c, 30)
+    assert p.free == [(30, 70)]           # merged with both neighbours
+    with pytest.raises(ValueError):
+        p.release(40, 10)                 # inside a free range
+    p.release(a, 30)
+    assert p.free == [(0, 100)]
+    q = DevicePool(7 << 20, align=2 << 20)
+    assert q.size == 6 << 20 and q.alloc(1) == 0 and q.alloc(1) == 2 << 20 and q.alloc(2 << 20) == 4 << 20
+    assert q.alloc(1) is None
+
+
+def _check_disjoint(srv):
+    """Wrap the server's placement so that every placement is checked: each resident range
+    inside the pool, no two overlapping."""
+    place = srv._place
+
+    def checked(name):
+        ok = place(name)
+        spans = sorted(srv.ranges.values())
+        assert all(o >= 0 and o + n <= srv.mem_cap for o, n in spans)
+        assert all(o1 + n1 <= o2 for (o1, n1), (o2, _) in zip(spans, spans[1:]))
+        return ok
+    srv._place = checked
+
+
+def test_eviction_until_one_range_holds_the_system():
+    """The pool holds a system's buffers in one range: with the free bytes split around a
+    resident system, idle systems are evicted (least recently used first) until a single
+    range is free, not just enough bytes."""
+    specs = [FakeSpec("A", 4, 0.002), FakeSpec("B", 2, 0.002), FakeSpec("C", 4, 0.002), FakeSpec("D", 6, 0.002)]
+    srv, meter = _server(specs, 10)
+    _check_disjoint(srv)
+    srv.run([(0.0, "A"), (0.0, "B"), (0.0, "C")])
+    assert srv.ranges == {"A": (0, 4), "B": (4, 2), "C": (6, 4)}
+    srv.run([(0.0, "B")])                 # B most recently used
+    srv.run([(0.0, "D")])
+    evicted = [e[2] for e in srv.log if e[1] == "evict"]
+    assert evicted == ["A", "C", "B"]     # A + C free 8 bytes, but on both sides of B
+    assert srv.ranges == {"D": (0, 6)}
+    srv.close()
+    assert meter.used == 0
+
+
+def test_requests_of_one_system_run_in_arrival_order():
+    """Two requests of a system that waits for room: the freed room goes to the earlier
+    one (an iteration's state advances request by request, so order matters)."""
+    specs = [FakeSpec("big", 3294, 0.03), FakeSpec("c1", 113, 0.002), FakeSpec("mx", 7, 0.002),
+             FakeSpec("c0", 4, 0.002)]
+    srv, meter = _server(specs, 3294 + 56)
+    _check_disjoint(srv)
+    for s in specs:  # known plans: every bring-in takes the worker path
+        s.plan_bytes = 0
+    order = ["big", "c1", "mx", "c0", "c1", "big", "mx", "c0"]
+    reqs = srv.run([(0.002 * i, n) for i, n in enumerate(order)])
+    for name in ("big", "c1", "mx", "c0"):
+        mine = [r for r in reqs if r.system == name]
+        assert [r.sigma_k for r in mine] == list(range(1, len(mine) + 1))  # state carried in order
+        assert all(a.admitted < b.admitted for a, b in zip(mine, mine[1:]))
+    srv.close()
+    assert meter.used == 0
