@@ -83,6 +83,9 @@ def parse():
                     help="only the batched uneven systems (the 16-system family in one launch per contraction)")
     ap.add_argument("--serve", action="store_true",
                     help="Poisson request stream of whole GW iterations: p50/p99 latency")
+    ap.add_argument("--w-solve", action="store_true",
+                    help="time the W solve (Eq. W_1) of the configuration-2 cell of --atoms atoms on the P of "
+                         "its own FP64 rows; one JSON line")
     ap.add_argument("--scaling", type=int, nargs="*", default=None,
                     help="time the P+Sigma rows (no W solve) of the 64-function diamond series at these atom "
                          "counts (default 8 16 32 48 72), FP64 and mixed; one JSON line")
@@ -1158,6 +1161,67 @@ def run_batch3(args, local, peaks):
     return out
 
 
+def run_w_solve(args, local):
+    """The W solve of Eq. W_1 on the configuration-2 cell (N_PB = 64 x atoms): P(R, i nu)
+    from the cell's own FP64 rows a1-a3, v(q) from the cell, W~(R, i nu) by the plan's
+    inverse (block Gauss-Jordan over tensor-core pivot inverses beyond N_PB = 384).  One
+    solve to warm up (it also fixes the frequency chunks), one timed with CUDA events on
+    its stream; the kernels' shares from the plan's own launch timing."""
+    import torch
+    import synth
+    from paper_1911_05633_gb300 import gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    cell = synth.make_config(2, atoms=args.atoms)
+    vq, _ = cell.coulomb()
+    t_host = time.perf_counter() - t0
+    plan = gw.Plan.from_cell(cell, device=local, w_solver=args.w_solver)
+    inf = plan.info
+    nt, nn = inf["n_tau"], inf["n_nu"]
+    stream = torch.cuda.Stream(device=local)
+    sp = stream.cuda_stream
+    G_k = torch.from_numpy(cell.green_k_tau().reshape(-1)).to(dev)
+    v_q = torch.from_numpy(vq.reshape(-1)).to(dev)
+    del vq
+    G_R = plan.green_k_to_R(G_k, stream=sp)
+    P_R = plan.polarizability_tau(G_R, precision="fp64", stream=sp)
+    P_iw = plan.transform_tau_iw("B", "tau_to_iw", "pb", P_R, stream=sp, structure=p_iw_structure(inf))
+    stream.synchronize()  # before the inputs go back to the allocator
+    del P_R, G_R, G_k
+    W = torch.empty(plan.len("pb", nn), dtype=torch.complex128, device=dev)
+    plan.screened_W_iw(P_iw, v_q, W, stream=sp)
+    plan.sync(stream=sp)
+    plan.timing_reset()
+    plan.timing_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.screened_W_iw(P_iw, v_q, W, stream=sp)
+    e1.record(stream)
+    plan.sync(stream=sp)
+    torch.cuda.synchronize()
+    kt = plan.timing_read()
+    plan.timing_enable(False)
+    sec = e0.elapsed_time(e1) / 1e3
+    N = inf["n_pb_total"]
+    n_nu_solved = int((np.asarray(cell.nu_idx) >= 0).sum()) if inf["w_symmetric"] else nn
+    problems = inf["n_q_solved"] * n_nu_solved
+    inverses = problems + inf["n_q_solved"]          # and v(q)^-1 once per solved momentum
+    flops = inverses * 8.0 * N ** 3                   # a complex inverse: N^3 complex multiply-adds
+    finite = bool(torch.isfinite(torch.view_as_real(W)).all().item())
+    out = {"metric": "W solve of Eq. W_1 (W~(R, i nu) from P(R, i nu))", "unit": "s", "value": round(sec, 3),
+           "config": {"workload": f"configuration 2, {args.atoms}-atom diamond supercell", "n_pb": N,
+                      "n_q_solved": inf["n_q_solved"], "nu_solved": n_nu_solved, "problems": problems,
+                      "inverse": ("block Gauss-Jordan, pivot blocks of %d" % inf["w_block"]) if inf["w_block"]
+                      else ("tensor-core" if inf["w_tensor"] else "FP64 Gauss-Jordan"),
+                      "nu_chunk": inf["nu_chunk"], "workspace_GB": round(inf["workspace_bytes"] / 1e9, 1)},
+           "ms_per_inverse": round(1e3 * sec / inverses, 2),
+           "fp64_equivalent_tflops": round(flops / sec / 1e12, 2),
+           "finite": finite, "host_setup_s": round(t_host, 1),
+           "kernels": dict(list(kernels_table(kt, 1).items())[:8])}
+    return out
+
+
 def run_scaling(args, local):
     """P + Sigma rows (a1-a4 and a6-a8; the W solve is timed apart by the metric) of the
     diamond supercell series with 9 orbitals and 64 product functions per atom, a 2x2x2
@@ -1319,6 +1383,10 @@ def main():
     if args.scaling is not None:
         if rank == 0:
             print(json.dumps(run_scaling(args, local)), flush=True)
+        return
+    if args.w_solve:
+        if rank == 0:
+            print(json.dumps(run_w_solve(args, local)), flush=True)
         return
     if args.batch:
         if rank == 0:

@@ -105,9 +105,12 @@ typedef struct {
   int strict_kmesh;       /* 1: reject a k-mesh below the rule of Sec. 2 */
   int host_only;          /* 1: build host tables only; compute calls fail with GW_ERR_NO_DEVICE */
   int device;             /* CUDA device ordinal used by the plan */
-  size_t workspace_bytes; /* cap on the W-solve scratch (0: 24 GiB for the tensor-core inverse, 4 GiB otherwise) */
+  size_t workspace_bytes; /* cap on the W-solve scratch (0: 24 GiB for the tensor-core and the block
+                             inverse, 4 GiB otherwise) */
   int no_symmetry;        /* 1: never use the frequency / momentum symmetries in the W solve */
-  int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384),
+  int w_solver;           /* 0: automatic (tensor-core inverse when N_PB is 128, 256 or 384;
+                             block Gauss-Jordan over pivot blocks of 384, 256 or 128 that the
+                             tensor-core inverse takes when N_PB is a larger multiple of 128),
                              1: FP64 Gauss-Jordan inverse always */
   int fp64_products;      /* 0 automatic: FP64-accurate digit products on the tensor cores for
                              the W~ C^b stage of the GW_FP64 Sigma (every K <= 384), the Y C^b
@@ -152,6 +155,7 @@ typedef struct {
                                  (0 when n_prod_near is NULL) */
   int mixed_queue;            /* GW_MIXED contractions as persistent tensor-core kernels over a queue
                                  of (entry, tau) units: bit 0 P, bit 1 Sigma (device plans) */
+  int w_block;                /* pivot block size of the block Gauss-Jordan W inverse (0: not used) */
 } gw_plan_info;
 
 /* ---- plan ------------------------------------------------------------------ */
@@ -235,8 +239,14 @@ gw_status gw_transform_tau_iw_ex(gw_plan_t plan, gw_statistics st, gw_direction 
 /* W~(R, i nu) on the kept entries from P(R, i nu) (Eq. W_1 with W = v + W~):
  * P(q) = sum_{kept R} e^{iq.R} P(R); W(q) = (I - v(q) P(q))^{-1} v(q), computed as
  * (v(q)^{-1} - P(q))^{-1}, each inverse either by FP64 Gauss-Jordan with partial
- * pivoting or (w_tensor) by FP32 Gauss-Jordan refined once with a residual
- * I - A X0 evaluated to FP64 accuracy on the tensor cores (exact BF16 slices);
+ * pivoting or (w_tensor) by FP32 Gauss-Jordan refined twice with a residual
+ * I - A X evaluated to FP64 accuracy on the tensor cores (exact BF16 slices), or
+ * (w_block, N_PB beyond 384) by Gauss-Jordan over pivot blocks of w_block rows without
+ * pivoting across blocks, each pivot block inverted as in w_tensor and every block
+ * product (w_block terms) taken to FP64 accuracy from exact BF16 slices: it needs the
+ * leading blocks well conditioned, as they are for v(q) and v(q)^{-1} - P(q, i nu)
+ * (Hermitian positive definite when P comes from a Hermitian G), and reports
+ * GW_ERR_SINGULAR from gw_sync for a singular pivot block;
  * W~(R) = (1/N_k) sum_q e^{-iq.R} (W(q) - v(q)).
  * P_R_iw, Wt_R_iw: PB layout, N_nu slices.  v_q: dense [N_k][N_PB][N_PB].
  * When the plan reports w_symmetric (C symmetric in (L, L''), a symmetric bosonic

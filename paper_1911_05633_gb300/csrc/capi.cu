@@ -71,6 +71,16 @@ struct gw_plan_s {
   uint16_t* t_Xsl = nullptr;
   int* t_eA = nullptr;
   int* t_eX = nullptr;
+  // block Gauss-Jordan for N_PB beyond the tensor-core inverse (pivot blocks of w_bs,
+  // each inverted by the tensor-core inverse; the t_* buffers above sized for them)
+  bool w_block = false;
+  int w_bs = 0;
+  double2* b_D = nullptr;
+  double2* b_Rp = nullptr;
+  uint16_t* b_Asl = nullptr;
+  uint16_t* b_Bsl = nullptr;
+  int* b_eA = nullptr;
+  int* b_eB = nullptr;
   gw::MixedPlan mixed;
   // mixed-precision contractions as persistent tensor-core kernels over a unit queue
   gw::CTables ct;
@@ -145,7 +155,8 @@ void free_device(gw_plan_s* p) {
                   p->d_pb_atom, p->d_phase, p->d_pcode,
                   p->d_C, p->d_Tf_fwd, p->d_Tf_inv, p->d_Tb_fwd, p->d_Tb_mirror, p->d_Tb_inv, p->d_qh, p->d_qw,
                   p->d_numirror, p->d_wsV, p->d_wsA, p->d_perm, p->d_status, p->t_X32, p->t_lo, p->t_R, p->t_PX, p->t_Asl,
-                  p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_unitsX, p->d_counter};
+                  p->t_Xsl, p->t_eA, p->t_eX, p->d_unitsP, p->d_unitsS, p->d_unitsX, p->d_counter,
+                  p->b_D, p->b_Rp, p->b_Asl, p->b_Bsl, p->b_eA, p->b_eB};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   gw::mixed_free(p->mixed);
@@ -289,6 +300,27 @@ gw_status launch_tensor_inverse(gw_plan_s* p, double2* mats, int batch, long lon
   return check_launch("tensor-core inverse");
 }
 
+gw_status launch_block_inverse(gw_plan_s* p, double2* mats, int batch, long long N, cudaStream_t st) {
+  gw::WblkBuffers w{};
+  w.D = p->b_D;
+  w.Rp = p->b_Rp;
+  w.Asl = p->b_Asl;
+  w.Bsl = p->b_Bsl;
+  w.eA = p->b_eA;
+  w.eB = p->b_eB;
+  w.inner.X32 = p->t_X32;
+  w.inner.lo = p->t_lo;
+  w.inner.R = p->t_R;
+  w.inner.Asl = p->t_Asl;
+  w.inner.Xsl = p->t_Xsl;
+  w.inner.PX = p->t_PX;
+  w.inner.eA = p->t_eA;
+  w.inner.eX = p->t_eX;
+  w.inner.status = p->d_status;
+  gw::wblk_inverse(w, mats, batch, (int)N, p->w_bs, p->smem_GJ32, st);
+  return check_launch("block inverse");
+}
+
 size_t smem_polar(const gw::HostPlan& h) {
   size_t m = 0;
   for (int s = 0; s < h.n_species; ++s)
@@ -320,10 +352,17 @@ static gw_status alloc_w_scratch(gw_plan_s* p) {
   // bytes per inverted matrix: FP64 matrix, pivots, and (tensor path) the FP32 inverse,
   // its correction and the residual, the BF16 digit planes of both operands, the term
   // planes of X0 and the scale exponents
-  const size_t per_mat = mat + npb * sizeof(int) +
-                         (p->w_tensor ? npb * npb * (3 * sizeof(float2) + 2 * (gw::kWSA + gw::kWSX1) * 2 + 6 * 2) +
-                                            2 * npb * sizeof(int)
-                                      : 0);
+  // the tensor-core inverse's scratch per inverted matrix of order ni (the matrix itself,
+  // or the pivot block of the block Gauss-Jordan)
+  const size_t ni = p->w_block ? (size_t)p->w_bs : npb;
+  const size_t tc_per = ni * ni * (3 * sizeof(float2) + 2 * (gw::kWSA + gw::kWSX1) * 2 + 6 * 2) + 2 * ni * sizeof(int);
+  // block Gauss-Jordan: the pivot block, the row panel, the digits of a column and a row
+  // panel (2 kWSA, 2 kWSX1 BF16 planes per element) and 2 npb exponents
+  const size_t bs = (size_t)p->w_bs;
+  const size_t blk_per = p->w_block ? bs * bs * sizeof(double2) + bs * npb * sizeof(double2) +
+                                          npb * bs * 2 * (gw::kWSA + gw::kWSX1) * 2 + 2 * npb * sizeof(int)
+                                    : 0;
+  const size_t per_mat = mat + npb * sizeof(int) + (p->w_tensor || p->w_block ? tc_per : 0) + blk_per;
   const size_t per_nu = (size_t)p->n_qh * per_mat;
   const size_t cap = p->ws_cap;
   const int n_work_nu = h.n_nu - p->nu_start;
@@ -343,16 +382,25 @@ static gw_status alloc_w_scratch(gw_plan_s* p) {
   if ((st = up((void**)&p->d_wsA, (size_t)nch * p->n_qh * mat)) != GW_OK) return st;
   if ((st = up((void**)&p->d_perm, (size_t)nch * p->n_qh * npb * sizeof(int))) != GW_OK) return st;
   p->ws_bytes = (size_t)p->n_qh * mat + (size_t)nch * per_nu;
-  if (p->w_tensor) {
+  if (p->w_tensor || p->w_block) {
     const size_t nm = (size_t)nch * p->n_qh;
-    if ((st = up((void**)&p->t_X32, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
-    if ((st = up((void**)&p->t_lo, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
-    if ((st = up((void**)&p->t_R, nm * npb * npb * sizeof(float2))) != GW_OK) return st;
-    if ((st = up((void**)&p->t_PX, nm * npb * npb * 6 * 2)) != GW_OK) return st;
-    if ((st = up((void**)&p->t_Asl, nm * npb * npb * 2 * gw::kWSA * 2)) != GW_OK) return st;
-    if ((st = up((void**)&p->t_Xsl, nm * npb * npb * 2 * gw::kWSX1 * 2)) != GW_OK) return st;
-    if ((st = up((void**)&p->t_eA, nm * npb * sizeof(int))) != GW_OK) return st;
-    if ((st = up((void**)&p->t_eX, nm * npb * sizeof(int))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_X32, nm * ni * ni * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_lo, nm * ni * ni * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_R, nm * ni * ni * sizeof(float2))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_PX, nm * ni * ni * 6 * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_Asl, nm * ni * ni * 2 * gw::kWSA * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_Xsl, nm * ni * ni * 2 * gw::kWSX1 * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->t_eA, nm * ni * sizeof(int))) != GW_OK) return st;
+    if ((st = up((void**)&p->t_eX, nm * ni * sizeof(int))) != GW_OK) return st;
+  }
+  if (p->w_block) {
+    const size_t nm = (size_t)nch * p->n_qh;
+    if ((st = up((void**)&p->b_D, nm * bs * bs * sizeof(double2))) != GW_OK) return st;
+    if ((st = up((void**)&p->b_Rp, nm * bs * npb * sizeof(double2))) != GW_OK) return st;
+    if ((st = up((void**)&p->b_Asl, nm * npb * bs * 2 * gw::kWSA * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->b_Bsl, nm * npb * bs * 2 * gw::kWSX1 * 2)) != GW_OK) return st;
+    if ((st = up((void**)&p->b_eA, nm * npb * sizeof(int))) != GW_OK) return st;
+    if ((st = up((void**)&p->b_eB, nm * npb * sizeof(int))) != GW_OK) return st;
   }
   p->w_pending = false;
   return GW_OK;
@@ -447,6 +495,9 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
     // FP32 level accumulators of the residual are exact)
     const size_t n = (size_t)hh.n_pb_total();
     p->w_tensor = !(opt && opt->w_solver == 1) && n % 128 == 0 && n > 0 && n <= (size_t)gw::kWNmax;
+    // beyond it: block Gauss-Jordan over pivot blocks that the tensor-core inverse takes
+    p->w_bs = !(opt && opt->w_solver == 1) && !p->w_tensor ? gw::wblk_block_size((int)n) : 0;
+    p->w_block = p->w_bs > 0;
     bool k_ok = true;  // the tensor-core Sigma stage sums levels 0-4 exactly for K_b <= 384
     for (int s = 0; s < hh.n_species; ++s) k_ok = k_ok && hh.n_prod[s] <= 16 * gw::kOzMaxKS;
     p->sigma_tensor = !(opt && opt->fp64_products == 1) && k_ok;
@@ -502,10 +553,10 @@ gw_status gw_plan_create(const gw_cell* cell, const gw_basis* basis, const int k
   if ((st = upload(&p->d_qw, qw.data(), qw.size() * sizeof(double))) != GW_OK) return fail(st);
   if ((st = upload(&p->d_numirror, numirror.data(), numirror.size() * sizeof(int))) != GW_OK) return fail(st);
   p->ws_cap = (opt && opt->workspace_bytes) ? opt->workspace_bytes
-                                            : (p->w_tensor ? ((size_t)24 << 30) : ((size_t)4 << 30));
-  if (p->w_tensor) {
-    p->smem_GJ32 = gw::gj32_smem((int)npb);
-    if (gw::wtc_setup(p->smem_GJ32) != cudaSuccess) {
+                                            : (p->w_tensor || p->w_block ? ((size_t)24 << 30) : ((size_t)4 << 30));
+  if (p->w_tensor || p->w_block) {
+    p->smem_GJ32 = gw::gj32_smem(p->w_block ? p->w_bs : (int)npb);
+    if ((p->w_block ? gw::wblk_setup(p->smem_GJ32) : gw::wtc_setup(p->smem_GJ32)) != cudaSuccess) {
       cudaError_t e = cudaGetLastError();
       set_last_error(std::string("cudaFuncSetAttribute (tensor W): ") + cudaGetErrorString(e));
       return fail(GW_ERR_UNSUPPORTED);
@@ -607,6 +658,7 @@ gw_status gw_plan_query(gw_plan_t p, gw_plan_info* info) {
   info->cond_boson = h.cond_b;
   info->w_symmetric = p->w_sym ? 1 : 0;
   info->w_tensor = p->w_tensor ? 1 : 0;
+  info->w_block = p->w_bs;
   info->sigma_tensor = p->sigma_tensor ? 1 : 0;
   info->p_tensor = (p->ozp.ready || p->ozp_pending) ? 1 : 0;  // pending: planned at the first call
   info->mixed_queue = (p->contract_p ? 1 : 0) | (p->contract_s ? 2 : 0);
@@ -951,6 +1003,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
     }
     if ((st = check_launch("k_copy_mats")) != GW_OK) return st;
     if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsV, nq, N, s);
+    else if (p->w_block) st = launch_block_inverse(p, p->d_wsV, nq, N, s);
     else st = launch_gj(p, p->d_wsV, nq, N, s);
     if (st != GW_OK) return st;
   }
@@ -964,6 +1017,7 @@ gw_status gw_screened_W_iw(gw_plan_t p, const void* P_R_iw, const void* v_q, voi
                              (long long)nq * NN, s, p->d_qh, nq, p->d_wsV, -1.0, p->w_sym)) != GW_OK)
       return st;
     if (p->w_tensor) st = launch_tensor_inverse(p, p->d_wsA, nc * nq, N, s);
+    else if (p->w_block) st = launch_block_inverse(p, p->d_wsA, nc * nq, N, s);
     else st = launch_gj(p, p->d_wsA, nc * nq, N, s);
     if (st != GW_OK) return st;
     // W~(R) = (1/N_k) sum_q e^{-iqR} (W(q) - v(q)); in symmetric mode the sum runs over

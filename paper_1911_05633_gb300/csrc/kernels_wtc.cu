@@ -640,9 +640,10 @@ __global__ void k_split3_cols(const float2* __restrict__ M, uint16_t* __restrict
 // accumulated in FP32 in two 128-column tensor-memory accumulators.  R is small, so the
 // product is needed to 2^-24 of itself only.  kRefStages shared-memory stages; while step
 // ks runs, the stage of step ks - 1 is refilled with step ks - 1 + kRefStages.
-//   FINAL = false: lo[b] = D (X1 = X0 + lo is kept as the unevaluated FP32 pair)
-//   FINAL = true:  out[b] = hi + lo + D in FP64
-template <bool FINAL>
+//   MODE 0: lo[b] = D (X1 = X0 + lo is kept as the unevaluated FP32 pair)
+//   MODE 1: out[b] = hi + lo + D in FP64
+//   MODE 2: out[b] += D (a further refinement of the FP64 inverse in out)
+template <int MODE>
 __global__ void __launch_bounds__(128, 1)
 k_refine_tc(const uint16_t* __restrict__ PX, const uint16_t* __restrict__ PR, const float2* __restrict__ hi,
             float2* __restrict__ lo, double2* __restrict__ out, int N, int* status) {
@@ -739,9 +740,12 @@ k_refine_tc(const uint16_t* __restrict__ PX, const uint16_t* __restrict__ PR, co
         const int rr = t >> 1, cc = 32 * (t & 1) + lane;
         const float2 z = stg[rr * 65 + cc];
         const long long o = row0 + (long long)rr * N + c0 + cc;
-        if (FINAL) {
+        if (MODE == 1) {
           const float2 h = hi[o], l = lo[o];
           out[o] = make_double2(f2d(h.x) + f2d(l.x) + f2d(z.x), f2d(h.y) + f2d(l.y) + f2d(z.y));
+        } else if (MODE == 2) {
+          const double2 x = out[o];
+          out[o] = make_double2(x.x + f2d(z.x), x.y + f2d(z.y));
         } else {
           lo[o] = z;
         }
@@ -758,12 +762,14 @@ cudaError_t wtc_setup(size_t smem_gj32) {
   cudaError_t e = raise_smem_limit(k_gj_inverse_f32, smem_gj32);
   if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX0, kWL0>, w_residual_smem(kWSX0, kWL0));
   if (e == cudaSuccess) e = raise_smem_limit(k_ozaki_residual<kWSX1, kWLmax>, w_residual_smem(kWSX1, kWLmax));
-  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<false>, w_refine_smem());
-  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<true>, w_refine_smem());
+  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<0>, w_refine_smem());
+  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<1>, w_refine_smem());
+  if (e == cudaSuccess) e = raise_smem_limit(k_refine_tc<2>, w_refine_smem());
   return e;
 }
 
-void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t smem_gj32, cudaStream_t st) {
+void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t smem_gj32, cudaStream_t st,
+                 int refinements) {
   const long long NN = (long long)N * N;
   const long long tot = (long long)batch * NN;
   const unsigned g1 = (unsigned)((tot + 255) / 256 < 65535LL * 8 ? (tot + 255) / 256 : 65535LL * 8);
@@ -814,7 +820,7 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
   }
   {
     gw::TimedLaunch tl_("k_refine_tc<first>", st);
-    k_refine_tc<false><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, nullptr, N, w.status);
+    k_refine_tc<0><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, nullptr, N, w.status);
   }
   // R1 = I - A X1 (FP32), X2 = X1 + X0 R1 in FP64, written over A
   {
@@ -836,7 +842,396 @@ void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t sm
   }
   {
     gw::TimedLaunch tl_("k_refine_tc<final>", st);
-    k_refine_tc<true><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, mats, N, w.status);
+    k_refine_tc<1><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, mats, N, w.status);
+  }
+  // X <- X + X (I - A X) again, the left factor now the current X rounded to FP32 (the
+  // correction is needed to 2^-24 of itself only): with X0 there the error would shrink
+  // by |I - A X0| per step, with X by about kappa 2^-24 |I - A X|
+  for (int r = 3; r <= refinements; ++r) {
+    {
+      gw::TimedLaunch tl_("k_to_f32", st);
+      k_to_f32<<<g1, 256, 0, st>>>(mats, w.X32, tot);
+    }
+    {
+      gw::TimedLaunch tl_("k_split3_rows", st);
+      k_split3_rows<<<g8, 256, 0, st>>>(w.X32, w.PX, N, tot);
+    }
+    {
+      gw::TimedLaunch tl_("k_panel_col_exp", st);
+      k_panel_col_exp<<<dim3((unsigned)((N + 127) / 128), (unsigned)batch), 128, 0, st>>>(mats, NN, N, N, N, w.eX);
+    }
+    {
+      gw::TimedLaunch tl_("k_slice_panel_B", st);
+      k_slice_panel_B<<<g8, 256, 0, st>>>(mats, NN, N, w.eX, w.Xsl, N, N, t8);
+    }
+    {
+      gw::TimedLaunch tl_("k_ozaki_residual<third>", st);
+      k_ozaki_residual<kWSX1, kWLmax><<<gres, 128, w_residual_smem(kWSX1, kWLmax), st>>>(w.Asl, w.Xsl, w.eA, w.eX,
+                                                                                        w.R, N, w.status);
+    }
+    {
+      gw::TimedLaunch tl_("k_split3_cols", st);
+      k_split3_cols<<<g8, 256, 0, st>>>(w.R, w.Xsl, N, tot);
+    }
+    {
+      gw::TimedLaunch tl_("k_refine_tc<add>", st);
+      k_refine_tc<2><<<gref, 128, w_refine_smem(), st>>>(w.PX, w.Xsl, w.X32, w.lo, mats, N, w.status);
+    }
+  }
+}
+
+
+// ---- Block Gauss-Jordan for N_PB beyond kWNmax --------------------------------------
+//
+// The inverse of an N x N matrix with N = nb bs (bs <= kWNmax) by Gauss-Jordan over
+// blocks of bs rows and columns, without pivoting across blocks (the matrices of the W
+// solve, v(q) and v(q)^-1 - P(q, i nu), are Hermitian positive definite, so every pivot
+// block is too).  Pivot step k, with D = A_kk^-1 (the tensor-core inverse of bs x bs):
+//   Rp = D A_k,:  (its block k replaced by I + D),
+//   A_i,: -= A_ik Rp for every row block i != k   (so A_ik becomes -A_ik D),
+//   A_k,: = Rp with block k = D.
+// Every product has K = bs <= kWNmax terms, so it runs as the residual does: exact BF16
+// digits of the two panels (per-row and per-column power-of-two scales), the level sums
+// exact in FP32 tensor-memory accumulators, one exact 64-bit sum rounded once to FP64.
+
+// Scale exponent of each row of an M x K panel (rows ld apart, matrices ms apart): one
+// warp per row.
+__global__ void k_panel_row_exp(const double2* __restrict__ A, long long ms, int ld, int M, int K, int batch,
+                                int* __restrict__ e) {
+  const int warps = blockDim.x >> 5;
+  const long long row = (long long)blockIdx.x * warps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= (long long)batch * M) return;
+  const long long b = row / M, i = row % M;
+  const double2* a = A + b * ms + i * ld;
+  int m = 0;
+  for (int k = lane; k < K; k += 32) m = max(m, max(exp_field(a[k].x), exp_field(a[k].y)));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[row] = m > 0 ? m - 1022 : 0;
+}
+
+// Scale exponent of each column of a K x Nc panel: one thread per column.
+__global__ void k_panel_col_exp(const double2* __restrict__ B, long long ms, int ld, int K, int Nc,
+                                int* __restrict__ e) {
+  const int b = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Nc) return;
+  const double2* c = B + (long long)b * ms + j;
+  int m = 0;
+  for (int k = 0; k < K; ++k) {
+    const double2 z = c[(long long)k * ld];
+    m = max(m, max(exp_field(z.x), exp_field(z.y)));
+  }
+  e[(long long)b * Nc + j] = m > 0 ? m - 1022 : 0;
+}
+
+// A-operand digits of an M x K panel, chunks as k_slice_A: one per (matrix, 128-row
+// block, 16-wide K step) with the kWSA digits of Re, then of Im.
+__global__ void k_slice_panel_A(const double2* __restrict__ A, long long ms, int ld, const int* __restrict__ eA,
+                                uint16_t* __restrict__ Asl, int M, int K, long long n_thr) {
+  const int NKS = K / 16, NIB = M / 128;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;  // (b, ib, ks, row group pair)
+    const int gp = (int)(w % 8); w /= 8;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int ib = (int)(w % NIB);
+    const long long b = w / NIB;
+    const int h = (lane >> 3) & 1;
+    const int il = (lane & 7) + 8 * ((lane >> 4) + 2 * gp);
+    const int i = ib * 128 + il;
+    const int k0 = ks * 16 + 8 * h;
+    const int e = eA[b * M + i];
+    const double2* src = A + b * ms + (long long)i * ld + k0;
+    long long mr[8], mi[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 z = src[u];
+      mr[u] = fixed56(z.x, e);
+      mi[u] = fixed56(z.y, e);
+    }
+    uint16_t* chunk = Asl + ((b * NIB + ib) * NKS + ks) * (long long)(kWAChunk / 2);
+    const uint32_t off = kmajor_offset(128, il, 8 * h) / 2;
+#pragma unroll
+    for (int s = 0; s < kWSA; ++s) {
+      uint32_t pr[4], pi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t r0 = digit_bf16(next_digit(mr[2 * u], s), s), r1 = digit_bf16(next_digit(mr[2 * u + 1], s), s);
+        const uint32_t i0 = digit_bf16(next_digit(mi[2 * u], s), s), i1 = digit_bf16(next_digit(mi[2 * u + 1], s), s);
+        pr[u] = r0 | (r1 << 16);
+        pi[u] = i0 | (i1 << 16);
+      }
+      *reinterpret_cast<uint4*>(chunk + (0 * kWSA + s) * (128 * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (1 * kWSA + s) * (128 * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+    }
+  }
+}
+
+// B-operand digits of a K x Nc panel (FP64), chunks as k_slice_X<kWSX1>: one per
+// (matrix, kWTN-column block, 16-wide K step) with the kWSX1 digits of Re, then of Im.
+__global__ void k_slice_panel_B(const double2* __restrict__ B, long long ms, int ld, const int* __restrict__ eB,
+                                uint16_t* __restrict__ Bsl, int K, int Nc, long long n_thr) {
+  constexpr int JG = kWTN / 16;
+  const int NKS = K / 16, NJB = Nc / kWTN;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_thr; x += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    long long w = x >> 5;  // (b, jb, ks, column group)
+    const int jg = (int)(w % JG); w /= JG;
+    const int ks = (int)(w % NKS); w /= NKS;
+    const int jb = (int)(w % NJB);
+    const long long b = w / NJB;
+    const int h = (lane >> 3) & 1;
+    const int jl = (lane & 7) + 8 * ((lane >> 4) + 2 * jg);
+    const int j = jb * kWTN + jl;
+    const int k0 = ks * 16 + 8 * h;
+    const int e = eB[b * Nc + j];
+    const double2* src = B + b * ms + (long long)k0 * ld + j;
+    long long mr[8], mi[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 z = src[(long long)u * ld];
+      mr[u] = fixed56(z.x, e);
+      mi[u] = fixed56(z.y, e);
+    }
+    uint16_t* chunk = Bsl + ((b * NJB + jb) * NKS + ks) * (long long)(wx_chunk(kWSX1) / 2);
+    const uint32_t off = kmajor_offset(kWTN, jl, 8 * h) / 2;
+#pragma unroll
+    for (int t = 0; t < kWSX1; ++t) {
+      uint32_t pr[4], pi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t r0 = digit_bf16(next_digit(mr[2 * u], t), t), r1 = digit_bf16(next_digit(mr[2 * u + 1], t), t);
+        const uint32_t i0 = digit_bf16(next_digit(mi[2 * u], t), t), i1 = digit_bf16(next_digit(mi[2 * u + 1], t), t);
+        pr[u] = r0 | (r1 << 16);
+        pi[u] = i0 | (i1 << 16);
+      }
+      *reinterpret_cast<uint4*>(chunk + (0 * kWSX1 + t) * (kWTN * 16) + off) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<uint4*>(chunk + (1 * kWSX1 + t) * (kWTN * 16) + off) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+    }
+  }
+}
+
+// dst[b][r][c] = src[b][r][c] (+ 1 on the diagonal r == c when add_identity), r < rows,
+// c < cols, for matrices of row strides sld / dld and matrix strides sms / dms.
+__global__ void k_copy_panel(const double2* __restrict__ src, long long sms, int sld, double2* __restrict__ dst,
+                             long long dms, int dld, int rows, int cols, int batch, int add_identity) {
+  const long long per = (long long)rows * cols, n = per * batch;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const long long b = x / per, rc = x % per;
+    const int r = (int)(rc / cols), c = (int)(rc % cols);
+    double2 z = src[b * sms + (long long)r * sld + c];
+    if (add_identity && r == c) z.x += 1.0;
+    dst[b * dms + (long long)r * dld + c] = z;
+  }
+}
+
+
+// C = A B (accumulate 0) or C = C - A B (accumulate 1) for an M x K panel A and a K x Nc
+// panel B given as digits (k_slice_panel_A / _B), K <= kWNmax, FP64 out.  Blocks as the
+// residual's: 128 output rows (Re rows for blockIdx.y < M/128, else Im rows) x kWTN
+// columns, the products a_s b_t with s + t <= kWLmax in the eight level accumulators;
+// row blocks [skip0, skip1) are left alone.  The epilogue sums the levels as one exact
+// 64-bit integer in units of 2^(eA + eB - 52), rounds it once to FP64 and stages each
+// warp's 32 x 16 results in shared memory so that a store covers two rows of 16 columns.
+__global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant__ PanelGemmArgs g) {
+  constexpr int SX = kWSX1, LMAX = kWLmax, NA = LMAX + 1;
+  static_assert(NA <= kWSA, "A has kWSA digits");
+  constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;
+  constexpr uint32_t AB = NA * PA, XB = SX * PX, SB = AB + XB;
+  constexpr uint32_t XC = wx_chunk(SX);
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t full[kWStages];
+  __shared__ __align__(8) uint64_t mmad[kWStages];
+  const int jb = blockIdx.x;
+  const int NKS = g.K / 16, NIB = g.M / 128, NJB = g.Nc / kWTN;
+  const bool imrow = (int)blockIdx.y >= NIB;
+  const int ib = imrow ? (int)blockIdx.y - NIB : (int)blockIdx.y;
+  if (ib >= g.skip0 && ib < g.skip1) return;  // the whole block: before any barrier or allocation
+  const long long b = blockIdx.z;
+  const int NK2 = 2 * NKS;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int* status = g.status;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kWStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&mmad[s], 1);
+    }
+    fence_mbar_init();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tm = tmem_base;
+  const unsigned char* Abase =
+      reinterpret_cast<const unsigned char*>(g.Asl) + ((b * NIB + ib) * NKS) * (long long)kWAChunk;
+  const unsigned char* Xbase = reinterpret_cast<const unsigned char*>(g.Bsl) + ((b * NJB + jb) * NKS) * (long long)XC;
+  // step kk: half 0 takes (Ar | Ai for Im rows) with Br, half 1 (Ai negated | Ar) with Bi
+  auto load = [&](int kk, int st) {
+    const int half = kk >= NKS ? 1 : 0, ks = kk - half * NKS;
+    const int cA = imrow ? 1 - half : half;
+    unsigned char* dst = sm + st * SB;
+    mbar_arrive_expect_tx(&full[st], SB);
+    bulk_g2s(dst, Abase + (long long)ks * kWAChunk + (long long)cA * kWSA * PA, AB, &full[st]);
+    bulk_g2s(dst + AB, Xbase + (long long)ks * XC + (long long)half * SX * PX, XB, &full[st]);
+  };
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t id = idesc_bf16_f32(128, kWTN), idn = idesc_bf16_f32_negA(128, kWTN);
+    const uint32_t s0 = smem_u32(sm);
+    for (int s = 0; s < kWStages && s < NK2; ++s) load(s, s);
+    for (int kk = 0; kk < NK2; ++kk) {
+      const int st = kk % kWStages;
+      if (!mbar_wait(&full[st], (uint32_t)(kk / kWStages) & 1u, kWaitNs, status)) { ok = false; break; }
+      fence_after_sync();
+      const int half = kk >= NKS ? 1 : 0;
+      const uint32_t fresh = kk == 0 ? 0xFFu : (kk == NKS ? ((1u << 4) | (1u << 6)) : 0u);
+      ozaki_issue_step<SX, NA, LMAX>(tm, smem_desc(s0 + st * SB, 128, 256), smem_desc(s0 + st * SB + AB, 128, 256),
+                                     (!imrow && half) ? idn : id, half, fresh);
+      mma_commit(&mmad[st]);
+      if (kk >= 1 && kk - 1 + kWStages < NK2) {
+        const int so = (kk - 1) % kWStages;
+        if (!mbar_wait(&mmad[so], (uint32_t)((kk - 1) / kWStages) & 1u, kWaitNs, status)) { ok = false; break; }
+        load(kk - 1 + kWStages, so);
+      }
+    }
+  }
+  const int last = NK2 - 1;
+  const bool done = ok && mbar_wait(&mmad[last % kWStages], (uint32_t)(last / kWStages) & 1u, kWaitNs, status);
+  ok = __syncthreads_and(done ? 1 : 0) != 0;
+  fence_after_sync();
+  if (!ok) {
+    if (tid == 0) atomicExch(status, 2);
+  } else {
+    const int i = ib * 128 + 32 * warp + lane;
+    const int ea = g.eA[b * g.M + i];
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    double* stg = reinterpret_cast<double*>(sm) + warp * (32 * 17);
+    double* Cw = reinterpret_cast<double*>(g.C + b * g.c_ms + (long long)(ib * 128 + 32 * warp) * g.ldc) + (imrow ? 1 : 0);
+    for (int c0 = 0; c0 < kWTN; c0 += 16) {
+      float v[128];  // accumulator q, column c at v[16 q + c]
+      tmem_ld16x4(tm + lane_base + (uint32_t)c0, kWTN, v);
+      tmem_ld16x4(tm + lane_base + (uint32_t)(4 * kWTN + c0), kWTN, v + 64);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        long long val = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) val += level_units52(v[16 * q + c], q);
+        const int j = jb * kWTN + c0 + c;
+        stg[lane * 17 + c] = i2d_scaled(val, ea + g.eB[b * g.Nc + j] - 52);
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int t = 0; t < 16; ++t) {
+        const int rr = 2 * t + (lane >> 4), cc = lane & 15;
+        double* o = Cw + 2 * ((long long)rr * g.ldc + jb * kWTN + c0 + cc);
+        const double pv = stg[rr * 17 + cc];
+        *o = g.accumulate ? *o - pv : pv;
+      }
+      __syncwarp();
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+
+namespace {
+
+unsigned grid_for(long long n_thr) {
+  const long long g = (n_thr + 255) / 256;
+  return (unsigned)(g < 65535LL * 8 ? (g > 0 ? g : 1) : 65535LL * 8);
+}
+
+// C (M x Nc, rows ldc apart, matrices c_ms apart) = / -= A B for the panels A (M x K at
+// A, rows lda apart) and B (K x Nc at B, rows ldb apart), every matrix of the batch.
+void panel_gemm(const WblkBuffers& w, const double2* A, long long a_ms, int lda, const double2* B, long long b_ms,
+                int ldb, double2* C, long long c_ms, int ldc, int M, int Nc, int K, int batch, int skip0, int skip1,
+                int accumulate, cudaStream_t st) {
+  {
+    gw::TimedLaunch tl_("k_panel_row_exp", st);
+    k_panel_row_exp<<<(unsigned)((batch * (long long)M + 7) / 8), 256, 0, st>>>(A, a_ms, lda, M, K, batch, w.eA);
+  }
+  {
+    gw::TimedLaunch tl_("k_slice_panel_A", st);
+    k_slice_panel_A<<<grid_for((long long)batch * M * K / 8), 256, 0, st>>>(A, a_ms, lda, w.eA, w.Asl, M, K,
+                                                                             (long long)batch * M * K / 8);
+  }
+  {
+    gw::TimedLaunch tl_("k_panel_col_exp", st);
+    k_panel_col_exp<<<dim3((unsigned)((Nc + 127) / 128), (unsigned)batch), 128, 0, st>>>(B, b_ms, ldb, K, Nc, w.eB);
+  }
+  {
+    gw::TimedLaunch tl_("k_slice_panel_B", st);
+    k_slice_panel_B<<<grid_for((long long)batch * K * Nc / 8), 256, 0, st>>>(B, b_ms, ldb, w.eB, w.Bsl, K, Nc,
+                                                                              (long long)batch * K * Nc / 8);
+  }
+  PanelGemmArgs g{};
+  g.Asl = w.Asl;
+  g.Bsl = w.Bsl;
+  g.eA = w.eA;
+  g.eB = w.eB;
+  g.C = C;
+  g.c_ms = c_ms;
+  g.ldc = ldc;
+  g.M = M;
+  g.Nc = Nc;
+  g.K = K;
+  g.skip0 = skip0;
+  g.skip1 = skip1;
+  g.accumulate = accumulate;
+  g.status = w.inner.status;
+  {
+    gw::TimedLaunch tl_("k_oz_panel_gemm", st);
+    k_oz_panel_gemm<<<dim3((unsigned)(Nc / kWTN), (unsigned)(2 * (M / 128)), (unsigned)batch), 128,
+                      w_residual_smem(kWSX1, kWLmax), st>>>(g);
+  }
+}
+
+void copy_panel(const double2* src, long long sms, int sld, double2* dst, long long dms, int dld, int rows, int cols,
+                int batch, int add_identity, cudaStream_t st) {
+  gw::TimedLaunch tl_("k_copy_panel", st);
+  k_copy_panel<<<grid_for((long long)batch * rows * cols), 256, 0, st>>>(src, sms, sld, dst, dms, dld, rows, cols,
+                                                                          batch, add_identity);
+}
+
+}  // namespace
+
+int wblk_block_size(int N) {
+  if (N <= kWNmax || N % 128 != 0) return 0;
+  for (int bs = kWNmax; bs >= 128; bs -= 128)
+    if (N % bs == 0) return bs;
+  return 0;
+}
+
+cudaError_t wblk_setup(size_t smem_gj32_bs) {
+  cudaError_t e = wtc_setup(smem_gj32_bs);
+  if (e == cudaSuccess) e = raise_smem_limit(k_oz_panel_gemm, w_residual_smem(kWSX1, kWLmax));
+  return e;
+}
+
+void wblk_inverse(const WblkBuffers& w, double2* mats, int batch, int N, int bs, size_t smem_gj32_bs,
+                  cudaStream_t st) {
+  const long long NN = (long long)N * N, BB = (long long)bs * bs, BN = (long long)bs * N;
+  for (int k = 0; k < N / bs; ++k) {
+    const int r0 = k * bs;
+    // D = A_kk^-1
+    copy_panel(mats + (long long)r0 * N + r0, NN, N, w.D, BB, bs, bs, bs, batch, 0, st);
+    wtc_inverse(w.inner, w.D, batch, bs, smem_gj32_bs, st, kWblkRefinements);
+    // Rp = D A_k,: with block k = I + D
+    panel_gemm(w, w.D, BB, bs, mats + (long long)r0 * N, NN, N, w.Rp, BN, N, bs, N, bs, batch, 0, 0, 0, st);
+    copy_panel(w.D, BB, bs, w.Rp + r0, BN, N, bs, bs, batch, 1, st);
+    // A_i,: -= A_ik Rp for the other row blocks (the column panel is sliced before any write)
+    panel_gemm(w, mats + r0, NN, N, w.Rp, BN, N, mats, NN, N, N, N, bs, batch, r0 / 128, (r0 + bs) / 128, 1, st);
+    // A_k,: = Rp with block k = D
+    copy_panel(w.Rp, BN, N, mats + (long long)r0 * N, NN, N, bs, N, batch, 0, st);
+    copy_panel(w.D, BB, bs, mats + (long long)r0 * N + r0, NN, N, bs, bs, batch, 0, st);
   }
 }
 

@@ -62,7 +62,52 @@ struct WtcBuffers {
 
 // Raise the shared-memory limits of the kernels (once per device and size).
 cudaError_t wtc_setup(size_t smem_gj32);
-// In place: mats[b] (FP64, N x N, N a multiple of 128) -> inverse, for b < batch.
-void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t smem_gj32, cudaStream_t st);
+
+// ---- block Gauss-Jordan for N beyond kWNmax (kernels_wtc.cu) ----------------------
+// Arguments of k_oz_panel_gemm: C = A B (accumulate 0) or C -= A B (1) from the digits
+// of an M x K and a K x Nc panel (M a multiple of 128, Nc of kWTN, K of 16 and <= kWNmax).
+struct PanelGemmArgs {
+  const uint16_t* Asl;
+  const uint16_t* Bsl;
+  const int* eA;
+  const int* eB;
+  double2* C;
+  long long c_ms;  // matrix stride of C (elements)
+  int ldc;         // row stride of C (elements)
+  int M, Nc, K;
+  int skip0, skip1;  // 128-row blocks of C left alone
+  int accumulate;
+  int* status;
+};
+// Scratch of one batch of block inverses of N x N with pivot blocks of bs (per matrix:
+// the pivot block D, the row panel Rp, the digits of a bs-column and a bs-row panel, 2 N
+// exponents) and the tensor-core inverse of the bs x bs pivot blocks.
+struct WblkBuffers {
+  double2* D;     // [batch][bs][bs]
+  double2* Rp;    // [batch][bs][N]
+  uint16_t* Asl;  // digits of the N x bs column panel (or of D)
+  uint16_t* Bsl;  // digits of the bs x N row panel
+  int* eA;        // [batch][N]
+  int* eB;        // [batch][N]
+  WtcBuffers inner;  // for batch matrices of bs x bs
+};
+// refinements of the FP32 inverse of each pivot block
+constexpr int kWblkRefinements = 4;
+// Pivot block size for N (the largest multiple of 128 up to kWNmax dividing N), or 0
+// when N needs no blocks (N <= kWNmax) or has none (N not a multiple of 128).
+int wblk_block_size(int N);
+cudaError_t wblk_setup(size_t smem_gj32_bs);
+// In place: mats[b] (FP64, N x N, Hermitian positive definite or with well-conditioned
+// leading blocks) -> inverse, for b < batch; bs = wblk_block_size(N).
+void wblk_inverse(const WblkBuffers& w, double2* mats, int batch, int N, int bs, size_t smem_gj32_bs,
+                  cudaStream_t st);
+// In place: mats[b] (FP64, N x N, N a multiple of 128) -> inverse, for b < batch, with
+// `refinements` (at least 2) FP64-accurate refinements of the FP32 inverse.
+void wtc_inverse(const WtcBuffers& w, double2* mats, int batch, int N, size_t smem_gj32, cudaStream_t st,
+                 int refinements = 2);
+__global__ void k_panel_col_exp(const double2* __restrict__ B, long long ms, int ld, int K, int Nc,
+                                int* __restrict__ e);
+__global__ void k_slice_panel_B(const double2* __restrict__ B, long long ms, int ld, const int* __restrict__ eB,
+                                uint16_t* __restrict__ Bsl, int K, int Nc, long long n_thr);
 
 }  // namespace gw

@@ -71,7 +71,8 @@ class GwPlanInfo(C.Structure):
                 ("nu_chunk", C.c_int), ("cond_fermion", C.c_double), ("cond_boson", C.c_double),
                 ("w_symmetric", C.c_int), ("n_q_solved", C.c_int), ("w_tensor", C.c_int),
                 ("sigma_tensor", C.c_int), ("p_tensor", C.c_int), ("transform_tensor", C.c_int),
-                ("n_entries_far", C.c_int), ("n_entries_near", C.c_int), ("mixed_queue", C.c_int)]
+                ("n_entries_far", C.c_int), ("n_entries_near", C.c_int), ("mixed_queue", C.c_int),
+                ("w_block", C.c_int)]
 
 
 class GwBatchInfo(C.Structure):

@@ -75,6 +75,9 @@ class Sys:
         # N_PB of 128, 256 or 384 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
         n = cell.n_pb_total
         assert self.plan.info["w_tensor"] == int(n % 128 == 0 and n <= 384 and plan_kw.get("w_solver") != "gauss_jordan")
+        # beyond 384: block Gauss-Jordan over the largest pivot block of 384, 256 or 128 dividing N_PB
+        bs = next((b for b in (384, 256, 128) if n > 384 and n % b == 0), 0)
+        assert self.plan.info["w_block"] == (bs if plan_kw.get("w_solver") != "gauss_jordan" else 0)
         # the FP64 Sigma takes its W~ C^b stage from the tensor cores for K <= 64 unless the plan
         # asks for FP64 only
         # FP64-accurate tensor-core products (reductions up to 384 terms) unless the plan asks
@@ -139,6 +142,13 @@ def system(name):
         elif name == "c1_3tier":  # 8-atom cell, cutoff 7.5: nearest neighbours 36 of 48, second ones 24
             _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=7.5, n_tau=12, kmesh=(2, 2, 2)),
                                                     4.6, [24], n_prod_near=[36]))
+        elif name == "c2_8_blk":  # N_PB 512: two pivot blocks of 256
+            _CACHE[name] = Sys(synth.make_config(2, atoms=8, cutoff=5.0, n_tau=12))
+        elif name == "c2_16_blk":  # N_PB 1024: four pivot blocks of 256
+            _CACHE[name] = Sys(synth.make_config(2, atoms=16, cutoff=5.0, n_tau=12))
+        elif name == "c2_16_k48_blk":  # N_PB 768: two pivot blocks of 384
+            _CACHE[name] = Sys(synth.make_config(2, atoms=16, cutoff=5.0, n_tau=12,
+                                                 species=[synth.Species("spd", 9, 48, None)]))
         elif name == "c1_far_fp64":
             _CACHE[name] = Sys(synth.with_far_basis(synth.make_config(1, cutoff=5.0, n_tau=12, kmesh=(2, 2, 2)),
                                                     4.0, [24]), fp64_products="fp64")
@@ -224,7 +234,10 @@ def test_transform_structured_inputs(name):
     assert np.all(pack(kept) == 7.0 - 3.0j)
 
 
-@pytest.mark.parametrize("name", SMALL + FAR + ["c0_nosym", "c1_cut5_gj"])
+BLOCK = ["c2_8_blk", "c2_16_blk", "c2_16_k48_blk"]  # N_PB beyond 384: the block Gauss-Jordan inverse
+
+
+@pytest.mark.parametrize("name", SMALL + FAR + BLOCK + ["c0_nosym", "c1_cut5_gj"])
 def test_screened_W(name):
     s = system(name)
     PR = oracle.polarizability_R(s.G_R(), s.orc.entries, s.orc.C_atom, s.cell.spin, s.orc.kdims)
