@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--w-solve", action="store_true",
                     help="time the W solve (Eq. W_1) of the configuration-2 cell of --atoms atoms on the P of "
                          "its own FP64 rows; one JSON line")
+    ap.add_argument("--workspace-gb", type=float, default=0.0,
+                    help="--w-solve: cap on the W-solve scratch in GB (0: the library's default)")
     ap.add_argument("--scaling", type=int, nargs="*", default=None,
                     help="time the P+Sigma rows (no W solve) of the 64-function diamond series at these atom "
                          "counts (default 8 16 32 48 72), FP64 and mixed; one JSON line")
@@ -1176,7 +1178,8 @@ def run_w_solve(args, local):
     cell = synth.make_config(2, atoms=args.atoms)
     vq, _ = cell.coulomb()
     t_host = time.perf_counter() - t0
-    plan = gw.Plan.from_cell(cell, device=local, w_solver=args.w_solver)
+    plan = gw.Plan.from_cell(cell, device=local, w_solver=args.w_solver,
+                             workspace_bytes=int(args.workspace_gb * 1e9))
     inf = plan.info
     nt, nn = inf["n_tau"], inf["n_nu"]
     stream = torch.cuda.Stream(device=local)

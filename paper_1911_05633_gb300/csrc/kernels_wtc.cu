@@ -1027,15 +1027,53 @@ __global__ void k_copy_panel(const double2* __restrict__ src, long long sms, int
 }
 
 
+// Level L of a panel product (accumulator L) in units of 2^-52.  With K <= kWblkMaxK
+// complex terms (2K real products per level) the sums of levels 0..5 are integers in their
+// unit 2^-7(L+2) below 2^24, so exact in FP32; levels 6 and 7 are rounded there and here,
+// far below 2^-52 of the scale.
+__device__ __forceinline__ long long panel_units52(float v, int L) {
+  switch (L) {
+    case 0: return (long long)__float2int_rn(v * 0x1p14f) << 38;
+    case 1: return (long long)__float2int_rn(v * 0x1p21f) << 31;
+    case 2: return (long long)__float2int_rn(v * 0x1p28f) << 24;
+    case 3: return (long long)__float2int_rn(v * 0x1p35f) << 17;
+    case 4: return (long long)__float2int_rn(v * 0x1p42f) << 10;
+    case 5: return (long long)__float2int_rn(v * 0x1p49f) << 3;
+    default: return __float2ll_rn(v * 0x1p52f);
+  }
+}
+
+// The MMAs of one 16-wide K step of a panel product: accumulator L holds level L, so for
+// digit s of A the digits t = 0 .. 7 - s of B feed the consecutive accumulators s .. 7, and
+// a run of up to four B planes (consecutive in shared memory) is one MMA of 64 x run
+// columns: 11 MMAs per K step, each A plane read at most twice.
+// `first`: the first K step, whose runs of digit 0 write their accumulators (every level
+// has one) and the later runs add to them.
+__device__ __forceinline__ void panel_issue_step(uint32_t tm, uint64_t da0, uint64_t dx0, bool neg, bool first) {
+  constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;  // bytes per A / B plane
+#pragma unroll
+  for (int s = 0; s <= kWLmax; ++s) {
+#pragma unroll
+    for (int t0 = 0; t0 <= kWLmax - s; t0 += 4) {
+      const int n = (kWLmax - s - t0 + 1) < 4 ? (kWLmax - s - t0 + 1) : 4;
+      const uint32_t id = neg ? idesc_bf16_f32_negA(128, kWTN * n) : idesc_bf16_f32(128, kWTN * n);
+      mma_bf16(tm + (uint32_t)(s + t0) * kWTN, da0 + (uint64_t)((s * PA) >> 4), dx0 + (uint64_t)((t0 * PX) >> 4), id,
+               (first && s == 0) ? 0u : 1u);
+    }
+  }
+}
+
 // C = A B (accumulate 0) or C = C - A B (accumulate 1) for an M x K panel A and a K x Nc
-// panel B given as digits (k_slice_panel_A / _B), K <= kWNmax, FP64 out.  Blocks as the
-// residual's: 128 output rows (Re rows for blockIdx.y < M/128, else Im rows) x kWTN
-// columns, the products a_s b_t with s + t <= kWLmax in the eight level accumulators;
-// row blocks [skip0, skip1) are left alone.  The epilogue sums the levels as one exact
-// 64-bit integer in units of 2^(eA + eB - 52), rounds it once to FP64 and stages each
-// warp's 32 x 16 results in shared memory so that a store covers two rows of 16 columns.
+// panel B given as digits (k_slice_panel_A / _B), K <= kWblkMaxK, FP64 out.  Blocks of
+// 128 output rows (Re rows for blockIdx.y < M/128, else Im rows) x kWTN columns, the
+// products a_s b_t with s + t <= 7 in eight level accumulators (one per level, both K
+// halves together); row blocks [skip0, skip1) are left alone.  The epilogue sums the
+// levels as one exact 64-bit integer in units of 2^(eA + eB - 52), rounds it once to FP64
+// and stages each warp's 32 x 16 results in shared memory so that a store covers two rows
+// of 16 columns.
 __global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant__ PanelGemmArgs g) {
   constexpr int SX = kWSX1, LMAX = kWLmax, NA = LMAX + 1;
+  static_assert(LMAX == 7 && SX == 8, "eight levels, eight accumulators of kWTN columns");
   static_assert(NA <= kWSA, "A has kWSA digits");
   constexpr uint32_t PA = 128 * 16 * 2, PX = kWTN * 16 * 2;
   constexpr uint32_t AB = NA * PA, XB = SX * PX, SB = AB + XB;
@@ -1082,7 +1120,6 @@ __global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant_
   };
   bool ok = true;
   if (tid == 0) {
-    const uint32_t id = idesc_bf16_f32(128, kWTN), idn = idesc_bf16_f32_negA(128, kWTN);
     const uint32_t s0 = smem_u32(sm);
     for (int s = 0; s < kWStages && s < NK2; ++s) load(s, s);
     for (int kk = 0; kk < NK2; ++kk) {
@@ -1090,9 +1127,8 @@ __global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant_
       if (!mbar_wait(&full[st], (uint32_t)(kk / kWStages) & 1u, kWaitNs, status)) { ok = false; break; }
       fence_after_sync();
       const int half = kk >= NKS ? 1 : 0;
-      const uint32_t fresh = kk == 0 ? 0xFFu : (kk == NKS ? ((1u << 4) | (1u << 6)) : 0u);
-      ozaki_issue_step<SX, NA, LMAX>(tm, smem_desc(s0 + st * SB, 128, 256), smem_desc(s0 + st * SB + AB, 128, 256),
-                                     (!imrow && half) ? idn : id, half, fresh);
+      panel_issue_step(tm, smem_desc(s0 + st * SB, 128, 256), smem_desc(s0 + st * SB + AB, 128, 256), !imrow && half,
+                       kk == 0);
       mma_commit(&mmad[st]);
       if (kk >= 1 && kk - 1 + kWStages < NK2) {
         const int so = (kk - 1) % kWStages;
@@ -1113,7 +1149,19 @@ __global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant_
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     double* stg = reinterpret_cast<double*>(sm) + warp * (32 * 17);
     double* Cw = reinterpret_cast<double*>(g.C + b * g.c_ms + (long long)(ib * 128 + 32 * warp) * g.ldc) + (imrow ? 1 : 0);
+    const int* eBj = g.eB + b * g.Nc + jb * kWTN;
     for (int c0 = 0; c0 < kWTN; c0 += 16) {
+      // this group's old C values and column exponents first: independent loads in flight
+      // while the accumulators are read (a load after each store would wait out its latency)
+      double cold[16];
+      int eb[16];
+      const int cc = lane & 15;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int rr = 2 * t + (lane >> 4);
+        cold[t] = g.accumulate ? Cw[2 * ((long long)rr * g.ldc + jb * kWTN + c0 + cc)] : 0.0;
+        eb[t] = eBj[c0 + t];
+      }
       float v[128];  // accumulator q, column c at v[16 q + c]
       tmem_ld16x4(tm + lane_base + (uint32_t)c0, kWTN, v);
       tmem_ld16x4(tm + lane_base + (uint32_t)(4 * kWTN + c0), kWTN, v + 64);
@@ -1121,17 +1169,15 @@ __global__ void __launch_bounds__(128, 1) k_oz_panel_gemm(const __grid_constant_
       for (int c = 0; c < 16; ++c) {
         long long val = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) val += level_units52(v[16 * q + c], q);
-        const int j = jb * kWTN + c0 + c;
-        stg[lane * 17 + c] = i2d_scaled(val, ea + g.eB[b * g.Nc + j] - 52);
+        for (int q = 0; q < 8; ++q) val += panel_units52(v[16 * q + c], q);
+        stg[lane * 17 + c] = i2d_scaled(val, ea + eb[c] - 52);
       }
       __syncwarp();
-#pragma unroll 4
+#pragma unroll
       for (int t = 0; t < 16; ++t) {
-        const int rr = 2 * t + (lane >> 4), cc = lane & 15;
-        double* o = Cw + 2 * ((long long)rr * g.ldc + jb * kWTN + c0 + cc);
+        const int rr = 2 * t + (lane >> 4);
         const double pv = stg[rr * 17 + cc];
-        *o = g.accumulate ? *o - pv : pv;
+        Cw[2 * ((long long)rr * g.ldc + jb * kWTN + c0 + cc)] = g.accumulate ? cold[t] - pv : pv;
       }
       __syncwarp();
     }
@@ -1205,7 +1251,7 @@ void copy_panel(const double2* src, long long sms, int sld, double2* dst, long l
 
 int wblk_block_size(int N) {
   if (N <= kWNmax || N % 128 != 0) return 0;
-  for (int bs = kWNmax; bs >= 128; bs -= 128)
+  for (int bs = kWblkMaxK; bs >= 128; bs -= 128)
     if (N % bs == 0) return bs;
   return 0;
 }

@@ -65,7 +65,7 @@ cudaError_t wtc_setup(size_t smem_gj32);
 
 // ---- block Gauss-Jordan for N beyond kWNmax (kernels_wtc.cu) ----------------------
 // Arguments of k_oz_panel_gemm: C = A B (accumulate 0) or C -= A B (1) from the digits
-// of an M x K and a K x Nc panel (M a multiple of 128, Nc of kWTN, K of 16 and <= kWNmax).
+// of an M x K and a K x Nc panel (M a multiple of 128, Nc of kWTN, K of 16 and <= kWblkMaxK).
 struct PanelGemmArgs {
   const uint16_t* Asl;
   const uint16_t* Bsl;
@@ -93,7 +93,10 @@ struct WblkBuffers {
 };
 // refinements of the FP32 inverse of each pivot block
 constexpr int kWblkRefinements = 4;
-// Pivot block size for N (the largest multiple of 128 up to kWNmax dividing N), or 0
+// largest pivot block: the panel products keep one accumulator per level over both K
+// halves, exact for levels 0..5 up to 256 complex terms
+constexpr int kWblkMaxK = 256;
+// Pivot block size for N (the largest multiple of 128 up to kWblkMaxK dividing N), or 0
 // when N needs no blocks (N <= kWNmax) or has none (N not a multiple of 128).
 int wblk_block_size(int N);
 cudaError_t wblk_setup(size_t smem_gj32_bs);

@@ -75,8 +75,8 @@ class Sys:
         # N_PB of 128, 256 or 384 selects the tensor-core inverse unless the plan asks for Gauss-Jordan
         n = cell.n_pb_total
         assert self.plan.info["w_tensor"] == int(n % 128 == 0 and n <= 384 and plan_kw.get("w_solver") != "gauss_jordan")
-        # beyond 384: block Gauss-Jordan over the largest pivot block of 384, 256 or 128 dividing N_PB
-        bs = next((b for b in (384, 256, 128) if n > 384 and n % b == 0), 0)
+        # beyond 384: block Gauss-Jordan over the largest pivot block of 256 or 128 dividing N_PB
+        bs = next((b for b in (256, 128) if n > 384 and n % b == 0), 0)
         assert self.plan.info["w_block"] == (bs if plan_kw.get("w_solver") != "gauss_jordan" else 0)
         # the FP64 Sigma takes its W~ C^b stage from the tensor cores for K <= 64 unless the plan
         # asks for FP64 only
@@ -146,7 +146,7 @@ def system(name):
             _CACHE[name] = Sys(synth.make_config(2, atoms=8, cutoff=5.0, n_tau=12))
         elif name == "c2_16_blk":  # N_PB 1024: four pivot blocks of 256
             _CACHE[name] = Sys(synth.make_config(2, atoms=16, cutoff=5.0, n_tau=12))
-        elif name == "c2_16_k48_blk":  # N_PB 768: two pivot blocks of 384
+        elif name == "c2_16_k48_blk":  # N_PB 768: three pivot blocks of 256
             _CACHE[name] = Sys(synth.make_config(2, atoms=16, cutoff=5.0, n_tau=12,
                                                  species=[synth.Species("spd", 9, 48, None)]))
         elif name == "c1_far_fp64":

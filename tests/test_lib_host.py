@@ -135,7 +135,8 @@ def test_w_solve_mode(gwlib):
 def test_w_solver_choice(gwlib):
     """The tensor-core inverse is chosen for N_PB in {128, 256, 384} only (the range in
     which its FP32 level sums are exact), block Gauss-Jordan over such pivot blocks for
-    larger multiples of 128; FP64 Gauss-Jordan otherwise or when asked for."""
+    larger multiples of 128 (pivot blocks of 256 or 128); FP64 Gauss-Jordan otherwise or
+    when asked for."""
     from paper_1911_05633_gb300 import gw
     c1 = synth.make_config(1, build=False)
     c1._draw_basis(np.random.default_rng(0))
@@ -146,13 +147,13 @@ def test_w_solver_choice(gwlib):
     c2._draw_basis(np.random.default_rng(0))
     assert c2.n_pb_total == 512
     assert gw.Plan.from_cell(c2, host_only=True).info["w_tensor"] == 0
-    # beyond 384: block Gauss-Jordan over the largest pivot block of 384, 256, 128 dividing N_PB
+    # beyond 384: block Gauss-Jordan over the largest pivot block of 256 or 128 dividing N_PB
     assert gw.Plan.from_cell(c2, host_only=True).info["w_block"] == 256
     assert gw.Plan.from_cell(c2, host_only=True, w_solver="gauss_jordan").info["w_block"] == 0
     assert gw.Plan.from_cell(c1, host_only=True).info["w_block"] == 0
     c72 = synth.make_config(2, build=False)
     c72._draw_basis(np.random.default_rng(0))
-    assert c72.n_pb_total == 4608 and gw.Plan.from_cell(c72, host_only=True).info["w_block"] == 384
+    assert c72.n_pb_total == 4608 and gw.Plan.from_cell(c72, host_only=True).info["w_block"] == 256
     mixed = synth.mixed_species_cell(n_tau=10)
     assert mixed.n_pb_total % 128 != 0
     assert gw.Plan.from_cell(mixed, host_only=True).info["w_tensor"] == 0
