@@ -48,10 +48,10 @@ TRAFFIC = {
     # bench.py --atoms 8 captures (profiles/k_contract_diamond8_small.md): 352 entries of the
     # same species as the 72-atom cell; units are (entry, node) pairs: 352 x 64 for Sigma,
     # 352 x 32 computed nodes for P (each writing its node and the mirrored one)
-    "k_contract_s_tc": {"file": "kernels_contract.cu", "src_sha": "d086e265316d2289",
-                        "bytes_per_unit": (1.506191e9 + 0.031040e9) / (352 * 64)},
-    "k_contract_p_tc": {"file": "kernels_contract.cu", "src_sha": "d086e265316d2289",
-                        "bytes_per_unit": (0.029749e9 + 1.461140e9) / (352 * 32)},
+    "k_contract_s_tc": {"file": "kernels_contract.cu", "src_sha": "67b0441118f621b0",
+                        "bytes_per_unit": (1.506173e9 + 0.031087e9) / (352 * 64)},
+    "k_contract_p_tc": {"file": "kernels_contract.cu", "src_sha": "67b0441118f621b0",
+                        "bytes_per_unit": (0.029668e9 + 1.465074e9) / (352 * 32)},
 }
 
 

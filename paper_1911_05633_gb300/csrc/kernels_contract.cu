@@ -238,8 +238,8 @@ __device__ bool p_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
   {
     const double2* Gin = S.G + E.off_orb * nt;
     for (int x = t; x < na * nb; x += kTG) {
-      const double2 g1 = Gin[(long long)it * na * nb + x];
-      const double2 g2 = Gin[(long long)im * na * nb + x];
+      const double2 g1 = __ldg(Gin + (long long)it * na * nb + x);
+      const double2 g2 = __ldg(Gin + (long long)im * na * nb + x);
       G1[x] = make_float2(d2f(g1.x), d2f(g1.y));
       const int L2 = x / nb, L3 = x - L2 * nb;
       G2t[L3 * na + L2] = make_float2(d2f(g2.x), -d2f(g2.y));
@@ -388,7 +388,7 @@ __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
     const int gs = S.g_fixed >= 0 ? S.g_fixed : it;
     const double2* Gin = S.G + E.off_orb * S.g_slices + (long long)gs * na * nb;
     for (int x = t; x < na * nb; x += kTG) {
-      const double2 gv = Gin[x];
+      const double2 gv = __ldg(Gin + x);
       c.Gs[x] = make_float2(d2f(gv.x), d2f(gv.y));
     }
   }
@@ -418,8 +418,8 @@ __device__ bool s_unit(const GCtx& c, const CSys& S, const DevEntry& E, int it, 
         for (int u2 = 0; u2 < 4; ++u2) {
           float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
           const int k = kk + 2 * u2;
-          if (k < Kb) { const double2 w = wrow[k]; a0 = d2f(w.x); b0 = d2f(w.y); }
-          if (k + 1 < Kb) { const double2 w = wrow[k + 1]; a1 = d2f(w.x); b1 = d2f(w.y); }
+          if (k < Kb) { const double2 w = __ldg(wrow + k); a0 = d2f(w.x); b0 = d2f(w.y); }
+          if (k + 1 < Kb) { const double2 w = __ldg(wrow + k + 1); a1 = d2f(w.x); b1 = d2f(w.y); }
           split3x2(a0, a1, pk[0][u2], pk[1][u2], pk[2][u2]);
           split3x2(b0, b1, pk[3][u2], pk[4][u2], pk[5][u2]);
         }
