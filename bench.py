@@ -8,15 +8,16 @@ atom, 2x2x2 k-mesh, beta = 1000, 64 tau nodes, 12-bohr cutoff: 3312 pair entries
   W~(R,i nu) -> W~(R,tau) -> Sigma(R,tau) + Sigma_x        (rows a6, a7)
   -> Sigma(R,i omega) -> Sigma(k,i omega), Sigma_x(k)      (row a8)
 The W solve between P(R,i nu) and W~(R,i nu) (Eq. W_1, with the dense momentum-space
-halves of rows a4 and a6 that stream inside it) is timed apart, as the metric states;
-at this size (N_PB = 4608) W~(R,i nu) and v(R) are seeded inputs of the plan's shapes.
+halves of rows a4 and a6 that stream inside it) is timed apart, as the metric states
+(`w_solve`: the same cell's solve on the P of its own FP64 rows); inside the rows
+W~(R,i nu) and v(R) are seeded inputs of the plan's shapes.
 Inputs G(k,tau), W~(R,i nu) and v(R) are resident in HBM when the timed region starts.
 
 `value` is P+Sigma sweeps per second in mixed precision (BF16x3 contractions with FP32
 accumulation, FP64-accurate transforms), summed over ranks (weak scaling: each rank
 runs its own replica; the sweep does not shard).  The FP64 path of the same rows is
-timed beside it (`fp64`), and the 8-atom workload's whole sweep with its W solve is
-kept as `full_sweep_8_atoms`.  `--impl reference` times the FP64 CPU oracle on a
+timed beside it (`fp64`), the 8-atom workload's whole sweep with its W solve is kept as
+`full_sweep_8_atoms`, the batched uneven systems as `batched_uneven_systems`.  `--impl reference` times the FP64 CPU oracle on a
 bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
@@ -1192,7 +1193,7 @@ def run_batch3(args, local, peaks):
     return out
 
 
-def run_w_solve(args, local):
+def run_w_solve(args, local, cell=None):
     """The W solve of Eq. W_1 on the configuration-2 cell (N_PB = 64 x atoms): P(R, i nu)
     from the cell's own FP64 rows a1-a3, v(q) from the cell, W~(R, i nu) by the plan's
     inverse (block Gauss-Jordan over tensor-core pivot inverses beyond N_PB = 384).  One
@@ -1204,7 +1205,8 @@ def run_w_solve(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
-    cell = synth.make_config(2, atoms=args.atoms)
+    if cell is None:
+        cell = synth.make_config(2, atoms=args.atoms)
     vq, _ = cell.coulomb()
     t_host = time.perf_counter() - t0
     plan = gw.Plan.from_cell(cell, device=local, w_solver=args.w_solver,
@@ -1453,8 +1455,14 @@ def main():
             peaks = {}
         # extra blocks: each on a device emptied of the previous one's plans and buffers;
         # a failure is recorded in the line instead of losing the line
+        def w_solve():  # the W solve of the same cell (Eq. W_1), timed apart from the rows
+            r = run_w_solve(args, local, cell)
+            return {k: r[k] for k in ("value", "unit", "config", "ms_per_inverse", "fp64_equivalent_tflops",
+                                      "finite")} | {"kernels": dict(list(r["kernels"].items())[:3])}
+
         for key, fn in (("full_sweep_8_atoms", lambda: run_full(args, local)[0]),
-                        ("batched_uneven_systems", lambda: run_batch3(args, local, peaks))):
+                        ("batched_uneven_systems", lambda: run_batch3(args, local, peaks)),
+                        ("w_solve", w_solve)):
             release_device()
             try:
                 out[key] = fn()
