@@ -1092,8 +1092,9 @@ def release_device():
 def run_batch3(args, local, peaks):
     """The mixed P and Sigma contractions of the 16-system batch family (15 diamond-like
     supercells of 8 to 56 atoms with different meshes and cutoffs, and the 56-atom layered
-    perovskite-like cell) as one persistent launch each (gw_batch_*), autotuned, captured in
-    a CUDA graph and replayed; beside it the same contractions launched system by system.
+    perovskite-like cell) as one persistent launch per shape class each (gw_batch_*),
+    autotuned, captured in a CUDA graph and replayed; beside it the same contractions
+    launched system by system.
     Inputs: G(R, tau) from each cell's G(k, tau), W~(R, tau) seeded.  Checks that every
     system's result is the same bits in the batch and alone."""
     import torch
@@ -1182,6 +1183,7 @@ def run_batch3(args, local, peaks):
                         "unit": "GB/s", "frac": round(byt / (ms_batch * 1e-3) / 1e9 / hbm, 4) if hbm else None,
                         "algorithmic_bytes": byt, "note": "P and Sigma launches together, algorithmic bytes of both"},
            "tuned": {k: info[k] for k in ("groups_p", "groups_s", "kc_p", "kc_s", "order_p", "order_s")},
+           "launch_classes": info["n_classes"],
            "tune_s": round(t_tune, 2), "setup_s": round(t_setup, 1), "batched_equals_alone_bitwise": bool(same),
            "units": {"P": info["n_units_p"], "Sigma": info["n_units_s"]}, "steps": args.steps,
            "l2": "256 MB buffer written before each timed step"}

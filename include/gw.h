@@ -318,8 +318,10 @@ const char* gw_last_error(void);
  * contractions (Eqs. P_MM and S_MM) run as ONE persistent launch each: a queue of
  * (system, pair entry, tau node) units drained by one resident block per SM, so that
  * systems with different atom counts, pair lists and basis sizes share the GPU without
- * one launch per system.  The batch holds its unit queue and launch configuration; the
- * plans must outlive it.  Results are those of gw_polarizability_tau and
+ * one launch per system.  Plans whose contractions take the same launch shape (thread
+ * groups, hi x hi accumulators) form a class; each class has its own unit queue and
+ * launch configuration, and a batch call is one launch per class.  The plans must
+ * outlive the batch.  Results are those of gw_polarizability_tau and
  * gw_self_energy_tau (without exchange) with GW_MIXED on each plan alone. */
 #define GW_BATCH_MAX 24
 typedef struct gw_batch_s* gw_batch_t;
@@ -331,6 +333,8 @@ typedef struct {
   int kc_p, kc_s;                  /* reduction chunk (product-basis or orbital-pair columns) */
   int order_p, order_s;            /* unit order: 0 by shape class, 1 heaviest first */
   int tuned;                       /* 1 after gw_batch_tune */
+  int n_classes;                   /* launch classes (launches per contraction); the groups, kc and
+                                      order fields above are the first class's */
 } gw_batch_info;
 
 /* GW_ERR_ARG for n_plans outside [1, GW_BATCH_MAX], plans on different devices or host-only

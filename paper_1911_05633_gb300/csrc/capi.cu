@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1362,15 +1363,23 @@ extern "C" gw_status gw_screened_W_iw_noalloc(gw_plan_t p, const void* P_R_iw, c
 // Batches of systems: the GW_MIXED contractions of several plans in one queue launch
 // ---------------------------------------------------------------------------------------
 
-struct gw_batch_s {
-  std::vector<gw_plan_s*> plans;
-  int device = 0;
+// One shape class of a batch: the plans whose contractions take the same launch shape
+// (thread groups and hi x hi accumulators of each stage), with their own unit queues and
+// configurations; a batch launch is one kernel launch per class.
+struct BatchClass {
+  std::vector<int> sys;  // plan indices of the batch
   int ncols_p = 0, kd_p = 0, ncols_s = 0, kd_s = 0;
   gw::CConfig cfgP, cfgS;
   int orderP = 0, orderS = 0;
   gw::CUnit* d_unitsP = nullptr;
   gw::CUnit* d_unitsS = nullptr;
   int nP = 0, nS = 0;
+};
+
+struct gw_batch_s {
+  std::vector<gw_plan_s*> plans;
+  int device = 0;
+  std::vector<BatchClass> cls;
   int* d_counter = nullptr;
   int* d_status = nullptr;
   bool tuned = false;
@@ -1378,13 +1387,13 @@ struct gw_batch_s {
 
 namespace {
 
-// The batch's units of one contraction in the given order: 0 grouped by shape class
-// (species pair and basis size, so that consecutive units share their B operand), 1 the
-// heaviest first (so that the queue's tail is made of light units).
-std::vector<gw::CUnit> batch_units(const gw_batch_s* b, bool sigma, int order) {
+// The class's units of one contraction in the given order: 0 grouped by shape (species
+// pair and basis size, so that consecutive units share their B operand), 1 the heaviest
+// first (so that the queue's tail is made of light units).
+std::vector<gw::CUnit> batch_units(const gw_batch_s* b, const BatchClass& k, bool sigma, int order) {
   std::vector<gw::CUnit> u;
   std::vector<long long> key;
-  for (int i = 0; i < (int)b->plans.size(); ++i) {
+  for (int i : k.sys) {
     const gw::HostPlan& h = b->plans[i]->h;
     for (const gw::CUnit& x : gw::contract_units(h, i, sigma)) {
       u.push_back(x);
@@ -1398,24 +1407,24 @@ std::vector<gw::CUnit> batch_units(const gw_batch_s* b, bool sigma, int order) {
     }
   }
   std::vector<size_t> idx(u.size());
-  for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+  for (size_t q = 0; q < idx.size(); ++q) idx[q] = q;
   std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return key[x] < key[y]; });
   std::vector<gw::CUnit> out(u.size());
-  for (size_t k = 0; k < idx.size(); ++k) out[k] = u[idx[k]];
+  for (size_t q = 0; q < idx.size(); ++q) out[q] = u[idx[q]];
   return out;
 }
 
-gw_status batch_upload_units(gw_batch_s* b, bool sigma, int order) {
-  const std::vector<gw::CUnit> u = batch_units(b, sigma, order);
-  gw::CUnit*& d = sigma ? b->d_unitsS : b->d_unitsP;
+gw_status batch_upload_units(gw_batch_s* b, BatchClass& k, bool sigma, int order) {
+  const std::vector<gw::CUnit> u = batch_units(b, k, sigma, order);
+  gw::CUnit*& d = sigma ? k.d_unitsS : k.d_unitsP;
   if (!d) {
     gw_status st = upload(&d, nullptr, u.size() * sizeof(gw::CUnit));
     if (st != GW_OK) return st;
   }
   GW_CUDA(cudaMemcpy(d, u.data(), u.size() * sizeof(gw::CUnit), cudaMemcpyHostToDevice));
   GW_CUDA(gw::uploads_landed());
-  (sigma ? b->nS : b->nP) = (int)u.size();
-  (sigma ? b->orderS : b->orderP) = order;
+  (sigma ? k.nS : k.nP) = (int)u.size();
+  (sigma ? k.orderS : k.orderP) = order;
   return GW_OK;
 }
 
@@ -1451,17 +1460,40 @@ gw_status gw_batch_create(const gw_plan_t* plans, int n_plans, gw_batch_t* out) 
       return GW_ERR_UNSUPPORTED;
     }
     b->plans.push_back(p);
-    b->ncols_p = std::max(b->ncols_p, p->ct.np_max);
-    b->kd_p = std::max(b->kd_p, p->ct.kd_max);
-    b->ncols_s = std::max(b->ncols_s, p->ct.nj_max);
-    b->kd_s = std::max(b->kd_s, p->ct.kds_max);
   }
   b->device = plans[0]->device;
   DeviceGuard guard(b->device);
-  gw_status st = gw::contract_config(false, b->ncols_p, b->kd_p, b->cfgP, b->device);
-  if (st == GW_OK) st = gw::contract_config(true, b->ncols_s, b->kd_s, b->cfgS, b->device);
-  if (st == GW_OK) st = batch_upload_units(b, false, 0);
-  if (st == GW_OK) st = batch_upload_units(b, true, 0);
+  // shape classes: plans whose own configurations agree on the thread groups and the hi x hi
+  // accumulators of both stages share a class (and one launch per contraction); a wide plan
+  // then no longer sets the shape of every other plan's launch
+  gw_status st = GW_OK;
+  std::vector<std::array<int, 4>> keys;
+  for (int i = 0; i < n_plans && st == GW_OK; ++i) {
+    const gw_plan_s* p = plans[i];
+    gw::CConfig cp, cs;
+    st = gw::contract_config(false, p->ct.np_max, p->ct.kd_max, cp, b->device);
+    if (st == GW_OK) st = gw::contract_config(true, p->ct.nj_max, p->ct.kds_max, cs, b->device);
+    if (st != GW_OK) break;
+    const std::array<int, 4> key{cp.groups, cp.n_hh, cs.groups, cs.n_hh};
+    size_t c = 0;
+    while (c < keys.size() && keys[c] != key) ++c;
+    if (c == keys.size()) {
+      keys.push_back(key);
+      b->cls.emplace_back();
+    }
+    BatchClass& k = b->cls[c];
+    k.sys.push_back(i);
+    k.ncols_p = std::max(k.ncols_p, p->ct.np_max);
+    k.kd_p = std::max(k.kd_p, p->ct.kd_max);
+    k.ncols_s = std::max(k.ncols_s, p->ct.nj_max);
+    k.kd_s = std::max(k.kd_s, p->ct.kds_max);
+  }
+  for (BatchClass& k : b->cls) {
+    if (st == GW_OK) st = gw::contract_config(false, k.ncols_p, k.kd_p, k.cfgP, b->device);
+    if (st == GW_OK) st = gw::contract_config(true, k.ncols_s, k.kd_s, k.cfgS, b->device);
+    if (st == GW_OK) st = batch_upload_units(b, k, false, 0);
+    if (st == GW_OK) st = batch_upload_units(b, k, true, 0);
+  }
   if (st == GW_OK) st = upload(&b->d_counter, nullptr, 16);
   if (st == GW_OK) st = upload(&b->d_status, nullptr, 16);
   if (st == GW_OK && cudaMemset(b->d_status, 0, 16) != cudaSuccess) st = GW_ERR_CUDA;
@@ -1478,8 +1510,10 @@ gw_status gw_batch_destroy(gw_batch_t b) {
   if (!b) return GW_OK;
   {
     DeviceGuard guard(b->device);
-    cudaFree(b->d_unitsP);
-    cudaFree(b->d_unitsS);
+    for (BatchClass& k : b->cls) {
+      cudaFree(k.d_unitsP);
+      cudaFree(k.d_unitsS);
+    }
     cudaFree(b->d_counter);
     cudaFree(b->d_status);
   }
@@ -1490,15 +1524,20 @@ gw_status gw_batch_destroy(gw_batch_t b) {
 gw_status gw_batch_query(gw_batch_t b, gw_batch_info* info) {
   if (!b || !info) return GW_ERR_ARG;
   info->n_plans = (int)b->plans.size();
-  info->n_units_p = b->nP;
-  info->n_units_s = b->nS;
-  info->groups_p = b->cfgP.groups;
-  info->groups_s = b->cfgS.groups;
-  info->kc_p = b->cfgP.kc;
-  info->kc_s = b->cfgS.kc;
-  info->order_p = b->orderP;
-  info->order_s = b->orderS;
+  info->n_units_p = info->n_units_s = 0;
+  for (const BatchClass& k : b->cls) {
+    info->n_units_p += k.nP;
+    info->n_units_s += k.nS;
+  }
+  const BatchClass& k0 = b->cls[0];
+  info->groups_p = k0.cfgP.groups;
+  info->groups_s = k0.cfgS.groups;
+  info->kc_p = k0.cfgP.kc;
+  info->kc_s = k0.cfgS.kc;
+  info->order_p = k0.orderP;
+  info->order_s = k0.orderS;
   info->tuned = b->tuned ? 1 : 0;
+  info->n_classes = (int)b->cls.size();
   return GW_OK;
 }
 
@@ -1509,7 +1548,11 @@ gw_status gw_batch_polarizability_tau(gw_batch_t b, const void* const* G_R, void
   DeviceGuard guard(b->device);
   gw::ActiveTimer timing(&b->plans[0]->timer);
   const gw::CBatch cb = batch_systems(b, G_R, nullptr, P_R);
-  return gw::contract_launch(false, b->cfgP, cb, b->d_unitsP, b->nP, b->d_counter, b->d_status, S(stream));
+  for (const BatchClass& k : b->cls) {
+    const gw_status st = gw::contract_launch(false, k.cfgP, cb, k.d_unitsP, k.nP, b->d_counter, b->d_status, S(stream));
+    if (st != GW_OK) return st;
+  }
+  return GW_OK;
 }
 
 gw_status gw_batch_self_energy_tau(gw_batch_t b, const void* const* G_R, const void* const* Wt_R,
@@ -1520,7 +1563,11 @@ gw_status gw_batch_self_energy_tau(gw_batch_t b, const void* const* G_R, const v
   DeviceGuard guard(b->device);
   gw::ActiveTimer timing(&b->plans[0]->timer);
   const gw::CBatch cb = batch_systems(b, G_R, Wt_R, Sig_R);
-  return gw::contract_launch(true, b->cfgS, cb, b->d_unitsS, b->nS, b->d_counter, b->d_status, S(stream));
+  for (const BatchClass& k : b->cls) {
+    const gw_status st = gw::contract_launch(true, k.cfgS, cb, k.d_unitsS, k.nS, b->d_counter, b->d_status, S(stream));
+    if (st != GW_OK) return st;
+  }
+  return GW_OK;
 }
 
 gw_status gw_batch_sync(gw_batch_t b, void* stream) {
@@ -1553,47 +1600,51 @@ gw_status gw_batch_tune(gw_batch_t b, const void* const* G_R, void* const* P_R, 
   for (int sig = 0; sig < 2 && result == GW_OK; ++sig) {
     const bool sigma = sig == 1;
     const gw::CBatch cb = sigma ? batch_systems(b, G_R, Wt_R, Sig_R) : batch_systems(b, G_R, nullptr, P_R);
-    const int ncols = sigma ? b->ncols_s : b->ncols_p, kd = sigma ? b->kd_s : b->kd_p;
-    float best = 1e30f;
-    gw::CConfig best_cfg = sigma ? b->cfgS : b->cfgP;
-    int best_order = 0;
-    for (int order = 0; order < 2 && result == GW_OK; ++order) {
-      if ((result = batch_upload_units(b, sigma, order)) != GW_OK) break;
-      for (int groups = 1; groups <= 2; ++groups) {
-        // the longest chunk that fits, and half of it
-        for (int half = 0; half < 2; ++half) {
-          gw::CConfig c;
-          if (gw::contract_config(sigma, ncols, kd, c, b->device, groups) != GW_OK || c.groups != groups) continue;
-          if (half) {
-            const int kc2 = (c.kc / 2) & ~15;
-            gw::CConfig c2;
-            if (kc2 < 16 || gw::contract_config(sigma, ncols, kd, c2, b->device, groups, kc2) != GW_OK ||
-                c2.kc == c.kc)
-              continue;
-            c = c2;
-          }
-          const gw::CUnit* du = sigma ? b->d_unitsS : b->d_unitsP;
-          const int nu = sigma ? b->nS : b->nP;
-          if ((result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st)) != GW_OK) break;
-          GW_CUDA(cudaEventRecord(e0, st));
-          for (int r = 0; r < reps && result == GW_OK; ++r)
-            result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st);
-          GW_CUDA(cudaEventRecord(e1, st));
-          GW_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          GW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (result == GW_OK && ms < best) {
-            best = ms;
-            best_cfg = c;
-            best_order = order;
+    // each class on its own: its launch is timed alone with every candidate
+    for (size_t ci = 0; ci < b->cls.size() && result == GW_OK; ++ci) {
+      BatchClass& k = b->cls[ci];
+      const int ncols = sigma ? k.ncols_s : k.ncols_p, kd = sigma ? k.kd_s : k.kd_p;
+      float best = 1e30f;
+      gw::CConfig best_cfg = sigma ? k.cfgS : k.cfgP;
+      int best_order = 0;
+      for (int order = 0; order < 2 && result == GW_OK; ++order) {
+        if ((result = batch_upload_units(b, k, sigma, order)) != GW_OK) break;
+        for (int groups = 1; groups <= 2; ++groups) {
+          // the longest chunk that fits, and half of it
+          for (int half = 0; half < 2; ++half) {
+            gw::CConfig c;
+            if (gw::contract_config(sigma, ncols, kd, c, b->device, groups) != GW_OK || c.groups != groups) continue;
+            if (half) {
+              const int kc2 = (c.kc / 2) & ~15;
+              gw::CConfig c2;
+              if (kc2 < 16 || gw::contract_config(sigma, ncols, kd, c2, b->device, groups, kc2) != GW_OK ||
+                  c2.kc == c.kc)
+                continue;
+              c = c2;
+            }
+            const gw::CUnit* du = sigma ? k.d_unitsS : k.d_unitsP;
+            const int nu = sigma ? k.nS : k.nP;
+            if ((result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st)) != GW_OK) break;
+            GW_CUDA(cudaEventRecord(e0, st));
+            for (int r = 0; r < reps && result == GW_OK; ++r)
+              result = gw::contract_launch(sigma, c, cb, du, nu, b->d_counter, b->d_status, st);
+            GW_CUDA(cudaEventRecord(e1, st));
+            GW_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            GW_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (result == GW_OK && ms < best) {
+              best = ms;
+              best_cfg = c;
+              best_order = order;
+            }
           }
         }
       }
+      if (result != GW_OK) break;
+      (sigma ? k.cfgS : k.cfgP) = best_cfg;
+      // the chosen configuration's shared-memory opt-in (raised for every candidate already)
+      result = batch_upload_units(b, k, sigma, best_order);
     }
-    if (result != GW_OK) break;
-    (sigma ? b->cfgS : b->cfgP) = best_cfg;
-    // the chosen configuration's shared-memory opt-in (raised for every candidate already)
-    result = batch_upload_units(b, sigma, best_order);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -78,7 +78,7 @@ class GwPlanInfo(C.Structure):
 class GwBatchInfo(C.Structure):
     _fields_ = [("n_plans", C.c_int), ("n_units_p", C.c_longlong), ("n_units_s", C.c_longlong),
                 ("groups_p", C.c_int), ("groups_s", C.c_int), ("kc_p", C.c_int), ("kc_s", C.c_int),
-                ("order_p", C.c_int), ("order_s", C.c_int), ("tuned", C.c_int)]
+                ("order_p", C.c_int), ("order_s", C.c_int), ("tuned", C.c_int), ("n_classes", C.c_int)]
 
 
 class GwError(RuntimeError):

@@ -57,6 +57,7 @@ def test_batch_autotuner_and_graph_replay():
     S = [torch.empty_like(t) for t in S0]
     info = b.tune(G, P, W, S, reps=2)
     assert info["tuned"] == 1 and info["groups_p"] in (1, 2) and info["order_p"] in (0, 1)
+    assert 1 <= info["n_classes"] <= len(NAMES)
     for x in P + S:
         x.zero_()
     stream = torch.cuda.Stream()
