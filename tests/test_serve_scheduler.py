@@ -237,3 +237,29 @@ def test_requests_of_one_system_run_in_arrival_order():
         assert all(a.admitted < b.admitted for a, b in zip(mine, mine[1:]))
     srv.close()
     assert meter.used == 0
+
+
+def test_failed_bring_in_gives_its_range_back():
+    """A system whose making fails in the worker: the request loop raises the error, and
+    the reservation (its resident slot and its range of the pool) is gone."""
+    specs = [FakeSpec("a", 6, 0.002), FakeSpec("b", 6, 0.002)]
+    meter = Meter()
+    made = {"b": 0}
+
+    def factory(spec, st):
+        if spec.name == "b":
+            made["b"] += 1
+            if made["b"] > 1:
+                raise RuntimeError("bring-in failed")
+        return FakeSystem(spec, st, meter)
+
+    srv = Server({s.name: s for s in specs}, mem_cap_bytes=10, factory=factory, meter=meter)
+    srv.run([(0.0, "a"), (0.01, "b")])      # b's first making measures it; a is evicted
+    srv.run([(0.0, "a")])                   # a back in, b evicted
+    with pytest.raises(RuntimeError, match="bring-in failed"):
+        srv.run([(0.0, "b")])               # b made in a worker: fails there
+    assert "b" not in srv.resident and "b" not in srv.ranges
+    assert all(v is not None for v in srv.resident.values())
+    assert srv._dpool.free_bytes() + sum(n for _, n in srv.ranges.values()) == srv._dpool.size
+    srv.close()
+    assert meter.used == 0
